@@ -1,0 +1,32 @@
+"""CPU FP64 oracle for the Radau-collocation interior-point Newton step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+this package.  The product path (the CUDA library and its binding) never
+does, and this package imports nothing from the product path except the
+seeded input generator ``paper_2607_12201_gb300.workloads``, which holds none
+of the method's arithmetic.
+
+Plain, slow, obviously-correct restatement of the paper's method:
+
+* ``radau``  - collocation nodes, Lagrange basis and differentiation weights
+  (Eq. 3, "Collocation equation with condition independence").
+* ``nlp``    - the simultaneous-method NLP of Eq. 2 / Eq. 3 for mass-action
+  kinetics: objective, constraints, constraint Jacobian, Lagrangian Hessian.
+* ``kkt``    - the regularised primal-dual KKT matrix, its inertia and its
+  solution (dense Bunch-Kaufman or natural-order block elimination with
+  pivoted dense LU), with FP64 iterative refinement.
+* ``ipm``    - a filter line-search primal-dual interior-point method in the
+  form of Waechter & Biegler (2006), the algorithm family of the solver the
+  paper uses (Introduction: "a filter line-search interior point solver").
+* ``init``   - the initial state guess: an element-by-element collocation
+  forward sweep at theta0 (paper: initial guesses from a forward solve at
+  the nominal parameters, Section "Optimization framework configurations").
+
+Pins (tests/test_oracle_*.py, all ``-m "not gpu"``): closed-form Radau
+nodes; row sums / polynomial exactness of the differentiation weights; the
+(2,3) Pade closed form of collocation on linear ODEs; the h^(2K-1) endpoint
+order; finite-difference Jacobian and Hessian; brute-force dense solves and
+eigenvalue inertia on tiny KKT systems; an independent reduced-space
+Gauss-Newton solve of the linear-cascade estimation problem.
+"""

@@ -1,0 +1,97 @@
+"""Pins for the oracle's interior-point solve.
+
+The linear-cascade estimation problem discretised by Radau IIA collocation
+has an independent reduced-space form: for given theta the discrete states
+follow from the Radau IIA Runge-Kutta stage equations (published Butcher
+matrix) element by element, and the model output at an observation time is
+the cubic through the element's four points.  Minimising the weighted misfit
+over theta alone (scipy's Levenberg-Marquardt) must give the same optimum as
+the full-space interior-point method.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import least_squares
+
+from paper_2607_12201_gb300 import workloads as W
+from oracle import ipm
+from oracle.nlp import Problem
+
+S6 = math.sqrt(6.0)
+C_RADAU = np.array([(4 - S6) / 10, (4 + S6) / 10, 1.0])
+A_RADAU = np.array([
+    [(88 - 7 * S6) / 360, (296 - 169 * S6) / 1800, (-2 + 3 * S6) / 225],
+    [(296 + 169 * S6) / 1800, (88 + 7 * S6) / 360, (-2 - 3 * S6) / 225],
+    [(16 - S6) / 36, (16 + S6) / 36, 1.0 / 9.0]])
+
+
+def reduced_residuals(theta, inst):
+    t1, t2 = theta
+    A = np.array([[-t1, 0.0], [t1, -t2]])
+    h = inst.T / inst.N
+    # stage system: Z_k = z0 + h sum_l a_kl A Z_l  ->  (I - h A_rk (x) A) Z = 1 (x) z0
+    big = np.eye(6) - h * np.kron(A_RADAU, A)
+    z0 = inst.x0.copy()
+    pts = []
+    for i in range(inst.N):
+        Z = np.linalg.solve(big, np.tile(z0, 3)).reshape(3, 2)
+        pts.append((z0.copy(), Z))
+        z0 = Z[2]
+    res = []
+    for m in range(inst.M):
+        t = inst.obs_t[m]
+        i = min(max(int(math.ceil(t * inst.N / inst.T)) - 1, 0), inst.N - 1)
+        zs, Z = pts[i]
+        ts = i * h + h * np.concatenate([[0.0], C_RADAU])
+        vals = np.concatenate([[zs[inst.obs_s[m]]], Z[:, inst.obs_s[m]]])
+        yhat = np.polyval(np.polyfit(ts - i * h, vals, 3), t - i * h)
+        res.append((yhat - inst.obs_y[m]) / inst.obs_sigma[m])
+    return np.array(res)
+
+
+def test_cascade_ipm_matches_reduced_space_least_squares():
+    inst = W.config1()
+    ref = least_squares(reduced_residuals, inst.theta0, args=(inst,), xtol=1e-15, ftol=1e-15,
+                        gtol=1e-15, method="lm")
+    res = ipm.solve(inst, opt=ipm.Options(tol=1e-10))
+    assert res.status == ipm.SUCCESS
+    prob = Problem(inst)
+    th = res.theta(prob)
+    assert np.max(np.abs(th - ref.x) / np.abs(ref.x)) < 1e-8, (th, ref.x)
+    assert abs(res.phi - 0.5 * np.sum(ref.fun ** 2)) < 1e-8 * res.phi
+    # the estimate lands near the data-generating parameters (0.7, 0.3)
+    assert np.max(np.abs(th - [0.7, 0.3])) < 0.05
+
+
+def test_trivial_start_at_optimum_takes_few_iterations():
+    # Paper, "Trivial solves": started at the optimum the IPM still iterates,
+    # but only to re-centre the barrier.
+    inst = W.config1()
+    first = ipm.solve(inst)
+    th = first.x[-2:]
+    again = ipm.solve(inst.with_theta0(th))
+    assert again.status == ipm.SUCCESS
+    assert again.iterations <= first.iterations
+    assert np.max(np.abs(again.x[-2:] - th)) < 1e-5
+
+
+def test_kkt_conditions_hold_at_solution():
+    inst = W.config1()
+    res = ipm.solve(inst, opt=ipm.Options(tol=1e-9))
+    prob = Problem(inst)
+    ev = prob.evaluate(res.x, res.lam)
+    dual = ev["grad"] + ev["J"].T @ res.lam
+    dual[prob.nz:] += -res.zl + res.zu
+    assert np.max(np.abs(dual)) < 1e-8 * max(1.0, np.max(np.abs(res.lam)))
+    assert np.max(np.abs(ev["c"])) < 1e-10
+    # continuity constraints: z[i,0] = z[i-1,K]
+    z, _ = prob.split(res.x)
+    assert np.max(np.abs(z[1:, 0] - z[:-1, 3])) < 1e-10
+
+
+@pytest.mark.slow
+def test_small_random_network_converges():
+    inst = W.random_network(4, 6, n_obs=4, M=20, T=5.0, N=20, seed=41, theta0_spread=0.1)
+    res = ipm.solve(inst)
+    assert res.status in (ipm.SUCCESS, ipm.ACCEPTABLE)

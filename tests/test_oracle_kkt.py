@@ -1,0 +1,64 @@
+"""Pins for the oracle's KKT factorizations: brute-force solves and eigenvalue inertia."""
+import numpy as np
+import pytest
+
+from paper_2607_12201_gb300 import workloads as W
+from oracle import kkt
+from oracle.nlp import Problem
+
+
+def _kkt(prob, seed, delta_w, delta_c):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.2, 1.0, prob.n_x)
+    x[prob.nz:] = rng.uniform(-0.5, 0.5, prob.p) if prob.inst.logscale else rng.uniform(0.2, 1, prob.p)
+    lam = rng.standard_normal(prob.n_c)
+    ev = prob.evaluate(x, lam)
+    sigma = np.zeros(prob.n_x)
+    sigma[prob.nz:] = rng.uniform(0.1, 2.0, prob.p)
+    return kkt.assemble(ev["J"], ev["W"], sigma, delta_w, delta_c)
+
+
+CASES = [(lambda: W.small_network(n=2, r=3, N=2, seed=21), 0.0, 1e-8),
+         (lambda: W.small_network(n=3, r=4, N=3, seed=22), 1e-3, 1e-6),
+         (lambda: W.small_network(n=3, r=5, N=4, seed=23), 0.0, 1e-8),
+         (lambda: W.linear_cascade(N=4), 0.0, 1e-8)]
+
+
+@pytest.mark.parametrize("make,dw,dc", CASES)
+def test_dense_and_block_match_bruteforce(make, dw, dc):
+    prob = Problem(make())
+    K = _kkt(prob, 3, dw, dc)
+    A = K.toarray()
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(A.shape[0])
+    x_ref = np.linalg.solve(A, b)          # partial-pivoting LU, LAPACK gesv
+    ev = np.linalg.eigvalsh(A)
+    tol_ev = 1e-12 * np.max(np.abs(ev))
+    inertia_ref = (int(np.sum(ev > tol_ev)), int(np.sum(ev < -tol_ev)), int(np.sum(np.abs(ev) <= tol_ev)))
+    for mode in ["dense", "block"]:
+        fac = kkt.factor(K, prob, mode)
+        x = kkt.solve(fac, b)
+        assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+        assert tuple(fac.inertia) == inertia_ref, (mode, fac.inertia, inertia_ref)
+
+
+def test_inertia_detects_negative_curvature():
+    # KKT of min -x^2 s.t. nothing, bordered: a negative-curvature primal direction
+    prob = Problem(W.small_network(n=2, r=3, N=2, seed=31))
+    K = _kkt(prob, 5, 0.0, 1e-8)
+    A = K.toarray()
+    A[prob.nz, prob.nz] -= 1e6            # theta_0 diagonal strongly negative
+    import scipy.sparse as sp
+    K2 = sp.csr_matrix(A)
+    for mode in ["dense", "block"]:
+        fac = kkt.factor(K2, prob, mode)
+        ev = np.linalg.eigvalsh(A)
+        assert fac.inertia == (int(np.sum(ev > 0)), int(np.sum(ev < 0)), 0)
+        assert fac.inertia != (prob.n_x, prob.n_c, 0)
+
+
+def test_inertia_of_D_two_by_two_blocks():
+    d = np.array([[1.0, 0, 0, 0], [0, 0.0, 2.0, 0], [0, 2.0, 0.0, 0], [0, 0, 0, -3.0]])
+    assert kkt.inertia_of_D(d) == (2, 2, 0)
+    d2 = np.array([[2.0, 1.0], [1.0, 2.0]])
+    assert kkt.inertia_of_D(d2) == (2, 0, 0)
