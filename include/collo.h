@@ -1,0 +1,261 @@
+/*
+ * collo.h -- C ABI of the GB300 Radau-collocation interior-point Newton step.
+ *
+ * The library solves the parameter-estimation problem of the paper's Eq. 1
+ * (min Phi(z, theta) s.t. dz/dt = f(z, theta), z(0) = x0, theta_lo <= theta
+ * <= theta_hi) by the simultaneous method of Eq. 2: the states are kept as
+ * NLP variables on a collocation mesh of N elements with K + 1 interpolation
+ * points each, and the ODE becomes the collocation equations of Eq. 3.
+ * Interpolation points are right Radau (Radau IIA) roots with tau_0 = 0,
+ * so the continuity weights of Eq. 2c are b_j = delta_jK.  Only K = 3 is
+ * built.  One experiment (N_c = 1 in Eq. 1d / 2e).
+ *
+ * ---- Layouts (all arrays are C-contiguous, 0-based) ----------------------
+ *   n species, r reactions, p estimated parameters, N elements, K = 3,
+ *   n_x = n N (K+1) + p primal unknowns, n_c = n N (K+1) constraints.
+ *   x      = [ z[N][K+1][n], theta[p] ]       (z[i][j][s]: element i, point j)
+ *   lambda = c = [N][K+1][n]:
+ *            c[i][0][s]  continuity z[i][0][s] - z[i-1][K][s]  (Eq. 2c), or
+ *                        the initial condition z[0][0][s] - x0[s]  (Eq. 2d);
+ *            c[i][k][s]  collocation sum_j D[k][j] z[i][j][s] - h f_s(z[i][k], theta)
+ *                        for k = 1..K  (Eq. 3), h = T / N.
+ *   KKT vectors (rhs, solution) are [ x-part (n_x), lambda-part (n_c) ].
+ *
+ * ---- Memory ----------------------------------------------------------------
+ *   Every array argument may be host memory (pageable or pinned) or device
+ *   memory of the problem's GPU; the library copies with cudaMemcpyDefault.
+ *   Arguments are caller-owned and only read / written during the call.
+ *   collo_problem_create deep-copies its inputs; the problem owns all device
+ *   memory it allocates and collo_problem_destroy frees it.
+ *   Calls on one problem are not thread-safe; distinct problems may be used
+ *   concurrently from different threads (each has its own CUDA stream).
+ *
+ * ---- Errors ----------------------------------------------------------------
+ *   Every call returns a collo_status and never aborts; on failure
+ *   collo_last_error() returns a thread-local message.
+ */
+#ifndef COLLO_H
+#define COLLO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int collo_status;
+enum {
+  COLLO_OK = 0,                 /* solved to tol ("0" in the paper's Table 1) */
+  COLLO_ACCEPTABLE = 1,         /* solved to the acceptable level ("0A")      */
+  COLLO_ERR_INVALID_ARG = -1,   /* bad size, pointer, NaN input               */
+  COLLO_ERR_OOM = -2,           /* device allocation failed / over budget     */
+  COLLO_ERR_NUMERIC = -3,       /* non-finite values in an iterate            */
+  COLLO_ERR_INERTIA = -4,       /* inertia correction failed (delta_w > max)  */
+  COLLO_ERR_MAXITER = -5,       /* iteration cap                              */
+  COLLO_ERR_TIMEOUT = -6,       /* wall-time cap ("T")                        */
+  COLLO_ERR_LINESEARCH = -7,    /* step below alpha_min; no restoration ("R") */
+  COLLO_ERR_NOT_FACTORED = -8,  /* collo_kkt_solve before collo_kkt_factor    */
+  COLLO_ERR_DEVICE = -9,        /* CUDA runtime error                         */
+  COLLO_ERR_NOT_EVALUATED = -10 /* collo_kkt_factor before collo_eval         */
+};
+
+/* Arithmetic of the KKT factorization and solve. */
+enum {
+  COLLO_PRECISION_FP64 = 0,  /* everything in FP64 (the plain path)            */
+  COLLO_PRECISION_MIXED = 1  /* element blocks and block cyclic reduction in
+                                FP32, parameter Schur complement, residuals and
+                                refinement in FP64                              */
+};
+
+/* Mass-action reaction network: f_s(z, theta) = sum_r nu[s][r] k_r prod_{a in R_r} z_a,
+ * nu[s][r] = (#s among products of r) - (#s among reactants of r).
+ * Paper Eq. 1b (right-hand side f) and Eq. 1c (z(0) = x0, not theta-dependent). */
+typedef struct collo_network {
+  int n_species;              /* n >= 1                                        */
+  int n_reactions;            /* r >= 1                                        */
+  const int* reactants;       /* [r][2] species index or -1; 1 or 2 used slots;
+                                 a repeated index means stoichiometry 2         */
+  const int* products;        /* [r][2] species index or -1                    */
+  const int* param_index;     /* [r] estimated parameter driving k_r, or -1    */
+  const double* k_fixed;      /* [r] rate constant used when param_index = -1  */
+  int log10_params;           /* 1: k_r = 10^theta_q; 0: k_r = theta_q         */
+  const double* x0;           /* [n] initial state                             */
+  int n_params;               /* p >= 0                                        */
+  const double* theta_lo;     /* [p] lower bounds (finite), Eq. 1a             */
+  const double* theta_hi;     /* [p] upper bounds (finite), theta_lo < theta_hi */
+} collo_network;
+
+/* Linear observables: observable o measures species species[o]. */
+typedef struct collo_observables {
+  int n_observables;
+  const int* species;         /* [n_observables] */
+} collo_observables;
+
+/* Measurements (t_m, observable o_m, y_m, sigma_m), m = 0..M-1.
+ * Objective Phi = 1/2 sum_m ((yhat_m - y_m) / sigma_m)^2, Eq. 2a, with
+ * yhat_m = sum_j l_j(tau_m) z[i_m][j][s(o_m)]; i_m = ceil(t_m N / T) - 1
+ * clamped to [0, N-1], tau_m = t_m N / T - i_m (a boundary time belongs to the
+ * left element). */
+typedef struct collo_data {
+  int n_obs;                  /* M >= 0 */
+  const double* t;            /* [M] in [0, T] */
+  const int* observable;      /* [M] */
+  const double* y;            /* [M] */
+  const double* sigma;        /* [M] > 0 */
+} collo_data;
+
+/* Uniform collocation mesh, paper "collocation mesh t_ij = t_(i-1)0 + h_i tau_j". */
+typedef struct collo_mesh {
+  double T;                   /* horizon > 0 */
+  int N;                      /* elements >= 1 */
+  int K;                      /* interior collocation points; must be 3 */
+} collo_mesh;
+
+typedef struct collo_problem_options {
+  int precision;              /* COLLO_PRECISION_*, default for factor/solve */
+  void* stream;               /* cudaStream_t to run on, or NULL for an own stream */
+  int device;                 /* CUDA device ordinal (default 0) */
+  int reserved[7];
+} collo_problem_options;
+
+typedef struct collo_problem collo_problem;
+
+typedef struct collo_sizes {
+  int n, r, p, N, K, M;
+  int64_t n_x, n_c;
+  int levels;                 /* block cyclic reduction levels */
+  int64_t device_bytes;       /* device memory held by the problem */
+} collo_sizes;
+
+/* Outputs of collo_eval.  Any pointer may be NULL (not wanted).
+ * Jacobian of c (Eq. 2c, 2d, 3): the constant parts (D[k][j] I, +-I) are
+ * implied; the variable blocks are
+ *   jac_z[i][k-1][s][t]   = d c[i][k][s] / d z[i][k][t] - D[k][k] delta_st = -h df_s/dz_t
+ *   jac_theta[i][k-1][s][q] = d c[i][k][s] / d theta_q                      = -h df_s/dtheta_q
+ * Lagrangian Hessian W = obj_factor grad^2 Phi + sum lambda_c grad^2 c:
+ *   hess_zz[i][k-1][s][t], hess_ztheta[i][k-1][s][q]  (node k = 1..K),
+ *   hess_thth[q] (the theta-theta block is diagonal for mass action),
+ *   hess_obj[i][s][j][l]  = obj_factor d^2 Phi / d z[i][j][s] d z[i][l][s]. */
+typedef struct collo_eval_out {
+  double* phi;                /* [1]  Phi (without obj_factor) */
+  double* c;                  /* [n_c] */
+  double* grad;               /* [n_x] obj_factor * grad Phi */
+  double* jac_z;              /* [N][K][n][n] */
+  double* jac_theta;          /* [N][K][n][p] */
+  double* hess_zz;            /* [N][K][n][n] */
+  double* hess_ztheta;        /* [N][K][n][p] */
+  double* hess_thth;          /* [p] */
+  double* hess_obj;           /* [N][n][K+1][K+1] */
+} collo_eval_out;
+
+typedef struct collo_inertia {
+  int64_t n_pos, n_neg, n_zero;
+} collo_inertia;
+
+typedef struct collo_solve_info {
+  int refinement_sweeps;      /* iterative-refinement sweeps performed */
+  double residual;            /* final ||b - K x||_inf / max(1, ||b||_inf) */
+} collo_solve_info;
+
+typedef struct collo_ipm_options {
+  double tol;                 /* scaled KKT error, default 1e-6 (paper)            */
+  double acceptable_tol;      /* default 1e-4 (paper)                              */
+  int acceptable_iter;        /* default 15 (paper)                                */
+  int max_iter;               /* default 3000                                      */
+  double max_wall_time;       /* seconds, default 3600 (paper's 1 h cap)          */
+  int precision;              /* COLLO_PRECISION_*                                 */
+  double mixed_mu_switch;     /* MIXED: use FP64 factorization once mu < this
+                                 (default 1e-6); 0 = never switch                   */
+  int refine_max;             /* max iterative-refinement sweeps (default 10)      */
+  double refine_tol;          /* stop refining at ||r||/||b|| <= this (1e-12)       */
+  int verbose;                /* print an iteration log to stdout                  */
+  int reserved[8];
+} collo_ipm_options;
+
+typedef struct collo_result {
+  collo_status status;
+  int iterations;             /* Newton steps taken */
+  int factorizations;         /* KKT factorizations (inertia corrections included) */
+  int line_search_trials;
+  double phi;                 /* objective at the final iterate */
+  double kkt_error;           /* scaled optimality error E_0 at the final iterate */
+  double mu;                  /* final barrier parameter */
+  double wall_seconds;
+  double* theta;              /* [p]   out (may be NULL) */
+  double* x;                  /* [n_x] out (may be NULL) */
+  double* lambda;             /* [n_c] out (may be NULL) */
+} collo_result;
+
+/* Build a problem: validates and deep-copies the inputs to device memory,
+ * precomputes observation elements and interpolation weights.
+ * Returns INVALID_ARG on bad sizes, indices, K != 3, non-finite inputs or
+ * sigma <= 0; OOM / DEVICE on CUDA failure.  On success *out owns the
+ * device memory. */
+collo_status collo_problem_create(const collo_network* net, const collo_observables* obs,
+                                  const collo_data* data, const collo_mesh* mesh,
+                                  const collo_problem_options* opts, collo_problem** out);
+
+void collo_problem_destroy(collo_problem* prob);
+
+collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out);
+
+/* The problem's CUDA stream (cudaStream_t), for callers that time or order work. */
+void* collo_problem_stream(const collo_problem* prob);
+
+/* Evaluate objective, constraints, constraint Jacobian and Lagrangian Hessian
+ * at (x, lambda) on every (element, node) pair (the paper's SIMD evaluation of
+ * Eq. 3 and its first and second derivatives, Introduction and Section
+ * "Constructing GPU kernels").  x [n_x], lambda [n_c] (lambda may be NULL:
+ * zero multipliers).  The derivatives are also kept inside the problem for
+ * the next collo_kkt_factor.  Returns NUMERIC if a value is non-finite. */
+collo_status collo_eval(collo_problem* prob, const double* x, const double* lambda,
+                        double obj_factor, collo_eval_out* out);
+
+/* Factor the regularised KKT matrix of the most recent collo_eval:
+ *   [ W + diag(sigma) + delta_w I    J^T       ]
+ *   [ J                            -delta_c I  ]
+ * sigma [n_x] (host or device).  Element blocks are condensed onto their
+ * interface, the interface chain is reduced by block cyclic reduction, and
+ * the p x p parameter Schur complement is factored in FP64; every pivot is a
+ * static (state, multiplier) 2x2 block, so no pivoting is data dependent.
+ * *out receives the inertia from Sylvester's law (counts of pivot-block
+ * eigenvalue signs); the factorization does NOT correct it.
+ * precision: COLLO_PRECISION_* or -1 for the problem default.
+ * Returns NOT_EVALUATED if collo_eval has not run. */
+collo_status collo_kkt_factor(collo_problem* prob, const double* sigma, double delta_w,
+                              double delta_c, int precision, collo_inertia* out);
+
+/* Solve K sol = rhs with the last factorization, refining in FP64 with the
+ * exact KKT matrix until ||r||_inf <= refine_tol max(1, ||rhs||_inf) or
+ * refine_max sweeps.  rhs, sol: [n_x + n_c]; may alias.  info may be NULL.
+ * Returns NOT_FACTORED without a factorization. */
+collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol,
+                             int refine_max, double refine_tol, collo_solve_info* info);
+
+void collo_ipm_options_default(collo_ipm_options* opts);
+
+/* Solve the estimation problem from theta0 [p] with the filter line-search
+ * primal-dual interior-point method (paper Introduction; Waechter & Biegler
+ * 2006), all iterates resident on the device.  States start from a
+ * collocation forward sweep at theta0.  opts may be NULL (defaults).
+ * result->status is the solver outcome; the return value is the same. */
+collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
+                             const collo_ipm_options* opts, collo_result* result);
+
+/* Collocation forward sweep at theta (the IPM's initial states): writes
+ * z [N][K+1][n] into x_out [n_x] (theta copied into its tail).  Returns the
+ * number of elements whose Newton iteration failed in *failures. */
+collo_status collo_initial_states(collo_problem* prob, const double* theta, double* x_out,
+                                  int* failures);
+
+const char* collo_last_error(void);
+
+/* Library version string. */
+const char* collo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLLO_H */

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libcollo (include/collo.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy
+arrays / raw device pointers to the C structures and back.  Importing it
+loads ``libcollo.so`` and fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcollo.so")
+
+OK, ACCEPTABLE = 0, 1
+ERR_INVALID_ARG, ERR_OOM, ERR_NUMERIC, ERR_INERTIA = -1, -2, -3, -4
+ERR_MAXITER, ERR_TIMEOUT, ERR_LINESEARCH, ERR_NOT_FACTORED = -5, -6, -7, -8
+ERR_DEVICE, ERR_NOT_EVALUATED = -9, -10
+FP64, MIXED = 0, 1
+
+
+class ColloError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"collo status {status}: {msg}")
+        self.status = status
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class Network(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("n_reactions", C.c_int), ("reactants", _ip),
+                ("products", _ip), ("param_index", _ip), ("k_fixed", _dp),
+                ("log10_params", C.c_int), ("x0", _dp), ("n_params", C.c_int),
+                ("theta_lo", _dp), ("theta_hi", _dp)]
+
+
+class Observables(C.Structure):
+    _fields_ = [("n_observables", C.c_int), ("species", _ip)]
+
+
+class Data(C.Structure):
+    _fields_ = [("n_obs", C.c_int), ("t", _dp), ("observable", _ip), ("y", _dp), ("sigma", _dp)]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("T", C.c_double), ("N", C.c_int), ("K", C.c_int)]
+
+
+class ProblemOptions(C.Structure):
+    _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("device", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("p", C.c_int), ("N", C.c_int), ("K", C.c_int),
+                ("M", C.c_int), ("n_x", C.c_int64), ("n_c", C.c_int64), ("levels", C.c_int),
+                ("device_bytes", C.c_int64)]
+
+
+class EvalOut(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in
+                ["phi", "c", "grad", "jac_z", "jac_theta", "hess_zz", "hess_ztheta", "hess_thth",
+                 "hess_obj"]]
+
+
+class Inertia(C.Structure):
+    _fields_ = [("n_pos", C.c_int64), ("n_neg", C.c_int64), ("n_zero", C.c_int64)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("refinement_sweeps", C.c_int), ("residual", C.c_double)]
+
+
+class IpmOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("acceptable_tol", C.c_double), ("acceptable_iter", C.c_int),
+                ("max_iter", C.c_int), ("max_wall_time", C.c_double), ("precision", C.c_int),
+                ("mixed_mu_switch", C.c_double), ("refine_max", C.c_int),
+                ("refine_tol", C.c_double), ("verbose", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("factorizations", C.c_int),
+                ("line_search_trials", C.c_int), ("phi", C.c_double), ("kkt_error", C.c_double),
+                ("mu", C.c_double), ("wall_seconds", C.c_double), ("theta", C.c_void_p),
+                ("x", C.c_void_p), ("lambda_", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2607_12201_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.collo_problem_create.argtypes = [C.POINTER(Network), C.POINTER(Observables),
+                                         C.POINTER(Data), C.POINTER(Mesh),
+                                         C.POINTER(ProblemOptions), C.POINTER(P)]
+    lib.collo_problem_create.restype = C.c_int
+    lib.collo_problem_destroy.argtypes = [P]
+    lib.collo_problem_destroy.restype = None
+    lib.collo_problem_sizes.argtypes = [P, C.POINTER(Sizes)]
+    lib.collo_problem_sizes.restype = C.c_int
+    lib.collo_problem_stream.argtypes = [P]
+    lib.collo_problem_stream.restype = C.c_void_p
+    lib.collo_eval.argtypes = [P, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(EvalOut)]
+    lib.collo_eval.restype = C.c_int
+    lib.collo_kkt_factor.argtypes = [P, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                     C.POINTER(Inertia)]
+    lib.collo_kkt_factor.restype = C.c_int
+    lib.collo_kkt_solve.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                    C.POINTER(SolveInfo)]
+    lib.collo_kkt_solve.restype = C.c_int
+    lib.collo_ipm_options_default.argtypes = [C.POINTER(IpmOptions)]
+    lib.collo_ipm_options_default.restype = None
+    lib.collo_ipm_solve.argtypes = [P, C.c_void_p, C.POINTER(IpmOptions), C.POINTER(Result)]
+    lib.collo_ipm_solve.restype = C.c_int
+    lib.collo_initial_states.argtypes = [P, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.collo_initial_states.restype = C.c_int
+    lib.collo_last_error.argtypes = []
+    lib.collo_last_error.restype = C.c_char_p
+    lib.collo_version.argtypes = []
+    lib.collo_version.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.collo_last_error().decode()
+
+
+def _check(status, allow=(OK,)):
+    if status not in allow:
+        raise ColloError(status, last_error())
+    return status
+
+
+def _ptr(a):
+    """Address of a numpy array, a torch tensor or an int (device pointer)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Problem:
+    """One estimation problem resident on the GPU (wraps collo_problem)."""
+
+    def __init__(self, inst, precision: int = FP64, stream: int | None = None, device: int = 0):
+        self.inst = inst
+        species = np.unique(inst.obs_s)
+        obs_index = np.searchsorted(species, inst.obs_s)
+        self._keep = dict(
+            react=_i32(inst.react), prod=_i32(inst.prod), pidx=_i32(inst.pidx),
+            kfix=_f64(inst.kfix), x0=_f64(inst.x0), lo=_f64(inst.theta_lo),
+            hi=_f64(inst.theta_hi), species=_i32(species), t=_f64(inst.obs_t),
+            obs=_i32(obs_index), y=_f64(inst.obs_y), sig=_f64(inst.obs_sigma))
+        k = self._keep
+        dp = lambda a: a.ctypes.data_as(_dp)
+        ip = lambda a: a.ctypes.data_as(_ip)
+        net = Network(inst.n, inst.r, ip(k["react"]), ip(k["prod"]), ip(k["pidx"]), dp(k["kfix"]),
+                      int(inst.logscale), dp(k["x0"]), inst.p, dp(k["lo"]), dp(k["hi"]))
+        obs = Observables(len(species), ip(k["species"]))
+        data = Data(inst.M, dp(k["t"]), ip(k["obs"]), dp(k["y"]), dp(k["sig"]))
+        mesh = Mesh(float(inst.T), int(inst.N), int(inst.K))
+        opt = ProblemOptions(precision, stream, device)
+        h = C.c_void_p()
+        _check(lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh),
+                                        C.byref(opt), C.byref(h)))
+        self.h = h
+        s = Sizes()
+        _check(lib.collo_problem_sizes(self.h, C.byref(s)))
+        self.sizes = s
+        self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.n_x, self.n_c = int(s.n_x), int(s.n_c)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.collo_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self) -> int:
+        return lib.collo_problem_stream(self.h)
+
+    # --- evaluation ------------------------------------------------------------
+    def eval(self, x, lam=None, obj_factor: float = 1.0, outputs: bool = True):
+        """collo_eval on host arrays; returns a dict of host arrays."""
+        n, p, N = self.n, self.p, self.N
+        x = _f64(x)
+        lam = None if lam is None else _f64(lam)
+        out = {}
+        eo = EvalOut()
+        if outputs:
+            shapes = dict(phi=(1,), c=(self.n_c,), grad=(self.n_x,), jac_z=(N, 3, n, n),
+                          jac_theta=(N, 3, n, p), hess_zz=(N, 3, n, n),
+                          hess_ztheta=(N, 3, n, p), hess_thth=(p,), hess_obj=(N, n, 4, 4))
+            for name, shp in shapes.items():
+                out[name] = np.zeros(shp)
+                setattr(eo, name, out[name].ctypes.data)
+        st = lib.collo_eval(self.h, _ptr(x), _ptr(lam), float(obj_factor), C.byref(eo))
+        _check(st)
+        if outputs:
+            out["phi"] = float(out["phi"][0])
+        return out
+
+    def eval_raw(self, x_ptr, lam_ptr, obj_factor=1.0):
+        """collo_eval on raw (device or host) pointers, no outputs copied."""
+        return _check(lib.collo_eval(self.h, x_ptr, lam_ptr, float(obj_factor), None))
+
+    # --- KKT ---------------------------------------------------------------------
+    def kkt_factor(self, sigma=None, delta_w=0.0, delta_c=0.0, precision: int = -1):
+        inr = Inertia()
+        sig = None if sigma is None else (_f64(sigma) if isinstance(sigma, np.ndarray) else sigma)
+        _check(lib.collo_kkt_factor(self.h, _ptr(sig), float(delta_w), float(delta_c),
+                                    int(precision), C.byref(inr)))
+        return (int(inr.n_pos), int(inr.n_neg), int(inr.n_zero))
+
+    def kkt_solve(self, rhs, refine_max: int = 10, refine_tol: float = 1e-12, out=None):
+        info = SolveInfo()
+        if isinstance(rhs, np.ndarray):
+            rhs = _f64(rhs)
+            sol = np.zeros_like(rhs) if out is None else out
+        else:
+            sol = out
+        _check(lib.collo_kkt_solve(self.h, _ptr(rhs), _ptr(sol), int(refine_max),
+                                   float(refine_tol), C.byref(info)))
+        return sol, dict(sweeps=info.refinement_sweeps, residual=info.residual)
+
+    # --- solver ------------------------------------------------------------------
+    @staticmethod
+    def ipm_options(**kw) -> IpmOptions:
+        o = IpmOptions()
+        lib.collo_ipm_options_default(C.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def ipm_solve(self, theta0=None, want_x: bool = True, **kw):
+        th0 = _f64(self.inst.theta0 if theta0 is None else theta0)
+        o = self.ipm_options(**kw)
+        res = Result()
+        theta = np.zeros(self.p)
+        x = np.zeros(self.n_x) if want_x else None
+        lam = np.zeros(self.n_c) if want_x else None
+        res.theta = theta.ctypes.data
+        res.x = None if x is None else x.ctypes.data
+        res.lambda_ = None if lam is None else lam.ctypes.data
+        lib.collo_ipm_solve(self.h, th0.ctypes.data, C.byref(o), C.byref(res))
+        return dict(status=res.status, iterations=res.iterations,
+                    factorizations=res.factorizations, trials=res.line_search_trials,
+                    phi=res.phi, kkt_error=res.kkt_error, mu=res.mu, wall=res.wall_seconds,
+                    theta=theta, x=x, lam=lam)
+
+    def initial_states(self, theta):
+        x = np.zeros(self.n_x)
+        f = C.c_int(0)
+        _check(lib.collo_initial_states(self.h, _f64(theta).ctypes.data, x.ctypes.data,
+                                        C.byref(f)))
+        return x, int(f.value)
+
+
+def version() -> str:
+    return lib.collo_version().decode()

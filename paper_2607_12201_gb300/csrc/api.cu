@@ -1,0 +1,481 @@
+// C ABI of libcollo: problem construction, evaluation, KKT factor / solve.
+// The interior-point driver is in ipm.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "problem.cuh"
+
+namespace collo {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Radau IIA points for K = 3 (closed form) and D[k][j] = l_j'(tau_k) from the
+// barycentric weights w_j = 1 / prod_{l != j} (tau_j - tau_l):
+//   D[k][j] = (w_j / w_k) / (tau_k - tau_j),  D[k][k] = -sum_{j != k} D[k][j].
+static void radau_tables(double tau[NP], double D[NP][NP]) {
+  const double s6 = std::sqrt(6.0);
+  tau[0] = 0.0;
+  tau[1] = (4.0 - s6) / 10.0;
+  tau[2] = (4.0 + s6) / 10.0;
+  tau[3] = 1.0;
+  double w[NP];
+  for (int j = 0; j < NP; ++j) {
+    w[j] = 1.0;
+    for (int l = 0; l < NP; ++l)
+      if (l != j) w[j] /= (tau[j] - tau[l]);
+  }
+  for (int k = 0; k < NP; ++k) {
+    double sum = 0.0;
+    for (int j = 0; j < NP; ++j) {
+      if (j == k) continue;
+      D[k][j] = (w[j] / w[k]) / (tau[k] - tau[j]);
+      sum += D[k][j];
+    }
+    D[k][k] = -sum;
+  }
+}
+
+template <typename T>
+static collo_status alloc_factor(collo_problem* pr, FactorStore<T>& fs) {
+  if (fs.allocated) return COLLO_OK;
+  const DevProb& P = pr->P;
+  const size_t N = P.N, n = P.n, p = P.p;
+  DevArena& A = pr->arena;
+  DevFactor<T>& F = fs.F;
+  F.Lel = A.alloc<T>(N * 6 * n * P.ext);
+  F.Del = A.alloc<T>(N * 3 * n * 3);
+  F.Aif = A.alloc<T>(N * 4 * n * n);
+  F.Cpl = A.alloc<T>(N * n * n);
+  F.Bif = A.alloc<T>(N * 2 * n * p);
+  F.Lb = A.alloc<T>(N * 2 * n * P.bext);
+  F.Db = A.alloc<T>(N * n * 3);
+  F.Scon = A.alloc<double>(2 * N * p * p);
+  F.inert = A.alloc<int>(2 * N * 3);
+  F.Vint = A.alloc<T>(N * 6 * n);
+  F.Rif = A.alloc<T>(N * 2 * n);
+  F.Vb = A.alloc<T>(N * 2 * n);
+  F.Rth = A.alloc<double>(2 * N * p);
+  F.n_slabs = pr->n_slabs;
+  size_t w = factor_work_elems<T>(P, pr->n_slabs);
+  F.work = w ? A.alloc<T>(w) : nullptr;
+  if (!F.Lel || !F.Del || !F.Aif || !F.Cpl || !F.Bif || !F.Lb || !F.Db || !F.Scon || !F.inert ||
+      !F.Vint || !F.Rif || !F.Vb || !F.Rth || (w && !F.work)) {
+    set_error("device allocation failed for the factorization storage");
+    return COLLO_ERR_OOM;
+  }
+  fs.allocated = true;
+  return COLLO_OK;
+}
+
+collo_status ensure_factor_storage(collo_problem* pr, int precision) {
+  return precision == COLLO_PRECISION_MIXED ? alloc_factor(pr, pr->f32) : alloc_factor(pr, pr->f64);
+}
+
+static bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+}  // namespace collo
+
+using namespace collo;
+
+extern "C" {
+
+const char* collo_last_error(void) { return g_last_error.c_str(); }
+const char* collo_version(void) { return "collo 0.1 (sm_103a)"; }
+
+collo_status collo_problem_create(const collo_network* net, const collo_observables* obs,
+                                  const collo_data* data, const collo_mesh* mesh,
+                                  const collo_problem_options* opts, collo_problem** out) {
+  if (!out) { set_error("out is NULL"); return COLLO_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!net || !mesh || !data || !obs) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  const int n = net->n_species, r = net->n_reactions, p = net->n_params;
+  const int N = mesh->N, M = data->n_obs;
+  if (n < 1 || r < 1 || p < 0 || N < 1 || M < 0) { set_error("bad sizes"); return COLLO_ERR_INVALID_ARG; }
+  if (mesh->K != KC) { set_error("only K = 3 (Radau IIA) is built"); return COLLO_ERR_INVALID_ARG; }
+  if (!(mesh->T > 0) || !std::isfinite(mesh->T)) { set_error("T must be positive"); return COLLO_ERR_INVALID_ARG; }
+  if (!net->reactants || !net->products || !net->param_index || !net->k_fixed || !net->x0 ||
+      (p > 0 && (!net->theta_lo || !net->theta_hi))) {
+    set_error("NULL network array"); return COLLO_ERR_INVALID_ARG;
+  }
+  if (M > 0 && (!data->t || !data->observable || !data->y || !data->sigma || !obs->species)) {
+    set_error("NULL data array"); return COLLO_ERR_INVALID_ARG;
+  }
+  for (int j = 0; j < r; ++j) {
+    int a = net->reactants[2 * j], b = net->reactants[2 * j + 1];
+    if (a < 0 || a >= n || b < -1 || b >= n) { set_error("bad reactant index"); return COLLO_ERR_INVALID_ARG; }
+    for (int k = 0; k < 2; ++k) {
+      int s = net->products[2 * j + k];
+      if (s < -1 || s >= n) { set_error("bad product index"); return COLLO_ERR_INVALID_ARG; }
+    }
+    int q = net->param_index[j];
+    if (q < -1 || q >= p) { set_error("bad parameter index"); return COLLO_ERR_INVALID_ARG; }
+    if (q < 0 && !std::isfinite(net->k_fixed[j])) { set_error("non-finite fixed rate"); return COLLO_ERR_INVALID_ARG; }
+  }
+  if (!finite_all(net->x0, n)) { set_error("non-finite x0"); return COLLO_ERR_INVALID_ARG; }
+  for (int q = 0; q < p; ++q)
+    if (!std::isfinite(net->theta_lo[q]) || !std::isfinite(net->theta_hi[q]) ||
+        !(net->theta_lo[q] < net->theta_hi[q])) {
+      set_error("parameter bounds must be finite with lo < hi"); return COLLO_ERR_INVALID_ARG;
+    }
+  for (int m = 0; m < M; ++m) {
+    int o = data->observable[m];
+    if (o < 0 || o >= obs->n_observables) { set_error("bad observable index"); return COLLO_ERR_INVALID_ARG; }
+    int s = obs->species[o];
+    if (s < 0 || s >= n) { set_error("bad observed species"); return COLLO_ERR_INVALID_ARG; }
+    if (!std::isfinite(data->t[m]) || !std::isfinite(data->y[m]) || !(data->sigma[m] > 0) ||
+        !std::isfinite(data->sigma[m]) || data->t[m] < 0 || data->t[m] > mesh->T) {
+      set_error("bad measurement (non-finite, sigma <= 0 or t outside [0, T])");
+      return COLLO_ERR_INVALID_ARG;
+    }
+  }
+  int dev = opts ? opts->device : 0;
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaSetDevice failed (no CUDA device?)");
+    return COLLO_ERR_DEVICE;
+  }
+  std::unique_ptr<collo_problem> pr(new collo_problem());
+  pr->device = dev;
+  pr->precision = opts ? opts->precision : 0;
+  if (opts && opts->stream) {
+    pr->stream = (cudaStream_t)opts->stream;
+  } else {
+    COLLO_CUDA(cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking));
+    pr->own_stream = true;
+  }
+  DevProb& P = pr->P;
+  P.n = n; P.r = r; P.p = p; P.N = N; P.M = M;
+  P.m = 8 * n; P.ext = 8 * n + p; P.bext = 4 * n + p;
+  P.logscale = net->log10_params ? 1 : 0;
+  P.T = mesh->T; P.h = mesh->T / N;
+  radau_tables(P.tau, P.D);
+  pr->n_x = (int64_t)n * N * NP + p;
+  pr->n_c = (int64_t)n * N * NP;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  pr->n_slabs = std::max(1, std::min(N, 2 * std::max(1, sms)));
+
+  // host-side CSR structures (index bookkeeping only)
+  std::vector<int> nu_ptr(n + 1, 0), nu_r, rs_ptr(n + 1, 0), rs_r, pr_ptr(p + 1, 0), pr_r;
+  std::vector<double> nu_v;
+  {
+    std::vector<std::vector<std::pair<int, double>>> lists(n);
+    std::vector<std::vector<int>> cons(n);
+    std::vector<std::vector<int>> pl(p);
+    for (int j = 0; j < r; ++j) {
+      std::vector<double> nu(n, 0.0);
+      for (int k = 0; k < 2; ++k) {
+        int a = net->reactants[2 * j + k];
+        if (a >= 0) nu[a] -= 1.0;
+        int b = net->products[2 * j + k];
+        if (b >= 0) nu[b] += 1.0;
+      }
+      for (int s = 0; s < n; ++s)
+        if (nu[s] != 0.0) lists[s].push_back({j, nu[s]});
+      int a = net->reactants[2 * j], b = net->reactants[2 * j + 1];
+      cons[a].push_back(j);
+      if (b >= 0 && b != a) cons[b].push_back(j);
+      if (net->param_index[j] >= 0) pl[net->param_index[j]].push_back(j);
+    }
+    for (int s = 0; s < n; ++s) {
+      nu_ptr[s + 1] = nu_ptr[s] + (int)lists[s].size();
+      for (auto& e : lists[s]) { nu_r.push_back(e.first); nu_v.push_back(e.second); }
+      rs_ptr[s + 1] = rs_ptr[s] + (int)cons[s].size();
+      for (int j : cons[s]) rs_r.push_back(j);
+    }
+    for (int q = 0; q < p; ++q) {
+      pr_ptr[q + 1] = pr_ptr[q] + (int)pl[q].size();
+      for (int j : pl[q]) pr_r.push_back(j);
+    }
+  }
+  // observations: element from the same rule the kernels use, grouped by element
+  std::vector<int> oelem(M);
+  for (int m = 0; m < M; ++m) {
+    double u = data->t[m] * N / mesh->T;
+    int i = (int)std::ceil(u) - 1;
+    oelem[m] = std::min(std::max(i, 0), N - 1);
+  }
+  std::vector<int> order(M);
+  for (int m = 0; m < M; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return oelem[a] < oelem[b]; });
+  std::vector<int> obs_ptr(N + 1, 0), obs_s(M);
+  std::vector<double> obs_t(M), obs_y(M), obs_sig(M);
+  for (int k = 0; k < M; ++k) {
+    int m = order[k];
+    obs_ptr[oelem[m] + 1]++;
+    obs_s[k] = obs->species[data->observable[m]];
+    obs_t[k] = data->t[m];
+    obs_y[k] = data->y[m];
+    obs_sig[k] = data->sigma[m];
+  }
+  for (int i = 0; i < N; ++i) obs_ptr[i + 1] += obs_ptr[i];
+
+  DevArena& A = pr->arena;
+  auto up_i = [&](const int* h, size_t cnt) -> const int* {
+    int* d = A.alloc<int>(cnt);
+    if (d && cnt) cudaMemcpy(d, h, cnt * sizeof(int), cudaMemcpyDefault);
+    return d;
+  };
+  auto up_d = [&](const double* h, size_t cnt) -> const double* {
+    double* d = A.alloc<double>(cnt);
+    if (d && cnt) cudaMemcpy(d, h, cnt * sizeof(double), cudaMemcpyDefault);
+    return d;
+  };
+  P.react = up_i(net->reactants, 2 * (size_t)r);
+  P.prod = up_i(net->products, 2 * (size_t)r);
+  P.pidx = up_i(net->param_index, r);
+  P.kfix = up_d(net->k_fixed, r);
+  P.x0 = up_d(net->x0, n);
+  P.theta_lo = up_d(p ? net->theta_lo : nullptr, p);
+  P.theta_hi = up_d(p ? net->theta_hi : nullptr, p);
+  P.nu_ptr = up_i(nu_ptr.data(), n + 1);
+  P.nu_r = up_i(nu_r.data(), nu_r.size());
+  P.nu_v = up_d(nu_v.data(), nu_v.size());
+  P.rs_ptr = up_i(rs_ptr.data(), n + 1);
+  P.rs_r = up_i(rs_r.data(), rs_r.size());
+  P.pr_ptr = up_i(pr_ptr.data(), p + 1);
+  P.pr_r = up_i(pr_r.data(), pr_r.size());
+  P.obs_ptr = up_i(obs_ptr.data(), N + 1);
+  P.obs_s = up_i(obs_s.data(), M);
+  P.obs_y = up_d(obs_y.data(), M);
+  P.obs_sig = up_d(obs_sig.data(), M);
+  const double* d_obs_t = up_d(obs_t.data(), M);
+  double* obs_w = A.alloc<double>((size_t)M * NP);
+  int* obs_elem_chk = A.alloc<int>(M);
+  P.obs_w = obs_w;
+  const size_t NN = (size_t)N, nn = (size_t)n * n, np_ = (size_t)n * p;
+  DevEval& E = pr->E;
+  E.c = A.alloc<double>(pr->n_c);
+  E.grad = A.alloc<double>(pr->n_x);
+  E.JZ = A.alloc<double>(NN * KC * nn);
+  E.JT = A.alloc<double>(NN * KC * np_);
+  E.Wzz = A.alloc<double>(NN * KC * nn);
+  E.Wzt = A.alloc<double>(NN * KC * np_);
+  E.Wobj = A.alloc<double>(NN * n * NP * NP);
+  E.part = A.alloc<double>(NN * 4);
+  E.wtt_part = A.alloc<double>(NN * p);
+  E.red = A.alloc<double>(8);
+  E.wtt = A.alloc<double>(p);
+  DevSchur& S = pr->S;
+  S.S = A.alloc<double>((size_t)p * p);
+  S.Sd = A.alloc<double>(p);
+  S.xth = A.alloc<double>(p);
+  S.inertia = A.alloc<long long>(3);
+  S.diag = A.alloc<double>(p);
+  const size_t nk = pr->n_x + pr->n_c;
+  pr->sigma = A.alloc<double>(pr->n_x);
+  pr->kvec_a = A.alloc<double>(nk);
+  pr->kvec_b = A.alloc<double>(nk);
+  pr->kvec_r = A.alloc<double>(nk);
+  pr->kvec_c = A.alloc<double>(nk);
+  pr->thpart = A.alloc<double>(NN * p);
+  pr->npart = A.alloc<double>(NN * 2);
+  pr->scal = A.alloc<double>(64);
+  pr->red_parts = A.alloc<double>(256);
+  pr->x = A.alloc<double>(pr->n_x);
+  pr->lam = A.alloc<double>(pr->n_c);
+  pr->zl = A.alloc<double>(p);
+  pr->zu = A.alloc<double>(p);
+  pr->dz = A.alloc<double>(2 * (size_t)p);
+  pr->thx = A.alloc<double>(8 * (size_t)p + 8);
+  pr->fails = A.alloc<int>(1);
+  const size_t sweep_dim = 3 * (size_t)n;
+  if (sweep_dim * (sweep_dim + 1) * sizeof(double) > 200 * 1024)
+    pr->sweep_work = A.alloc<double>(sweep_dim * (sweep_dim + 1));
+  bool ok = P.react && P.prod && P.pidx && P.kfix && P.x0 && P.theta_lo && P.theta_hi &&
+            P.nu_ptr && P.nu_r && P.nu_v && P.rs_ptr && P.rs_r && P.pr_ptr && P.pr_r &&
+            P.obs_ptr && P.obs_s && P.obs_y && P.obs_sig && d_obs_t && obs_w && obs_elem_chk &&
+            E.c && E.grad && E.JZ && E.JT && E.Wzz && E.Wzt && E.Wobj && E.part && E.wtt_part &&
+            E.red && E.wtt && S.S && S.Sd && S.xth && S.inertia && S.diag && pr->sigma &&
+            pr->kvec_a && pr->kvec_b && pr->kvec_r && pr->kvec_c && pr->thpart && pr->npart &&
+            pr->scal && pr->red_parts && pr->x && pr->lam && pr->zl && pr->zu && pr->dz && pr->thx && pr->fails &&
+            (sweep_dim * (sweep_dim + 1) * sizeof(double) <= 200 * 1024 || pr->sweep_work);
+  if (!ok) { set_error("device allocation failed"); return COLLO_ERR_OOM; }
+  if (cudaMallocHost(&pr->hscal, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    return COLLO_ERR_OOM;
+  }
+  COLLO_CUDA(cudaMemsetAsync(pr->sigma, 0, pr->n_x * sizeof(double), pr->stream));
+  COLLO_CUDA(launch_obs_weights(P, M, N, mesh->T, d_obs_t, obs_elem_chk, obs_w, pr->stream));
+  COLLO_CUDA(cudaStreamSynchronize(pr->stream));
+  COLLO_CUDA(cudaGetLastError());
+  *out = pr.release();
+  return COLLO_OK;
+}
+
+void collo_problem_destroy(collo_problem* prob) {
+  if (!prob) return;
+  cudaSetDevice(prob->device);
+  cudaStreamSynchronize(prob->stream);
+  if (prob->hscal) cudaFreeHost(prob->hscal);
+  if (prob->own_stream) cudaStreamDestroy(prob->stream);
+  delete prob;
+}
+
+collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out) {
+  if (!prob || !out) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  out->n = prob->P.n; out->r = prob->P.r; out->p = prob->P.p; out->N = prob->P.N;
+  out->K = KC; out->M = prob->P.M; out->n_x = prob->n_x; out->n_c = prob->n_c;
+  out->levels = bcr_levels(prob->P.N);
+  out->device_bytes = (int64_t)prob->arena.bytes;
+  return COLLO_OK;
+}
+
+void* collo_problem_stream(const collo_problem* prob) { return prob ? (void*)prob->stream : nullptr; }
+
+collo_status collo_eval(collo_problem* prob, const double* x, const double* lambda,
+                        double obj_factor, collo_eval_out* out) {
+  if (!prob || !x) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  cudaStream_t st = prob->stream;
+  const DevProb& P = prob->P;
+  const DevEval& E = prob->E;
+  double* dx = prob->kvec_c;                    // staging for x
+  double* dl = prob->kvec_c + prob->n_x;       // staging for lambda
+  COLLO_CUDA(cudaMemcpyAsync(dx, x, prob->n_x * sizeof(double), cudaMemcpyDefault, st));
+  if (lambda)
+    COLLO_CUDA(cudaMemcpyAsync(dl, lambda, prob->n_c * sizeof(double), cudaMemcpyDefault, st));
+  else
+    COLLO_CUDA(cudaMemsetAsync(dl, 0, prob->n_c * sizeof(double), st));
+  COLLO_CUDA(launch_eval(P, E, dx, nullptr, 0.0, dl, obj_factor, true, st));
+  const size_t NN = P.N, nn = (size_t)P.n * P.n, np_ = (size_t)P.n * P.p;
+  if (out) {
+    auto cp = [&](double* dst, const double* src, size_t cnt) -> cudaError_t {
+      if (!dst || cnt == 0) return cudaSuccess;
+      return cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyDefault, st);
+    };
+    COLLO_CUDA(cp(out->phi, E.red, 1));
+    COLLO_CUDA(cp(out->c, E.c, prob->n_c));
+    COLLO_CUDA(cp(out->grad, E.grad, prob->n_x));
+    COLLO_CUDA(cp(out->jac_z, E.JZ, NN * KC * nn));
+    COLLO_CUDA(cp(out->jac_theta, E.JT, NN * KC * np_));
+    COLLO_CUDA(cp(out->hess_zz, E.Wzz, NN * KC * nn));
+    COLLO_CUDA(cp(out->hess_ztheta, E.Wzt, NN * KC * np_));
+    COLLO_CUDA(cp(out->hess_thth, E.wtt, P.p));
+    COLLO_CUDA(cp(out->hess_obj, E.Wobj, NN * P.n * NP * NP));
+  }
+  COLLO_CUDA(cudaMemcpyAsync(prob->hscal, E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  COLLO_CUDA(cudaStreamSynchronize(st));
+  prob->evaluated = true;
+  prob->factored = -1;
+  if (!std::isfinite(prob->hscal[0]) || !std::isfinite(prob->hscal[1])) {
+    set_error("non-finite objective or constraint values");
+    return COLLO_ERR_NUMERIC;
+  }
+  return COLLO_OK;
+}
+
+}  // extern "C"
+
+namespace collo {
+
+// Factor with the sigma already in prob->sigma; reads back the inertia.
+collo_status factor_internal(collo_problem* prob, double dw, double dc, int precision,
+                             long long inertia[3]) {
+  collo_status s = ensure_factor_storage(prob, precision);
+  if (s != COLLO_OK) return s;
+  cudaStream_t st = prob->stream;
+  if (precision == COLLO_PRECISION_MIXED)
+    COLLO_CUDA(launch_factor<float>(prob->P, prob->E, prob->sigma, dw, dc, prob->f32.F, prob->S, st));
+  else
+    COLLO_CUDA(launch_factor<double>(prob->P, prob->E, prob->sigma, dw, dc, prob->f64.F, prob->S, st));
+  COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 40, prob->S.inertia, 3 * sizeof(long long),
+                             cudaMemcpyDeviceToHost, st));
+  COLLO_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(inertia, prob->hscal + 40, 3 * sizeof(long long));
+  prob->factored = precision;
+  prob->fac_dw = dw;
+  prob->fac_dc = dc;
+  return COLLO_OK;
+}
+
+// Solve K sol = b (device vectors, may not alias) with FP64 iterative refinement.
+collo_status solve_internal(collo_problem* prob, const double* b, double* sol, int refine_max,
+                            double refine_tol, int* sweeps, double* resid) {
+  cudaStream_t st = prob->stream;
+  const DevProb& P = prob->P;
+  const size_t nk = prob->n_x + prob->n_c;
+  auto inner = [&](const double* rhs, double* out) -> cudaError_t {
+    if (prob->factored == COLLO_PRECISION_MIXED)
+      return launch_solve<float>(P, prob->f32.F, prob->S, rhs, out, st);
+    return launch_solve<double>(P, prob->f64.F, prob->S, rhs, out, st);
+  };
+  COLLO_CUDA(inner(b, sol));
+  int k = 0;
+  double rel = 0.0;
+  for (;;) {
+    COLLO_CUDA(launch_kkt_resid(P, prob->E, prob->sigma, prob->fac_dw, prob->fac_dc, sol,
+                                sol + prob->n_x, b, 1.0, b + prob->n_x, 1.0, prob->kvec_r,
+                                prob->thpart, prob->npart, nullptr, prob->scal + 8, st));
+    COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 8, prob->scal + 8, 3 * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+    COLLO_CUDA(cudaStreamSynchronize(st));
+    double rn = std::max(prob->hscal[8], prob->hscal[9]);
+    double bn = std::max(1.0, prob->hscal[10]);
+    rel = rn / bn;
+    if (!(rel > refine_tol) || k >= refine_max || !std::isfinite(rel)) break;
+    COLLO_CUDA(inner(prob->kvec_r, prob->kvec_c));
+    ++k;
+    COLLO_CUDA(launch_axpy(sol, prob->kvec_c, 1.0, nk, st));   // sol += correction
+  }
+  if (sweeps) *sweeps = k;
+  if (resid) *resid = rel;
+  if (!std::isfinite(rel)) { set_error("non-finite KKT solution"); return COLLO_ERR_NUMERIC; }
+  return COLLO_OK;
+}
+
+}  // namespace collo
+
+extern "C" {
+
+collo_status collo_kkt_factor(collo_problem* prob, const double* sigma, double delta_w,
+                              double delta_c, int precision, collo_inertia* out) {
+  if (!prob) { set_error("NULL problem"); return COLLO_ERR_INVALID_ARG; }
+  if (!prob->evaluated) { set_error("collo_eval has not run"); return COLLO_ERR_NOT_EVALUATED; }
+  if (!std::isfinite(delta_w) || !std::isfinite(delta_c) || delta_w < 0 || delta_c < 0) {
+    set_error("regularisation must be finite and >= 0"); return COLLO_ERR_INVALID_ARG;
+  }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  if (precision < 0) precision = prob->precision;
+  if (precision != COLLO_PRECISION_FP64 && precision != COLLO_PRECISION_MIXED) {
+    set_error("bad precision"); return COLLO_ERR_INVALID_ARG;
+  }
+  if (sigma)
+    COLLO_CUDA(cudaMemcpyAsync(prob->sigma, sigma, prob->n_x * sizeof(double), cudaMemcpyDefault,
+                               prob->stream));
+  else
+    COLLO_CUDA(cudaMemsetAsync(prob->sigma, 0, prob->n_x * sizeof(double), prob->stream));
+  long long in[3];
+  collo_status s = factor_internal(prob, delta_w, delta_c, precision, in);
+  if (s != COLLO_OK) return s;
+  if (out) { out->n_pos = in[0]; out->n_neg = in[1]; out->n_zero = in[2]; }
+  return COLLO_OK;
+}
+
+collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol, int refine_max,
+                             double refine_tol, collo_solve_info* info) {
+  if (!prob || !rhs || !sol) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  if (prob->factored < 0) { set_error("no factorization"); return COLLO_ERR_NOT_FACTORED; }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  const size_t nk = prob->n_x + prob->n_c;
+  cudaStream_t st = prob->stream;
+  COLLO_CUDA(cudaMemcpyAsync(prob->kvec_a, rhs, nk * sizeof(double), cudaMemcpyDefault, st));
+  int sweeps = 0;
+  double resid = 0.0;
+  collo_status s = solve_internal(prob, prob->kvec_a, prob->kvec_b, refine_max < 0 ? 0 : refine_max,
+                                  refine_tol, &sweeps, &resid);
+  if (s != COLLO_OK) return s;
+  COLLO_CUDA(cudaMemcpyAsync(sol, prob->kvec_b, nk * sizeof(double), cudaMemcpyDefault, st));
+  COLLO_CUDA(cudaStreamSynchronize(st));
+  if (info) { info->refinement_sweeps = sweeps; info->residual = resid; }
+  return COLLO_OK;
+}
+
+}  // extern "C"

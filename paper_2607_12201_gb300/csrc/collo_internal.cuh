@@ -1,0 +1,122 @@
+// Internal definitions shared by the CUDA translation units of libcollo.
+//
+// Notation follows the paper's Eq. 2 / Eq. 3: element i = 0..N-1, interpolation
+// point j = 0..K (K = 3, Radau IIA), species s, parameter q, h = T / N.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "collo.h"
+
+namespace collo {
+
+constexpr int KC = 3;        // collocation points per element
+constexpr int NP = KC + 1;   // interpolation points per element
+
+// ---- element-local ordering of the KKT unknowns -----------------------------
+// The 8n unknowns of element i are grouped into 4 groups of n (state,
+// multiplier) pairs.  Group g pairs state z[i][pt(g)][s] with the multiplier
+// of constraint c[i][con(g)][s]:
+//   g = 0: (z1, c1)   g = 1: (z2, c2)   g = 2: (z0, c3)   g = 3: (z3, c0)
+// Groups 0..2 are the element interior (eliminated locally); group 3 is the
+// interface (z3 couples forward to the next element's continuity row c0,
+// c0 couples back to the previous element's z3).  Local index of the state of
+// pair (g, s) is 2 (g n + s), of the multiplier 2 (g n + s) + 1.
+__host__ __device__ inline int grp_point(int g) { return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 0 : 3)); }
+__host__ __device__ inline int grp_con(int g) { return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 0)); }
+
+// Plain-old-data view of one problem's device arrays, passed by value.
+struct DevProb {
+  int n, r, p, N, M;
+  int m;        // 8 n: element unknowns
+  int ext;      // 8 n + p: element block plus parameter border
+  int bext;     // 4 n + p: cyclic-reduction block (2n) + two neighbour slices + border
+  int logscale;
+  double h, T;
+  // Radau IIA tables (kernel-parameter space): tau[j], D[k][j] = l_j'(tau_k)
+  double tau[NP];
+  double D[NP][NP];
+  // network
+  const int* react;      // [r][2]
+  const int* prod;       // [r][2]
+  const int* pidx;       // [r]
+  const double* kfix;    // [r]
+  const double* x0;      // [n]
+  const double* theta_lo, *theta_hi;  // [p]
+  // species -> (reaction, stoichiometric coefficient) CSR
+  const int* nu_ptr; const int* nu_r; const double* nu_v;
+  // species -> reactions consuming it (each reaction listed once) CSR
+  const int* rs_ptr; const int* rs_r;
+  // parameter -> reactions it drives CSR
+  const int* pr_ptr; const int* pr_r;
+  // observations grouped by element: CSR over elements
+  const int* obs_ptr;    // [N+1]
+  const int* obs_s;      // [M] species
+  const double* obs_y;   // [M]
+  const double* obs_sig; // [M]
+  const double* obs_w;   // [M][4] Lagrange weights l_j(tau_m)
+};
+
+// Evaluation outputs kept in the problem (FP64).
+struct DevEval {
+  double* c;        // [N][4][n]
+  double* grad;     // [n_x]
+  double* JZ;       // [N][3][n][n]
+  double* JT;       // [N][3][n][p]
+  double* Wzz;      // [N][3][n][n]
+  double* Wzt;      // [N][3][n][p]
+  double* Wobj;     // [N][n][4][4]
+  double* part;     // [N][4] per element: phi, sum|c|, max|c|, unused
+  double* wtt_part; // [N][p]
+  double* red;      // [8]: phi, |c|_1, |c|_inf, ...
+  double* wtt;      // [p]
+};
+
+// Factorization storage (T = double or float).
+template <typename T>
+struct DevFactor {
+  T* Lel;        // [N][6n][ext]   element interior L columns (column-major)
+  T* Del;        // [N][3n][3]     element interior 2x2 pivots (a, b, d)
+  T* Aif;        // [N][2n][2n]    interface blocks (full symmetric)
+  T* Cpl;        // [N][n][n]      coupling K[c0 of block, z3 of left neighbour]
+  T* Bif;        // [N][2n][p]     interface border
+  T* Lb;         // [N][2n][bext]  cyclic-reduction L columns
+  T* Db;         // [N][n][3]      cyclic-reduction 2x2 pivots
+  double* Scon;  // [2N][p][p]     parameter Schur contributions
+  int* inert;    // [2N][3]        (pos, neg, zero) per factored block
+  T* work;       // global slab workspace for element blocks too large for smem
+  int n_slabs;
+  // solve vectors
+  T* Vint;       // [N][6n]  D^-1 L^-1 rhs of the interior
+  T* Rif;        // [N][2n]  interface rhs (updated through the reduction)
+  T* Vb;         // [N][2n]  D^-1 L^-1 rhs of each reduced block
+  double* Rth;   // [2N][p]  parameter rhs contributions
+};
+
+struct DevSchur {
+  double* S;       // [p][p] assembled, then overwritten by L (unit lower) and D
+  double* Sd;      // [p] pivots
+  double* xth;     // [p] parameter solution
+  long long* inertia;  // [3] total inertia
+  double* diag;    // [p] W_thth + sigma_theta + delta_w (assembled by host-side launch)
+};
+
+// ---- error handling -----------------------------------------------------------
+void set_error(const std::string& msg);
+#define COLLO_CUDA(call)                                                         \
+  do {                                                                           \
+    cudaError_t _e = (call);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      ::collo::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));    \
+      return COLLO_ERR_DEVICE;                                                   \
+    }                                                                            \
+  } while (0)
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace collo

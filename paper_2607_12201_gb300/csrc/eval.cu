@@ -1,0 +1,477 @@
+// Evaluation kernels: residuals, constraint Jacobian, Lagrangian Hessian and
+// objective of the Radau-collocation NLP (paper Eq. 2 and Eq. 3), evaluated in
+// parallel over every (element, node) pair -- the "single instruction,
+// multiple data" evaluation the paper builds with ExaModels (Section
+// "Constructing GPU kernels with ExaModels.jl"), written here as one CUDA
+// block per element.  Also the structured FP64 KKT matrix-vector product used
+// by iterative refinement and by the optimality test.
+#include "collo_internal.cuh"
+
+namespace collo {
+
+// Deterministic block reductions (fixed tree over a fixed thread order).
+template <int BS>
+__device__ double block_sum(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = BS / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <int BS>
+__device__ double block_max(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = BS / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] = fmax(sh[t], sh[t + s]);
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+constexpr int EVAL_BS = 128;
+
+// Observation weights l_j(tau_m) (Lagrange basis on the Radau points) and
+// the observation's element; one thread per observation.
+__global__ void k_obs_weights(DevProb P, int M, int N, double T, const double* __restrict__ t,
+                              int* __restrict__ elem, double* __restrict__ w) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double u = t[m] * N / T;
+  int i = (int)ceil(u) - 1;
+  i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+  double tau = u - i;
+  elem[m] = i;
+  for (int j = 0; j < NP; ++j) {
+    double v = 1.0;
+    for (int l = 0; l < NP; ++l)
+      if (l != j) v *= (tau - P.tau[l]) / (P.tau[j] - P.tau[l]);
+    w[m * NP + j] = v;
+  }
+}
+
+// Rate constant of reaction j and its first and second theta derivatives.
+__device__ inline void rate_const(const DevProb& P, int j, const double* x, const double* dx,
+                                  double alpha, double& k, double& dk, double& d2k) {
+  int q = P.pidx[j];
+  if (q < 0) {
+    k = P.kfix[j]; dk = 0.0; d2k = 0.0;
+    return;
+  }
+  size_t o = (size_t)P.N * NP * P.n + q;
+  double th = x[o];
+  if (dx) th += alpha * dx[o];
+  if (P.logscale) {
+    const double ln10 = 2.302585092994045684;
+    k = exp10(th);
+    dk = ln10 * k;
+    d2k = ln10 * ln10 * k;
+  } else {
+    k = th; dk = 1.0; d2k = 0.0;
+  }
+}
+
+// One block per element i.  Evaluates at x + alpha dx (dx may be null).
+// DERIV = false: residuals, objective and norms only (line-search trials).
+template <bool DERIV>
+__global__ void __launch_bounds__(EVAL_BS)
+k_eval(DevProb P, const double* __restrict__ x, const double* __restrict__ dx, double alpha,
+       const double* __restrict__ lam, double obj_factor, DevEval E) {
+  extern __shared__ double sm[];
+  __shared__ double red[EVAL_BS];
+  const int n = P.n, r = P.r, p = P.p;
+  const int i = blockIdx.x;
+  const int tid = threadIdx.x;
+  double* ze = sm;              // [4][n]
+  double* le = ze + NP * n;     // [4][n]
+  double* kr = le + NP * n;     // [r]
+  double* dkr = kr + r;         // [r]
+  double* d2kr = dkr + r;       // [r]
+  double* mon = d2kr + r;       // [3][r]
+  double* da = mon + KC * r;    // [3][r] d mon / d z(slot 0)
+  double* db = da + KC * r;     // [3][r] d mon / d z(slot 1)
+  double* om = db + KC * r;     // [3][r] sum_s lambda_s nu_s,r
+  const size_t zoff = (size_t)i * NP * n;
+
+  for (int t = tid; t < NP * n; t += EVAL_BS) {
+    double v = x[zoff + t];
+    if (dx) v += alpha * dx[zoff + t];
+    ze[t] = v;
+    le[t] = (DERIV && lam) ? lam[zoff + t] : 0.0;
+  }
+  for (int j = tid; j < r; j += EVAL_BS) rate_const(P, j, x, dx, alpha, kr[j], dkr[j], d2kr[j]);
+  __syncthreads();
+  for (int idx = tid; idx < KC * r; idx += EVAL_BS) {
+    const int k = idx / r + 1, j = idx - (idx / r) * r;
+    const int a = P.react[2 * j], b = P.react[2 * j + 1];
+    const double za = ze[k * n + a];
+    double mo, dA, dB;
+    if (b < 0) { mo = za; dA = 1.0; dB = 0.0; }
+    else { const double zb = ze[k * n + b]; mo = za * zb; dA = zb; dB = za; }
+    mon[idx] = mo; da[idx] = dA; db[idx] = dB;
+    if (DERIV) {
+      double o = -le[k * n + a];
+      if (b >= 0) o -= le[k * n + b];
+      const int p0 = P.prod[2 * j], p1 = P.prod[2 * j + 1];
+      if (p0 >= 0) o += le[k * n + p0];
+      if (p1 >= 0) o += le[k * n + p1];
+      om[idx] = o;
+    }
+  }
+  __syncthreads();
+
+  // constraints: continuity / initial (point 0) and collocation (points 1..3)
+  double csum = 0.0, cmax = 0.0;
+  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
+    const int j = idx / n, s = idx - j * n;
+    double c;
+    if (j == 0) {
+      double prev;
+      if (i > 0) {
+        prev = x[zoff - n + s];
+        if (dx) prev += alpha * dx[zoff - n + s];
+      } else {
+        prev = P.x0[s];
+      }
+      c = ze[s] - prev;
+    } else {
+      double acc = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < NP; ++jj) acc += P.D[j][jj] * ze[jj * n + s];
+      double f = 0.0;
+      for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
+        const int rr = P.nu_r[e];
+        f += P.nu_v[e] * kr[rr] * mon[(j - 1) * r + rr];
+      }
+      c = acc - P.h * f;
+    }
+    E.c[zoff + idx] = c;
+    csum += fabs(c);
+    cmax = fmax(cmax, fabs(c));
+  }
+
+  // objective terms of this element's observations
+  const int o0 = P.obs_ptr[i], o1 = P.obs_ptr[i + 1];
+  double phi = 0.0;
+  for (int o = o0 + tid; o < o1; o += EVAL_BS) {
+    const int s = P.obs_s[o];
+    double yh = 0.0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) yh += P.obs_w[o * NP + j] * ze[j * n + s];
+    const double res = (yh - P.obs_y[o]) / P.obs_sig[o];
+    phi += 0.5 * res * res;
+  }
+  phi = block_sum<EVAL_BS>(phi, red);
+  csum = block_sum<EVAL_BS>(csum, red);
+  cmax = block_max<EVAL_BS>(cmax, red);
+  if (tid == 0) {
+    E.part[i * 4 + 0] = phi;
+    E.part[i * 4 + 1] = csum;
+    E.part[i * 4 + 2] = cmax;
+    E.part[i * 4 + 3] = 0.0;
+  }
+  if (!DERIV) return;
+
+  // gradient of obj_factor * Phi with respect to z[i][j][s]
+  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
+    const int j = idx / n, s = idx - j * n;
+    double g = 0.0;
+    for (int o = o0; o < o1; ++o) {
+      if (P.obs_s[o] != s) continue;
+      double yh = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < NP; ++jj) yh += P.obs_w[o * NP + jj] * ze[jj * n + s];
+      const double sg = P.obs_sig[o];
+      g += P.obs_w[o * NP + j] * (yh - P.obs_y[o]) / (sg * sg);
+    }
+    E.grad[zoff + idx] = obj_factor * g;
+  }
+  if (i == 0)
+    for (int q = tid; q < p; q += EVAL_BS) E.grad[(size_t)P.N * NP * n + q] = 0.0;
+  // objective Hessian blocks Wobj[i][s][j][l]
+  for (int idx = tid; idx < n * NP * NP; idx += EVAL_BS) {
+    const int s = idx / (NP * NP), j = (idx / NP) % NP, l = idx % NP;
+    double w = 0.0;
+    for (int o = o0; o < o1; ++o) {
+      if (P.obs_s[o] != s) continue;
+      const double sg = P.obs_sig[o];
+      w += P.obs_w[o * NP + j] * P.obs_w[o * NP + l] / (sg * sg);
+    }
+    E.Wobj[(size_t)i * n * NP * NP + idx] = obj_factor * w;
+  }
+  const double mh = -P.h;
+  const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
+  // JZ[i][k-1][s][t] = -h df_s/dz_t at node k
+  for (int idx = tid; idx < KC * n * n; idx += EVAL_BS) {
+    const int k = idx / (n * n) + 1, s = (idx / n) % n, t = idx % n;
+    double v = 0.0;
+    for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
+      const int rr = P.nu_r[e];
+      const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+      const int mi = (k - 1) * r + rr;
+      double dm = 0.0;
+      if (a == t) dm += da[mi];
+      if (b == t) dm += db[mi];
+      v += P.nu_v[e] * kr[rr] * dm;
+    }
+    E.JZ[(size_t)i * KC * nn + idx] = mh * v;
+  }
+  // JT[i][k-1][s][q] = -h df_s/dtheta_q at node k
+  for (int idx = tid; idx < KC * n * p; idx += EVAL_BS) {
+    const int k = idx / (n * p) + 1, s = (idx / p) % n, q = idx % p;
+    double v = 0.0;
+    for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
+      const int rr = P.nu_r[e];
+      if (P.pidx[rr] != q) continue;
+      v += P.nu_v[e] * dkr[rr] * mon[(k - 1) * r + rr];
+    }
+    E.JT[(size_t)i * KC * np_ + idx] = mh * v;
+  }
+  // Wzz[i][k-1][t][u] = -h sum_r om_r k_r d2 mon_r / dz_t dz_u
+  for (int idx = tid; idx < KC * n * n; idx += EVAL_BS) {
+    const int k = idx / (n * n) + 1, t = (idx / n) % n, u = idx % n;
+    double v = 0.0;
+    for (int e = P.rs_ptr[t]; e < P.rs_ptr[t + 1]; ++e) {
+      const int rr = P.rs_r[e];
+      const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+      if (b < 0) continue;
+      const double d2 = (double)((a == t && b == u) + (b == t && a == u));
+      v += om[(k - 1) * r + rr] * kr[rr] * d2;
+    }
+    E.Wzz[(size_t)i * KC * nn + idx] = mh * v;
+  }
+  // Wzt[i][k-1][t][q] = -h sum_r om_r dk_r d mon_r / dz_t
+  for (int idx = tid; idx < KC * n * p; idx += EVAL_BS) {
+    const int k = idx / (n * p) + 1, t = (idx / p) % n, q = idx % p;
+    double v = 0.0;
+    for (int e = P.rs_ptr[t]; e < P.rs_ptr[t + 1]; ++e) {
+      const int rr = P.rs_r[e];
+      if (P.pidx[rr] != q) continue;
+      const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+      const int mi = (k - 1) * r + rr;
+      double dm = 0.0;
+      if (a == t) dm += da[mi];
+      if (b == t) dm += db[mi];
+      v += om[mi] * dkr[rr] * dm;
+    }
+    E.Wzt[(size_t)i * KC * np_ + idx] = mh * v;
+  }
+  // theta-theta diagonal partial sums of this element
+  for (int q = tid; q < p; q += EVAL_BS) {
+    double v = 0.0;
+    for (int k = 1; k <= KC; ++k)
+      for (int e = P.pr_ptr[q]; e < P.pr_ptr[q + 1]; ++e) {
+        const int rr = P.pr_r[e];
+        const int mi = (k - 1) * r + rr;
+        v += om[mi] * d2kr[rr] * mon[mi];
+      }
+    E.wtt_part[(size_t)i * p + q] = mh * v;
+  }
+}
+
+// Sum the per-element partials in a fixed order: phi, |c|_1, |c|_inf, W_thth.
+constexpr int RED_BS = 256;
+__global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, int deriv) {
+  __shared__ double sh[RED_BS];
+  const int tid = threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = tid; i < P.N; i += RED_BS) {
+    a += E.part[i * 4 + 0];
+    b += E.part[i * 4 + 1];
+    c = fmax(c, E.part[i * 4 + 2]);
+  }
+  a = block_sum<RED_BS>(a, sh);
+  b = block_sum<RED_BS>(b, sh);
+  c = block_max<RED_BS>(c, sh);
+  if (tid == 0) { E.red[0] = a; E.red[1] = b; E.red[2] = c; }
+  if (!deriv) return;
+  for (int q = tid; q < P.p; q += RED_BS) {
+    double v = 0.0;
+    for (int i = 0; i < P.N; ++i) v += E.wtt_part[(size_t)i * P.p + q];
+    E.wtt[q] = v;
+  }
+}
+
+// Structured FP64 product y = K v of the regularised KKT matrix
+//   [ W + diag(sigma) + dw I   J^T  ] [vx]
+//   [ J                       -dc I ] [vl]
+// and r = b - y (b may be null: r = -y).  One block per element computes the
+// element's 8n rows and its contribution to the p parameter rows; norms of r
+// per element go to npart[i][0..1] (max |r_x|, max |r_c|).
+__global__ void __launch_bounds__(EVAL_BS)
+k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
+            const double* __restrict__ vx, const double* __restrict__ vl,
+            const double* __restrict__ bx, double bxs, const double* __restrict__ bc, double bcs,
+            double* __restrict__ rout, double* __restrict__ thpart, double* __restrict__ npart) {
+  __shared__ double red[EVAL_BS];
+  const int n = P.n, p = P.p, N = P.N;
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const size_t nz = (size_t)N * NP * n, nx = nz + p;
+  const size_t zoff = (size_t)i * NP * n;
+  const double* vz = vx;
+  const double* vt = vx ? vx + nz : nullptr;
+  const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
+  const double* JZ = E.JZ + (size_t)i * KC * nn;
+  const double* JT = E.JT + (size_t)i * KC * np_;
+  const double* Wzz = E.Wzz + (size_t)i * KC * nn;
+  const double* Wzt = E.Wzt + (size_t)i * KC * np_;
+  const double* Wob = E.Wobj + (size_t)i * n * NP * NP;
+  double mx = 0.0, mc = 0.0;
+  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
+    const int j = idx / n, s = idx - j * n;
+    // primal row z[i][j][s]
+    double y = 0.0;
+#pragma unroll
+    if (vz) {
+      for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
+      if (j >= 1) {
+        const double* wr = Wzz + (size_t)(j - 1) * nn + (size_t)s * n;
+        for (int t = 0; t < n; ++t) y += wr[t] * vz[zoff + j * n + t];
+        const double* wt = Wzt + (size_t)(j - 1) * np_ + (size_t)s * p;
+        for (int q = 0; q < p; ++q) y += wt[q] * vt[q];
+      }
+      y += ((sigma ? sigma[zoff + idx] : 0.0) + dw) * vz[zoff + idx];
+    }
+    if (vl) {
+      if (j >= 1) {
+        const double* jz = JZ + (size_t)(j - 1) * nn;
+        for (int t = 0; t < n; ++t) y += jz[(size_t)t * n + s] * vl[zoff + j * n + t];
+      }
+#pragma unroll
+      for (int k = 1; k < NP; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
+      if (j == 0) y += vl[zoff + s];
+      if (j == KC && i + 1 < N) y -= vl[zoff + NP * n + s];
+    }
+    double rr = (bx ? bxs * bx[zoff + idx] : 0.0) - y;
+    if (rout) rout[zoff + idx] = rr;
+    mx = fmax(mx, fabs(rr));
+    // dual row c[i][j][s]
+    double yc = 0.0;
+    if (vz) {
+      if (j == 0) {
+        yc = vz[zoff + s] - (i > 0 ? vz[zoff - n + s] : 0.0);
+      } else {
+#pragma unroll
+        for (int l = 0; l < NP; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];
+        const double* jz = JZ + (size_t)(j - 1) * nn + (size_t)s * n;
+        for (int t = 0; t < n; ++t) yc += jz[t] * vz[zoff + j * n + t];
+        const double* jt = JT + (size_t)(j - 1) * np_ + (size_t)s * p;
+        for (int q = 0; q < p; ++q) yc += jt[q] * vt[q];
+      }
+    }
+    if (vl) yc -= dc * vl[zoff + idx];
+    double rc = (bc ? bcs * bc[zoff + idx] : 0.0) - yc;
+    if (rout) rout[nx + zoff + idx] = rc;
+    mc = fmax(mc, fabs(rc));
+  }
+  // this element's part of the parameter rows
+  for (int q = tid; q < p; q += EVAL_BS) {
+    double y = 0.0;
+    for (int k = 1; k < NP; ++k)
+      for (int s = 0; s < n; ++s) {
+        if (vz) y += Wzt[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vz[zoff + k * n + s];
+        if (vl) y += JT[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vl[zoff + k * n + s];
+      }
+    thpart[(size_t)i * p + q] = y;
+  }
+  mx = block_max<EVAL_BS>(mx, red);
+  mc = block_max<EVAL_BS>(mc, red);
+  if (tid == 0) { npart[i * 2 + 0] = mx; npart[i * 2 + 1] = mc; }
+}
+
+// Parameter rows of r = b - K v, and the global norms:
+// out[0] = max|r_x|, out[1] = max|r_c|, out[2] = max|b| (b may be null).
+__global__ void __launch_bounds__(RED_BS)
+k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
+                  const double* __restrict__ vx, const double* __restrict__ bx, double bxs,
+                  const double* __restrict__ bc, double bcs,
+                  double* __restrict__ rout, const double* __restrict__ thpart,
+                  const double* __restrict__ npart, const double* __restrict__ th_extra,
+                  double* __restrict__ out) {
+  __shared__ double sh[RED_BS];
+  const int tid = threadIdx.x, p = P.p, N = P.N;
+  const size_t nz = (size_t)N * NP * P.n, nx = nz + p;
+  double mx = 0.0, mc = 0.0, mb = 0.0;
+  for (int q = tid; q < p; q += RED_BS) {
+    double y = 0.0;
+    for (int i = 0; i < N; ++i) y += thpart[(size_t)i * p + q];
+    if (vx) y += (E.wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw) * vx[nz + q];
+    if (th_extra) y -= th_extra[q];
+    double rr = (bx ? bxs * bx[nz + q] : 0.0) - y;
+    if (rout) rout[nz + q] = rr;
+    mx = fmax(mx, fabs(rr));
+  }
+  for (int i = tid; i < N; i += RED_BS) {
+    mx = fmax(mx, npart[i * 2 + 0]);
+    mc = fmax(mc, npart[i * 2 + 1]);
+  }
+  if (bx)
+    for (size_t k = tid; k < nx; k += RED_BS) mb = fmax(mb, fabs(bx[k]));
+  if (bc)
+    for (size_t k = tid; k < nz; k += RED_BS) mb = fmax(mb, fabs(bc[k]));
+  mx = block_max<RED_BS>(mx, sh);
+  mc = block_max<RED_BS>(mc, sh);
+  mb = block_max<RED_BS>(mb, sh);
+  if (tid == 0) { out[0] = mx; out[1] = mc; out[2] = mb; }
+}
+
+// ---- host launchers -------------------------------------------------------------
+size_t eval_smem_bytes(const DevProb& P) {
+  return sizeof(double) * (size_t)(2 * NP * P.n + 3 * P.r + 4 * KC * P.r);
+}
+
+cudaError_t launch_obs_weights(const DevProb& P, int M, int N, double T, const double* t,
+                               int* elem, double* w, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_obs_weights<<<ceil_div(M, 128), 128, 0, st>>>(P, M, N, T, t, elem, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const DevProb& P, const DevEval& E, const double* x, const double* dx,
+                        double alpha, const double* lam, double obj_factor, bool deriv,
+                        cudaStream_t st) {
+  size_t sm = eval_smem_bytes(P);
+  if (deriv) {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_eval<true><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
+  } else {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_eval<false><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_eval_reduce<<<1, RED_BS, 0, st>>>(P, E, deriv ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// r = [bxs bx; bcs bc] - K [vx; vl] (null vectors are zero; th_extra, if given,
+// is subtracted from the parameter rows of K v).  out[0..2] = max|r_x|,
+// max|r_c|, max|b|.  rout may be null (norms only).
+cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                             double dc, const double* vx, const double* vl, const double* bx,
+                             double bxs, const double* bc, double bcs, double* rout,
+                             double* thpart, double* npart, const double* th_extra, double* out,
+                             cudaStream_t st) {
+  k_kkt_resid<<<P.N, EVAL_BS, 0, st>>>(P, E, sigma, dw, dc, vx, vl, bx, bxs, bc, bcs, rout,
+                                       thpart, npart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, bcs, rout, thpart,
+                                          npart, th_extra, out);
+  return cudaGetLastError();
+}
+
+}  // namespace collo

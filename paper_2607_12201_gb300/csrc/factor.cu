@@ -1,0 +1,639 @@
+// Structured, pivot-free factorization and solve of the element-banded KKT
+// system bordered by the parameter block.
+//
+// The paper attributes most of the GPU benefit to sparse linear algebra on a
+// KKT system put in a "pivoting-free factorizable form", with parallelism at
+// the level of the elimination tree (Abstract; Introduction).  Here the
+// elimination tree is explicit:
+//
+//  1. Element condensation (one CUDA block per element, all elements in
+//     parallel): the element's 8n unknowns are ordered as n (state,
+//     multiplier) pairs per group -- (z1,c1), (z2,c2), (z0,c3) interior and
+//     (z3,c0) interface -- and the 3n interior pairs are eliminated with
+//     static 2x2 pivots [[w, j], [j, -delta_c]].  Their determinant is
+//     -(w delta_c + j^2) < 0 for the collocation Jacobian entry j, so each pivot
+//     is nonsingular whatever the sign of the Hessian entry w; the sequence is
+//     Gaussian elimination without pivoting on the element's square
+//     collocation Jacobian.  The parameter border rides along as extra rows.
+//  2. Block cyclic reduction over the chain of 2n x 2n interface blocks
+//     (ceil(log2 N) levels; at each level the odd blocks are eliminated in
+//     parallel, each updating its two neighbours, creating the n x n fill
+//     coupling between them, and contributing to the parameter Schur block).
+//  3. The p x p parameter Schur complement, summed from all contributions in
+//     a fixed order and factored in FP64 (LDL^T, 1x1 pivots).
+//
+// Inertia is counted from every pivot block (Sylvester's law of inertia).
+// T = double (plain path) or float (mixed path; residuals and refinement
+// are FP64 elsewhere).
+#include "collo_internal.cuh"
+
+namespace collo {
+
+constexpr int FBS = 256;   // threads per factor block
+constexpr int FTY = FBS / 32;
+
+__device__ inline void pivot_inertia(double a, double b, double d, int& pos, int& neg, int& zero) {
+  double det = a * d - b * b;
+  if (!(det == det) || det == 0.0 || !isfinite(det)) { zero += 2; return; }
+  if (det < 0) { pos += 1; neg += 1; return; }
+  if (a + d > 0) pos += 2; else neg += 2;
+}
+
+// Eliminate the first npairs (state, multiplier) pairs of the symmetric
+// matrix A (size msz, leading dimension ld, lower triangle valid).  L columns
+// go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to Dout[3 q].
+// Scratch: cc0, cc1, l0s, l1s of length msz (shared memory).
+template <typename T>
+__device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict__ Lout, int lds,
+                               T* __restrict__ Dout, T* cc0, T* cc1, T* l0s, T* l1s,
+                               int& pos, int& neg, int& zero) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wy = tid >> 5;
+  for (int q = 0; q < npairs; ++q) {
+    const int c0 = 2 * q, c1 = c0 + 1;
+    const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
+    const T det = a * d - b * b;
+    T ia, ib, id;
+    if (det != T(0) && isfinite((double)det)) {
+      const T inv = T(1) / det;
+      ia = d * inv; ib = -b * inv; id = a * inv;
+    } else {
+      ia = ib = id = T(0);
+    }
+    for (int r = c1 + 1 + tid; r < msz; r += FBS) {
+      const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
+      const T l0 = x0 * ia + x1 * ib;
+      const T l1 = x0 * ib + x1 * id;
+      cc0[r] = x0; cc1[r] = x1; l0s[r] = l0; l1s[r] = l1;
+      Lout[(size_t)c0 * lds + r] = l0;
+      Lout[(size_t)c1 * lds + r] = l1;
+    }
+    if (tid == 0) {
+      Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
+      pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
+    }
+    __syncthreads();
+    for (int r = c1 + 1 + wy; r < msz; r += FTY) {
+      const T l0 = l0s[r], l1 = l1s[r];
+      T* Ar = A + (size_t)r * ld;
+      for (int c = c1 + 1 + lane; c <= r; c += 32) Ar[c] -= l0 * cc0[c] + l1 * cc1[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Entry (a, b), a >= b, of element e's bordered KKT block in local order.
+__device__ inline double elem_entry(const DevProb& P, const DevEval& E, int e, int a, int b,
+                                    const double* __restrict__ sigma, double dw, double dc) {
+  const int n = P.n, m = P.m, p = P.p;
+  if (a >= m) {
+    if (b >= m) return 0.0;
+    const int q = a - m;
+    const int pr = b >> 1, g = pr / n, s = pr - g * n;
+    if ((b & 1) == 0) {
+      const int j = grp_point(g);
+      return j >= 1 ? E.Wzt[(((size_t)e * KC + (j - 1)) * n + s) * p + q] : 0.0;
+    }
+    const int k = grp_con(g);
+    return k >= 1 ? E.JT[(((size_t)e * KC + (k - 1)) * n + s) * p + q] : 0.0;
+  }
+  const int pa = a >> 1, ga = pa / n, sa = pa - ga * n;
+  const int pb = b >> 1, gb = pb / n, sb = pb - gb * n;
+  const bool adual = a & 1, bdual = b & 1;
+  if (!adual && !bdual) {
+    const int ja = grp_point(ga), jb = grp_point(gb);
+    double v = 0.0;
+    if (sa == sb) v += E.Wobj[(((size_t)e * n + sa) * NP + ja) * NP + jb];
+    if (ja == jb && ja >= 1) v += E.Wzz[(((size_t)e * KC + (ja - 1)) * n + sa) * n + sb];
+    if (a == b) v += (sigma ? sigma[((size_t)e * NP + ja) * n + sa] : 0.0) + dw;
+    return v;
+  }
+  if (adual && bdual) return a == b ? -dc : 0.0;
+  int kd, sd, jp, sp;
+  if (adual) { kd = grp_con(ga); sd = sa; jp = grp_point(gb); sp = sb; }
+  else { kd = grp_con(gb); sd = sb; jp = grp_point(ga); sp = sa; }
+  if (kd == 0) return (jp == 0 && sd == sp) ? 1.0 : 0.0;
+  double v = (sd == sp) ? P.D[kd][jp] : 0.0;
+  if (jp == kd) v += E.JZ[(((size_t)e * KC + (kd - 1)) * n + sd) * n + sp];
+  return v;
+}
+
+__host__ __device__ inline int odd_ld(int m) { return (m & 1) ? m : m + 1; }
+
+// ---- 1. element condensation --------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FBS)
+k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
+              DevFactor<T> F, int use_smem) {
+  extern __shared__ unsigned char smraw[];
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext, ld = odd_ld(ext);
+  T* cc0 = reinterpret_cast<T*>(smraw);
+  T* cc1 = cc0 + ext;
+  T* l0s = cc1 + ext;
+  T* l1s = l0s + ext;
+  T* A = use_smem ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
+  const int tid = threadIdx.x;
+  const int nint = 3 * n;          // interior pairs
+  const int i0 = 2 * nint;         // first interface row (6n)
+  for (int e = blockIdx.x; e < P.N; e += gridDim.x) {
+    for (int a = tid >> 5; a < ext; a += FTY)
+      for (int b = tid & 31; b <= a; b += 32)
+        A[a * ld + b] = (T)elem_entry(P, E, e, a, b, sigma, dw, dc);
+    __syncthreads();
+    int pos = 0, neg = 0, zero = 0;
+    pair_eliminate<T>(A, ld, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+                      F.Del + (size_t)e * nint * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+    if (tid == 0) {
+      F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
+    }
+    const int n2 = 2 * n;
+    T* Aif = F.Aif + (size_t)e * n2 * n2;
+    for (int idx = tid; idx < n2 * n2; idx += FBS) {
+      const int u = idx / n2, v = idx - u * n2;
+      Aif[idx] = u >= v ? A[(i0 + u) * ld + i0 + v] : A[(i0 + v) * ld + i0 + u];
+    }
+    T* Bif = F.Bif + (size_t)e * n2 * p;
+    for (int idx = tid; idx < n2 * p; idx += FBS) {
+      const int u = idx / p, q = idx - u * p;
+      Bif[idx] = A[(m + q) * ld + i0 + u];
+    }
+    double* Sc = F.Scon + (size_t)e * p * p;
+    for (int idx = tid; idx < p * p; idx += FBS) {
+      const int q = idx / p, q2 = idx - q * p;
+      Sc[idx] = (double)(q >= q2 ? A[(m + q) * ld + m + q2] : A[(m + q2) * ld + m + q]);
+    }
+    T* C = F.Cpl + (size_t)e * n * n;
+    for (int idx = tid; idx < n * n; idx += FBS) {
+      const int s = idx / n, t = idx - s * n;
+      C[idx] = (e > 0 && s == t) ? T(-1) : T(0);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- 2. one level of block cyclic reduction -------------------------------------
+// Eliminates the blocks at odd multiples of `stride` (final = 1: block 0 alone).
+// Local order of the extended block: [interface of block i (2n) | z3 of the
+// left neighbour (n) | c0 of the right neighbour (n) | theta (p)].
+template <typename T>
+__global__ void __launch_bounds__(FBS)
+k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
+  extern __shared__ unsigned char smraw[];
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
+  T* cc0 = reinterpret_cast<T*>(smraw);
+  T* cc1 = cc0 + bext;
+  T* l0s = cc1 + bext;
+  T* l1s = l0s + bext;
+  T* A = use_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
+  const int tid = threadIdx.x;
+  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const int i = final_level ? 0 : stride * (2 * bi + 1);
+    const int L = final_level ? -1 : i - stride;
+    const int R = (!final_level && i + stride < N) ? i + stride : -1;
+    const T* Ai = F.Aif + (size_t)i * n2 * n2;
+    const T* Ci = F.Cpl + (size_t)i * n * n;
+    const T* CR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
+    const T* Bi = F.Bif + (size_t)i * n2 * p;
+    for (int a = tid >> 5; a < bext; a += FTY)
+      for (int b = tid & 31; b <= a; b += 32) {
+        T v = T(0);
+        if (a < n2) {
+          v = Ai[a * n2 + b];
+        } else if (b < n2) {
+          if (a < 3 * n) {                       // z3 of left neighbour, t = a - 2n
+            if (L >= 0 && (b & 1)) v = Ci[(b >> 1) * n + (a - n2)];
+          } else if (a < 4 * n) {                // c0 of right neighbour, s = a - 3n
+            if (R >= 0 && !(b & 1)) v = CR[(a - 3 * n) * n + (b >> 1)];
+          } else {                               // theta row q = a - 4n
+            v = Bi[b * p + (a - 4 * n)];
+          }
+        }
+        A[a * ld + b] = v;
+      }
+    __syncthreads();
+    int pos = 0, neg = 0, zero = 0;
+    pair_eliminate<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
+                      F.Db + (size_t)i * n * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+    if (tid == 0) {
+      int* in = F.inert + (size_t)(N + i) * 3;
+      in[0] = pos; in[1] = neg; in[2] = zero;
+    }
+    // scatter the trailing (Schur) block into the neighbours
+    if (L >= 0) {
+      T* AL = F.Aif + (size_t)L * n2 * n2;
+      for (int idx = tid; idx < n * n; idx += FBS) {
+        const int t = idx / n, t2 = idx - t * n;
+        const int ra = n2 + t, rb = n2 + t2;
+        AL[(2 * t) * n2 + 2 * t2] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
+      }
+      T* BL = F.Bif + (size_t)L * n2 * p;
+      for (int idx = tid; idx < n * p; idx += FBS) {
+        const int t = idx / p, q = idx - t * p;
+        BL[(2 * t) * p + q] += A[(4 * n + q) * ld + n2 + t];
+      }
+    }
+    if (R >= 0) {
+      T* AR = F.Aif + (size_t)R * n2 * n2;
+      T* CRw = F.Cpl + (size_t)R * n * n;
+      for (int idx = tid; idx < n * n; idx += FBS) {
+        const int s = idx / n, s2 = idx - s * n;
+        const int ra = 3 * n + s, rb = 3 * n + s2;
+        AR[(2 * s + 1) * n2 + 2 * s2 + 1] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
+        CRw[idx] = (L >= 0) ? A[(3 * n + s) * ld + n2 + s2] : T(0);
+      }
+      T* BR = F.Bif + (size_t)R * n2 * p;
+      for (int idx = tid; idx < n * p; idx += FBS) {
+        const int s = idx / p, q = idx - s * p;
+        BR[(2 * s + 1) * p + q] += A[(4 * n + q) * ld + 3 * n + s];
+      }
+    }
+    double* Sc = F.Scon + (size_t)(N + i) * p * p;
+    for (int idx = tid; idx < p * p; idx += FBS) {
+      const int q = idx / p, q2 = idx - q * p;
+      const int ra = 4 * n + q, rb = 4 * n + q2;
+      Sc[idx] = (double)(ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- 3. parameter Schur complement (FP64) ------------------------------------------
+constexpr int SBS = 256;
+__global__ void __launch_bounds__(SBS)
+k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ Scon,
+        const double* __restrict__ wtt, const double* __restrict__ sigma, double dw,
+        DevSchur S) {
+  extern __shared__ double sS[];      // [p][p] then l[p]
+  __shared__ long long cnt[3];
+  const int p = P.p, N = P.N, tid = threadIdx.x;
+  const size_t nz = (size_t)N * NP * P.n;
+  double* l = sS + (size_t)p * p;
+  for (int idx = tid; idx < p * p; idx += SBS) {
+    const int q = idx / p, q2 = idx - q * p;
+    double v = 0.0;
+    for (int c = 0; c < 2 * N; ++c) v += Scon[(size_t)c * p * p + idx];
+    if (q == q2) v += wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw;
+    sS[idx] = v;
+  }
+  if (tid == 0) {
+    long long a = 0, b = 0, c = 0;
+    for (int k = 0; k < 2 * N; ++k) { a += inert[3 * k]; b += inert[3 * k + 1]; c += inert[3 * k + 2]; }
+    cnt[0] = a; cnt[1] = b; cnt[2] = c;
+  }
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    const double d = sS[k * p + k];
+    const bool ok = (d != 0.0) && isfinite(d);
+    const double inv = ok ? 1.0 / d : 0.0;
+    for (int r = k + 1 + tid; r < p; r += SBS) l[r] = sS[r * p + k] * inv;
+    if (tid == 0) {
+      if (!ok) cnt[2] += 1; else if (d > 0) cnt[0] += 1; else cnt[1] += 1;
+      S.Sd[k] = d;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (p - k - 1) * (p - k - 1); idx += SBS) {
+      const int r = k + 1 + idx / (p - k - 1), c = k + 1 + idx % (p - k - 1);
+      if (c <= r) sS[r * p + c] -= l[r] * sS[c * p + k];
+    }
+    __syncthreads();
+    for (int r = k + 1 + tid; r < p; r += SBS) sS[r * p + k] = l[r];
+    __syncthreads();
+  }
+  for (int idx = tid; idx < p * p; idx += SBS) S.S[idx] = sS[idx];
+  if (tid == 0) { S.inertia[0] = cnt[0]; S.inertia[1] = cnt[1]; S.inertia[2] = cnt[2]; }
+}
+
+// ---- solves: one warp per block ----------------------------------------------------
+constexpr int SOLVE_WARPS = 4;
+
+template <typename T>
+__device__ inline void pair_solve_d(T a, T b, T d, T w0, T w1, T& v0, T& v1) {
+  const T det = a * d - b * b;
+  if (det != T(0) && isfinite((double)det)) {
+    const T inv = T(1) / det;
+    v0 = (d * w0 - b * w1) * inv;
+    v1 = (-b * w0 + a * w1) * inv;
+  } else {
+    v0 = T(0); v1 = T(0);
+  }
+}
+
+// Forward substitution through a block's eliminated pairs: w (length msz)
+// in shared memory, L columns Lc[c * lds + r].
+template <typename T>
+__device__ void warp_forward(T* w, int msz, int npairs, const T* __restrict__ Lc, int lds) {
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < npairs; ++q) {
+    const int c0 = 2 * q, c1 = c0 + 1;
+    const T w0 = w[c0], w1 = w[c1];
+    const T* L0 = Lc + (size_t)c0 * lds;
+    const T* L1 = Lc + (size_t)c1 * lds;
+    for (int r = c1 + 1 + lane; r < msz; r += 32) w[r] -= L0[r] * w0 + L1[r] * w1;
+    __syncwarp();
+  }
+}
+
+// Back substitution: x (length msz) holds the known tail values; pairs are
+// solved from the last to the first: x_q = v_q - sum_{r > q} L[r][q] x_r.
+template <typename T>
+__device__ void warp_backward(T* x, const T* v, int msz, int npairs, const T* __restrict__ Lc,
+                              int lds) {
+  const int lane = threadIdx.x & 31;
+  for (int q = npairs - 1; q >= 0; --q) {
+    const int c0 = 2 * q, c1 = c0 + 1;
+    const T* L0 = Lc + (size_t)c0 * lds;
+    const T* L1 = Lc + (size_t)c1 * lds;
+    T s0 = T(0), s1 = T(0);
+    for (int r = c1 + 1 + lane; r < msz; r += 32) {
+      const T xr = x[r];
+      s0 += L0[r] * xr;
+      s1 += L1[r] * xr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) { x[c0] = v[c0] - s0; x[c1] = v[c1] - s1; }
+    __syncwarp();
+  }
+}
+
+// local index -> position in the API-layout KKT vector of element e
+__device__ inline size_t elem_global(const DevProb& P, int e, int a) {
+  const int n = P.n;
+  const size_t nx = (size_t)P.N * NP * n + P.p;
+  const int pr = a >> 1, g = pr / n, s = pr - g * n;
+  if (a & 1) return nx + ((size_t)e * NP + grp_con(g)) * n + s;
+  return ((size_t)e * NP + grp_point(g)) * n + s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_elem_fwd(DevProb P, DevFactor<T> F, const double* __restrict__ b) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * SOLVE_WARPS + warp;
+  const int n = P.n, ext = P.ext, m = P.m, p = P.p;
+  T* w = reinterpret_cast<T*>(smraw) + (size_t)warp * ext;
+  if (e >= P.N) return;
+  for (int a = lane; a < ext; a += 32) w[a] = a < m ? (T)b[elem_global(P, e, a)] : T(0);
+  __syncwarp();
+  const int nint = 3 * n;
+  const T* Lc = F.Lel + (size_t)e * (2 * nint) * ext;
+  warp_forward<T>(w, ext, nint, Lc, ext);
+  const T* D = F.Del + (size_t)e * nint * 3;
+  T* V = F.Vint + (size_t)e * 2 * nint;
+  for (int q = lane; q < nint; q += 32) {
+    T v0, v1;
+    pair_solve_d<T>(D[3 * q], D[3 * q + 1], D[3 * q + 2], w[2 * q], w[2 * q + 1], v0, v1);
+    V[2 * q] = v0; V[2 * q + 1] = v1;
+  }
+  T* Rif = F.Rif + (size_t)e * 2 * n;
+  for (int u = lane; u < 2 * n; u += 32) Rif[u] = w[2 * nint + u];
+  double* Rth = F.Rth + (size_t)e * p;
+  for (int q = lane; q < p; q += 32) Rth[q] = (double)w[m + q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_bcr_fwd(DevProb P, DevFactor<T> F, int stride, int final_level) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
+  T* w = reinterpret_cast<T*>(smraw) + (size_t)warp * bext;
+  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
+  const int bi = blockIdx.x * SOLVE_WARPS + warp;
+  if (bi >= nblk) return;
+  const int i = final_level ? 0 : stride * (2 * bi + 1);
+  const int L = final_level ? -1 : i - stride;
+  const int R = (!final_level && i + stride < N) ? i + stride : -1;
+  const T* Rii = F.Rif + (size_t)i * n2;
+  for (int a = lane; a < bext; a += 32) w[a] = a < n2 ? Rii[a] : T(0);
+  __syncwarp();
+  warp_forward<T>(w, bext, n, F.Lb + (size_t)i * n2 * bext, bext);
+  const T* D = F.Db + (size_t)i * n * 3;
+  T* V = F.Vb + (size_t)i * n2;
+  for (int q = lane; q < n; q += 32) {
+    T v0, v1;
+    pair_solve_d<T>(D[3 * q], D[3 * q + 1], D[3 * q + 2], w[2 * q], w[2 * q + 1], v0, v1);
+    V[2 * q] = v0; V[2 * q + 1] = v1;
+  }
+  if (L >= 0) {
+    T* RL = F.Rif + (size_t)L * n2;
+    for (int t = lane; t < n; t += 32) RL[2 * t] += w[n2 + t];
+  }
+  if (R >= 0) {
+    T* RR = F.Rif + (size_t)R * n2;
+    for (int s = lane; s < n; s += 32) RR[2 * s + 1] += w[3 * n + s];
+  }
+  double* Rth = F.Rth + (size_t)(N + i) * p;
+  for (int q = lane; q < p; q += 32) Rth[q] = (double)w[4 * n + q];
+}
+
+// Parameter solve: rhs = b_theta + all contributions (fixed order), then the
+// FP64 LDL^T of the Schur complement.  Writes x_theta into sol.
+__global__ void __launch_bounds__(SBS)
+k_theta_solve(DevProb P, const double* __restrict__ Rth, const double* __restrict__ b,
+              DevSchur S, double* __restrict__ sol) {
+  extern __shared__ double sv[];
+  const int p = P.p, N = P.N, tid = threadIdx.x;
+  const size_t nz = (size_t)N * NP * P.n;
+  for (int q = tid; q < p; q += SBS) {
+    double v = b[nz + q];
+    for (int c = 0; c < 2 * N; ++c) v += Rth[(size_t)c * p + q];
+    sv[q] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < p; ++k)
+      for (int r = k + 1; r < p; ++r) sv[r] -= S.S[r * p + k] * sv[k];
+    for (int k = 0; k < p; ++k) {
+      const double d = S.Sd[k];
+      sv[k] = (d != 0.0 && isfinite(d)) ? sv[k] / d : 0.0;
+    }
+    for (int k = p - 1; k >= 0; --k)
+      for (int r = k + 1; r < p; ++r) sv[k] -= S.S[r * p + k] * sv[r];
+  }
+  __syncthreads();
+  for (int q = tid; q < p; q += SBS) { sol[nz + q] = sv[q]; S.xth[q] = sv[q]; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_bcr_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol, int stride,
+          int final_level) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
+  T* x = reinterpret_cast<T*>(smraw) + (size_t)warp * bext;
+  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
+  const int bi = blockIdx.x * SOLVE_WARPS + warp;
+  if (bi >= nblk) return;
+  const int i = final_level ? 0 : stride * (2 * bi + 1);
+  const int L = final_level ? -1 : i - stride;
+  const int R = (!final_level && i + stride < N) ? i + stride : -1;
+  const size_t nx = (size_t)N * NP * n + p;
+  for (int a = lane; a < bext; a += 32) {
+    T v = T(0);
+    if (a >= n2 && a < 3 * n) {
+      if (L >= 0) v = (T)sol[((size_t)L * NP + KC) * n + (a - n2)];
+    } else if (a >= 3 * n && a < 4 * n) {
+      if (R >= 0) v = (T)sol[nx + (size_t)R * NP * n + (a - 3 * n)];
+    } else if (a >= 4 * n) {
+      v = (T)S.xth[a - 4 * n];
+    }
+    x[a] = v;
+  }
+  __syncwarp();
+  warp_backward<T>(x, F.Vb + (size_t)i * n2, bext, n, F.Lb + (size_t)i * n2 * bext, bext);
+  for (int s = lane; s < n; s += 32) {
+    sol[((size_t)i * NP + KC) * n + s] = (double)x[2 * s];
+    sol[nx + (size_t)i * NP * n + s] = (double)x[2 * s + 1];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * SOLVE_WARPS + warp;
+  const int n = P.n, ext = P.ext, m = P.m;
+  T* x = reinterpret_cast<T*>(smraw) + (size_t)warp * ext;
+  if (e >= P.N) return;
+  const int nint = 3 * n;
+  for (int a = lane; a < ext; a += 32) {
+    T v = T(0);
+    if (a >= 2 * nint && a < m) v = (T)sol[elem_global(P, e, a)];
+    else if (a >= m) v = (T)S.xth[a - m];
+    x[a] = v;
+  }
+  __syncwarp();
+  warp_backward<T>(x, F.Vint + (size_t)e * 2 * nint, ext, nint,
+                   F.Lel + (size_t)e * (2 * nint) * ext, ext);
+  for (int a = lane; a < 2 * nint; a += 32) sol[elem_global(P, e, a)] = (double)x[a];
+}
+
+// ---- host launchers ------------------------------------------------------------------
+int bcr_levels(int N) {
+  int lv = 0;
+  for (int s = 1; s < N; s *= 2) ++lv;
+  return lv;
+}
+
+template <typename T>
+size_t elem_factor_smem(const DevProb& P, bool full) {
+  size_t v = sizeof(T) * 4 * (size_t)P.ext;
+  if (full) v += sizeof(T) * (size_t)odd_ld(P.ext) * P.ext;
+  return v;
+}
+template <typename T>
+size_t bcr_factor_smem(const DevProb& P, bool full) {
+  size_t v = sizeof(T) * 4 * (size_t)P.bext;
+  if (full) v += sizeof(T) * (size_t)odd_ld(P.bext) * P.bext;
+  return v;
+}
+
+constexpr size_t SMEM_LIMIT = 220 * 1024;
+
+template <typename T>
+bool elem_uses_smem(const DevProb& P) { return elem_factor_smem<T>(P, true) <= SMEM_LIMIT; }
+template <typename T>
+bool bcr_uses_smem(const DevProb& P) { return bcr_factor_smem<T>(P, true) <= SMEM_LIMIT; }
+
+// Global workspace (in T elements) needed when a block does not fit in shared memory.
+template <typename T>
+size_t factor_work_elems(const DevProb& P, int n_slabs) {
+  size_t w = 0;
+  if (!elem_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.ext) * P.ext * n_slabs);
+  if (!bcr_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.bext) * P.bext * n_slabs);
+  return w;
+}
+
+template <typename T>
+cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                          double dc, const DevFactor<T>& F, const DevSchur& S, cudaStream_t st) {
+  bool es = elem_uses_smem<T>(P);
+  size_t sm = elem_factor_smem<T>(P, es);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int grid = es ? P.N : std::min(P.N, F.n_slabs);
+  k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bool bs = bcr_uses_smem<T>(P);
+  size_t smb = bcr_factor_smem<T>(P, bs);
+  if (smb > 48 * 1024)
+    cudaFuncSetAttribute(k_bcr_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+  for (int s = 1; s < P.N; s *= 2) {
+    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    int g = bs ? nblk : std::min(nblk, F.n_slabs);
+    k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
+  if (sms > 48 * 1024)
+    cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  k_schur<<<1, SBS, sms, st>>>(P, F.inert, F.Scon, E.wtt, sigma, dw, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur& S,
+                         const double* b, double* sol, cudaStream_t st) {
+  const int tpb = 32 * SOLVE_WARPS;
+  size_t sme = sizeof(T) * (size_t)P.ext * SOLVE_WARPS;
+  size_t smb = sizeof(T) * (size_t)P.bext * SOLVE_WARPS;
+  if (sme > 48 * 1024) {
+    cudaFuncSetAttribute(k_elem_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme);
+    cudaFuncSetAttribute(k_elem_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme);
+  }
+  if (smb > 48 * 1024) {
+    cudaFuncSetAttribute(k_bcr_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    cudaFuncSetAttribute(k_bcr_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+  }
+  cudaError_t e;
+  k_elem_fwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, b);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  std::vector<int> strides;
+  for (int s = 1; s < P.N; s *= 2) strides.push_back(s);
+  for (int s : strides) {
+    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    k_bcr_fwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, s, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_bcr_fwd<T><<<1, tpb, smb, st>>>(P, F, 1, 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  size_t smt = sizeof(double) * (size_t)(P.p > 0 ? P.p : 1);
+  k_theta_solve<<<1, SBS, smt, st>>>(P, F.Rth, b, S, sol);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_bcr_bwd<T><<<1, tpb, smb, st>>>(P, F, S, sol, 1, 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int k = (int)strides.size() - 1; k >= 0; --k) {
+    int s = strides[k];
+    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    k_bcr_bwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, S, sol, s, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_elem_bwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, S, sol);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_factor<double>(const DevProb&, const DevEval&, const double*, double,
+                                           double, const DevFactor<double>&, const DevSchur&,
+                                           cudaStream_t);
+template cudaError_t launch_factor<float>(const DevProb&, const DevEval&, const double*, double,
+                                          double, const DevFactor<float>&, const DevSchur&,
+                                          cudaStream_t);
+template cudaError_t launch_solve<double>(const DevProb&, const DevFactor<double>&,
+                                          const DevSchur&, const double*, double*, cudaStream_t);
+template cudaError_t launch_solve<float>(const DevProb&, const DevFactor<float>&,
+                                         const DevSchur&, const double*, double*, cudaStream_t);
+template size_t factor_work_elems<double>(const DevProb&, int);
+template size_t factor_work_elems<float>(const DevProb&, int);
+
+}  // namespace collo

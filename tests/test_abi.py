@@ -1,0 +1,85 @@
+"""The C-ABI library loads and exports every function include/collo.h declares;
+host-side argument validation (runs without a GPU: no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_12201_gb300 import build
+    build.build()
+    from paper_2607_12201_gb300 import collo
+    return collo
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "collo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(collo_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["collo_problem_create", "collo_eval", "collo_kkt_factor", "collo_kkt_solve",
+                     "collo_ipm_solve", "collo_problem_destroy", "collo_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = C.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version_and_options_defaults(lib):
+    assert "sm_103a" in lib.version()
+    o = lib.Problem.ipm_options()
+    assert o.tol == 1e-6 and o.acceptable_tol == 1e-4 and o.acceptable_iter == 15
+
+
+def _structs(lib, inst, K=3, sigma_scale=1.0, t_shift=0.0):
+    species = np.unique(inst.obs_s)
+    k = dict(react=np.ascontiguousarray(inst.react, np.int32),
+             prod=np.ascontiguousarray(inst.prod, np.int32),
+             pidx=np.ascontiguousarray(inst.pidx, np.int32), kfix=np.array(inst.kfix, float),
+             x0=np.array(inst.x0, float), lo=np.array(inst.theta_lo, float),
+             hi=np.array(inst.theta_hi, float), sp=species.astype(np.int32),
+             t=np.array(inst.obs_t, float) + t_shift,
+             o=np.searchsorted(species, inst.obs_s).astype(np.int32),
+             y=np.array(inst.obs_y, float), s=np.array(inst.obs_sigma, float) * sigma_scale)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+    net = lib.Network(inst.n, inst.r, ip(k["react"]), ip(k["prod"]), ip(k["pidx"]), dp(k["kfix"]),
+                      int(inst.logscale), dp(k["x0"]), inst.p, dp(k["lo"]), dp(k["hi"]))
+    obs = lib.Observables(len(species), ip(k["sp"]))
+    data = lib.Data(inst.M, dp(k["t"]), ip(k["o"]), dp(k["y"]), dp(k["s"]))
+    mesh = lib.Mesh(float(inst.T), int(inst.N), K)
+    return net, obs, data, mesh, k
+
+
+@pytest.mark.parametrize("case", ["K4", "sigma0", "t_out"])
+def test_create_rejects_bad_arguments_before_touching_the_device(lib, case):
+    from paper_2607_12201_gb300 import workloads
+    inst = workloads.linear_cascade(N=4)
+    kw = {"K4": dict(K=4), "sigma0": dict(sigma_scale=0.0), "t_out": dict(t_shift=100.0)}[case]
+    net, obs, data, mesh, keep = _structs(lib, inst, **kw)
+    h = C.c_void_p()
+    st = lib.lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh),
+                                      None, C.byref(h))
+    assert st == lib.ERR_INVALID_ARG
+    assert lib.last_error()
+    assert not h.value
+
+
+def test_calls_on_null_problem_fail_cleanly(lib):
+    L = lib.lib
+    assert L.collo_eval(None, None, None, 1.0, None) == lib.ERR_INVALID_ARG
+    assert L.collo_kkt_factor(None, None, 0.0, 0.0, 0, None) == lib.ERR_INVALID_ARG
+    assert L.collo_kkt_solve(None, None, None, 0, 0.0, None) == lib.ERR_INVALID_ARG
+    L.collo_problem_destroy(None)
