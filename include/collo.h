@@ -249,6 +249,32 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
 collo_status collo_initial_states(collo_problem* prob, const double* theta, double* x_out,
                                   int* failures);
 
+/* Measurement hooks (used by the benchmark's roofline report).
+ * collo_time_phase re-launches one phase reps times between CUDA events on
+ * the problem's stream and returns the average milliseconds per launch:
+ *   phase 0: element condensation kernel alone (needs collo_eval; uses the
+ *            sigma and regularisation of the last collo_kkt_factor), leaves
+ *            the problem unfactored;
+ *   phase 1: whole factorization (element condensation, cyclic reduction,
+ *            parameter Schur complement);
+ *   phase 2: one solve without refinement (needs a factorization in
+ *            `precision`), on the last right-hand side;
+ *   phase 3: evaluation with derivatives at the solver's current iterate;
+ *   phase 4: collocation forward sweep at the current theta.
+ * Returns NOT_EVALUATED / NOT_FACTORED when its input state is missing. */
+collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int reps,
+                              double* ms_per_launch);
+
+/* Fused multiply-add throughput of the current device in TFLOP/s (2 flops
+ * per FMA), for precision COLLO_PRECISION_FP64 (DFMA) or _MIXED (FFMA):
+ * the arithmetic roof of the element factorization.  Allocates a small
+ * buffer and runs about a millisecond. */
+collo_status collo_alu_peak(int precision, double* tflops);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all problems, all threads); a monotone counter for launch accounting. */
+long long collo_launch_count(void);
+
 const char* collo_last_error(void);
 
 /* Library version string. */

@@ -118,6 +118,12 @@ def _load():
     lib.collo_ipm_solve.restype = C.c_int
     lib.collo_initial_states.argtypes = [P, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.collo_initial_states.restype = C.c_int
+    lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    lib.collo_time_phase.restype = C.c_int
+    lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    lib.collo_alu_peak.restype = C.c_int
+    lib.collo_launch_count.argtypes = []
+    lib.collo_launch_count.restype = C.c_longlong
     lib.collo_last_error.argtypes = []
     lib.collo_last_error.restype = C.c_char_p
     lib.collo_version.argtypes = []
@@ -279,12 +285,30 @@ class Problem:
                     phi=res.phi, kkt_error=res.kkt_error, mu=res.mu, wall=res.wall_seconds,
                     theta=theta, x=x, lam=lam)
 
+    def time_phase(self, phase: int, precision: int = -1, reps: int = 20) -> float:
+        """Average milliseconds per launch of one phase (see collo_time_phase)."""
+        ms = C.c_double()
+        _check(lib.collo_time_phase(self.h, int(phase), int(precision), int(reps), C.byref(ms)))
+        return ms.value
+
     def initial_states(self, theta):
         x = np.zeros(self.n_x)
         f = C.c_int(0)
         _check(lib.collo_initial_states(self.h, _f64(theta).ctypes.data, x.ctypes.data,
                                         C.byref(f)))
         return x, int(f.value)
+
+
+def alu_peak(precision: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device, FP64 or FP32."""
+    t = C.c_double()
+    _check(lib.collo_alu_peak(int(precision), C.byref(t)))
+    return t.value
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since load (collo_launch_count)."""
+    return int(lib.collo_launch_count())
 
 
 def version() -> str:

@@ -1,6 +1,7 @@
 // C ABI of libcollo: problem construction, evaluation, KKT factor / solve.
 // The interior-point driver is in ipm.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -10,6 +11,8 @@ namespace collo {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Radau IIA points for K = 3 (closed form) and D[k][j] = l_j'(tau_k) from the
 // barycentric weights w_j = 1 / prod_{l != j} (tau_j - tau_l):
@@ -87,6 +90,7 @@ extern "C" {
 
 const char* collo_last_error(void) { return g_last_error.c_str(); }
 const char* collo_version(void) { return "collo 0.1 (sm_103a)"; }
+long long collo_launch_count(void) { return g_launches.load(); }
 
 collo_status collo_problem_create(const collo_network* net, const collo_observables* obs,
                                   const collo_data* data, const collo_mesh* mesh,

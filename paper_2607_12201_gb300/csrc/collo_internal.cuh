@@ -117,6 +117,9 @@ void set_error(const std::string& msg);
     }                                                                            \
   } while (0)
 
+// Count of kernels this library has launched (all threads, all problems).
+void count_launch(int k = 1);
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace collo

@@ -434,6 +434,7 @@ size_t eval_smem_bytes(const DevProb& P) {
 cudaError_t launch_obs_weights(const DevProb& P, int M, int N, double T, const double* t,
                                int* elem, double* w, cudaStream_t st) {
   if (M == 0) return cudaSuccess;
+  count_launch();
   k_obs_weights<<<ceil_div(M, 128), 128, 0, st>>>(P, M, N, T, t, elem, w);
   return cudaGetLastError();
 }
@@ -445,14 +446,17 @@ cudaError_t launch_eval(const DevProb& P, const DevEval& E, const double* x, con
   if (deriv) {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
     k_eval<true><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
   } else {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
     k_eval<false><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  count_launch();
   k_eval_reduce<<<1, RED_BS, 0, st>>>(P, E, deriv ? 1 : 0);
   return cudaGetLastError();
 }
@@ -465,10 +469,12 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
                              double bxs, const double* bc, double bcs, double* rout,
                              double* thpart, double* npart, const double* th_extra, double* out,
                              cudaStream_t st) {
+  count_launch();
   k_kkt_resid<<<P.N, EVAL_BS, 0, st>>>(P, E, sigma, dw, dc, vx, vl, bx, bxs, bc, bcs, rout,
                                        thpart, npart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  count_launch();
   k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, bcs, rout, thpart,
                                           npart, th_extra, out);
   return cudaGetLastError();

@@ -553,15 +553,22 @@ size_t factor_work_elems(const DevProb& P, int n_slabs) {
 }
 
 template <typename T>
-cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
-                          double dc, const DevFactor<T>& F, const DevSchur& S, cudaStream_t st) {
+cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                               double dc, const DevFactor<T>& F, cudaStream_t st) {
   bool es = elem_uses_smem<T>(P);
   size_t sm = elem_factor_smem<T>(P, es);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int grid = es ? P.N : std::min(P.N, F.n_slabs);
+  count_launch();
   k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                          double dc, const DevFactor<T>& F, const DevSchur& S, cudaStream_t st) {
+  cudaError_t e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st);
   if (e != cudaSuccess) return e;
   bool bs = bcr_uses_smem<T>(P);
   size_t smb = bcr_factor_smem<T>(P, bs);
@@ -570,14 +577,17 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   for (int s = 1; s < P.N; s *= 2) {
     int nblk = (P.N - s + 2 * s - 1) / (2 * s);
     int g = bs ? nblk : std::min(nblk, F.n_slabs);
+    count_launch();
     k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  count_launch();
   k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   if (sms > 48 * 1024)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  count_launch();
   k_schur<<<1, SBS, sms, st>>>(P, F.inert, F.Scon, E.wtt, sigma, dw, S);
   return cudaGetLastError();
 }
@@ -597,28 +607,35 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
     cudaFuncSetAttribute(k_bcr_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
   }
   cudaError_t e;
+  count_launch();
   k_elem_fwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, b);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::vector<int> strides;
   for (int s = 1; s < P.N; s *= 2) strides.push_back(s);
   for (int s : strides) {
     int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    count_launch();
     k_bcr_fwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, s, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  count_launch();
   k_bcr_fwd<T><<<1, tpb, smb, st>>>(P, F, 1, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   size_t smt = sizeof(double) * (size_t)(P.p > 0 ? P.p : 1);
+  count_launch();
   k_theta_solve<<<1, SBS, smt, st>>>(P, F.Rth, b, S, sol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launch();
   k_bcr_bwd<T><<<1, tpb, smb, st>>>(P, F, S, sol, 1, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int k = (int)strides.size() - 1; k >= 0; --k) {
     int s = strides[k];
     int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    count_launch();
     k_bcr_bwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, S, sol, s, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  count_launch();
   k_elem_bwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, S, sol);
   return cudaGetLastError();
 }
@@ -633,6 +650,12 @@ template cudaError_t launch_solve<double>(const DevProb&, const DevFactor<double
                                           const DevSchur&, const double*, double*, cudaStream_t);
 template cudaError_t launch_solve<float>(const DevProb&, const DevFactor<float>&,
                                          const DevSchur&, const double*, double*, cudaStream_t);
+template cudaError_t launch_elem_factor<double>(const DevProb&, const DevEval&, const double*,
+                                                double, double, const DevFactor<double>&,
+                                                cudaStream_t);
+template cudaError_t launch_elem_factor<float>(const DevProb&, const DevEval&, const double*,
+                                               double, double, const DevFactor<float>&,
+                                               cudaStream_t);
 template size_t factor_work_elems<double>(const DevProb&, int);
 template size_t factor_work_elems<float>(const DevProb&, int);
 

@@ -68,6 +68,7 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, dou
 
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st) {
   int g = (int)std::min<size_t>((n + 255) / 256, 4096);
+  count_launch();
   k_axpy<<<std::max(g, 1), 256, 0, st>>>(y, x, a, n);
   return cudaGetLastError();
 }
@@ -255,6 +256,7 @@ cudaError_t launch_forward_sweep(collo_problem* pr) {
   size_t sm = sweep_smem_bytes(pr->P, insm);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_forward_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
   k_forward_sweep<<<1, 32, sm, pr->stream>>>(pr->P, pr->x, pr->fails, pr->sweep_work);
   return cudaGetLastError();
 }
@@ -456,6 +458,7 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
 
   // initial point
   if (p) COLLO_CUDA(cudaMemcpyAsync(th0, theta0, p * sizeof(double), cudaMemcpyDefault, st));
+  count_launch();
   k_init_point<<<1, 256, 0, st>>>(P, th0, prob->x, prob->zl, prob->zu, o.kappa1, o.kappa2);
   COLLO_CUDA(cudaGetLastError());
   COLLO_CUDA(launch_forward_sweep(prob));
@@ -480,12 +483,16 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
     double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     // 1. derivatives at the iterate and the optimality measures
     COLLO_CUDA(launch_eval(P, prob->E, prob->x, nullptr, 0.0, prob->lam, 1.0, true, st));
+    prob->evaluated = true;
+    count_launch();
     k_theta_prep<<<1, IBS, 0, st>>>(P, prob->x, prob->zl, prob->zu, mu, prob->sigma, bar, zlmzu,
                                     d + 16);
     COLLO_CUDA(launch_kkt_resid(P, prob->E, nullptr, 0.0, 0.0, nullptr, prob->lam,
                                 prob->E.grad, -1.0, nullptr, 0.0, nullptr, prob->thpart,
                                 prob->npart, zlmzu, d + 20, st));
+    count_launch();
     k_dot_part<<<RGRID, IBS, 0, st>>>(prob->lam, nullptr, nc, 1, dots);
+    count_launch();
     k_sum_parts<<<1, IBS, 0, st>>>(dots, d + 24);
     COLLO_CUDA(cudaGetLastError());
     COLLO_CUDA(cudaMemcpyAsync(h + 16, d + 16, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -517,6 +524,7 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
       filt.clear();
     }
     // 3. Newton direction with inertia correction
+    count_launch();
     k_theta_prep<<<1, IBS, 0, st>>>(P, prob->x, prob->zl, prob->zu, mu, prob->sigma, bar, zlmzu,
                                     d + 16);
     COLLO_CUDA(launch_kkt_resid(P, prob->E, nullptr, 0.0, 0.0, nullptr, prob->lam,
@@ -549,8 +557,11 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
     s = solve_internal(prob, rhs, sol, o.refine_max, o.refine_tol, &sweeps, &rres);
     if (s != COLLO_OK) { status = s; break; }
     // 4. step sizes
+    count_launch();
     k_theta_step<<<1, IBS, 0, st>>>(P, prob->x, sol, prob->zl, prob->zu, mu, tau, prob->dz, d + 28);
+    count_launch();
     k_dot_part<<<RGRID, IBS, 0, st>>>(prob->E.grad, sol, nx, 0, dots);
+    count_launch();
     k_sum_parts<<<1, IBS, 0, st>>>(dots, d + 32);
     COLLO_CUDA(cudaGetLastError());
     COLLO_CUDA(cudaMemcpyAsync(h + 16, d + 16, 17 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -577,6 +588,7 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
     while (alpha >= alpha_min) {
       ++trials;
       COLLO_CUDA(launch_eval(P, prob->E, prob->x, sol, alpha, nullptr, 1.0, false, st));
+      count_launch();
       k_trial_barrier<<<1, IBS, 0, st>>>(P, prob->x, sol, alpha, d + 36);
       COLLO_CUDA(cudaGetLastError());
       COLLO_CUDA(cudaMemcpyAsync(h, prob->E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -607,6 +619,7 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
     res->line_search_trials += trials;
     if (!accepted) { status = COLLO_ERR_LINESEARCH; break; }
     if (!ftype) filt.push_back({(1.0 - o.gamma_theta) * theta_k, phi_k - o.gamma_phi * theta_k});
+    count_launch();
     k_update<<<std::min<size_t>((nx + nc + 255) / 256, 8192), 256, 0, st>>>(
         P, prob->x, prob->lam, prob->zl, prob->zu, sol, prob->dz, alpha, alpha_z, mu,
         o.kappa_sigma, nx, nc);

@@ -6,6 +6,8 @@
 
 #include "collo_internal.cuh"
 
+struct collo_problem;
+
 namespace collo {
 
 // launchers (eval.cu)
@@ -25,6 +27,9 @@ int bcr_levels(int N);
 template <typename T>
 size_t factor_work_elems(const DevProb& P, int n_slabs);
 template <typename T>
+cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                               double dc, const DevFactor<T>& F, cudaStream_t st);
+template <typename T>
 cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
                           double dc, const DevFactor<T>& F, const DevSchur& S, cudaStream_t st);
 template <typename T>
@@ -33,6 +38,7 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
 
 // launchers (ipm.cu)
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+cudaError_t launch_forward_sweep(collo_problem* pr);
 
 // Device allocations owned by a problem; freed in the destructor.
 struct DevArena {
