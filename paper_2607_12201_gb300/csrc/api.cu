@@ -60,11 +60,13 @@ static collo_status alloc_factor(collo_problem* pr, FactorStore<T>& fs) {
   F.Rif = A.alloc<T>(N * 2 * n);
   F.Vb = A.alloc<T>(N * 2 * n);
   F.Rth = A.alloc<double>(2 * N * p);
+  F.chunkS = A.alloc<double>((size_t)CHUNKS * p * p);
+  F.chunkR = A.alloc<double>((size_t)CHUNKS * p);
   F.n_slabs = pr->n_slabs;
   size_t w = factor_work_elems<T>(P, pr->n_slabs);
   F.work = w ? A.alloc<T>(w) : nullptr;
   if (!F.Lel || !F.Del || !F.Aif || !F.Cpl || !F.Bif || !F.Lb || !F.Db || !F.Scon || !F.inert ||
-      !F.Vint || !F.Rif || !F.Vb || !F.Rth || (w && !F.work)) {
+      !F.Vint || !F.Rif || !F.Vb || !F.Rth || !F.chunkS || !F.chunkR || (w && !F.work)) {
     set_error("device allocation failed for the factorization storage");
     return COLLO_ERR_OOM;
   }
@@ -278,7 +280,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   pr->kvec_b = A.alloc<double>(nk);
   pr->kvec_r = A.alloc<double>(nk);
   pr->kvec_c = A.alloc<double>(nk);
-  pr->thpart = A.alloc<double>(NN * p);
+  pr->thpart = A.alloc<double>(NN * p + (size_t)CHUNKS * p);
   pr->npart = A.alloc<double>(NN * 2);
   pr->scal = A.alloc<double>(64);
   pr->red_parts = A.alloc<double>(256);
@@ -290,8 +292,8 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   pr->thx = A.alloc<double>(8 * (size_t)p + 8);
   pr->fails = A.alloc<int>(1);
   const size_t sweep_dim = 3 * (size_t)n;
-  if (sweep_dim * (sweep_dim + 1) * sizeof(double) > 200 * 1024)
-    pr->sweep_work = A.alloc<double>(sweep_dim * (sweep_dim + 1));
+  const bool sweep_global = sweep_dim * (sweep_dim + 1) * sizeof(float) > 160 * 1024;
+  if (sweep_global) pr->sweep_work = A.alloc<float>(sweep_dim * (sweep_dim + 1));
   bool ok = P.react && P.prod && P.pidx && P.kfix && P.x0 && P.theta_lo && P.theta_hi &&
             P.nu_ptr && P.nu_r && P.nu_v && P.rs_ptr && P.rs_r && P.pr_ptr && P.pr_r &&
             P.obs_ptr && P.obs_s && P.obs_y && P.obs_sig && d_obs_t && obs_w && obs_elem_chk &&
@@ -299,7 +301,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
             E.red && E.wtt && S.S && S.Sd && S.xth && S.inertia && S.diag && pr->sigma &&
             pr->kvec_a && pr->kvec_b && pr->kvec_r && pr->kvec_c && pr->thpart && pr->npart &&
             pr->scal && pr->red_parts && pr->x && pr->lam && pr->zl && pr->zu && pr->dz && pr->thx && pr->fails &&
-            (sweep_dim * (sweep_dim + 1) * sizeof(double) <= 200 * 1024 || pr->sweep_work);
+            (!sweep_global || pr->sweep_work);
   if (!ok) { set_error("device allocation failed"); return COLLO_ERR_OOM; }
   if (cudaMallocHost(&pr->hscal, 64 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();

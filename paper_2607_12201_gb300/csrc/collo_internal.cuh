@@ -96,7 +96,15 @@ struct DevFactor {
   T* Rif;        // [N][2n]  interface rhs (updated through the reduction)
   T* Vb;         // [N][2n]  D^-1 L^-1 rhs of each reduced block
   double* Rth;   // [2N][p]  parameter rhs contributions
+  double* chunkS;  // [CHUNKS][p][p] partial sums of Scon
+  double* chunkR;  // [CHUNKS][p]    partial sums of Rth
 };
+
+// Deterministic two-stage sums over many per-block contributions: stage 1
+// sums fixed chunks of the contribution index in parallel, stage 2 (inside
+// the consumer kernel) adds the chunk sums in order.
+constexpr int CHUNKS = 64;
+__host__ __device__ inline int n_chunks(int C) { return C < CHUNKS ? (C > 0 ? C : 1) : CHUNKS; }
 
 struct DevSchur {
   double* S;       // [p][p] assembled, then overwritten by L (unit lower) and D

@@ -9,6 +9,8 @@
 
 namespace collo {
 
+cudaError_t launch_chunk_sums(const double* X, int C, int L, double* part, cudaStream_t st);
+
 // Deterministic block reductions (fixed tree over a fixed thread order).
 template <int BS>
 __device__ double block_sum(double v, double* sh) {
@@ -41,6 +43,19 @@ __device__ double block_max(double v, double* sh) {
 }
 
 constexpr int EVAL_BS = 128;
+
+__device__ inline double sum_chunks(const double* __restrict__ part, int G, int L, int l) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int g = 0;
+  for (; g + 3 < G; g += 4) {
+    a0 += part[(size_t)g * L + l];
+    a1 += part[(size_t)(g + 1) * L + l];
+    a2 += part[(size_t)(g + 2) * L + l];
+    a3 += part[(size_t)(g + 3) * L + l];
+  }
+  for (; g < G; ++g) a0 += part[(size_t)g * L + l];
+  return (a0 + a1) + (a2 + a3);
+}
 
 // Observation weights l_j(tau_m) (Lagrange basis on the Radau points) and
 // the observation's element; one thread per observation.
@@ -332,8 +347,8 @@ k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, d
     const int j = idx / n, s = idx - j * n;
     // primal row z[i][j][s]
     double y = 0.0;
-#pragma unroll
     if (vz) {
+#pragma unroll
       for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
       if (j >= 1) {
         const double* wr = Wzz + (size_t)(j - 1) * nn + (size_t)s * n;
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(RED_BS)
 k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
                   const double* __restrict__ vx, const double* __restrict__ bx, double bxs,
                   const double* __restrict__ bc, double bcs,
-                  double* __restrict__ rout, const double* __restrict__ thpart,
+                  double* __restrict__ rout, const double* __restrict__ chunkT,
                   const double* __restrict__ npart, const double* __restrict__ th_extra,
                   double* __restrict__ out) {
   __shared__ double sh[RED_BS];
@@ -404,8 +419,7 @@ k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double
   const size_t nz = (size_t)N * NP * P.n, nx = nz + p;
   double mx = 0.0, mc = 0.0, mb = 0.0;
   for (int q = tid; q < p; q += RED_BS) {
-    double y = 0.0;
-    for (int i = 0; i < N; ++i) y += thpart[(size_t)i * p + q];
+    double y = sum_chunks(chunkT, n_chunks(N), p, q);
     if (vx) y += (E.wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw) * vx[nz + q];
     if (th_extra) y -= th_extra[q];
     double rr = (bx ? bxs * bx[nz + q] : 0.0) - y;
@@ -474,9 +488,11 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
                                        thpart, npart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if ((e = launch_chunk_sums(thpart, P.N, P.p, thpart + (size_t)P.N * P.p, st)) != cudaSuccess)
+    return e;
   count_launch();
-  k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, bcs, rout, thpart,
-                                          npart, th_extra, out);
+  k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, bcs, rout,
+                                          thpart + (size_t)P.N * P.p, npart, th_extra, out);
   return cudaGetLastError();
 }
 

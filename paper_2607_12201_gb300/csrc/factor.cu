@@ -259,9 +259,50 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
 }
 
 // ---- 3. parameter Schur complement (FP64) ------------------------------------------
+// part[g][l] = sum of X[c][l] over the g-th of G contiguous chunks of c.
+constexpr int CS_BS = 256;
+__global__ void __launch_bounds__(CS_BS)
+k_chunk_sums(const double* __restrict__ X, int C, int L, int G, double* __restrict__ part) {
+  const int l = blockIdx.x * CS_BS + threadIdx.x;
+  const int g = blockIdx.y;
+  if (l >= L) return;
+  const int c0 = (int)((long long)C * g / G), c1 = (int)((long long)C * (g + 1) / G);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = c0;
+  for (; c + 3 < c1; c += 4) {
+    a0 += X[(size_t)c * L + l];
+    a1 += X[(size_t)(c + 1) * L + l];
+    a2 += X[(size_t)(c + 2) * L + l];
+    a3 += X[(size_t)(c + 3) * L + l];
+  }
+  for (; c < c1; ++c) a0 += X[(size_t)c * L + l];
+  part[(size_t)g * L + l] = (a0 + a1) + (a2 + a3);
+}
+
+cudaError_t launch_chunk_sums(const double* X, int C, int L, double* part, cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  dim3 grid(ceil_div(L, CS_BS), n_chunks(C));
+  count_launch();
+  k_chunk_sums<<<grid, CS_BS, 0, st>>>(X, C, L, n_chunks(C), part);
+  return cudaGetLastError();
+}
+
+__device__ inline double sum_chunks(const double* __restrict__ part, int G, int L, int l) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int g = 0;
+  for (; g + 3 < G; g += 4) {
+    a0 += part[(size_t)g * L + l];
+    a1 += part[(size_t)(g + 1) * L + l];
+    a2 += part[(size_t)(g + 2) * L + l];
+    a3 += part[(size_t)(g + 3) * L + l];
+  }
+  for (; g < G; ++g) a0 += part[(size_t)g * L + l];
+  return (a0 + a1) + (a2 + a3);
+}
+
 constexpr int SBS = 256;
 __global__ void __launch_bounds__(SBS)
-k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ Scon,
+k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chunkS,
         const double* __restrict__ wtt, const double* __restrict__ sigma, double dw,
         DevSchur S) {
   extern __shared__ double sS[];      // [p][p] then l[p]
@@ -271,15 +312,21 @@ k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ Sco
   double* l = sS + (size_t)p * p;
   for (int idx = tid; idx < p * p; idx += SBS) {
     const int q = idx / p, q2 = idx - q * p;
-    double v = 0.0;
-    for (int c = 0; c < 2 * N; ++c) v += Scon[(size_t)c * p * p + idx];
+    double v = sum_chunks(chunkS, n_chunks(2 * N), p * p, idx);
     if (q == q2) v += wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw;
     sS[idx] = v;
   }
-  if (tid == 0) {
+  {
     long long a = 0, b = 0, c = 0;
-    for (int k = 0; k < 2 * N; ++k) { a += inert[3 * k]; b += inert[3 * k + 1]; c += inert[3 * k + 2]; }
-    cnt[0] = a; cnt[1] = b; cnt[2] = c;
+    for (int k = tid; k < 2 * N; k += SBS) { a += inert[3 * k]; b += inert[3 * k + 1]; c += inert[3 * k + 2]; }
+    __shared__ long long red[3][SBS];
+    red[0][tid] = a; red[1][tid] = b; red[2][tid] = c;
+    __syncthreads();
+    for (int s = SBS / 2; s > 0; s >>= 1) {
+      if (tid < s) { red[0][tid] += red[0][tid + s]; red[1][tid] += red[1][tid + s]; red[2][tid] += red[2][tid + s]; }
+      __syncthreads();
+    }
+    if (tid == 0) { cnt[0] = red[0][0]; cnt[1] = red[1][0]; cnt[2] = red[2][0]; }
   }
   __syncthreads();
   for (int k = 0; k < p; ++k) {
@@ -435,16 +482,12 @@ k_bcr_fwd(DevProb P, DevFactor<T> F, int stride, int final_level) {
 // Parameter solve: rhs = b_theta + all contributions (fixed order), then the
 // FP64 LDL^T of the Schur complement.  Writes x_theta into sol.
 __global__ void __launch_bounds__(SBS)
-k_theta_solve(DevProb P, const double* __restrict__ Rth, const double* __restrict__ b,
+k_theta_solve(DevProb P, const double* __restrict__ chunkR, const double* __restrict__ b,
               DevSchur S, double* __restrict__ sol) {
   extern __shared__ double sv[];
   const int p = P.p, N = P.N, tid = threadIdx.x;
   const size_t nz = (size_t)N * NP * P.n;
-  for (int q = tid; q < p; q += SBS) {
-    double v = b[nz + q];
-    for (int c = 0; c < 2 * N; ++c) v += Rth[(size_t)c * p + q];
-    sv[q] = v;
-  }
+  for (int q = tid; q < p; q += SBS) sv[q] = b[nz + q] + sum_chunks(chunkR, n_chunks(2 * N), p, q);
   __syncthreads();
   if (tid == 0) {
     for (int k = 0; k < p; ++k)
@@ -587,8 +630,9 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   if (sms > 48 * 1024)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  if ((e = launch_chunk_sums(F.Scon, 2 * P.N, P.p * P.p, F.chunkS, st)) != cudaSuccess) return e;
   count_launch();
-  k_schur<<<1, SBS, sms, st>>>(P, F.inert, F.Scon, E.wtt, sigma, dw, S);
+  k_schur<<<1, SBS, sms, st>>>(P, F.inert, F.chunkS, E.wtt, sigma, dw, S);
   return cudaGetLastError();
 }
 
@@ -622,8 +666,9 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
   k_bcr_fwd<T><<<1, tpb, smb, st>>>(P, F, 1, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   size_t smt = sizeof(double) * (size_t)(P.p > 0 ? P.p : 1);
+  if ((e = launch_chunk_sums(F.Rth, 2 * P.N, P.p, F.chunkR, st)) != cudaSuccess) return e;
   count_launch();
-  k_theta_solve<<<1, SBS, smt, st>>>(P, F.Rth, b, S, sol);
+  k_theta_solve<<<1, SBS, smt, st>>>(P, F.chunkR, b, S, sol);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   count_launch();
   k_bcr_bwd<T><<<1, tpb, smb, st>>>(P, F, S, sol, 1, 1);

@@ -111,17 +111,28 @@ __global__ void k_init_point(DevProb P, const double* __restrict__ theta0, doubl
 }
 
 // Collocation forward sweep at theta = x[nz..]: for each element in turn,
-// Newton's method on the K collocation equations in the interior states
-// (dense LU with partial pivoting of the 3n x 3n Jacobian), started at the
-// element's initial state; stop when max|dZ| <= 1e-12 max(1, max|Z|), at most
-// 30 iterations; a failed element keeps the constant guess.  One warp.
+// Newton's method on the K collocation equations in the element's interior
+// states, started at the element's initial state, stopped when
+// max|dZ| <= 1e-12 max(1, max|Z|) (at most 30 iterations); an element whose
+// iteration fails keeps the constant guess.  The residual, the update and
+// the stopping test are FP64; the Newton correction solves the Jacobian
+// system by FP32 LU with partial pivoting (an inexact Newton step whose
+// error the FP64 residual of the next iteration corrects), so the sweep
+// converges to the same FP64 collocation solution.  One block of SWEEP_BS
+// threads; the FP32 augmented matrix [J | G] sits in shared memory, or in
+// gwork when 3n is too large.
 constexpr int SWEEP_MAXIT = 30;
-__global__ void __launch_bounds__(32) k_forward_sweep(DevProb P, double* __restrict__ x,
-                                                      int* __restrict__ fails,
-                                                      double* __restrict__ gwork) {
+constexpr int SWEEP_BS = 256;
+__global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* __restrict__ x,
+                                                            int* __restrict__ fails,
+                                                            float* __restrict__ gwork) {
   extern __shared__ double sm[];
+  __shared__ int s_piv;
+  __shared__ float s_inv;
+  __shared__ double s_red[SWEEP_BS];
+  __shared__ int s_flag;
   const int n = P.n, r = P.r, dim = KC * n, ldj = dim + 1;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* kr = sm;                 // [r]
   double* mon = kr + r;            // [3][r]
   double* da = mon + KC * r;       // [3][r]
@@ -129,125 +140,145 @@ __global__ void __launch_bounds__(32) k_forward_sweep(DevProb P, double* __restr
   double* z0 = db + KC * r;        // [n]
   double* Z = z0 + n;              // [3n]
   double* dZ = Z + dim;            // [3n]
-  double* Jm = gwork ? gwork : (dZ + dim);  // [dim][dim+1]
+  float* Jm = gwork ? gwork : reinterpret_cast<float*>(dZ + dim);  // [dim][dim+1]
   const size_t nz = (size_t)P.N * NP * n;
-  for (int j = lane; j < r; j += 32) {
+  for (int j = tid; j < r; j += SWEEP_BS) {
     const int q = P.pidx[j];
     if (q < 0) kr[j] = P.kfix[j];
     else kr[j] = P.logscale ? exp10(x[nz + q]) : x[nz + q];
   }
-  for (int s = lane; s < n; s += 32) z0[s] = P.x0[s];
-  __syncwarp();
+  for (int s = tid; s < n; s += SWEEP_BS) z0[s] = P.x0[s];
+  __syncthreads();
   int nfail = 0;
   for (int i = 0; i < P.N; ++i) {
-    for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
-    __syncwarp();
+    for (int t = tid; t < dim; t += SWEEP_BS) Z[t] = z0[t % n];
+    __syncthreads();
     bool ok = false;
     for (int it = 0; it < SWEEP_MAXIT; ++it) {
-      for (int idx = lane; idx < KC * r; idx += 32) {
+      for (int idx = tid; idx < KC * r; idx += SWEEP_BS) {
         const int k = idx / r, j = idx - k * r;
         const int a = P.react[2 * j], b = P.react[2 * j + 1];
         const double za = Z[k * n + a];
         if (b < 0) { mon[idx] = za; da[idx] = 1.0; db[idx] = 0.0; }
         else { const double zb = Z[k * n + b]; mon[idx] = za * zb; da[idx] = zb; db[idx] = za; }
       }
-      __syncwarp();
-      // residual G (augmented column) and Jacobian rows
-      for (int row = lane; row < dim; row += 32) {
+      __syncthreads();
+      // Jacobian entries D[k][j] delta_st - delta_kj h df_s/dz_t, and G (FP64)
+      for (int idx = tid; idx < dim * dim; idx += SWEEP_BS) {
+        const int row = idx / dim, col = idx - row * dim;
         const int k = row / n + 1, s = row - (k - 1) * n;
-        double* Jr = Jm + (size_t)row * ldj;
+        const int j = col / n + 1, t = col - (j - 1) * n;
+        double v = (s == t) ? P.D[k][j] : 0.0;
+        if (j == k) {
+          double fz = 0.0;
+          for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
+            const int rr = P.nu_r[e];
+            const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+            const int mi = (k - 1) * r + rr;
+            double dm = 0.0;
+            if (a == t) dm += da[mi];
+            if (b == t) dm += db[mi];
+            fz += P.nu_v[e] * kr[rr] * dm;
+          }
+          v -= P.h * fz;
+        }
+        Jm[(size_t)row * ldj + col] = (float)v;
+      }
+      for (int row = tid; row < dim; row += SWEEP_BS) {
+        const int k = row / n + 1, s = row - (k - 1) * n;
         double g = P.D[k][0] * z0[s];
         for (int j = 1; j <= KC; ++j) g += P.D[k][j] * Z[(j - 1) * n + s];
-        for (int c = 0; c < dim; ++c) Jr[c] = 0.0;
-        for (int j = 1; j <= KC; ++j) Jr[(j - 1) * n + s] = P.D[k][j];
         double f = 0.0;
-        for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
-          const int rr = P.nu_r[e];
-          const double nk = P.nu_v[e] * kr[rr];
-          const int mi = (k - 1) * r + rr;
-          f += nk * mon[mi];
-          const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
-          Jr[(k - 1) * n + a] -= P.h * nk * da[mi];
-          if (b >= 0) Jr[(k - 1) * n + b] -= P.h * nk * db[mi];
-        }
-        Jr[dim] = g - P.h * f;
+        for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e)
+          f += P.nu_v[e] * kr[P.nu_r[e]] * mon[(k - 1) * r + P.nu_r[e]];
+        g -= P.h * f;
+        dZ[row] = g;
+        Jm[(size_t)row * ldj + dim] = (float)g;
       }
-      __syncwarp();
-      // LU with partial pivoting on the augmented matrix
-      bool singular = false;
+      if (tid == 0) s_flag = 0;
+      __syncthreads();
+      // FP32 LU with partial pivoting of [J | G]
       for (int c = 0; c < dim; ++c) {
-        double best = -1.0;
-        int bidx = dim;
-        for (int rr = c + lane; rr < dim; rr += 32) {
-          const double v = fabs(Jm[(size_t)rr * ldj + c]);
-          if (v > best) { best = v; bidx = rr; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-          if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-        }
-        if (!(best > 0.0) || !isfinite(best)) { singular = true; break; }
-        if (bidx != c)
-          for (int cc = c + lane; cc <= dim; cc += 32) {
-            const double t0 = Jm[(size_t)c * ldj + cc];
-            Jm[(size_t)c * ldj + cc] = Jm[(size_t)bidx * ldj + cc];
-            Jm[(size_t)bidx * ldj + cc] = t0;
+        if (warp == 0) {
+          float best = -1.f;
+          int bidx = dim;
+          for (int rr = c + lane; rr < dim; rr += 32) {
+            const float v = fabsf(Jm[(size_t)rr * ldj + c]);
+            if (v > best) { best = v; bidx = rr; }
           }
-        __syncwarp();
-        const double piv = Jm[(size_t)c * ldj + c];
-        for (int rr = c + 1 + lane; rr < dim; rr += 32) {
-          double* Jr = Jm + (size_t)rr * ldj;
-          const double f = Jr[c] / piv;
-          const double* Jc = Jm + (size_t)c * ldj;
-          for (int cc = c + 1; cc <= dim; ++cc) Jr[cc] -= f * Jc[cc];
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+          }
+          if (lane == 0) {
+            s_piv = bidx;
+            if (!(best > 0.f) || !isfinite(best)) s_flag = 1;
+          }
         }
-        __syncwarp();
+        __syncthreads();
+        if (s_flag) break;
+        const int piv = s_piv;
+        if (piv != c)
+          for (int cc = c + tid; cc <= dim; cc += SWEEP_BS) {
+            const float t0 = Jm[(size_t)c * ldj + cc];
+            Jm[(size_t)c * ldj + cc] = Jm[(size_t)piv * ldj + cc];
+            Jm[(size_t)piv * ldj + cc] = t0;
+          }
+        __syncthreads();
+        if (tid == 0) s_inv = 1.f / Jm[(size_t)c * ldj + c];
+        __syncthreads();
+        const float inv = s_inv;
+        const int w = dim - c;   // columns c+1..dim
+        for (int idx = tid; idx < (dim - c - 1) * w; idx += SWEEP_BS) {
+          const int rr = c + 1 + idx / w, cc = c + 1 + idx % w;
+          Jm[(size_t)rr * ldj + cc] -= (Jm[(size_t)rr * ldj + c] * inv) * Jm[(size_t)c * ldj + cc];
+        }
+        __syncthreads();
       }
-      if (singular) break;
+      if (s_flag) break;
+      // back substitution U dZ = g (FP32), columns eliminated from the right
       for (int c = dim - 1; c >= 0; --c) {
-        double s = 0.0;
-        for (int cc = c + 1 + lane; cc < dim; cc += 32) s += Jm[(size_t)c * ldj + cc] * dZ[cc];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) dZ[c] = (Jm[(size_t)c * ldj + dim] - s) / Jm[(size_t)c * ldj + c];
-        __syncwarp();
+        if (tid == 0) s_inv = Jm[(size_t)c * ldj + dim] / Jm[(size_t)c * ldj + c];
+        __syncthreads();
+        const float xc = s_inv;
+        for (int rr = tid; rr < c; rr += SWEEP_BS) Jm[(size_t)rr * ldj + dim] -= Jm[(size_t)rr * ldj + c] * xc;
+        if (tid == 0) dZ[c] = (double)xc;
+        __syncthreads();
       }
-      double mdz = 0.0, mz = 0.0;
-      bool fin = true;
-      for (int t = lane; t < dim; t += 32) {
+      double mdz = 0.0, mz = 0.0, bad = 0.0;
+      for (int t = tid; t < dim; t += SWEEP_BS) {
         Z[t] -= dZ[t];
-        fin = fin && isfinite(Z[t]);
+        if (!isfinite(Z[t])) bad = 1.0;
         mdz = fmax(mdz, fabs(dZ[t]));
         mz = fmax(mz, fabs(Z[t]));
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        mdz = fmax(mdz, __shfl_xor_sync(0xffffffffu, mdz, o));
-        mz = fmax(mz, __shfl_xor_sync(0xffffffffu, mz, o));
-      }
-      fin = __all_sync(0xffffffffu, fin);
-      __syncwarp();
-      if (!fin) break;
+      mdz = bmax<SWEEP_BS>(mdz, s_red);
+      mz = bmax<SWEEP_BS>(mz, s_red);
+      bad = bmax<SWEEP_BS>(bad, s_red);
+      if (bad > 0) break;
       if (mdz <= 1e-12 * fmax(1.0, mz)) { ok = true; break; }
     }
+    __syncthreads();
     if (!ok) {
       ++nfail;
-      for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
-      __syncwarp();
+      for (int t = tid; t < dim; t += SWEEP_BS) Z[t] = z0[t % n];
+      __syncthreads();
     }
     double* xi = x + (size_t)i * NP * n;
-    for (int s = lane; s < n; s += 32) xi[s] = z0[s];
-    for (int t = lane; t < dim; t += 32) xi[n + t] = Z[t];
-    __syncwarp();
-    for (int s = lane; s < n; s += 32) z0[s] = Z[(KC - 1) * n + s];
-    __syncwarp();
+    for (int s = tid; s < n; s += SWEEP_BS) xi[s] = z0[s];
+    for (int t = tid; t < dim; t += SWEEP_BS) xi[n + t] = Z[t];
+    __syncthreads();
+    for (int s = tid; s < n; s += SWEEP_BS) z0[s] = Z[(KC - 1) * n + s];
+    __syncthreads();
   }
-  if (lane == 0) *fails = nfail;
+  if (tid == 0) *fails = nfail;
 }
 
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
   const size_t dim = KC * (size_t)P.n;
   size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * KC) + P.n + 2 * dim);
-  if (jm_in_smem) v += sizeof(double) * dim * (dim + 1);
+  if (jm_in_smem) v += sizeof(float) * dim * (dim + 1);
   return v;
 }
 
@@ -257,7 +288,7 @@ cudaError_t launch_forward_sweep(collo_problem* pr) {
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_forward_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   count_launch();
-  k_forward_sweep<<<1, 32, sm, pr->stream>>>(pr->P, pr->x, pr->fails, pr->sweep_work);
+  k_forward_sweep<<<1, SWEEP_BS, sm, pr->stream>>>(pr->P, pr->x, pr->fails, pr->sweep_work);
   return cudaGetLastError();
 }
 

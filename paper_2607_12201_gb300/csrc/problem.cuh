@@ -23,6 +23,7 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
                              double* thpart, double* npart, const double* th_extra, double* out,
                              cudaStream_t st);
 // launchers (factor.cu)
+cudaError_t launch_chunk_sums(const double* X, int C, int L, double* part, cudaStream_t st);
 int bcr_levels(int N);
 template <typename T>
 size_t factor_work_elems(const DevProb& P, int n_slabs);
@@ -100,7 +101,7 @@ struct collo_problem {
   double* kvec_b = nullptr;   // [n_x + n_c]  solution
   double* kvec_r = nullptr;   // [n_x + n_c]  residual
   double* kvec_c = nullptr;   // [n_x + n_c]  correction
-  double* thpart = nullptr;   // [N][p]
+  double* thpart = nullptr;   // [N][p] then [CHUNKS][p] chunk sums
   double* npart = nullptr;    // [N][2]
   double* scal = nullptr;     // [64] device scalars
   double* red_parts = nullptr;  // [256] partial sums of two-stage reductions
@@ -113,6 +114,6 @@ struct collo_problem {
   double* dz = nullptr;       // [2p] bound-dual steps
   double* thx = nullptr;      // [2p] parameter-space helper vectors
   int* fails = nullptr;       // [1]
-  double* sweep_work = nullptr;  // forward-sweep Newton matrix when too big for smem
+  float* sweep_work = nullptr;   // forward-sweep FP32 Newton matrix when too big for smem
   int64_t n_x = 0, n_c = 0;
 };
