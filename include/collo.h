@@ -116,7 +116,11 @@ typedef struct collo_problem_options {
   int precision;              /* COLLO_PRECISION_*, default for factor/solve */
   void* stream;               /* cudaStream_t to run on, or NULL for an own stream */
   int device;                 /* CUDA device ordinal (default 0) */
-  int reserved[7];
+  int launch_mode;            /* 0: each factorization / solve is one persistent
+                                 cooperative kernel (levels separated by a bounded
+                                 grid barrier); 1: one kernel launch per level.
+                                 Both give bitwise-identical results. */
+  int reserved[6];
 } collo_problem_options;
 
 typedef struct collo_problem collo_problem;

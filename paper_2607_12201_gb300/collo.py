@@ -52,7 +52,7 @@ class Mesh(C.Structure):
 
 class ProblemOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("device", C.c_int),
-                ("reserved", C.c_int * 7)]
+                ("launch_mode", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class Sizes(C.Structure):
@@ -167,7 +167,8 @@ def _i32(a):
 class Problem:
     """One estimation problem resident on the GPU (wraps collo_problem)."""
 
-    def __init__(self, inst, precision: int = FP64, stream: int | None = None, device: int = 0):
+    def __init__(self, inst, precision: int = FP64, stream: int | None = None, device: int = 0,
+                 launch_mode: int = 0):
         self.inst = inst
         species = np.unique(inst.obs_s)
         obs_index = np.searchsorted(species, inst.obs_s)
@@ -184,7 +185,7 @@ class Problem:
         obs = Observables(len(species), ip(k["species"]))
         data = Data(inst.M, dp(k["t"]), ip(k["obs"]), dp(k["y"]), dp(k["sig"]))
         mesh = Mesh(float(inst.T), int(inst.N), int(inst.K))
-        opt = ProblemOptions(precision, stream, device)
+        opt = ProblemOptions(precision, stream, device, launch_mode)
         h = C.c_void_p()
         _check(lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh),
                                         C.byref(opt), C.byref(h)))

@@ -62,6 +62,9 @@ static collo_status alloc_factor(collo_problem* pr, FactorStore<T>& fs) {
   F.Rth = A.alloc<double>(2 * N * p);
   F.chunkS = A.alloc<double>((size_t)CHUNKS * p * p);
   F.chunkR = A.alloc<double>((size_t)CHUNKS * p);
+  F.gbar = A.alloc<GridBar>(1);
+  if (F.gbar) cudaMemset(F.gbar, 0, sizeof(GridBar));
+  F.persistent = pr->launch_mode == 0 ? 1 : 0;
   F.n_slabs = pr->n_slabs;
   size_t w = factor_work_elems<T>(P, pr->n_slabs);
   F.work = w ? A.alloc<T>(w) : nullptr;
@@ -149,6 +152,11 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   std::unique_ptr<collo_problem> pr(new collo_problem());
   pr->device = dev;
   pr->precision = opts ? opts->precision : 0;
+  pr->launch_mode = opts ? opts->launch_mode : 0;
+  if (pr->launch_mode != 0 && pr->launch_mode != 1) {
+    set_error("launch_mode must be 0 or 1");
+    return COLLO_ERR_INVALID_ARG;
+  }
   if (opts && opts->stream) {
     pr->stream = (cudaStream_t)opts->stream;
   } else {
@@ -394,8 +402,17 @@ collo_status factor_internal(collo_problem* prob, double dw, double dc, int prec
     COLLO_CUDA(launch_factor<double>(prob->P, prob->E, prob->sigma, dw, dc, prob->f64.F, prob->S, st));
   COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 40, prob->S.inertia, 3 * sizeof(long long),
                              cudaMemcpyDeviceToHost, st));
+  GridBar* gb = precision == COLLO_PRECISION_MIXED ? prob->f32.F.gbar : prob->f64.F.gbar;
+  COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 44, &gb->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   COLLO_CUDA(cudaStreamSynchronize(st));
   std::memcpy(inertia, prob->hscal + 40, 3 * sizeof(long long));
+  int berr = 0;
+  std::memcpy(&berr, prob->hscal + 44, sizeof(int));
+  if (berr) {
+    cudaMemsetAsync(&gb->err, 0, sizeof(int), st);
+    set_error("grid barrier of the factorization kernel timed out");
+    return COLLO_ERR_TIMEOUT;
+  }
   prob->factored = precision;
   prob->fac_dw = dw;
   prob->fac_dc = dc;
@@ -422,7 +439,16 @@ collo_status solve_internal(collo_problem* prob, const double* b, double* sol, i
                                 prob->thpart, prob->npart, nullptr, prob->scal + 8, st));
     COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 8, prob->scal + 8, 3 * sizeof(double),
                                cudaMemcpyDeviceToHost, st));
+    GridBar* gb = prob->factored == COLLO_PRECISION_MIXED ? prob->f32.F.gbar : prob->f64.F.gbar;
+    COLLO_CUDA(cudaMemcpyAsync(prob->hscal + 12, &gb->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     COLLO_CUDA(cudaStreamSynchronize(st));
+    int berr = 0;
+    std::memcpy(&berr, prob->hscal + 12, sizeof(int));
+    if (berr) {
+      cudaMemsetAsync(&gb->err, 0, sizeof(int), st);
+      set_error("grid barrier of the solve kernel timed out");
+      return COLLO_ERR_TIMEOUT;
+    }
     double rn = std::max(prob->hscal[8], prob->hscal[9]);
     double bn = std::max(1.0, prob->hscal[10]);
     rel = rn / bn;

@@ -77,6 +77,15 @@ struct DevEval {
   double* wtt;      // [p]
 };
 
+// Grid barrier state of the persistent cooperative kernels (device memory,
+// zero-initialised; err != 0 records a barrier that gave up waiting).
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
 // Factorization storage (T = double or float).
 template <typename T>
 struct DevFactor {
@@ -98,6 +107,8 @@ struct DevFactor {
   double* Rth;   // [2N][p]  parameter rhs contributions
   double* chunkS;  // [CHUNKS][p][p] partial sums of Scon
   double* chunkR;  // [CHUNKS][p]    partial sums of Rth
+  GridBar* gbar;   // barrier of the persistent kernels
+  int persistent;  // 1: persistent cooperative kernels, 0: one launch per level
 };
 
 // Deterministic two-stage sums over many per-block contributions: stage 1

@@ -121,54 +121,65 @@ __device__ inline double elem_entry(const DevProb& P, const DevEval& E, int e, i
 __host__ __device__ inline int odd_ld(int m) { return (m & 1) ? m : m + 1; }
 
 // ---- 1. element condensation --------------------------------------------------
+// One CUDA block condenses element e: assemble the bordered (8n + p) block,
+// eliminate the 3n interior pairs, write L, pivots, the 2n x 2n interface
+// block, its border, the p x p Schur contribution and the coupling -I.
+template <typename T>
+__device__ void elem_factor_one(const DevProb& P, const DevEval& E,
+                                const double* __restrict__ sigma, double dw, double dc,
+                                const DevFactor<T>& F, int e, T* A, T* cc0, T* cc1, T* l0s,
+                                T* l1s) {
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext, ld = odd_ld(ext);
+  const int tid = threadIdx.x;
+  const int nint = 3 * n;          // interior pairs
+  const int i0 = 2 * nint;         // first interface row (6n)
+  for (int a = tid >> 5; a < ext; a += FTY)
+    for (int b = tid & 31; b <= a; b += 32)
+      A[a * ld + b] = (T)elem_entry(P, E, e, a, b, sigma, dw, dc);
+  __syncthreads();
+  int pos = 0, neg = 0, zero = 0;
+  pair_eliminate<T>(A, ld, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+                    F.Del + (size_t)e * nint * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+  if (tid == 0) {
+    F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
+  }
+  const int n2 = 2 * n;
+  T* Aif = F.Aif + (size_t)e * n2 * n2;
+  for (int idx = tid; idx < n2 * n2; idx += FBS) {
+    const int u = idx / n2, v = idx - u * n2;
+    Aif[idx] = u >= v ? A[(i0 + u) * ld + i0 + v] : A[(i0 + v) * ld + i0 + u];
+  }
+  T* Bif = F.Bif + (size_t)e * n2 * p;
+  for (int idx = tid; idx < n2 * p; idx += FBS) {
+    const int u = idx / p, q = idx - u * p;
+    Bif[idx] = A[(m + q) * ld + i0 + u];
+  }
+  double* Sc = F.Scon + (size_t)e * p * p;
+  for (int idx = tid; idx < p * p; idx += FBS) {
+    const int q = idx / p, q2 = idx - q * p;
+    Sc[idx] = (double)(q >= q2 ? A[(m + q) * ld + m + q2] : A[(m + q2) * ld + m + q]);
+  }
+  T* C = F.Cpl + (size_t)e * n * n;
+  for (int idx = tid; idx < n * n; idx += FBS) {
+    const int s = idx / n, t = idx - s * n;
+    C[idx] = (e > 0 && s == t) ? T(-1) : T(0);
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FBS)
 k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
               DevFactor<T> F, int use_smem) {
   extern __shared__ unsigned char smraw[];
-  const int n = P.n, p = P.p, m = P.m, ext = P.ext, ld = odd_ld(ext);
+  const int ext = P.ext, ld = odd_ld(ext);
   T* cc0 = reinterpret_cast<T*>(smraw);
   T* cc1 = cc0 + ext;
   T* l0s = cc1 + ext;
   T* l1s = l0s + ext;
   T* A = use_smem ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
-  const int tid = threadIdx.x;
-  const int nint = 3 * n;          // interior pairs
-  const int i0 = 2 * nint;         // first interface row (6n)
-  for (int e = blockIdx.x; e < P.N; e += gridDim.x) {
-    for (int a = tid >> 5; a < ext; a += FTY)
-      for (int b = tid & 31; b <= a; b += 32)
-        A[a * ld + b] = (T)elem_entry(P, E, e, a, b, sigma, dw, dc);
-    __syncthreads();
-    int pos = 0, neg = 0, zero = 0;
-    pair_eliminate<T>(A, ld, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                      F.Del + (size_t)e * nint * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
-    if (tid == 0) {
-      F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
-    }
-    const int n2 = 2 * n;
-    T* Aif = F.Aif + (size_t)e * n2 * n2;
-    for (int idx = tid; idx < n2 * n2; idx += FBS) {
-      const int u = idx / n2, v = idx - u * n2;
-      Aif[idx] = u >= v ? A[(i0 + u) * ld + i0 + v] : A[(i0 + v) * ld + i0 + u];
-    }
-    T* Bif = F.Bif + (size_t)e * n2 * p;
-    for (int idx = tid; idx < n2 * p; idx += FBS) {
-      const int u = idx / p, q = idx - u * p;
-      Bif[idx] = A[(m + q) * ld + i0 + u];
-    }
-    double* Sc = F.Scon + (size_t)e * p * p;
-    for (int idx = tid; idx < p * p; idx += FBS) {
-      const int q = idx / p, q2 = idx - q * p;
-      Sc[idx] = (double)(q >= q2 ? A[(m + q) * ld + m + q2] : A[(m + q2) * ld + m + q]);
-    }
-    T* C = F.Cpl + (size_t)e * n * n;
-    for (int idx = tid; idx < n * n; idx += FBS) {
-      const int s = idx / n, t = idx - s * n;
-      C[idx] = (e > 0 && s == t) ? T(-1) : T(0);
-    }
-    __syncthreads();
-  }
+  for (int e = blockIdx.x; e < P.N; e += gridDim.x)
+    elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, cc0, cc1, l0s, l1s);
 }
 
 // ---- 2. one level of block cyclic reduction -------------------------------------
@@ -176,96 +187,103 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
 // Local order of the extended block: [interface of block i (2n) | z3 of the
 // left neighbour (n) | c0 of the right neighbour (n) | theta (p)].
 template <typename T>
+__device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stride,
+                               int final_level, int bi, T* A, T* cc0, T* cc1, T* l0s, T* l1s) {
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
+  const int tid = threadIdx.x;
+  const int i = final_level ? 0 : stride * (2 * bi + 1);
+  const int L = final_level ? -1 : i - stride;
+  const int R = (!final_level && i + stride < N) ? i + stride : -1;
+  const T* Ai = F.Aif + (size_t)i * n2 * n2;
+  const T* Ci = F.Cpl + (size_t)i * n * n;
+  const T* CR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
+  const T* Bi = F.Bif + (size_t)i * n2 * p;
+  for (int a = tid >> 5; a < bext; a += FTY)
+    for (int b = tid & 31; b <= a; b += 32) {
+      T v = T(0);
+      if (a < n2) {
+        v = Ai[a * n2 + b];
+      } else if (b < n2) {
+        if (a < 3 * n) {                       // z3 of left neighbour, t = a - 2n
+          if (L >= 0 && (b & 1)) v = Ci[(b >> 1) * n + (a - n2)];
+        } else if (a < 4 * n) {                // c0 of right neighbour, s = a - 3n
+          if (R >= 0 && !(b & 1)) v = CR[(a - 3 * n) * n + (b >> 1)];
+        } else {                               // theta row q = a - 4n
+          v = Bi[b * p + (a - 4 * n)];
+        }
+      }
+      A[a * ld + b] = v;
+    }
+  __syncthreads();
+  int pos = 0, neg = 0, zero = 0;
+  pair_eliminate<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
+                    F.Db + (size_t)i * n * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+  if (tid == 0) {
+    int* in = F.inert + (size_t)(N + i) * 3;
+    in[0] = pos; in[1] = neg; in[2] = zero;
+  }
+  // scatter the trailing (Schur) block into the neighbours
+  if (L >= 0) {
+    T* AL = F.Aif + (size_t)L * n2 * n2;
+    for (int idx = tid; idx < n * n; idx += FBS) {
+      const int t = idx / n, t2 = idx - t * n;
+      const int ra = n2 + t, rb = n2 + t2;
+      AL[(2 * t) * n2 + 2 * t2] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
+    }
+    T* BL = F.Bif + (size_t)L * n2 * p;
+    for (int idx = tid; idx < n * p; idx += FBS) {
+      const int t = idx / p, q = idx - t * p;
+      BL[(2 * t) * p + q] += A[(4 * n + q) * ld + n2 + t];
+    }
+  }
+  if (R >= 0) {
+    T* AR = F.Aif + (size_t)R * n2 * n2;
+    T* CRw = F.Cpl + (size_t)R * n * n;
+    for (int idx = tid; idx < n * n; idx += FBS) {
+      const int s = idx / n, s2 = idx - s * n;
+      const int ra = 3 * n + s, rb = 3 * n + s2;
+      AR[(2 * s + 1) * n2 + 2 * s2 + 1] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
+      CRw[idx] = (L >= 0) ? A[(3 * n + s) * ld + n2 + s2] : T(0);
+    }
+    T* BR = F.Bif + (size_t)R * n2 * p;
+    for (int idx = tid; idx < n * p; idx += FBS) {
+      const int s = idx / p, q = idx - s * p;
+      BR[(2 * s + 1) * p + q] += A[(4 * n + q) * ld + 3 * n + s];
+    }
+  }
+  double* Sc = F.Scon + (size_t)(N + i) * p * p;
+  for (int idx = tid; idx < p * p; idx += FBS) {
+    const int q = idx / p, q2 = idx - q * p;
+    const int ra = 4 * n + q, rb = 4 * n + q2;
+    Sc[idx] = (double)(ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra]);
+  }
+  __syncthreads();
+}
+
+__host__ __device__ inline int bcr_level_blocks(int N, int stride) {
+  return (N - stride + 2 * stride - 1) / (2 * stride);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(FBS)
 k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
   extern __shared__ unsigned char smraw[];
-  const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
+  const int bext = P.bext, ld = odd_ld(bext);
   T* cc0 = reinterpret_cast<T*>(smraw);
   T* cc1 = cc0 + bext;
   T* l0s = cc1 + bext;
   T* l1s = l0s + bext;
   T* A = use_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
-  const int tid = threadIdx.x;
-  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
-  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
-    const int i = final_level ? 0 : stride * (2 * bi + 1);
-    const int L = final_level ? -1 : i - stride;
-    const int R = (!final_level && i + stride < N) ? i + stride : -1;
-    const T* Ai = F.Aif + (size_t)i * n2 * n2;
-    const T* Ci = F.Cpl + (size_t)i * n * n;
-    const T* CR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
-    const T* Bi = F.Bif + (size_t)i * n2 * p;
-    for (int a = tid >> 5; a < bext; a += FTY)
-      for (int b = tid & 31; b <= a; b += 32) {
-        T v = T(0);
-        if (a < n2) {
-          v = Ai[a * n2 + b];
-        } else if (b < n2) {
-          if (a < 3 * n) {                       // z3 of left neighbour, t = a - 2n
-            if (L >= 0 && (b & 1)) v = Ci[(b >> 1) * n + (a - n2)];
-          } else if (a < 4 * n) {                // c0 of right neighbour, s = a - 3n
-            if (R >= 0 && !(b & 1)) v = CR[(a - 3 * n) * n + (b >> 1)];
-          } else {                               // theta row q = a - 4n
-            v = Bi[b * p + (a - 4 * n)];
-          }
-        }
-        A[a * ld + b] = v;
-      }
-    __syncthreads();
-    int pos = 0, neg = 0, zero = 0;
-    pair_eliminate<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
-                      F.Db + (size_t)i * n * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
-    if (tid == 0) {
-      int* in = F.inert + (size_t)(N + i) * 3;
-      in[0] = pos; in[1] = neg; in[2] = zero;
-    }
-    // scatter the trailing (Schur) block into the neighbours
-    if (L >= 0) {
-      T* AL = F.Aif + (size_t)L * n2 * n2;
-      for (int idx = tid; idx < n * n; idx += FBS) {
-        const int t = idx / n, t2 = idx - t * n;
-        const int ra = n2 + t, rb = n2 + t2;
-        AL[(2 * t) * n2 + 2 * t2] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
-      }
-      T* BL = F.Bif + (size_t)L * n2 * p;
-      for (int idx = tid; idx < n * p; idx += FBS) {
-        const int t = idx / p, q = idx - t * p;
-        BL[(2 * t) * p + q] += A[(4 * n + q) * ld + n2 + t];
-      }
-    }
-    if (R >= 0) {
-      T* AR = F.Aif + (size_t)R * n2 * n2;
-      T* CRw = F.Cpl + (size_t)R * n * n;
-      for (int idx = tid; idx < n * n; idx += FBS) {
-        const int s = idx / n, s2 = idx - s * n;
-        const int ra = 3 * n + s, rb = 3 * n + s2;
-        AR[(2 * s + 1) * n2 + 2 * s2 + 1] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
-        CRw[idx] = (L >= 0) ? A[(3 * n + s) * ld + n2 + s2] : T(0);
-      }
-      T* BR = F.Bif + (size_t)R * n2 * p;
-      for (int idx = tid; idx < n * p; idx += FBS) {
-        const int s = idx / p, q = idx - s * p;
-        BR[(2 * s + 1) * p + q] += A[(4 * n + q) * ld + 3 * n + s];
-      }
-    }
-    double* Sc = F.Scon + (size_t)(N + i) * p * p;
-    for (int idx = tid; idx < p * p; idx += FBS) {
-      const int q = idx / p, q2 = idx - q * p;
-      const int ra = 4 * n + q, rb = 4 * n + q2;
-      Sc[idx] = (double)(ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra]);
-    }
-    __syncthreads();
-  }
+  const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
+    bcr_factor_one<T>(P, F, stride, final_level, bi, A, cc0, cc1, l0s, l1s);
 }
 
 // ---- 3. parameter Schur complement (FP64) ------------------------------------------
 // part[g][l] = sum of X[c][l] over the g-th of G contiguous chunks of c.
 constexpr int CS_BS = 256;
-__global__ void __launch_bounds__(CS_BS)
-k_chunk_sums(const double* __restrict__ X, int C, int L, int G, double* __restrict__ part) {
-  const int l = blockIdx.x * CS_BS + threadIdx.x;
-  const int g = blockIdx.y;
-  if (l >= L) return;
+__device__ inline double chunk_sum_item(const double* __restrict__ X, int C, int L, int G, int g,
+                                        int l) {
   const int c0 = (int)((long long)C * g / G), c1 = (int)((long long)C * (g + 1) / G);
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int c = c0;
@@ -276,7 +294,15 @@ k_chunk_sums(const double* __restrict__ X, int C, int L, int G, double* __restri
     a3 += X[(size_t)(c + 3) * L + l];
   }
   for (; c < c1; ++c) a0 += X[(size_t)c * L + l];
-  part[(size_t)g * L + l] = (a0 + a1) + (a2 + a3);
+  return (a0 + a1) + (a2 + a3);
+}
+
+__global__ void __launch_bounds__(CS_BS)
+k_chunk_sums(const double* __restrict__ X, int C, int L, int G, double* __restrict__ part) {
+  const int l = blockIdx.x * CS_BS + threadIdx.x;
+  const int g = blockIdx.y;
+  if (l >= L) return;
+  part[(size_t)g * L + l] = chunk_sum_item(X, C, L, G, g, l);
 }
 
 cudaError_t launch_chunk_sums(const double* X, int C, int L, double* part, cudaStream_t st) {
@@ -301,12 +327,14 @@ __device__ inline double sum_chunks(const double* __restrict__ part, int G, int 
 }
 
 constexpr int SBS = 256;
-__global__ void __launch_bounds__(SBS)
-k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chunkS,
-        const double* __restrict__ wtt, const double* __restrict__ sigma, double dw,
-        DevSchur S) {
-  extern __shared__ double sS[];      // [p][p] then l[p]
+// One block: S = (chunk sums of all contributions) + diag(W_thth + sigma + dw),
+// FP64 LDL^T with 1x1 pivots, total inertia.  sS: dynamic shared [p][p] + [p].
+__device__ void schur_block(const DevProb& P, const int* __restrict__ inert,
+                            const double* __restrict__ chunkS, const double* __restrict__ wtt,
+                            const double* __restrict__ sigma, double dw, const DevSchur& S,
+                            double* sS) {
   __shared__ long long cnt[3];
+  __shared__ long long red[3][SBS];
   const int p = P.p, N = P.N, tid = threadIdx.x;
   const size_t nz = (size_t)N * NP * P.n;
   double* l = sS + (size_t)p * p;
@@ -319,7 +347,6 @@ k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chu
   {
     long long a = 0, b = 0, c = 0;
     for (int k = tid; k < 2 * N; k += SBS) { a += inert[3 * k]; b += inert[3 * k + 1]; c += inert[3 * k + 2]; }
-    __shared__ long long red[3][SBS];
     red[0][tid] = a; red[1][tid] = b; red[2][tid] = c;
     __syncthreads();
     for (int s = SBS / 2; s > 0; s >>= 1) {
@@ -339,8 +366,9 @@ k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chu
       S.Sd[k] = d;
     }
     __syncthreads();
-    for (int idx = tid; idx < (p - k - 1) * (p - k - 1); idx += SBS) {
-      const int r = k + 1 + idx / (p - k - 1), c = k + 1 + idx % (p - k - 1);
+    const int w = p - k - 1;
+    for (int idx = tid; idx < w * w; idx += SBS) {
+      const int r = k + 1 + idx / w, c = k + 1 + idx % w;
       if (c <= r) sS[r * p + c] -= l[r] * sS[c * p + k];
     }
     __syncthreads();
@@ -349,6 +377,15 @@ k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chu
   }
   for (int idx = tid; idx < p * p; idx += SBS) S.S[idx] = sS[idx];
   if (tid == 0) { S.inertia[0] = cnt[0]; S.inertia[1] = cnt[1]; S.inertia[2] = cnt[2]; }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SBS)
+k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chunkS,
+        const double* __restrict__ wtt, const double* __restrict__ sigma, double dw,
+        DevSchur S) {
+  extern __shared__ double sS[];
+  schur_block(P, inert, chunkS, wtt, sigma, dw, S, sS);
 }
 
 // ---- solves: one warp per block ----------------------------------------------------
@@ -417,14 +454,10 @@ __device__ inline size_t elem_global(const DevProb& P, int e, int a) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * SOLVE_WARPS)
-k_elem_fwd(DevProb P, DevFactor<T> F, const double* __restrict__ b) {
-  extern __shared__ unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * SOLVE_WARPS + warp;
+__device__ void elem_fwd_one(const DevProb& P, const DevFactor<T>& F, const double* __restrict__ b,
+                             int e, T* w) {
+  const int lane = threadIdx.x & 31;
   const int n = P.n, ext = P.ext, m = P.m, p = P.p;
-  T* w = reinterpret_cast<T*>(smraw) + (size_t)warp * ext;
-  if (e >= P.N) return;
   for (int a = lane; a < ext; a += 32) w[a] = a < m ? (T)b[elem_global(P, e, a)] : T(0);
   __syncwarp();
   const int nint = 3 * n;
@@ -441,18 +474,14 @@ k_elem_fwd(DevProb P, DevFactor<T> F, const double* __restrict__ b) {
   for (int u = lane; u < 2 * n; u += 32) Rif[u] = w[2 * nint + u];
   double* Rth = F.Rth + (size_t)e * p;
   for (int q = lane; q < p; q += 32) Rth[q] = (double)w[m + q];
+  __syncwarp();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * SOLVE_WARPS)
-k_bcr_fwd(DevProb P, DevFactor<T> F, int stride, int final_level) {
-  extern __shared__ unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ void bcr_fwd_one(const DevProb& P, const DevFactor<T>& F, int stride, int final_level,
+                            int bi, T* w) {
+  const int lane = threadIdx.x & 31;
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
-  T* w = reinterpret_cast<T*>(smraw) + (size_t)warp * bext;
-  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
-  const int bi = blockIdx.x * SOLVE_WARPS + warp;
-  if (bi >= nblk) return;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
   const int R = (!final_level && i + stride < N) ? i + stride : -1;
@@ -477,43 +506,50 @@ k_bcr_fwd(DevProb P, DevFactor<T> F, int stride, int final_level) {
   }
   double* Rth = F.Rth + (size_t)(N + i) * p;
   for (int q = lane; q < p; q += 32) Rth[q] = (double)w[4 * n + q];
+  __syncwarp();
 }
 
-// Parameter solve: rhs = b_theta + all contributions (fixed order), then the
-// FP64 LDL^T of the Schur complement.  Writes x_theta into sol.
+// Parameter solve by one block: rhs = b_theta + chunk sums of the
+// contributions, then the FP64 LDL^T of the Schur complement (column-oriented
+// substitutions, one barrier per column).  sv: dynamic shared [p].
+__device__ void theta_solve_block(const DevProb& P, const double* __restrict__ chunkR,
+                                  const double* __restrict__ b, const DevSchur& S,
+                                  double* __restrict__ sol, double* sv) {
+  const int p = P.p, N = P.N, tid = threadIdx.x;
+  const size_t nz = (size_t)N * NP * P.n;
+  for (int q = tid; q < p; q += blockDim.x) sv[q] = b[nz + q] + sum_chunks(chunkR, n_chunks(2 * N), p, q);
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    const double xk = sv[k];
+    for (int r = k + 1 + tid; r < p; r += blockDim.x) sv[r] -= S.S[r * p + k] * xk;
+    __syncthreads();
+  }
+  for (int k = tid; k < p; k += blockDim.x) {
+    const double d = S.Sd[k];
+    sv[k] = (d != 0.0 && isfinite(d)) ? sv[k] / d : 0.0;
+  }
+  __syncthreads();
+  for (int k = p - 1; k >= 0; --k) {
+    const double xk = sv[k];
+    for (int r = tid; r < k; r += blockDim.x) sv[r] -= S.S[k * p + r] * xk;
+    __syncthreads();
+  }
+  for (int q = tid; q < p; q += blockDim.x) { sol[nz + q] = sv[q]; S.xth[q] = sv[q]; }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(SBS)
 k_theta_solve(DevProb P, const double* __restrict__ chunkR, const double* __restrict__ b,
               DevSchur S, double* __restrict__ sol) {
   extern __shared__ double sv[];
-  const int p = P.p, N = P.N, tid = threadIdx.x;
-  const size_t nz = (size_t)N * NP * P.n;
-  for (int q = tid; q < p; q += SBS) sv[q] = b[nz + q] + sum_chunks(chunkR, n_chunks(2 * N), p, q);
-  __syncthreads();
-  if (tid == 0) {
-    for (int k = 0; k < p; ++k)
-      for (int r = k + 1; r < p; ++r) sv[r] -= S.S[r * p + k] * sv[k];
-    for (int k = 0; k < p; ++k) {
-      const double d = S.Sd[k];
-      sv[k] = (d != 0.0 && isfinite(d)) ? sv[k] / d : 0.0;
-    }
-    for (int k = p - 1; k >= 0; --k)
-      for (int r = k + 1; r < p; ++r) sv[k] -= S.S[r * p + k] * sv[r];
-  }
-  __syncthreads();
-  for (int q = tid; q < p; q += SBS) { sol[nz + q] = sv[q]; S.xth[q] = sv[q]; }
+  theta_solve_block(P, chunkR, b, S, sol, sv);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * SOLVE_WARPS)
-k_bcr_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol, int stride,
-          int final_level) {
-  extern __shared__ unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ void bcr_bwd_one(const DevProb& P, const DevFactor<T>& F, const DevSchur& S,
+                            double* __restrict__ sol, int stride, int final_level, int bi, T* x) {
+  const int lane = threadIdx.x & 31;
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
-  T* x = reinterpret_cast<T*>(smraw) + (size_t)warp * bext;
-  const int nblk = final_level ? 1 : (N - stride + 2 * stride - 1) / (2 * stride);
-  const int bi = blockIdx.x * SOLVE_WARPS + warp;
-  if (bi >= nblk) return;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
   const int R = (!final_level && i + stride < N) ? i + stride : -1;
@@ -535,17 +571,14 @@ k_bcr_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol, int s
     sol[((size_t)i * NP + KC) * n + s] = (double)x[2 * s];
     sol[nx + (size_t)i * NP * n + s] = (double)x[2 * s + 1];
   }
+  __syncwarp();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * SOLVE_WARPS)
-k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
-  extern __shared__ unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * SOLVE_WARPS + warp;
+__device__ void elem_bwd_one(const DevProb& P, const DevFactor<T>& F, const DevSchur& S,
+                             double* __restrict__ sol, int e, T* x) {
+  const int lane = threadIdx.x & 31;
   const int n = P.n, ext = P.ext, m = P.m;
-  T* x = reinterpret_cast<T*>(smraw) + (size_t)warp * ext;
-  if (e >= P.N) return;
   const int nint = 3 * n;
   for (int a = lane; a < ext; a += 32) {
     T v = T(0);
@@ -557,6 +590,167 @@ k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
   warp_backward<T>(x, F.Vint + (size_t)e * 2 * nint, ext, nint,
                    F.Lel + (size_t)e * (2 * nint) * ext, ext);
   for (int a = lane; a < 2 * nint; a += 32) sol[elem_global(P, e, a)] = (double)x[a];
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_elem_fwd(DevProb P, DevFactor<T> F, const double* __restrict__ b) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * SOLVE_WARPS + warp;
+  if (e >= P.N) return;
+  elem_fwd_one<T>(P, F, b, e, reinterpret_cast<T*>(smraw) + (size_t)warp * P.ext);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_bcr_fwd(DevProb P, DevFactor<T> F, int stride, int final_level) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
+  const int bi = blockIdx.x * SOLVE_WARPS + warp;
+  if (bi >= nblk) return;
+  bcr_fwd_one<T>(P, F, stride, final_level, bi, reinterpret_cast<T*>(smraw) + (size_t)warp * P.bext);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_bcr_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol, int stride,
+          int final_level) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
+  const int bi = blockIdx.x * SOLVE_WARPS + warp;
+  if (bi >= nblk) return;
+  bcr_bwd_one<T>(P, F, S, sol, stride, final_level, bi,
+                 reinterpret_cast<T*>(smraw) + (size_t)warp * P.bext);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * SOLVE_WARPS + warp;
+  if (e >= P.N) return;
+  elem_bwd_one<T>(P, F, S, sol, e, reinterpret_cast<T*>(smraw) + (size_t)warp * P.ext);
+}
+
+// ---- persistent cooperative kernels ------------------------------------------------
+// A whole factorization or a whole solve in one cooperative launch: the phases
+// of the elimination tree (elements, each cyclic-reduction level, the
+// parameter block) are separated by a grid barrier instead of kernel
+// boundaries.  The barrier's wait is bounded: after GRID_SPIN_LIMIT polls it
+// records an error in GridBar::err and continues, so a fault shows up as a
+// status on the host instead of a hang.
+constexpr long long GRID_SPIN_LIMIT = 20000000;   // ~1-2 s of polling
+
+__device__ void grid_barrier(GridBar* gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &gb->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        __nanosleep(40);
+        if (++spins > GRID_SPIN_LIMIT) { atomicExch(&gb->err, 1); break; }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FBS)
+k_factor_persistent(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
+                    DevFactor<T> F, DevSchur S, GridBar* gb, int elem_smem, int bcr_smem) {
+  extern __shared__ unsigned char smraw[];
+  const int N = P.N;
+  {
+    const int ext = P.ext, ld = odd_ld(ext);
+    T* cc0 = reinterpret_cast<T*>(smraw);
+    T* cc1 = cc0 + ext;
+    T* l0s = cc1 + ext;
+    T* l1s = l0s + ext;
+    T* A = elem_smem ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
+    for (int e = blockIdx.x; e < N; e += gridDim.x)
+      elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, cc0, cc1, l0s, l1s);
+  }
+  grid_barrier(gb);
+  {
+    const int bext = P.bext, ld = odd_ld(bext);
+    T* cc0 = reinterpret_cast<T*>(smraw);
+    T* cc1 = cc0 + bext;
+    T* l0s = cc1 + bext;
+    T* l1s = l0s + bext;
+    T* A = bcr_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
+    for (int s = 1; s < N; s *= 2) {
+      const int nblk = bcr_level_blocks(N, s);
+      for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
+        bcr_factor_one<T>(P, F, s, 0, bi, A, cc0, cc1, l0s, l1s);
+      grid_barrier(gb);
+    }
+    if (blockIdx.x == 0) bcr_factor_one<T>(P, F, 1, 1, 0, A, cc0, cc1, l0s, l1s);
+  }
+  grid_barrier(gb);
+  {
+    const int L = P.p * P.p, G = n_chunks(2 * N);
+    for (int it = blockIdx.x * FBS + threadIdx.x; it < G * L; it += gridDim.x * FBS)
+      F.chunkS[it] = chunk_sum_item(F.Scon, 2 * N, L, G, it / L, it % L);
+  }
+  grid_barrier(gb);
+  if (blockIdx.x == 0)
+    schur_block(P, F.inert, F.chunkS, E.wtt, sigma, dw, S, reinterpret_cast<double*>(smraw));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FBS)
+k_solve_persistent(DevProb P, DevFactor<T> F, DevSchur S, const double* __restrict__ b,
+                   double* __restrict__ sol, GridBar* gb) {
+  extern __shared__ unsigned char smraw[];
+  const int N = P.N, warp = threadIdx.x >> 5;
+  const int wpb = FBS / 32;
+  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  T* wv = reinterpret_cast<T*>(smraw) + (size_t)warp * (P.ext > P.bext ? P.ext : P.bext);
+  for (int e = gw; e < N; e += nw) elem_fwd_one<T>(P, F, b, e, wv);
+  grid_barrier(gb);
+  int top = 0;
+  for (int s = 1; s < N; s *= 2, ++top) {
+    const int nblk = bcr_level_blocks(N, s);
+    for (int bi = gw; bi < nblk; bi += nw) bcr_fwd_one<T>(P, F, s, 0, bi, wv);
+    grid_barrier(gb);
+  }
+  if (gw == 0) bcr_fwd_one<T>(P, F, 1, 1, 0, wv);
+  grid_barrier(gb);
+  {
+    const int L = P.p, G = n_chunks(2 * N);
+    for (int it = blockIdx.x * FBS + threadIdx.x; it < G * L; it += gridDim.x * FBS)
+      F.chunkR[it] = chunk_sum_item(F.Rth, 2 * N, L, G, it / L, it % L);
+  }
+  grid_barrier(gb);
+  if (blockIdx.x == 0) {
+    double* sv = reinterpret_cast<double*>(smraw);
+    theta_solve_block(P, F.chunkR, b, S, sol, sv);
+  }
+  grid_barrier(gb);
+  if (gw == 0) bcr_bwd_one<T>(P, F, S, sol, 1, 1, 0, wv);
+  grid_barrier(gb);
+  for (int lv = top - 1; lv >= 0; --lv) {
+    const int s = 1 << lv;
+    const int nblk = bcr_level_blocks(N, s);
+    for (int bi = gw; bi < nblk; bi += nw) bcr_bwd_one<T>(P, F, S, sol, s, 0, bi, wv);
+    grid_barrier(gb);
+  }
+  for (int e = gw; e < N; e += nw) elem_bwd_one<T>(P, F, S, sol, e, wv);
 }
 
 // ---- host launchers ------------------------------------------------------------------
@@ -608,17 +802,59 @@ cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double*
   return cudaGetLastError();
 }
 
+static int g_coop_checked = -1;   // device supports cooperative launches (-1: unknown)
+static bool coop_supported() {
+  if (g_coop_checked < 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev);
+    g_coop_checked = v ? 1 : 0;
+  }
+  return g_coop_checked == 1;
+}
+
+template <typename KernelT>
+static int coop_grid(KernelT kern, int threads, size_t smem, int want) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return std::max(0, std::min(want, per * sms));
+}
+
 template <typename T>
 cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
                           double dc, const DevFactor<T>& F, const DevSchur& S, cudaStream_t st) {
-  cudaError_t e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st);
-  if (e != cudaSuccess) return e;
-  bool bs = bcr_uses_smem<T>(P);
-  size_t smb = bcr_factor_smem<T>(P, bs);
+  const bool es = elem_uses_smem<T>(P), bs = bcr_uses_smem<T>(P);
+  const size_t sme = elem_factor_smem<T>(P, es), smb = bcr_factor_smem<T>(P, bs);
+  const size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
+  cudaError_t e;
+  if (F.persistent && F.gbar && coop_supported()) {
+    const size_t sm = std::max(std::max(sme, smb), sms);
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_factor_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+    int want = std::max(P.N, 1);
+    if (!es || !bs) want = std::min(want, F.n_slabs);
+    const int grid = coop_grid(k_factor_persistent<T>, FBS, sm, want);
+    if (grid >= 1) {
+      DevProb Pc = P; DevEval Ec = E; DevFactor<T> Fc = F; DevSchur Sc = S;
+      GridBar* gb = F.gbar;
+      int esi = es ? 1 : 0, bsi = bs ? 1 : 0;
+      void* args[] = {&Pc, &Ec, (void*)&sigma, &dw, &dc, &Fc, &Sc, &gb, &esi, &bsi};
+      count_launch();
+      return cudaLaunchCooperativeKernel((void*)k_factor_persistent<T>, dim3(grid), dim3(FBS),
+                                         args, sm, st);
+    }
+  }
+  if ((e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st)) != cudaSuccess) return e;
   if (smb > 48 * 1024)
     cudaFuncSetAttribute(k_bcr_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
   for (int s = 1; s < P.N; s *= 2) {
-    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    int nblk = bcr_level_blocks(P.N, s);
     int g = bs ? nblk : std::min(nblk, F.n_slabs);
     count_launch();
     k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0);
@@ -627,7 +863,6 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   count_launch();
   k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   if (sms > 48 * 1024)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
   if ((e = launch_chunk_sums(F.Scon, 2 * P.N, P.p * P.p, F.chunkS, st)) != cudaSuccess) return e;
@@ -640,6 +875,24 @@ template <typename T>
 cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur& S,
                          const double* b, double* sol, cudaStream_t st) {
   const int tpb = 32 * SOLVE_WARPS;
+  cudaError_t e;
+  if (F.persistent && F.gbar && coop_supported()) {
+    const size_t per_warp = sizeof(T) * (size_t)std::max(P.ext, P.bext);
+    const size_t sm = std::max(per_warp * (FBS / 32), sizeof(double) * (size_t)std::max(P.p, 1));
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_solve_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+    const int want = std::max(1, ceil_div(P.N, FBS / 32));
+    const int grid = coop_grid(k_solve_persistent<T>, FBS, sm, want);
+    if (grid >= 1) {
+      DevProb Pc = P; DevFactor<T> Fc = F; DevSchur Sc = S;
+      GridBar* gb = F.gbar;
+      void* args[] = {&Pc, &Fc, &Sc, (void*)&b, (void*)&sol, &gb};
+      count_launch();
+      return cudaLaunchCooperativeKernel((void*)k_solve_persistent<T>, dim3(grid), dim3(FBS), args,
+                                         sm, st);
+    }
+  }
   size_t sme = sizeof(T) * (size_t)P.ext * SOLVE_WARPS;
   size_t smb = sizeof(T) * (size_t)P.bext * SOLVE_WARPS;
   if (sme > 48 * 1024) {
@@ -650,14 +903,13 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
     cudaFuncSetAttribute(k_bcr_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     cudaFuncSetAttribute(k_bcr_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
   }
-  cudaError_t e;
   count_launch();
   k_elem_fwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, b);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   std::vector<int> strides;
   for (int s = 1; s < P.N; s *= 2) strides.push_back(s);
   for (int s : strides) {
-    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    int nblk = bcr_level_blocks(P.N, s);
     count_launch();
     k_bcr_fwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, s, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -675,7 +927,7 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int k = (int)strides.size() - 1; k >= 0; --k) {
     int s = strides[k];
-    int nblk = (P.N - s + 2 * s - 1) / (2 * s);
+    int nblk = bcr_level_blocks(P.N, s);
     count_launch();
     k_bcr_bwd<T><<<ceil_div(nblk, SOLVE_WARPS), tpb, smb, st>>>(P, F, S, sol, s, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -275,6 +275,152 @@ __global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* _
   if (tid == 0) *fails = nfail;
 }
 
+// The same sweep for 3n <= 32 on one warp: lane l owns row l of the FP32
+// Newton matrix in registers, so the LU with partial pivoting and the back
+// substitution run on warp shuffles without block barriers.
+constexpr int WSWEEP = 32;
+__global__ void __launch_bounds__(32) k_forward_sweep_warp(DevProb P, double* __restrict__ x,
+                                                           int* __restrict__ fails) {
+  extern __shared__ double sm[];
+  const int n = P.n, r = P.r, dim = KC * n;
+  const int lane = threadIdx.x;
+  const unsigned FULL = 0xffffffffu;
+  double* kr = sm;                 // [r]
+  double* mon = kr + r;            // [3][r]
+  float* daf = reinterpret_cast<float*>(mon + KC * r);   // [3][r]
+  float* dbf = daf + KC * r;                             // [3][r]
+  float* rows = dbf + KC * r;                            // [32][33] staging
+  double* z0 = reinterpret_cast<double*>(rows + WSWEEP * (WSWEEP + 1));  // [n]
+  double* Z = z0 + n;              // [3n]
+  const size_t nz = (size_t)P.N * NP * n;
+  for (int j = lane; j < r; j += 32) {
+    const int q = P.pidx[j];
+    if (q < 0) kr[j] = P.kfix[j];
+    else kr[j] = P.logscale ? exp10(x[nz + q]) : x[nz + q];
+  }
+  for (int s = lane; s < n; s += 32) z0[s] = P.x0[s];
+  __syncwarp();
+  const int rk = lane < dim ? lane / n + 1 : 1;
+  const int rs = lane < dim ? lane - (rk - 1) * n : 0;
+  int nfail = 0;
+  for (int i = 0; i < P.N; ++i) {
+    for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
+    __syncwarp();
+    bool ok = false;
+    for (int it = 0; it < SWEEP_MAXIT; ++it) {
+      for (int idx = lane; idx < KC * r; idx += 32) {
+        const int k = idx / r, j = idx - k * r;
+        const int a = P.react[2 * j], b = P.react[2 * j + 1];
+        const double za = Z[k * n + a];
+        if (b < 0) { mon[idx] = za; daf[idx] = 1.f; dbf[idx] = 0.f; }
+        else { const double zb = Z[k * n + b]; mon[idx] = za * zb; daf[idx] = (float)zb; dbf[idx] = (float)za; }
+      }
+      __syncwarp();
+      float* myrow = rows + lane * (WSWEEP + 1);
+      double g = 0.0;
+      if (lane < dim) {
+        for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
+        for (int j = 1; j <= KC; ++j) myrow[(j - 1) * n + rs] = (float)P.D[rk][j];
+        g = P.D[rk][0] * z0[rs];
+        for (int j = 1; j <= KC; ++j) g += P.D[rk][j] * Z[(j - 1) * n + rs];
+        double f = 0.0;
+        const float hf = (float)P.h;
+        for (int e = P.nu_ptr[rs]; e < P.nu_ptr[rs + 1]; ++e) {
+          const int rr = P.nu_r[e];
+          const int mi = (rk - 1) * r + rr;
+          const double nk = P.nu_v[e] * kr[rr];
+          f += nk * mon[mi];
+          const float nkf = (float)nk;
+          const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+          myrow[(rk - 1) * n + a] -= hf * nkf * daf[mi];
+          if (b >= 0) myrow[(rk - 1) * n + b] -= hf * nkf * dbf[mi];
+        }
+        g -= P.h * f;
+      } else {
+        for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
+      }
+      __syncwarp();
+      float row[WSWEEP];
+#pragma unroll
+      for (int c = 0; c < WSWEEP; ++c) row[c] = myrow[c];
+      float rhs = (float)g;
+      bool singular = false;
+#pragma unroll
+      for (int c = 0; c < WSWEEP; ++c) {
+        if (c < dim && !singular) {
+          float v = (lane >= c && lane < dim) ? fabsf(row[c]) : -1.f;
+          int idx = lane;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(FULL, v, o);
+            const int oi = __shfl_xor_sync(FULL, idx, o);
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+          }
+          if (!(v > 0.f) || !isfinite(v)) {
+            singular = true;
+          } else {
+            if (idx != c) {
+              const int src = lane == c ? idx : (lane == idx ? c : lane);
+#pragma unroll
+              for (int k = c; k < WSWEEP; ++k) row[k] = __shfl_sync(FULL, row[k], src);
+              rhs = __shfl_sync(FULL, rhs, src);
+            }
+            const float pv = __shfl_sync(FULL, row[c], c);
+            const float f = (lane > c && lane < dim) ? row[c] / pv : 0.f;
+#pragma unroll
+            for (int k = c + 1; k < WSWEEP; ++k) {
+              const float pk = __shfl_sync(FULL, row[k], c);
+              row[k] -= f * pk;
+            }
+            const float pr = __shfl_sync(FULL, rhs, c);
+            rhs -= f * pr;
+          }
+        }
+      }
+      if (singular) break;
+      float sol = 0.f;
+#pragma unroll
+      for (int c = WSWEEP - 1; c >= 0; --c) {
+        if (c < dim) {
+          const float xc = __shfl_sync(FULL, rhs / row[c], c);
+          if (lane < c) rhs -= row[c] * xc;
+          if (lane == c) sol = xc;
+        }
+      }
+      double mdz = 0.0, mz = 0.0;
+      bool fin = true;
+      if (lane < dim) {
+        const double d = (double)sol;
+        Z[lane] -= d;
+        fin = isfinite(Z[lane]);
+        mdz = fabs(d);
+        mz = fabs(Z[lane]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mdz = fmax(mdz, __shfl_xor_sync(FULL, mdz, o));
+        mz = fmax(mz, __shfl_xor_sync(FULL, mz, o));
+      }
+      fin = __all_sync(FULL, fin);
+      __syncwarp();
+      if (!fin) break;
+      if (mdz <= 1e-12 * fmax(1.0, mz)) { ok = true; break; }
+    }
+    if (!ok) {
+      ++nfail;
+      for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
+      __syncwarp();
+    }
+    double* xi = x + (size_t)i * NP * n;
+    for (int s = lane; s < n; s += 32) xi[s] = z0[s];
+    for (int t = lane; t < dim; t += 32) xi[n + t] = Z[t];
+    __syncwarp();
+    for (int s = lane; s < n; s += 32) z0[s] = Z[(KC - 1) * n + s];
+    __syncwarp();
+  }
+  if (lane == 0) *fails = nfail;
+}
+
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
   const size_t dim = KC * (size_t)P.n;
   size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * KC) + P.n + 2 * dim);
@@ -283,6 +429,17 @@ size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
 }
 
 cudaError_t launch_forward_sweep(collo_problem* pr) {
+  const DevProb& P = pr->P;
+  if (KC * P.n <= WSWEEP) {
+    size_t sm = sizeof(double) * ((size_t)P.r * (1 + KC) + P.n + KC * (size_t)P.n) +
+                sizeof(float) * ((size_t)2 * KC * P.r + WSWEEP * (WSWEEP + 1));
+    sm = (sm + 15) & ~size_t(15);
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_forward_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
+    k_forward_sweep_warp<<<1, 32, sm, pr->stream>>>(P, pr->x, pr->fails);
+    return cudaGetLastError();
+  }
   const bool insm = pr->sweep_work == nullptr;
   size_t sm = sweep_smem_bytes(pr->P, insm);
   if (sm > 48 * 1024)

@@ -84,6 +84,7 @@ struct collo_problem {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int precision = 0;
+  int launch_mode = 0;
   collo::DevProb P{};
   collo::DevEval E{};
   collo::DevSchur S{};

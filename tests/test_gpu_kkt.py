@@ -137,3 +137,23 @@ def test_wrong_inertia_is_reported(collo):
         assert prob.kkt_factor(ref["sigma"], 0.0, dc, precision=collo.FP64) == ref["inertia"]
         assert prob.kkt_factor(big["sigma"], 1e6, dc, precision=collo.FP64) == big["inertia"]
         assert big["inertia"] == (oprob.n_x, oprob.n_c, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_persistent_and_per_level_launches_agree_bitwise(collo, prec):
+    """The persistent cooperative kernels and the per-level launches run the same
+    arithmetic in the same order: identical inertia and identical bits."""
+    inst = CASES["config2_N400"]()
+    oprob = OProblem(inst)
+    x, lam, zl, zu = _point(oprob, 31)
+    ref = newton_system(oprob, x, lam, zl, zu, 0.05, 1e-3, 1e-8)
+    P = collo.MIXED if prec == "mixed" else collo.FP64
+    sols = []
+    for mode in (0, 1):
+        with collo.Problem(inst, launch_mode=mode) as prob:
+            prob.eval(x, lam)
+            inertia = prob.kkt_factor(ref["sigma"], 1e-3, 1e-8, precision=P)
+            sol, _ = prob.kkt_solve(ref["rhs"], refine_max=0)
+            sols.append((inertia, sol))
+    assert sols[0][0] == sols[1][0] == ref["inertia"]
+    assert np.array_equal(sols[0][1], sols[1][1])
