@@ -172,7 +172,7 @@ typedef struct collo_ipm_options {
   double mixed_mu_switch;     /* MIXED: use FP64 factorization once mu < this
                                  (default 1e-6); 0 = never switch                   */
   int refine_max;             /* max iterative-refinement sweeps (default 10)      */
-  double refine_tol;          /* stop refining at ||r||/||b|| <= this (1e-12)       */
+  double refine_tol;          /* stop refining at ||r||/||b|| <= this (1e-10)       */
   int verbose;                /* print an iteration log to stdout                  */
   int reserved[8];
 } collo_ipm_options;

@@ -590,7 +590,7 @@ void collo_ipm_options_default(collo_ipm_options* o) {
   o->precision = COLLO_PRECISION_FP64;
   o->mixed_mu_switch = 1e-6;
   o->refine_max = 10;
-  o->refine_tol = 1e-12;
+  o->refine_tol = 1e-10;
   o->verbose = 0;
 }
 
