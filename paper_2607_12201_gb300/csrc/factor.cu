@@ -260,151 +260,23 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
   __syncthreads();
 }
 
-// Warp-synchronous variant of pair_eliminate for one block per warp: the
-// same arithmetic in the same order, with __syncwarp instead of block barriers.
-template <typename T>
-__device__ void pair_eliminate_warp(T* A, int ld, int msz, int npairs, T* __restrict__ Lout,
-                                    int lds, T* __restrict__ Dout, T* cc0, T* cc1, T* l0s,
-                                    T* l1s, int& pos, int& neg, int& zero) {
-  const int lane = threadIdx.x & 31;
-  for (int q = 0; q < npairs; ++q) {
-    const int c0 = 2 * q, c1 = c0 + 1;
-    const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
-    const T det = a * d - b * b;
-    T ia, ib, id;
-    if (det != T(0) && isfinite((double)det)) {
-      const T inv = T(1) / det;
-      ia = d * inv; ib = -b * inv; id = a * inv;
-    } else {
-      ia = ib = id = T(0);
-    }
-    for (int r = c1 + 1 + lane; r < msz; r += 32) {
-      const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
-      const T l0 = x0 * ia + x1 * ib;
-      const T l1 = x0 * ib + x1 * id;
-      cc0[r] = x0; cc1[r] = x1; l0s[r] = l0; l1s[r] = l1;
-      Lout[(size_t)c0 * lds + r] = l0;
-      Lout[(size_t)c1 * lds + r] = l1;
-    }
-    if (lane == 0) {
-      Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
-      pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
-    }
-    __syncwarp();
-    for (int r = c1 + 1; r < msz; ++r) {
-      const T l0 = l0s[r], l1 = l1s[r];
-      T* Ar = A + (size_t)r * ld;
-      for (int c = c1 + 1 + lane; c <= r; c += 32) Ar[c] -= l0 * cc0[c] + l1 * cc1[c];
-    }
-    __syncwarp();
-  }
-}
-
-// One cyclic-reduction block eliminated by one warp (same arithmetic as
-// bcr_factor_one).  A: the warp's (4n+p) x ld slice, vecs: 4 (4n+p).
-template <typename T>
-__device__ void bcr_factor_one_warp(const DevProb& P, const DevFactor<T>& F, int stride,
-                                    int final_level, int bi, T* A, T* cc0, T* cc1, T* l0s,
-                                    T* l1s) {
-  const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
-  const int lane = threadIdx.x & 31;
-  const int i = final_level ? 0 : stride * (2 * bi + 1);
-  const int L = final_level ? -1 : i - stride;
-  const int R = (!final_level && i + stride < N) ? i + stride : -1;
-  const T* Ai = F.Aif + (size_t)i * n2 * n2;
-  const T* Ci = F.Cpl + (size_t)i * n * n;
-  const T* CR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
-  const T* Bi = F.Bif + (size_t)i * n2 * p;
-  for (int a = 0; a < bext; ++a)
-    for (int b = lane; b <= a; b += 32) {
-      T v = T(0);
-      if (a < n2) {
-        v = Ai[a * n2 + b];
-      } else if (b < n2) {
-        if (a < 3 * n) {
-          if (L >= 0 && (b & 1)) v = Ci[(b >> 1) * n + (a - n2)];
-        } else if (a < 4 * n) {
-          if (R >= 0 && !(b & 1)) v = CR[(a - 3 * n) * n + (b >> 1)];
-        } else {
-          v = Bi[b * p + (a - 4 * n)];
-        }
-      }
-      A[a * ld + b] = v;
-    }
-  __syncwarp();
-  int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_warp<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
-                         F.Db + (size_t)i * n * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
-  if (lane == 0) {
-    int* in = F.inert + (size_t)(N + i) * 3;
-    in[0] = pos; in[1] = neg; in[2] = zero;
-  }
-  if (L >= 0) {
-    T* AL = F.Aif + (size_t)L * n2 * n2;
-    for (int idx = lane; idx < n * n; idx += 32) {
-      const int t = idx / n, t2 = idx - t * n;
-      const int ra = n2 + t, rb = n2 + t2;
-      AL[(2 * t) * n2 + 2 * t2] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
-    }
-    T* BL = F.Bif + (size_t)L * n2 * p;
-    for (int idx = lane; idx < n * p; idx += 32) {
-      const int t = idx / p, q = idx - t * p;
-      BL[(2 * t) * p + q] += A[(4 * n + q) * ld + n2 + t];
-    }
-  }
-  if (R >= 0) {
-    T* AR = F.Aif + (size_t)R * n2 * n2;
-    T* CRw = F.Cpl + (size_t)R * n * n;
-    for (int idx = lane; idx < n * n; idx += 32) {
-      const int s = idx / n, s2 = idx - s * n;
-      const int ra = 3 * n + s, rb = 3 * n + s2;
-      AR[(2 * s + 1) * n2 + 2 * s2 + 1] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
-      CRw[idx] = (L >= 0) ? A[(3 * n + s) * ld + n2 + s2] : T(0);
-    }
-    T* BR = F.Bif + (size_t)R * n2 * p;
-    for (int idx = lane; idx < n * p; idx += 32) {
-      const int s = idx / p, q = idx - s * p;
-      BR[(2 * s + 1) * p + q] += A[(4 * n + q) * ld + 3 * n + s];
-    }
-  }
-  double* Sc = F.Scon + (size_t)(N + i) * p * p;
-  for (int idx = lane; idx < p * p; idx += 32) {
-    const int q = idx / p, q2 = idx - q * p;
-    const int ra = 4 * n + q, rb = 4 * n + q2;
-    Sc[idx] = (double)(ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra]);
-  }
-  __syncwarp();
-}
-
 __host__ __device__ inline int bcr_level_blocks(int N, int stride) {
   return (N - stride + 2 * stride - 1) / (2 * stride);
 }
 
-// One warp per cyclic-reduction block; `wpb` warps per CTA, each with its
-// own (4n+p) x ld slice (shared memory, or a global slab per warp).
-template <typename T>
-__host__ __device__ inline size_t bcr_warp_elems(int bext) {
-  return (size_t)odd_ld(bext) * bext + 4 * (size_t)bext;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(FBS)
-k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem, int wpb) {
+k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
   extern __shared__ unsigned char smraw[];
   const int bext = P.bext, ld = odd_ld(bext);
-  const int warp = threadIdx.x >> 5;
-  if (warp >= wpb) return;
-  const size_t per = bcr_warp_elems<T>(bext);
-  const int slot = blockIdx.x * wpb + warp;
-  T* base = use_smem ? reinterpret_cast<T*>(smraw) + (size_t)warp * per : F.work + (size_t)slot * per;
-  T* A = base;
-  T* cc0 = A + (size_t)ld * bext;
+  T* cc0 = reinterpret_cast<T*>(smraw);
   T* cc1 = cc0 + bext;
   T* l0s = cc1 + bext;
   T* l1s = l0s + bext;
+  T* A = use_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
   const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
-  for (int bi = slot; bi < nblk; bi += gridDim.x * wpb)
-    bcr_factor_one_warp<T>(P, F, stride, final_level, bi, A, cc0, cc1, l0s, l1s);
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
+    bcr_factor_one<T>(P, F, stride, final_level, bi, A, cc0, cc1, l0s, l1s);
 }
 
 // ---- 3. parameter Schur complement (FP64) ------------------------------------------
@@ -800,8 +672,7 @@ __device__ void grid_barrier(GridBar* gb) {
 template <typename T>
 __global__ void __launch_bounds__(FBS)
 k_factor_persistent(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
-                    DevFactor<T> F, DevSchur S, GridBar* gb, int elem_smem, int bcr_smem,
-                    int bcr_wpb) {
+                    DevFactor<T> F, DevSchur S, GridBar* gb, int elem_smem, int bcr_smem) {
   extern __shared__ unsigned char smraw[];
   const int N = P.N;
   {
@@ -817,23 +688,18 @@ k_factor_persistent(DevProb P, DevEval E, const double* __restrict__ sigma, doub
   grid_barrier(gb);
   {
     const int bext = P.bext, ld = odd_ld(bext);
-    const int warp = threadIdx.x >> 5;
-    const size_t per = bcr_warp_elems<T>(bext);
-    const int slot = blockIdx.x * bcr_wpb + warp;
-    const bool active = warp < bcr_wpb;
-    T* A = bcr_smem ? reinterpret_cast<T*>(smraw) + (size_t)warp * per : F.work + (size_t)slot * per;
-    T* cc0 = A + (size_t)ld * bext;
+    T* cc0 = reinterpret_cast<T*>(smraw);
     T* cc1 = cc0 + bext;
     T* l0s = cc1 + bext;
     T* l1s = l0s + bext;
+    T* A = bcr_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
     for (int s = 1; s < N; s *= 2) {
       const int nblk = bcr_level_blocks(N, s);
-      if (active)
-        for (int bi = slot; bi < nblk; bi += gridDim.x * bcr_wpb)
-          bcr_factor_one_warp<T>(P, F, s, 0, bi, A, cc0, cc1, l0s, l1s);
+      for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
+        bcr_factor_one<T>(P, F, s, 0, bi, A, cc0, cc1, l0s, l1s);
       grid_barrier(gb);
     }
-    if (blockIdx.x == 0 && warp == 0) bcr_factor_one_warp<T>(P, F, 1, 1, 0, A, cc0, cc1, l0s, l1s);
+    if (blockIdx.x == 0) bcr_factor_one<T>(P, F, 1, 1, 0, A, cc0, cc1, l0s, l1s);
   }
   grid_barrier(gb);
   {
@@ -900,17 +766,11 @@ size_t elem_factor_smem(const DevProb& P, bool full) {
   if (full) v += sizeof(T) * (size_t)odd_ld(P.ext) * P.ext;
   return v;
 }
-// Warps per CTA of the cyclic-reduction phase and its shared memory.
-template <typename T>
-int bcr_wpb(const DevProb& P) {
-  const size_t per = sizeof(T) * bcr_warp_elems<T>(P.bext);
-  int w = (int)std::min<size_t>(FBS / 32, (200 * 1024) / per);
-  return w;   // 0: slices do not fit in shared memory (global slabs, 8 warps)
-}
 template <typename T>
 size_t bcr_factor_smem(const DevProb& P, bool full) {
-  if (!full) return 0;
-  return sizeof(T) * bcr_warp_elems<T>(P.bext) * (size_t)bcr_wpb<T>(P);
+  size_t v = sizeof(T) * 4 * (size_t)P.bext;
+  if (full) v += sizeof(T) * (size_t)odd_ld(P.bext) * P.bext;
+  return v;
 }
 
 constexpr size_t SMEM_LIMIT = 220 * 1024;
@@ -918,14 +778,14 @@ constexpr size_t SMEM_LIMIT = 220 * 1024;
 template <typename T>
 bool elem_uses_smem(const DevProb& P) { return elem_factor_smem<T>(P, true) <= SMEM_LIMIT; }
 template <typename T>
-bool bcr_uses_smem(const DevProb& P) { return bcr_wpb<T>(P) >= 1; }
+bool bcr_uses_smem(const DevProb& P) { return bcr_factor_smem<T>(P, true) <= SMEM_LIMIT; }
 
 // Global workspace (in T elements) needed when a block does not fit in shared memory.
 template <typename T>
 size_t factor_work_elems(const DevProb& P, int n_slabs) {
   size_t w = 0;
   if (!elem_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.ext) * P.ext * n_slabs);
-  if (!bcr_uses_smem<T>(P)) w = std::max(w, bcr_warp_elems<T>(P.bext) * n_slabs * (FBS / 32));
+  if (!bcr_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.bext) * P.bext * n_slabs);
   return w;
 }
 
@@ -973,12 +833,7 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   const size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   cudaError_t e;
   if (F.persistent && F.gbar && coop_supported()) {
-    // cyclic-reduction warps per CTA limited so the phase does not raise the
-    // kernel's shared memory above the element phase's (keeps occupancy)
-    const size_t per = sizeof(T) * bcr_warp_elems<T>(P.bext);
-    int pwpb = bs ? (int)std::max<size_t>(1, std::min<size_t>(bcr_wpb<T>(P), sme / per)) : FBS / 32;
-    const size_t smb_p = bs ? per * pwpb : 0;
-    const size_t sm = std::max(std::max(sme, smb_p), sms);
+    const size_t sm = std::max(std::max(sme, smb), sms);
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_factor_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
@@ -988,8 +843,8 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
     if (grid >= 1) {
       DevProb Pc = P; DevEval Ec = E; DevFactor<T> Fc = F; DevSchur Sc = S;
       GridBar* gb = F.gbar;
-      int esi = es ? 1 : 0, bsi = bs ? 1 : 0, wpb = pwpb;
-      void* args[] = {&Pc, &Ec, (void*)&sigma, &dw, &dc, &Fc, &Sc, &gb, &esi, &bsi, &wpb};
+      int esi = es ? 1 : 0, bsi = bs ? 1 : 0;
+      void* args[] = {&Pc, &Ec, (void*)&sigma, &dw, &dc, &Fc, &Sc, &gb, &esi, &bsi};
       count_launch();
       return cudaLaunchCooperativeKernel((void*)k_factor_persistent<T>, dim3(grid), dim3(FBS),
                                          args, sm, st);
@@ -998,17 +853,15 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   if ((e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st)) != cudaSuccess) return e;
   if (smb > 48 * 1024)
     cudaFuncSetAttribute(k_bcr_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-  const int wpb = bs ? bcr_wpb<T>(P) : FBS / 32;
   for (int s = 1; s < P.N; s *= 2) {
     int nblk = bcr_level_blocks(P.N, s);
-    int g = ceil_div(nblk, wpb);
-    if (!bs) g = std::min(g, F.n_slabs);
+    int g = bs ? nblk : std::min(nblk, F.n_slabs);
     count_launch();
-    k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0, wpb);
+    k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   count_launch();
-  k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0, wpb);
+  k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (sms > 48 * 1024)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
