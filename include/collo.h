@@ -57,7 +57,8 @@ enum {
   COLLO_ERR_LINESEARCH = -7,    /* step below alpha_min; no restoration ("R") */
   COLLO_ERR_NOT_FACTORED = -8,  /* collo_kkt_solve before collo_kkt_factor    */
   COLLO_ERR_DEVICE = -9,        /* CUDA runtime error                         */
-  COLLO_ERR_NOT_EVALUATED = -10 /* collo_kkt_factor before collo_eval         */
+  COLLO_ERR_NOT_EVALUATED = -10, /* collo_kkt_factor before collo_eval        */
+  COLLO_PENDING = 2              /* collo_server_poll: not finished yet        */
 };
 
 /* Arithmetic of the KKT factorization and solve. */
@@ -246,6 +247,36 @@ void collo_ipm_options_default(collo_ipm_options* opts);
  * result->status is the solver outcome; the return value is the same. */
 collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
                              const collo_ipm_options* opts, collo_result* result);
+
+/* Solve `count` independent problems (e.g. the starts of a multistart run,
+ * or instances of different networks and sizes) together: every phase of
+ * every Newton step runs as one launch over all unfinished problems
+ * (element-level grids, one cooperative kernel for all factorizations /
+ * solves), and each problem follows exactly the iterates it would follow
+ * alone.  probs: [count] problems created on the same device; theta0[i]:
+ * [p_i] start of problem i; results[i] as for collo_ipm_solve (its theta / x /
+ * lambda pointers are honoured).  The call returns COLLO_OK when every
+ * problem has a final status in results[i].status. */
+collo_status collo_batch_solve(collo_problem* const* probs, int count, const double* const* theta0,
+                               const collo_ipm_options* opts, collo_result* results);
+
+/* Continuous-batching server.  Problems are submitted at any time; each
+ * collo_server_step admits waiting problems into free slots while the device
+ * memory held by admitted problems stays within budget_bytes (0: no limit),
+ * initialises them, advances every admitted problem by one Newton step in
+ * batched launches, and retires finished ones.  Their state (x, lambda, bound
+ * duals, barrier parameter, filter) stays on the device between steps.
+ * collo_server_poll returns COLLO_PENDING until the ticket's solve ended,
+ * then COLLO_OK with the result (theta copied if result->theta is set).
+ * Submitted problems must stay alive until polled as done. */
+typedef struct collo_server collo_server;
+collo_status collo_server_create(int max_slots, int64_t budget_bytes,
+                                 const collo_ipm_options* opts, int device, collo_server** out);
+collo_status collo_server_submit(collo_server* server, collo_problem* prob, const double* theta0,
+                                 long long* ticket);
+collo_status collo_server_step(collo_server* server, int* n_active, int* n_waiting);
+collo_status collo_server_poll(collo_server* server, long long ticket, collo_result* result);
+void collo_server_destroy(collo_server* server);
 
 /* Collocation forward sweep at theta (the IPM's initial states): writes
  * z [N][K+1][n] into x_out [n_x] (theta copied into its tail).  Returns the

@@ -18,6 +18,7 @@ OK, ACCEPTABLE = 0, 1
 ERR_INVALID_ARG, ERR_OOM, ERR_NUMERIC, ERR_INERTIA = -1, -2, -3, -4
 ERR_MAXITER, ERR_TIMEOUT, ERR_LINESEARCH, ERR_NOT_FACTORED = -5, -6, -7, -8
 ERR_DEVICE, ERR_NOT_EVALUATED = -9, -10
+PENDING = 2
 FP64, MIXED = 0, 1
 
 
@@ -118,6 +119,20 @@ def _load():
     lib.collo_ipm_solve.restype = C.c_int
     lib.collo_initial_states.argtypes = [P, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.collo_initial_states.restype = C.c_int
+    lib.collo_batch_solve.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_void_p),
+                                       C.POINTER(IpmOptions), C.POINTER(Result)]
+    lib.collo_batch_solve.restype = C.c_int
+    lib.collo_server_create.argtypes = [C.c_int, C.c_int64, C.POINTER(IpmOptions), C.c_int,
+                                        C.POINTER(P)]
+    lib.collo_server_create.restype = C.c_int
+    lib.collo_server_submit.argtypes = [P, P, C.c_void_p, C.POINTER(C.c_longlong)]
+    lib.collo_server_submit.restype = C.c_int
+    lib.collo_server_step.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.collo_server_step.restype = C.c_int
+    lib.collo_server_poll.argtypes = [P, C.c_longlong, C.POINTER(Result)]
+    lib.collo_server_poll.restype = C.c_int
+    lib.collo_server_destroy.argtypes = [P]
+    lib.collo_server_destroy.restype = None
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
     lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -298,6 +313,79 @@ class Problem:
         _check(lib.collo_initial_states(self.h, _f64(theta).ctypes.data, x.ctypes.data,
                                         C.byref(f)))
         return x, int(f.value)
+
+
+def _result_dict(res, theta, x, lam):
+    return dict(status=res.status, iterations=res.iterations, factorizations=res.factorizations,
+                trials=res.line_search_trials, phi=res.phi, kkt_error=res.kkt_error, mu=res.mu,
+                wall=res.wall_seconds, theta=theta, x=x, lam=lam)
+
+
+def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
+    """collo_batch_solve: solve several problems together; list of result dicts."""
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p.h.value for p in problems])
+    th = [_f64(p.inst.theta0 if theta0s is None else theta0s[i]) for i, p in enumerate(problems)]
+    thp = (C.c_void_p * n)(*[t.ctypes.data for t in th])
+    res = (Result * n)()
+    outs = []
+    for i, p in enumerate(problems):
+        theta = np.zeros(p.p)
+        x = np.zeros(p.n_x) if want_x else None
+        lam = np.zeros(p.n_c) if want_x else None
+        res[i].theta = theta.ctypes.data
+        res[i].x = None if x is None else x.ctypes.data
+        res[i].lambda_ = None if lam is None else lam.ctypes.data
+        outs.append((theta, x, lam))
+    o = Problem.ipm_options(**kw)
+    _check(lib.collo_batch_solve(handles, n, thp, C.byref(o), res))
+    return [_result_dict(res[i], *outs[i]) for i in range(n)]
+
+
+class Server:
+    """collo_server_*: continuous batching of IPM solves on one GPU."""
+
+    def __init__(self, max_slots: int, budget_bytes: int = 0, device: int = 0, **kw):
+        o = Problem.ipm_options(**kw)
+        h = C.c_void_p()
+        _check(lib.collo_server_create(int(max_slots), int(budget_bytes), C.byref(o), int(device),
+                                       C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, problem, theta0=None) -> int:
+        th = _f64(problem.inst.theta0 if theta0 is None else theta0)
+        t = C.c_longlong()
+        _check(lib.collo_server_submit(self.h, problem.h, th.ctypes.data, C.byref(t)))
+        self._keep[t.value] = (problem, th)
+        return t.value
+
+    def step(self):
+        a, w = C.c_int(), C.c_int()
+        _check(lib.collo_server_step(self.h, C.byref(a), C.byref(w)))
+        return a.value, w.value
+
+    def poll(self, ticket: int):
+        problem, _ = self._keep[ticket]
+        res = Result()
+        theta = np.zeros(problem.p)
+        res.theta = theta.ctypes.data
+        st = lib.collo_server_poll(self.h, int(ticket), C.byref(res))
+        if st == PENDING:
+            return None
+        _check(st)
+        return _result_dict(res, theta, None, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.collo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def alu_peak(precision: int) -> float:

@@ -316,6 +316,15 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
     set_error("pinned host allocation failed");
     return COLLO_ERR_OOM;
   }
+  {
+    DevInst& I = pr->inst;
+    I.P = P; I.E = E; I.S = S;
+    I.sigma = pr->sigma; I.x = pr->x; I.lam = pr->lam; I.zl = pr->zl; I.zu = pr->zu;
+    I.dz = pr->dz; I.bar = pr->thx; I.zlmzu = pr->thx + p; I.th0 = pr->thx + 2 * (size_t)p;
+    I.ka = pr->kvec_a; I.kb = pr->kvec_b; I.kr = pr->kvec_r; I.kc = pr->kvec_c;
+    I.thpart = pr->thpart; I.npart = pr->npart; I.fails = pr->fails; I.sweep_work = pr->sweep_work;
+    I.n_x = pr->n_x; I.n_c = pr->n_c;
+  }
   COLLO_CUDA(cudaMemsetAsync(pr->sigma, 0, pr->n_x * sizeof(double), pr->stream));
   COLLO_CUDA(launch_obs_weights(P, M, N, mesh->T, d_obs_t, obs_elem_chk, obs_w, pr->stream));
   COLLO_CUDA(cudaStreamSynchronize(pr->stream));
@@ -358,7 +367,12 @@ collo_status collo_eval(collo_problem* prob, const double* x, const double* lamb
     COLLO_CUDA(cudaMemcpyAsync(dl, lambda, prob->n_c * sizeof(double), cudaMemcpyDefault, st));
   else
     COLLO_CUDA(cudaMemsetAsync(dl, 0, prob->n_c * sizeof(double), st));
-  COLLO_CUDA(launch_eval(P, E, dx, nullptr, 0.0, dl, obj_factor, true, st));
+  if (prob->launch_mode == 0) {
+    collo_status s = runner_eval(prob, obj_factor);
+    if (s != COLLO_OK) return s;
+  } else {
+    COLLO_CUDA(launch_eval(P, E, dx, nullptr, 0.0, dl, obj_factor, true, st));
+  }
   const size_t NN = P.N, nn = (size_t)P.n * P.n, np_ = (size_t)P.n * P.p;
   if (out) {
     auto cp = [&](double* dst, const double* src, size_t cnt) -> cudaError_t {
@@ -485,7 +499,8 @@ collo_status collo_kkt_factor(collo_problem* prob, const double* sigma, double d
   else
     COLLO_CUDA(cudaMemsetAsync(prob->sigma, 0, prob->n_x * sizeof(double), prob->stream));
   long long in[3];
-  collo_status s = factor_internal(prob, delta_w, delta_c, precision, in);
+  collo_status s = prob->launch_mode == 0 ? runner_factor(prob, precision, delta_w, delta_c, in)
+                                          : factor_internal(prob, delta_w, delta_c, precision, in);
   if (s != COLLO_OK) return s;
   if (out) { out->n_pos = in[0]; out->n_neg = in[1]; out->n_zero = in[2]; }
   return COLLO_OK;
@@ -501,8 +516,11 @@ collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol
   COLLO_CUDA(cudaMemcpyAsync(prob->kvec_a, rhs, nk * sizeof(double), cudaMemcpyDefault, st));
   int sweeps = 0;
   double resid = 0.0;
-  collo_status s = solve_internal(prob, prob->kvec_a, prob->kvec_b, refine_max < 0 ? 0 : refine_max,
-                                  refine_tol, &sweeps, &resid);
+  collo_status s =
+      prob->launch_mode == 0
+          ? runner_solve(prob, refine_max < 0 ? 0 : refine_max, refine_tol, &sweeps, &resid)
+          : solve_internal(prob, prob->kvec_a, prob->kvec_b, refine_max < 0 ? 0 : refine_max,
+                           refine_tol, &sweeps, &resid);
   if (s != COLLO_OK) return s;
   COLLO_CUDA(cudaMemcpyAsync(sol, prob->kvec_b, nk * sizeof(double), cudaMemcpyDefault, st));
   COLLO_CUDA(cudaStreamSynchronize(st));

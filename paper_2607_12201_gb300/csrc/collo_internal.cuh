@@ -125,6 +125,58 @@ struct DevSchur {
   double* diag;    // [p] W_thth + sigma_theta + delta_w (assembled by host-side launch)
 };
 
+// ---- batched execution ------------------------------------------------------------
+// Everything one instance owns on the device, gathered for batched kernels.
+struct DevInst {
+  DevProb P;
+  DevEval E;
+  DevFactor<float> F32;
+  DevFactor<double> F64;
+  DevSchur S;
+  double* sigma;      // [n_x]
+  double* x;          // [n_x] iterate
+  double* lam;        // [n_c]
+  double* zl, *zu;    // [p]
+  double* dz;         // [2p]
+  double* bar;        // [p]  mu/sl - mu/su
+  double* zlmzu;      // [p]  zl - zu
+  double* th0;        // [p]  starting parameters
+  double* ka, *kb, *kr, *kc;   // [n_x + n_c] rhs, solution, residual, correction
+  double* thpart;     // [N][p]
+  double* npart;      // [N][2]
+  double* out;        // [64] per-instance scalar outputs of the batched kernels
+  int* fails;         // [1]
+  float* sweep_work;  // forward-sweep FP32 matrix when 3n is large
+  long long n_x, n_c;
+};
+
+// Per-instance, per-launch parameters written by the host.
+struct InstParams {
+  double dw, dc, mu, tau, alpha, alpha_z, ksig, obj_factor;
+};
+
+// Slots of DevInst::out
+enum OutSlot {
+  O_PHI = 0, O_C1 = 1, O_CINF = 2,            // eval reduction
+  O_WMAX = 4, O_WMIN = 5, O_ZSUM = 6, O_LOG = 7,  // theta_prep
+  O_RX = 8, O_RC = 9, O_BMAX = 10,           // residual norms
+  O_LAM1 = 12, O_GDX = 13,                    // |lambda|_1, grad^T dx
+  O_AMAX = 16, O_AZ = 17, O_GPHI = 18,        // theta_step
+  O_TLOG = 20, O_TOK = 21,                    // trial barrier
+  O_INERT = 24,                               // 3 x long long (24..26)
+  O_BERR = 28,                                // grid barrier error flag (as double)
+};
+
+// Find k with pre[k] <= t < pre[k+1] (pre[0] = 0, A + 1 entries).
+__device__ inline int find_item(const int* __restrict__ pre, int A, int t) {
+  int lo = 0, hi = A;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // ---- error handling -----------------------------------------------------------
 void set_error(const std::string& msg);
 #define COLLO_CUDA(call)                                                         \

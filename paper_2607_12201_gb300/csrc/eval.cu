@@ -100,13 +100,11 @@ __device__ inline void rate_const(const DevProb& P, int j, const double* x, cons
 // One block per element i.  Evaluates at x + alpha dx (dx may be null).
 // DERIV = false: residuals, objective and norms only (line-search trials).
 template <bool DERIV>
-__global__ void __launch_bounds__(EVAL_BS)
-k_eval(DevProb P, const double* __restrict__ x, const double* __restrict__ dx, double alpha,
-       const double* __restrict__ lam, double obj_factor, DevEval E) {
-  extern __shared__ double sm[];
-  __shared__ double red[EVAL_BS];
+__device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
+                          const double* __restrict__ dx, double alpha,
+                          const double* __restrict__ lam, double obj_factor, const DevEval& E,
+                          int i, double* sm, double* red) {
   const int n = P.n, r = P.r, p = P.p;
-  const int i = blockIdx.x;
   const int tid = threadIdx.x;
   double* ze = sm;              // [4][n]
   double* le = ze + NP * n;     // [4][n]
@@ -295,10 +293,49 @@ k_eval(DevProb P, const double* __restrict__ x, const double* __restrict__ dx, d
   }
 }
 
+template <bool DERIV>
+__global__ void __launch_bounds__(EVAL_BS)
+k_eval(DevProb P, const double* __restrict__ x, const double* __restrict__ dx, double alpha,
+       const double* __restrict__ lam, double obj_factor, DevEval E) {
+  extern __shared__ double sm[];
+  __shared__ double red[EVAL_BS];
+  eval_elem<DERIV>(P, x, dx, alpha, lam, obj_factor, E, blockIdx.x, sm, red);
+}
+
+// Vector selectors of the batched kernels (which per-instance array to use).
+enum VecSel { V_NONE = 0, V_X = 1, V_LAM = 2, V_STAGE_X = 3, V_STAGE_L = 4, V_KB = 5 };
+
+__device__ inline const double* pick_vec(const DevInst& I, int sel) {
+  switch (sel) {
+    case V_X: return I.x;
+    case V_LAM: return I.lam;
+    case V_STAGE_X: return I.kc;
+    case V_STAGE_L: return I.kc + I.n_x;
+    case V_KB: return I.kb;
+    default: return nullptr;
+  }
+}
+
+// Batched evaluation: block t evaluates element t - pre[k] of instance act[k]
+// at x + alpha_k dx.
+template <bool DERIV>
+__global__ void __launch_bounds__(EVAL_BS)
+k_eval_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+         const int* __restrict__ pre, const InstParams* __restrict__ prm, int xsel, int dxsel,
+         int lsel) {
+  extern __shared__ double sm[];
+  __shared__ double red[EVAL_BS];
+  const int t = blockIdx.x;
+  const int k = find_item(pre, A, t);
+  const DevInst& I = insts[act[k]];
+  eval_elem<DERIV>(I.P, pick_vec(I, xsel), pick_vec(I, dxsel), prm[k].alpha, pick_vec(I, lsel),
+                   prm[k].obj_factor, I.E, t - pre[k], sm, red);
+}
+
 // Sum the per-element partials in a fixed order: phi, |c|_1, |c|_inf, W_thth.
 constexpr int RED_BS = 256;
-__global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, int deriv) {
-  __shared__ double sh[RED_BS];
+__device__ void eval_reduce_one(const DevProb& P, const DevEval& E, int deriv, double* out,
+                                double* sh) {
   const int tid = threadIdx.x;
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = tid; i < P.N; i += RED_BS) {
@@ -309,13 +346,32 @@ __global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, in
   a = block_sum<RED_BS>(a, sh);
   b = block_sum<RED_BS>(b, sh);
   c = block_max<RED_BS>(c, sh);
-  if (tid == 0) { E.red[0] = a; E.red[1] = b; E.red[2] = c; }
-  if (!deriv) return;
-  for (int q = tid; q < P.p; q += RED_BS) {
-    double v = 0.0;
-    for (int i = 0; i < P.N; ++i) v += E.wtt_part[(size_t)i * P.p + q];
-    E.wtt[q] = v;
+  if (tid == 0) {
+    E.red[0] = a; E.red[1] = b; E.red[2] = c;
+    if (out) { out[O_PHI] = a; out[O_C1] = b; out[O_CINF] = c; }
   }
+  if (!deriv) return;
+  // W_thth: warp w sums column q over elements lane, lane + 32, ... then a
+  // fixed shuffle tree
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int q = warp; q < P.p; q += RED_BS / 32) {
+    double v = 0.0;
+    for (int i = lane; i < P.N; i += 32) v += E.wtt_part[(size_t)i * P.p + q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) E.wtt[q] = v;
+  }
+}
+
+__global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, int deriv) {
+  __shared__ double sh[RED_BS];
+  eval_reduce_one(P, E, deriv, nullptr, sh);
+}
+
+__global__ void __launch_bounds__(RED_BS)
+k_eval_reduce_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int deriv) {
+  __shared__ double sh[RED_BS];
+  const DevInst& I = insts[act[blockIdx.x]];
+  eval_reduce_one(I.P, I.E, deriv, I.out, sh);
 }
 
 // Structured FP64 product y = K v of the regularised KKT matrix
@@ -324,14 +380,14 @@ __global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, in
 // and r = b - y (b may be null: r = -y).  One block per element computes the
 // element's 8n rows and its contribution to the p parameter rows; norms of r
 // per element go to npart[i][0..1] (max |r_x|, max |r_c|).
-__global__ void __launch_bounds__(EVAL_BS)
-k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
-            const double* __restrict__ vx, const double* __restrict__ vl,
-            const double* __restrict__ bx, double bxs, const double* __restrict__ bc, double bcs,
-            double* __restrict__ rout, double* __restrict__ thpart, double* __restrict__ npart) {
-  __shared__ double red[EVAL_BS];
+__device__ void resid_elem(const DevProb& P, const DevEval& E, const double* __restrict__ sigma,
+                           double dw, double dc, const double* __restrict__ vx,
+                           const double* __restrict__ vl, const double* __restrict__ bx,
+                           double bxs, const double* __restrict__ bc, double bcs,
+                           double* __restrict__ rout, double* __restrict__ thpart,
+                           double* __restrict__ npart, int i, double* red) {
   const int n = P.n, p = P.p, N = P.N;
-  const int i = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const size_t nz = (size_t)N * NP * n, nx = nz + p;
   const size_t zoff = (size_t)i * NP * n;
   const double* vz = vx;
@@ -405,26 +461,81 @@ k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, d
   if (tid == 0) { npart[i * 2 + 0] = mx; npart[i * 2 + 1] = mc; }
 }
 
+__global__ void __launch_bounds__(EVAL_BS)
+k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
+            const double* __restrict__ vx, const double* __restrict__ vl,
+            const double* __restrict__ bx, double bxs, const double* __restrict__ bc, double bcs,
+            double* __restrict__ rout, double* __restrict__ thpart, double* __restrict__ npart) {
+  __shared__ double red[EVAL_BS];
+  resid_elem(P, E, sigma, dw, dc, vx, vl, bx, bxs, bc, bcs, rout, thpart, npart, blockIdx.x, red);
+}
+
+// Residual modes of the batched product (which vectors of the instance):
+//   R_DUAL: r_x = -(grad + J^T lambda - zl + zu)   (dual infeasibility)
+//   R_RHS:  Newton right-hand side -[grad phi_mu + J^T lambda; c] into ka
+//   R_IR:   r = ka - K kb with the factorization's sigma / delta_w / delta_c into kr
+enum ResidMode { R_DUAL = 0, R_RHS = 1, R_IR = 2 };
+
+struct ResidArgs {
+  const double *sigma, *vx, *vl, *bx, *bc, *th_extra;
+  double bxs, bcs, dw, dc;
+  double* rout;
+};
+
+__device__ inline ResidArgs resid_args(const DevInst& I, const InstParams& pr, int mode) {
+  ResidArgs a{};
+  if (mode == R_DUAL) {
+    a.vl = I.lam; a.bx = I.E.grad; a.bxs = -1.0; a.th_extra = I.zlmzu;
+  } else if (mode == R_RHS) {
+    a.vl = I.lam; a.bx = I.E.grad; a.bxs = -1.0; a.bc = I.E.c; a.bcs = -1.0;
+    a.th_extra = I.bar; a.rout = I.ka;
+  } else {
+    a.sigma = I.sigma; a.vx = I.kb; a.vl = I.kb + I.n_x; a.bx = I.ka; a.bxs = 1.0;
+    a.bc = I.ka + I.n_x; a.bcs = 1.0; a.dw = pr.dw; a.dc = pr.dc; a.rout = I.kr;
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(EVAL_BS)
+k_kkt_resid_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+              const int* __restrict__ pre, const InstParams* __restrict__ prm, int mode) {
+  __shared__ double red[EVAL_BS];
+  const int t = blockIdx.x;
+  const int k = find_item(pre, A, t);
+  const DevInst& I = insts[act[k]];
+  const ResidArgs a = resid_args(I, prm[k], mode);
+  resid_elem(I.P, I.E, a.sigma, a.dw, a.dc, a.vx, a.vl, a.bx, a.bxs, a.bc, a.bcs, a.rout,
+             I.thpart, I.npart, t - pre[k], red);
+}
+
 // Parameter rows of r = b - K v, and the global norms:
 // out[0] = max|r_x|, out[1] = max|r_c|, out[2] = max|b| (b may be null).
-__global__ void __launch_bounds__(RED_BS)
-k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
-                  const double* __restrict__ vx, const double* __restrict__ bx, double bxs,
-                  const double* __restrict__ bc, double bcs,
-                  double* __restrict__ rout, const double* __restrict__ chunkT,
-                  const double* __restrict__ npart, const double* __restrict__ th_extra,
-                  double* __restrict__ out) {
-  __shared__ double sh[RED_BS];
+// The element contributions thpart[N][p] are summed by warp w for the
+// columns q = w, w + 8, ...: lane-strided partial sums, then a fixed
+// shuffle tree.
+__device__ void resid_theta_one(const DevProb& P, const DevEval& E,
+                                const double* __restrict__ sigma, double dw,
+                                const double* __restrict__ vx, const double* __restrict__ bx,
+                                double bxs, const double* __restrict__ bc,
+                                double* __restrict__ rout, const double* __restrict__ thpart,
+                                const double* __restrict__ npart,
+                                const double* __restrict__ th_extra, double* __restrict__ out,
+                                double* sh) {
   const int tid = threadIdx.x, p = P.p, N = P.N;
+  const int lane = tid & 31, warp = tid >> 5;
   const size_t nz = (size_t)N * NP * P.n, nx = nz + p;
   double mx = 0.0, mc = 0.0, mb = 0.0;
-  for (int q = tid; q < p; q += RED_BS) {
-    double y = sum_chunks(chunkT, n_chunks(N), p, q);
-    if (vx) y += (E.wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw) * vx[nz + q];
-    if (th_extra) y -= th_extra[q];
-    double rr = (bx ? bxs * bx[nz + q] : 0.0) - y;
-    if (rout) rout[nz + q] = rr;
-    mx = fmax(mx, fabs(rr));
+  for (int q = warp; q < p; q += RED_BS / 32) {
+    double y = 0.0;
+    for (int i = lane; i < N; i += 32) y += thpart[(size_t)i * p + q];
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) {
+      if (vx) y += (E.wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw) * vx[nz + q];
+      if (th_extra) y -= th_extra[q];
+      const double rr = (bx ? bxs * bx[nz + q] : 0.0) - y;
+      if (rout) rout[nz + q] = rr;
+      mx = fmax(mx, fabs(rr));
+    }
   }
   for (int i = tid; i < N; i += RED_BS) {
     mx = fmax(mx, npart[i * 2 + 0]);
@@ -438,6 +549,27 @@ k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double
   mc = block_max<RED_BS>(mc, sh);
   mb = block_max<RED_BS>(mb, sh);
   if (tid == 0) { out[0] = mx; out[1] = mc; out[2] = mb; }
+}
+
+__global__ void __launch_bounds__(RED_BS)
+k_kkt_resid_theta(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
+                  const double* __restrict__ vx, const double* __restrict__ bx, double bxs,
+                  const double* __restrict__ bc, double* __restrict__ rout,
+                  const double* __restrict__ thpart, const double* __restrict__ npart,
+                  const double* __restrict__ th_extra, double* __restrict__ out) {
+  __shared__ double sh[RED_BS];
+  resid_theta_one(P, E, sigma, dw, vx, bx, bxs, bc, rout, thpart, npart, th_extra, out, sh);
+}
+
+__global__ void __launch_bounds__(RED_BS)
+k_kkt_resid_theta_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
+                    const InstParams* __restrict__ prm, int mode) {
+  __shared__ double sh[RED_BS];
+  const int k = blockIdx.x;
+  const DevInst& I = insts[act[k]];
+  const ResidArgs a = resid_args(I, prm[k], mode);
+  resid_theta_one(I.P, I.E, a.sigma, a.dw, a.vx, a.bx, a.bxs, a.bc, a.rout, I.thpart, I.npart,
+                  a.th_extra, I.out + O_RX, sh);
 }
 
 // ---- host launchers -------------------------------------------------------------
@@ -488,11 +620,44 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
                                        thpart, npart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = launch_chunk_sums(thpart, P.N, P.p, thpart + (size_t)P.N * P.p, st)) != cudaSuccess)
-    return e;
   count_launch();
-  k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, bcs, rout,
-                                          thpart + (size_t)P.N * P.p, npart, th_extra, out);
+  k_kkt_resid_theta<<<1, RED_BS, 0, st>>>(P, E, sigma, dw, vx, bx, bxs, bc, rout, thpart, npart,
+                                          th_extra, out);
+  return cudaGetLastError();
+}
+
+// ---- batched launchers (plan arrays in device memory) --------------------------
+cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                          int total_elems, const InstParams* prm, int xsel, int dxsel, int lsel,
+                          bool deriv, size_t smem, cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  if (deriv) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_eval_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    k_eval_b<true><<<total_elems, EVAL_BS, smem, st>>>(insts, act, A, pre_elem, prm, xsel, dxsel, lsel);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_eval_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    k_eval_b<false><<<total_elems, EVAL_BS, smem, st>>>(insts, act, A, pre_elem, prm, xsel, dxsel, lsel);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_eval_reduce_b<<<A, RED_BS, 0, st>>>(insts, act, deriv ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                           int total_elems, const InstParams* prm, int mode, cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_kkt_resid_b<<<total_elems, EVAL_BS, 0, st>>>(insts, act, A, pre_elem, prm, mode);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_kkt_resid_theta_b<<<A, RED_BS, 0, st>>>(insts, act, prm, mode);
   return cudaGetLastError();
 }
 

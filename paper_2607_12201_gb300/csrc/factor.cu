@@ -669,88 +669,148 @@ __device__ void grid_barrier(GridBar* gb) {
   __syncthreads();
 }
 
+// ---- batched persistent kernels -------------------------------------------------------
+// Work of all active instances of a batch in one cooperative launch.  Plan
+// arrays (device memory, written by the host):
+//   pre_elem[A+1]       prefix of element counts
+//   pre_lv[l][A+1]      prefix of cyclic-reduction blocks eliminated at level l
+//   pre_cs[A+1]         prefix of chunk-sum items (chunks x p^2 for the factor,
+//                       chunks x p for the solve)
+// Per-instance flags (InstFlags) say whether that instance's blocks fit the
+// kernel's shared memory or use its global slabs.
+template <typename T>
+__device__ inline const DevFactor<T>& inst_factor(const DevInst& I);
+template <>
+__device__ inline const DevFactor<float>& inst_factor<float>(const DevInst& I) { return I.F32; }
+template <>
+__device__ inline const DevFactor<double>& inst_factor<double>(const DevInst& I) { return I.F64; }
+
 template <typename T>
 __global__ void __launch_bounds__(FBS)
-k_factor_persistent(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
-                    DevFactor<T> F, DevSchur S, GridBar* gb, int elem_smem, int bcr_smem) {
+k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+           const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
+           const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
+           const int* __restrict__ flags, GridBar* gb, size_t smem_bytes) {
   extern __shared__ unsigned char smraw[];
-  const int N = P.N;
-  {
-    const int ext = P.ext, ld = odd_ld(ext);
+  // 1. element condensation
+  for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
+    const int k = find_item(pre_elem, A, t);
+    const DevInst& I = insts[act[k]];
+    const DevFactor<T>& F = inst_factor<T>(I);
+    const int ext = I.P.ext, ld = odd_ld(ext);
     T* cc0 = reinterpret_cast<T*>(smraw);
     T* cc1 = cc0 + ext;
     T* l0s = cc1 + ext;
     T* l1s = l0s + ext;
-    T* A = elem_smem ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
-    for (int e = blockIdx.x; e < N; e += gridDim.x)
-      elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, cc0, cc1, l0s, l1s);
+    T* Am = (flags[k] & 1) ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
+    elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, cc0,
+                       cc1, l0s, l1s);
   }
   grid_barrier(gb);
-  {
-    const int bext = P.bext, ld = odd_ld(bext);
-    T* cc0 = reinterpret_cast<T*>(smraw);
-    T* cc1 = cc0 + bext;
-    T* l0s = cc1 + bext;
-    T* l1s = l0s + bext;
-    T* A = bcr_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
-    for (int s = 1; s < N; s *= 2) {
-      const int nblk = bcr_level_blocks(N, s);
-      for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-        bcr_factor_one<T>(P, F, s, 0, bi, A, cc0, cc1, l0s, l1s);
-      grid_barrier(gb);
+  // 2. cyclic-reduction levels, then each instance's final block
+  for (int lv = 0; lv <= maxL; ++lv) {
+    const int* pre = pre_lv + (size_t)lv * (A + 1);
+    const bool fin = lv == maxL;
+    const int tot = fin ? A : pre[A];
+    for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+      const int k = fin ? t : find_item(pre, A, t);
+      const DevInst& I = insts[act[k]];
+      const DevFactor<T>& F = inst_factor<T>(I);
+      const int bext = I.P.bext, ld = odd_ld(bext);
+      T* cc0 = reinterpret_cast<T*>(smraw);
+      T* cc1 = cc0 + bext;
+      T* l0s = cc1 + bext;
+      T* l1s = l0s + bext;
+      T* Am = (flags[k] & 2) ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
+      if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, cc0, cc1, l0s, l1s);
+      else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, cc0, cc1, l0s, l1s);
     }
-    if (blockIdx.x == 0) bcr_factor_one<T>(P, F, 1, 1, 0, A, cc0, cc1, l0s, l1s);
+    grid_barrier(gb);
+  }
+  // 3. chunk sums of the parameter contributions
+  for (int t = blockIdx.x * FBS + threadIdx.x; t < pre_cs[A]; t += gridDim.x * FBS) {
+    const int k = find_item(pre_cs, A, t);
+    const DevInst& I = insts[act[k]];
+    const DevFactor<T>& F = inst_factor<T>(I);
+    const int L = I.P.p * I.P.p, G = n_chunks(2 * I.P.N);
+    const int it = t - pre_cs[k];
+    F.chunkS[it] = chunk_sum_item(F.Scon, 2 * I.P.N, L, G, it / L, it % L);
   }
   grid_barrier(gb);
-  {
-    const int L = P.p * P.p, G = n_chunks(2 * N);
-    for (int it = blockIdx.x * FBS + threadIdx.x; it < G * L; it += gridDim.x * FBS)
-      F.chunkS[it] = chunk_sum_item(F.Scon, 2 * N, L, G, it / L, it % L);
+  // 4. parameter Schur complement, one block per instance
+  for (int k = blockIdx.x; k < A; k += gridDim.x) {
+    const DevInst& I = insts[act[k]];
+    const DevFactor<T>& F = inst_factor<T>(I);
+    const size_t need = sizeof(double) * ((size_t)I.P.p * I.P.p + I.P.p);
+    double* sS = need <= smem_bytes ? reinterpret_cast<double*>(smraw) : I.S.S;
+    schur_block(I.P, F.inert, F.chunkS, I.E.wtt, I.sigma, prm[k].dw, I.S, sS);
+    if (threadIdx.x == 0) {
+      long long* o = reinterpret_cast<long long*>(I.out + O_INERT);
+      o[0] = I.S.inertia[0]; o[1] = I.S.inertia[1]; o[2] = I.S.inertia[2];
+    }
   }
-  grid_barrier(gb);
-  if (blockIdx.x == 0)
-    schur_block(P, F.inert, F.chunkS, E.wtt, sigma, dw, S, reinterpret_cast<double*>(smraw));
 }
 
 template <typename T>
 __global__ void __launch_bounds__(FBS)
-k_solve_persistent(DevProb P, DevFactor<T> F, DevSchur S, const double* __restrict__ b,
-                   double* __restrict__ sol, GridBar* gb) {
+k_solve_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+          const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
+          const int* __restrict__ pre_cs, int ir, int per_warp, GridBar* gb) {
   extern __shared__ unsigned char smraw[];
-  const int N = P.N, warp = threadIdx.x >> 5;
-  const int wpb = FBS / 32;
+  const int warp = threadIdx.x >> 5, wpb = FBS / 32;
   const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
-  T* wv = reinterpret_cast<T*>(smraw) + (size_t)warp * (P.ext > P.bext ? P.ext : P.bext);
-  for (int e = gw; e < N; e += nw) elem_fwd_one<T>(P, F, b, e, wv);
+  T* wv = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp;
+  for (int t = gw; t < pre_elem[A]; t += nw) {
+    const int k = find_item(pre_elem, A, t);
+    const DevInst& I = insts[act[k]];
+    elem_fwd_one<T>(I.P, inst_factor<T>(I), ir ? I.kr : I.ka, t - pre_elem[k], wv);
+  }
   grid_barrier(gb);
-  int top = 0;
-  for (int s = 1; s < N; s *= 2, ++top) {
-    const int nblk = bcr_level_blocks(N, s);
-    for (int bi = gw; bi < nblk; bi += nw) bcr_fwd_one<T>(P, F, s, 0, bi, wv);
+  for (int lv = 0; lv <= maxL; ++lv) {
+    const int* pre = pre_lv + (size_t)lv * (A + 1);
+    const bool fin = lv == maxL;
+    const int tot = fin ? A : pre[A];
+    for (int t = gw; t < tot; t += nw) {
+      const int k = fin ? t : find_item(pre, A, t);
+      const DevInst& I = insts[act[k]];
+      if (fin) bcr_fwd_one<T>(I.P, inst_factor<T>(I), 1, 1, 0, wv);
+      else bcr_fwd_one<T>(I.P, inst_factor<T>(I), 1 << lv, 0, t - pre[k], wv);
+    }
     grid_barrier(gb);
   }
-  if (gw == 0) bcr_fwd_one<T>(P, F, 1, 1, 0, wv);
-  grid_barrier(gb);
-  {
-    const int L = P.p, G = n_chunks(2 * N);
-    for (int it = blockIdx.x * FBS + threadIdx.x; it < G * L; it += gridDim.x * FBS)
-      F.chunkR[it] = chunk_sum_item(F.Rth, 2 * N, L, G, it / L, it % L);
+  for (int t = blockIdx.x * FBS + threadIdx.x; t < pre_cs[A]; t += gridDim.x * FBS) {
+    const int k = find_item(pre_cs, A, t);
+    const DevInst& I = insts[act[k]];
+    const DevFactor<T>& F = inst_factor<T>(I);
+    const int L = I.P.p, G = n_chunks(2 * I.P.N);
+    const int it = t - pre_cs[k];
+    F.chunkR[it] = chunk_sum_item(F.Rth, 2 * I.P.N, L, G, it / L, it % L);
   }
   grid_barrier(gb);
-  if (blockIdx.x == 0) {
-    double* sv = reinterpret_cast<double*>(smraw);
-    theta_solve_block(P, F.chunkR, b, S, sol, sv);
+  for (int k = blockIdx.x; k < A; k += gridDim.x) {
+    const DevInst& I = insts[act[k]];
+    theta_solve_block(I.P, inst_factor<T>(I).chunkR, ir ? I.kr : I.ka, I.S, ir ? I.kc : I.kb,
+                      reinterpret_cast<double*>(smraw));
   }
   grid_barrier(gb);
-  if (gw == 0) bcr_bwd_one<T>(P, F, S, sol, 1, 1, 0, wv);
-  grid_barrier(gb);
-  for (int lv = top - 1; lv >= 0; --lv) {
-    const int s = 1 << lv;
-    const int nblk = bcr_level_blocks(N, s);
-    for (int bi = gw; bi < nblk; bi += nw) bcr_bwd_one<T>(P, F, S, sol, s, 0, bi, wv);
+  for (int lv = maxL; lv >= 0; --lv) {
+    const int* pre = pre_lv + (size_t)lv * (A + 1);
+    const bool fin = lv == maxL;
+    const int tot = fin ? A : pre[A];
+    for (int t = gw; t < tot; t += nw) {
+      const int k = fin ? t : find_item(pre, A, t);
+      const DevInst& I = insts[act[k]];
+      double* sol = ir ? I.kc : I.kb;
+      if (fin) bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, sol, 1, 1, 0, wv);
+      else bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, sol, 1 << lv, 0, t - pre[k], wv);
+    }
     grid_barrier(gb);
   }
-  for (int e = gw; e < N; e += nw) elem_bwd_one<T>(P, F, S, sol, e, wv);
+  for (int t = gw; t < pre_elem[A]; t += nw) {
+    const int k = find_item(pre_elem, A, t);
+    const DevInst& I = insts[act[k]];
+    elem_bwd_one<T>(I.P, inst_factor<T>(I), I.S, ir ? I.kc : I.kb, t - pre_elem[k], wv);
+  }
 }
 
 // ---- host launchers ------------------------------------------------------------------
@@ -832,24 +892,6 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   const size_t sme = elem_factor_smem<T>(P, es), smb = bcr_factor_smem<T>(P, bs);
   const size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   cudaError_t e;
-  if (F.persistent && F.gbar && coop_supported()) {
-    const size_t sm = std::max(std::max(sme, smb), sms);
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_factor_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm);
-    int want = std::max(P.N, 1);
-    if (!es || !bs) want = std::min(want, F.n_slabs);
-    const int grid = coop_grid(k_factor_persistent<T>, FBS, sm, want);
-    if (grid >= 1) {
-      DevProb Pc = P; DevEval Ec = E; DevFactor<T> Fc = F; DevSchur Sc = S;
-      GridBar* gb = F.gbar;
-      int esi = es ? 1 : 0, bsi = bs ? 1 : 0;
-      void* args[] = {&Pc, &Ec, (void*)&sigma, &dw, &dc, &Fc, &Sc, &gb, &esi, &bsi};
-      count_launch();
-      return cudaLaunchCooperativeKernel((void*)k_factor_persistent<T>, dim3(grid), dim3(FBS),
-                                         args, sm, st);
-    }
-  }
   if ((e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st)) != cudaSuccess) return e;
   if (smb > 48 * 1024)
     cudaFuncSetAttribute(k_bcr_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
@@ -876,23 +918,6 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
                          const double* b, double* sol, cudaStream_t st) {
   const int tpb = 32 * SOLVE_WARPS;
   cudaError_t e;
-  if (F.persistent && F.gbar && coop_supported()) {
-    const size_t per_warp = sizeof(T) * (size_t)std::max(P.ext, P.bext);
-    const size_t sm = std::max(per_warp * (FBS / 32), sizeof(double) * (size_t)std::max(P.p, 1));
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_solve_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm);
-    const int want = std::max(1, ceil_div(P.N, FBS / 32));
-    const int grid = coop_grid(k_solve_persistent<T>, FBS, sm, want);
-    if (grid >= 1) {
-      DevProb Pc = P; DevFactor<T> Fc = F; DevSchur Sc = S;
-      GridBar* gb = F.gbar;
-      void* args[] = {&Pc, &Fc, &Sc, (void*)&b, (void*)&sol, &gb};
-      count_launch();
-      return cudaLaunchCooperativeKernel((void*)k_solve_persistent<T>, dim3(grid), dim3(FBS), args,
-                                         sm, st);
-    }
-  }
   size_t sme = sizeof(T) * (size_t)P.ext * SOLVE_WARPS;
   size_t smb = sizeof(T) * (size_t)P.bext * SOLVE_WARPS;
   if (sme > 48 * 1024) {
@@ -936,6 +961,58 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
   k_elem_bwd<T><<<ceil_div(P.N, SOLVE_WARPS), tpb, sme, st>>>(P, F, S, sol);
   return cudaGetLastError();
 }
+
+// Batched launchers.  `grid_cap` limits the grid when some instance uses its
+// global slabs (at most n_slabs blocks may run).
+template <typename T>
+cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                            const int* pre_lv, int maxL, const int* pre_cs,
+                            const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
+                            int grid_cap, cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_factor_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = coop_grid(k_factor_b<T>, FBS, smem, grid_cap);
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
+                  (void*)&pre_cs, (void*)&prm, (void*)&flags, &gb, &smem};
+  count_launch();
+  return cudaLaunchCooperativeKernel((void*)k_factor_b<T>, dim3(grid), dim3(FBS), args, smem, st);
+}
+
+template <typename T>
+cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                           const int* pre_lv, int maxL, const int* pre_cs, int ir, int per_warp,
+                           GridBar* gb, int max_p, int grid_want, cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  size_t smem = std::max(sizeof(T) * (size_t)per_warp * (FBS / 32),
+                         sizeof(double) * (size_t)std::max(max_p, 1));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_solve_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want);
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
+                  (void*)&pre_cs, &ir, &per_warp, &gb};
+  count_launch();
+  return cudaLaunchCooperativeKernel((void*)k_solve_b<T>, dim3(grid), dim3(FBS), args, smem, st);
+}
+
+template cudaError_t launch_factor_b<float>(const DevInst*, const int*, int, const int*,
+                                            const int*, int, const int*, const InstParams*,
+                                            const int*, GridBar*, size_t, int, cudaStream_t);
+template cudaError_t launch_factor_b<double>(const DevInst*, const int*, int, const int*,
+                                             const int*, int, const int*, const InstParams*,
+                                             const int*, GridBar*, size_t, int, cudaStream_t);
+template cudaError_t launch_solve_b<float>(const DevInst*, const int*, int, const int*, const int*,
+                                           int, const int*, int, int, GridBar*, int, int,
+                                           cudaStream_t);
+template cudaError_t launch_solve_b<double>(const DevInst*, const int*, int, const int*,
+                                            const int*, int, const int*, int, int, GridBar*, int,
+                                            int, cudaStream_t);
+template size_t elem_factor_smem<float>(const DevProb&, bool);
+template size_t elem_factor_smem<double>(const DevProb&, bool);
+template size_t bcr_factor_smem<float>(const DevProb&, bool);
+template size_t bcr_factor_smem<double>(const DevProb&, bool);
 
 template cudaError_t launch_factor<double>(const DevProb&, const DevEval&, const double*, double,
                                            double, const DevFactor<double>&, const DevSchur&,

@@ -123,10 +123,8 @@ __global__ void k_init_point(DevProb P, const double* __restrict__ theta0, doubl
 // gwork when 3n is too large.
 constexpr int SWEEP_MAXIT = 30;
 constexpr int SWEEP_BS = 256;
-__global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* __restrict__ x,
-                                                            int* __restrict__ fails,
-                                                            float* __restrict__ gwork) {
-  extern __shared__ double sm[];
+__device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
+                          float* __restrict__ gwork, double* sm) {
   __shared__ int s_piv;
   __shared__ float s_inv;
   __shared__ double s_red[SWEEP_BS];
@@ -275,13 +273,19 @@ __global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* _
   if (tid == 0) *fails = nfail;
 }
 
+__global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* __restrict__ x,
+                                                            int* __restrict__ fails,
+                                                            float* __restrict__ gwork) {
+  extern __shared__ double sm[];
+  sweep_cta(P, x, fails, gwork, sm);
+}
+
 // The same sweep for 3n <= 32 on one warp: lane l owns row l of the FP32
 // Newton matrix in registers, so the LU with partial pivoting and the back
 // substitution run on warp shuffles without block barriers.
 constexpr int WSWEEP = 32;
-__global__ void __launch_bounds__(32) k_forward_sweep_warp(DevProb P, double* __restrict__ x,
-                                                           int* __restrict__ fails) {
-  extern __shared__ double sm[];
+__device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
+                           double* sm) {
   const int n = P.n, r = P.r, dim = KC * n;
   const int lane = threadIdx.x;
   const unsigned FULL = 0xffffffffu;
@@ -421,6 +425,32 @@ __global__ void __launch_bounds__(32) k_forward_sweep_warp(DevProb P, double* __
   if (lane == 0) *fails = nfail;
 }
 
+__global__ void __launch_bounds__(32) k_forward_sweep_warp(DevProb P, double* __restrict__ x,
+                                                           int* __restrict__ fails) {
+  extern __shared__ double sm[];
+  sweep_warp(P, x, fails, sm);
+}
+
+size_t sweep_warp_smem_bytes(const DevProb& P) {
+  size_t sm = sizeof(double) * ((size_t)P.r * (1 + KC) + P.n + KC * (size_t)P.n) +
+              sizeof(float) * ((size_t)2 * KC * P.r + WSWEEP * (WSWEEP + 1));
+  return (sm + 15) & ~size_t(15);
+}
+
+// Batched sweeps: one block per instance.
+__global__ void __launch_bounds__(32) k_sweep_warp_b(const DevInst* __restrict__ insts,
+                                                     const int* __restrict__ act) {
+  extern __shared__ double sm[];
+  const DevInst& I = insts[act[blockIdx.x]];
+  sweep_warp(I.P, I.x, I.fails, sm);
+}
+__global__ void __launch_bounds__(SWEEP_BS) k_sweep_cta_b(const DevInst* __restrict__ insts,
+                                                          const int* __restrict__ act) {
+  extern __shared__ double sm[];
+  const DevInst& I = insts[act[blockIdx.x]];
+  sweep_cta(I.P, I.x, I.fails, I.sweep_work, sm);
+}
+
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
   const size_t dim = KC * (size_t)P.n;
   size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * KC) + P.n + 2 * dim);
@@ -431,9 +461,7 @@ size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
 cudaError_t launch_forward_sweep(collo_problem* pr) {
   const DevProb& P = pr->P;
   if (KC * P.n <= WSWEEP) {
-    size_t sm = sizeof(double) * ((size_t)P.r * (1 + KC) + P.n + KC * (size_t)P.n) +
-                sizeof(float) * ((size_t)2 * KC * P.r + WSWEEP * (WSWEEP + 1));
-    sm = (sm + 15) & ~size_t(15);
+    size_t sm = sweep_warp_smem_bytes(P);
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_forward_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
@@ -449,389 +477,230 @@ cudaError_t launch_forward_sweep(collo_problem* pr) {
   return cudaGetLastError();
 }
 
+// ---- batched IPM kernels (one block per instance unless stated) ------------------
+
+// theta0 pushed into the bounds (Waechter & Biegler 2006, Sec. 3.6), bound
+// duals 1.
+__global__ void k_init_point_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
+                               double kappa1, double kappa2) {
+  const DevInst& I = insts[act[blockIdx.x]];
+  const DevProb& P = I.P;
+  const size_t nz = (size_t)P.N * NP * P.n;
+  for (int q = threadIdx.x; q < P.p; q += blockDim.x) {
+    const double lo = P.theta_lo[q], hi = P.theta_hi[q];
+    const double pl = fmin(kappa1 * fmax(1.0, fabs(lo)), kappa2 * (hi - lo));
+    const double pu = fmin(kappa1 * fmax(1.0, fabs(hi)), kappa2 * (hi - lo));
+    I.x[nz + q] = fmin(fmax(I.th0[q], lo + pl), hi - pu);
+    I.zl[q] = 1.0;
+    I.zu[q] = 1.0;
+  }
+}
+
 // Parameter-space quantities for barrier parameter mu:
 //   sigma_theta = zl/sl + zu/su (into sigma[nz..]); bar = mu/sl - mu/su;
-//   zlmzu = zl - zu; out[0] = max(sl zl, su zu), out[1] = min(...),
-//   out[2] = sum zl + sum zu, out[3] = sum log sl + sum log su.
+//   zlmzu = zl - zu; out: max / min of (sl zl, su zu), sum zl + zu,
+//   sum log sl + log su.
 __global__ void __launch_bounds__(IBS)
-k_theta_prep(DevProb P, const double* __restrict__ x, const double* __restrict__ zl,
-             const double* __restrict__ zu, double mu, double* __restrict__ sigma,
-             double* __restrict__ bar, double* __restrict__ zlmzu, double* __restrict__ out) {
+k_theta_prep_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
+               const InstParams* __restrict__ prm) {
   __shared__ double sh[IBS];
+  const DevInst& I = insts[act[blockIdx.x]];
+  const DevProb& P = I.P;
+  const double mu = prm[blockIdx.x].mu;
   const size_t nz = (size_t)P.N * NP * P.n;
   double wmax = 0.0, wmin = 1e300, zs = 0.0, lg = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
-    const double th = x[nz + q];
+    const double th = I.x[nz + q];
     const double sl = th - P.theta_lo[q], su = P.theta_hi[q] - th;
-    sigma[nz + q] = zl[q] / sl + zu[q] / su;
-    bar[q] = mu / sl - mu / su;
-    zlmzu[q] = zl[q] - zu[q];
-    wmax = fmax(wmax, fmax(sl * zl[q], su * zu[q]));
-    wmin = fmin(wmin, fmin(sl * zl[q], su * zu[q]));
-    zs += zl[q] + zu[q];
+    I.sigma[nz + q] = I.zl[q] / sl + I.zu[q] / su;
+    I.bar[q] = mu / sl - mu / su;
+    I.zlmzu[q] = I.zl[q] - I.zu[q];
+    wmax = fmax(wmax, fmax(sl * I.zl[q], su * I.zu[q]));
+    wmin = fmin(wmin, fmin(sl * I.zl[q], su * I.zu[q]));
+    zs += I.zl[q] + I.zu[q];
     lg += log(sl) + log(su);
   }
   wmax = bmax<IBS>(wmax, sh);
   wmin = bmin<IBS>(wmin, sh);
   zs = bsum<IBS>(zs, sh);
   lg = bsum<IBS>(lg, sh);
-  if (threadIdx.x == 0) { out[0] = wmax; out[1] = wmin; out[2] = zs; out[3] = lg; }
+  if (threadIdx.x == 0) {
+    I.out[O_WMAX] = wmax; I.out[O_WMIN] = wmin; I.out[O_ZSUM] = zs; I.out[O_LOG] = lg;
+  }
+}
+
+// |lambda|_1 (which = 0) or grad^T kb over the primal entries (which = 1).
+__global__ void __launch_bounds__(IBS)
+k_vec_reduce_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int which) {
+  __shared__ double sh[IBS];
+  const DevInst& I = insts[act[blockIdx.x]];
+  double v = 0.0;
+  if (which == 0)
+    for (long long i = threadIdx.x; i < I.n_c; i += IBS) v += fabs(I.lam[i]);
+  else
+    for (long long i = threadIdx.x; i < I.n_x; i += IBS) v += I.E.grad[i] * I.kb[i];
+  v = bsum<IBS>(v, sh);
+  if (threadIdx.x == 0) I.out[which == 0 ? O_LAM1 : O_GDX] = v;
 }
 
 // Bound-dual steps, fraction-to-boundary step sizes and the barrier part of
-// grad(phi_mu)^T dx:  out[0] = alpha_max, out[1] = alpha_z, out[2] = gphi_theta.
+// grad(phi_mu)^T dx.
 __global__ void __launch_bounds__(IBS)
-k_theta_step(DevProb P, const double* __restrict__ x, const double* __restrict__ dx,
-             const double* __restrict__ zl, const double* __restrict__ zu, double mu, double tau,
-             double* __restrict__ dz, double* __restrict__ out) {
+k_theta_step_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
+               const InstParams* __restrict__ prm) {
   __shared__ double sh[IBS];
+  const DevInst& I = insts[act[blockIdx.x]];
+  const DevProb& P = I.P;
+  const double mu = prm[blockIdx.x].mu, tau = prm[blockIdx.x].tau;
   const size_t nz = (size_t)P.N * NP * P.n;
   double amax = 1.0, az = 1.0, g = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
-    const double th = x[nz + q], d = dx[nz + q];
+    const double th = I.x[nz + q], d = I.kb[nz + q];
     const double sl = th - P.theta_lo[q], su = P.theta_hi[q] - th;
-    const double dzl = mu / sl - zl[q] - (zl[q] / sl) * d;
-    const double dzu = mu / su - zu[q] + (zu[q] / su) * d;
-    dz[q] = dzl;
-    dz[P.p + q] = dzu;
+    const double dzl = mu / sl - I.zl[q] - (I.zl[q] / sl) * d;
+    const double dzu = mu / su - I.zu[q] + (I.zu[q] / su) * d;
+    I.dz[q] = dzl;
+    I.dz[P.p + q] = dzu;
     if (d < 0) amax = fmin(amax, -tau * sl / d);
     if (-d < 0) amax = fmin(amax, tau * su / d);
-    if (dzl < 0) az = fmin(az, -tau * zl[q] / dzl);
-    if (dzu < 0) az = fmin(az, -tau * zu[q] / dzu);
+    if (dzl < 0) az = fmin(az, -tau * I.zl[q] / dzl);
+    if (dzu < 0) az = fmin(az, -tau * I.zu[q] / dzu);
     g += (-mu / sl + mu / su) * d;
   }
   amax = bmin<IBS>(amax, sh);
   az = bmin<IBS>(az, sh);
   g = bsum<IBS>(g, sh);
-  if (threadIdx.x == 0) { out[0] = amax; out[1] = az; out[2] = g; }
+  if (threadIdx.x == 0) { I.out[O_AMAX] = amax; I.out[O_AZ] = az; I.out[O_GPHI] = g; }
 }
 
 // Barrier log terms at the trial point theta + alpha dtheta.
-// out[0] = sum log sl + log su, out[1] = 1 if all slacks > 0.
 __global__ void __launch_bounds__(IBS)
-k_trial_barrier(DevProb P, const double* __restrict__ x, const double* __restrict__ dx,
-                double alpha, double* __restrict__ out) {
+k_trial_barrier_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
+                  const InstParams* __restrict__ prm) {
   __shared__ double sh[IBS];
+  const DevInst& I = insts[act[blockIdx.x]];
+  const DevProb& P = I.P;
+  const double alpha = prm[blockIdx.x].alpha;
   const size_t nz = (size_t)P.N * NP * P.n;
   double lg = 0.0, bad = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
-    const double th = x[nz + q] + alpha * dx[nz + q];
+    const double th = I.x[nz + q] + alpha * I.kb[nz + q];
     const double sl = th - P.theta_lo[q], su = P.theta_hi[q] - th;
     if (!(sl > 0) || !(su > 0)) bad = 1.0;
     else lg += log(sl) + log(su);
   }
   lg = bsum<IBS>(lg, sh);
   bad = bmax<IBS>(bad, sh);
-  if (threadIdx.x == 0) { out[0] = lg; out[1] = bad > 0 ? 0.0 : 1.0; }
+  if (threadIdx.x == 0) { I.out[O_TLOG] = lg; I.out[O_TOK] = bad > 0 ? 0.0 : 1.0; }
 }
 
-// Accept the step: x += alpha dx, lambda += alpha dlambda, bound duals
-// += alpha_z dz, then reset into [mu/(kS s), kS mu/s].
-__global__ void k_update(DevProb P, double* __restrict__ x, double* __restrict__ lam,
-                         double* __restrict__ zl, double* __restrict__ zu,
-                         const double* __restrict__ sol, const double* __restrict__ dz,
-                         double alpha, double alpha_z, double mu, double ksig, size_t nx,
-                         size_t nc) {
-  const size_t nz = (size_t)P.N * NP * P.n;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  for (size_t i = tid; i < (size_t)P.p; i += stride) {
-    const double th = x[nz + i] + alpha * sol[nz + i];
-    const double sl = th - P.theta_lo[i], su = P.theta_hi[i] - th;
-    double a = zl[i] + alpha_z * dz[i];
-    double b = zu[i] + alpha_z * dz[P.p + i];
-    a = fmax(fmin(a, ksig * mu / sl), mu / (ksig * sl));
-    b = fmax(fmin(b, ksig * mu / su), mu / (ksig * su));
-    zl[i] = a;
-    zu[i] = b;
+// Grid-stride over the n_x + n_c entries of every active instance (prefix
+// pre): mode 0 accepts the step (x += alpha dx, lambda += alpha dlambda,
+// bound duals += alpha_z dz then reset into [mu/(kS s), kS mu/s]); mode 1
+// adds the refinement correction (kb += kc); mode 2 zeroes lambda.
+__global__ void k_update_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+                           const long long* __restrict__ pre, const InstParams* __restrict__ prm,
+                           int mode) {
+  const long long total = pre[A];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = A;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int k = lo;
+    const DevInst& I = insts[act[k]];
+    const long long j = t - pre[k];
+    if (mode == 1) { I.kb[j] += I.kc[j]; continue; }
+    if (mode == 2) { if (j < I.n_c) I.lam[j] = 0.0; continue; }
+    const InstParams pr = prm[k];
+    if (j < I.P.p) {
+      const DevProb& P = I.P;
+      const size_t nz = (size_t)P.N * NP * P.n;
+      const double th = I.x[nz + j] + pr.alpha * I.kb[nz + j];
+      const double sl = th - P.theta_lo[j], su = P.theta_hi[j] - th;
+      double a = I.zl[j] + pr.alpha_z * I.dz[j];
+      double b = I.zu[j] + pr.alpha_z * I.dz[P.p + j];
+      a = fmax(fmin(a, pr.ksig * pr.mu / sl), pr.mu / (pr.ksig * sl));
+      b = fmax(fmin(b, pr.ksig * pr.mu / su), pr.mu / (pr.ksig * su));
+      I.zl[j] = a;
+      I.zu[j] = b;
+    }
+    if (j < I.n_x) I.x[j] += pr.alpha * I.kb[j];
+    else I.lam[j - I.n_x] += pr.alpha * I.kb[j];
   }
-  for (size_t i = tid; i < nx + nc; i += stride) {
-    if (i < nx) x[i] += alpha * sol[i];
-    else lam[i - nx] += alpha * sol[i];
+}
+
+// ---- batched launchers -------------------------------------------------------------
+cudaError_t launch_init_point_b(const DevInst* insts, const int* act, int A, double k1, double k2,
+                                cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_init_point_b<<<A, 128, 0, st>>>(insts, act, k1, k2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_b(const DevInst* insts, const int* act_warp, int A_warp,
+                           size_t smem_warp, const int* act_cta, int A_cta, size_t smem_cta,
+                           cudaStream_t st) {
+  if (A_warp > 0) {
+    if (smem_warp > 48 * 1024)
+      cudaFuncSetAttribute(k_sweep_warp_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp);
+    count_launch();
+    k_sweep_warp_b<<<A_warp, 32, smem_warp, st>>>(insts, act_warp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  if (A_cta > 0) {
+    if (smem_cta > 48 * 1024)
+      cudaFuncSetAttribute(k_sweep_cta_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta);
+    count_launch();
+    k_sweep_cta_b<<<A_cta, SWEEP_BS, smem_cta, st>>>(insts, act_cta);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_theta_prep_b(const DevInst* insts, const int* act, int A, const InstParams* prm,
+                                cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_theta_prep_b<<<A, IBS, 0, st>>>(insts, act, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_reduce_b(const DevInst* insts, const int* act, int A, int which,
+                                cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_vec_reduce_b<<<A, IBS, 0, st>>>(insts, act, which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_theta_step_b(const DevInst* insts, const int* act, int A, const InstParams* prm,
+                                cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_theta_step_b<<<A, IBS, 0, st>>>(insts, act, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trial_barrier_b(const DevInst* insts, const int* act, int A,
+                                   const InstParams* prm, cudaStream_t st) {
+  if (A == 0) return cudaSuccess;
+  count_launch();
+  k_trial_barrier_b<<<A, IBS, 0, st>>>(insts, act, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_b(const DevInst* insts, const int* act, int A, const long long* pre,
+                            long long total, const InstParams* prm, int mode, cudaStream_t st) {
+  if (A == 0 || total == 0) return cudaSuccess;
+  int g = (int)std::min<long long>((total + 255) / 256, 8192);
+  count_launch();
+  k_update_b<<<std::max(g, 1), 256, 0, st>>>(insts, act, A, pre, prm, mode);
+  return cudaGetLastError();
 }
 
 }  // namespace collo
-
-using namespace collo;
-
-namespace {
-
-struct Opt {
-  double tol, acc_tol;
-  int acc_iter, max_iter;
-  double max_wall;
-  int precision;
-  double mixed_mu_switch;
-  int refine_max;
-  double refine_tol;
-  int verbose;
-  // Waechter & Biegler (2006) constants
-  double mu_init = 0.1, kappa_mu = 0.2, theta_mu = 1.5, kappa_eps = 10.0, tau_min = 0.99;
-  double s_max = 100.0, kappa1 = 1e-2, kappa2 = 1e-2, kappa_sigma = 1e10;
-  double gamma_theta = 1e-5, gamma_phi = 1e-5, delta = 1.0, s_theta = 1.1, s_phi = 2.3;
-  double eta_phi = 1e-4, gamma_alpha = 0.05;
-  double dw_min = 1e-20, dw_0 = 1e-4, dw_max = 1e40, kw_minus = 1.0 / 3.0, kw_plus = 8.0;
-  double kw_plus_bar = 100.0, dc_coef = 1e-8, dc_exp = 0.25;
-};
-
-}  // namespace
-
-extern "C" {
-
-void collo_ipm_options_default(collo_ipm_options* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->tol = 1e-6;
-  o->acceptable_tol = 1e-4;
-  o->acceptable_iter = 15;
-  o->max_iter = 3000;
-  o->max_wall_time = 3600.0;
-  o->precision = COLLO_PRECISION_FP64;
-  o->mixed_mu_switch = 1e-6;
-  o->refine_max = 10;
-  o->refine_tol = 1e-10;
-  o->verbose = 0;
-}
-
-collo_status collo_initial_states(collo_problem* prob, const double* theta, double* x_out,
-                                  int* failures) {
-  if (!prob || !theta) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
-  COLLO_CUDA(cudaSetDevice(prob->device));
-  cudaStream_t st = prob->stream;
-  const size_t nz = (size_t)prob->P.N * NP * prob->P.n;
-  if (prob->P.p)
-    COLLO_CUDA(cudaMemcpyAsync(prob->x + nz, theta, prob->P.p * sizeof(double),
-                               cudaMemcpyDefault, st));
-  COLLO_CUDA(launch_forward_sweep(prob));
-  int f = 0;
-  COLLO_CUDA(cudaMemcpyAsync(&f, prob->fails, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (x_out)
-    COLLO_CUDA(cudaMemcpyAsync(x_out, prob->x, prob->n_x * sizeof(double), cudaMemcpyDefault, st));
-  COLLO_CUDA(cudaStreamSynchronize(st));
-  if (failures) *failures = f;
-  return COLLO_OK;
-}
-
-collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
-                             const collo_ipm_options* opts, collo_result* res) {
-  if (!prob || !res || (prob->P.p > 0 && !theta0)) {
-    set_error("NULL argument");
-    return COLLO_ERR_INVALID_ARG;
-  }
-  COLLO_CUDA(cudaSetDevice(prob->device));
-  collo_ipm_options uo;
-  if (opts) uo = *opts; else collo_ipm_options_default(&uo);
-  Opt o;
-  o.tol = uo.tol; o.acc_tol = uo.acceptable_tol; o.acc_iter = uo.acceptable_iter;
-  o.max_iter = uo.max_iter; o.max_wall = uo.max_wall_time; o.precision = uo.precision;
-  o.mixed_mu_switch = uo.mixed_mu_switch; o.refine_max = uo.refine_max;
-  o.refine_tol = uo.refine_tol; o.verbose = uo.verbose;
-  const auto t_start = std::chrono::steady_clock::now();
-  cudaStream_t st = prob->stream;
-  const DevProb& P = prob->P;
-  const int p = P.p;
-  const size_t nx = prob->n_x, nc = prob->n_c, nz = nx - p;
-  double* h = prob->hscal;
-  double* d = prob->scal;
-  double* bar = prob->thx;            // [p]
-  double* zlmzu = prob->thx + p;      // [p]
-  double* th0 = prob->thx + 2 * p;    // [p]
-  double* dots = prob->red_parts;     // [RGRID] reduction partials
-  double* rhs = prob->kvec_a;
-  double* sol = prob->kvec_b;
-
-  res->status = COLLO_ERR_MAXITER;
-  res->iterations = 0; res->factorizations = 0; res->line_search_trials = 0;
-
-  // initial point
-  if (p) COLLO_CUDA(cudaMemcpyAsync(th0, theta0, p * sizeof(double), cudaMemcpyDefault, st));
-  count_launch();
-  k_init_point<<<1, 256, 0, st>>>(P, th0, prob->x, prob->zl, prob->zu, o.kappa1, o.kappa2);
-  COLLO_CUDA(cudaGetLastError());
-  COLLO_CUDA(launch_forward_sweep(prob));
-  COLLO_CUDA(cudaMemsetAsync(prob->lam, 0, nc * sizeof(double), st));
-  double mu = o.mu_init;
-  double tau = std::max(o.tau_min, 1.0 - mu);
-  std::vector<std::pair<double, double>> filt;
-  double dw_last = 0.0;
-  int acc_count = 0;
-  COLLO_CUDA(launch_eval(P, prob->E, prob->x, nullptr, 0.0, nullptr, 1.0, false, st));
-  COLLO_CUDA(cudaMemcpyAsync(h, prob->E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  COLLO_CUDA(cudaStreamSynchronize(st));
-  const double th_init = h[1];
-  const double theta_max = 1e4 * std::max(1.0, th_init);
-  const double theta_min = 1e-4 * std::max(1.0, th_init);
-  int it = 0;
-  double err = INFINITY, phi = NAN;
-  collo_status status = COLLO_ERR_MAXITER;
-  const long long want_pos = (long long)nx, want_neg = (long long)nc;
-
-  for (;;) {
-    double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    // 1. derivatives at the iterate and the optimality measures
-    COLLO_CUDA(launch_eval(P, prob->E, prob->x, nullptr, 0.0, prob->lam, 1.0, true, st));
-    prob->evaluated = true;
-    count_launch();
-    k_theta_prep<<<1, IBS, 0, st>>>(P, prob->x, prob->zl, prob->zu, mu, prob->sigma, bar, zlmzu,
-                                    d + 16);
-    COLLO_CUDA(launch_kkt_resid(P, prob->E, nullptr, 0.0, 0.0, nullptr, prob->lam,
-                                prob->E.grad, -1.0, nullptr, 0.0, nullptr, prob->thpart,
-                                prob->npart, zlmzu, d + 20, st));
-    count_launch();
-    k_dot_part<<<RGRID, IBS, 0, st>>>(prob->lam, nullptr, nc, 1, dots);
-    count_launch();
-    k_sum_parts<<<1, IBS, 0, st>>>(dots, d + 24);
-    COLLO_CUDA(cudaGetLastError());
-    COLLO_CUDA(cudaMemcpyAsync(h + 16, d + 16, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    COLLO_CUDA(cudaMemcpyAsync(h, prob->E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    COLLO_CUDA(cudaStreamSynchronize(st));
-    phi = h[0];
-    const double cinf = h[2];
-    if (!std::isfinite(phi) || !std::isfinite(h[1])) { status = COLLO_ERR_NUMERIC; break; }
-    const double wmax = h[16], wmin = h[17], zsum = h[18];
-    const double dual = h[20], lam1 = h[24];
-    const double s_d = std::max(o.s_max, (lam1 + zsum) / (double)(nc + 2 * p)) / o.s_max;
-    const double s_c = std::max(o.s_max, zsum / (double)std::max(2 * p, 1)) / o.s_max;
-    auto Emu = [&](double m) {
-      double compl_ = p ? std::max(wmax - m, m - wmin) : 0.0;
-      return std::max(std::max(dual / s_d, cinf), compl_ / s_c);
-    };
-    err = Emu(0.0);
-    if (err <= o.tol) { status = COLLO_OK; break; }
-    acc_count = err <= o.acc_tol ? acc_count + 1 : 0;
-    if (acc_count >= o.acc_iter) { status = COLLO_ACCEPTABLE; break; }
-    if (it >= o.max_iter) { status = COLLO_ERR_MAXITER; break; }
-    if (wall > o.max_wall) { status = COLLO_ERR_TIMEOUT; break; }
-    // 2. barrier update (monotone)
-    while (Emu(mu) <= o.kappa_eps * mu) {
-      double nm = std::max(o.tol / 10.0, std::min(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
-      if (nm >= mu) break;
-      mu = nm;
-      tau = std::max(o.tau_min, 1.0 - mu);
-      filt.clear();
-    }
-    // 3. Newton direction with inertia correction
-    count_launch();
-    k_theta_prep<<<1, IBS, 0, st>>>(P, prob->x, prob->zl, prob->zu, mu, prob->sigma, bar, zlmzu,
-                                    d + 16);
-    COLLO_CUDA(launch_kkt_resid(P, prob->E, nullptr, 0.0, 0.0, nullptr, prob->lam,
-                                prob->E.grad, -1.0, prob->E.c, -1.0, rhs, prob->thpart,
-                                prob->npart, bar, d + 20, st));
-    const int prec = (o.precision == COLLO_PRECISION_MIXED &&
-                      !(o.mixed_mu_switch > 0 && mu < o.mixed_mu_switch))
-                         ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64;
-    const double dc = o.dc_coef * std::pow(mu, o.dc_exp);
-    double dw = 0.0;
-    long long in[3];
-    collo_status s = factor_internal(prob, dw, dc, prec, in);
-    if (s != COLLO_OK) return res->status = s;
-    res->factorizations++;
-    if (!(in[0] == want_pos && in[1] == want_neg && in[2] == 0)) {
-      dw = dw_last == 0.0 ? o.dw_0 : std::max(o.dw_min, o.kw_minus * dw_last);
-      bool good = false;
-      for (;;) {
-        s = factor_internal(prob, dw, dc, prec, in);
-        if (s != COLLO_OK) return res->status = s;
-        res->factorizations++;
-        if (in[0] == want_pos && in[1] == want_neg && in[2] == 0) { good = true; dw_last = dw; break; }
-        dw *= dw_last == 0.0 ? o.kw_plus_bar : o.kw_plus;
-        if (dw > o.dw_max) break;
-      }
-      if (!good) { status = COLLO_ERR_INERTIA; break; }
-    }
-    int sweeps = 0;
-    double rres = 0.0;
-    s = solve_internal(prob, rhs, sol, o.refine_max, o.refine_tol, &sweeps, &rres);
-    if (s != COLLO_OK) { status = s; break; }
-    // 4. step sizes
-    count_launch();
-    k_theta_step<<<1, IBS, 0, st>>>(P, prob->x, sol, prob->zl, prob->zu, mu, tau, prob->dz, d + 28);
-    count_launch();
-    k_dot_part<<<RGRID, IBS, 0, st>>>(prob->E.grad, sol, nx, 0, dots);
-    count_launch();
-    k_sum_parts<<<1, IBS, 0, st>>>(dots, d + 32);
-    COLLO_CUDA(cudaGetLastError());
-    COLLO_CUDA(cudaMemcpyAsync(h + 16, d + 16, 17 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    COLLO_CUDA(cudaStreamSynchronize(st));
-    const double alpha_max = h[28], alpha_z = h[29];
-    const double gphi = h[32] + h[30];
-    const double theta_k = h[1] > 0 ? h[1] : 0.0;
-    const double phi_k = phi - mu * h[19];
-    double alpha_min;
-    if (gphi < 0) {
-      if (theta_k <= theta_min)
-        alpha_min = o.gamma_alpha * std::min(std::min(o.gamma_theta, o.gamma_phi * theta_k / (-gphi)),
-                                             o.delta * std::pow(theta_k, o.s_theta) /
-                                                 std::pow(-gphi, o.s_phi));
-      else
-        alpha_min = o.gamma_alpha * std::min(o.gamma_theta, o.gamma_phi * theta_k / (-gphi));
-    } else {
-      alpha_min = o.gamma_alpha * o.gamma_theta;
-    }
-    // 5. backtracking filter line search
-    double alpha = alpha_max;
-    bool accepted = false, ftype = false;
-    int trials = 0;
-    while (alpha >= alpha_min) {
-      ++trials;
-      COLLO_CUDA(launch_eval(P, prob->E, prob->x, sol, alpha, nullptr, 1.0, false, st));
-      count_launch();
-      k_trial_barrier<<<1, IBS, 0, st>>>(P, prob->x, sol, alpha, d + 36);
-      COLLO_CUDA(cudaGetLastError());
-      COLLO_CUDA(cudaMemcpyAsync(h, prob->E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      COLLO_CUDA(cudaMemcpyAsync(h + 36, d + 36, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      COLLO_CUDA(cudaStreamSynchronize(st));
-      const double phit = h[0], thetat = h[1];
-      if (std::isfinite(phit) && std::isfinite(thetat) && h[37] > 0.5) {
-        const double phibt = phit - mu * h[36];
-        bool ok = std::isfinite(phibt) && thetat < theta_max;
-        if (ok)
-          for (auto& f : filt)
-            if (thetat >= f.first && phibt >= f.second) { ok = false; break; }
-        if (ok) {
-          const bool sw = gphi < 0 &&
-                          alpha * std::pow(-gphi, o.s_phi) > o.delta * std::pow(theta_k, o.s_theta);
-          if (theta_k <= theta_min && sw) {
-            ftype = true;
-            accepted = phibt <= phi_k + o.eta_phi * alpha * gphi;
-          } else {
-            ftype = false;
-            accepted = thetat <= (1.0 - o.gamma_theta) * theta_k || phibt <= phi_k - o.gamma_phi * theta_k;
-          }
-          if (accepted) break;
-        }
-      }
-      alpha *= 0.5;
-    }
-    res->line_search_trials += trials;
-    if (!accepted) { status = COLLO_ERR_LINESEARCH; break; }
-    if (!ftype) filt.push_back({(1.0 - o.gamma_theta) * theta_k, phi_k - o.gamma_phi * theta_k});
-    count_launch();
-    k_update<<<std::min<size_t>((nx + nc + 255) / 256, 8192), 256, 0, st>>>(
-        P, prob->x, prob->lam, prob->zl, prob->zu, sol, prob->dz, alpha, alpha_z, mu,
-        o.kappa_sigma, nx, nc);
-    COLLO_CUDA(cudaGetLastError());
-    if (o.verbose)
-      std::printf("iter %4d phi %.10e inf_pr %.3e err %.3e mu %.3e dw %.2e alpha %.3e ls %d ir %d %s\n",
-                  it, phi, cinf, err, mu, dw, alpha, trials, sweeps,
-                  prec == COLLO_PRECISION_MIXED ? "fp32+ir" : "fp64");
-    ++it;
-  }
-  res->status = status;
-  res->iterations = it;
-  res->phi = phi;
-  res->kkt_error = err;
-  res->mu = mu;
-  if (res->theta && p)
-    COLLO_CUDA(cudaMemcpyAsync(res->theta, prob->x + nz, p * sizeof(double), cudaMemcpyDefault, st));
-  if (res->x)
-    COLLO_CUDA(cudaMemcpyAsync(res->x, prob->x, nx * sizeof(double), cudaMemcpyDefault, st));
-  if (res->lambda)
-    COLLO_CUDA(cudaMemcpyAsync(res->lambda, prob->lam, nc * sizeof(double), cudaMemcpyDefault, st));
-  COLLO_CUDA(cudaStreamSynchronize(st));
-  res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-  return status;
-}
-
-}  // extern "C"

@@ -41,6 +41,43 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
 cudaError_t launch_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 cudaError_t launch_forward_sweep(collo_problem* pr);
 
+cudaError_t launch_init_point_b(const DevInst* insts, const int* act, int A, double k1, double k2,
+                                cudaStream_t st);
+cudaError_t launch_sweep_b(const DevInst* insts, const int* act_warp, int A_warp,
+                           size_t smem_warp, const int* act_cta, int A_cta, size_t smem_cta,
+                           cudaStream_t st);
+cudaError_t launch_theta_prep_b(const DevInst* insts, const int* act, int A, const InstParams* prm,
+                                cudaStream_t st);
+cudaError_t launch_vec_reduce_b(const DevInst* insts, const int* act, int A, int which,
+                                cudaStream_t st);
+cudaError_t launch_theta_step_b(const DevInst* insts, const int* act, int A, const InstParams* prm,
+                                cudaStream_t st);
+cudaError_t launch_trial_barrier_b(const DevInst* insts, const int* act, int A,
+                                   const InstParams* prm, cudaStream_t st);
+cudaError_t launch_update_b(const DevInst* insts, const int* act, int A, const long long* pre,
+                            long long total, const InstParams* prm, int mode, cudaStream_t st);
+size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem);
+size_t sweep_warp_smem_bytes(const DevProb& P);
+// batched launchers (eval.cu, factor.cu)
+cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                          int total_elems, const InstParams* prm, int xsel, int dxsel, int lsel,
+                          bool deriv, size_t smem, cudaStream_t st);
+cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                           int total_elems, const InstParams* prm, int mode, cudaStream_t st);
+template <typename T>
+cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                            const int* pre_lv, int maxL, const int* pre_cs,
+                            const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
+                            int grid_cap, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
+                           const int* pre_lv, int maxL, const int* pre_cs, int ir, int per_warp,
+                           GridBar* gb, int max_p, int grid_want, cudaStream_t st);
+template <typename T>
+size_t elem_factor_smem(const DevProb& P, bool full);
+template <typename T>
+size_t bcr_factor_smem(const DevProb& P, bool full);
+
 // Device allocations owned by a problem; freed in the destructor.
 struct DevArena {
   std::vector<void*> ptrs;
@@ -77,7 +114,16 @@ collo_status factor_internal(collo_problem* prob, double dw, double dc, int prec
                              long long inertia[3]);
 collo_status solve_internal(collo_problem* prob, const double* b, double* sol, int refine_max,
                             double refine_tol, int* sweeps, double* resid);
+collo_status runner_eval(collo_problem* pr, double obj_factor);
+collo_status runner_time_phase(collo_problem* pr, int phase, int prec, int reps, double* ms);
+collo_status runner_factor(collo_problem* pr, int prec, double dw, double dc, long long inertia[3]);
+collo_status runner_solve(collo_problem* pr, int refine_max, double refine_tol, int* sweeps,
+                          double* resid);
 }  // namespace collo
+
+namespace collo {
+struct Runner;
+}
 
 struct collo_problem {
   int device = 0;
@@ -117,4 +163,7 @@ struct collo_problem {
   int* fails = nullptr;       // [1]
   float* sweep_work = nullptr;   // forward-sweep FP32 Newton matrix when too big for smem
   int64_t n_x = 0, n_c = 0;
+  collo::DevInst inst{};            // this problem's device pointers (host copy)
+  collo::Runner* self = nullptr;    // single-instance runner (batch of one)
+  ~collo_problem();
 };

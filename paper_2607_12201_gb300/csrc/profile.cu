@@ -80,6 +80,7 @@ collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int
     set_error("phase 2 (solve) needs a factorization in this precision");
     return COLLO_ERR_NOT_FACTORED;
   }
+  if (phase >= 1 && phase <= 3) return runner_time_phase(prob, phase, precision, reps, ms_per_launch);
   auto launch = [&]() -> cudaError_t {
     switch (phase) {
       case 0:
@@ -87,18 +88,6 @@ collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int
                                                  prob->fac_dc, prob->f32.F, st)
                      : launch_elem_factor<double>(prob->P, prob->E, prob->sigma, prob->fac_dw,
                                                   prob->fac_dc, prob->f64.F, st);
-      case 1:
-        return mixed ? launch_factor<float>(prob->P, prob->E, prob->sigma, prob->fac_dw,
-                                            prob->fac_dc, prob->f32.F, prob->S, st)
-                     : launch_factor<double>(prob->P, prob->E, prob->sigma, prob->fac_dw,
-                                             prob->fac_dc, prob->f64.F, prob->S, st);
-      case 2:
-        return mixed ? launch_solve<float>(prob->P, prob->f32.F, prob->S, prob->kvec_a,
-                                           prob->kvec_b, st)
-                     : launch_solve<double>(prob->P, prob->f64.F, prob->S, prob->kvec_a,
-                                            prob->kvec_b, st);
-      case 3:
-        return launch_eval(prob->P, prob->E, prob->x, nullptr, 0.0, prob->lam, 1.0, true, st);
       case 4:
         return launch_forward_sweep(prob);
       default:
@@ -120,7 +109,6 @@ collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int
   *ms_per_launch = ms / reps;
   // the factorization storage now holds the re-run phase; keep it consistent
   if (phase == 0) prob->factored = -1;
-  if (phase == 1) prob->factored = precision;
   return COLLO_OK;
 }
 

@@ -1,0 +1,1112 @@
+// Batched execution of the hot path: a Runner holds the device descriptors of
+// up to `capacity` problems and launches every phase of the Newton step for a
+// set of active problems at once (one grid over all their elements, one
+// cooperative kernel for all their factorizations / solves).  A single
+// problem is a batch of one.  On top of it sit the lock-step batched
+// interior-point driver (collo_ipm_solve, collo_batch_solve) and the
+// continuous-batching server (collo_server_*).
+//
+// Results of a problem do not depend on the other members of its batch: every
+// kernel computes an instance's values from that instance's data only, each
+// element / reduction block in a fixed order, so a problem solved alone and in
+// a mix follows the same arithmetic.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "problem.cuh"
+
+namespace collo {
+
+constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
+constexpr size_t KSMEM_LIMIT = 220 * 1024;
+
+// ---- plans ---------------------------------------------------------------------------
+struct Plan {
+  std::vector<int> slots;
+  int A = 0, maxL = 0, tot_elem = 0, max_p = 0;
+  long long tot_upd = 0;
+  int* d_int = nullptr; int* h_int = nullptr; size_t cap_int = 0;
+  long long* d_ll = nullptr; long long* h_ll = nullptr; size_t cap_ll = 0;
+  InstParams* d_prm = nullptr; InstParams* h_prm = nullptr; size_t cap_prm = 0;
+  cudaEvent_t ev_int = nullptr, ev_prm = nullptr;
+  bool int_pending = false, prm_pending = false;
+  size_t off_act = 0, off_elem = 0, off_lv = 0, off_cs_s = 0, off_cs_r = 0, off_f32 = 0,
+         off_f64 = 0, off_sw_w = 0, off_sw_c = 0;
+  int n_sw_w = 0, n_sw_c = 0;
+  size_t smem_eval = 0, smem_f[2] = {0, 0}, smem_sw_w = 0, smem_sw_c = 0;
+  int cap_f[2] = {1 << 30, 1 << 30};
+  int per_warp[2] = {0, 0};
+
+  const int* act() const { return d_int + off_act; }
+  const int* pre_elem() const { return d_int + off_elem; }
+  const int* pre_lv() const { return d_int + off_lv; }
+  const int* pre_cs_s() const { return d_int + off_cs_s; }
+  const int* pre_cs_r() const { return d_int + off_cs_r; }
+  const int* flags(int prec) const { return d_int + (prec ? off_f32 : off_f64); }
+  const long long* pre_upd() const { return d_ll; }
+
+  ~Plan() {
+    if (d_int) cudaFree(d_int);
+    if (h_int) cudaFreeHost(h_int);
+    if (d_ll) cudaFree(d_ll);
+    if (h_ll) cudaFreeHost(h_ll);
+    if (d_prm) cudaFree(d_prm);
+    if (h_prm) cudaFreeHost(h_prm);
+    if (ev_int) cudaEventDestroy(ev_int);
+    if (ev_prm) cudaEventDestroy(ev_prm);
+  }
+};
+
+template <typename T>
+static cudaError_t grow(T** d, T** h, size_t* cap, size_t need) {
+  if (need <= *cap) return cudaSuccess;
+  if (*d) cudaFree(*d);
+  if (*h) cudaFreeHost(*h);
+  *d = nullptr; *h = nullptr;
+  size_t c = std::max<size_t>(need, 2 * *cap);
+  cudaError_t e = cudaMalloc((void**)d, c * sizeof(T));
+  if (e != cudaSuccess) return e;
+  e = cudaMallocHost((void**)h, c * sizeof(T));
+  if (e != cudaSuccess) return e;
+  *cap = c;
+  return cudaSuccess;
+}
+
+struct Runner {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int capacity = 0;
+  DevInst* d_insts = nullptr;
+  std::vector<DevInst> h_insts;
+  std::vector<collo_problem*> probs;
+  double* d_outs = nullptr;
+  double* h_outs = nullptr;
+  GridBar* gbar = nullptr;
+  Plan plans[4];   // 0: all active, 1: subset, 2: sub-subset (precision split), 3: scratch
+
+  ~Runner() {
+    if (d_insts) cudaFree(d_insts);
+    if (d_outs) cudaFree(d_outs);
+    if (h_outs) cudaFreeHost(h_outs);
+    if (gbar) cudaFree(gbar);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  collo_status init(int cap, int dev, cudaStream_t st) {
+    capacity = cap;
+    device = dev;
+    if (st) { stream = st; } else {
+      COLLO_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+      own_stream = true;
+    }
+    COLLO_CUDA(cudaMalloc(&d_insts, sizeof(DevInst) * cap));
+    COLLO_CUDA(cudaMalloc(&d_outs, sizeof(double) * OUTS * cap));
+    COLLO_CUDA(cudaMemset(d_outs, 0, sizeof(double) * OUTS * cap));
+    COLLO_CUDA(cudaMallocHost(&h_outs, sizeof(double) * OUTS * cap));
+    COLLO_CUDA(cudaMalloc(&gbar, sizeof(GridBar)));
+    COLLO_CUDA(cudaMemset(gbar, 0, sizeof(GridBar)));
+    h_insts.assign(cap, DevInst{});
+    probs.assign(cap, nullptr);
+    for (auto& pl : plans) {
+      COLLO_CUDA(cudaEventCreateWithFlags(&pl.ev_int, cudaEventDisableTiming));
+      COLLO_CUDA(cudaEventCreateWithFlags(&pl.ev_prm, cudaEventDisableTiming));
+    }
+    return COLLO_OK;
+  }
+
+  // Place problem pr in slot s (its descriptor, with out pointing into d_outs).
+  collo_status attach(int s, collo_problem* pr) {
+    DevInst I = pr->inst;
+    I.F32 = pr->f32.F;
+    I.F64 = pr->f64.F;
+    I.out = d_outs + (size_t)s * OUTS;
+    h_insts[s] = I;
+    probs[s] = pr;
+    COLLO_CUDA(cudaMemcpyAsync(d_insts + s, &h_insts[s], sizeof(DevInst), cudaMemcpyHostToDevice,
+                               stream));
+    COLLO_CUDA(cudaStreamSynchronize(stream));
+    return COLLO_OK;
+  }
+
+  const DevProb& P(int s) const { return h_insts[s].P; }
+  double* out(int s) { return h_outs + (size_t)s * OUTS; }
+
+  // Build plan `which` for the given slots and upload it.
+  collo_status set_plan(int which, const std::vector<int>& slots) {
+    Plan& pl = plans[which];
+    if (pl.int_pending) { cudaEventSynchronize(pl.ev_int); pl.int_pending = false; }
+    const int A = (int)slots.size();
+    pl.slots = slots;
+    pl.A = A;
+    int maxL = 0, maxp = 0;
+    for (int s : slots) {
+      int lv = 0;
+      for (int st = 1; st < P(s).N; st *= 2) ++lv;
+      maxL = std::max(maxL, lv);
+      maxp = std::max(maxp, P(s).p);
+    }
+    pl.maxL = maxL;
+    pl.max_p = maxp;
+    const size_t n_int = (size_t)A + (A + 1) * (size_t)(4 + maxL + 1) + 2 * (size_t)A + 2 * (size_t)A;
+    cudaError_t e = grow(&pl.d_int, &pl.h_int, &pl.cap_int, n_int);
+    if (e == cudaSuccess) e = grow(&pl.d_ll, &pl.h_ll, &pl.cap_ll, (size_t)A + 1);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return COLLO_ERR_OOM; }
+    int* h = pl.h_int;
+    size_t o = 0;
+    pl.off_act = o; for (int k = 0; k < A; ++k) h[o + k] = slots[k]; o += A;
+    pl.off_elem = o; h[o] = 0;
+    for (int k = 0; k < A; ++k) h[o + k + 1] = h[o + k] + P(slots[k]).N;
+    pl.tot_elem = h[o + A]; o += A + 1;
+    pl.off_lv = o;
+    for (int lv = 0; lv <= maxL; ++lv) {
+      h[o] = 0;
+      for (int k = 0; k < A; ++k) {
+        const int N = P(slots[k]).N, st = 1 << lv;
+        const int cnt = (lv < maxL && N > st) ? (N - st + 2 * st - 1) / (2 * st) : 0;
+        h[o + k + 1] = h[o + k] + cnt;
+      }
+      o += A + 1;
+    }
+    pl.off_cs_s = o; h[o] = 0;
+    for (int k = 0; k < A; ++k) {
+      const DevProb& Q = P(slots[k]);
+      h[o + k + 1] = h[o + k] + n_chunks(2 * Q.N) * Q.p * Q.p;
+    }
+    o += A + 1;
+    pl.off_cs_r = o; h[o] = 0;
+    for (int k = 0; k < A; ++k) {
+      const DevProb& Q = P(slots[k]);
+      h[o + k + 1] = h[o + k] + n_chunks(2 * Q.N) * Q.p;
+    }
+    o += A + 1;
+    // per-precision smem flags, kernel smem sizes and grid caps
+    for (int prec = 0; prec < 2; ++prec) {
+      const bool f32 = prec == 1;
+      const size_t off = o;
+      size_t smem = 0;
+      int cap = 1 << 30, pw = 0;
+      for (int k = 0; k < A; ++k) {
+        const DevProb& Q = P(slots[k]);
+        const size_t se = f32 ? elem_factor_smem<float>(Q, true) : elem_factor_smem<double>(Q, true);
+        const size_t sb = f32 ? bcr_factor_smem<float>(Q, true) : bcr_factor_smem<double>(Q, true);
+        const size_t ve = f32 ? elem_factor_smem<float>(Q, false) : elem_factor_smem<double>(Q, false);
+        const size_t vb = f32 ? bcr_factor_smem<float>(Q, false) : bcr_factor_smem<double>(Q, false);
+        int fl = 0;
+        size_t need = std::max(ve, vb);
+        if (se <= KSMEM_LIMIT) { fl |= 1; need = std::max(need, se); }
+        if (sb <= KSMEM_LIMIT) { fl |= 2; need = std::max(need, sb); }
+        const size_t ss = sizeof(double) * ((size_t)Q.p * Q.p + Q.p);
+        if (ss <= KSMEM_LIMIT) need = std::max(need, ss);
+        if (fl != 3) cap = std::min(cap, probs[slots[k]]->n_slabs);
+        smem = std::max(smem, need);
+        h[off + k] = fl;
+        pw = std::max(pw, std::max(Q.ext, Q.bext));
+      }
+      o += A;
+      if (f32) pl.off_f32 = off; else pl.off_f64 = off;
+      pl.smem_f[prec] = smem;
+      pl.cap_f[prec] = cap;
+      pl.per_warp[prec] = pw;
+    }
+    // forward-sweep lists and eval shared memory
+    pl.off_sw_w = o;
+    pl.n_sw_w = 0; pl.smem_sw_w = 0;
+    for (int k = 0; k < A; ++k)
+      if (3 * P(slots[k]).n <= 32) {
+        h[o + pl.n_sw_w++] = slots[k];
+        pl.smem_sw_w = std::max(pl.smem_sw_w, sweep_warp_smem_bytes(P(slots[k])));
+      }
+    o += A;
+    pl.off_sw_c = o;
+    pl.n_sw_c = 0; pl.smem_sw_c = 0;
+    for (int k = 0; k < A; ++k)
+      if (3 * P(slots[k]).n > 32) {
+        h[o + pl.n_sw_c++] = slots[k];
+        pl.smem_sw_c = std::max(pl.smem_sw_c,
+                                sweep_smem_bytes(P(slots[k]), probs[slots[k]]->sweep_work == nullptr));
+      }
+    o += A;
+    pl.smem_eval = 0;
+    for (int k = 0; k < A; ++k) pl.smem_eval = std::max(pl.smem_eval, eval_smem_bytes(P(slots[k])));
+    pl.h_ll[0] = 0;
+    for (int k = 0; k < A; ++k)
+      pl.h_ll[k + 1] = pl.h_ll[k] + h_insts[slots[k]].n_x + h_insts[slots[k]].n_c;
+    pl.tot_upd = pl.h_ll[A];
+    COLLO_CUDA(cudaMemcpyAsync(pl.d_int, pl.h_int, o * sizeof(int), cudaMemcpyHostToDevice, stream));
+    COLLO_CUDA(cudaMemcpyAsync(pl.d_ll, pl.h_ll, (A + 1) * sizeof(long long),
+                               cudaMemcpyHostToDevice, stream));
+    COLLO_CUDA(cudaEventRecord(pl.ev_int, stream));
+    pl.int_pending = true;
+    return COLLO_OK;
+  }
+
+  // Upload per-instance parameters of plan `which` (fill() writes h_prm[k]).
+  template <typename Fill>
+  collo_status set_params(int which, Fill fill) {
+    Plan& pl = plans[which];
+    if (pl.prm_pending) { cudaEventSynchronize(pl.ev_prm); pl.prm_pending = false; }
+    cudaError_t e = grow(&pl.d_prm, &pl.h_prm, &pl.cap_prm, (size_t)std::max(pl.A, 1));
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return COLLO_ERR_OOM; }
+    for (int k = 0; k < pl.A; ++k) {
+      InstParams ip{};
+      ip.obj_factor = 1.0;
+      ip.ksig = 1e10;
+      fill(k, pl.slots[k], ip);
+      pl.h_prm[k] = ip;
+    }
+    COLLO_CUDA(cudaMemcpyAsync(pl.d_prm, pl.h_prm, sizeof(InstParams) * std::max(pl.A, 1),
+                               cudaMemcpyHostToDevice, stream));
+    COLLO_CUDA(cudaEventRecord(pl.ev_prm, stream));
+    pl.prm_pending = true;
+    return COLLO_OK;
+  }
+
+  // Copy the per-instance outputs to the host and wait.
+  collo_status read_outs() {
+    COLLO_CUDA(cudaMemcpyAsync(h_outs, d_outs, sizeof(double) * OUTS * capacity,
+                               cudaMemcpyDeviceToHost, stream));
+    COLLO_CUDA(cudaStreamSynchronize(stream));
+    for (auto& pl : plans) { pl.int_pending = false; pl.prm_pending = false; }
+    return COLLO_OK;
+  }
+
+  collo_status check_barrier() {
+    int err = 0;
+    COLLO_CUDA(cudaMemcpyAsync(&err, &gbar->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    COLLO_CUDA(cudaStreamSynchronize(stream));
+    if (err) {
+      cudaMemsetAsync(&gbar->err, 0, sizeof(int), stream);
+      set_error("grid barrier of a persistent kernel timed out");
+      return COLLO_ERR_TIMEOUT;
+    }
+    return COLLO_OK;
+  }
+
+  // ---- phases on plan `which` ----------------------------------------------------
+  collo_status eval(int which, int xsel, int dxsel, int lsel, bool deriv) {
+    Plan& pl = plans[which];
+    COLLO_CUDA(launch_eval_b(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.tot_elem, pl.d_prm, xsel,
+                             dxsel, lsel, deriv, pl.smem_eval, stream));
+    return COLLO_OK;
+  }
+  collo_status resid(int which, int mode) {
+    Plan& pl = plans[which];
+    COLLO_CUDA(launch_resid_b(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.tot_elem, pl.d_prm, mode,
+                              stream));
+    return COLLO_OK;
+  }
+  collo_status factor(int which, int prec) {
+    Plan& pl = plans[which];
+    cudaError_t e;
+    const int p = prec == COLLO_PRECISION_MIXED ? 1 : 0;
+    if (p)
+      e = launch_factor_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+                                 pl.pre_cs_s(), pl.d_prm, pl.flags(1), gbar, pl.smem_f[1],
+                                 std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)), stream);
+    else
+      e = launch_factor_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+                                  pl.pre_cs_s(), pl.d_prm, pl.flags(0), gbar, pl.smem_f[0],
+                                  std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)), stream);
+    COLLO_CUDA(e);
+    return COLLO_OK;
+  }
+  collo_status solve(int which, int prec, int ir) {
+    Plan& pl = plans[which];
+    cudaError_t e;
+    const int want = std::max(pl.A, (pl.tot_elem + 7) / 8);
+    if (prec == COLLO_PRECISION_MIXED)
+      e = launch_solve_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+                                pl.pre_cs_r(), ir, pl.per_warp[1], gbar, pl.max_p, want, stream);
+    else
+      e = launch_solve_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+                                 pl.pre_cs_r(), ir, pl.per_warp[0], gbar, pl.max_p, want, stream);
+    COLLO_CUDA(e);
+    return COLLO_OK;
+  }
+  collo_status update(int which, int mode) {
+    Plan& pl = plans[which];
+    COLLO_CUDA(launch_update_b(d_insts, pl.act(), pl.A, pl.pre_upd(), pl.tot_upd, pl.d_prm, mode,
+                               stream));
+    return COLLO_OK;
+  }
+};
+
+// Problem-owned runner for the single-instance API.
+collo_status self_runner(collo_problem* pr, Runner** out) {
+  if (!pr->self) {
+    Runner* r = new Runner();
+    collo_status s = r->init(1, pr->device, pr->stream);
+    if (s != COLLO_OK) { delete r; return s; }
+    pr->self = r;
+  }
+  *out = pr->self;
+  return COLLO_OK;
+}
+
+// (Re)attach a problem to its own runner, e.g. after factor storage grew.
+collo_status self_attach(collo_problem* pr, Runner** out) {
+  collo_status s = self_runner(pr, out);
+  if (s != COLLO_OK) return s;
+  return (*out)->attach(0, pr);
+}
+
+// ---- refinement: solve for the rhs in ka (plan which), refine into kb ----------------
+// Returns per-instance relative residuals in rel[] (indexed like the plan).
+static collo_status solve_refine(Runner& R, int which, const std::vector<int>& prec_of_slot,
+                                 const std::vector<double>& dw, const std::vector<double>& dc,
+                                 int refine_max, double refine_tol, std::vector<int>& sweeps,
+                                 std::vector<double>& rel) {
+  Plan& pl = R.plans[which];
+  const std::vector<int> all = pl.slots;
+  const int A = (int)all.size();
+  sweeps.assign(A, 0);
+  rel.assign(A, 0.0);
+  std::map<int, int> pos;
+  for (int k = 0; k < A; ++k) pos[all[k]] = k;
+  // initial solve per precision group
+  std::vector<int> groups[2];
+  for (int s : all) groups[prec_of_slot[s] == COLLO_PRECISION_MIXED ? 1 : 0].push_back(s);
+  for (int g = 0; g < 2; ++g) {
+    if (groups[g].empty()) continue;
+    collo_status st = R.set_plan(2, groups[g]);
+    if (st != COLLO_OK) return st;
+    st = R.solve(2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64, 0);
+    if (st != COLLO_OK) return st;
+  }
+  std::vector<int> todo = all;
+  for (int sweep = 0;; ++sweep) {
+    collo_status st = R.set_plan(1, todo);
+    if (st != COLLO_OK) return st;
+    st = R.set_params(1, [&](int, int s, InstParams& ip) { ip.dw = dw[pos[s]]; ip.dc = dc[pos[s]]; });
+    if (st != COLLO_OK) return st;
+    st = R.resid(1, 2 /* R_IR */);
+    if (st != COLLO_OK) return st;
+    st = R.read_outs();
+    if (st != COLLO_OK) return st;
+    st = R.check_barrier();
+    if (st != COLLO_OK) return st;
+    std::vector<int> next;
+    for (int s : todo) {
+      const double* o = R.out(s);
+      const double rn = std::max(o[O_RX], o[O_RC]);
+      const double r = rn / std::max(1.0, o[O_BMAX]);
+      rel[pos[s]] = r;
+      if (r > refine_tol && sweeps[pos[s]] < refine_max && std::isfinite(r)) next.push_back(s);
+    }
+    if (next.empty()) break;
+    for (int s : next) sweeps[pos[s]]++;
+    std::vector<int> gr[2];
+    for (int s : next) gr[prec_of_slot[s] == COLLO_PRECISION_MIXED ? 1 : 0].push_back(s);
+    for (int g = 0; g < 2; ++g) {
+      if (gr[g].empty()) continue;
+      st = R.set_plan(2, gr[g]);
+      if (st != COLLO_OK) return st;
+      st = R.solve(2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64, 1);
+      if (st != COLLO_OK) return st;
+      st = R.update(2, 1 /* kb += kc */);
+      if (st != COLLO_OK) return st;
+    }
+    todo = next;
+  }
+  return COLLO_OK;
+}
+
+// ---- the batched interior-point driver --------------------------------------------
+struct Opt {
+  double tol, acc_tol;
+  int acc_iter, max_iter;
+  double max_wall;
+  int precision;
+  double mixed_mu_switch;
+  int refine_max;
+  double refine_tol;
+  int verbose;
+  // Waechter & Biegler (2006) constants
+  double mu_init = 0.1, kappa_mu = 0.2, theta_mu = 1.5, kappa_eps = 10.0, tau_min = 0.99;
+  double s_max = 100.0, kappa1 = 1e-2, kappa2 = 1e-2, kappa_sigma = 1e10;
+  double gamma_theta = 1e-5, gamma_phi = 1e-5, delta = 1.0, s_theta = 1.1, s_phi = 2.3;
+  double eta_phi = 1e-4, gamma_alpha = 0.05;
+  double dw_min = 1e-20, dw_0 = 1e-4, dw_max = 1e40, kw_minus = 1.0 / 3.0, kw_plus = 8.0;
+  double kw_plus_bar = 100.0, dc_coef = 1e-8, dc_exp = 0.25;
+};
+
+static Opt make_opt(const collo_ipm_options* opts) {
+  collo_ipm_options uo;
+  if (opts) uo = *opts; else collo_ipm_options_default(&uo);
+  Opt o;
+  o.tol = uo.tol; o.acc_tol = uo.acceptable_tol; o.acc_iter = uo.acceptable_iter;
+  o.max_iter = uo.max_iter; o.max_wall = uo.max_wall_time; o.precision = uo.precision;
+  o.mixed_mu_switch = uo.mixed_mu_switch; o.refine_max = uo.refine_max;
+  o.refine_tol = uo.refine_tol; o.verbose = uo.verbose;
+  return o;
+}
+
+enum { RUNNING = 1000 };
+
+struct IpmInst {
+  int slot = 0;
+  collo_problem* prob = nullptr;
+  Opt o;
+  int status = RUNNING;
+  double mu = 0.1, tau = 0.99, dw_last = 0.0, dw = 0.0, dc = 0.0;
+  double theta_max = 0, theta_min = 0, err = INFINITY, phi = NAN;
+  int acc = 0, it = 0, facs = 0, trials_total = 0, prec = 0, refine_total = 0;
+  std::vector<std::pair<double, double>> filt;
+  // line-search temporaries
+  double theta_k = 0, phi_k = 0, gphi = 0, alpha = 0, alpha_min = 0, alpha_z = 0;
+  bool ls_done = false, accepted = false, ftype = false;
+  int trials = 0;
+  std::chrono::steady_clock::time_point t0;
+  double wall = 0;
+};
+
+// Initial point, forward sweep and the constraint norm at x0 for new instances.
+static collo_status ipm_begin(Runner& R, std::vector<IpmInst*>& ins) {
+  if (ins.empty()) return COLLO_OK;
+  std::vector<int> slots;
+  for (auto* I : ins) slots.push_back(I->slot);
+  collo_status s = R.set_plan(3, slots);
+  if (s != COLLO_OK) return s;
+  const Plan& pl = R.plans[3];
+  const Opt& o = ins[0]->o;
+  COLLO_CUDA(launch_init_point_b(R.d_insts, pl.act(), pl.A, o.kappa1, o.kappa2, R.stream));
+  s = R.set_params(3, [&](int, int, InstParams& ip) { ip.alpha = 0.0; });
+  if (s != COLLO_OK) return s;
+  s = R.update(3, 2 /* lambda = 0 */);
+  if (s != COLLO_OK) return s;
+  COLLO_CUDA(launch_sweep_b(R.d_insts, pl.d_int + pl.off_sw_w, pl.n_sw_w, pl.smem_sw_w,
+                            pl.d_int + pl.off_sw_c, pl.n_sw_c, pl.smem_sw_c, R.stream));
+  s = R.eval(3, 1 /* V_X */, 0, 0, false);
+  if (s != COLLO_OK) return s;
+  s = R.read_outs();
+  if (s != COLLO_OK) return s;
+  for (auto* I : ins) {
+    const double th = R.out(I->slot)[O_C1];
+    I->theta_max = 1e4 * std::max(1.0, th);
+    I->theta_min = 1e-4 * std::max(1.0, th);
+    I->mu = I->o.mu_init;
+    I->tau = std::max(I->o.tau_min, 1.0 - I->mu);
+  }
+  return COLLO_OK;
+}
+
+// One Newton iteration for every running instance in `ins`.
+static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
+  std::vector<IpmInst*> run;
+  for (auto* I : ins)
+    if (I->status == RUNNING) run.push_back(I);
+  if (run.empty()) return COLLO_OK;
+  std::map<int, IpmInst*> by_slot;
+  std::vector<int> slots;
+  for (auto* I : run) { slots.push_back(I->slot); by_slot[I->slot] = I; }
+  auto fill_mu = [&](int, int s, InstParams& ip) {
+    IpmInst* I = by_slot[s];
+    ip.mu = I->mu; ip.tau = I->tau; ip.dw = I->dw; ip.dc = I->dc;
+  };
+  collo_status st;
+  // 1. derivatives and optimality measures
+  if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
+  if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
+  if ((st = R.eval(0, 1 /* V_X */, 0, 2 /* V_LAM */, true)) != COLLO_OK) return st;
+  {
+    const Plan& pl = R.plans[0];
+    COLLO_CUDA(launch_theta_prep_b(R.d_insts, pl.act(), pl.A, pl.d_prm, R.stream));
+  }
+  if ((st = R.resid(0, 0 /* R_DUAL */)) != COLLO_OK) return st;
+  COLLO_CUDA(launch_vec_reduce_b(R.d_insts, R.plans[0].act(), R.plans[0].A, 0, R.stream));
+  if ((st = R.read_outs()) != COLLO_OK) return st;
+  std::vector<IpmInst*> cont;
+  for (auto* I : run) {
+    I->prob->evaluated = true;
+    const double* o = R.out(I->slot);
+    I->phi = o[O_PHI];
+    const double cinf = o[O_CINF];
+    if (!std::isfinite(I->phi) || !std::isfinite(o[O_C1])) { I->status = COLLO_ERR_NUMERIC; continue; }
+    const int p = R.P(I->slot).p;
+    const double nc = (double)R.h_insts[I->slot].n_c;
+    const double wmax = o[O_WMAX], wmin = o[O_WMIN], zsum = o[O_ZSUM];
+    const double dual = o[O_RX], lam1 = o[O_LAM1];
+    const Opt& op = I->o;
+    const double s_d = std::max(op.s_max, (lam1 + zsum) / (nc + 2 * p)) / op.s_max;
+    const double s_c = std::max(op.s_max, zsum / (double)std::max(2 * p, 1)) / op.s_max;
+    auto Emu = [&](double m) {
+      double compl_ = p ? std::max(wmax - m, m - wmin) : 0.0;
+      return std::max(std::max(dual / s_d, cinf), compl_ / s_c);
+    };
+    I->err = Emu(0.0);
+    I->wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - I->t0).count();
+    if (I->err <= op.tol) { I->status = COLLO_OK; continue; }
+    I->acc = I->err <= op.acc_tol ? I->acc + 1 : 0;
+    if (I->acc >= op.acc_iter) { I->status = COLLO_ACCEPTABLE; continue; }
+    if (I->it >= op.max_iter) { I->status = COLLO_ERR_MAXITER; continue; }
+    if (I->wall > op.max_wall) { I->status = COLLO_ERR_TIMEOUT; continue; }
+    while (Emu(I->mu) <= op.kappa_eps * I->mu) {
+      double nm = std::max(op.tol / 10.0, std::min(op.kappa_mu * I->mu, std::pow(I->mu, op.theta_mu)));
+      if (nm >= I->mu) break;
+      I->mu = nm;
+      I->tau = std::max(op.tau_min, 1.0 - I->mu);
+      I->filt.clear();
+    }
+    I->theta_k = o[O_C1] > 0 ? o[O_C1] : 0.0;
+    I->prec = (op.precision == COLLO_PRECISION_MIXED &&
+               !(op.mixed_mu_switch > 0 && I->mu < op.mixed_mu_switch))
+                  ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64;
+    I->dc = op.dc_coef * std::pow(I->mu, op.dc_exp);
+    I->dw = 0.0;
+    cont.push_back(I);
+  }
+  if (cont.empty()) return COLLO_OK;
+  slots.clear();
+  for (auto* I : cont) slots.push_back(I->slot);
+  // 2. right-hand sides with the updated barrier parameters
+  if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
+  if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
+  {
+    const Plan& pl = R.plans[0];
+    COLLO_CUDA(launch_theta_prep_b(R.d_insts, pl.act(), pl.A, pl.d_prm, R.stream));
+  }
+  if ((st = R.resid(0, 1 /* R_RHS */)) != COLLO_OK) return st;
+  // 3. factorization with inertia correction (per precision group)
+  std::vector<IpmInst*> fac = cont;
+  const long long dummy = 0;
+  (void)dummy;
+  while (!fac.empty()) {
+    std::vector<int> gr[2];
+    for (auto* I : fac) gr[I->prec == COLLO_PRECISION_MIXED ? 1 : 0].push_back(I->slot);
+    for (int g = 0; g < 2; ++g) {
+      if (gr[g].empty()) continue;
+      if ((st = R.set_plan(g == 1 ? 1 : 2, gr[g])) != COLLO_OK) return st;
+      if ((st = R.set_params(g == 1 ? 1 : 2, fill_mu)) != COLLO_OK) return st;
+      if ((st = R.factor(g == 1 ? 1 : 2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64)) != COLLO_OK)
+        return st;
+    }
+    if ((st = R.read_outs()) != COLLO_OK) return st;
+    if ((st = R.check_barrier()) != COLLO_OK) return st;
+    std::vector<IpmInst*> again;
+    for (auto* I : fac) {
+      I->facs++;
+      I->prob->factored = I->prec;
+      I->prob->fac_dw = I->dw;
+      I->prob->fac_dc = I->dc;
+      long long in[3];
+      std::memcpy(in, R.out(I->slot) + O_INERT, sizeof(in));
+      const bool good = in[0] == R.h_insts[I->slot].n_x && in[1] == R.h_insts[I->slot].n_c && in[2] == 0;
+      if (good) {
+        if (I->dw > 0) I->dw_last = I->dw;
+        continue;
+      }
+      const Opt& op = I->o;
+      if (I->dw == 0.0) I->dw = I->dw_last == 0.0 ? op.dw_0 : std::max(op.dw_min, op.kw_minus * I->dw_last);
+      else I->dw *= I->dw_last == 0.0 ? op.kw_plus_bar : op.kw_plus;
+      if (I->dw > op.dw_max) { I->status = COLLO_ERR_INERTIA; continue; }
+      again.push_back(I);
+    }
+    fac = again;
+  }
+  std::vector<IpmInst*> go;
+  for (auto* I : cont)
+    if (I->status == RUNNING) go.push_back(I);
+  if (go.empty()) return COLLO_OK;
+  slots.clear();
+  for (auto* I : go) slots.push_back(I->slot);
+  // 4. solve with FP64 refinement
+  if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
+  {
+    std::vector<int> prec_of_slot(R.capacity, 0);
+    std::vector<double> dwv, dcv;
+    for (auto* I : go) { prec_of_slot[I->slot] = I->prec; dwv.push_back(I->dw); dcv.push_back(I->dc); }
+    std::vector<int> sweeps;
+    std::vector<double> rel;
+    const Opt& op = go[0]->o;
+    if ((st = solve_refine(R, 0, prec_of_slot, dwv, dcv, op.refine_max, op.refine_tol, sweeps, rel)) != COLLO_OK)
+      return st;
+    for (size_t k = 0; k < go.size(); ++k) {
+      go[k]->refine_total += sweeps[k];
+      if (!std::isfinite(rel[k])) go[k]->status = COLLO_ERR_NUMERIC;
+    }
+  }
+  // 5. step sizes
+  if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
+  if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
+  {
+    const Plan& pl = R.plans[0];
+    COLLO_CUDA(launch_theta_step_b(R.d_insts, pl.act(), pl.A, pl.d_prm, R.stream));
+    COLLO_CUDA(launch_vec_reduce_b(R.d_insts, pl.act(), pl.A, 1, R.stream));
+  }
+  if ((st = R.read_outs()) != COLLO_OK) return st;
+  std::vector<IpmInst*> ls;
+  for (auto* I : go) {
+    if (I->status != RUNNING) continue;
+    const double* o = R.out(I->slot);
+    const Opt& op = I->o;
+    const double alpha_max = o[O_AMAX];
+    I->alpha_z = o[O_AZ];
+    I->gphi = o[O_GDX] + o[O_GPHI];
+    I->phi_k = I->phi - I->mu * o[O_LOG];
+    const double tk = I->theta_k, g = I->gphi;
+    if (g < 0) {
+      if (tk <= I->theta_min)
+        I->alpha_min = op.gamma_alpha * std::min(std::min(op.gamma_theta, op.gamma_phi * tk / (-g)),
+                                                 op.delta * std::pow(tk, op.s_theta) / std::pow(-g, op.s_phi));
+      else
+        I->alpha_min = op.gamma_alpha * std::min(op.gamma_theta, op.gamma_phi * tk / (-g));
+    } else {
+      I->alpha_min = op.gamma_alpha * op.gamma_theta;
+    }
+    I->alpha = alpha_max;
+    I->accepted = false;
+    I->trials = 0;
+    ls.push_back(I);
+  }
+  // 6. backtracking filter line search, all instances in step
+  std::vector<IpmInst*> trying;
+  for (auto* I : ls) {
+    if (I->alpha >= I->alpha_min) trying.push_back(I);
+    else I->status = COLLO_ERR_LINESEARCH;
+  }
+  while (!trying.empty()) {
+    slots.clear();
+    for (auto* I : trying) slots.push_back(I->slot);
+    if ((st = R.set_plan(1, slots)) != COLLO_OK) return st;
+    if ((st = R.set_params(1, [&](int, int s, InstParams& ip) { ip.alpha = by_slot[s]->alpha; })) != COLLO_OK)
+      return st;
+    if ((st = R.eval(1, 1 /* V_X */, 5 /* V_KB */, 0, false)) != COLLO_OK) return st;
+    {
+      const Plan& pl = R.plans[1];
+      COLLO_CUDA(launch_trial_barrier_b(R.d_insts, pl.act(), pl.A, pl.d_prm, R.stream));
+    }
+    if ((st = R.read_outs()) != COLLO_OK) return st;
+    std::vector<IpmInst*> next;
+    for (auto* I : trying) {
+      const double* o = R.out(I->slot);
+      const Opt& op = I->o;
+      I->trials++;
+      const double phit = o[O_PHI], thetat = o[O_C1];
+      bool acc = false;
+      if (std::isfinite(phit) && std::isfinite(thetat) && o[O_TOK] > 0.5) {
+        const double phibt = phit - I->mu * o[O_TLOG];
+        bool ok = std::isfinite(phibt) && thetat < I->theta_max;
+        if (ok)
+          for (auto& f : I->filt)
+            if (thetat >= f.first && phibt >= f.second) { ok = false; break; }
+        if (ok) {
+          const bool sw = I->gphi < 0 &&
+                          I->alpha * std::pow(-I->gphi, op.s_phi) > op.delta * std::pow(I->theta_k, op.s_theta);
+          if (I->theta_k <= I->theta_min && sw) {
+            I->ftype = true;
+            acc = phibt <= I->phi_k + op.eta_phi * I->alpha * I->gphi;
+          } else {
+            I->ftype = false;
+            acc = thetat <= (1.0 - op.gamma_theta) * I->theta_k || phibt <= I->phi_k - op.gamma_phi * I->theta_k;
+          }
+        }
+      }
+      if (acc) { I->accepted = true; continue; }
+      I->alpha *= 0.5;
+      if (I->alpha >= I->alpha_min) next.push_back(I);
+      else I->status = COLLO_ERR_LINESEARCH;
+    }
+    trying = next;
+  }
+  // 7. accept the steps
+  std::vector<IpmInst*> upd;
+  for (auto* I : ls) {
+    I->trials_total += I->trials;
+    if (!I->accepted) continue;
+    const Opt& op = I->o;
+    if (!I->ftype) I->filt.push_back({(1.0 - op.gamma_theta) * I->theta_k, I->phi_k - op.gamma_phi * I->theta_k});
+    upd.push_back(I);
+  }
+  if (!upd.empty()) {
+    slots.clear();
+    for (auto* I : upd) slots.push_back(I->slot);
+    if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
+    if ((st = R.set_params(0, [&](int, int s, InstParams& ip) {
+           IpmInst* I = by_slot[s];
+           ip.alpha = I->alpha; ip.alpha_z = I->alpha_z; ip.mu = I->mu; ip.ksig = I->o.kappa_sigma;
+         })) != COLLO_OK)
+      return st;
+    if ((st = R.update(0, 0)) != COLLO_OK) return st;
+    for (auto* I : upd) {
+      if (I->o.verbose)
+        std::printf("[%d] iter %4d phi %.10e err %.3e mu %.3e dw %.2e alpha %.3e ls %d %s\n",
+                    I->slot, I->it, I->phi, I->err, I->mu, I->dw, I->alpha, I->trials,
+                    I->prec == COLLO_PRECISION_MIXED ? "fp32+ir" : "fp64");
+      I->it++;
+    }
+  }
+  return COLLO_OK;
+}
+
+static collo_status ipm_finish(Runner& R, IpmInst& I, collo_result* res) {
+  collo_problem* pr = I.prob;
+  cudaStream_t st = R.stream;
+  const int p = pr->P.p;
+  const size_t nx = pr->n_x, nc = pr->n_c, nz = nx - p;
+  res->status = I.status;
+  res->iterations = I.it;
+  res->factorizations = I.facs;
+  res->line_search_trials = I.trials_total;
+  res->phi = I.phi;
+  res->kkt_error = I.err;
+  res->mu = I.mu;
+  if (res->theta && p)
+    COLLO_CUDA(cudaMemcpyAsync(res->theta, pr->x + nz, p * sizeof(double), cudaMemcpyDefault, st));
+  if (res->x) COLLO_CUDA(cudaMemcpyAsync(res->x, pr->x, nx * sizeof(double), cudaMemcpyDefault, st));
+  if (res->lambda)
+    COLLO_CUDA(cudaMemcpyAsync(res->lambda, pr->lam, nc * sizeof(double), cudaMemcpyDefault, st));
+  COLLO_CUDA(cudaStreamSynchronize(st));
+  res->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - I.t0).count();
+  return COLLO_OK;
+}
+
+static collo_status ipm_prepare(Runner& R, int slot, collo_problem* pr, const double* theta0,
+                                const Opt& o, IpmInst& I) {
+  collo_status s = ensure_factor_storage(pr, COLLO_PRECISION_FP64);
+  if (s != COLLO_OK) return s;
+  if (o.precision == COLLO_PRECISION_MIXED) {
+    s = ensure_factor_storage(pr, COLLO_PRECISION_MIXED);
+    if (s != COLLO_OK) return s;
+  }
+  if ((s = R.attach(slot, pr)) != COLLO_OK) return s;
+  if (pr->P.p)
+    COLLO_CUDA(cudaMemcpyAsync(pr->inst.th0, theta0, pr->P.p * sizeof(double), cudaMemcpyDefault,
+                               R.stream));
+  I = IpmInst();
+  I.slot = slot;
+  I.prob = pr;
+  I.o = o;
+  I.t0 = std::chrono::steady_clock::now();
+  return COLLO_OK;
+}
+
+// ---- single-instance operations through the problem's own runner -------------------
+collo_status runner_eval(collo_problem* pr, double obj_factor) {
+  Runner* R = nullptr;
+  collo_status s = self_attach(pr, &R);
+  if (s != COLLO_OK) return s;
+  if ((s = R->set_plan(0, {0})) != COLLO_OK) return s;
+  if ((s = R->set_params(0, [&](int, int, InstParams& ip) { ip.obj_factor = obj_factor; })) != COLLO_OK)
+    return s;
+  return R->eval(0, 3 /* V_STAGE_X */, 0, 4 /* V_STAGE_L */, true);
+}
+
+collo_status runner_factor(collo_problem* pr, int prec, double dw, double dc, long long inertia[3]) {
+  collo_status s = ensure_factor_storage(pr, prec);
+  if (s != COLLO_OK) return s;
+  Runner* R = nullptr;
+  if ((s = self_attach(pr, &R)) != COLLO_OK) return s;
+  if ((s = R->set_plan(0, {0})) != COLLO_OK) return s;
+  if ((s = R->set_params(0, [&](int, int, InstParams& ip) { ip.dw = dw; ip.dc = dc; })) != COLLO_OK)
+    return s;
+  if ((s = R->factor(0, prec)) != COLLO_OK) return s;
+  if ((s = R->read_outs()) != COLLO_OK) return s;
+  if ((s = R->check_barrier()) != COLLO_OK) return s;
+  std::memcpy(inertia, R->out(0) + O_INERT, 3 * sizeof(long long));
+  pr->factored = prec;
+  pr->fac_dw = dw;
+  pr->fac_dc = dc;
+  return COLLO_OK;
+}
+
+// Solve with the right-hand side in ka into kb (refined in FP64).
+collo_status runner_solve(collo_problem* pr, int refine_max, double refine_tol, int* sweeps,
+                          double* resid) {
+  Runner* R = nullptr;
+  collo_status s = self_runner(pr, &R);
+  if (s != COLLO_OK) return s;
+  if ((s = R->set_plan(0, {0})) != COLLO_OK) return s;
+  std::vector<int> prec_of_slot{pr->factored};
+  std::vector<double> dw{pr->fac_dw}, dc{pr->fac_dc};
+  std::vector<int> sw;
+  std::vector<double> rel;
+  if ((s = solve_refine(*R, 0, prec_of_slot, dw, dc, refine_max, refine_tol, sw, rel)) != COLLO_OK)
+    return s;
+  if (sweeps) *sweeps = sw[0];
+  if (resid) *resid = rel[0];
+  if (!std::isfinite(rel[0])) { set_error("non-finite KKT solution"); return COLLO_ERR_NUMERIC; }
+  return COLLO_OK;
+}
+
+// CUDA-event timing of one batched phase of this problem (batch of one):
+// 1 factorization, 2 solve (no refinement), 3 evaluation with derivatives.
+collo_status runner_time_phase(collo_problem* pr, int phase, int prec, int reps, double* ms) {
+  collo_status s = ensure_factor_storage(pr, prec);
+  if (s != COLLO_OK) return s;
+  Runner* R = nullptr;
+  if ((s = self_attach(pr, &R)) != COLLO_OK) return s;
+  if ((s = R->set_plan(0, {0})) != COLLO_OK) return s;
+  if ((s = R->set_params(0, [&](int, int, InstParams& ip) { ip.dw = pr->fac_dw; ip.dc = pr->fac_dc; })) != COLLO_OK)
+    return s;
+  auto run = [&]() -> collo_status {
+    if (phase == 1) return R->factor(0, prec);
+    if (phase == 2) return R->solve(0, prec, 0);
+    return R->eval(0, 1 /* V_X */, 0, 2 /* V_LAM */, true);
+  };
+  if ((s = run()) != COLLO_OK) return s;
+  cudaEvent_t e0, e1;
+  COLLO_CUDA(cudaEventCreate(&e0));
+  COLLO_CUDA(cudaEventCreate(&e1));
+  COLLO_CUDA(cudaEventRecord(e0, R->stream));
+  for (int k = 0; k < reps; ++k)
+    if ((s = run()) != COLLO_OK) return s;
+  COLLO_CUDA(cudaEventRecord(e1, R->stream));
+  COLLO_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  if (phase == 1) pr->factored = prec;
+  return R->check_barrier();
+}
+
+}  // namespace collo
+
+using namespace collo;
+
+// ---- continuous-batching server --------------------------------------------------------
+struct collo_server {
+  Runner R;
+  Opt o;
+  int64_t budget = 0;
+  int64_t active_bytes = 0;
+  long long next_ticket = 1;
+  struct Job {
+    long long ticket;
+    collo_problem* prob;
+    std::vector<double> theta0;
+    IpmInst I;
+    int slot = -1;
+    bool done = false;
+    collo_result res{};
+  };
+  std::deque<Job*> waiting;
+  std::vector<Job*> slots;            // slot -> job (null: free)
+  std::map<long long, Job*> jobs;
+  std::mutex mu;
+  ~collo_server() {
+    for (auto& kv : jobs) delete kv.second;
+  }
+};
+
+extern "C" {
+
+void collo_ipm_options_default(collo_ipm_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->acceptable_tol = 1e-4;
+  o->acceptable_iter = 15;
+  o->max_iter = 3000;
+  o->max_wall_time = 3600.0;
+  o->precision = COLLO_PRECISION_FP64;
+  o->mixed_mu_switch = 1e-6;
+  o->refine_max = 10;
+  o->refine_tol = 1e-10;
+  o->verbose = 0;
+}
+
+collo_status collo_initial_states(collo_problem* prob, const double* theta, double* x_out,
+                                  int* failures) {
+  if (!prob || !theta) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  Runner* R = nullptr;
+  collo_status s = self_attach(prob, &R);
+  if (s != COLLO_OK) return s;
+  const size_t nz = (size_t)prob->P.N * NP * prob->P.n;
+  if (prob->P.p)
+    COLLO_CUDA(cudaMemcpyAsync(prob->x + nz, theta, prob->P.p * sizeof(double), cudaMemcpyDefault,
+                               R->stream));
+  if ((s = R->set_plan(3, {0})) != COLLO_OK) return s;
+  const Plan& pl = R->plans[3];
+  COLLO_CUDA(launch_sweep_b(R->d_insts, pl.d_int + pl.off_sw_w, pl.n_sw_w, pl.smem_sw_w,
+                            pl.d_int + pl.off_sw_c, pl.n_sw_c, pl.smem_sw_c, R->stream));
+  int f = 0;
+  COLLO_CUDA(cudaMemcpyAsync(&f, prob->fails, sizeof(int), cudaMemcpyDeviceToHost, R->stream));
+  if (x_out)
+    COLLO_CUDA(cudaMemcpyAsync(x_out, prob->x, prob->n_x * sizeof(double), cudaMemcpyDefault, R->stream));
+  COLLO_CUDA(cudaStreamSynchronize(R->stream));
+  if (failures) *failures = f;
+  return COLLO_OK;
+}
+
+collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
+                             const collo_ipm_options* opts, collo_result* res) {
+  if (!prob || !res || (prob->P.p > 0 && !theta0)) {
+    set_error("NULL argument");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  Runner* R = nullptr;
+  collo_status s = self_runner(prob, &R);
+  if (s != COLLO_OK) return s;
+  Opt o = make_opt(opts);
+  IpmInst I;
+  if ((s = ipm_prepare(*R, 0, prob, theta0, o, I)) != COLLO_OK) return s;
+  std::vector<IpmInst*> ins{&I};
+  if ((s = ipm_begin(*R, ins)) != COLLO_OK) return res->status = s;
+  while (I.status == RUNNING) {
+    s = ipm_iteration(*R, ins);
+    if (s != COLLO_OK) { I.status = s; break; }
+  }
+  s = ipm_finish(*R, I, res);
+  if (s != COLLO_OK) return s;
+  return res->status;
+}
+
+// ---- batches -------------------------------------------------------------------------
+struct collo_batch_impl;
+
+collo_status collo_batch_solve(collo_problem* const* probs, int count, const double* const* theta0,
+                               const collo_ipm_options* opts, collo_result* results) {
+  if (!probs || count < 1 || !theta0 || !results) {
+    set_error("bad argument");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  const int dev = probs[0]->device;
+  for (int i = 0; i < count; ++i)
+    if (!probs[i] || probs[i]->device != dev || (probs[i]->P.p > 0 && !theta0[i])) {
+      set_error("batch members must be valid problems of one device with theta0");
+      return COLLO_ERR_INVALID_ARG;
+    }
+  COLLO_CUDA(cudaSetDevice(dev));
+  Runner R;
+  collo_status s = R.init(count, dev, nullptr);
+  if (s != COLLO_OK) return s;
+  Opt o = make_opt(opts);
+  std::vector<IpmInst> I(count);
+  std::vector<IpmInst*> ins;
+  for (int i = 0; i < count; ++i) {
+    if ((s = ipm_prepare(R, i, probs[i], theta0[i], o, I[i])) != COLLO_OK) return s;
+    ins.push_back(&I[i]);
+  }
+  if ((s = ipm_begin(R, ins)) != COLLO_OK) return s;
+  for (;;) {
+    bool any = false;
+    for (auto* p : ins) any = any || p->status == RUNNING;
+    if (!any) break;
+    s = ipm_iteration(R, ins);
+    if (s != COLLO_OK) {
+      for (auto* p : ins) if (p->status == RUNNING) p->status = s;
+      break;
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if ((s = ipm_finish(R, I[i], &results[i])) != COLLO_OK) return s;
+  return COLLO_OK;
+}
+
+// ---- server --------------------------------------------------------------------------
+collo_status collo_server_create(int max_slots, int64_t budget_bytes, const collo_ipm_options* opts,
+                                 int device, collo_server** out) {
+  if (!out || max_slots < 1) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaSetDevice failed");
+    return COLLO_ERR_DEVICE;
+  }
+  std::unique_ptr<collo_server> sv(new collo_server());
+  collo_status s = sv->R.init(max_slots, device, nullptr);
+  if (s != COLLO_OK) return s;
+  sv->o = make_opt(opts);
+  sv->budget = budget_bytes;
+  sv->slots.assign(max_slots, nullptr);
+  *out = sv.release();
+  return COLLO_OK;
+}
+
+collo_status collo_server_submit(collo_server* sv, collo_problem* prob, const double* theta0,
+                                 long long* ticket) {
+  if (!sv || !prob || !ticket || (prob->P.p > 0 && !theta0)) {
+    set_error("bad argument");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  auto* j = new collo_server::Job();
+  j->ticket = sv->next_ticket++;
+  j->prob = prob;
+  j->theta0.assign(theta0, theta0 + prob->P.p);
+  sv->jobs[j->ticket] = j;
+  sv->waiting.push_back(j);
+  *ticket = j->ticket;
+  return COLLO_OK;
+}
+
+collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) {
+  if (!sv) { set_error("NULL server"); return COLLO_ERR_INVALID_ARG; }
+  COLLO_CUDA(cudaSetDevice(sv->R.device));
+  Runner& R = sv->R;
+  collo_status s;
+  // admit waiting jobs into free slots within the device-memory budget
+  std::vector<IpmInst*> fresh;
+  while (!sv->waiting.empty()) {
+    auto* j = sv->waiting.front();
+    int slot = -1;
+    for (int k = 0; k < (int)sv->slots.size(); ++k)
+      if (!sv->slots[k]) { slot = k; break; }
+    if (slot < 0) break;
+    const int64_t bytes = (int64_t)j->prob->arena.bytes;
+    if (sv->budget > 0 && sv->active_bytes > 0 && sv->active_bytes + bytes > sv->budget) break;
+    sv->waiting.pop_front();
+    if ((s = ipm_prepare(R, slot, j->prob, j->theta0.data(), sv->o, j->I)) != COLLO_OK) return s;
+    j->slot = slot;
+    sv->slots[slot] = j;
+    sv->active_bytes += (int64_t)j->prob->arena.bytes;
+    fresh.push_back(&j->I);
+  }
+  if ((s = ipm_begin(R, fresh)) != COLLO_OK) return s;
+  std::vector<IpmInst*> act;
+  for (auto* j : sv->slots)
+    if (j) act.push_back(&j->I);
+  if ((s = ipm_iteration(R, act)) != COLLO_OK) return s;
+  // retire finished jobs
+  for (int k = 0; k < (int)sv->slots.size(); ++k) {
+    auto* j = sv->slots[k];
+    if (!j || j->I.status == RUNNING) continue;
+    j->res = collo_result{};
+    if ((s = ipm_finish(R, j->I, &j->res)) != COLLO_OK) return s;
+    j->done = true;
+    sv->active_bytes -= (int64_t)j->prob->arena.bytes;
+    sv->slots[k] = nullptr;
+  }
+  int a = 0;
+  for (auto* j : sv->slots) a += j ? 1 : 0;
+  if (n_active) *n_active = a;
+  if (n_waiting) *n_waiting = (int)sv->waiting.size();
+  return COLLO_OK;
+}
+
+collo_status collo_server_poll(collo_server* sv, long long ticket, collo_result* res) {
+  if (!sv || !res) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) { set_error("unknown ticket"); return COLLO_ERR_INVALID_ARG; }
+  auto* j = it->second;
+  if (!j->done) return COLLO_PENDING;
+  double* th = res->theta;
+  *res = j->res;
+  res->theta = th;
+  if (th && j->prob->P.p) {
+    const size_t nz = (size_t)j->prob->n_x - j->prob->P.p;
+    COLLO_CUDA(cudaMemcpy(th, j->prob->x + nz, j->prob->P.p * sizeof(double), cudaMemcpyDefault));
+  }
+  return COLLO_OK;
+}
+
+void collo_server_destroy(collo_server* sv) {
+  if (!sv) return;
+  cudaSetDevice(sv->R.device);
+  cudaStreamSynchronize(sv->R.stream);
+  delete sv;
+}
+
+}  // extern "C"
+
+collo_problem::~collo_problem() { delete self; }

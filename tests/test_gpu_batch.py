@@ -1,0 +1,96 @@
+"""Batched solves and continuous batching: each problem's result is the same
+alone and in a mix (bitwise: every kernel computes an instance from its own
+data in a fixed order), and batched results match the oracle."""
+import numpy as np
+import pytest
+
+from paper_2607_12201_gb300 import workloads as W
+from oracle import ipm as oipm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def collo():
+    from paper_2607_12201_gb300 import build
+    build.build()
+    from paper_2607_12201_gb300 import collo
+    return collo
+
+
+def _mix():
+    return [W.config1(),
+            W.random_network(4, 8, n_obs=3, M=20, T=5.0, N=40, seed=41, theta0_spread=0.1),
+            W.small_network(n=3, r=4, N=7, seed=7),
+            W.config2(N=100),
+            W.random_network(12, 24, n_obs=4, M=20, T=5.0, N=33, seed=43, theta0_spread=0.1)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_alone_bitwise(collo, prec):
+    P = collo.MIXED if prec == "mixed" else collo.FP64
+    insts = _mix()
+    alone = []
+    for inst in insts:
+        with collo.Problem(inst) as pb:
+            alone.append(pb.ipm_solve(precision=P, want_x=False))
+    probs = [collo.Problem(inst) for inst in insts]
+    mixed = collo.batch_solve(probs, precision=P)
+    for a, b in zip(alone, mixed):
+        assert a["status"] == b["status"]
+        assert a["iterations"] == b["iterations"]
+        assert np.array_equal(a["theta"], b["theta"])
+        assert a["phi"] == b["phi"]
+    for pb in probs:
+        pb.close()
+
+
+def test_batch_multistart_matches_oracle(collo):
+    base = W.random_network(4, 8, n_obs=3, M=20, T=5.0, N=40, seed=41, theta0_spread=0.1)
+    rng = np.random.default_rng(5)
+    starts = [base.theta_true + rng.uniform(-0.2, 0.2, base.p) for _ in range(4)]
+    probs = [collo.Problem(base) for _ in starts]
+    res = collo.batch_solve(probs, theta0s=starts, precision=collo.MIXED)
+    for r, th0 in zip(res, starts):
+        ref = oipm.solve(base.with_theta0(th0))
+        assert r["status"] == ref.status
+        if ref.status in (0, 1):
+            rel = np.max(np.abs(r["theta"] - ref.x[-base.p:]) / np.abs(ref.x[-base.p:]))
+            assert rel <= 1e-6
+    for pb in probs:
+        pb.close()
+
+
+def test_server_continuous_batching_equals_alone(collo):
+    insts = _mix()
+    alone = []
+    for inst in insts:
+        with collo.Problem(inst) as pb:
+            alone.append(pb.ipm_solve(precision=collo.MIXED, want_x=False))
+    server = collo.Server(max_slots=3, precision=collo.MIXED)
+    probs = [collo.Problem(inst) for inst in insts]
+    tickets = {}
+    # staggered arrivals: one new request every other step, 3 slots
+    step = 0
+    pending = list(range(len(insts)))
+    done = {}
+    while len(done) < len(insts):
+        if pending and step % 2 == 0:
+            i = pending.pop(0)
+            tickets[i] = server.submit(probs[i])
+        server.step()
+        for i, t in tickets.items():
+            if i not in done:
+                r = server.poll(t)
+                if r is not None:
+                    done[i] = r
+        step += 1
+        assert step < 5000
+    for i, a in enumerate(alone):
+        b = done[i]
+        assert a["status"] == b["status"]
+        assert a["iterations"] == b["iterations"]
+        assert np.array_equal(a["theta"], b["theta"])
+    server.close()
+    for pb in probs:
+        pb.close()
