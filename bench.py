@@ -3,24 +3,26 @@
 
 Workload: the 10-species / 20-reaction random mass-action network on
 N = 400 Radau elements (K = 3), 4 observed species x 50 times, T = 20,
-seed 3 (``workloads.config2()``): 16 020 primal unknowns, 16 000
-constraints, 20 log10 rate constants.
+seed 3 (``workloads.config2()``): 16 020 primal unknowns, 16 000 constraints,
+20 log10 rate constants, solved from B seeded starting points
+theta_true + U[-0.1, 0.1] (a multistart run, ``--batch``, default 64).
 
-A timed step is one full interior-point solve (from theta0 to convergence) in
-the mixed-precision path (FP32 element factorization and block cyclic
-reduction, FP64 parameter Schur complement, residuals and refinement).
-``value`` = Newton steps per second over the K timed solves; the plain FP64
-path, solves/s, p50/p99 solve latency, an end-to-end number through host
-buffers, the dominant kernel's roofline and the CPU oracle are reported
-beside it.  Between timed solves the L2 cache is flushed by writing a 256 MiB
-buffer (the working set is ~40 MB, smaller than L2).
+A timed step is one batched solve: all B starts advance together, one Newton
+step per iteration of the lock-step driver, every phase one launch over all
+unfinished instances, in the mixed-precision path (FP32 element
+factorization and block cyclic reduction, FP64 parameter Schur complement,
+residuals and refinement, FP64 factorization once mu < 1e-6).  ``value`` =
+Newton steps per second summed over the batch.  Beside it: the same path and
+the plain FP64 path on a single instance, per-instance latency percentiles,
+an end-to-end number through host buffers, the dominant kernel's roofline,
+the CPU oracle.  Between timed steps the L2 cache is flushed (256 MiB write).
 
-``--impl reference`` times the CPU oracle instead (a bounded sample: each
-step is the oracle's initial point plus two Newton iterations).
+``--impl reference`` times the CPU oracle instead (a bounded sample: each step
+is the oracle's initial point plus two Newton iterations of one instance).
 
-Multi-GPU (torchrun, one process per GPU): each rank solves its own copy of
-the workload with no collective on the data path (weak scaling); the timed
-region is bracketed by barriers and the slowest rank's time is used.
+Multi-GPU (torchrun, one process per GPU): each rank solves its own batch
+with no collective on the data path (weak scaling); the timed region is
+bracketed by barriers and the slowest rank's time is used.
 """
 from __future__ import annotations
 
@@ -38,20 +40,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "massaction_n10_r20_N400_K3 (config 2: 10 species, 20 reactions, N=400, T=20, seed 3)"
-METRIC = "Newton steps/s (mixed-precision IPM path, config 2)"
+WORKLOAD = ("massaction_n10_r20_N400_K3 x {B} multistart (config 2: 10 species, 20 reactions, "
+            "N=400, T=20, seed 3; starts theta_true + U[-0.1,0.1])")
+METRIC = "Newton steps/s (mixed-precision batched IPM path, config 2 multistart)"
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--only-solve", choices=["mixed", "fp64"], default=None,
-                    help="run one solve of the workload and exit (for profiler launch lists)")
+                    help="run one single-instance solve and exit (for profiler launch lists)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run one batched solve and exit (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -149,24 +155,45 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def _pair_flops(msz: int, pairs: int) -> int:
+    """Flops of eliminating `pairs` 2x2 pivots from a symmetric msz x msz block:
+    pair q updates t(t+1)/2 trailing entries with two FMAs and forms 2t
+    multipliers with four FMAs per row (t = msz - 2q - 2)."""
+    fl = 0
+    for q in range(pairs):
+        t = msz - 2 * q - 2
+        fl += 2 * t * (t + 1) + 8 * t
+    return fl
+
+
 def elem_factor_work(n: int, p: int, N: int, bytes_per: int):
     """Algorithmic flops and bytes of one element-condensation launch.
 
-    Per element: eliminating the 3n interior (state, multiplier) pairs of the
-    symmetric (8n + p) block; pair q updates the t(t+1)/2 trailing entries
-    (t = 8n + p - 2q - 2) with two FMAs each and forms 2t multipliers with four
-    FMAs per row.  Bytes: FP64 derivative blocks read (jac_z, hess_zz at
-    3 n^2, jac_theta, hess_ztheta at 3 n p, objective block 16 n doubles) and
-    the factor written (6n L columns of length 8n + p, 3n pivots, the 2n x 2n
+    Per element: eliminating the 3n interior pairs of the symmetric (8n + p)
+    block.  Bytes: FP64 derivative blocks read (jac_z, hess_zz at 3 n^2,
+    jac_theta, hess_ztheta at 3 n p, objective block 16 n doubles) and the
+    factor written (6n L columns of length 8n + p, 3n pivots, the 2n x 2n
     interface block, its 2n x p border, the p x p FP64 Schur part)."""
     ext = 8 * n + p
-    fl = 0
-    for q in range(3 * n):
-        t = ext - 2 * q - 2
-        fl += 2 * t * (t + 1) + 8 * t
+    fl = _pair_flops(ext, 3 * n)
     rd = 8 * (2 * 3 * n * n + 2 * 3 * n * p + 16 * n)
     wr = bytes_per * (6 * n * ext + 9 * n + 4 * n * n + n * n + 2 * n * p) + 8 * p * p
     return fl * N, (rd + wr) * N
+
+
+def factor_work(n: int, p: int, N: int, bytes_per: int):
+    """Algorithmic flops and bytes of one whole factorization of one instance:
+    element condensation (above), the N eliminations of the cyclic reduction
+    (n pairs of a (4n + p) block each: interface block, neighbour couplings
+    and border read, L columns written), the parameter Schur complement
+    (2N p^2 FP64 contributions summed, p^3/3 for its LDL^T)."""
+    fl_e, by_e = elem_factor_work(n, p, N, bytes_per)
+    bext = 4 * n + p
+    fl_b = _pair_flops(bext, n) * N
+    by_b = bytes_per * N * (4 * n * n + 2 * n * n + 2 * n * p + 2 * n * bext + 3 * n)
+    fl_s = p ** 3 // 3 + 2 * N * p * p
+    by_s = 8 * 2 * N * p * p
+    return fl_e + fl_b + fl_s, by_e + by_b + by_s
 
 
 def measured_peaks():
@@ -186,84 +213,95 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    dist = init_dist(world, "nccl")
+    init_dist(world, "nccl")
     inst = workloads.config2()
-    prob = collo.Problem(inst, device=local)
-    stream = torch.cuda.ExternalStream(prob.stream)
+    nb = args.batch
+    starts = workloads.multistart_thetas(inst, nb, seed=2002 + rank)
+    probs = [collo.Problem(inst, device=local) for _ in range(nb)]
+    stream = torch.cuda.ExternalStream(probs[0].stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def flush_l2(i):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
 
-    def timed_solve(prec):
+    def timed_batch(prec):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = prob.ipm_solve(precision=prec, want_x=False)
+        res = collo.batch_solve(probs, theta0s=starts, precision=prec)
         e1.record(stream)
         e1.synchronize()
-        return r, e0.elapsed_time(e1)
+        return res, e0.elapsed_time(e1)
 
     for i in range(args.warmup):
         flush_l2(i)
-        timed_solve(collo.MIXED)
+        timed_batch(collo.MIXED)
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     l0 = collo.launch_count()
-    its, ms_list, statuses, theta_mixed = [], [], [], None
+    its, ms_list, statuses, lat, last = 0, [], [], [], None
     for i in range(args.steps):
         flush_l2(i)
-        r, ms = timed_solve(collo.MIXED)
-        its.append(r["iterations"])
+        res, ms = timed_batch(collo.MIXED)
+        its += sum(r["iterations"] for r in res)
         ms_list.append(ms)
-        statuses.append(r["status"])
-        theta_mixed = r["theta"]
+        statuses += [r["status"] for r in res]
+        lat += [1e3 * r["wall"] for r in res]
+        last = res
     launches = collo.launch_count() - l0
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     t_total = reduce_max(sum(ms_list), world)
-    its_total = reduce_sum(float(sum(its)), world)
-    solves_total = reduce_sum(float(args.steps), world)
+    its_total = reduce_sum(float(its), world)
+    solves_total = reduce_sum(float(args.steps * nb), world)
     value = its_total / (t_total * 1e-3)
 
-    # plain FP64 path on the same GPU
-    k64 = max(1, min(args.steps, 5))
-    flush_l2(1)
-    timed_solve(collo.FP64)
-    ms64, its64, theta64 = [], [], None
-    for i in range(k64):
-        flush_l2(i)
-        r, ms = timed_solve(collo.FP64)
-        ms64.append(ms)
-        its64.append(r["iterations"])
-        theta64 = r["theta"]
-    fp64_value = sum(its64) / (sum(ms64) * 1e-3)
-    perr = float(np.max(np.abs(theta_mixed - theta64) / np.maximum(np.abs(theta64), 1e-12)))
+    # single-instance paths on the same GPU: mixed and the plain FP64 path
+    one = probs[0]
+    single = {}
+    for name, prec in [("mixed", collo.MIXED), ("fp64", collo.FP64)]:
+        one.ipm_solve(theta0=starts[0], precision=prec, want_x=False)
+        ms_s, its_s, th = [], 0, None
+        for i in range(3):
+            flush_l2(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = one.ipm_solve(theta0=starts[0], precision=prec, want_x=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms_s.append(e0.elapsed_time(e1))
+            its_s += r["iterations"]
+            th = r["theta"]
+        single[name] = {"newton_steps_per_s": its_s / (sum(ms_s) * 1e-3),
+                        "solves_per_s": len(ms_s) / (sum(ms_s) * 1e-3),
+                        "ms_per_solve": sum(ms_s) / len(ms_s), "theta": th}
+    # parameter error of the batched mixed path against single-instance FP64 solves
+    perr = 0.0
+    for j in range(min(4, nb)):
+        r64 = one.ipm_solve(theta0=starts[j], precision=collo.FP64, want_x=False)
+        if r64["status"] in (collo.OK, collo.ACCEPTABLE):
+            th = last[j]["theta"]
+            perr = max(perr, float(np.max(np.abs(th - r64["theta"]) /
+                                          np.maximum(np.abs(r64["theta"]), 1e-12))))
 
-    # phase timings and the dominant kernel's roofline (CUDA events on the
-    # library's stream, after a final mixed solve so its state is current)
-    timed_solve(collo.MIXED)
-    phases = {}
-    for name, ph, prec in [("eval", 3, -1), ("factor_fp32", 1, collo.MIXED),
-                           ("solve_fp32", 2, collo.MIXED), ("forward_sweep", 4, -1),
-                           ("elem_condense_fp32", 0, collo.MIXED)]:
-        phases[name] = prob.time_phase(ph, prec, reps=20)
-    timed_solve(collo.FP64)
-    for name, ph, prec in [("factor_fp64", 1, collo.FP64), ("solve_fp64", 2, collo.FP64),
-                           ("elem_condense_fp64", 0, collo.FP64)]:
-        phases[name] = prob.time_phase(ph, prec, reps=20)
-    fl32, by32 = elem_factor_work(inst.n, inst.p, inst.N, 4)
+    # dominant kernel (batched factorization) and phase timings with CUDA events
+    timed_batch(collo.MIXED)
+    ph = {"factor_fp32": collo.batch_time_phase(probs, 1, collo.MIXED, reps=5),
+          "solve_fp32": collo.batch_time_phase(probs, 2, collo.MIXED, reps=5),
+          "eval": collo.batch_time_phase(probs, 3, collo.MIXED, reps=5)}
+    fl32, by32 = factor_work(inst.n, inst.p, inst.N, 4)
+    fl32 *= nb
+    by32 *= nb
     peak32 = collo.alu_peak(collo.MIXED)
     peak64 = collo.alu_peak(collo.FP64)
     hbm = measured_peaks().get("hbm_gbs")
-    t_el = phases["elem_condense_fp32"] * 1e-3
-    ach_fl = fl32 / t_el / 1e12
-    ach_by = by32 / t_el / 1e9
-    # the roof that bounds this kernel: compare its compute and memory times at the peaks
+    t_f = ph["factor_fp32"] * 1e-3
+    ach_fl, ach_by = fl32 / t_f / 1e12, by32 / t_f / 1e9
     if hbm and by32 / (hbm * 1e9) > fl32 / (peak32 * 1e12):
         roof = {"bound": "hbm", "achieved": ach_by, "peak": hbm, "unit": "GB/s",
                 "frac": ach_by / hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
@@ -271,62 +309,64 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": ach_fl, "peak": peak32, "unit": "TFLOP/s",
                 "frac": ach_fl / peak32,
                 "peak_source": "measured live: FP32 FFMA throughput probe (collo_alu_peak)"}
-    roof.update({"kernel": "k_elem_factor<float> (element condensation)",
-                 "algorithmic_flops": fl32, "algorithmic_bytes": by32, "ms": phases["elem_condense_fp32"],
-                 "traffic": None})
-    fl64, _ = elem_factor_work(inst.n, inst.p, inst.N, 8)
-    fp64_kernel = {"kernel": "k_elem_factor<double>", "ms": phases["elem_condense_fp64"],
-                   "achieved_tflops": fl64 / (phases["elem_condense_fp64"] * 1e-3) / 1e12,
-                   "fp64_peak_tflops": peak64}
+    roof.update({"kernel": f"k_factor_b<float> (batched factorization, {nb} instances)",
+                 "algorithmic_flops": fl32, "algorithmic_bytes": by32,
+                 "ms": ph["factor_fp32"], "traffic": None,
+                 "other_roof": {"alu_tflops": ach_fl, "alu_peak_tflops": peak32,
+                                "hbm_gbs": ach_by, "hbm_peak_gbs": hbm}})
 
     out = {
         "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32 factor + fp64 residual/refinement",
-        "data": "synthetic (seeded mass-action network, noisy observations)",
-        "config": {"workload": WORKLOAD, "step": "one full IPM solve from theta0",
-                   "newton_steps_per_solve": statistics.mean(its),
-                   "n_x": prob.n_x, "n_c": prob.n_c, "p": inst.p,
-                   "l2": "flushed between timed solves (256 MiB write)",
-                   "parallelism": f"replicas x{world}"},
+        "data": "synthetic (seeded mass-action network, noisy observations, seeded starts)",
+        "config": {"workload": WORKLOAD.format(B=nb), "batch": nb,
+                   "step": f"one batched solve of {nb} starts from theta0 to convergence",
+                   "newton_steps_per_step": its / max(args.steps, 1),
+                   "n_x_per_instance": one.n_x, "n_c_per_instance": one.n_c, "p": inst.p,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (independent batches)"},
         "solves_per_s": solves_total / (t_total * 1e-3),
-        "latency_ms": {"p50": float(np.percentile(ms_list, 50)),
-                       "p99": float(np.percentile(ms_list, 99))},
-        "status": sorted(set(statuses)),
-        "fp64_path": {"newton_steps_per_s": fp64_value,
-                      "solves_per_s": k64 / (sum(ms64) * 1e-3),
-                      "ms_per_solve": sum(ms64) / k64, "solves": k64},
-        "mixed_vs_fp64_speedup": value / fp64_value,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "per-instance time from batch start to that instance's result"},
+        "status_counts": {str(s): statuses.count(s) for s in sorted(set(statuses))},
+        "single_instance": {k: {kk: vv for kk, vv in v.items() if kk != "theta"}
+                            for k, v in single.items()},
+        "speedup_vs_fp64_single": value / single["fp64"]["newton_steps_per_s"],
         "param_rel_err_vs_fp64": perr,
-        "phases_ms": phases, "roofline": roof, "fp64_elem_kernel": fp64_kernel,
+        "phases_ms": ph, "roofline": roof,
+        "peaks_tflops": {"fp32_ffma": peak32, "fp64_dfma": peak64},
         "gpu_launches": launches, "clocks": clk,
     }
     if not args.no_e2e:
-        k_e = max(1, min(args.steps, 5))
         keep = [inst.react, inst.prod, inst.pidx, inst.kfix, inst.x0, inst.theta_lo,
-                inst.theta_hi, inst.obs_t, inst.obs_s, inst.obs_y, inst.obs_sigma, inst.theta0]
-        h2d = int(sum(np.asarray(a).nbytes for a in keep))
+                inst.theta_hi, inst.obs_t, inst.obs_s, inst.obs_y, inst.obs_sigma]
+        h2d = nb * int(sum(np.asarray(a).nbytes for a in keep)) + 8 * inst.p * nb
         tot, its_e = 0.0, 0
+        k_e = max(1, min(args.steps, 3))
         for i in range(k_e):
             flush_l2(i)
             t0 = time.perf_counter()
-            with collo.Problem(inst, device=local) as p2:
-                r = p2.ipm_solve(precision=collo.MIXED, want_x=False)
+            ps = [collo.Problem(inst, device=local) for _ in range(nb)]
+            res = collo.batch_solve(ps, theta0s=starts, precision=collo.MIXED)
+            for pb in ps:
+                pb.close()
             t1 = time.perf_counter()
             tot += t1 - t0
-            its_e += r["iterations"]
+            its_e += sum(r["iterations"] for r in res)
         tot = reduce_max(tot, world)
         its_e = reduce_sum(float(its_e), world)
         out["e2e"] = {"value": its_e / tot, "unit": "Newton steps/s",
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * inst.p + 8,
-                      "what": "collo_problem_create from host arrays + collo_ipm_solve + "
-                              "theta* read back, per solve", "solves": k_e}
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nb * (8 * inst.p + 64),
+                      "what": f"{nb} x collo_problem_create from host arrays + "
+                              "collo_batch_solve + theta* read back, per step", "steps": k_e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst, iters=6)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    prob.close()
+    for pb in probs:
+        pb.close()
 
 
 def cpu_baseline(inst, iters):
@@ -350,6 +390,7 @@ def run_reference(args):
     from oracle import ipm as oipm
     from paper_2607_12201_gb300 import workloads
     inst = workloads.config2()
+    inst = inst.with_theta0(workloads.multistart_thetas(inst, 1, seed=2002)[0])
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     per = 2
     for _ in range(args.warmup):
@@ -364,8 +405,8 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
-           "config": {"workload": WORKLOAD,
-                      "step": f"oracle initial point + {per} Newton iterations"},
+           "config": {"workload": WORKLOAD.format(B=args.batch),
+                      "step": f"oracle initial point + {per} Newton iterations of one start"},
            "cpu_baseline": {"value": v, "unit": "Newton steps/s", "cores": cores,
                             "kind": "oracle",
                             "sample": f"{args.steps} x (initial point + {per} Newton iterations)"},
@@ -390,10 +431,30 @@ def only_solve(prec_name):
             sys.exit(1)
 
 
+def only_batch(nb):
+    from paper_2607_12201_gb300 import build as B
+    B.build()
+    from paper_2607_12201_gb300 import collo, workloads
+    inst = workloads.config2()
+    starts = workloads.multistart_thetas(inst, nb, seed=2002)
+    probs = [collo.Problem(inst) for _ in range(nb)]
+    l0 = collo.launch_count()
+    t0 = time.perf_counter()
+    res = collo.batch_solve(probs, theta0s=starts, precision=collo.MIXED)
+    print(json.dumps({"only_batch": nb, "wall_s": time.perf_counter() - t0,
+                      "iterations": sum(r["iterations"] for r in res),
+                      "status": sorted(set(r["status"] for r in res)),
+                      "launches": collo.launch_count() - l0}), flush=True)
+    for pb in probs:
+        pb.close()
+
+
 def main():
     args = parse_args()
     if args.only_solve:
         only_solve(args.only_solve)
+    elif args.only_batch:
+        only_batch(args.batch)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -255,10 +255,20 @@ collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
  * solves), and each problem follows exactly the iterates it would follow
  * alone.  probs: [count] problems created on the same device; theta0[i]:
  * [p_i] start of problem i; results[i] as for collo_ipm_solve (its theta / x /
- * lambda pointers are honoured).  The call returns COLLO_OK when every
- * problem has a final status in results[i].status. */
+ * lambda pointers are honoured).  The batch runs on the first problem's
+ * CUDA stream.  The call returns COLLO_OK when every problem has a final
+ * status in results[i].status. */
 collo_status collo_batch_solve(collo_problem* const* probs, int count, const double* const* theta0,
                                const collo_ipm_options* opts, collo_result* results);
+
+/* Measurement hook for batches: re-runs one batched phase of `count`
+ * problems (phase 1 factorization in `precision` with each problem's last
+ * regularisation, 2 solve without refinement, 3 evaluation with derivatives at
+ * each problem's current iterate) reps times between CUDA events and returns
+ * the average milliseconds per launch.  Problems must have been evaluated
+ * (e.g. by a solve). */
+collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
+                                    int precision, int reps, double* ms_per_launch);
 
 /* Continuous-batching server.  Problems are submitted at any time; each
  * collo_server_step admits waiting problems into free slots while the device

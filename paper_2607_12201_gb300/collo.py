@@ -122,6 +122,9 @@ def _load():
     lib.collo_batch_solve.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_void_p),
                                        C.POINTER(IpmOptions), C.POINTER(Result)]
     lib.collo_batch_solve.restype = C.c_int
+    lib.collo_batch_time_phase.argtypes = [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_int,
+                                           C.POINTER(C.c_double)]
+    lib.collo_batch_time_phase.restype = C.c_int
     lib.collo_server_create.argtypes = [C.c_int, C.c_int64, C.POINTER(IpmOptions), C.c_int,
                                         C.POINTER(P)]
     lib.collo_server_create.restype = C.c_int
@@ -340,6 +343,16 @@ def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
     o = Problem.ipm_options(**kw)
     _check(lib.collo_batch_solve(handles, n, thp, C.byref(o), res))
     return [_result_dict(res[i], *outs[i]) for i in range(n)]
+
+
+def batch_time_phase(problems, phase: int, precision: int, reps: int = 10) -> float:
+    """collo_batch_time_phase: ms per batched launch of phase 1/2/3."""
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p.h.value for p in problems])
+    ms = C.c_double()
+    _check(lib.collo_batch_time_phase(handles, n, int(phase), int(precision), int(reps),
+                                      C.byref(ms)))
+    return ms.value
 
 
 class Server:

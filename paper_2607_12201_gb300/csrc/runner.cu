@@ -979,7 +979,7 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
     }
   COLLO_CUDA(cudaSetDevice(dev));
   Runner R;
-  collo_status s = R.init(count, dev, nullptr);
+  collo_status s = R.init(count, dev, probs[0]->stream);   // runs on the first problem's stream
   if (s != COLLO_OK) return s;
   Opt o = make_opt(opts);
   std::vector<IpmInst> I(count);
@@ -1002,6 +1002,56 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
   for (int i = 0; i < count; ++i)
     if ((s = ipm_finish(R, I[i], &results[i])) != COLLO_OK) return s;
   return COLLO_OK;
+}
+
+// CUDA-event timing of one batched phase over problems that each hold an
+// evaluated iterate and a factorization (e.g. after collo_batch_solve):
+// phase 1 factorization, 2 solve (no refinement), 3 evaluation.
+collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
+                                    int precision, int reps, double* ms_per_launch) {
+  if (!probs || count < 1 || reps < 1 || !ms_per_launch || phase < 1 || phase > 3) {
+    set_error("bad argument");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  const int dev = probs[0]->device;
+  COLLO_CUDA(cudaSetDevice(dev));
+  Runner R;
+  collo_status s = R.init(count, dev, nullptr);
+  if (s != COLLO_OK) return s;
+  std::vector<int> slots;
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i]->evaluated) { set_error("problem not evaluated"); return COLLO_ERR_NOT_EVALUATED; }
+    if ((s = ensure_factor_storage(probs[i], precision)) != COLLO_OK) return s;
+    if ((s = R.attach(i, probs[i])) != COLLO_OK) return s;
+    slots.push_back(i);
+  }
+  if ((s = R.set_plan(0, slots)) != COLLO_OK) return s;
+  if ((s = R.set_params(0, [&](int, int sl, InstParams& ip) {
+         ip.dw = probs[sl]->fac_dw; ip.dc = probs[sl]->fac_dc; })) != COLLO_OK)
+    return s;
+  auto run = [&]() -> collo_status {
+    if (phase == 1) return R.factor(0, precision);
+    if (phase == 2) return R.solve(0, precision, 0);
+    return R.eval(0, 1, 0, 2, true);
+  };
+  if (phase == 2 && (s = R.factor(0, precision)) != COLLO_OK) return s;
+  if ((s = run()) != COLLO_OK) return s;
+  cudaEvent_t e0, e1;
+  COLLO_CUDA(cudaEventCreate(&e0));
+  COLLO_CUDA(cudaEventCreate(&e1));
+  COLLO_CUDA(cudaEventRecord(e0, R.stream));
+  for (int k = 0; k < reps; ++k)
+    if ((s = run()) != COLLO_OK) return s;
+  COLLO_CUDA(cudaEventRecord(e1, R.stream));
+  COLLO_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = t / reps;
+  for (int i = 0; i < count; ++i)
+    if (phase <= 2) probs[i]->factored = precision;
+  return R.check_barrier();
 }
 
 // ---- server --------------------------------------------------------------------------

@@ -277,6 +277,14 @@ def config2(seed: int = 3, N: int = 400, theta0_spread: float = 0.1) -> Instance
                           name=f"massaction_n10_r20_N{N}")
 
 
+def multistart_thetas(inst: Instance, count: int, seed: int = 2002,
+                      spread: float = 0.1) -> list:
+    """Seeded starting points theta_true + U[-spread, spread] (log10 units) for
+    a multistart run of one instance."""
+    rng = _rng(seed, 31337)
+    return [inst.theta_true + rng.uniform(-spread, spread, inst.p) for _ in range(count)]
+
+
 def config3(seed: int = 1003, N: int = 2000, est: str = "even",
             theta0_spread: float = 0.1) -> Instance:
     """Stiff: 30 species / 60 reactions, log10 k ~ U[-3,3], 8 observed x 100 times, T=50."""
