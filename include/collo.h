@@ -183,6 +183,8 @@ typedef struct collo_result {
   int iterations;             /* Newton steps taken */
   int factorizations;         /* KKT factorizations (inertia corrections included) */
   int line_search_trials;
+  int refinement_sweeps;      /* FP64 iterative-refinement sweeps over all steps */
+  int reserved_i;
   double phi;                 /* objective at the final iterate */
   double kkt_error;           /* scaled optimality error E_0 at the final iterate */
   double mu;                  /* final barrier parameter */

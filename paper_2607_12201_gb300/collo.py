@@ -85,7 +85,8 @@ class IpmOptions(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("factorizations", C.c_int),
-                ("line_search_trials", C.c_int), ("phi", C.c_double), ("kkt_error", C.c_double),
+                ("line_search_trials", C.c_int), ("refinement_sweeps", C.c_int),
+                ("reserved_i", C.c_int), ("phi", C.c_double), ("kkt_error", C.c_double),
                 ("mu", C.c_double), ("wall_seconds", C.c_double), ("theta", C.c_void_p),
                 ("x", C.c_void_p), ("lambda_", C.c_void_p)]
 
@@ -299,10 +300,7 @@ class Problem:
         res.x = None if x is None else x.ctypes.data
         res.lambda_ = None if lam is None else lam.ctypes.data
         lib.collo_ipm_solve(self.h, th0.ctypes.data, C.byref(o), C.byref(res))
-        return dict(status=res.status, iterations=res.iterations,
-                    factorizations=res.factorizations, trials=res.line_search_trials,
-                    phi=res.phi, kkt_error=res.kkt_error, mu=res.mu, wall=res.wall_seconds,
-                    theta=theta, x=x, lam=lam)
+        return _result_dict(res, theta, x, lam)
 
     def time_phase(self, phase: int, precision: int = -1, reps: int = 20) -> float:
         """Average milliseconds per launch of one phase (see collo_time_phase)."""
@@ -320,8 +318,9 @@ class Problem:
 
 def _result_dict(res, theta, x, lam):
     return dict(status=res.status, iterations=res.iterations, factorizations=res.factorizations,
-                trials=res.line_search_trials, phi=res.phi, kkt_error=res.kkt_error, mu=res.mu,
-                wall=res.wall_seconds, theta=theta, x=x, lam=lam)
+                trials=res.line_search_trials, refine=res.refinement_sweeps, phi=res.phi,
+                kkt_error=res.kkt_error, mu=res.mu, wall=res.wall_seconds, theta=theta, x=x,
+                lam=lam)
 
 
 def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):

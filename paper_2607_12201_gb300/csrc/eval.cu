@@ -224,61 +224,52 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
     E.Wobj[(size_t)i * n * NP * NP + idx] = obj_factor * w;
   }
   const double mh = -P.h;
-  const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
-  // JZ[i][k-1][s][t] = -h df_s/dz_t at node k
-  for (int idx = tid; idx < KC * n * n; idx += EVAL_BS) {
-    const int k = idx / (n * n) + 1, s = (idx / n) % n, t = idx % n;
-    double v = 0.0;
+  // Derivative blocks, one thread per row.  Row s of JZ / JT at node k
+  // accumulates, over the reactions r changing species s (nu[s][r] != 0),
+  // -h nu k_r dmon_r/dz (into the reactant columns) and -h nu dk_r mon_r
+  // (into column pidx[r]).  Row t of Wzz / Wzt at node k accumulates, over the
+  // reactions consuming t, -h om_r k_r d2mon_r/dz_t dz_u and
+  // -h om_r dk_r dmon_r/dz_t.  Each row is owned by one thread (fixed order).
+  for (int idx = tid; idx < KC * n; idx += EVAL_BS) {
+    const int k = idx / n + 1, s = idx - (k - 1) * n;
+    double* jz = E.JZ + (((size_t)i * KC + (k - 1)) * n + s) * n;
+    double* jt = E.JT + (((size_t)i * KC + (k - 1)) * n + s) * p;
+    for (int t = 0; t < n; ++t) jz[t] = 0.0;
+    for (int q = 0; q < p; ++q) jt[q] = 0.0;
     for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
       const int rr = P.nu_r[e];
       const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
       const int mi = (k - 1) * r + rr;
-      double dm = 0.0;
-      if (a == t) dm += da[mi];
-      if (b == t) dm += db[mi];
-      v += P.nu_v[e] * kr[rr] * dm;
+      const double c = mh * P.nu_v[e];
+      jz[a] += c * kr[rr] * da[mi];
+      if (b >= 0) jz[b] += c * kr[rr] * db[mi];
+      const int q = P.pidx[rr];
+      if (q >= 0) jt[q] += c * dkr[rr] * mon[mi];
     }
-    E.JZ[(size_t)i * KC * nn + idx] = mh * v;
   }
-  // JT[i][k-1][s][q] = -h df_s/dtheta_q at node k
-  for (int idx = tid; idx < KC * n * p; idx += EVAL_BS) {
-    const int k = idx / (n * p) + 1, s = (idx / p) % n, q = idx % p;
-    double v = 0.0;
-    for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
-      const int rr = P.nu_r[e];
-      if (P.pidx[rr] != q) continue;
-      v += P.nu_v[e] * dkr[rr] * mon[(k - 1) * r + rr];
-    }
-    E.JT[(size_t)i * KC * np_ + idx] = mh * v;
-  }
-  // Wzz[i][k-1][t][u] = -h sum_r om_r k_r d2 mon_r / dz_t dz_u
-  for (int idx = tid; idx < KC * n * n; idx += EVAL_BS) {
-    const int k = idx / (n * n) + 1, t = (idx / n) % n, u = idx % n;
-    double v = 0.0;
+  for (int idx = tid; idx < KC * n; idx += EVAL_BS) {
+    const int k = idx / n + 1, t = idx - (k - 1) * n;
+    double* wz = E.Wzz + (((size_t)i * KC + (k - 1)) * n + t) * n;
+    double* wt = E.Wzt + (((size_t)i * KC + (k - 1)) * n + t) * p;
+    for (int u = 0; u < n; ++u) wz[u] = 0.0;
+    for (int q = 0; q < p; ++q) wt[q] = 0.0;
     for (int e = P.rs_ptr[t]; e < P.rs_ptr[t + 1]; ++e) {
       const int rr = P.rs_r[e];
-      const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
-      if (b < 0) continue;
-      const double d2 = (double)((a == t && b == u) + (b == t && a == u));
-      v += om[(k - 1) * r + rr] * kr[rr] * d2;
-    }
-    E.Wzz[(size_t)i * KC * nn + idx] = mh * v;
-  }
-  // Wzt[i][k-1][t][q] = -h sum_r om_r dk_r d mon_r / dz_t
-  for (int idx = tid; idx < KC * n * p; idx += EVAL_BS) {
-    const int k = idx / (n * p) + 1, t = (idx / p) % n, q = idx % p;
-    double v = 0.0;
-    for (int e = P.rs_ptr[t]; e < P.rs_ptr[t + 1]; ++e) {
-      const int rr = P.rs_r[e];
-      if (P.pidx[rr] != q) continue;
       const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
       const int mi = (k - 1) * r + rr;
-      double dm = 0.0;
-      if (a == t) dm += da[mi];
-      if (b == t) dm += db[mi];
-      v += om[mi] * dkr[rr] * dm;
+      const double c = mh * om[mi];
+      if (b >= 0) {
+        if (a == b) wz[t] += c * kr[rr] * 2.0;
+        else wz[a == t ? b : a] += c * kr[rr];
+      }
+      const int q = P.pidx[rr];
+      if (q >= 0) {
+        double dm = 0.0;
+        if (a == t) dm += da[mi];
+        if (b == t) dm += db[mi];
+        wt[q] += c * dkr[rr] * dm;
+      }
     }
-    E.Wzt[(size_t)i * KC * np_ + idx] = mh * v;
   }
   // theta-theta diagonal partial sums of this element
   for (int q = tid; q < p; q += EVAL_BS) {

@@ -40,43 +40,106 @@ __device__ inline void pivot_inertia(double a, double b, double d, int& pos, int
 }
 
 // Eliminate the first npairs (state, multiplier) pairs of the symmetric
-// matrix A (size msz, leading dimension ld, lower triangle valid).  L columns
-// go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to Dout[3 q].
-// Scratch: cc0, cc1, l0s, l1s of length msz (shared memory).
+// matrix A (size msz, leading dimension ld, lower triangle valid), blocked
+// right-looking: pairs are taken in panels of PB; inside a panel each pair's
+// multipliers are formed and only the panel's remaining columns are updated;
+// then the trailing matrix receives one rank-2PB update, computed in 4 x 4
+// register tiles from the panel's multipliers Lp and unscaled columns Up.
+// L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
+// Dout[3 q].  Scratch Lp, Up: msz x (2 PB + 1) each (shared memory).
+constexpr int PB = 8;
+constexpr int PLD = 2 * PB + 1;
+
+__device__ inline void tri_tile(int t, int& ti, int& tj) {
+  int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
 template <typename T>
 __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict__ Lout, int lds,
-                               T* __restrict__ Dout, T* cc0, T* cc1, T* l0s, T* l1s,
-                               int& pos, int& neg, int& zero) {
+                               T* __restrict__ Dout, T* Lp, T* Up, int& pos, int& neg, int& zero) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, wy = tid >> 5;
-  for (int q = 0; q < npairs; ++q) {
-    const int c0 = 2 * q, c1 = c0 + 1;
-    const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
-    const T det = a * d - b * b;
-    T ia, ib, id;
-    if (det != T(0) && isfinite((double)det)) {
-      const T inv = T(1) / det;
-      ia = d * inv; ib = -b * inv; id = a * inv;
-    } else {
-      ia = ib = id = T(0);
+  for (int q0 = 0; q0 < npairs; q0 += PB) {
+    const int pe = min(q0 + PB, npairs);
+    const int cend = 2 * pe;
+    for (int q = q0; q < pe; ++q) {
+      const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
+      const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
+      const T det = a * d - b * b;
+      T ia, ib, id;
+      if (det != T(0) && isfinite((double)det)) {
+        const T inv = T(1) / det;
+        ia = d * inv; ib = -b * inv; id = a * inv;
+      } else {
+        ia = ib = id = T(0);
+      }
+      for (int r = c1 + 1 + tid; r < msz; r += FBS) {
+        const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
+        const T l0 = x0 * ia + x1 * ib;
+        const T l1 = x0 * ib + x1 * id;
+        Up[r * PLD + kk] = x0; Up[r * PLD + kk + 1] = x1;
+        Lp[r * PLD + kk] = l0; Lp[r * PLD + kk + 1] = l1;
+        Lout[(size_t)c0 * lds + r] = l0;
+        Lout[(size_t)c1 * lds + r] = l1;
+      }
+      if (tid == 0) {
+        Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
+        pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
+      }
+      __syncthreads();
+      // remaining panel columns c in (c1, cend), all rows r >= c
+      const int w = cend - c1 - 1;
+      if (w > 0)
+        for (int r = c1 + 1 + wy; r < msz; r += FTY) {
+          const T l0 = Lp[r * PLD + kk], l1 = Lp[r * PLD + kk + 1];
+          T* Ar = A + (size_t)r * ld;
+          for (int c = c1 + 1 + lane; c < cend && c <= r; c += 32)
+            Ar[c] -= l0 * Up[c * PLD + kk] + l1 * Up[c * PLD + kk + 1];
+        }
+      __syncthreads();
     }
-    for (int r = c1 + 1 + tid; r < msz; r += FBS) {
-      const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
-      const T l0 = x0 * ia + x1 * ib;
-      const T l1 = x0 * ib + x1 * id;
-      cc0[r] = x0; cc1[r] = x1; l0s[r] = l0; l1s[r] = l1;
-      Lout[(size_t)c0 * lds + r] = l0;
-      Lout[(size_t)c1 * lds + r] = l1;
-    }
-    if (tid == 0) {
-      Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
-      pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
-    }
-    __syncthreads();
-    for (int r = c1 + 1 + wy; r < msz; r += FTY) {
-      const T l0 = l0s[r], l1 = l1s[r];
-      T* Ar = A + (size_t)r * ld;
-      for (int c = c1 + 1 + lane; c <= r; c += 32) Ar[c] -= l0 * cc0[c] + l1 * cc1[c];
+    // trailing rank-2PB update of rows / columns >= cend (lower part)
+    const int K = 2 * (pe - q0);
+    const int Tn = msz - cend;
+    if (Tn > 0) {
+      const int nt = (Tn + 3) >> 2;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int t = tid; t < ntiles; t += FBS) {
+        int ti, tj;
+        tri_tile(t, ti, tj);
+        const int r0 = cend + 4 * ti, cb = cend + 4 * tj;
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        for (int k = 0; k < K; ++k) {
+          T lr[4], uc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            lr[u] = (r0 + u < msz) ? Lp[(r0 + u) * PLD + k] : T(0);
+            uc[u] = (cb + u < msz) ? Up[(cb + u) * PLD + k] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * uc[v];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u;
+          if (r >= msz) continue;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int c = cb + v;
+            if (c <= r && c < msz) A[r * ld + c] -= acc[u][v];
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -127,8 +190,7 @@ __host__ __device__ inline int odd_ld(int m) { return (m & 1) ? m : m + 1; }
 template <typename T>
 __device__ void elem_factor_one(const DevProb& P, const DevEval& E,
                                 const double* __restrict__ sigma, double dw, double dc,
-                                const DevFactor<T>& F, int e, T* A, T* cc0, T* cc1, T* l0s,
-                                T* l1s) {
+                                const DevFactor<T>& F, int e, T* A, T* Lp, T* Up) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext, ld = odd_ld(ext);
   const int tid = threadIdx.x;
   const int nint = 3 * n;          // interior pairs
@@ -139,7 +201,7 @@ __device__ void elem_factor_one(const DevProb& P, const DevEval& E,
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
   pair_eliminate<T>(A, ld, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                    F.Del + (size_t)e * nint * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+                    F.Del + (size_t)e * nint * 3, Lp, Up, pos, neg, zero);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
   }
@@ -173,13 +235,11 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
               DevFactor<T> F, int use_smem) {
   extern __shared__ unsigned char smraw[];
   const int ext = P.ext, ld = odd_ld(ext);
-  T* cc0 = reinterpret_cast<T*>(smraw);
-  T* cc1 = cc0 + ext;
-  T* l0s = cc1 + ext;
-  T* l1s = l0s + ext;
-  T* A = use_smem ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
+  T* Lp = reinterpret_cast<T*>(smraw);
+  T* Up = Lp + (size_t)ext * PLD;
+  T* A = use_smem ? (Up + (size_t)ext * PLD) : (F.work + (size_t)blockIdx.x * ld * ext);
   for (int e = blockIdx.x; e < P.N; e += gridDim.x)
-    elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, cc0, cc1, l0s, l1s);
+    elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, Lp, Up);
 }
 
 // ---- 2. one level of block cyclic reduction -------------------------------------
@@ -188,7 +248,7 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
 // left neighbour (n) | c0 of the right neighbour (n) | theta (p)].
 template <typename T>
 __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stride,
-                               int final_level, int bi, T* A, T* cc0, T* cc1, T* l0s, T* l1s) {
+                               int final_level, int bi, T* A, T* Lp, T* Up) {
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
   const int tid = threadIdx.x;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
@@ -217,7 +277,7 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
   pair_eliminate<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
-                    F.Db + (size_t)i * n * 3, cc0, cc1, l0s, l1s, pos, neg, zero);
+                    F.Db + (size_t)i * n * 3, Lp, Up, pos, neg, zero);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
     in[0] = pos; in[1] = neg; in[2] = zero;
@@ -269,14 +329,12 @@ __global__ void __launch_bounds__(FBS)
 k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
   extern __shared__ unsigned char smraw[];
   const int bext = P.bext, ld = odd_ld(bext);
-  T* cc0 = reinterpret_cast<T*>(smraw);
-  T* cc1 = cc0 + bext;
-  T* l0s = cc1 + bext;
-  T* l1s = l0s + bext;
-  T* A = use_smem ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
+  T* Lp = reinterpret_cast<T*>(smraw);
+  T* Up = Lp + (size_t)bext * PLD;
+  T* A = use_smem ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
   const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
   for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-    bcr_factor_one<T>(P, F, stride, final_level, bi, A, cc0, cc1, l0s, l1s);
+    bcr_factor_one<T>(P, F, stride, final_level, bi, A, Lp, Up);
 }
 
 // ---- 3. parameter Schur complement (FP64) ------------------------------------------
@@ -698,13 +756,10 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     const DevInst& I = insts[act[k]];
     const DevFactor<T>& F = inst_factor<T>(I);
     const int ext = I.P.ext, ld = odd_ld(ext);
-    T* cc0 = reinterpret_cast<T*>(smraw);
-    T* cc1 = cc0 + ext;
-    T* l0s = cc1 + ext;
-    T* l1s = l0s + ext;
-    T* Am = (flags[k] & 1) ? (l1s + ext) : (F.work + (size_t)blockIdx.x * ld * ext);
-    elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, cc0,
-                       cc1, l0s, l1s);
+    T* Lp = reinterpret_cast<T*>(smraw);
+    T* Up = Lp + (size_t)ext * PLD;
+    T* Am = (flags[k] & 1) ? (Up + (size_t)ext * PLD) : (F.work + (size_t)blockIdx.x * ld * ext);
+    elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, Lp, Up);
   }
   grid_barrier(gb);
   // 2. cyclic-reduction levels, then each instance's final block
@@ -717,13 +772,11 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       const DevInst& I = insts[act[k]];
       const DevFactor<T>& F = inst_factor<T>(I);
       const int bext = I.P.bext, ld = odd_ld(bext);
-      T* cc0 = reinterpret_cast<T*>(smraw);
-      T* cc1 = cc0 + bext;
-      T* l0s = cc1 + bext;
-      T* l1s = l0s + bext;
-      T* Am = (flags[k] & 2) ? (l1s + bext) : (F.work + (size_t)blockIdx.x * ld * bext);
-      if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, cc0, cc1, l0s, l1s);
-      else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, cc0, cc1, l0s, l1s);
+      T* Lp = reinterpret_cast<T*>(smraw);
+      T* Up = Lp + (size_t)bext * PLD;
+      T* Am = (flags[k] & 2) ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
+      if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, Lp, Up);
+      else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, Lp, Up);
     }
     grid_barrier(gb);
   }
@@ -822,13 +875,13 @@ int bcr_levels(int N) {
 
 template <typename T>
 size_t elem_factor_smem(const DevProb& P, bool full) {
-  size_t v = sizeof(T) * 4 * (size_t)P.ext;
+  size_t v = sizeof(T) * 2 * (size_t)P.ext * PLD;
   if (full) v += sizeof(T) * (size_t)odd_ld(P.ext) * P.ext;
   return v;
 }
 template <typename T>
 size_t bcr_factor_smem(const DevProb& P, bool full) {
-  size_t v = sizeof(T) * 4 * (size_t)P.bext;
+  size_t v = sizeof(T) * 2 * (size_t)P.bext * PLD;
   if (full) v += sizeof(T) * (size_t)odd_ld(P.bext) * P.bext;
   return v;
 }

@@ -754,6 +754,7 @@ static collo_status ipm_finish(Runner& R, IpmInst& I, collo_result* res) {
   res->iterations = I.it;
   res->factorizations = I.facs;
   res->line_search_trials = I.trials_total;
+  res->refinement_sweeps = I.refine_total;
   res->phi = I.phi;
   res->kkt_error = I.err;
   res->mu = I.mu;
