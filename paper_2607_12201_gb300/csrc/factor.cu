@@ -62,47 +62,51 @@ template <typename T>
 __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict__ Lout, int lds,
                                T* __restrict__ Dout, T* Lp, T* Up, int& pos, int& neg, int& zero) {
   const int tid = threadIdx.x;
-  const int lane = tid & 31, wy = tid >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
   for (int q0 = 0; q0 < npairs; q0 += PB) {
     const int pe = min(q0 + PB, npairs);
     const int cend = 2 * pe;
-    for (int q = q0; q < pe; ++q) {
-      const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
-      const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
-      const T det = a * d - b * b;
-      T ia, ib, id;
-      if (det != T(0) && isfinite((double)det)) {
-        const T inv = T(1) / det;
-        ia = d * inv; ib = -b * inv; id = a * inv;
-      } else {
-        ia = ib = id = T(0);
-      }
-      for (int r = c1 + 1 + tid; r < msz; r += FBS) {
-        const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
-        const T l0 = x0 * ia + x1 * ib;
-        const T l1 = x0 * ib + x1 * id;
-        Up[r * PLD + kk] = x0; Up[r * PLD + kk + 1] = x1;
-        Lp[r * PLD + kk] = l0; Lp[r * PLD + kk + 1] = l1;
-        Lout[(size_t)c0 * lds + r] = l0;
-        Lout[(size_t)c1 * lds + r] = l1;
-      }
-      if (tid == 0) {
-        Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
-        pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
-      }
-      __syncthreads();
-      // remaining panel columns c in (c1, cend), all rows r >= c
-      const int w = cend - c1 - 1;
-      if (w > 0)
-        for (int r = c1 + 1 + wy; r < msz; r += FTY) {
-          const T l0 = Lp[r * PLD + kk], l1 = Lp[r * PLD + kk + 1];
-          T* Ar = A + (size_t)r * ld;
-          for (int c = c1 + 1 + lane; c < cend && c <= r; c += 32)
-            Ar[c] -= l0 * Up[c * PLD + kk] + l1 * Up[c * PLD + kk + 1];
+    // panel: warp 0 alone, warp-synchronous
+    if (warp == 0) {
+      for (int q = q0; q < pe; ++q) {
+        const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
+        const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
+        const T det = a * d - b * b;
+        T ia, ib, id;
+        if (det != T(0) && isfinite((double)det)) {
+          const T inv = T(1) / det;
+          ia = d * inv; ib = -b * inv; id = a * inv;
+        } else {
+          ia = ib = id = T(0);
         }
-      __syncthreads();
+        for (int r = c1 + 1 + lane; r < msz; r += 32) {
+          const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
+          const T l0 = x0 * ia + x1 * ib;
+          const T l1 = x0 * ib + x1 * id;
+          Up[r * PLD + kk] = x0; Up[r * PLD + kk + 1] = x1;
+          Lp[r * PLD + kk] = l0; Lp[r * PLD + kk + 1] = l1;
+          Lout[(size_t)c0 * lds + r] = l0;
+          Lout[(size_t)c1 * lds + r] = l1;
+        }
+        if (lane == 0) {
+          Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
+          pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
+        }
+        __syncwarp();
+        // remaining panel columns c in (c1, cend), rows r >= c
+        if (c1 + 1 < cend)
+          for (int r = c1 + 1 + lane; r < msz; r += 32) {
+            const T l0 = Lp[r * PLD + kk], l1 = Lp[r * PLD + kk + 1];
+            T* Ar = A + (size_t)r * ld;
+            const int cmax = min(cend - 1, r);
+            for (int c = c1 + 1; c <= cmax; ++c)
+              Ar[c] -= l0 * Up[c * PLD + kk] + l1 * Up[c * PLD + kk + 1];
+          }
+        __syncwarp();
+      }
     }
-    // trailing rank-2PB update of rows / columns >= cend (lower part)
+    __syncthreads();
+    // trailing rank-2PB update of rows / columns >= cend (lower part), all warps
     const int K = 2 * (pe - q0);
     const int Tn = msz - cend;
     if (Tn > 0) {

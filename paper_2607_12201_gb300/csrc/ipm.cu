@@ -615,20 +615,25 @@ __global__ void k_update_b(const DevInst* __restrict__ insts, const int* __restr
     if (mode == 1) { I.kb[j] += I.kc[j]; continue; }
     if (mode == 2) { if (j < I.n_c) I.lam[j] = 0.0; continue; }
     const InstParams pr = prm[k];
-    if (j < I.P.p) {
+    const long long nz = I.n_x - I.P.p;
+    if (j >= nz && j < I.n_x) {
+      // parameter entry q: the same thread moves theta_q and its bound duals
       const DevProb& P = I.P;
-      const size_t nz = (size_t)P.N * NP * P.n;
-      const double th = I.x[nz + j] + pr.alpha * I.kb[nz + j];
-      const double sl = th - P.theta_lo[j], su = P.theta_hi[j] - th;
-      double a = I.zl[j] + pr.alpha_z * I.dz[j];
-      double b = I.zu[j] + pr.alpha_z * I.dz[P.p + j];
+      const int q = (int)(j - nz);
+      const double th = I.x[j] + pr.alpha * I.kb[j];
+      I.x[j] = th;
+      const double sl = th - P.theta_lo[q], su = P.theta_hi[q] - th;
+      double a = I.zl[q] + pr.alpha_z * I.dz[q];
+      double b = I.zu[q] + pr.alpha_z * I.dz[P.p + q];
       a = fmax(fmin(a, pr.ksig * pr.mu / sl), pr.mu / (pr.ksig * sl));
       b = fmax(fmin(b, pr.ksig * pr.mu / su), pr.mu / (pr.ksig * su));
-      I.zl[j] = a;
-      I.zu[j] = b;
+      I.zl[q] = a;
+      I.zu[q] = b;
+    } else if (j < I.n_x) {
+      I.x[j] += pr.alpha * I.kb[j];
+    } else {
+      I.lam[j - I.n_x] += pr.alpha * I.kb[j];
     }
-    if (j < I.n_x) I.x[j] += pr.alpha * I.kb[j];
-    else I.lam[j - I.n_x] += pr.alpha * I.kb[j];
   }
 }
 

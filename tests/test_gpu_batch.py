@@ -94,3 +94,17 @@ def test_server_continuous_batching_equals_alone(collo):
     server.close()
     for pb in probs:
         pb.close()
+
+
+def test_repeated_batches_are_bitwise_reproducible(collo):
+    insts = _mix()
+    runs = []
+    for _ in range(3):
+        probs = [collo.Problem(inst) for inst in insts]
+        runs.append(collo.batch_solve(probs, precision=collo.MIXED))
+        for pb in probs:
+            pb.close()
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert a["iterations"] == b["iterations"]
+            assert np.array_equal(a["theta"], b["theta"])
