@@ -219,6 +219,29 @@ void* collo_problem_stream(const collo_problem* prob);
 collo_status collo_eval(collo_problem* prob, const double* x, const double* lambda,
                         double obj_factor, collo_eval_out* out);
 
+/* collo_eval for callers that cannot allocate device memory while they run
+ * (inside CUDA graph capture, real-time loops that allocate everything ahead
+ * of time, processes whose device allocator belongs to another runtime).  The
+ * paper has no counterpart; it computes exactly what collo_eval computes, and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * x [n_x] and lambda [n_c] (lambda may be NULL) and every pointer of *out
+ * (all must be set; hess_thth may be NULL only when p = 0) are DEVICE
+ * pointers of the problem's GPU, in the collo_eval layouts.  The kernels are
+ * queued on `stream` (a cudaStream_t; NULL: the problem's stream) and the
+ * call returns without waiting; *out is valid once the stream reaches it.
+ * Its scratch (per-element partial sums, N (4 + p) + 8 doubles) is a fixed
+ * 4 MiB device array of the library (2^19 doubles), held by every GPU that
+ * loads the library until the process exits; larger problems are rejected
+ * with COLLO_ERR_INVALID_ARG.  The scratch needs no clearing (each call
+ * overwrites all of it), but every call shares it: calls whose kernels
+ * overlap on the GPU race, so issue them on one stream or order them.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The problem's derivative buffers are not touched, so it does not replace
+ * collo_eval before collo_kkt_factor. */
+collo_status collo_eval_noalloc(collo_problem* prob, const double* x, const double* lambda,
+                                double obj_factor, const collo_eval_out* out, void* stream);
+
 /* Factor the regularised KKT matrix of the most recent collo_eval:
  *   [ W + diag(sigma) + delta_w I    J^T       ]
  *   [ J                            -delta_c I  ]

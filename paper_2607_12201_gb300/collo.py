@@ -120,6 +120,9 @@ def _load():
     lib.collo_ipm_solve.restype = C.c_int
     lib.collo_initial_states.argtypes = [P, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.collo_initial_states.restype = C.c_int
+    lib.collo_eval_noalloc.argtypes = [P, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.POINTER(EvalOut), C.c_void_p]
+    lib.collo_eval_noalloc.restype = C.c_int
     lib.collo_batch_solve.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_void_p),
                                        C.POINTER(IpmOptions), C.POINTER(Result)]
     lib.collo_batch_solve.restype = C.c_int
@@ -256,6 +259,16 @@ class Problem:
         if outputs:
             out["phi"] = float(out["phi"][0])
         return out
+
+    def eval_noalloc(self, x_ptr: int, lam_ptr, out_ptrs: dict, obj_factor: float = 1.0,
+                     stream: int | None = None):
+        """collo_eval_noalloc on device pointers (ints); out_ptrs maps the
+        collo_eval_out field names to device pointers.  Asynchronous."""
+        eo = EvalOut()
+        for name, ptr in out_ptrs.items():
+            setattr(eo, name, ptr)
+        return _check(lib.collo_eval_noalloc(self.h, x_ptr, lam_ptr, float(obj_factor),
+                                             C.byref(eo), stream))
 
     def eval_raw(self, x_ptr, lam_ptr, obj_factor=1.0):
         """collo_eval on raw (device or host) pointers, no outputs copied."""

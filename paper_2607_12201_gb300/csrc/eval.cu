@@ -5,7 +5,10 @@
 // "Constructing GPU kernels with ExaModels.jl"), written here as one CUDA
 // block per element.  Also the structured FP64 KKT matrix-vector product used
 // by iterative refinement and by the optimality test.
+#include <mutex>
+
 #include "collo_internal.cuh"
+#include "problem.cuh"
 
 namespace collo {
 
@@ -358,6 +361,14 @@ __global__ void __launch_bounds__(RED_BS) k_eval_reduce(DevProb P, DevEval E, in
   eval_reduce_one(P, E, deriv, nullptr, sh);
 }
 
+// Reduction of collo_eval_noalloc: the partials in the fixed scratch, Phi
+// into the caller's output (out[0] = Phi).
+__global__ void __launch_bounds__(RED_BS) k_eval_reduce_noalloc(DevProb P, DevEval E, double* phi) {
+  __shared__ double sh[RED_BS];
+  eval_reduce_one(P, E, 1, nullptr, sh);
+  if (threadIdx.x == 0) *phi = E.red[0];
+}
+
 __global__ void __launch_bounds__(RED_BS)
 k_eval_reduce_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int deriv) {
   __shared__ double sh[RED_BS];
@@ -617,6 +628,36 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
   return cudaGetLastError();
 }
 
+// ---- evaluation without allocation ------------------------------------------------
+// Callers that cannot allocate device memory while running (code inside a CUDA
+// graph capture, real-time control loops that allocate everything up front,
+// hosts whose allocator is owned by another runtime) use collo_eval_noalloc.
+// Its only scratch, the per-element partial sums of the objective, of the
+// constraint norms and of the parameter-parameter Hessian, lives in this
+// fixed device array instead of problem-owned buffers.  Every GPU that loads
+// the library holds it until the process exits.
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = 1 << 19;   // 4 MiB
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];   // device address of the array, per device ordinal
+
+// Device address of the scratch array on device `dev` (current device).
+// cudaGetSymbolAddress runs once per device; in host code the array's name is
+// only a host-side stand-in and must never be passed to a kernel.
+static cudaError_t noalloc_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = static_cast<double*>(g_noalloc_addr[dev]);
+  return cudaSuccess;
+}
+
 // ---- batched launchers (plan arrays in device memory) --------------------------
 cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                           int total_elems, const InstParams* prm, int xsel, int dxsel, int lsel,
@@ -653,3 +694,51 @@ cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const in
 }
 
 }  // namespace collo
+
+// ---- C ABI: evaluation without allocation -------------------------------------------
+
+extern "C" collo_status collo_eval_noalloc(collo_problem* prob, const double* x,
+                                           const double* lambda, double obj_factor,
+                                           const collo_eval_out* out, void* stream) {
+  using namespace collo;
+  if (!prob || !x || !out || !out->phi || !out->c || !out->grad || !out->jac_z ||
+      !out->jac_theta || !out->hess_zz || !out->hess_ztheta || !out->hess_obj ||
+      (prob->P.p > 0 && !out->hess_thth)) {
+    set_error("collo_eval_noalloc: x and every output must be device pointers (lambda may be NULL)");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  const DevProb& P = prob->P;
+  const size_t need = (size_t)P.N * (4 + (size_t)P.p) + 8;
+  if (need > NOALLOC_SCRATCH_DOUBLES) {
+    set_error("collo_eval_noalloc: N (4 + p) + 8 = " + std::to_string(need) +
+              " doubles exceeds the fixed scratch of " +
+              std::to_string(NOALLOC_SCRATCH_DOUBLES) + " doubles");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  double* scratch = nullptr;
+  COLLO_CUDA(noalloc_scratch(prob->device, &scratch));
+  DevEval E{};
+  E.c = out->c;
+  E.grad = out->grad;
+  E.JZ = out->jac_z;
+  E.JT = out->jac_theta;
+  E.Wzz = out->hess_zz;
+  E.Wzt = out->hess_ztheta;
+  E.Wobj = out->hess_obj;
+  E.wtt = out->hess_thth;
+  E.part = scratch;                                   // [N][4]
+  E.wtt_part = scratch + (size_t)P.N * 4;             // [N][p]
+  E.red = scratch + (size_t)P.N * (4 + (size_t)P.p);  // [8]
+  cudaStream_t st = stream ? (cudaStream_t)stream : prob->stream;
+  const size_t sm = eval_smem_bytes(P);
+  if (sm > 48 * 1024)
+    COLLO_CUDA(cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  count_launch();
+  k_eval<true><<<P.N, EVAL_BS, sm, st>>>(P, x, nullptr, 0.0, lambda, obj_factor, E);
+  COLLO_CUDA(cudaGetLastError());
+  count_launch();
+  k_eval_reduce_noalloc<<<1, RED_BS, 0, st>>>(P, E, out->phi);
+  COLLO_CUDA(cudaGetLastError());
+  return COLLO_OK;
+}
