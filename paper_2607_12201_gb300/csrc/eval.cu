@@ -592,12 +592,12 @@ cudaError_t launch_eval(const DevProb& P, const DevEval& E, const double* x, con
                         cudaStream_t st) {
   size_t sm = eval_smem_bytes(P);
   if (deriv) {
-    if (sm > 48 * 1024)
+    if (sm > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
     k_eval<true><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
   } else {
-    if (sm > 48 * 1024)
+    if (sm > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
     k_eval<false><<<P.N, EVAL_BS, sm, st>>>(P, x, dx, alpha, lam, obj_factor, E);
@@ -664,12 +664,12 @@ cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int
                           bool deriv, size_t smem, cudaStream_t st) {
   if (A == 0) return cudaSuccess;
   if (deriv) {
-    if (smem > 48 * 1024)
+    if (smem > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_eval_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_eval_b<true><<<total_elems, EVAL_BS, smem, st>>>(insts, act, A, pre_elem, prm, xsel, dxsel, lsel);
   } else {
-    if (smem > 48 * 1024)
+    if (smem > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_eval_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_eval_b<false><<<total_elems, EVAL_BS, smem, st>>>(insts, act, A, pre_elem, prm, xsel, dxsel, lsel);
@@ -732,7 +732,7 @@ extern "C" collo_status collo_eval_noalloc(collo_problem* prob, const double* x,
   E.red = scratch + (size_t)P.N * (4 + (size_t)P.p);  // [8]
   cudaStream_t st = stream ? (cudaStream_t)stream : prob->stream;
   const size_t sm = eval_smem_bytes(P);
-  if (sm > 48 * 1024)
+  if (sm > SMEM_OPTIN_ABOVE)
     COLLO_CUDA(cudaFuncSetAttribute(k_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   count_launch();
   k_eval<true><<<P.N, EVAL_BS, sm, st>>>(P, x, nullptr, 0.0, lambda, obj_factor, E);

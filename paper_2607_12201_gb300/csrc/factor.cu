@@ -246,6 +246,268 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
     elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, Lp, Up);
 }
 
+// ---- 1'. pair elimination with the block held in registers -------------------------
+// The same elimination as pair_eliminate, organised for small blocks
+// (ext <= RT_MAX_EXT): the lower triangle is cut into 4 x 4 tiles and each of
+// the NT threads keeps up to TPT tiles in registers for the whole
+// elimination.  For every pair the owners of the pair's tile column publish
+// the two pivot columns (rows >= the pair) into a shared vector; after one
+// barrier every thread forms the pivot inverse and the multipliers of its own
+// rows and applies the rank-2 update to its tiles.  The shared vector
+// alternates between two buffers, so one barrier per pair suffices: a buffer
+// is rewritten only after the barrier that follows all reads of it.  Entries
+// that are already eliminated, above the diagonal or past ext take harmless
+// finite updates and are never read again.
+//   entry(r, c), c <= r < ext: the block's lower triangle (assembly);
+//   sink(r, c, v), 2 npairs <= c <= r < ext: the eliminated trailing block;
+//   bar(): barrier over the NT threads; tid in [0, NT).
+// L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
+// Dout[3 q]; thread 0 accumulates the pivots' inertia.
+constexpr int RT_MAX_TR = 31;            // tile rows: ext <= 124
+constexpr int RT_UB = 4 * RT_MAX_TR + 4;  // rows per pivot-column buffer
+
+template <typename T>
+struct alignas(2 * sizeof(T)) Pair {
+  T x, y;
+};
+
+template <typename T, int NT, int TPT, class Entry, class Sink, class Bar>
+__device__ void pair_eliminate_rt(int tid, int ext, int npairs, Entry entry, T* __restrict__ Lout,
+                                  int lds, T* __restrict__ Dout, Sink sink, Bar bar,
+                                  Pair<T>* ub, int& pos, int& neg, int& zero) {
+  const int R = (ext + 3) >> 2, ntile = R * (R + 1) / 2;
+  for (int r = tid; r < 2 * RT_UB; r += NT) ub[r] = Pair<T>{T(0), T(0)};
+  int ti[TPT], tj[TPT];
+  T a[TPT][4][4];
+#pragma unroll
+  for (int j = 0; j < TPT; ++j) {
+    const int t = tid + NT * j;
+    ti[j] = -1; tj[j] = 0;
+    if (t < ntile) tri_tile(t, ti[j], tj[j]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = 4 * ti[j] + u, c = 4 * tj[j] + v;
+        a[j][u][v] = (ti[j] >= 0 && r < ext && c <= r) ? entry(r, c) : T(0);
+      }
+  }
+  bar();
+  for (int q = 0; q < npairs; ++q) {
+    const int c0 = 2 * q, c1 = c0 + 1, tq = c0 >> 2;
+    const bool hi = (c0 & 2) != 0;
+    Pair<T>* b = ub + (q & 1) * RT_UB;
+#pragma unroll
+    for (int j = 0; j < TPT; ++j)
+      if (ti[j] >= 0 && tj[j] == tq)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = 4 * ti[j] + u;
+          if (r >= c0 && r < ext)
+            b[r] = Pair<T>{hi ? a[j][u][2] : a[j][u][0], hi ? a[j][u][3] : a[j][u][1]};
+        }
+    bar();
+    const T pa = b[c0].x, pb = b[c1].x, pd = b[c1].y;
+    const T det = pa * pd - pb * pb;
+    T ia, ib, id;
+    if (det != T(0) && isfinite((double)det)) {
+      const T inv = T(1) / det;
+      ia = pd * inv; ib = -pb * inv; id = pa * inv;
+    } else {
+      ia = ib = id = T(0);
+    }
+    if (tid == 0) {
+      Dout[3 * q + 0] = pa; Dout[3 * q + 1] = pb; Dout[3 * q + 2] = pd;
+      pivot_inertia((double)pa, (double)pb, (double)pd, pos, neg, zero);
+    }
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+      if (ti[j] < 0 || 4 * ti[j] + 3 <= c1) continue;   // no live row
+      T l0[4], l1[4], y0[4], y1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const Pair<T> xr = b[4 * ti[j] + u];
+        l0[u] = xr.x * ia + xr.y * ib;
+        l1[u] = xr.x * ib + xr.y * id;
+        const Pair<T> yc = b[4 * tj[j] + u];
+        y0[u] = yc.x; y1[u] = yc.y;
+      }
+      if (tj[j] == tq)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = 4 * ti[j] + u;
+          if (r > c1 && r < ext) {
+            Lout[(size_t)c0 * lds + r] = l0[u];
+            Lout[(size_t)c1 * lds + r] = l1[u];
+          }
+        }
+      if (4 * tj[j] + 3 <= c1) continue;                 // no live column
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          a[j][u][v] = fma(-l1[u], y1[v], fma(-l0[u], y0[v], a[j][u][v]));
+    }
+  }
+  const int cs = 2 * npairs;
+#pragma unroll
+  for (int j = 0; j < TPT; ++j) {
+    if (ti[j] < 0) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = 4 * ti[j] + u, c = 4 * tj[j] + v;
+        if (r < ext && c <= r && c >= cs) sink(r, c, a[j][u][v]);
+      }
+  }
+}
+
+struct CtaBar {
+  __device__ void operator()() const { __syncthreads(); }
+};
+// Barrier over the 128 threads of one half of a 256-thread block (named
+// barrier 1 + half; barrier 0 is __syncthreads).
+struct HalfBar {
+  int id;
+  __device__ void operator()() const {
+    if (id == 1) asm volatile("bar.sync 1, 128;" ::: "memory");
+    else asm volatile("bar.sync 2, 128;" ::: "memory");
+  }
+};
+
+// Shared-memory staging of one element for elem_factor_rt (doubles, then
+// ints): D[4][4], JZ and Wzz [3][n][n], JT and Wzt [3][n][p], Wobj [n][4][4],
+// sigma [4][n], and a descriptor per local index (species, point, constraint,
+// multiplier flag; or the parameter index) that replaces elem_entry's
+// divisions.  All loads are contiguous per element.
+__host__ __device__ inline size_t elem_stage_doubles(int n, int p) {
+  return 16 + 6 * (size_t)n * n + 6 * (size_t)n * p + 20 * (size_t)n;
+}
+__host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
+  return sizeof(double) * elem_stage_doubles(P.n, P.p) + sizeof(int) * (size_t)(P.ext + 1);
+}
+constexpr int DS_THETA = 1 << 28, DS_DUAL = 1 << 24;
+
+// Element condensation (same result as elem_factor_one) with pair_eliminate_rt.
+template <typename T, int NT, int TPT>
+__device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
+                               const double* __restrict__ sigma, double dw, double dc,
+                               const DevFactor<T>& F, int e, Pair<T>* ub, double* stage) {
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext;
+  const int tid = threadIdx.x;
+  const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
+  const size_t nn3 = 3 * (size_t)n * n, np3 = 3 * (size_t)n * p;
+  double* sD = stage;
+  double* sJZ = sD + 16;
+  double* sWzz = sJZ + nn3;
+  double* sJT = sWzz + nn3;
+  double* sWzt = sJT + np3;
+  double* sWobj = sWzt + np3;
+  double* sSig = sWobj + 16 * (size_t)n;
+  int* desc = reinterpret_cast<int*>(sSig + 4 * (size_t)n);
+  for (int i = tid; i < 16; i += NT) sD[i] = P.D[i >> 2][i & 3];
+  for (size_t i = tid; i < nn3; i += NT) {
+    sJZ[i] = E.JZ[(size_t)e * nn3 + i];
+    sWzz[i] = E.Wzz[(size_t)e * nn3 + i];
+  }
+  for (size_t i = tid; i < np3; i += NT) {
+    sJT[i] = E.JT[(size_t)e * np3 + i];
+    sWzt[i] = E.Wzt[(size_t)e * np3 + i];
+  }
+  for (int i = tid; i < 16 * n; i += NT) sWobj[i] = E.Wobj[(size_t)e * 16 * n + i];
+  for (int i = tid; i < 4 * n; i += NT) sSig[i] = sigma ? sigma[(size_t)e * 4 * n + i] : 0.0;
+  for (int a = tid; a < ext; a += NT) {
+    if (a >= m) {
+      desc[a] = DS_THETA | (a - m);
+    } else {
+      const int pa = a >> 1, g = pa / n, s = pa - g * n;
+      desc[a] = s | (grp_point(g) << 16) | (grp_con(g) << 20) | ((a & 1) ? DS_DUAL : 0);
+    }
+  }
+  __syncthreads();
+  // entry (a, b), a >= b: the arithmetic of elem_entry on the staged data
+  auto entry = [&](int a, int b) -> T {
+    const int da = desc[a], db = desc[b];
+    const int sb = db & 0xFFFF;
+    if (da & DS_THETA) {
+      if (db & DS_THETA) return T(0);
+      const int q = da & 0xFFFF;
+      if (!(db & DS_DUAL)) {
+        const int j = (db >> 16) & 15;
+        return j >= 1 ? (T)sWzt[((j - 1) * n + sb) * p + q] : T(0);
+      }
+      const int k = (db >> 20) & 15;
+      return k >= 1 ? (T)sJT[((k - 1) * n + sb) * p + q] : T(0);
+    }
+    const int sa = da & 0xFFFF;
+    const bool adual = da & DS_DUAL, bdual = db & DS_DUAL;
+    if (!adual && !bdual) {
+      const int ja = (da >> 16) & 15, jb = (db >> 16) & 15;
+      double v = 0.0;
+      if (sa == sb) v += sWobj[(sa * NP + ja) * NP + jb];
+      if (ja == jb && ja >= 1) v += sWzz[((ja - 1) * n + sa) * n + sb];
+      if (a == b) v += sSig[ja * n + sa] + dw;
+      return (T)v;
+    }
+    if (adual && bdual) return a == b ? (T)(-dc) : T(0);
+    int kd, sd, jp, sp;
+    if (adual) { kd = (da >> 20) & 15; sd = sa; jp = (db >> 16) & 15; sp = sb; }
+    else { kd = (db >> 20) & 15; sd = sb; jp = (da >> 16) & 15; sp = sa; }
+    if (kd == 0) return (jp == 0 && sd == sp) ? T(1) : T(0);
+    double v = (sd == sp) ? sD[kd * NP + jp] : 0.0;
+    if (jp == kd) v += sJZ[((kd - 1) * n + sd) * n + sp];
+    return (T)v;
+  };
+  T* Aif = F.Aif + (size_t)e * n2 * n2;
+  T* Bif = F.Bif + (size_t)e * n2 * p;
+  double* Sc = F.Scon + (size_t)e * p * p;
+  // trailing block: interface (2n x 2n), its border (p x 2n), parameter part
+  auto sink = [&](int r, int c, T val) {
+    if (r < m) {
+      Aif[(r - i0) * n2 + (c - i0)] = val;
+      Aif[(c - i0) * n2 + (r - i0)] = val;
+    } else if (c < m) {
+      Bif[(c - i0) * p + (r - m)] = val;
+    } else {
+      Sc[(r - m) * p + (c - m)] = (double)val;
+      Sc[(c - m) * p + (r - m)] = (double)val;
+    }
+  };
+  int pos = 0, neg = 0, zero = 0;
+  pair_eliminate_rt<T, NT, TPT>(tid, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+                                F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pos, neg, zero);
+  if (tid == 0) {
+    F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
+  }
+  T* C = F.Cpl + (size_t)e * n * n;
+  for (int idx = tid; idx < n * n; idx += NT) {
+    const int s2 = idx / n, t = idx - s2 * n;
+    C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
+  }
+}
+
+// Threads per block and tiles per thread of elem_factor_rt for an element of
+// size ext: 0 when the block does not fit (elem_factor_one is used).
+template <typename T>
+__host__ __device__ constexpr int rt_threads() { return sizeof(T) == 4 ? 128 : 256; }
+template <typename T>
+__host__ __device__ inline int rt_tiles_per_thread(int ext) {
+  const int R = (ext + 3) >> 2;
+  if (R > RT_MAX_TR) return 0;
+  const int nt = rt_threads<T>(), tpt = (R * (R + 1) / 2 + nt - 1) / nt;
+  return tpt <= (sizeof(T) == 4 ? 4 : 2) ? tpt : 0;
+}
+
+template <typename T, int TPT>
+__global__ void __launch_bounds__(rt_threads<T>())
+k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
+                 DevFactor<T> F) {
+  __shared__ Pair<T> ub[2 * RT_UB];
+  extern __shared__ double stage_dyn[];
+  elem_factor_rt<T, rt_threads<T>(), TPT>(P, E, sigma, dw, dc, F, blockIdx.x, ub, stage_dyn);
+}
+
 // ---- 2. one level of block cyclic reduction -------------------------------------
 // Eliminates the blocks at odd multiples of `stride` (final = 1: block 0 alone).
 // Local order of the extended block: [interface of block i (2n) | z3 of the
@@ -324,21 +586,124 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
   __syncthreads();
 }
 
+// Cyclic-reduction block (same result as bcr_factor_one) with
+// pair_eliminate_rt on one half (128 threads) of the block: tid in [0, 128).
+// Its inputs are first staged in `stage` (T elements, bcr_stage_elems):
+// the block's interface block [2n][2n], its coupling [n][n], the right
+// neighbour's coupling [n][n] and its border [2n][p].
+__host__ __device__ inline size_t bcr_stage_elems(int n, int p) {
+  return 6 * (size_t)n * n + 2 * (size_t)n * p;
+}
+template <typename T, int TPT>
+__device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int stride,
+                              int final_level, int bi, int tid, HalfBar bar, Pair<T>* ub,
+                              T* stage) {
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
+  const int i = final_level ? 0 : stride * (2 * bi + 1);
+  const int L = final_level ? -1 : i - stride;
+  const int R = (!final_level && i + stride < N) ? i + stride : -1;
+  T* Ai = stage;
+  T* Ci = Ai + 4 * n * n;
+  T* CR = Ci + n * n;
+  T* Bi = CR + n * n;
+  {
+    const T* gA = F.Aif + (size_t)i * n2 * n2;
+    const T* gC = F.Cpl + (size_t)i * n * n;
+    const T* gCR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
+    const T* gB = F.Bif + (size_t)i * n2 * p;
+    for (int k = tid; k < 4 * n * n; k += 128) Ai[k] = gA[k];
+    for (int k = tid; k < n * n; k += 128) {
+      Ci[k] = gC[k];
+      CR[k] = gCR ? gCR[k] : T(0);
+    }
+    for (int k = tid; k < n2 * p; k += 128) Bi[k] = gB[k];
+  }
+  bar();
+  auto entry = [&](int a, int b) -> T {
+    if (a < n2) return Ai[a * n2 + b];
+    if (b >= n2) return T(0);
+    if (a < 3 * n)                 // z3 of left neighbour, t = a - 2n
+      return (L >= 0 && (b & 1)) ? Ci[(b >> 1) * n + (a - n2)] : T(0);
+    if (a < 4 * n)                 // c0 of right neighbour, s = a - 3n
+      return (R >= 0 && !(b & 1)) ? CR[(a - 3 * n) * n + (b >> 1)] : T(0);
+    return Bi[b * p + (a - 4 * n)];  // theta row q = a - 4n
+  };
+  // the trailing (Schur) block goes to the neighbours and the parameter part
+  T* AL = L >= 0 ? F.Aif + (size_t)L * n2 * n2 : nullptr;
+  T* BL = L >= 0 ? F.Bif + (size_t)L * n2 * p : nullptr;
+  T* AR = R >= 0 ? F.Aif + (size_t)R * n2 * n2 : nullptr;
+  T* BR = R >= 0 ? F.Bif + (size_t)R * n2 * p : nullptr;
+  T* CRw = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
+  double* Sc = F.Scon + (size_t)(N + i) * p * p;
+  auto sink = [&](int r, int c, T val) {
+    if (r < 3 * n) {                               // z3(L) x z3(L)
+      if (L < 0) return;
+      const int t = r - n2, t2 = c - n2;
+      AL[(2 * t) * n2 + 2 * t2] += val;
+      if (t != t2) AL[(2 * t2) * n2 + 2 * t] += val;
+    } else if (r < 4 * n) {
+      if (R < 0) return;
+      const int s = r - 3 * n;
+      if (c < 3 * n) {                             // c0(R) x z3(L): new coupling
+        CRw[s * n + (c - n2)] = L >= 0 ? val : T(0);
+      } else {                                     // c0(R) x c0(R)
+        const int s2 = c - 3 * n;
+        AR[(2 * s + 1) * n2 + 2 * s2 + 1] += val;
+        if (s != s2) AR[(2 * s2 + 1) * n2 + 2 * s + 1] += val;
+      }
+    } else {
+      const int q = r - 4 * n;
+      if (c < 3 * n) {
+        if (L >= 0) BL[(2 * (c - n2)) * p + q] += val;
+      } else if (c < 4 * n) {
+        if (R >= 0) BR[(2 * (c - 3 * n) + 1) * p + q] += val;
+      } else {
+        const int q2 = c - 4 * n;
+        Sc[q * p + q2] = (double)val;
+        Sc[q2 * p + q] = (double)val;
+      }
+    }
+  };
+  int pos = 0, neg = 0, zero = 0;
+  pair_eliminate_rt<T, 128, TPT>(tid, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
+                                 F.Db + (size_t)i * n * 3, sink, bar, ub, pos, neg, zero);
+  if (tid == 0) {
+    int* in = F.inert + (size_t)(N + i) * 3;
+    in[0] = pos; in[1] = neg; in[2] = zero;
+  }
+}
+
+// Tiles per thread of bcr_factor_rt for P (0: use bcr_factor_one).
+__host__ __device__ inline int bcr_rt_tiles(int bext) {
+  const int R = (bext + 3) >> 2, tpt = (R * (R + 1) / 2 + 127) / 128;
+  return tpt <= 2 ? tpt : 0;
+}
+
 __host__ __device__ inline int bcr_level_blocks(int N, int stride) {
   return (N - stride + 2 * stride - 1) / (2 * stride);
 }
 
-template <typename T>
+template <typename T, int BT>
 __global__ void __launch_bounds__(FBS)
 k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
   extern __shared__ unsigned char smraw[];
-  const int bext = P.bext, ld = odd_ld(bext);
-  T* Lp = reinterpret_cast<T*>(smraw);
-  T* Up = Lp + (size_t)bext * PLD;
-  T* A = use_smem ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
   const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
-  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-    bcr_factor_one<T>(P, F, stride, final_level, bi, A, Lp, Up);
+  if constexpr (BT > 0) {
+    // two blocks of the level per CUDA block, one per half
+    __shared__ Pair<T> ub[2][2 * RT_UB];
+    const int half = threadIdx.x >> 7;
+    T* stage = reinterpret_cast<T*>(smraw) + half * bcr_stage_elems(P.n, P.p);
+    for (int bi = 2 * blockIdx.x + half; bi < nblk; bi += 2 * gridDim.x)
+      bcr_factor_rt<T, BT>(P, F, stride, final_level, bi, threadIdx.x & 127, HalfBar{1 + half},
+                           ub[half], stage);
+  } else {
+    const int bext = P.bext, ld = odd_ld(bext);
+    T* Lp = reinterpret_cast<T*>(smraw);
+    T* Up = Lp + (size_t)bext * PLD;
+    T* A = use_smem ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
+    for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
+      bcr_factor_one<T>(P, F, stride, final_level, bi, A, Lp, Up);
+  }
 }
 
 // ---- 3. parameter Schur complement (FP64) ------------------------------------------
@@ -747,16 +1112,34 @@ __device__ inline const DevFactor<float>& inst_factor<float>(const DevInst& I) {
 template <>
 __device__ inline const DevFactor<double>& inst_factor<double>(const DevInst& I) { return I.F64; }
 
-template <typename T>
+// Element condensation of a batch with elem_factor_rt: one block per element of
+// the work list; instances without flag 4 are condensed inside k_factor_b.
+template <typename T, int TPT>
+__global__ void __launch_bounds__(rt_threads<T>())
+k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+                   const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
+                   const int* __restrict__ flags) {
+  __shared__ Pair<T> ub[2 * RT_UB];
+  extern __shared__ double stage_dyn[];
+  const int t = blockIdx.x;
+  const int k = find_item(pre_elem, A, t);
+  if (!(flags[k] & 4)) return;
+  const DevInst& I = insts[act[k]];
+  elem_factor_rt<T, rt_threads<T>(), TPT>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc,
+                                          inst_factor<T>(I), t - pre_elem[k], ub, stage_dyn);
+}
+
+template <typename T, int BT>
 __global__ void __launch_bounds__(FBS)
 k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
            const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
            const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
-           const int* __restrict__ flags, GridBar* gb, size_t smem_bytes) {
+           const int* __restrict__ flags, GridBar* gb, size_t smem_bytes, int bcr_full) {
   extern __shared__ unsigned char smraw[];
   // 1. element condensation
   for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
     const int k = find_item(pre_elem, A, t);
+    if (flags[k] & 4) continue;   // condensed by k_elem_factor_rt_b
     const DevInst& I = insts[act[k]];
     const DevFactor<T>& F = inst_factor<T>(I);
     const int ext = I.P.ext, ld = odd_ld(ext);
@@ -771,8 +1154,25 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     const int* pre = pre_lv + (size_t)lv * (A + 1);
     const bool fin = lv == maxL;
     const int tot = fin ? A : pre[A];
-    for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+    if constexpr (BT > 0) {
+      // instances with flag 8: two blocks of the level per CUDA block
+      __shared__ Pair<T> ubh[2][2 * RT_UB];
+      const int half = threadIdx.x >> 7;
+      for (int t = 2 * blockIdx.x + half; t < tot; t += 2 * gridDim.x) {
+        const int k = fin ? t : find_item(pre, A, t);
+        if (!(flags[k] & 8)) continue;
+        const DevInst& I = insts[act[k]];
+        // each half owns a fixed half of the dynamic shared memory (instances
+        // of different sizes may share the block)
+        T* stage = reinterpret_cast<T*>(smraw + half * ((smem_bytes / 2) & ~size_t(15)));
+        bcr_factor_rt<T, BT>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
+                             fin ? 0 : t - pre[k], threadIdx.x & 127, HalfBar{1 + half}, ubh[half],
+                             stage);
+      }
+    }
+    for (int t = blockIdx.x; bcr_full && t < tot; t += gridDim.x) {
       const int k = fin ? t : find_item(pre, A, t);
+      if (BT > 0 && (flags[k] & 8)) continue;
       const DevInst& I = insts[act[k]];
       const DevFactor<T>& F = inst_factor<T>(I);
       const int bext = I.P.bext, ld = odd_ld(bext);
@@ -909,9 +1309,20 @@ size_t factor_work_elems(const DevProb& P, int n_slabs) {
 template <typename T>
 cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
                                double dc, const DevFactor<T>& F, cudaStream_t st) {
+  const int tpt = rt_tiles_per_thread<T>(P.ext);
+  if (tpt > 0) {
+    const size_t sm = elem_stage_bytes(P);
+    auto kern = tpt == 1 ? k_elem_factor_rt<T, 1> : tpt == 2 ? k_elem_factor_rt<T, 2>
+              : tpt == 3 ? k_elem_factor_rt<T, 3> : k_elem_factor_rt<T, 4>;
+    if (sm > SMEM_OPTIN_ABOVE)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
+    kern<<<P.N, rt_threads<T>(), sm, st>>>(P, E, sigma, dw, dc, F);
+    return cudaGetLastError();
+  }
   bool es = elem_uses_smem<T>(P);
   size_t sm = elem_factor_smem<T>(P, es);
-  if (sm > 48 * 1024)
+  if (sm > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int grid = es ? P.N : std::min(P.N, F.n_slabs);
   count_launch();
@@ -950,19 +1361,29 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   const size_t sms = sizeof(double) * ((size_t)P.p * P.p + P.p);
   cudaError_t e;
   if ((e = launch_elem_factor<T>(P, E, sigma, dw, dc, F, st)) != cudaSuccess) return e;
-  if (smb > 48 * 1024)
-    cudaFuncSetAttribute(k_bcr_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-  for (int s = 1; s < P.N; s *= 2) {
-    int nblk = bcr_level_blocks(P.N, s);
-    int g = bs ? nblk : std::min(nblk, F.n_slabs);
+  const int bt = bcr_rt_tiles(P.bext);
+  auto bcr_level = [&](int s, int fin) -> cudaError_t {
+    const int nblk = fin ? 1 : bcr_level_blocks(P.N, s);
+    const size_t smr = 2 * sizeof(T) * bcr_stage_elems(P.n, P.p);
     count_launch();
-    k_bcr_factor<T><<<g, FBS, smb, st>>>(P, F, s, 0, bs ? 1 : 0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  count_launch();
-  k_bcr_factor<T><<<1, FBS, smb, st>>>(P, F, 1, 1, bs ? 1 : 0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (sms > 48 * 1024)
+    if (bt == 1 || bt == 2) {
+      auto kern = bt == 1 ? k_bcr_factor<T, 1> : k_bcr_factor<T, 2>;
+      if (smr > SMEM_OPTIN_ABOVE)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+      kern<<<(nblk + 1) / 2, FBS, smr, st>>>(P, F, s, fin, 1);
+    } else {
+      if (smb > SMEM_OPTIN_ABOVE)
+        cudaFuncSetAttribute(k_bcr_factor<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smb);
+      const int g = bs ? nblk : std::min(nblk, F.n_slabs);
+      k_bcr_factor<T, 0><<<g, FBS, smb, st>>>(P, F, s, fin, bs ? 1 : 0);
+    }
+    return cudaGetLastError();
+  };
+  for (int s = 1; s < P.N; s *= 2)
+    if ((e = bcr_level(s, 0)) != cudaSuccess) return e;
+  if ((e = bcr_level(1, 1)) != cudaSuccess) return e;
+  if (sms > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
   if ((e = launch_chunk_sums(F.Scon, 2 * P.N, P.p * P.p, F.chunkS, st)) != cudaSuccess) return e;
   count_launch();
@@ -977,11 +1398,11 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
   cudaError_t e;
   size_t sme = sizeof(T) * (size_t)P.ext * SOLVE_WARPS;
   size_t smb = sizeof(T) * (size_t)P.bext * SOLVE_WARPS;
-  if (sme > 48 * 1024) {
+  if (sme > SMEM_OPTIN_ABOVE) {
     cudaFuncSetAttribute(k_elem_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme);
     cudaFuncSetAttribute(k_elem_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme);
   }
-  if (smb > 48 * 1024) {
+  if (smb > SMEM_OPTIN_ABOVE) {
     cudaFuncSetAttribute(k_bcr_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     cudaFuncSetAttribute(k_bcr_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
   }
@@ -1025,16 +1446,29 @@ template <typename T>
 cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                             const int* pre_lv, int maxL, const int* pre_cs,
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
-                            int grid_cap, cudaStream_t st) {
+                            int grid_cap, int rt_tpt, size_t rt_smem, int tot_elem, int bcr_tpt,
+                            int bcr_full, cudaStream_t st) {
   if (A == 0) return cudaSuccess;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_factor_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int grid = coop_grid(k_factor_b<T>, FBS, smem, grid_cap);
+  if (rt_tpt > 0 && tot_elem > 0) {
+    if (rt_tpt > 4) return cudaErrorInvalidValue;
+    auto kern = rt_tpt == 1 ? k_elem_factor_rt_b<T, 1> : rt_tpt == 2 ? k_elem_factor_rt_b<T, 2>
+              : rt_tpt == 3 ? k_elem_factor_rt_b<T, 3> : k_elem_factor_rt_b<T, 4>;
+    if (rt_smem > SMEM_OPTIN_ABOVE)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rt_smem);
+    count_launch();
+    kern<<<tot_elem, rt_threads<T>(), rt_smem, st>>>(insts, act, A, pre_elem, prm, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  auto kern = bcr_tpt == 1 ? k_factor_b<T, 1> : bcr_tpt == 2 ? k_factor_b<T, 2> : k_factor_b<T, 0>;
+  if (smem > SMEM_OPTIN_ABOVE)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = coop_grid(kern, FBS, smem, grid_cap);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
-                  (void*)&pre_cs, (void*)&prm, (void*)&flags, &gb, &smem};
+                  (void*)&pre_cs, (void*)&prm, (void*)&flags, &gb, &smem, &bcr_full};
   count_launch();
-  return cudaLaunchCooperativeKernel((void*)k_factor_b<T>, dim3(grid), dim3(FBS), args, smem, st);
+  return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(FBS), args, smem, st);
 }
 
 template <typename T>
@@ -1044,7 +1478,7 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
   if (A == 0) return cudaSuccess;
   size_t smem = std::max(sizeof(T) * (size_t)per_warp * (FBS / 32),
                          sizeof(double) * (size_t)std::max(max_p, 1));
-  if (smem > 48 * 1024)
+  if (smem > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(k_solve_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want);
   if (grid < 1) return cudaErrorInvalidConfiguration;
@@ -1056,10 +1490,21 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
 
 template cudaError_t launch_factor_b<float>(const DevInst*, const int*, int, const int*,
                                             const int*, int, const int*, const InstParams*,
-                                            const int*, GridBar*, size_t, int, cudaStream_t);
+                                            const int*, GridBar*, size_t, int, int, size_t, int,
+                                            int, int, cudaStream_t);
 template cudaError_t launch_factor_b<double>(const DevInst*, const int*, int, const int*,
                                              const int*, int, const int*, const InstParams*,
-                                             const int*, GridBar*, size_t, int, cudaStream_t);
+                                             const int*, GridBar*, size_t, int, int, size_t, int,
+                                             int, int, cudaStream_t);
+int bcr_rt_tiles_of(const DevProb& P) { return bcr_rt_tiles(P.bext); }
+size_t elem_rt_stage_bytes(const DevProb& P) { return elem_stage_bytes(P); }
+size_t bcr_rt_stage_bytes(const DevProb& P, bool f32) {
+  const size_t one = (f32 ? sizeof(float) : sizeof(double)) * bcr_stage_elems(P.n, P.p);
+  return 2 * ((one + 15) & ~size_t(15));
+}
+int elem_rt_tiles(const DevProb& P, bool f32) {
+  return f32 ? rt_tiles_per_thread<float>(P.ext) : rt_tiles_per_thread<double>(P.ext);
+}
 template cudaError_t launch_solve_b<float>(const DevInst*, const int*, int, const int*, const int*,
                                            int, const int*, int, int, GridBar*, int, int,
                                            cudaStream_t);

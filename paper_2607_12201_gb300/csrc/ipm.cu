@@ -462,7 +462,7 @@ cudaError_t launch_forward_sweep(collo_problem* pr) {
   const DevProb& P = pr->P;
   if (KC * P.n <= WSWEEP) {
     size_t sm = sweep_warp_smem_bytes(P);
-    if (sm > 48 * 1024)
+    if (sm > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_forward_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
     k_forward_sweep_warp<<<1, 32, sm, pr->stream>>>(P, pr->x, pr->fails);
@@ -470,7 +470,7 @@ cudaError_t launch_forward_sweep(collo_problem* pr) {
   }
   const bool insm = pr->sweep_work == nullptr;
   size_t sm = sweep_smem_bytes(pr->P, insm);
-  if (sm > 48 * 1024)
+  if (sm > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(k_forward_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   count_launch();
   k_forward_sweep<<<1, SWEEP_BS, sm, pr->stream>>>(pr->P, pr->x, pr->fails, pr->sweep_work);
@@ -650,7 +650,7 @@ cudaError_t launch_sweep_b(const DevInst* insts, const int* act_warp, int A_warp
                            size_t smem_warp, const int* act_cta, int A_cta, size_t smem_cta,
                            cudaStream_t st) {
   if (A_warp > 0) {
-    if (smem_warp > 48 * 1024)
+    if (smem_warp > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_sweep_warp_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp);
     count_launch();
     k_sweep_warp_b<<<A_warp, 32, smem_warp, st>>>(insts, act_warp);
@@ -658,7 +658,7 @@ cudaError_t launch_sweep_b(const DevInst* insts, const int* act_warp, int A_warp
     if (e != cudaSuccess) return e;
   }
   if (A_cta > 0) {
-    if (smem_cta > 48 * 1024)
+    if (smem_cta > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_sweep_cta_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta);
     count_launch();
     k_sweep_cta_b<<<A_cta, SWEEP_BS, smem_cta, st>>>(insts, act_cta);

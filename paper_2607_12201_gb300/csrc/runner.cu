@@ -42,6 +42,10 @@ struct Plan {
   size_t smem_eval = 0, smem_f[2] = {0, 0}, smem_sw_w = 0, smem_sw_c = 0;
   int cap_f[2] = {1 << 30, 1 << 30};
   int per_warp[2] = {0, 0};
+  int rt_tpt[2] = {0, 0};   // tiles per thread of the register-tiled element kernel
+  size_t rt_smem = 0;       // its dynamic shared memory
+  int bcr_tpt = 0;          // ... of the register-tiled cyclic-reduction blocks
+  int bcr_full = 0;         // some instance's reduction blocks use the whole-block path
 
   const int* act() const { return d_int + off_act; }
   const int* pre_elem() const { return d_int + off_elem; }
@@ -191,20 +195,37 @@ struct Runner {
       const bool f32 = prec == 1;
       const size_t off = o;
       size_t smem = 0;
-      int cap = 1 << 30, pw = 0;
+      int cap = 1 << 30, pw = 0, tpt = 0, btpt = 0, bfull = 0;
+      size_t rts = 0;
       for (int k = 0; k < A; ++k) {
         const DevProb& Q = P(slots[k]);
         const size_t se = f32 ? elem_factor_smem<float>(Q, true) : elem_factor_smem<double>(Q, true);
         const size_t sb = f32 ? bcr_factor_smem<float>(Q, true) : bcr_factor_smem<double>(Q, true);
         const size_t ve = f32 ? elem_factor_smem<float>(Q, false) : elem_factor_smem<double>(Q, false);
         const size_t vb = f32 ? bcr_factor_smem<float>(Q, false) : bcr_factor_smem<double>(Q, false);
+        const int rt = elem_rt_tiles(Q, f32), brt = bcr_rt_tiles_of(Q);
         int fl = 0;
-        size_t need = std::max(ve, vb);
-        if (se <= KSMEM_LIMIT) { fl |= 1; need = std::max(need, se); }
-        if (sb <= KSMEM_LIMIT) { fl |= 2; need = std::max(need, sb); }
+        size_t need = 0;
+        if (rt > 0) {                  // elements condensed by the register-tiled kernel
+          fl |= 1 | 4;
+          tpt = std::max(tpt, rt);
+          rts = std::max(rts, elem_rt_stage_bytes(Q));
+        } else {
+          need = std::max(need, ve);
+          if (se <= KSMEM_LIMIT) { fl |= 1; need = std::max(need, se); }
+        }
+        if (brt > 0) {                 // register-tiled reduction blocks
+          fl |= 2 | 8;
+          btpt = std::max(btpt, brt);
+          need = std::max(need, bcr_rt_stage_bytes(Q, f32));
+        } else {
+          bfull = 1;
+          need = std::max(need, vb);
+          if (sb <= KSMEM_LIMIT) { fl |= 2; need = std::max(need, sb); }
+        }
         const size_t ss = sizeof(double) * ((size_t)Q.p * Q.p + Q.p);
         if (ss <= KSMEM_LIMIT) need = std::max(need, ss);
-        if (fl != 3) cap = std::min(cap, probs[slots[k]]->n_slabs);
+        if ((fl & 3) != 3) cap = std::min(cap, probs[slots[k]]->n_slabs);
         smem = std::max(smem, need);
         h[off + k] = fl;
         pw = std::max(pw, std::max(Q.ext, Q.bext));
@@ -214,6 +235,10 @@ struct Runner {
       pl.smem_f[prec] = smem;
       pl.cap_f[prec] = cap;
       pl.per_warp[prec] = pw;
+      pl.rt_tpt[prec] = tpt;
+      pl.rt_smem = rts;
+      pl.bcr_tpt = btpt;
+      pl.bcr_full = bfull;
     }
     // forward-sweep lists and eval shared memory
     pl.off_sw_w = o;
@@ -309,11 +334,15 @@ struct Runner {
     if (p)
       e = launch_factor_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                  pl.pre_cs_s(), pl.d_prm, pl.flags(1), gbar, pl.smem_f[1],
-                                 std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)), stream);
+                                 std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)),
+                                 pl.rt_tpt[1], pl.rt_smem, pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
+                                 stream);
     else
       e = launch_factor_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                   pl.pre_cs_s(), pl.d_prm, pl.flags(0), gbar, pl.smem_f[0],
-                                  std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)), stream);
+                                  std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)),
+                                  pl.rt_tpt[0], pl.rt_smem, pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
+                                  stream);
     COLLO_CUDA(e);
     return COLLO_OK;
   }
