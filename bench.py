@@ -4,23 +4,26 @@
 Workload: the 10-species / 20-reaction random mass-action network on
 N = 400 Radau elements (K = 3), 4 observed species x 50 times, T = 20,
 seed 3 (``workloads.config2()``): 16 020 primal unknowns, 16 000 constraints,
-20 log10 rate constants, solved from B seeded starting points
-theta_true + U[-0.1, 0.1] (a multistart run, ``--batch``, default 64).
+20 log10 rate constants, solved from Q seeded starting points
+theta_true + U[-0.1, 0.1] (a multistart run; ``--queue``, default 256).
 
-A timed step is one batched solve: all B starts advance together, one Newton
-step per iteration of the lock-step driver, every phase one launch over all
-unfinished instances, in the mixed-precision path (FP32 element
-factorization and block cyclic reduction, FP64 parameter Schur complement,
-residuals and refinement, FP64 factorization once mu < 1e-6).  ``value`` =
-Newton steps per second summed over the batch.  Beside it: the same path and
-the plain FP64 path on a single instance, per-instance latency percentiles,
-an end-to-end number through host buffers, the dominant kernel's roofline,
+A timed step serves the Q starts through the continuous-batching server
+(``collo_server_*``) with ``--slots`` (default 64) slots: all Q are submitted
+at once, admitted as slots free up (in groups of ``--admit``), and every
+server step advances all admitted solves by one Newton step in batched
+launches, in the mixed-precision path (FP32 element factorization and block
+cyclic reduction, FP64 parameter Schur complement, residuals and refinement,
+FP64 factorization once mu < 1e-6).  ``value`` = Newton steps per second over
+all Q solves.  Beside it: one lock-step batch of ``--slots`` starts (no
+refill), the same path and the plain FP64 path on a single instance,
+per-solve latency percentiles, the parameter agreement with FP64 solves, an
+end-to-end number through host buffers, the dominant kernel's roofline and
 the CPU oracle.  Between timed steps the L2 cache is flushed (256 MiB write).
 
 ``--impl reference`` times the CPU oracle instead (a bounded sample: each step
 is the oracle's initial point plus two Newton iterations of one instance).
 
-Multi-GPU (torchrun, one process per GPU): each rank solves its own batch
+Multi-GPU (torchrun, one process per GPU): each rank serves its own queue
 with no collective on the data path (weak scaling); the timed region is
 bracketed by barriers and the slowest rank's time is used.
 """
@@ -40,9 +43,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = ("massaction_n10_r20_N400_K3 x {B} multistart (config 2: 10 species, 20 reactions, "
-            "N=400, T=20, seed 3; starts theta_true + U[-0.1,0.1])")
-METRIC = "Newton steps/s (mixed-precision batched IPM path, config 2 multistart)"
+WORKLOAD = ("massaction_n10_r20_N400_K3 x {Q} multistart solves served with {S} slots "
+            "(config 2: 10 species, 20 reactions, N=400, T=20, seed 3; "
+            "starts theta_true + U[-0.1,0.1])")
+METRIC = "Newton steps/s (mixed-precision continuous-batching IPM path, config 2 multistart)"
 
 
 def parse_args():
@@ -53,7 +57,12 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=64,
+                    help="instances of --only-batch")
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--queue", type=int, default=256)
+    ap.add_argument("--admit", type=int, default=16,
+                    help="admit waiting solves in groups of at least this many free slots")
     ap.add_argument("--only-solve", choices=["mixed", "fp64"], default=None,
                     help="run one single-instance solve and exit (for profiler launch lists)")
     ap.add_argument("--only-batch", action="store_true",
@@ -203,6 +212,12 @@ def measured_peaks():
         return {}
 
 
+def rate_rel_err(theta, theta_ref):
+    """Largest relative error of the rate constants k = 10**theta."""
+    import numpy as np
+    return float(np.max(np.abs(np.expm1(np.log(10.0) * (np.asarray(theta) - theta_ref)))))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -215,28 +230,34 @@ def run_ours(args):
     torch.cuda.set_device(local)
     init_dist(world, "nccl")
     inst = workloads.config2()
-    nb = args.batch
-    starts = workloads.multistart_thetas(inst, nb, seed=2002 + rank)
-    probs = [collo.Problem(inst, device=local) for _ in range(nb)]
-    stream = torch.cuda.ExternalStream(probs[0].stream)
+    S, Q = args.slots, args.queue
+    starts = workloads.multistart_thetas(inst, Q, seed=2002 + rank)
+    probs = [collo.Problem(inst, device=local) for _ in range(Q)]
+    server = collo.Server(S, device=local, precision=collo.MIXED)
+    server.set_admission(args.admit)
+    sstream = torch.cuda.ExternalStream(server.stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def flush_l2(i):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
 
-    def timed_batch(prec):
+    def timed_serve():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = collo.batch_solve(probs, theta0s=starts, precision=prec)
-        e1.record(stream)
+        e0.record(sstream)
+        tickets = [server.submit(p, theta0=th) for p, th in zip(probs, starts)]
+        while True:
+            act, wait = server.step()
+            if act == 0 and wait == 0:
+                break
+        e1.record(sstream)
         e1.synchronize()
-        return res, e0.elapsed_time(e1)
+        return [server.poll(t) for t in tickets], e0.elapsed_time(e1)
 
     for i in range(args.warmup):
         flush_l2(i)
-        timed_batch(collo.MIXED)
+        timed_serve()
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -245,7 +266,7 @@ def run_ours(args):
     its, ms_list, statuses, lat, last = 0, [], [], [], None
     for i in range(args.steps):
         flush_l2(i)
-        res, ms = timed_batch(collo.MIXED)
+        res, ms = timed_serve()
         its += sum(r["iterations"] for r in res)
         ms_list.append(ms)
         statuses += [r["status"] for r in res]
@@ -257,63 +278,73 @@ def run_ours(args):
     clk = clocks.stop()
     t_total = reduce_max(sum(ms_list), world)
     its_total = reduce_sum(float(its), world)
-    solves_total = reduce_sum(float(args.steps * nb), world)
+    solves_total = reduce_sum(float(args.steps * Q), world)
+    conv_total = reduce_sum(float(sum(1 for s_ in statuses if s_ in (collo.OK, collo.ACCEPTABLE))),
+                            world)
     value = its_total / (t_total * 1e-3)
+
+    # one lock-step batch of S starts (no refill), on the problems' own streams
+    bstream = torch.cuda.ExternalStream(probs[0].stream)
+    flush_l2(0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(bstream)
+    bres = collo.batch_solve(probs[:S], theta0s=starts[:S], precision=collo.MIXED)
+    e1.record(bstream)
+    e1.synchronize()
+    b_ms = e0.elapsed_time(e1)
+    b_its = sum(r["iterations"] for r in bres)
 
     # single-instance paths on the same GPU: mixed and the plain FP64 path
     one = probs[0]
     single = {}
     for name, prec in [("mixed", collo.MIXED), ("fp64", collo.FP64)]:
         one.ipm_solve(theta0=starts[0], precision=prec, want_x=False)
-        ms_s, its_s, th = [], 0, None
+        ms_s, its_s = [], 0
         for i in range(3):
             flush_l2(i)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(bstream)
             r = one.ipm_solve(theta0=starts[0], precision=prec, want_x=False)
-            e1.record(stream)
+            e1.record(bstream)
             e1.synchronize()
             ms_s.append(e0.elapsed_time(e1))
             its_s += r["iterations"]
-            th = r["theta"]
         single[name] = {"newton_steps_per_s": its_s / (sum(ms_s) * 1e-3),
                         "solves_per_s": len(ms_s) / (sum(ms_s) * 1e-3),
-                        "ms_per_solve": sum(ms_s) / len(ms_s), "theta": th}
-    # parameter error of the batched mixed path against single-instance FP64 solves
-    perr = 0.0
-    for j in range(min(4, nb)):
+                        "ms_per_solve": sum(ms_s) / len(ms_s)}
+    # parameter agreement of the served mixed solves with single FP64 solves
+    perr, n_cmp = 0.0, 0
+    for j in range(min(8, Q)):
+        if last[j]["status"] not in (collo.OK, collo.ACCEPTABLE):
+            continue
         r64 = one.ipm_solve(theta0=starts[j], precision=collo.FP64, want_x=False)
         if r64["status"] in (collo.OK, collo.ACCEPTABLE):
-            th = last[j]["theta"]
-            perr = max(perr, float(np.max(np.abs(th - r64["theta"]) /
-                                          np.maximum(np.abs(r64["theta"]), 1e-12))))
+            perr = max(perr, rate_rel_err(last[j]["theta"], r64["theta"]))
+            n_cmp += 1
 
-    # dominant kernel (batched factorization) and phase timings with CUDA events
-    timed_batch(collo.MIXED)
-    ph = {"factor_fp32": collo.batch_time_phase(probs, 1, collo.MIXED, reps=5),
-          "solve_fp32": collo.batch_time_phase(probs, 2, collo.MIXED, reps=5),
-          "eval": collo.batch_time_phase(probs, 3, collo.MIXED, reps=5)}
-    fl32, by32 = factor_work(inst.n, inst.p, inst.N, 4)
-    fl32 *= nb
-    by32 *= nb
+    # phase timings at S instances (CUDA events inside the library)
+    ph = {"factor_fp32": collo.batch_time_phase(probs[:S], 1, collo.MIXED, reps=5),
+          "factor_fp32_elements": collo.batch_time_phase(probs[:S], 4, collo.MIXED, reps=5),
+          "factor_fp32_reduction_schur": collo.batch_time_phase(probs[:S], 5, collo.MIXED, reps=5),
+          "solve_fp32": collo.batch_time_phase(probs[:S], 2, collo.MIXED, reps=5),
+          "eval": collo.batch_time_phase(probs[:S], 3, collo.MIXED, reps=5)}
     peak32 = collo.alu_peak(collo.MIXED)
     peak64 = collo.alu_peak(collo.FP64)
-    hbm = measured_peaks().get("hbm_gbs")
-    t_f = ph["factor_fp32"] * 1e-3
-    ach_fl, ach_by = fl32 / t_f / 1e12, by32 / t_f / 1e9
-    if hbm and by32 / (hbm * 1e9) > fl32 / (peak32 * 1e12):
-        roof = {"bound": "hbm", "achieved": ach_by, "peak": hbm, "unit": "GB/s",
-                "frac": ach_by / hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        roof = {"bound": "alu", "achieved": ach_fl, "peak": peak32, "unit": "TFLOP/s",
-                "frac": ach_fl / peak32,
-                "peak_source": "measured live: FP32 FFMA throughput probe (collo_alu_peak)"}
-    roof.update({"kernel": f"k_factor_b<float> (batched factorization, {nb} instances)",
-                 "algorithmic_flops": fl32, "algorithmic_bytes": by32,
-                 "ms": ph["factor_fp32"], "traffic": None,
-                 "other_roof": {"alu_tflops": ach_fl, "alu_peak_tflops": peak32,
-                                "hbm_gbs": ach_by, "hbm_peak_gbs": hbm}})
+    # dominant kernel: the FP32 element condensation (FP32 FMA bound)
+    fl_e, by_e = elem_factor_work(inst.n, inst.p, inst.N, 4)
+    fl_e *= S
+    by_e *= S
+    ach = fl_e / (ph["factor_fp32_elements"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+            "frac": ach / peak32, "traffic": None,
+            "peak_source": "measured FP32 FFMA throughput of this GPU (collo_alu_peak)",
+            "kernel": f"k_elem_factor_rt_b<float> (element condensation, {S} instances)",
+            "algorithmic_flops": fl_e, "algorithmic_bytes": by_e,
+            "ms": ph["factor_fp32_elements"],
+            "hbm": {"achieved_gbs": by_e / (ph["factor_fp32_elements"] * 1e-3) / 1e9,
+                    "peak_gbs": measured_peaks().get("hbm_gbs")}}
 
     out = {
         "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
@@ -321,20 +352,27 @@ def run_ours(args):
         "ms_per_step": t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32 factor + fp64 residual/refinement",
         "data": "synthetic (seeded mass-action network, noisy observations, seeded starts)",
-        "config": {"workload": WORKLOAD.format(B=nb), "batch": nb,
-                   "step": f"one batched solve of {nb} starts from theta0 to convergence",
+        "config": {"workload": WORKLOAD.format(Q=Q, S=S), "queue": Q, "slots": S,
+                   "admit_group": args.admit,
+                   "step": f"serve {Q} starts from theta0 to a final status",
                    "newton_steps_per_step": its / max(args.steps, 1),
                    "n_x_per_instance": one.n_x, "n_c_per_instance": one.n_c, "p": inst.p,
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world} (independent batches)"},
+                   "parallelism": f"replicas x{world} (independent queues)"},
         "solves_per_s": solves_total / (t_total * 1e-3),
+        "converged_solves_per_s": conv_total / (t_total * 1e-3),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "what": "per-instance time from batch start to that instance's result"},
-        "status_counts": {str(s): statuses.count(s) for s in sorted(set(statuses))},
-        "single_instance": {k: {kk: vv for kk, vv in v.items() if kk != "theta"}
-                            for k, v in single.items()},
+                       "what": "per-solve service time, admission to final status"},
+        "status_counts": {str(s_): statuses.count(s_) for s_ in sorted(set(statuses))},
+        "lockstep_batch": {"instances": S, "newton_steps_per_s": b_its / (b_ms * 1e-3),
+                           "ms": b_ms, "what": f"one collo_batch_solve of {S} starts, no refill"},
+        "single_instance": single,
         "speedup_vs_fp64_single": value / single["fp64"]["newton_steps_per_s"],
-        "param_rel_err_vs_fp64": perr,
+        "solves_speedup_vs_fp64_single": (solves_total / (t_total * 1e-3))
+                                         / single["fp64"]["solves_per_s"],
+        "param_rel_err_vs_fp64": {"value": perr, "compared": n_cmp,
+                                  "what": "max |k_mixed/k_fp64 - 1| over rate constants "
+                                          "k = 10^theta, starts where both paths converged"},
         "phases_ms": ph, "roofline": roof,
         "peaks_tflops": {"fp32_ffma": peak32, "fp64_dfma": peak64},
         "gpu_launches": launches, "clocks": clk,
@@ -342,14 +380,19 @@ def run_ours(args):
     if not args.no_e2e:
         keep = [inst.react, inst.prod, inst.pidx, inst.kfix, inst.x0, inst.theta_lo,
                 inst.theta_hi, inst.obs_t, inst.obs_s, inst.obs_y, inst.obs_sigma]
-        h2d = nb * int(sum(np.asarray(a).nbytes for a in keep)) + 8 * inst.p * nb
+        h2d = Q * int(sum(np.asarray(a).nbytes for a in keep)) + 8 * inst.p * Q
         tot, its_e = 0.0, 0
-        k_e = max(1, min(args.steps, 3))
+        k_e = max(1, min(args.steps, 2))
         for i in range(k_e):
             flush_l2(i)
             t0 = time.perf_counter()
-            ps = [collo.Problem(inst, device=local) for _ in range(nb)]
-            res = collo.batch_solve(ps, theta0s=starts, precision=collo.MIXED)
+            ps = [collo.Problem(inst, device=local) for _ in range(Q)]
+            tk = [server.submit(p, theta0=th) for p, th in zip(ps, starts)]
+            while True:
+                act, wait = server.step()
+                if act == 0 and wait == 0:
+                    break
+            res = [server.poll(t) for t in tk]
             for pb in ps:
                 pb.close()
             t1 = time.perf_counter()
@@ -358,13 +401,14 @@ def run_ours(args):
         tot = reduce_max(tot, world)
         its_e = reduce_sum(float(its_e), world)
         out["e2e"] = {"value": its_e / tot, "unit": "Newton steps/s",
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nb * (8 * inst.p + 64),
-                      "what": f"{nb} x collo_problem_create from host arrays + "
-                              "collo_batch_solve + theta* read back, per step", "steps": k_e}
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Q * (8 * inst.p + 64),
+                      "what": f"{Q} x collo_problem_create from host arrays + serving + "
+                              "theta* read back, per step", "steps": k_e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst, iters=6)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    server.close()
     for pb in probs:
         pb.close()
 
@@ -405,7 +449,7 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
-           "config": {"workload": WORKLOAD.format(B=args.batch),
+           "config": {"workload": WORKLOAD.format(Q=args.queue, S=args.slots),
                       "step": f"oracle initial point + {per} Newton iterations of one start"},
            "cpu_baseline": {"value": v, "unit": "Newton steps/s", "cores": cores,
                             "kind": "oracle",

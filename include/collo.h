@@ -171,7 +171,11 @@ typedef struct collo_ipm_options {
   double max_wall_time;       /* seconds, default 3600 (paper's 1 h cap)          */
   int precision;              /* COLLO_PRECISION_*                                 */
   double mixed_mu_switch;     /* MIXED: use FP64 factorization once mu < this
-                                 (default 1e-6); 0 = never switch                   */
+                                 (default 1e-6; 0 = never by mu).  Independently, a
+                                 MIXED solve whose refinement ends above a relative
+                                 residual of 1e-6 after refine_max sweeps redoes
+                                 that step with an FP64 factorization and keeps
+                                 FP64 from then on                               */
   int refine_max;             /* max iterative-refinement sweeps (default 10)      */
   double refine_tol;          /* stop refining at ||r||/||b|| <= this (1e-10)       */
   int verbose;                /* print an iteration log to stdout                  */
@@ -184,7 +188,8 @@ typedef struct collo_result {
   int factorizations;         /* KKT factorizations (inertia corrections included) */
   int line_search_trials;
   int refinement_sweeps;      /* FP64 iterative-refinement sweeps over all steps */
-  int reserved_i;
+  int fp64_factorizations;    /* of the factorizations, those in FP64 (MIXED: after a
+                                 mu switch or a refinement failure)              */
   double phi;                 /* objective at the final iterate */
   double kkt_error;           /* scaled optimality error E_0 at the final iterate */
   double mu;                  /* final barrier parameter */
@@ -289,7 +294,9 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
 /* Measurement hook for batches: re-runs one batched phase of `count`
  * problems (phase 1 factorization in `precision` with each problem's last
  * regularisation, 2 solve without refinement, 3 evaluation with derivatives at
- * each problem's current iterate) reps times between CUDA events and returns
+ * each problem's current iterate, 4 the element-condensation part of phase 1
+ * alone, 5 the rest of phase 1: cyclic reduction and parameter Schur
+ * complement) reps times between CUDA events and returns
  * the average milliseconds per launch.  Problems must have been evaluated
  * (e.g. by a solve). */
 collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
@@ -311,6 +318,23 @@ collo_status collo_server_submit(collo_server* server, collo_problem* prob, cons
                                  long long* ticket);
 collo_status collo_server_step(collo_server* server, int* n_active, int* n_waiting);
 collo_status collo_server_poll(collo_server* server, long long ticket, collo_result* result);
+/* Admission grouping: collo_server_step admits waiting problems only when at
+ * least min_free_slots slots are free (or no slot is busy); default 1.  Each
+ * admission round runs the new problems' forward sweeps before the step, so
+ * grouping trades idle slots for fewer rounds.  INVALID_ARG if < 1. */
+collo_status collo_server_set_admission(collo_server* server, int min_free_slots);
+/* The CUDA stream (cudaStream_t) all of the server's work is queued on. */
+void* collo_server_stream(collo_server* server);
+
+/* Measurement hook: with the environment variable COLLO_PROFILE=1 set before
+ * the first solve, the IPM driver synchronises its stream at each phase
+ * boundary and accumulates host wall milliseconds per phase (0 derivatives
+ * and optimality measures, 1 right-hand sides, 2 factorizations with inertia
+ * correction, 3 solves with refinement, 4 step sizes, 5 line search,
+ * 6 step update, 7 server admission) and the rounds of phases 2, 3, 5 and 7.
+ * Copies min(n, 8) entries into ms / rounds (either may be NULL), zeroes the
+ * totals if reset != 0, and returns 8 when profiling is on, else 0. */
+int collo_phase_profile(double* ms, long long* rounds, int n, int reset);
 void collo_server_destroy(collo_server* server);
 
 /* Collocation forward sweep at theta (the IPM's initial states): writes

@@ -86,7 +86,7 @@ class IpmOptions(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("factorizations", C.c_int),
                 ("line_search_trials", C.c_int), ("refinement_sweeps", C.c_int),
-                ("reserved_i", C.c_int), ("phi", C.c_double), ("kkt_error", C.c_double),
+                ("fp64_factorizations", C.c_int), ("phi", C.c_double), ("kkt_error", C.c_double),
                 ("mu", C.c_double), ("wall_seconds", C.c_double), ("theta", C.c_void_p),
                 ("x", C.c_void_p), ("lambda_", C.c_void_p)]
 
@@ -140,6 +140,13 @@ def _load():
     lib.collo_server_poll.restype = C.c_int
     lib.collo_server_destroy.argtypes = [P]
     lib.collo_server_destroy.restype = None
+    lib.collo_server_set_admission.argtypes = [P, C.c_int]
+    lib.collo_server_set_admission.restype = C.c_int
+    lib.collo_phase_profile.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int,
+                                        C.c_int]
+    lib.collo_phase_profile.restype = C.c_int
+    lib.collo_server_stream.argtypes = [P]
+    lib.collo_server_stream.restype = C.c_void_p
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
     lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -331,7 +338,8 @@ class Problem:
 
 def _result_dict(res, theta, x, lam):
     return dict(status=res.status, iterations=res.iterations, factorizations=res.factorizations,
-                trials=res.line_search_trials, refine=res.refinement_sweeps, phi=res.phi,
+                trials=res.line_search_trials, refine=res.refinement_sweeps,
+                fp64_facs=res.fp64_factorizations, phi=res.phi,
                 kkt_error=res.kkt_error, mu=res.mu, wall=res.wall_seconds, theta=theta, x=x,
                 lam=lam)
 
@@ -358,7 +366,8 @@ def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
 
 
 def batch_time_phase(problems, phase: int, precision: int, reps: int = 10) -> float:
-    """collo_batch_time_phase: ms per batched launch of phase 1/2/3."""
+    """collo_batch_time_phase: ms per batched launch of phase 1..5 (factor, solve,
+    eval, element condensation alone, reduction + Schur alone)."""
     n = len(problems)
     handles = (C.c_void_p * n)(*[p.h.value for p in problems])
     ms = C.c_double()
@@ -390,6 +399,13 @@ class Server:
         _check(lib.collo_server_step(self.h, C.byref(a), C.byref(w)))
         return a.value, w.value
 
+    def set_admission(self, min_free_slots: int):
+        _check(lib.collo_server_set_admission(self.h, int(min_free_slots)))
+
+    @property
+    def stream(self) -> int:
+        return int(lib.collo_server_stream(self.h) or 0)
+
     def poll(self, ticket: int):
         problem, _ = self._keep[ticket]
         res = Result()
@@ -411,6 +427,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+PROFILE_PHASES = ["eval", "rhs", "factor", "solve", "step", "linesearch", "update", "admit"]
+
+
+def phase_profile(reset: bool = True):
+    """collo_phase_profile: {phase: (ms, rounds)}, or None when COLLO_PROFILE is off."""
+    ms = (C.c_double * 8)()
+    rounds = (C.c_longlong * 8)()
+    if lib.collo_phase_profile(ms, rounds, 8, int(reset)) == 0:
+        return None
+    return {k: (ms[i], rounds[i]) for i, k in enumerate(PROFILE_PHASES)}
 
 
 def alu_peak(precision: int) -> float:

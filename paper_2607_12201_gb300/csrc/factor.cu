@@ -270,18 +270,38 @@ template <typename T>
 struct alignas(2 * sizeof(T)) Pair {
   T x, y;
 };
+// Pivot-column buffers: two per elimination, 16-byte aligned for load4.
+template <typename T>
+struct alignas(16) PivotBuf {
+  Pair<T> v[2 * RT_UB];
+};
 
-template <typename T, int NT, int TPT, class Entry, class Sink, class Bar>
-__device__ void pair_eliminate_rt(int tid, int ext, int npairs, Entry entry, T* __restrict__ Lout,
-                                  int lds, T* __restrict__ Dout, Sink sink, Bar bar,
-                                  Pair<T>* ub, int& pos, int& neg, int& zero) {
+// Four consecutive entries of a pivot-column buffer (16-byte aligned).
+__device__ inline void load4(const Pair<float>* p, float x[4], float y[4]) {
+  const float4 u = reinterpret_cast<const float4*>(p)[0];
+  const float4 v = reinterpret_cast<const float4*>(p)[1];
+  x[0] = u.x; y[0] = u.y; x[1] = u.z; y[1] = u.w;
+  x[2] = v.x; y[2] = v.y; x[3] = v.z; y[3] = v.w;
+}
+__device__ inline void load4(const Pair<double>* p, double x[4], double y[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 w = reinterpret_cast<const double2*>(p)[u];
+    x[u] = w.x; y[u] = w.y;
+  }
+}
+
+template <typename T, int TPT, class Entry, class Sink, class Bar>
+__device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry entry,
+                                  T* __restrict__ Lout, int lds, T* __restrict__ Dout, Sink sink,
+                                  Bar bar, Pair<T>* ub, int& pos, int& neg, int& zero) {
   const int R = (ext + 3) >> 2, ntile = R * (R + 1) / 2;
-  for (int r = tid; r < 2 * RT_UB; r += NT) ub[r] = Pair<T>{T(0), T(0)};
+  for (int r = tid; r < 2 * RT_UB; r += nt) ub[r] = Pair<T>{T(0), T(0)};
   int ti[TPT], tj[TPT];
   T a[TPT][4][4];
 #pragma unroll
   for (int j = 0; j < TPT; ++j) {
-    const int t = tid + NT * j;
+    const int t = tid + nt * j;
     ti[j] = -1; tj[j] = 0;
     if (t < ntile) tri_tile(t, ti[j], tj[j]);
 #pragma unroll
@@ -310,7 +330,7 @@ __device__ void pair_eliminate_rt(int tid, int ext, int npairs, Entry entry, T* 
     const T pa = b[c0].x, pb = b[c1].x, pd = b[c1].y;
     const T det = pa * pd - pb * pb;
     T ia, ib, id;
-    if (det != T(0) && isfinite((double)det)) {
+    if (det != T(0) && isfinite(det)) {
       const T inv = T(1) / det;
       ia = pd * inv; ib = -pb * inv; id = pa * inv;
     } else {
@@ -323,14 +343,13 @@ __device__ void pair_eliminate_rt(int tid, int ext, int npairs, Entry entry, T* 
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
       if (ti[j] < 0 || 4 * ti[j] + 3 <= c1) continue;   // no live row
-      T l0[4], l1[4], y0[4], y1[4];
+      T l0[4], l1[4], y0[4], y1[4], xr0[4], xr1[4];
+      load4(b + 4 * ti[j], xr0, xr1);
+      load4(b + 4 * tj[j], y0, y1);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const Pair<T> xr = b[4 * ti[j] + u];
-        l0[u] = xr.x * ia + xr.y * ib;
-        l1[u] = xr.x * ib + xr.y * id;
-        const Pair<T> yc = b[4 * tj[j] + u];
-        y0[u] = yc.x; y1[u] = yc.y;
+        l0[u] = xr0[u] * ia + xr1[u] * ib;
+        l1[u] = xr0[u] * ib + xr1[u] * id;
       }
       if (tj[j] == tq)
 #pragma unroll
@@ -376,48 +395,53 @@ struct HalfBar {
   }
 };
 
-// Shared-memory staging of one element for elem_factor_rt (doubles, then
-// ints): D[4][4], JZ and Wzz [3][n][n], JT and Wzt [3][n][p], Wobj [n][4][4],
-// sigma [4][n], and a descriptor per local index (species, point, constraint,
-// multiplier flag; or the parameter index) that replaces elem_entry's
-// divisions.  All loads are contiguous per element.
-__host__ __device__ inline size_t elem_stage_doubles(int n, int p) {
+// Shared-memory staging of one element for elem_factor_rt (T, then ints):
+// D[4][4], JZ and Wzz [3][n][n], JT and Wzt [3][n][p], Wobj [n][4][4],
+// sigma [4][n], and a descriptor per local index (species, point,
+// constraint, multiplier flag; or the parameter index) that replaces
+// elem_entry's divisions.  All loads are contiguous per element; the values
+// are rounded to T once, and the few entries that sum several terms add them
+// in T.
+__host__ __device__ inline size_t elem_stage_vals(int n, int p) {
   return 16 + 6 * (size_t)n * n + 6 * (size_t)n * p + 20 * (size_t)n;
 }
+template <typename T>
 __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
-  return sizeof(double) * elem_stage_doubles(P.n, P.p) + sizeof(int) * (size_t)(P.ext + 1);
+  return sizeof(T) * elem_stage_vals(P.n, P.p) + sizeof(int) * (size_t)(P.ext + 1);
 }
 constexpr int DS_THETA = 1 << 28, DS_DUAL = 1 << 24;
 
-// Element condensation (same result as elem_factor_one) with pair_eliminate_rt.
-template <typename T, int NT, int TPT>
+// Element condensation (same elimination as elem_factor_one) with
+// pair_eliminate_rt over the nt threads of the block.
+template <typename T, int TPT>
 __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
                                const double* __restrict__ sigma, double dw, double dc,
-                               const DevFactor<T>& F, int e, Pair<T>* ub, double* stage) {
+                               const DevFactor<T>& F, int e, Pair<T>* ub, T* stage) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
   const size_t nn3 = 3 * (size_t)n * n, np3 = 3 * (size_t)n * p;
-  double* sD = stage;
-  double* sJZ = sD + 16;
-  double* sWzz = sJZ + nn3;
-  double* sJT = sWzz + nn3;
-  double* sWzt = sJT + np3;
-  double* sWobj = sWzt + np3;
-  double* sSig = sWobj + 16 * (size_t)n;
+  T* sD = stage;
+  T* sJZ = sD + 16;
+  T* sWzz = sJZ + nn3;
+  T* sJT = sWzz + nn3;
+  T* sWzt = sJT + np3;
+  T* sWobj = sWzt + np3;
+  T* sSig = sWobj + 16 * (size_t)n;
   int* desc = reinterpret_cast<int*>(sSig + 4 * (size_t)n);
-  for (int i = tid; i < 16; i += NT) sD[i] = P.D[i >> 2][i & 3];
-  for (size_t i = tid; i < nn3; i += NT) {
-    sJZ[i] = E.JZ[(size_t)e * nn3 + i];
-    sWzz[i] = E.Wzz[(size_t)e * nn3 + i];
+  for (int i = tid; i < 16; i += nt) sD[i] = (T)P.D[i >> 2][i & 3];
+  for (size_t i = tid; i < nn3; i += nt) {
+    sJZ[i] = (T)E.JZ[(size_t)e * nn3 + i];
+    sWzz[i] = (T)E.Wzz[(size_t)e * nn3 + i];
   }
-  for (size_t i = tid; i < np3; i += NT) {
-    sJT[i] = E.JT[(size_t)e * np3 + i];
-    sWzt[i] = E.Wzt[(size_t)e * np3 + i];
+  for (size_t i = tid; i < np3; i += nt) {
+    sJT[i] = (T)E.JT[(size_t)e * np3 + i];
+    sWzt[i] = (T)E.Wzt[(size_t)e * np3 + i];
   }
-  for (int i = tid; i < 16 * n; i += NT) sWobj[i] = E.Wobj[(size_t)e * 16 * n + i];
-  for (int i = tid; i < 4 * n; i += NT) sSig[i] = sigma ? sigma[(size_t)e * 4 * n + i] : 0.0;
-  for (int a = tid; a < ext; a += NT) {
+  for (int i = tid; i < 16 * n; i += nt) sWobj[i] = (T)E.Wobj[(size_t)e * 16 * n + i];
+  for (int i = tid; i < 4 * n; i += nt)
+    sSig[i] = (T)((sigma ? sigma[(size_t)e * 4 * n + i] : 0.0) + dw);
+  for (int a = tid; a < ext; a += nt) {
     if (a >= m) {
       desc[a] = DS_THETA | (a - m);
     } else {
@@ -425,8 +449,9 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
       desc[a] = s | (grp_point(g) << 16) | (grp_con(g) << 20) | ((a & 1) ? DS_DUAL : 0);
     }
   }
+  const T mdc = (T)(-dc);
   __syncthreads();
-  // entry (a, b), a >= b: the arithmetic of elem_entry on the staged data
+  // entry (a, b), a >= b, of the bordered element block (as elem_entry)
   auto entry = [&](int a, int b) -> T {
     const int da = desc[a], db = desc[b];
     const int sb = db & 0xFFFF;
@@ -435,29 +460,29 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
       const int q = da & 0xFFFF;
       if (!(db & DS_DUAL)) {
         const int j = (db >> 16) & 15;
-        return j >= 1 ? (T)sWzt[((j - 1) * n + sb) * p + q] : T(0);
+        return j >= 1 ? sWzt[((j - 1) * n + sb) * p + q] : T(0);
       }
       const int k = (db >> 20) & 15;
-      return k >= 1 ? (T)sJT[((k - 1) * n + sb) * p + q] : T(0);
+      return k >= 1 ? sJT[((k - 1) * n + sb) * p + q] : T(0);
     }
     const int sa = da & 0xFFFF;
     const bool adual = da & DS_DUAL, bdual = db & DS_DUAL;
     if (!adual && !bdual) {
       const int ja = (da >> 16) & 15, jb = (db >> 16) & 15;
-      double v = 0.0;
+      T v = T(0);
       if (sa == sb) v += sWobj[(sa * NP + ja) * NP + jb];
       if (ja == jb && ja >= 1) v += sWzz[((ja - 1) * n + sa) * n + sb];
-      if (a == b) v += sSig[ja * n + sa] + dw;
-      return (T)v;
+      if (a == b) v += sSig[ja * n + sa];
+      return v;
     }
-    if (adual && bdual) return a == b ? (T)(-dc) : T(0);
+    if (adual && bdual) return a == b ? mdc : T(0);
     int kd, sd, jp, sp;
     if (adual) { kd = (da >> 20) & 15; sd = sa; jp = (db >> 16) & 15; sp = sb; }
     else { kd = (db >> 20) & 15; sd = sb; jp = (da >> 16) & 15; sp = sa; }
     if (kd == 0) return (jp == 0 && sd == sp) ? T(1) : T(0);
-    double v = (sd == sp) ? sD[kd * NP + jp] : 0.0;
+    T v = (sd == sp) ? sD[kd * NP + jp] : T(0);
     if (jp == kd) v += sJZ[((kd - 1) * n + sd) * n + sp];
-    return (T)v;
+    return v;
   };
   T* Aif = F.Aif + (size_t)e * n2 * n2;
   T* Bif = F.Bif + (size_t)e * n2 * p;
@@ -475,37 +500,46 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
     }
   };
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_rt<T, NT, TPT>(tid, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                                F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pos, neg, zero);
+  pair_eliminate_rt<T, TPT>(tid, nt, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+                            F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pos, neg, zero);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
   }
   T* C = F.Cpl + (size_t)e * n * n;
-  for (int idx = tid; idx < n * n; idx += NT) {
+  for (int idx = tid; idx < n * n; idx += nt) {
     const int s2 = idx / n, t = idx - s2 * n;
     C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
   }
 }
 
-// Threads per block and tiles per thread of elem_factor_rt for an element of
-// size ext: 0 when the block does not fit (elem_factor_one is used).
+// Tiles per thread of elem_factor_rt (2) and its block size for an element
+// of size ext (a multiple of 32 threads covering every tile; 0 when the
+// element is too large and elem_factor_one is used).
+constexpr int RT_MAX_THREADS = 512;
 template <typename T>
-__host__ __device__ constexpr int rt_threads() { return sizeof(T) == 4 ? 128 : 256; }
+__host__ __device__ constexpr int rt_tpt() { return 2; }
 template <typename T>
-__host__ __device__ inline int rt_tiles_per_thread(int ext) {
+__host__ __device__ inline int rt_block_threads(int ext) {
   const int R = (ext + 3) >> 2;
   if (R > RT_MAX_TR) return 0;
-  const int nt = rt_threads<T>(), tpt = (R * (R + 1) / 2 + nt - 1) / nt;
-  return tpt <= (sizeof(T) == 4 ? 4 : 2) ? tpt : 0;
+  const int per = (R * (R + 1) / 2 + rt_tpt<T>() - 1) / rt_tpt<T>();
+  const int nt = (per + 31) / 32 * 32;
+  return nt < 64 ? 64 : nt;
 }
 
-template <typename T, int TPT>
-__global__ void __launch_bounds__(rt_threads<T>())
+// Register cap of the element kernels: enough for the tiles, few enough for
+// four (float) or two (double) blocks of 192 threads per SM.
+template <typename T>
+constexpr int rt_maxnreg() { return sizeof(T) == 4 ? 80 : 128; }
+
+template <typename T>
+__global__ void __maxnreg__(rt_maxnreg<T>())
 k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
                  DevFactor<T> F) {
-  __shared__ Pair<T> ub[2 * RT_UB];
+  __shared__ PivotBuf<T> ub;
   extern __shared__ double stage_dyn[];
-  elem_factor_rt<T, rt_threads<T>(), TPT>(P, E, sigma, dw, dc, F, blockIdx.x, ub, stage_dyn);
+  elem_factor_rt<T, rt_tpt<T>()>(P, E, sigma, dw, dc, F, blockIdx.x, ub.v,
+                                 reinterpret_cast<T*>(stage_dyn));
 }
 
 // ---- 2. one level of block cyclic reduction -------------------------------------
@@ -665,8 +699,8 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
     }
   };
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_rt<T, 128, TPT>(tid, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
-                                 F.Db + (size_t)i * n * 3, sink, bar, ub, pos, neg, zero);
+  pair_eliminate_rt<T, TPT>(tid, 128, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
+                            F.Db + (size_t)i * n * 3, sink, bar, ub, pos, neg, zero);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
     in[0] = pos; in[1] = neg; in[2] = zero;
@@ -690,12 +724,12 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
   const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
   if constexpr (BT > 0) {
     // two blocks of the level per CUDA block, one per half
-    __shared__ Pair<T> ub[2][2 * RT_UB];
+    __shared__ PivotBuf<T> ub[2];
     const int half = threadIdx.x >> 7;
     T* stage = reinterpret_cast<T*>(smraw) + half * bcr_stage_elems(P.n, P.p);
     for (int bi = 2 * blockIdx.x + half; bi < nblk; bi += 2 * gridDim.x)
       bcr_factor_rt<T, BT>(P, F, stride, final_level, bi, threadIdx.x & 127, HalfBar{1 + half},
-                           ub[half], stage);
+                           ub[half].v, stage);
   } else {
     const int bext = P.bext, ld = odd_ld(bext);
     T* Lp = reinterpret_cast<T*>(smraw);
@@ -1114,19 +1148,19 @@ __device__ inline const DevFactor<double>& inst_factor<double>(const DevInst& I)
 
 // Element condensation of a batch with elem_factor_rt: one block per element of
 // the work list; instances without flag 4 are condensed inside k_factor_b.
-template <typename T, int TPT>
-__global__ void __launch_bounds__(rt_threads<T>())
+template <typename T>
+__global__ void __maxnreg__(rt_maxnreg<T>())
 k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
                    const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
                    const int* __restrict__ flags) {
-  __shared__ Pair<T> ub[2 * RT_UB];
+  __shared__ PivotBuf<T> ub;
   extern __shared__ double stage_dyn[];
   const int t = blockIdx.x;
   const int k = find_item(pre_elem, A, t);
   if (!(flags[k] & 4)) return;
   const DevInst& I = insts[act[k]];
-  elem_factor_rt<T, rt_threads<T>(), TPT>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc,
-                                          inst_factor<T>(I), t - pre_elem[k], ub, stage_dyn);
+  elem_factor_rt<T, rt_tpt<T>()>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, inst_factor<T>(I),
+                                 t - pre_elem[k], ub.v, reinterpret_cast<T*>(stage_dyn));
 }
 
 template <typename T, int BT>
@@ -1156,7 +1190,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     const int tot = fin ? A : pre[A];
     if constexpr (BT > 0) {
       // instances with flag 8: two blocks of the level per CUDA block
-      __shared__ Pair<T> ubh[2][2 * RT_UB];
+      __shared__ PivotBuf<T> ubh[2];
       const int half = threadIdx.x >> 7;
       for (int t = 2 * blockIdx.x + half; t < tot; t += 2 * gridDim.x) {
         const int k = fin ? t : find_item(pre, A, t);
@@ -1166,7 +1200,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
         // of different sizes may share the block)
         T* stage = reinterpret_cast<T*>(smraw + half * ((smem_bytes / 2) & ~size_t(15)));
         bcr_factor_rt<T, BT>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
-                             fin ? 0 : t - pre[k], threadIdx.x & 127, HalfBar{1 + half}, ubh[half],
+                             fin ? 0 : t - pre[k], threadIdx.x & 127, HalfBar{1 + half}, ubh[half].v,
                              stage);
       }
     }
@@ -1309,15 +1343,13 @@ size_t factor_work_elems(const DevProb& P, int n_slabs) {
 template <typename T>
 cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
                                double dc, const DevFactor<T>& F, cudaStream_t st) {
-  const int tpt = rt_tiles_per_thread<T>(P.ext);
-  if (tpt > 0) {
-    const size_t sm = elem_stage_bytes(P);
-    auto kern = tpt == 1 ? k_elem_factor_rt<T, 1> : tpt == 2 ? k_elem_factor_rt<T, 2>
-              : tpt == 3 ? k_elem_factor_rt<T, 3> : k_elem_factor_rt<T, 4>;
+  const int rtn = rt_block_threads<T>(P.ext);
+  if (rtn > 0) {
+    const size_t sm = elem_stage_bytes<T>(P);
     if (sm > SMEM_OPTIN_ABOVE)
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_elem_factor_rt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
-    kern<<<P.N, rt_threads<T>(), sm, st>>>(P, E, sigma, dw, dc, F);
+    k_elem_factor_rt<T><<<P.N, rtn, sm, st>>>(P, E, sigma, dw, dc, F);
     return cudaGetLastError();
   }
   bool es = elem_uses_smem<T>(P);
@@ -1446,20 +1478,21 @@ template <typename T>
 cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                             const int* pre_lv, int maxL, const int* pre_cs,
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
-                            int grid_cap, int rt_tpt, size_t rt_smem, int tot_elem, int bcr_tpt,
-                            int bcr_full, cudaStream_t st) {
+                            int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
+                            int bcr_tpt, int bcr_full, int parts, cudaStream_t st) {
   if (A == 0) return cudaSuccess;
-  if (rt_tpt > 0 && tot_elem > 0) {
-    if (rt_tpt > 4) return cudaErrorInvalidValue;
-    auto kern = rt_tpt == 1 ? k_elem_factor_rt_b<T, 1> : rt_tpt == 2 ? k_elem_factor_rt_b<T, 2>
-              : rt_tpt == 3 ? k_elem_factor_rt_b<T, 3> : k_elem_factor_rt_b<T, 4>;
+  if ((parts & 1) && rt_threads > 0 && tot_elem > 0) {
+    if (rt_threads > RT_MAX_THREADS) return cudaErrorInvalidValue;
     if (rt_smem > SMEM_OPTIN_ABOVE)
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rt_smem);
+      cudaFuncSetAttribute(k_elem_factor_rt_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)rt_smem);
     count_launch();
-    kern<<<tot_elem, rt_threads<T>(), rt_smem, st>>>(insts, act, A, pre_elem, prm, flags);
+    k_elem_factor_rt_b<T><<<tot_elem, rt_threads, rt_smem, st>>>(insts, act, A, pre_elem, prm,
+                                                                 flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (!(parts & 2)) return cudaSuccess;
   auto kern = bcr_tpt == 1 ? k_factor_b<T, 1> : bcr_tpt == 2 ? k_factor_b<T, 2> : k_factor_b<T, 0>;
   if (smem > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1491,19 +1524,21 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
 template cudaError_t launch_factor_b<float>(const DevInst*, const int*, int, const int*,
                                             const int*, int, const int*, const InstParams*,
                                             const int*, GridBar*, size_t, int, int, size_t, int,
-                                            int, int, cudaStream_t);
+                                            int, int, int, cudaStream_t);
 template cudaError_t launch_factor_b<double>(const DevInst*, const int*, int, const int*,
                                              const int*, int, const int*, const InstParams*,
                                              const int*, GridBar*, size_t, int, int, size_t, int,
-                                             int, int, cudaStream_t);
+                                             int, int, int, cudaStream_t);
 int bcr_rt_tiles_of(const DevProb& P) { return bcr_rt_tiles(P.bext); }
-size_t elem_rt_stage_bytes(const DevProb& P) { return elem_stage_bytes(P); }
+size_t elem_rt_stage_bytes(const DevProb& P, bool f32) {
+  return f32 ? elem_stage_bytes<float>(P) : elem_stage_bytes<double>(P);
+}
 size_t bcr_rt_stage_bytes(const DevProb& P, bool f32) {
   const size_t one = (f32 ? sizeof(float) : sizeof(double)) * bcr_stage_elems(P.n, P.p);
   return 2 * ((one + 15) & ~size_t(15));
 }
-int elem_rt_tiles(const DevProb& P, bool f32) {
-  return f32 ? rt_tiles_per_thread<float>(P.ext) : rt_tiles_per_thread<double>(P.ext);
+int elem_rt_threads(const DevProb& P, bool f32) {
+  return f32 ? rt_block_threads<float>(P.ext) : rt_block_threads<double>(P.ext);
 }
 template cudaError_t launch_solve_b<float>(const DevInst*, const int*, int, const int*, const int*,
                                            int, const int*, int, int, GridBar*, int, int,

@@ -281,9 +281,16 @@ __global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* _
 }
 
 // The same sweep for 3n <= 32 on one warp: lane l owns row l of the FP32
-// Newton matrix in registers, so the LU with partial pivoting and the back
-// substitution run on warp shuffles without block barriers.
+// Newton matrix in registers, so the LU with partial pivoting and the
+// substitutions run on warp shuffles without block barriers.  The Newton
+// iteration is a chord iteration: the LU's multipliers (lrow, per step and
+// lane, as they were applied) and pivot rows are kept, later iterations
+// replay the same elimination on the new residual, and the matrix is
+// refactored only when the step shrinks by less than CHORD_RATE.  Each
+// element starts from the previous element's stage increments added to its
+// initial state.
 constexpr int WSWEEP = 32;
+constexpr double CHORD_RATE = 0.25;
 __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
                            double* sm) {
   const int n = P.n, r = P.r, dim = KC * n;
@@ -307,11 +314,16 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
   const int rk = lane < dim ? lane / n + 1 : 1;
   const int rs = lane < dim ? lane - (rk - 1) * n : 0;
   int nfail = 0;
+  float row[WSWEEP], lrow[WSWEEP];
+  int piv[WSWEEP];
+  double dZ = 0.0;                 // lane's stage increment in the previous element
   for (int i = 0; i < P.N; ++i) {
-    for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
+    if (lane < dim) Z[lane] = z0[rs] + dZ;
     __syncwarp();
-    bool ok = false;
+    bool ok = false, have_lu = false;
+    double mdz_prev = 0.0;
     for (int it = 0; it < SWEEP_MAXIT; ++it) {
+      const bool refactor = !have_lu;
       for (int idx = lane; idx < KC * r; idx += 32) {
         const int k = idx / r, j = idx - k * r;
         const int a = P.react[2 * j], b = P.react[2 * j + 1];
@@ -323,8 +335,10 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
       float* myrow = rows + lane * (WSWEEP + 1);
       double g = 0.0;
       if (lane < dim) {
-        for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
-        for (int j = 1; j <= KC; ++j) myrow[(j - 1) * n + rs] = (float)P.D[rk][j];
+        if (refactor) {
+          for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
+          for (int j = 1; j <= KC; ++j) myrow[(j - 1) * n + rs] = (float)P.D[rk][j];
+        }
         g = P.D[rk][0] * z0[rs];
         for (int j = 1; j <= KC; ++j) g += P.D[rk][j] * Z[(j - 1) * n + rs];
         double f = 0.0;
@@ -334,54 +348,76 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
           const int mi = (rk - 1) * r + rr;
           const double nk = P.nu_v[e] * kr[rr];
           f += nk * mon[mi];
-          const float nkf = (float)nk;
-          const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
-          myrow[(rk - 1) * n + a] -= hf * nkf * daf[mi];
-          if (b >= 0) myrow[(rk - 1) * n + b] -= hf * nkf * dbf[mi];
+          if (refactor) {
+            const float nkf = (float)nk;
+            const int a = P.react[2 * rr], b = P.react[2 * rr + 1];
+            myrow[(rk - 1) * n + a] -= hf * nkf * daf[mi];
+            if (b >= 0) myrow[(rk - 1) * n + b] -= hf * nkf * dbf[mi];
+          }
         }
         g -= P.h * f;
-      } else {
+      } else if (refactor) {
         for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
       }
       __syncwarp();
-      float row[WSWEEP];
-#pragma unroll
-      for (int c = 0; c < WSWEEP; ++c) row[c] = myrow[c];
       float rhs = (float)g;
       bool singular = false;
+      if (refactor) {
 #pragma unroll
-      for (int c = 0; c < WSWEEP; ++c) {
-        if (c < dim && !singular) {
-          float v = (lane >= c && lane < dim) ? fabsf(row[c]) : -1.f;
-          int idx = lane;
+        for (int c = 0; c < WSWEEP; ++c) row[c] = myrow[c];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(FULL, v, o);
-            const int oi = __shfl_xor_sync(FULL, idx, o);
-            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        for (int c = 0; c < WSWEEP; ++c) {
+          lrow[c] = 0.f;
+          piv[c] = c;
+          if (c < dim && !singular) {
+            float v = (lane >= c && lane < dim) ? fabsf(row[c]) : -1.f;
+            int idx = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const float ov = __shfl_xor_sync(FULL, v, o);
+              const int oi = __shfl_xor_sync(FULL, idx, o);
+              if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+            }
+            if (!(v > 0.f) || !isfinite(v)) {
+              singular = true;
+            } else {
+              piv[c] = idx;
+              if (idx != c) {
+                const int src = lane == c ? idx : (lane == idx ? c : lane);
+#pragma unroll
+                for (int k = c; k < WSWEEP; ++k) row[k] = __shfl_sync(FULL, row[k], src);
+                rhs = __shfl_sync(FULL, rhs, src);
+              }
+              const float pv = __shfl_sync(FULL, row[c], c);
+              const float f = (lane > c && lane < dim) ? row[c] / pv : 0.f;
+              lrow[c] = f;
+#pragma unroll
+              for (int k = c + 1; k < WSWEEP; ++k) {
+                const float pk = __shfl_sync(FULL, row[k], c);
+                row[k] -= f * pk;
+              }
+              const float pr = __shfl_sync(FULL, rhs, c);
+              rhs -= f * pr;
+            }
           }
-          if (!(v > 0.f) || !isfinite(v)) {
-            singular = true;
-          } else {
-            if (idx != c) {
-              const int src = lane == c ? idx : (lane == idx ? c : lane);
+        }
+        if (singular) break;
+        have_lu = true;
+      } else {
+        // replay the factorization's row exchanges and eliminations on rhs
 #pragma unroll
-              for (int k = c; k < WSWEEP; ++k) row[k] = __shfl_sync(FULL, row[k], src);
+        for (int c = 0; c < WSWEEP; ++c) {
+          if (c < dim) {
+            const int pc = piv[c];
+            if (pc != c) {
+              const int src = lane == c ? pc : (lane == pc ? c : lane);
               rhs = __shfl_sync(FULL, rhs, src);
             }
-            const float pv = __shfl_sync(FULL, row[c], c);
-            const float f = (lane > c && lane < dim) ? row[c] / pv : 0.f;
-#pragma unroll
-            for (int k = c + 1; k < WSWEEP; ++k) {
-              const float pk = __shfl_sync(FULL, row[k], c);
-              row[k] -= f * pk;
-            }
             const float pr = __shfl_sync(FULL, rhs, c);
-            rhs -= f * pr;
+            rhs -= lrow[c] * pr;
           }
         }
       }
-      if (singular) break;
       float sol = 0.f;
 #pragma unroll
       for (int c = WSWEEP - 1; c >= 0; --c) {
@@ -409,12 +445,16 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
       __syncwarp();
       if (!fin) break;
       if (mdz <= 1e-12 * fmax(1.0, mz)) { ok = true; break; }
+      // slow contraction of the chord iteration: refactor at the current point
+      if (it > 0 && mdz > CHORD_RATE * mdz_prev) have_lu = false;
+      mdz_prev = mdz;
     }
     if (!ok) {
       ++nfail;
       for (int t = lane; t < dim; t += 32) Z[t] = z0[t % n];
       __syncwarp();
     }
+    dZ = lane < dim ? Z[lane] - z0[rs] : 0.0;
     double* xi = x + (size_t)i * NP * n;
     for (int s = lane; s < n; s += 32) xi[s] = z0[s];
     for (int t = lane; t < dim; t += 32) xi[n + t] = Z[t];

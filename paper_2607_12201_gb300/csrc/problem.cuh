@@ -68,15 +68,15 @@ template <typename T>
 cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                             const int* pre_lv, int maxL, const int* pre_cs,
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
-                            int grid_cap, int rt_tpt, size_t rt_smem, int tot_elem, int bcr_tpt,
-                            int bcr_full, cudaStream_t st);
-// Tiles per thread of the register-tiled element condensation for P (0: the
+                            int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
+                            int bcr_tpt, int bcr_full, int parts, cudaStream_t st);
+// Block size of the register-tiled element condensation for P (0: the
 // element does not fit it).
-int elem_rt_tiles(const DevProb& P, bool f32);
+int elem_rt_threads(const DevProb& P, bool f32);
 // Tiles per thread of the register-tiled cyclic-reduction blocks (0: none).
 int bcr_rt_tiles_of(const DevProb& P);
 // Dynamic shared memory of the register-tiled element kernel for P.
-size_t elem_rt_stage_bytes(const DevProb& P);
+size_t elem_rt_stage_bytes(const DevProb& P, bool f32);
 // Dynamic shared memory of the register-tiled reduction blocks (both halves).
 size_t bcr_rt_stage_bytes(const DevProb& P, bool f32);
 template <typename T>

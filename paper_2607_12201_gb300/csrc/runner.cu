@@ -19,12 +19,17 @@
 #include <mutex>
 #include <vector>
 
+#include <cstdlib>
+
 #include "problem.cuh"
 
 namespace collo {
 
 constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
 constexpr size_t KSMEM_LIMIT = 220 * 1024;
+// Relative KKT residual above which refinement from an FP32 factorization
+// counts as failed (the step is then redone with an FP64 factorization).
+constexpr double ESCALATE_REL = 1e-6;
 
 // ---- plans ---------------------------------------------------------------------------
 struct Plan {
@@ -42,8 +47,8 @@ struct Plan {
   size_t smem_eval = 0, smem_f[2] = {0, 0}, smem_sw_w = 0, smem_sw_c = 0;
   int cap_f[2] = {1 << 30, 1 << 30};
   int per_warp[2] = {0, 0};
-  int rt_tpt[2] = {0, 0};   // tiles per thread of the register-tiled element kernel
-  size_t rt_smem = 0;       // its dynamic shared memory
+  int rt_threads[2] = {0, 0};   // block size of the register-tiled element kernel
+  size_t rt_smem[2] = {0, 0};   // its dynamic shared memory
   int bcr_tpt = 0;          // ... of the register-tiled cyclic-reduction blocks
   int bcr_full = 0;         // some instance's reduction blocks use the whole-block path
 
@@ -203,13 +208,13 @@ struct Runner {
         const size_t sb = f32 ? bcr_factor_smem<float>(Q, true) : bcr_factor_smem<double>(Q, true);
         const size_t ve = f32 ? elem_factor_smem<float>(Q, false) : elem_factor_smem<double>(Q, false);
         const size_t vb = f32 ? bcr_factor_smem<float>(Q, false) : bcr_factor_smem<double>(Q, false);
-        const int rt = elem_rt_tiles(Q, f32), brt = bcr_rt_tiles_of(Q);
+        const int rt = elem_rt_threads(Q, f32), brt = bcr_rt_tiles_of(Q);
         int fl = 0;
         size_t need = 0;
         if (rt > 0) {                  // elements condensed by the register-tiled kernel
           fl |= 1 | 4;
           tpt = std::max(tpt, rt);
-          rts = std::max(rts, elem_rt_stage_bytes(Q));
+          rts = std::max(rts, elem_rt_stage_bytes(Q, f32));
         } else {
           need = std::max(need, ve);
           if (se <= KSMEM_LIMIT) { fl |= 1; need = std::max(need, se); }
@@ -235,8 +240,8 @@ struct Runner {
       pl.smem_f[prec] = smem;
       pl.cap_f[prec] = cap;
       pl.per_warp[prec] = pw;
-      pl.rt_tpt[prec] = tpt;
-      pl.rt_smem = rts;
+      pl.rt_threads[prec] = tpt;
+      pl.rt_smem[prec] = rts;
       pl.bcr_tpt = btpt;
       pl.bcr_full = bfull;
     }
@@ -327,7 +332,8 @@ struct Runner {
                               stream));
     return COLLO_OK;
   }
-  collo_status factor(int which, int prec) {
+  // parts: 1 element condensation (register-tiled kernel), 2 the rest, 3 both
+  collo_status factor(int which, int prec, int parts = 3) {
     Plan& pl = plans[which];
     cudaError_t e;
     const int p = prec == COLLO_PRECISION_MIXED ? 1 : 0;
@@ -335,14 +341,14 @@ struct Runner {
       e = launch_factor_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                  pl.pre_cs_s(), pl.d_prm, pl.flags(1), gbar, pl.smem_f[1],
                                  std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)),
-                                 pl.rt_tpt[1], pl.rt_smem, pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
-                                 stream);
+                                 pl.rt_threads[1], pl.rt_smem[1], pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
+                                 parts, stream);
     else
       e = launch_factor_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                   pl.pre_cs_s(), pl.d_prm, pl.flags(0), gbar, pl.smem_f[0],
                                   std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)),
-                                  pl.rt_tpt[0], pl.rt_smem, pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
-                                  stream);
+                                  pl.rt_threads[0], pl.rt_smem[0], pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
+                                  parts, stream);
     COLLO_CUDA(e);
     return COLLO_OK;
   }
@@ -479,6 +485,38 @@ static Opt make_opt(const collo_ipm_options* opts) {
 
 enum { RUNNING = 1000 };
 
+// ---- optional phase profile of the iteration driver (COLLO_PROFILE=1) --------------
+// Host wall time per phase of ipm_iteration, with a stream synchronisation at
+// each phase boundary (only when enabled), and counts of the rounds of the
+// phases that loop over shrinking subsets.
+enum ProfPhase { PF_EVAL = 0, PF_RHS, PF_FACTOR, PF_SOLVE, PF_STEP, PF_LINESEARCH, PF_UPDATE,
+                 PF_ADMIT, PF_N };
+static double g_prof_ms[PF_N];
+static long long g_prof_rounds[PF_N];
+static int g_prof_on = -1;
+struct ProfClock {
+  cudaStream_t st;
+  int cur = -1;
+  std::chrono::steady_clock::time_point t;
+  explicit ProfClock(cudaStream_t s) : st(s) {
+    if (g_prof_on < 0) {
+      const char* e = std::getenv("COLLO_PROFILE");
+      g_prof_on = (e && e[0] == '1') ? 1 : 0;
+    }
+    if (g_prof_on) t = std::chrono::steady_clock::now();
+  }
+  void mark(int next) {
+    if (!g_prof_on) return;
+    cudaStreamSynchronize(st);
+    const auto now = std::chrono::steady_clock::now();
+    if (cur >= 0) g_prof_ms[cur] += std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+    cur = next;
+  }
+  void round(int ph) { if (g_prof_on) g_prof_rounds[ph]++; }
+  ~ProfClock() { mark(-1); }
+};
+
 struct IpmInst {
   int slot = 0;
   collo_problem* prob = nullptr;
@@ -486,7 +524,8 @@ struct IpmInst {
   int status = RUNNING;
   double mu = 0.1, tau = 0.99, dw_last = 0.0, dw = 0.0, dc = 0.0;
   double theta_max = 0, theta_min = 0, err = INFINITY, phi = NAN;
-  int acc = 0, it = 0, facs = 0, trials_total = 0, prec = 0, refine_total = 0;
+  int acc = 0, it = 0, facs = 0, facs64 = 0, trials_total = 0, prec = 0, refine_total = 0;
+  bool fp64_factor = false;   // MIXED path: refinement failed once, factor in FP64 from now on
   std::vector<std::pair<double, double>> filt;
   // line-search temporaries
   double theta_k = 0, phi_k = 0, gphi = 0, alpha = 0, alpha_min = 0, alpha_z = 0;
@@ -540,6 +579,8 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
     ip.mu = I->mu; ip.tau = I->tau; ip.dw = I->dw; ip.dc = I->dc;
   };
   collo_status st;
+  ProfClock prof(R.stream);
+  prof.mark(PF_EVAL);
   // 1. derivatives and optimality measures
   if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
   if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
@@ -584,7 +625,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
       I->filt.clear();
     }
     I->theta_k = o[O_C1] > 0 ? o[O_C1] : 0.0;
-    I->prec = (op.precision == COLLO_PRECISION_MIXED &&
+    I->prec = (op.precision == COLLO_PRECISION_MIXED && !I->fp64_factor &&
                !(op.mixed_mu_switch > 0 && I->mu < op.mixed_mu_switch))
                   ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64;
     I->dc = op.dc_coef * std::pow(I->mu, op.dc_exp);
@@ -595,6 +636,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
   slots.clear();
   for (auto* I : cont) slots.push_back(I->slot);
   // 2. right-hand sides with the updated barrier parameters
+  prof.mark(PF_RHS);
   if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
   if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
   {
@@ -602,66 +644,95 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
     COLLO_CUDA(launch_theta_prep_b(R.d_insts, pl.act(), pl.A, pl.d_prm, R.stream));
   }
   if ((st = R.resid(0, 1 /* R_RHS */)) != COLLO_OK) return st;
-  // 3. factorization with inertia correction (per precision group)
-  std::vector<IpmInst*> fac = cont;
-  const long long dummy = 0;
-  (void)dummy;
-  while (!fac.empty()) {
-    std::vector<int> gr[2];
-    for (auto* I : fac) gr[I->prec == COLLO_PRECISION_MIXED ? 1 : 0].push_back(I->slot);
-    for (int g = 0; g < 2; ++g) {
-      if (gr[g].empty()) continue;
-      if ((st = R.set_plan(g == 1 ? 1 : 2, gr[g])) != COLLO_OK) return st;
-      if ((st = R.set_params(g == 1 ? 1 : 2, fill_mu)) != COLLO_OK) return st;
-      if ((st = R.factor(g == 1 ? 1 : 2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64)) != COLLO_OK)
-        return st;
+  // 3. factorization with inertia correction (per precision group), then
+  // 4. solve with FP64 refinement.  An instance of the MIXED path whose
+  // refinement leaves a relative residual above ESCALATE_REL after refine_max
+  // sweeps is factored and solved again in FP64, and stays in FP64 for the
+  // rest of its solve.
+  std::vector<IpmInst*> go;
+  auto factor_solve = [&](std::vector<IpmInst*> fac, std::vector<IpmInst*>& redo) -> collo_status {
+    std::vector<IpmInst*> list = fac;
+    prof.mark(PF_FACTOR);
+    while (!fac.empty()) {
+      prof.round(PF_FACTOR);
+      std::vector<int> gr[2];
+      for (auto* I : fac) gr[I->prec == COLLO_PRECISION_MIXED ? 1 : 0].push_back(I->slot);
+      for (int g = 0; g < 2; ++g) {
+        if (gr[g].empty()) continue;
+        if ((st = R.set_plan(g == 1 ? 1 : 2, gr[g])) != COLLO_OK) return st;
+        if ((st = R.set_params(g == 1 ? 1 : 2, fill_mu)) != COLLO_OK) return st;
+        if ((st = R.factor(g == 1 ? 1 : 2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64)) != COLLO_OK)
+          return st;
+      }
+      if ((st = R.read_outs()) != COLLO_OK) return st;
+      if ((st = R.check_barrier()) != COLLO_OK) return st;
+      std::vector<IpmInst*> again;
+      for (auto* I : fac) {
+        I->facs++;
+        if (I->prec != COLLO_PRECISION_MIXED) I->facs64++;
+        I->prob->factored = I->prec;
+        I->prob->fac_dw = I->dw;
+        I->prob->fac_dc = I->dc;
+        long long in[3];
+        std::memcpy(in, R.out(I->slot) + O_INERT, sizeof(in));
+        const bool good = in[0] == R.h_insts[I->slot].n_x && in[1] == R.h_insts[I->slot].n_c && in[2] == 0;
+        if (good) {
+          if (I->dw > 0) I->dw_last = I->dw;
+          continue;
+        }
+        const Opt& op = I->o;
+        if (I->dw == 0.0) I->dw = I->dw_last == 0.0 ? op.dw_0 : std::max(op.dw_min, op.kw_minus * I->dw_last);
+        else I->dw *= I->dw_last == 0.0 ? op.kw_plus_bar : op.kw_plus;
+        if (I->dw > op.dw_max) { I->status = COLLO_ERR_INERTIA; continue; }
+        again.push_back(I);
+      }
+      fac = again;
     }
-    if ((st = R.read_outs()) != COLLO_OK) return st;
-    if ((st = R.check_barrier()) != COLLO_OK) return st;
-    std::vector<IpmInst*> again;
-    for (auto* I : fac) {
-      I->facs++;
-      I->prob->factored = I->prec;
-      I->prob->fac_dw = I->dw;
-      I->prob->fac_dc = I->dc;
-      long long in[3];
-      std::memcpy(in, R.out(I->slot) + O_INERT, sizeof(in));
-      const bool good = in[0] == R.h_insts[I->slot].n_x && in[1] == R.h_insts[I->slot].n_c && in[2] == 0;
-      if (good) {
-        if (I->dw > 0) I->dw_last = I->dw;
+    std::vector<IpmInst*> run_now;
+    for (auto* I : list)
+      if (I->status == RUNNING) run_now.push_back(I);
+    if (run_now.empty()) return COLLO_OK;
+    std::vector<int> sl;
+    for (auto* I : run_now) sl.push_back(I->slot);
+    prof.mark(PF_SOLVE);
+    if ((st = R.set_plan(0, sl)) != COLLO_OK) return st;
+    std::vector<int> prec_of_slot(R.capacity, 0);
+    std::vector<double> dwv, dcv;
+    for (auto* I : run_now) { prec_of_slot[I->slot] = I->prec; dwv.push_back(I->dw); dcv.push_back(I->dc); }
+    std::vector<int> sweeps;
+    std::vector<double> rel;
+    const Opt& op = run_now[0]->o;
+    if ((st = solve_refine(R, 0, prec_of_slot, dwv, dcv, op.refine_max, op.refine_tol, sweeps, rel)) != COLLO_OK)
+      return st;
+    int max_sw = 0;
+    for (int v : sweeps) max_sw = std::max(max_sw, v);
+    for (int k = 0; k <= max_sw; ++k) prof.round(PF_SOLVE);
+    for (size_t k = 0; k < run_now.size(); ++k) {
+      IpmInst* I = run_now[k];
+      I->refine_total += sweeps[k];
+      if (I->prec == COLLO_PRECISION_MIXED && !(rel[k] <= ESCALATE_REL)) {
+        I->fp64_factor = true;
+        I->prec = COLLO_PRECISION_FP64;
+        I->dw = 0.0;
+        redo.push_back(I);
         continue;
       }
-      const Opt& op = I->o;
-      if (I->dw == 0.0) I->dw = I->dw_last == 0.0 ? op.dw_0 : std::max(op.dw_min, op.kw_minus * I->dw_last);
-      else I->dw *= I->dw_last == 0.0 ? op.kw_plus_bar : op.kw_plus;
-      if (I->dw > op.dw_max) { I->status = COLLO_ERR_INERTIA; continue; }
-      again.push_back(I);
+      if (!std::isfinite(rel[k])) I->status = COLLO_ERR_NUMERIC;
     }
-    fac = again;
+    return COLLO_OK;
+  };
+  {
+    std::vector<IpmInst*> redo, none;
+    if ((st = factor_solve(cont, redo)) != COLLO_OK) return st;
+    if (!redo.empty() && (st = factor_solve(redo, none)) != COLLO_OK) return st;
   }
-  std::vector<IpmInst*> go;
   for (auto* I : cont)
     if (I->status == RUNNING) go.push_back(I);
   if (go.empty()) return COLLO_OK;
   slots.clear();
   for (auto* I : go) slots.push_back(I->slot);
-  // 4. solve with FP64 refinement
-  if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
-  {
-    std::vector<int> prec_of_slot(R.capacity, 0);
-    std::vector<double> dwv, dcv;
-    for (auto* I : go) { prec_of_slot[I->slot] = I->prec; dwv.push_back(I->dw); dcv.push_back(I->dc); }
-    std::vector<int> sweeps;
-    std::vector<double> rel;
-    const Opt& op = go[0]->o;
-    if ((st = solve_refine(R, 0, prec_of_slot, dwv, dcv, op.refine_max, op.refine_tol, sweeps, rel)) != COLLO_OK)
-      return st;
-    for (size_t k = 0; k < go.size(); ++k) {
-      go[k]->refine_total += sweeps[k];
-      if (!std::isfinite(rel[k])) go[k]->status = COLLO_ERR_NUMERIC;
-    }
-  }
   // 5. step sizes
+  prof.mark(PF_STEP);
   if ((st = R.set_plan(0, slots)) != COLLO_OK) return st;
   if ((st = R.set_params(0, fill_mu)) != COLLO_OK) return st;
   {
@@ -700,7 +771,9 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
     if (I->alpha >= I->alpha_min) trying.push_back(I);
     else I->status = COLLO_ERR_LINESEARCH;
   }
+  prof.mark(PF_LINESEARCH);
   while (!trying.empty()) {
+    prof.round(PF_LINESEARCH);
     slots.clear();
     for (auto* I : trying) slots.push_back(I->slot);
     if ((st = R.set_plan(1, slots)) != COLLO_OK) return st;
@@ -745,6 +818,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
     trying = next;
   }
   // 7. accept the steps
+  prof.mark(PF_UPDATE);
   std::vector<IpmInst*> upd;
   for (auto* I : ls) {
     I->trials_total += I->trials;
@@ -784,6 +858,7 @@ static collo_status ipm_finish(Runner& R, IpmInst& I, collo_result* res) {
   res->factorizations = I.facs;
   res->line_search_trials = I.trials_total;
   res->refinement_sweeps = I.refine_total;
+  res->fp64_factorizations = I.facs64;
   res->phi = I.phi;
   res->kkt_error = I.err;
   res->mu = I.mu;
@@ -920,6 +995,7 @@ struct collo_server {
   };
   std::deque<Job*> waiting;
   std::vector<Job*> slots;            // slot -> job (null: free)
+  int admit_min = 1;                  // admit when this many slots are free (or none is busy)
   std::map<long long, Job*> jobs;
   std::mutex mu;
   ~collo_server() {
@@ -1039,7 +1115,7 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
 // phase 1 factorization, 2 solve (no refinement), 3 evaluation.
 collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
                                     int precision, int reps, double* ms_per_launch) {
-  if (!probs || count < 1 || reps < 1 || !ms_per_launch || phase < 1 || phase > 3) {
+  if (!probs || count < 1 || reps < 1 || !ms_per_launch || phase < 1 || phase > 5) {
     set_error("bad argument");
     return COLLO_ERR_INVALID_ARG;
   }
@@ -1062,9 +1138,11 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
   auto run = [&]() -> collo_status {
     if (phase == 1) return R.factor(0, precision);
     if (phase == 2) return R.solve(0, precision, 0);
+    if (phase == 4) return R.factor(0, precision, 1);
+    if (phase == 5) return R.factor(0, precision, 2);
     return R.eval(0, 1, 0, 2, true);
   };
-  if (phase == 2 && (s = R.factor(0, precision)) != COLLO_OK) return s;
+  if ((phase == 2 || phase == 5) && (s = R.factor(0, precision)) != COLLO_OK) return s;
   if ((s = run()) != COLLO_OK) return s;
   cudaEvent_t e0, e1;
   COLLO_CUDA(cudaEventCreate(&e0));
@@ -1080,7 +1158,7 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
   cudaEventDestroy(e1);
   *ms_per_launch = t / reps;
   for (int i = 0; i < count; ++i)
-    if (phase <= 2) probs[i]->factored = precision;
+    if (phase <= 2 || phase == 5) probs[i]->factored = precision;
   return R.check_barrier();
 }
 
@@ -1125,9 +1203,14 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
   COLLO_CUDA(cudaSetDevice(sv->R.device));
   Runner& R = sv->R;
   collo_status s;
-  // admit waiting jobs into free slots within the device-memory budget
+  // admit waiting jobs into free slots within the device-memory budget, in
+  // groups of at least admit_min (initialising a group costs one forward
+  // sweep of the longest horizon, whatever the group's size)
   std::vector<IpmInst*> fresh;
-  while (!sv->waiting.empty()) {
+  int n_free = 0, n_busy = 0;
+  for (auto* j : sv->slots) (j ? n_busy : n_free)++;
+  const bool admit = n_busy == 0 || n_free >= std::min(sv->admit_min, (int)sv->slots.size());
+  while (admit && !sv->waiting.empty()) {
     auto* j = sv->waiting.front();
     int slot = -1;
     for (int k = 0; k < (int)sv->slots.size(); ++k)
@@ -1142,7 +1225,11 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     sv->active_bytes += (int64_t)j->prob->arena.bytes;
     fresh.push_back(&j->I);
   }
-  if ((s = ipm_begin(R, fresh)) != COLLO_OK) return s;
+  {
+    ProfClock prof(R.stream);
+    if (!fresh.empty()) { prof.mark(PF_ADMIT); prof.round(PF_ADMIT); }
+    if ((s = ipm_begin(R, fresh)) != COLLO_OK) return s;
+  }
   std::vector<IpmInst*> act;
   for (auto* j : sv->slots)
     if (j) act.push_back(&j->I);
@@ -1163,6 +1250,25 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
   if (n_waiting) *n_waiting = (int)sv->waiting.size();
   return COLLO_OK;
 }
+
+int collo_phase_profile(double* ms, long long* rounds, int n, int reset) {
+  const int m = std::min(n, (int)PF_N);
+  for (int k = 0; k < m; ++k) {
+    if (ms) ms[k] = g_prof_ms[k];
+    if (rounds) rounds[k] = g_prof_rounds[k];
+  }
+  if (reset)
+    for (int k = 0; k < PF_N; ++k) { g_prof_ms[k] = 0.0; g_prof_rounds[k] = 0; }
+  return g_prof_on > 0 ? (int)PF_N : 0;
+}
+
+collo_status collo_server_set_admission(collo_server* sv, int min_free_slots) {
+  if (!sv || min_free_slots < 1) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
+  sv->admit_min = min_free_slots;
+  return COLLO_OK;
+}
+
+void* collo_server_stream(collo_server* sv) { return sv ? (void*)sv->R.stream : nullptr; }
 
 collo_status collo_server_poll(collo_server* sv, long long ticket, collo_result* res) {
   if (!sv || !res) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
