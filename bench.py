@@ -13,7 +13,7 @@ at once, admitted as slots free up (in groups of ``--admit``), and every
 server step advances all admitted solves by one Newton step in batched
 launches, in the mixed-precision path (FP32 element factorization and block
 cyclic reduction, FP64 parameter Schur complement, residuals and refinement,
-FP64 factorization once mu < 1e-6).  ``value`` = Newton steps per second over
+FP64 factorization where refinement from FP32 fails).  ``value`` = Newton steps per second over
 all Q solves.  Beside it: one lock-step batch of ``--slots`` starts (no
 refill), the same path and the plain FP64 path on a single instance,
 per-solve latency percentiles, the parameter agreement with FP64 solves, an

@@ -171,8 +171,8 @@ typedef struct collo_ipm_options {
   double max_wall_time;       /* seconds, default 3600 (paper's 1 h cap)          */
   int precision;              /* COLLO_PRECISION_*                                 */
   double mixed_mu_switch;     /* MIXED: use FP64 factorization once mu < this
-                                 (default 1e-6; 0 = never by mu).  Independently, a
-                                 MIXED solve whose refinement ends above a relative
+                                 (default 0 = never by mu).  Independently, a MIXED
+                                 solve whose refinement ends above a relative
                                  residual of 1e-6 after refine_max sweeps redoes
                                  that step with an FP64 factorization and keeps
                                  FP64 from then on                               */
@@ -185,7 +185,8 @@ typedef struct collo_ipm_options {
 typedef struct collo_result {
   collo_status status;
   int iterations;             /* Newton steps taken */
-  int factorizations;         /* KKT factorizations (inertia corrections included) */
+  int factorizations;         /* KKT factorizations (inertia corrections included,
+                                 the speculative second candidates too)          */
   int line_search_trials;
   int refinement_sweeps;      /* FP64 iterative-refinement sweeps over all steps */
   int fp64_factorizations;    /* of the factorizations, those in FP64 (MIXED: after a

@@ -81,6 +81,33 @@ collo_status ensure_factor_storage(collo_problem* pr, int precision) {
   return precision == COLLO_PRECISION_MIXED ? alloc_factor(pr, pr->f32) : alloc_factor(pr, pr->f64);
 }
 
+collo_status ensure_spare_storage(collo_problem* pr, int precision) {
+  collo_status s = precision == COLLO_PRECISION_MIXED ? alloc_factor(pr, pr->f32_spare)
+                                                       : alloc_factor(pr, pr->f64_spare);
+  if (s != COLLO_OK || pr->spare_S) return s;
+  const size_t p = pr->P.p;
+  DevArena& A = pr->arena;
+  DevSchur& S = pr->S_spare;
+  S.S = A.alloc<double>(p * p);
+  S.Sd = A.alloc<double>(p);
+  S.xth = A.alloc<double>(p);
+  S.inertia = A.alloc<long long>(3);
+  S.diag = A.alloc<double>(p);
+  if (!S.S || !S.Sd || !S.xth || !S.inertia || !S.diag) {
+    set_error("device allocation failed for the spare Schur storage");
+    return COLLO_ERR_OOM;
+  }
+  pr->spare_S = true;
+  return COLLO_OK;
+}
+
+void swap_spare(collo_problem* pr, int precision) {
+  if (precision == COLLO_PRECISION_MIXED) std::swap(pr->f32, pr->f32_spare);
+  else std::swap(pr->f64, pr->f64_spare);
+  std::swap(pr->S, pr->S_spare);
+  pr->inst.S = pr->S;
+}
+
 static bool finite_all(const double* v, int n) {
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(v[i])) return false;

@@ -180,8 +180,8 @@ __device__ inline int find_item(const int* __restrict__ pre, int A, int t) {
 // Launches whose dynamic shared memory exceeds this opt in through
 // cudaFuncAttributeMaxDynamicSharedMemorySize.  Without the opt-in a block may
 // use 48 KB of static plus dynamic shared memory; the kernels here declare
-// at most 16 KB statically, so 32 KB of dynamic memory always fits.
-constexpr size_t SMEM_OPTIN_ABOVE = 32 * 1024;
+// at most 32 KB statically, so 16 KB of dynamic memory always fits.
+constexpr size_t SMEM_OPTIN_ABOVE = 16 * 1024;
 
 // ---- error handling -----------------------------------------------------------
 void set_error(const std::string& msg);

@@ -291,10 +291,19 @@ __device__ inline void load4(const Pair<double>* p, double x[4], double y[4]) {
   }
 }
 
+template <typename T>
+struct Pivot {
+  T a, b, d;
+};
+// Correctly rounded reciprocal (the same value as 1 / x).
+__device__ inline float recip_rn(float x) { return __frcp_rn(x); }
+__device__ inline double recip_rn(double x) { return __drcp_rn(x); }
+constexpr int RT_MAX_PAIRS = 2 * RT_MAX_TR + 2;   // pairs of a block of <= 124 rows
+
 template <typename T, int TPT, class Entry, class Sink, class Bar>
 __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry entry,
                                   T* __restrict__ Lout, int lds, T* __restrict__ Dout, Sink sink,
-                                  Bar bar, Pair<T>* ub, int& pos, int& neg, int& zero) {
+                                  Bar bar, Pair<T>* ub, Pivot<T>* pivs, int* cnt) {
   const int R = (ext + 3) >> 2, ntile = R * (R + 1) / 2;
   for (int r = tid; r < 2 * RT_UB; r += nt) ub[r] = Pair<T>{T(0), T(0)};
   int ti[TPT], tj[TPT];
@@ -331,14 +340,14 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
     const T det = pa * pd - pb * pb;
     T ia, ib, id;
     if (det != T(0) && isfinite(det)) {
-      const T inv = T(1) / det;
+      const T inv = recip_rn(det);
       ia = pd * inv; ib = -pb * inv; id = pa * inv;
     } else {
       ia = ib = id = T(0);
     }
     if (tid == 0) {
       Dout[3 * q + 0] = pa; Dout[3 * q + 1] = pb; Dout[3 * q + 2] = pd;
-      pivot_inertia((double)pa, (double)pb, (double)pd, pos, neg, zero);
+      pivs[q] = Pivot<T>{pa, pb, pd};
     }
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
@@ -380,6 +389,17 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
         if (r < ext && c <= r && c >= cs) sink(r, c, a[j][u][v]);
       }
   }
+  // inertia of the pivots (exact FP64 sign test), off the elimination's
+  // critical path: cnt[0..2] = (pos, neg, zero) after the final barrier
+  if (tid < 3) cnt[tid] = 0;
+  bar();
+  int pos = 0, neg = 0, zero = 0;
+  for (int q = tid; q < npairs; q += nt)
+    pivot_inertia((double)pivs[q].a, (double)pivs[q].b, (double)pivs[q].d, pos, neg, zero);
+  if (pos) atomicAdd(&cnt[0], pos);
+  if (neg) atomicAdd(&cnt[1], neg);
+  if (zero) atomicAdd(&cnt[2], zero);
+  bar();
 }
 
 struct CtaBar {
@@ -395,119 +415,123 @@ struct HalfBar {
   }
 };
 
-// Shared-memory staging of one element for elem_factor_rt (T, then ints):
-// D[4][4], JZ and Wzz [3][n][n], JT and Wzt [3][n][p], Wobj [n][4][4],
-// sigma [4][n], and a descriptor per local index (species, point,
-// constraint, multiplier flag; or the parameter index) that replaces
-// elem_entry's divisions.  All loads are contiguous per element; the values
-// are rounded to T once, and the few entries that sum several terms add them
-// in T.
-__host__ __device__ inline size_t elem_stage_vals(int n, int p) {
-  return 16 + 6 * (size_t)n * n + 6 * (size_t)n * p + 20 * (size_t)n;
-}
+// Element block of elem_factor_rt, assembled in shared memory as a packed
+// lower triangle (entry (r, c), c <= r, at r (r + 1) / 2 + c) by structured
+// scatter passes over the element's derivative blocks, then loaded into the
+// threads' register tiles; after the elimination the trailing blocks go back
+// through the same buffer and leave in coalesced stores.
 template <typename T>
 __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
-  return sizeof(T) * elem_stage_vals(P.n, P.p) + sizeof(int) * (size_t)(P.ext + 1);
+  return sizeof(T) * ((size_t)P.ext * (P.ext + 1) / 2);
 }
-constexpr int DS_THETA = 1 << 28, DS_DUAL = 1 << 24;
+__device__ inline int tri_at(int r, int c) { return r * (r + 1) / 2 + c; }
+// i / d and i % d for 0 <= i < 2^22 and 1 <= d <= 4096 through the float
+// reciprocal inv = 1 / d: (i + 0.5) / d lies at least 0.5 / d from an integer,
+// far more than the float rounding of the product, so the truncation is exact.
+__device__ inline int quot(int i, int d, float inv) {
+  return (int)(((float)i + 0.5f) * inv);
+}
+// local index of the state of point j / the multiplier of constraint k
+// (groups (z1,c1), (z2,c2), (z0,c3), (z3,c0))
+__device__ inline int loc_state(int j, int s, int n) {
+  return 2 * ((j == 0 ? 2 : (j == 3 ? 3 : j - 1)) * n + s);
+}
+__device__ inline int loc_dual(int k, int s, int n) { return 2 * ((k == 0 ? 3 : k - 1) * n + s) + 1; }
 
 // Element condensation (same elimination as elem_factor_one) with
 // pair_eliminate_rt over the nt threads of the block.
 template <typename T, int TPT>
 __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
                                const double* __restrict__ sigma, double dw, double dc,
-                               const DevFactor<T>& F, int e, Pair<T>* ub, T* stage) {
+                               const DevFactor<T>& F, int e, Pair<T>* ub, T* blk) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
-  const size_t nn3 = 3 * (size_t)n * n, np3 = 3 * (size_t)n * p;
-  T* sD = stage;
-  T* sJZ = sD + 16;
-  T* sWzz = sJZ + nn3;
-  T* sJT = sWzz + nn3;
-  T* sWzt = sJT + np3;
-  T* sWobj = sWzt + np3;
-  T* sSig = sWobj + 16 * (size_t)n;
-  int* desc = reinterpret_cast<int*>(sSig + 4 * (size_t)n);
-  for (int i = tid; i < 16; i += nt) sD[i] = (T)P.D[i >> 2][i & 3];
-  for (size_t i = tid; i < nn3; i += nt) {
-    sJZ[i] = (T)E.JZ[(size_t)e * nn3 + i];
-    sWzz[i] = (T)E.Wzz[(size_t)e * nn3 + i];
-  }
-  for (size_t i = tid; i < np3; i += nt) {
-    sJT[i] = (T)E.JT[(size_t)e * np3 + i];
-    sWzt[i] = (T)E.Wzt[(size_t)e * np3 + i];
-  }
-  for (int i = tid; i < 16 * n; i += nt) sWobj[i] = (T)E.Wobj[(size_t)e * 16 * n + i];
-  for (int i = tid; i < 4 * n; i += nt)
-    sSig[i] = (T)((sigma ? sigma[(size_t)e * 4 * n + i] : 0.0) + dw);
-  for (int a = tid; a < ext; a += nt) {
-    if (a >= m) {
-      desc[a] = DS_THETA | (a - m);
-    } else {
-      const int pa = a >> 1, g = pa / n, s = pa - g * n;
-      desc[a] = s | (grp_point(g) << 16) | (grp_con(g) << 20) | ((a & 1) ? DS_DUAL : 0);
-    }
-  }
-  const T mdc = (T)(-dc);
+  const int nn = n * n, np = n * p, ntri = ext * (ext + 1) / 2;
+  auto put = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] = v; };
+  auto add = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] += v; };
+  for (int i = tid; i < ntri; i += nt) blk[i] = T(0);
   __syncthreads();
-  // entry (a, b), a >= b, of the bordered element block (as elem_entry)
-  auto entry = [&](int a, int b) -> T {
-    const int da = desc[a], db = desc[b];
-    const int sb = db & 0xFFFF;
-    if (da & DS_THETA) {
-      if (db & DS_THETA) return T(0);
-      const int q = da & 0xFFFF;
-      if (!(db & DS_DUAL)) {
-        const int j = (db >> 16) & 15;
-        return j >= 1 ? sWzt[((j - 1) * n + sb) * p + q] : T(0);
-      }
-      const int k = (db >> 20) & 15;
-      return k >= 1 ? sJT[((k - 1) * n + sb) * p + q] : T(0);
-    }
-    const int sa = da & 0xFFFF;
-    const bool adual = da & DS_DUAL, bdual = db & DS_DUAL;
-    if (!adual && !bdual) {
-      const int ja = (da >> 16) & 15, jb = (db >> 16) & 15;
-      T v = T(0);
-      if (sa == sb) v += sWobj[(sa * NP + ja) * NP + jb];
-      if (ja == jb && ja >= 1) v += sWzz[((ja - 1) * n + sa) * n + sb];
-      if (a == b) v += sSig[ja * n + sa];
-      return v;
-    }
-    if (adual && bdual) return a == b ? mdc : T(0);
-    int kd, sd, jp, sp;
-    if (adual) { kd = (da >> 20) & 15; sd = sa; jp = (db >> 16) & 15; sp = sb; }
-    else { kd = (db >> 20) & 15; sd = sb; jp = (da >> 16) & 15; sp = sa; }
-    if (kd == 0) return (jp == 0 && sd == sp) ? T(1) : T(0);
-    T v = (sd == sp) ? sD[kd * NP + jp] : T(0);
-    if (jp == kd) v += sJZ[((kd - 1) * n + sd) * n + sp];
-    return v;
-  };
-  T* Aif = F.Aif + (size_t)e * n2 * n2;
-  T* Bif = F.Bif + (size_t)e * n2 * p;
-  double* Sc = F.Scon + (size_t)e * p * p;
-  // trailing block: interface (2n x 2n), its border (p x 2n), parameter part
-  auto sink = [&](int r, int c, T val) {
-    if (r < m) {
-      Aif[(r - i0) * n2 + (c - i0)] = val;
-      Aif[(c - i0) * n2 + (r - i0)] = val;
-    } else if (c < m) {
-      Bif[(c - i0) * p + (r - m)] = val;
-    } else {
-      Sc[(r - m) * p + (c - m)] = (double)val;
-      Sc[(c - m) * p + (r - m)] = (double)val;
-    }
-  };
-  int pos = 0, neg = 0, zero = 0;
+  // 1. disjoint entries: point Hessian blocks, the identity parts of the
+  //    collocation rows (D[k][j]), continuity / initial rows, -delta_c, border
+  const double* Wzz = E.Wzz + (size_t)e * 3 * nn;
+  const double* JZ = E.JZ + (size_t)e * 3 * nn;
+  const double* Wzt = E.Wzt + (size_t)e * 3 * np;
+  const double* JT = E.JT + (size_t)e * 3 * np;
+  const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
+  for (int i = tid; i < 3 * nn; i += nt) {
+    const int rs = quot(i, n, inv_n), sb = i - rs * n;   // rs = k n + sa
+    const int k = quot(rs, n, inv_n), sa = rs - k * n;
+    if (sa >= sb) put(loc_state(k + 1, sa, n), loc_state(k + 1, sb, n), (T)Wzz[i]);
+  }
+  for (int i = tid; i < 12 * n; i += nt) {
+    const int kj = quot(i, n, inv_n), s2 = i - kj * n, k = (kj >> 2) + 1, j = kj & 3;
+    put(loc_dual(k, s2, n), loc_state(j, s2, n), (T)P.D[k][j]);
+  }
+  for (int s2 = tid; s2 < n; s2 += nt) put(loc_dual(0, s2, n), loc_state(0, s2, n), T(1));
+  for (int i = tid; i < 4 * n; i += nt) {
+    const int k = quot(i, n, inv_n), s2 = i - k * n;
+    const int a = loc_dual(k, s2, n);
+    put(a, a, (T)(-dc));
+  }
+  for (int i = tid; i < 3 * np; i += nt) {
+    const int ks = quot(i, p, inv_p), q = i - ks * p;     // ks = k n + s
+    const int k = quot(ks, n, inv_n), s2 = ks - k * n;
+    put(m + q, loc_state(k + 1, s2, n), (T)Wzt[i]);
+    put(m + q, loc_dual(k + 1, s2, n), (T)JT[i]);
+  }
+  __syncthreads();
+  // 2. sums onto those: objective blocks (same species across points) and the
+  //    -h df/dz part of the collocation rows
+  const double* Wobj = E.Wobj + (size_t)e * 16 * n;
+  for (int i = tid; i < 16 * n; i += nt) {
+    const int s2 = i >> 4, ja = (i >> 2) & 3, jb = i & 3;
+    const int a = loc_state(ja, s2, n), b = loc_state(jb, s2, n);
+    if (a >= b) add(a, b, (T)Wobj[i]);
+  }
+  for (int i = tid; i < 3 * nn; i += nt) {
+    const int rs = quot(i, n, inv_n), sp = i - rs * n;   // rs = k n + sd
+    const int k = quot(rs, n, inv_n), sd = rs - k * n;
+    add(loc_dual(k + 1, sd, n), loc_state(k + 1, sp, n), (T)JZ[i]);
+  }
+  __syncthreads();
+  // 3. barrier diagonal and delta_w on the states
+  for (int i = tid; i < 4 * n; i += nt) {
+    const int j = quot(i, n, inv_n), s2 = i - j * n;
+    const int a = loc_state(j, s2, n);
+    add(a, a, (T)((sigma ? sigma[(size_t)e * 4 * n + i] : 0.0) + dw));
+  }
+  __syncthreads();
+  auto entry = [&](int r, int c) -> T { return blk[tri_at(r, c)]; };
+  auto sink = [&](int r, int c, T val) { blk[tri_at(r, c)] = val; };
+  __shared__ Pivot<T> pivs[RT_MAX_PAIRS];
+  __shared__ int cnt[3];
   pair_eliminate_rt<T, TPT>(tid, nt, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                            F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pos, neg, zero);
+                            F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pivs, cnt);
   if (tid == 0) {
-    F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
+    F.inert[e * 3 + 0] = cnt[0]; F.inert[e * 3 + 1] = cnt[1]; F.inert[e * 3 + 2] = cnt[2];
+  }
+  // trailing block: interface (2n x 2n, both triangles), its border (p x 2n),
+  // parameter part (FP64)
+  const float inv_n2 = 1.f / (float)n2;
+  T* Aif = F.Aif + (size_t)e * n2 * n2;
+  for (int i = tid; i < n2 * n2; i += nt) {
+    const int u = quot(i, n2, inv_n2), v = i - u * n2;
+    Aif[i] = u >= v ? blk[tri_at(i0 + u, i0 + v)] : blk[tri_at(i0 + v, i0 + u)];
+  }
+  T* Bif = F.Bif + (size_t)e * n2 * p;
+  for (int i = tid; i < n2 * p; i += nt) {
+    const int u = quot(i, p, inv_p), q = i - u * p;
+    Bif[i] = blk[tri_at(m + q, i0 + u)];
+  }
+  double* Sc = F.Scon + (size_t)e * p * p;
+  for (int i = tid; i < p * p; i += nt) {
+    const int q = quot(i, p, inv_p), q2 = i - q * p;
+    Sc[i] = (double)(q >= q2 ? blk[tri_at(m + q, m + q2)] : blk[tri_at(m + q2, m + q)]);
   }
   T* C = F.Cpl + (size_t)e * n * n;
   for (int idx = tid; idx < n * n; idx += nt) {
-    const int s2 = idx / n, t = idx - s2 * n;
+    const int s2 = quot(idx, n, inv_n), t = idx - s2 * n;
     C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
   }
 }
@@ -625,13 +649,17 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
 // Its inputs are first staged in `stage` (T elements, bcr_stage_elems):
 // the block's interface block [2n][2n], its coupling [n][n], the right
 // neighbour's coupling [n][n] and its border [2n][p].
+// After the elimination the same buffer holds the trailing block (2n + p rows,
+// packed lower triangle) on its way to the neighbours.
 __host__ __device__ inline size_t bcr_stage_elems(int n, int p) {
-  return 6 * (size_t)n * n + 2 * (size_t)n * p;
+  const size_t in = 6 * (size_t)n * n + 2 * (size_t)n * p, m2 = 2 * (size_t)n + p;
+  const size_t out = m2 * (m2 + 1) / 2;
+  return in > out ? in : out;
 }
 template <typename T, int TPT>
 __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int stride,
                               int final_level, int bi, int tid, HalfBar bar, Pair<T>* ub,
-                              T* stage) {
+                              T* stage, Pivot<T>* pivs, int* cnt) {
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
@@ -645,11 +673,14 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
     const T* gC = F.Cpl + (size_t)i * n * n;
     const T* gCR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
     const T* gB = F.Bif + (size_t)i * n2 * p;
+#pragma unroll 4
     for (int k = tid; k < 4 * n * n; k += 128) Ai[k] = gA[k];
+#pragma unroll 4
     for (int k = tid; k < n * n; k += 128) {
       Ci[k] = gC[k];
       CR[k] = gCR ? gCR[k] : T(0);
     }
+#pragma unroll 4
     for (int k = tid; k < n2 * p; k += 128) Bi[k] = gB[k];
   }
   bar();
@@ -662,49 +693,54 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
       return (R >= 0 && !(b & 1)) ? CR[(a - 3 * n) * n + (b >> 1)] : T(0);
     return Bi[b * p + (a - 4 * n)];  // theta row q = a - 4n
   };
-  // the trailing (Schur) block goes to the neighbours and the parameter part
-  T* AL = L >= 0 ? F.Aif + (size_t)L * n2 * n2 : nullptr;
-  T* BL = L >= 0 ? F.Bif + (size_t)L * n2 * p : nullptr;
-  T* AR = R >= 0 ? F.Aif + (size_t)R * n2 * n2 : nullptr;
-  T* BR = R >= 0 ? F.Bif + (size_t)R * n2 * p : nullptr;
-  T* CRw = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
-  double* Sc = F.Scon + (size_t)(N + i) * p * p;
-  auto sink = [&](int r, int c, T val) {
-    if (r < 3 * n) {                               // z3(L) x z3(L)
-      if (L < 0) return;
-      const int t = r - n2, t2 = c - n2;
-      AL[(2 * t) * n2 + 2 * t2] += val;
-      if (t != t2) AL[(2 * t2) * n2 + 2 * t] += val;
-    } else if (r < 4 * n) {
-      if (R < 0) return;
-      const int s = r - 3 * n;
-      if (c < 3 * n) {                             // c0(R) x z3(L): new coupling
-        CRw[s * n + (c - n2)] = L >= 0 ? val : T(0);
-      } else {                                     // c0(R) x c0(R)
-        const int s2 = c - 3 * n;
-        AR[(2 * s + 1) * n2 + 2 * s2 + 1] += val;
-        if (s != s2) AR[(2 * s2 + 1) * n2 + 2 * s + 1] += val;
-      }
-    } else {
-      const int q = r - 4 * n;
-      if (c < 3 * n) {
-        if (L >= 0) BL[(2 * (c - n2)) * p + q] += val;
-      } else if (c < 4 * n) {
-        if (R >= 0) BR[(2 * (c - 3 * n) + 1) * p + q] += val;
-      } else {
-        const int q2 = c - 4 * n;
-        Sc[q * p + q2] = (double)val;
-        Sc[q2 * p + q] = (double)val;
-      }
-    }
-  };
-  int pos = 0, neg = 0, zero = 0;
+  // the trailing (Schur) block, local rows [z3 of L (n) | c0 of R (n) | theta (p)],
+  // is collected in the staging buffer (the inputs are in registers by now) ...
+  const int b2 = 2 * n;
+  auto sink = [&](int r, int c, T val) { stage[tri_at(r - b2, c - b2)] = val; };
   pair_eliminate_rt<T, TPT>(tid, 128, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
-                            F.Db + (size_t)i * n * 3, sink, bar, ub, pos, neg, zero);
+                            F.Db + (size_t)i * n * 3, sink, bar, ub, pivs, cnt);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
-    in[0] = pos; in[1] = neg; in[2] = zero;
+    in[0] = cnt[0]; in[1] = cnt[1]; in[2] = cnt[2];
   }
+  // ... and added into the neighbours in coalesced passes of independent
+  // read-modify-writes: z3 x z3 into the left neighbour's interface block and
+  // border, c0 x c0 into the right one's, the new coupling c0(R) x z3(L), and
+  // the p x p part into this block's parameter contribution
+  auto tr = [&](int a, int b) { return a >= b ? stage[tri_at(a, b)] : stage[tri_at(b, a)]; };
+  const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
+  if (L >= 0) {
+    T* AL = F.Aif + (size_t)L * n2 * n2;
+    for (int k = tid; k < n * n; k += 128) {
+      const int t = quot(k, n, inv_n), t2 = k - t * n;
+      AL[(2 * t) * n2 + 2 * t2] += tr(t, t2);
+    }
+    T* BL = F.Bif + (size_t)L * n2 * p;
+    for (int k = tid; k < n * p; k += 128) {
+      const int t = quot(k, p, inv_p), q = k - t * p;
+      BL[(2 * t) * p + q] += tr(2 * n + q, t);
+    }
+  }
+  if (R >= 0) {
+    T* AR = F.Aif + (size_t)R * n2 * n2;
+    T* CRw = F.Cpl + (size_t)R * n * n;
+    for (int k = tid; k < n * n; k += 128) {
+      const int s2 = quot(k, n, inv_n), t = k - s2 * n;
+      AR[(2 * s2 + 1) * n2 + 2 * t + 1] += tr(n + s2, n + t);
+      CRw[k] = L >= 0 ? tr(n + s2, t) : T(0);
+    }
+    T* BR = F.Bif + (size_t)R * n2 * p;
+    for (int k = tid; k < n * p; k += 128) {
+      const int s2 = quot(k, p, inv_p), q = k - s2 * p;
+      BR[(2 * s2 + 1) * p + q] += tr(2 * n + q, n + s2);
+    }
+  }
+  double* Sc = F.Scon + (size_t)(N + i) * p * p;
+  for (int k = tid; k < p * p; k += 128) {
+    const int q = quot(k, p, inv_p), q2 = k - q * p;
+    Sc[k] = (double)tr(2 * n + q, 2 * n + q2);
+  }
+  bar();   // the buffer is restaged by this half's next block
 }
 
 // Tiles per thread of bcr_factor_rt for P (0: use bcr_factor_one).
@@ -725,11 +761,13 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
   if constexpr (BT > 0) {
     // two blocks of the level per CUDA block, one per half
     __shared__ PivotBuf<T> ub[2];
+    __shared__ Pivot<T> pivs[2][RT_MAX_PAIRS];
+    __shared__ int cnt[2][3];
     const int half = threadIdx.x >> 7;
     T* stage = reinterpret_cast<T*>(smraw) + half * bcr_stage_elems(P.n, P.p);
     for (int bi = 2 * blockIdx.x + half; bi < nblk; bi += 2 * gridDim.x)
       bcr_factor_rt<T, BT>(P, F, stride, final_level, bi, threadIdx.x & 127, HalfBar{1 + half},
-                           ub[half].v, stage);
+                           ub[half].v, stage, pivs[half], cnt[half]);
   } else {
     const int bext = P.bext, ld = odd_ld(bext);
     T* Lp = reinterpret_cast<T*>(smraw);
@@ -1191,6 +1229,8 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     if constexpr (BT > 0) {
       // instances with flag 8: two blocks of the level per CUDA block
       __shared__ PivotBuf<T> ubh[2];
+      __shared__ Pivot<T> pivh[2][RT_MAX_PAIRS];
+      __shared__ int cnth[2][3];
       const int half = threadIdx.x >> 7;
       for (int t = 2 * blockIdx.x + half; t < tot; t += 2 * gridDim.x) {
         const int k = fin ? t : find_item(pre, A, t);
@@ -1201,7 +1241,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
         T* stage = reinterpret_cast<T*>(smraw + half * ((smem_bytes / 2) & ~size_t(15)));
         bcr_factor_rt<T, BT>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
                              fin ? 0 : t - pre[k], threadIdx.x & 127, HalfBar{1 + half}, ubh[half].v,
-                             stage);
+                             stage, pivh[half], cnth[half]);
       }
     }
     for (int t = blockIdx.x; bcr_full && t < tot; t += gridDim.x) {

@@ -120,6 +120,11 @@ struct FactorStore {
 struct collo_problem;
 namespace collo {
 collo_status ensure_factor_storage(collo_problem* pr, int precision);
+// Spare storage of `precision` (and the spare Schur block); swap_spare
+// exchanges the primary and spare factorization of `precision` together with
+// the Schur blocks.
+collo_status ensure_spare_storage(collo_problem* pr, int precision);
+void swap_spare(collo_problem* pr, int precision);
 collo_status factor_internal(collo_problem* prob, double dw, double dc, int precision,
                              long long inertia[3]);
 collo_status solve_internal(collo_problem* prob, const double* b, double* sol, int refine_max,
@@ -147,6 +152,13 @@ struct collo_problem {
   collo::DevArena arena;
   collo::FactorStore<double> f64;
   collo::FactorStore<float> f32;
+  // spare factorization and Schur storage: the second candidate of a
+  // speculative inertia-correction round is factored here (swapped with the
+  // primary storage when it is the one chosen)
+  collo::FactorStore<double> f64_spare;
+  collo::FactorStore<float> f32_spare;
+  collo::DevSchur S_spare{};
+  bool spare_S = false;
   int factored = -1;          // precision of the current factorization, -1 none
   bool evaluated = false;
   int n_slabs = 0;

@@ -26,7 +26,7 @@
 namespace collo {
 
 constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
-constexpr size_t KSMEM_LIMIT = 220 * 1024;
+constexpr size_t KSMEM_LIMIT = 200 * 1024;   // dynamic; leaves room for 27 KB static
 // Relative KKT residual above which refinement from an FP32 factorization
 // counts as failed (the step is then redone with an FP64 factorization).
 constexpr double ESCALATE_REL = 1e-6;
@@ -115,14 +115,16 @@ struct Runner {
       COLLO_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
       own_stream = true;
     }
-    COLLO_CUDA(cudaMalloc(&d_insts, sizeof(DevInst) * cap));
-    COLLO_CUDA(cudaMalloc(&d_outs, sizeof(double) * OUTS * cap));
-    COLLO_CUDA(cudaMemset(d_outs, 0, sizeof(double) * OUTS * cap));
-    COLLO_CUDA(cudaMallocHost(&h_outs, sizeof(double) * OUTS * cap));
+    // slots [0, cap) hold the problems, [cap, 2 cap) their shadows (spare
+    // factorization storage for speculative inertia correction)
+    COLLO_CUDA(cudaMalloc(&d_insts, sizeof(DevInst) * 2 * cap));
+    COLLO_CUDA(cudaMalloc(&d_outs, sizeof(double) * OUTS * 2 * cap));
+    COLLO_CUDA(cudaMemset(d_outs, 0, sizeof(double) * OUTS * 2 * cap));
+    COLLO_CUDA(cudaMallocHost(&h_outs, sizeof(double) * OUTS * 2 * cap));
     COLLO_CUDA(cudaMalloc(&gbar, sizeof(GridBar)));
     COLLO_CUDA(cudaMemset(gbar, 0, sizeof(GridBar)));
-    h_insts.assign(cap, DevInst{});
-    probs.assign(cap, nullptr);
+    h_insts.assign(2 * cap, DevInst{});
+    probs.assign(2 * cap, nullptr);
     for (auto& pl : plans) {
       COLLO_CUDA(cudaEventCreateWithFlags(&pl.ev_int, cudaEventDisableTiming));
       COLLO_CUDA(cudaEventCreateWithFlags(&pl.ev_prm, cudaEventDisableTiming));
@@ -130,7 +132,9 @@ struct Runner {
     return COLLO_OK;
   }
 
-  // Place problem pr in slot s (its descriptor, with out pointing into d_outs).
+  // Place problem pr in slot s (its descriptor, with out pointing into d_outs),
+  // and its shadow in slot capacity + s: the same problem with the spare
+  // factorization and Schur storage.
   collo_status attach(int s, collo_problem* pr) {
     DevInst I = pr->inst;
     I.F32 = pr->f32.F;
@@ -138,11 +142,21 @@ struct Runner {
     I.out = d_outs + (size_t)s * OUTS;
     h_insts[s] = I;
     probs[s] = pr;
+    const int sh = shadow(s);
+    I.F32 = pr->f32_spare.F;
+    I.F64 = pr->f64_spare.F;
+    I.S = pr->S_spare;
+    I.out = d_outs + (size_t)sh * OUTS;
+    h_insts[sh] = I;
+    probs[sh] = pr;
     COLLO_CUDA(cudaMemcpyAsync(d_insts + s, &h_insts[s], sizeof(DevInst), cudaMemcpyHostToDevice,
                                stream));
+    COLLO_CUDA(cudaMemcpyAsync(d_insts + sh, &h_insts[sh], sizeof(DevInst),
+                               cudaMemcpyHostToDevice, stream));
     COLLO_CUDA(cudaStreamSynchronize(stream));
     return COLLO_OK;
   }
+  int shadow(int s) const { return capacity + s; }
 
   const DevProb& P(int s) const { return h_insts[s].P; }
   double* out(int s) { return h_outs + (size_t)s * OUTS; }
@@ -300,7 +314,7 @@ struct Runner {
 
   // Copy the per-instance outputs to the host and wait.
   collo_status read_outs() {
-    COLLO_CUDA(cudaMemcpyAsync(h_outs, d_outs, sizeof(double) * OUTS * capacity,
+    COLLO_CUDA(cudaMemcpyAsync(h_outs, d_outs, sizeof(double) * OUTS * 2 * capacity,
                                cudaMemcpyDeviceToHost, stream));
     COLLO_CUDA(cudaStreamSynchronize(stream));
     for (auto& pl : plans) { pl.int_pending = false; pl.prm_pending = false; }
@@ -653,37 +667,76 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
   auto factor_solve = [&](std::vector<IpmInst*> fac, std::vector<IpmInst*>& redo) -> collo_status {
     std::vector<IpmInst*> list = fac;
     prof.mark(PF_FACTOR);
+    // Inertia correction (Wachter & Biegler 2006, Section 3.1): the candidate
+    // regularisations of one iteration are 0, then c1 = 1e-4 or
+    // max(dw_min, dw_last / 3), then c1 times 100 (no history) or 8, ... until
+    // the inertia is right.  From the second round on, each instance factors two
+    // consecutive candidates at once (the second in its shadow slot) and takes
+    // the first of the two, in sequence order, whose inertia is right: the same
+    // regularisation as the one-at-a-time sequence, in fewer rounds.
+    std::map<int, double> dw2;   // slot -> second candidate of this round (0: none)
     while (!fac.empty()) {
       prof.round(PF_FACTOR);
       std::vector<int> gr[2];
-      for (auto* I : fac) gr[I->prec == COLLO_PRECISION_MIXED ? 1 : 0].push_back(I->slot);
+      for (auto* I : fac) {
+        const int g = I->prec == COLLO_PRECISION_MIXED ? 1 : 0;
+        gr[g].push_back(I->slot);
+        auto it = dw2.find(I->slot);
+        if (it != dw2.end() && it->second > 0) gr[g].push_back(R.shadow(I->slot));
+      }
       for (int g = 0; g < 2; ++g) {
         if (gr[g].empty()) continue;
-        if ((st = R.set_plan(g == 1 ? 1 : 2, gr[g])) != COLLO_OK) return st;
-        if ((st = R.set_params(g == 1 ? 1 : 2, fill_mu)) != COLLO_OK) return st;
-        if ((st = R.factor(g == 1 ? 1 : 2, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64)) != COLLO_OK)
+        const int pl = g == 1 ? 1 : 2;
+        if ((st = R.set_plan(pl, gr[g])) != COLLO_OK) return st;
+        if ((st = R.set_params(pl, [&](int k, int s, InstParams& ip) {
+               if (s >= R.capacity) {
+                 fill_mu(k, s - R.capacity, ip);
+                 ip.dw = dw2[s - R.capacity];
+               } else {
+                 fill_mu(k, s, ip);
+               }
+             })) != COLLO_OK)
+          return st;
+        if ((st = R.factor(pl, g ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64)) != COLLO_OK)
           return st;
       }
       if ((st = R.read_outs()) != COLLO_OK) return st;
       if ((st = R.check_barrier()) != COLLO_OK) return st;
+      auto inertia_ok = [&](int s, int base) {
+        long long in[3];
+        std::memcpy(in, R.out(s) + O_INERT, sizeof(in));
+        return in[0] == R.h_insts[base].n_x && in[1] == R.h_insts[base].n_c && in[2] == 0;
+      };
       std::vector<IpmInst*> again;
       for (auto* I : fac) {
-        I->facs++;
-        if (I->prec != COLLO_PRECISION_MIXED) I->facs64++;
-        I->prob->factored = I->prec;
-        I->prob->fac_dw = I->dw;
-        I->prob->fac_dc = I->dc;
-        long long in[3];
-        std::memcpy(in, R.out(I->slot) + O_INERT, sizeof(in));
-        const bool good = in[0] == R.h_insts[I->slot].n_x && in[1] == R.h_insts[I->slot].n_c && in[2] == 0;
+        const double second = dw2.count(I->slot) ? dw2[I->slot] : 0.0;
+        const int nf = second > 0 ? 2 : 1;
+        I->facs += nf;
+        if (I->prec != COLLO_PRECISION_MIXED) I->facs64 += nf;
+        bool good = inertia_ok(I->slot, I->slot);
+        if (!good && second > 0 && inertia_ok(R.shadow(I->slot), I->slot)) {
+          swap_spare(I->prob, I->prec);
+          if ((st = R.attach(I->slot, I->prob)) != COLLO_OK) return st;
+          I->dw = second;
+          good = true;
+        }
         if (good) {
+          I->prob->factored = I->prec;
+          I->prob->fac_dw = I->dw;
+          I->prob->fac_dc = I->dc;
           if (I->dw > 0) I->dw_last = I->dw;
+          dw2.erase(I->slot);
           continue;
         }
         const Opt& op = I->o;
-        if (I->dw == 0.0) I->dw = I->dw_last == 0.0 ? op.dw_0 : std::max(op.dw_min, op.kw_minus * I->dw_last);
-        else I->dw *= I->dw_last == 0.0 ? op.kw_plus_bar : op.kw_plus;
-        if (I->dw > op.dw_max) { I->status = COLLO_ERR_INERTIA; continue; }
+        const double last = second > 0 ? second : I->dw;
+        const double mult = I->dw_last == 0.0 ? op.kw_plus_bar : op.kw_plus;
+        const double c1 = last == 0.0 ? (I->dw_last == 0.0 ? op.dw_0
+                                                          : std::max(op.dw_min, op.kw_minus * I->dw_last))
+                                      : last * mult;
+        if (c1 > op.dw_max) { I->status = COLLO_ERR_INERTIA; dw2.erase(I->slot); continue; }
+        I->dw = c1;
+        dw2[I->slot] = c1 * mult <= op.dw_max ? c1 * mult : 0.0;
         again.push_back(I);
       }
       fac = again;
@@ -876,9 +929,10 @@ static collo_status ipm_prepare(Runner& R, int slot, collo_problem* pr, const do
                                 const Opt& o, IpmInst& I) {
   collo_status s = ensure_factor_storage(pr, COLLO_PRECISION_FP64);
   if (s != COLLO_OK) return s;
+  if ((s = ensure_spare_storage(pr, COLLO_PRECISION_FP64)) != COLLO_OK) return s;
   if (o.precision == COLLO_PRECISION_MIXED) {
-    s = ensure_factor_storage(pr, COLLO_PRECISION_MIXED);
-    if (s != COLLO_OK) return s;
+    if ((s = ensure_factor_storage(pr, COLLO_PRECISION_MIXED)) != COLLO_OK) return s;
+    if ((s = ensure_spare_storage(pr, COLLO_PRECISION_MIXED)) != COLLO_OK) return s;
   }
   if ((s = R.attach(slot, pr)) != COLLO_OK) return s;
   if (pr->P.p)
@@ -1014,7 +1068,7 @@ void collo_ipm_options_default(collo_ipm_options* o) {
   o->max_iter = 3000;
   o->max_wall_time = 3600.0;
   o->precision = COLLO_PRECISION_FP64;
-  o->mixed_mu_switch = 1e-6;
+  o->mixed_mu_switch = 0.0;
   o->refine_max = 10;
   o->refine_tol = 1e-10;
   o->verbose = 0;
