@@ -8,44 +8,13 @@
 #include <mutex>
 
 #include "collo_internal.cuh"
+#include "resid.cuh"
 #include "problem.cuh"
 
 namespace collo {
 
 cudaError_t launch_chunk_sums(const double* X, int C, int L, double* part, cudaStream_t st);
 
-// Deterministic block reductions (fixed tree over a fixed thread order).
-template <int BS>
-__device__ double block_sum(double v, double* sh) {
-  const int t = threadIdx.x;
-  sh[t] = v;
-  __syncthreads();
-#pragma unroll
-  for (int s = BS / 2; s > 0; s >>= 1) {
-    if (t < s) sh[t] += sh[t + s];
-    __syncthreads();
-  }
-  double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-template <int BS>
-__device__ double block_max(double v, double* sh) {
-  const int t = threadIdx.x;
-  sh[t] = v;
-  __syncthreads();
-#pragma unroll
-  for (int s = BS / 2; s > 0; s >>= 1) {
-    if (t < s) sh[t] = fmax(sh[t], sh[t + s]);
-    __syncthreads();
-  }
-  double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-constexpr int EVAL_BS = 128;
 
 __device__ inline double sum_chunks(const double* __restrict__ part, int G, int L, int l) {
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -327,7 +296,6 @@ k_eval_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
 }
 
 // Sum the per-element partials in a fixed order: phi, |c|_1, |c|_inf, W_thth.
-constexpr int RED_BS = 256;
 __device__ void eval_reduce_one(const DevProb& P, const DevEval& E, int deriv, double* out,
                                 double* sh) {
   const int tid = threadIdx.x;
@@ -376,93 +344,6 @@ k_eval_reduce_b(const DevInst* __restrict__ insts, const int* __restrict__ act, 
   eval_reduce_one(I.P, I.E, deriv, I.out, sh);
 }
 
-// Structured FP64 product y = K v of the regularised KKT matrix
-//   [ W + diag(sigma) + dw I   J^T  ] [vx]
-//   [ J                       -dc I ] [vl]
-// and r = b - y (b may be null: r = -y).  One block per element computes the
-// element's 8n rows and its contribution to the p parameter rows; norms of r
-// per element go to npart[i][0..1] (max |r_x|, max |r_c|).
-__device__ void resid_elem(const DevProb& P, const DevEval& E, const double* __restrict__ sigma,
-                           double dw, double dc, const double* __restrict__ vx,
-                           const double* __restrict__ vl, const double* __restrict__ bx,
-                           double bxs, const double* __restrict__ bc, double bcs,
-                           double* __restrict__ rout, double* __restrict__ thpart,
-                           double* __restrict__ npart, int i, double* red) {
-  const int n = P.n, p = P.p, N = P.N;
-  const int tid = threadIdx.x;
-  const size_t nz = (size_t)N * NP * n, nx = nz + p;
-  const size_t zoff = (size_t)i * NP * n;
-  const double* vz = vx;
-  const double* vt = vx ? vx + nz : nullptr;
-  const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
-  const double* JZ = E.JZ + (size_t)i * KC * nn;
-  const double* JT = E.JT + (size_t)i * KC * np_;
-  const double* Wzz = E.Wzz + (size_t)i * KC * nn;
-  const double* Wzt = E.Wzt + (size_t)i * KC * np_;
-  const double* Wob = E.Wobj + (size_t)i * n * NP * NP;
-  double mx = 0.0, mc = 0.0;
-  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
-    const int j = idx / n, s = idx - j * n;
-    // primal row z[i][j][s]
-    double y = 0.0;
-    if (vz) {
-#pragma unroll
-      for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
-      if (j >= 1) {
-        const double* wr = Wzz + (size_t)(j - 1) * nn + (size_t)s * n;
-        for (int t = 0; t < n; ++t) y += wr[t] * vz[zoff + j * n + t];
-        const double* wt = Wzt + (size_t)(j - 1) * np_ + (size_t)s * p;
-        for (int q = 0; q < p; ++q) y += wt[q] * vt[q];
-      }
-      y += ((sigma ? sigma[zoff + idx] : 0.0) + dw) * vz[zoff + idx];
-    }
-    if (vl) {
-      if (j >= 1) {
-        const double* jz = JZ + (size_t)(j - 1) * nn;
-        for (int t = 0; t < n; ++t) y += jz[(size_t)t * n + s] * vl[zoff + j * n + t];
-      }
-#pragma unroll
-      for (int k = 1; k < NP; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
-      if (j == 0) y += vl[zoff + s];
-      if (j == KC && i + 1 < N) y -= vl[zoff + NP * n + s];
-    }
-    double rr = (bx ? bxs * bx[zoff + idx] : 0.0) - y;
-    if (rout) rout[zoff + idx] = rr;
-    mx = fmax(mx, fabs(rr));
-    // dual row c[i][j][s]
-    double yc = 0.0;
-    if (vz) {
-      if (j == 0) {
-        yc = vz[zoff + s] - (i > 0 ? vz[zoff - n + s] : 0.0);
-      } else {
-#pragma unroll
-        for (int l = 0; l < NP; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];
-        const double* jz = JZ + (size_t)(j - 1) * nn + (size_t)s * n;
-        for (int t = 0; t < n; ++t) yc += jz[t] * vz[zoff + j * n + t];
-        const double* jt = JT + (size_t)(j - 1) * np_ + (size_t)s * p;
-        for (int q = 0; q < p; ++q) yc += jt[q] * vt[q];
-      }
-    }
-    if (vl) yc -= dc * vl[zoff + idx];
-    double rc = (bc ? bcs * bc[zoff + idx] : 0.0) - yc;
-    if (rout) rout[nx + zoff + idx] = rc;
-    mc = fmax(mc, fabs(rc));
-  }
-  // this element's part of the parameter rows
-  for (int q = tid; q < p; q += EVAL_BS) {
-    double y = 0.0;
-    for (int k = 1; k < NP; ++k)
-      for (int s = 0; s < n; ++s) {
-        if (vz) y += Wzt[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vz[zoff + k * n + s];
-        if (vl) y += JT[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vl[zoff + k * n + s];
-      }
-    thpart[(size_t)i * p + q] = y;
-  }
-  mx = block_max<EVAL_BS>(mx, red);
-  mc = block_max<EVAL_BS>(mc, red);
-  if (tid == 0) { npart[i * 2 + 0] = mx; npart[i * 2 + 1] = mc; }
-}
-
 __global__ void __launch_bounds__(EVAL_BS)
 k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
             const double* __restrict__ vx, const double* __restrict__ vl,
@@ -470,32 +351,6 @@ k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, d
             double* __restrict__ rout, double* __restrict__ thpart, double* __restrict__ npart) {
   __shared__ double red[EVAL_BS];
   resid_elem(P, E, sigma, dw, dc, vx, vl, bx, bxs, bc, bcs, rout, thpart, npart, blockIdx.x, red);
-}
-
-// Residual modes of the batched product (which vectors of the instance):
-//   R_DUAL: r_x = -(grad + J^T lambda - zl + zu)   (dual infeasibility)
-//   R_RHS:  Newton right-hand side -[grad phi_mu + J^T lambda; c] into ka
-//   R_IR:   r = ka - K kb with the factorization's sigma / delta_w / delta_c into kr
-enum ResidMode { R_DUAL = 0, R_RHS = 1, R_IR = 2 };
-
-struct ResidArgs {
-  const double *sigma, *vx, *vl, *bx, *bc, *th_extra;
-  double bxs, bcs, dw, dc;
-  double* rout;
-};
-
-__device__ inline ResidArgs resid_args(const DevInst& I, const InstParams& pr, int mode) {
-  ResidArgs a{};
-  if (mode == R_DUAL) {
-    a.vl = I.lam; a.bx = I.E.grad; a.bxs = -1.0; a.th_extra = I.zlmzu;
-  } else if (mode == R_RHS) {
-    a.vl = I.lam; a.bx = I.E.grad; a.bxs = -1.0; a.bc = I.E.c; a.bcs = -1.0;
-    a.th_extra = I.bar; a.rout = I.ka;
-  } else {
-    a.sigma = I.sigma; a.vx = I.kb; a.vl = I.kb + I.n_x; a.bx = I.ka; a.bxs = 1.0;
-    a.bc = I.ka + I.n_x; a.bcs = 1.0; a.dw = pr.dw; a.dc = pr.dc; a.rout = I.kr;
-  }
-  return a;
 }
 
 __global__ void __launch_bounds__(EVAL_BS)
@@ -508,49 +363,6 @@ k_kkt_resid_b(const DevInst* __restrict__ insts, const int* __restrict__ act, in
   const ResidArgs a = resid_args(I, prm[k], mode);
   resid_elem(I.P, I.E, a.sigma, a.dw, a.dc, a.vx, a.vl, a.bx, a.bxs, a.bc, a.bcs, a.rout,
              I.thpart, I.npart, t - pre[k], red);
-}
-
-// Parameter rows of r = b - K v, and the global norms:
-// out[0] = max|r_x|, out[1] = max|r_c|, out[2] = max|b| (b may be null).
-// The element contributions thpart[N][p] are summed by warp w for the
-// columns q = w, w + 8, ...: lane-strided partial sums, then a fixed
-// shuffle tree.
-__device__ void resid_theta_one(const DevProb& P, const DevEval& E,
-                                const double* __restrict__ sigma, double dw,
-                                const double* __restrict__ vx, const double* __restrict__ bx,
-                                double bxs, const double* __restrict__ bc,
-                                double* __restrict__ rout, const double* __restrict__ thpart,
-                                const double* __restrict__ npart,
-                                const double* __restrict__ th_extra, double* __restrict__ out,
-                                double* sh) {
-  const int tid = threadIdx.x, p = P.p, N = P.N;
-  const int lane = tid & 31, warp = tid >> 5;
-  const size_t nz = (size_t)N * NP * P.n, nx = nz + p;
-  double mx = 0.0, mc = 0.0, mb = 0.0;
-  for (int q = warp; q < p; q += RED_BS / 32) {
-    double y = 0.0;
-    for (int i = lane; i < N; i += 32) y += thpart[(size_t)i * p + q];
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    if (lane == 0) {
-      if (vx) y += (E.wtt[q] + (sigma ? sigma[nz + q] : 0.0) + dw) * vx[nz + q];
-      if (th_extra) y -= th_extra[q];
-      const double rr = (bx ? bxs * bx[nz + q] : 0.0) - y;
-      if (rout) rout[nz + q] = rr;
-      mx = fmax(mx, fabs(rr));
-    }
-  }
-  for (int i = tid; i < N; i += RED_BS) {
-    mx = fmax(mx, npart[i * 2 + 0]);
-    mc = fmax(mc, npart[i * 2 + 1]);
-  }
-  if (bx)
-    for (size_t k = tid; k < nx; k += RED_BS) mb = fmax(mb, fabs(bx[k]));
-  if (bc)
-    for (size_t k = tid; k < nz; k += RED_BS) mb = fmax(mb, fabs(bc[k]));
-  mx = block_max<RED_BS>(mx, sh);
-  mc = block_max<RED_BS>(mc, sh);
-  mb = block_max<RED_BS>(mb, sh);
-  if (tid == 0) { out[0] = mx; out[1] = mc; out[2] = mb; }
 }
 
 __global__ void __launch_bounds__(RED_BS)
