@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the reduced uneven-batch and Poisson-stream measurements")
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of --only-batch")
     ap.add_argument("--slots", type=int, default=64)
@@ -411,6 +413,8 @@ def run_ours(args):
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Q * (8 * inst.p + 64),
                       "what": f"{Q} x collo_problem_create from host arrays + serving + "
                               "theta* read back, per step", "steps": k_e}
+    if not args.no_extra:
+        out.update(uneven_and_stream(collo, workloads, local))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst, iters=6)
     if rank == 0:
@@ -418,6 +422,84 @@ def run_ours(args):
     server.close()
     for pb in probs:
         pb.close()
+
+
+def uneven_and_stream(collo, workloads, device):
+    """Reduced-size versions of the uneven multistart batch and the Poisson
+    serving stream (species 5-15, 100-800 elements): mixed path through the
+    server, against the plain FP64 path solving the same instances one by one."""
+    import numpy as np
+    out = {}
+    # uneven batch: all submitted at once into as many slots
+    insts = workloads.multistart_batch(count=32, n_range=(5, 15), N_range=(100, 800))
+    probs = [collo.Problem(i, device=device) for i in insts]
+    srv = collo.Server(len(probs), device=device, precision=collo.MIXED, tol=TOL)
+    for rep in range(2):   # the first pass allocates the factor storage
+        t0 = time.perf_counter()
+        tk = [srv.submit(p) for p in probs]
+        while True:
+            act, wait = srv.step()
+            if act == 0 and wait == 0:
+                break
+        dt = time.perf_counter() - t0
+        res = [srv.poll(t) for t in tk]
+    srv.close()
+    t64 = 0.0
+    for p in probs:
+        t1 = time.perf_counter()
+        p.ipm_solve(precision=collo.FP64, want_x=False, tol=TOL)
+        t64 += time.perf_counter() - t1
+    lat = [1e3 * r["wall"] for r in res]
+    out["uneven_batch"] = {
+        "instances": len(probs), "species": [5, 15], "elements": [100, 800],
+        "sizes_n_N": [[i.n, i.N] for i in insts],
+        "newton_steps_per_s": sum(r["iterations"] for r in res) / dt,
+        "solves_per_s": len(res) / dt,
+        "fp64_single_solves_per_s": len(probs) / t64,
+        "solves_speedup_vs_fp64_single": (len(res) / dt) / (len(probs) / t64),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "status_counts": {str(s_): sum(1 for r in res if r["status"] == s_)
+                          for s_ in sorted(set(r["status"] for r in res))},
+        "what": "config-4 shape at reduced sizes: one server step advances every instance; "
+                "fp64 single = the same instances solved one after another on the plain FP64 path"}
+    for p in probs:
+        p.close()
+    # Poisson stream: requests submitted at their arrival times (host clock)
+    stream = workloads.serving_stream(count=48, rate_hz=200.0, n_range=(5, 15),
+                                      N_range=(200, 800))
+    probs = [collo.Problem(i, device=device) for _, i in stream]
+    srv = collo.Server(64, device=device, precision=collo.MIXED, tol=TOL)
+    srv.set_admission(1)
+    for rep in range(2):
+        t0 = time.perf_counter()
+        nxt, tk, done_at = 0, {}, {}
+        while len(done_at) < len(stream):
+            now = time.perf_counter() - t0
+            while nxt < len(stream) and stream[nxt][0] <= now:
+                tk[nxt] = srv.submit(probs[nxt])
+                nxt += 1
+            act, wait = srv.step()
+            for j, t in tk.items():
+                if j not in done_at and srv.poll(t) is not None:
+                    done_at[j] = time.perf_counter() - t0
+            if act == 0 and wait == 0 and nxt < len(stream):
+                time.sleep(max(0.0, stream[nxt][0] - (time.perf_counter() - t0)))
+        dt = time.perf_counter() - t0
+        res = [srv.poll(tk[j]) for j in range(len(stream))]
+    srv.close()
+    lat = [1e3 * (done_at[j] - stream[j][0]) for j in range(len(stream))]
+    out["poisson_stream"] = {
+        "requests": len(stream), "rate_hz": 200.0, "species": [5, 15], "elements": [200, 800],
+        "newton_steps_per_s": sum(r["iterations"] for r in res) / dt,
+        "solves_per_s": len(res) / dt,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "status_counts": {str(s_): sum(1 for r in res if r["status"] == s_)
+                          for s_ in sorted(set(r["status"] for r in res))},
+        "what": "config-5 shape at reduced sizes: seeded exponential gaps, each request "
+                "submitted at its arrival time; latency = arrival to result (host clock)"}
+    for p in probs:
+        p.close()
+    return out
 
 
 def cpu_baseline(inst, iters):

@@ -182,6 +182,9 @@ __device__ inline int find_item(const int* __restrict__ pre, int A, int t) {
 // use 48 KB of static plus dynamic shared memory; the kernels here declare
 // at most 32 KB statically, so 16 KB of dynamic memory always fits.
 constexpr size_t SMEM_OPTIN_ABOVE = 16 * 1024;
+// Dynamic shared memory of a factorization block above which its elimination
+// runs in a global slab instead (allocation and use both test against it).
+constexpr size_t FACTOR_SMEM_LIMIT = 200 * 1024;
 
 // ---- error handling -----------------------------------------------------------
 void set_error(const std::string& msg);

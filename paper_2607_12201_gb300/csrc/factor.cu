@@ -25,6 +25,10 @@
 // Inertia is counted from every pivot block (Sylvester's law of inertia).
 // T = double (plain path) or float (mixed path; residuals and refinement
 // are FP64 elsewhere).
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "collo_internal.cuh"
 
 namespace collo {
@@ -1244,6 +1248,8 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
                              stage, pivh[half], cnth[half]);
       }
     }
+    // the whole-block pass reuses the shared memory the halves staged in
+    if (BT > 0 && bcr_full) __syncthreads();
     for (int t = blockIdx.x; bcr_full && t < tot; t += gridDim.x) {
       const int k = fin ? t : find_item(pre, A, t);
       if (BT > 0 && (flags[k] & 8)) continue;
@@ -1364,7 +1370,11 @@ size_t bcr_factor_smem(const DevProb& P, bool full) {
   return v;
 }
 
-constexpr size_t SMEM_LIMIT = 220 * 1024;
+// Largest dynamic shared memory of a factorization block.  One limit decides
+// both whether a block is factored in shared memory (here and in the batched
+// plans) and whether its global slab is allocated; it leaves room for the
+// static shared memory of the persistent kernels (< 27 KB) under 227 KB.
+constexpr size_t SMEM_LIMIT = FACTOR_SMEM_LIMIT;
 
 template <typename T>
 bool elem_uses_smem(const DevProb& P) { return elem_factor_smem<T>(P, true) <= SMEM_LIMIT; }
@@ -1402,6 +1412,25 @@ cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double*
   return cudaGetLastError();
 }
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize, set only when a launch needs
+// more than the kernel's setting so far (per device).
+template <typename KernelT>
+static void opt_in_smem(KernelT kern, size_t bytes) {
+  if (bytes <= SMEM_OPTIN_ABOVE) return;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[{dev, (const void*)kern}];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      cudaSuccess)
+    cur = bytes;
+  else
+    cudaGetLastError();
+}
+
 static int g_coop_checked = -1;   // device supports cooperative launches (-1: unknown)
 static bool coop_supported() {
   if (g_coop_checked < 0) {
@@ -1415,13 +1444,35 @@ static bool coop_supported() {
 
 template <typename KernelT>
 static int coop_grid(KernelT kern, int threads, size_t smem, int want) {
-  int dev = 0, sms = 0, per = 0;
+  // co-resident blocks per (device, kernel, threads, shared memory), cached:
+  // the query costs more host time than a launch
+  struct Key {
+    int dev;
+    const void* k;
+    int threads;
+    size_t smem;
+    bool operator<(const Key& o) const {
+      return std::tie(dev, k, threads, smem) < std::tie(o.dev, o.k, o.threads, o.smem);
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, int> cache;
+  int dev = 0;
   cudaGetDevice(&dev);
+  const Key key{dev, (const void*)kern, threads, smem};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return std::max(0, std::min(want, it->second));
+  }
+  int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = per * sms;
   return std::max(0, std::min(want, per * sms));
 }
 
@@ -1523,9 +1574,7 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
   if (A == 0) return cudaSuccess;
   if ((parts & 1) && rt_threads > 0 && tot_elem > 0) {
     if (rt_threads > RT_MAX_THREADS) return cudaErrorInvalidValue;
-    if (rt_smem > SMEM_OPTIN_ABOVE)
-      cudaFuncSetAttribute(k_elem_factor_rt_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)rt_smem);
+    opt_in_smem(k_elem_factor_rt_b<T>, rt_smem);
     count_launch();
     k_elem_factor_rt_b<T><<<tot_elem, rt_threads, rt_smem, st>>>(insts, act, A, pre_elem, prm,
                                                                  flags);
@@ -1534,8 +1583,7 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
   }
   if (!(parts & 2)) return cudaSuccess;
   auto kern = bcr_tpt == 1 ? k_factor_b<T, 1> : bcr_tpt == 2 ? k_factor_b<T, 2> : k_factor_b<T, 0>;
-  if (smem > SMEM_OPTIN_ABOVE)
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  opt_in_smem(kern, smem);
   int grid = coop_grid(kern, FBS, smem, grid_cap);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
@@ -1551,8 +1599,7 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
   if (A == 0) return cudaSuccess;
   size_t smem = std::max(sizeof(T) * (size_t)per_warp * (FBS / 32),
                          sizeof(double) * (size_t)std::max(max_p, 1));
-  if (smem > SMEM_OPTIN_ABOVE)
-    cudaFuncSetAttribute(k_solve_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  opt_in_smem(k_solve_b<T>, smem);
   int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,

@@ -26,7 +26,7 @@
 namespace collo {
 
 constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
-constexpr size_t KSMEM_LIMIT = 200 * 1024;   // dynamic; leaves room for 27 KB static
+constexpr size_t KSMEM_LIMIT = FACTOR_SMEM_LIMIT;
 // Relative KKT residual above which refinement from an FP32 factorization
 // counts as failed (the step is then redone with an FP64 factorization).
 constexpr double ESCALATE_REL = 1e-6;
@@ -92,6 +92,8 @@ struct Runner {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int capacity = 0;
+  int* h_err = nullptr;        // pinned copy of the grid-barrier error flag
+  bool err_fresh = false;      // h_err read after the last launch
   DevInst* d_insts = nullptr;
   std::vector<DevInst> h_insts;
   std::vector<collo_problem*> probs;
@@ -104,6 +106,7 @@ struct Runner {
     if (d_insts) cudaFree(d_insts);
     if (d_outs) cudaFree(d_outs);
     if (h_outs) cudaFreeHost(h_outs);
+    if (h_err) cudaFreeHost(h_err);
     if (gbar) cudaFree(gbar);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -121,6 +124,8 @@ struct Runner {
     COLLO_CUDA(cudaMalloc(&d_outs, sizeof(double) * OUTS * 2 * cap));
     COLLO_CUDA(cudaMemset(d_outs, 0, sizeof(double) * OUTS * 2 * cap));
     COLLO_CUDA(cudaMallocHost(&h_outs, sizeof(double) * OUTS * 2 * cap));
+    COLLO_CUDA(cudaMallocHost(&h_err, sizeof(int)));
+    *h_err = 0;
     COLLO_CUDA(cudaMalloc(&gbar, sizeof(GridBar)));
     COLLO_CUDA(cudaMemset(gbar, 0, sizeof(GridBar)));
     h_insts.assign(2 * cap, DevInst{});
@@ -316,15 +321,22 @@ struct Runner {
   collo_status read_outs() {
     COLLO_CUDA(cudaMemcpyAsync(h_outs, d_outs, sizeof(double) * OUTS * 2 * capacity,
                                cudaMemcpyDeviceToHost, stream));
+    COLLO_CUDA(cudaMemcpyAsync(h_err, &gbar->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     COLLO_CUDA(cudaStreamSynchronize(stream));
+    err_fresh = true;
     for (auto& pl : plans) { pl.int_pending = false; pl.prm_pending = false; }
     return COLLO_OK;
   }
 
+  // Grid-barrier error of the persistent kernels launched so far (read with the
+  // last read_outs when nothing was launched since; otherwise read now).
   collo_status check_barrier() {
-    int err = 0;
-    COLLO_CUDA(cudaMemcpyAsync(&err, &gbar->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    COLLO_CUDA(cudaStreamSynchronize(stream));
+    if (!err_fresh) {
+      COLLO_CUDA(cudaMemcpyAsync(h_err, &gbar->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      COLLO_CUDA(cudaStreamSynchronize(stream));
+    }
+    err_fresh = false;
+    const int err = *h_err;
     if (err) {
       cudaMemsetAsync(&gbar->err, 0, sizeof(int), stream);
       set_error("grid barrier of a persistent kernel timed out");
@@ -349,6 +361,21 @@ struct Runner {
   // parts: 1 element condensation (register-tiled kernel), 2 the rest, 3 both
   collo_status factor(int which, int prec, int parts = 3) {
     Plan& pl = plans[which];
+    err_fresh = false;
+    {
+      // a block factored outside shared memory needs its global slab
+      const int p = prec == COLLO_PRECISION_MIXED ? 1 : 0;
+      const int* fl = pl.h_int + (p ? pl.off_f32 : pl.off_f64);
+      for (int k = 0; k < pl.A; ++k) {
+        const DevInst& I = h_insts[pl.slots[k]];
+        const bool slab = (fl[k] & 3) != 3;
+        const bool has = p ? I.F32.work != nullptr : I.F64.work != nullptr;
+        if (slab && !has) {
+          set_error("internal: factorization block needs a global slab that was not allocated");
+          return COLLO_ERR_DEVICE;
+        }
+      }
+    }
     cudaError_t e;
     const int p = prec == COLLO_PRECISION_MIXED ? 1 : 0;
     if (p)
@@ -368,6 +395,7 @@ struct Runner {
   }
   collo_status solve(int which, int prec, int ir) {
     Plan& pl = plans[which];
+    err_fresh = false;
     cudaError_t e;
     const int want = std::max(pl.A, (pl.tot_elem + 7) / 8);
     if (prec == COLLO_PRECISION_MIXED)

@@ -26,6 +26,32 @@ def _mix():
             W.random_network(12, 24, n_obs=4, M=20, T=5.0, N=33, seed=43, theta0_spread=0.1)]
 
 
+def _mixed_paths():
+    # element blocks of 8n + p = 50 (register tiles), 130 (shared memory) and, in
+    # FP64, 150 rows (216.8 KB: factored in a global slab) in one batch
+    return [W.random_network(5, 10, n_obs=3, M=20, T=5.0, N=24, seed=51, theta0_spread=0.1),
+            W.random_network(13, 26, n_obs=4, M=20, T=5.0, N=20, seed=52, theta0_spread=0.1),
+            W.random_network(15, 30, n_obs=4, M=20, T=5.0, N=18, seed=53, theta0_spread=0.1)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_mixed_factor_paths_equals_alone(collo, prec):
+    P = collo.MIXED if prec == "mixed" else collo.FP64
+    insts = _mixed_paths()
+    alone = []
+    for inst in insts:
+        with collo.Problem(inst) as pb:
+            alone.append(pb.ipm_solve(precision=P, want_x=False, max_iter=12))
+    probs = [collo.Problem(inst) for inst in insts]
+    mixed = collo.batch_solve(probs, precision=P, max_iter=12)
+    for a, b in zip(alone, mixed):
+        assert a["status"] == b["status"]
+        assert a["iterations"] == b["iterations"]
+        assert np.array_equal(a["theta"], b["theta"])
+    for pb in probs:
+        pb.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_batch_equals_alone_bitwise(collo, prec):
     P = collo.MIXED if prec == "mixed" else collo.FP64
