@@ -37,7 +37,7 @@ constexpr int FBS = 256;   // threads per factor block
 constexpr int FTY = FBS / 32;
 
 __device__ inline void pivot_inertia(double a, double b, double d, int& pos, int& neg, int& zero) {
-  double det = a * d - b * b;
+  const double det = fma(a, d, -(b * b));
   if (!(det == det) || det == 0.0 || !isfinite(det)) { zero += 2; return; }
   if (det < 0) { pos += 1; neg += 1; return; }
   if (a + d > 0) pos += 2; else neg += 2;
@@ -75,9 +75,9 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
       for (int q = q0; q < pe; ++q) {
         const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
         const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
-        const T det = a * d - b * b;
+        const T det = fma(a, d, -(b * b));
         T ia, ib, id;
-        if (det != T(0) && isfinite((double)det)) {
+        if (det != T(0) && isfinite(det)) {
           const T inv = T(1) / det;
           ia = d * inv; ib = -b * inv; id = a * inv;
         } else {
@@ -85,8 +85,8 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
         }
         for (int r = c1 + 1 + lane; r < msz; r += 32) {
           const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
-          const T l0 = x0 * ia + x1 * ib;
-          const T l1 = x0 * ib + x1 * id;
+          const T l0 = fma(x0, ia, x1 * ib);
+          const T l1 = fma(x0, ib, x1 * id);
           Up[r * PLD + kk] = x0; Up[r * PLD + kk + 1] = x1;
           Lp[r * PLD + kk] = l0; Lp[r * PLD + kk + 1] = l1;
           Lout[(size_t)c0 * lds + r] = l0;
@@ -104,7 +104,7 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
             T* Ar = A + (size_t)r * ld;
             const int cmax = min(cend - 1, r);
             for (int c = c1 + 1; c <= cmax; ++c)
-              Ar[c] -= l0 * Up[c * PLD + kk] + l1 * Up[c * PLD + kk + 1];
+              Ar[c] = fma(-l1, Up[c * PLD + kk + 1], fma(-l0, Up[c * PLD + kk], Ar[c]));
           }
         __syncwarp();
       }
@@ -135,7 +135,7 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * uc[v];
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(lr[u], uc[v], acc[u][v]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -304,26 +304,57 @@ __device__ inline float recip_rn(float x) { return __frcp_rn(x); }
 __device__ inline double recip_rn(double x) { return __drcp_rn(x); }
 constexpr int RT_MAX_PAIRS = 2 * RT_MAX_TR + 2;   // pairs of a block of <= 124 rows
 
-template <typename T, int TPT, class Entry, class Sink, class Bar>
+// Tiles are owned in pairs along a tile row: pair t is tiles (ti, 2k) and
+// (ti, 2k + 1) (the second absent when 2k + 1 > ti), so the multipliers of the
+// row are formed once for both.  Row ti holds ceil((ti + 1) / 2) pairs and the
+// rows before it floor((ti + 1)^2 / 4).
+__host__ __device__ inline int tile_pairs(int R) { return (R + 1) * (R + 1) / 4; }
+__device__ inline void tile_pair(int t, int& ti, int& k) {
+  int i = (int)(2.f * sqrtf((float)t + 0.25f)) - 1;
+  if (i < 0) i = 0;
+  while (tile_pairs(i + 1) <= t) ++i;
+  while (i > 0 && tile_pairs(i) > t) --i;
+  ti = i;
+  k = t - tile_pairs(i);
+}
+
+// PAIRED: each thread owns TPP row pairs of tiles (above); otherwise TPP
+// single tiles (for latency-bound small blocks, where every thread should
+// hold a tile).
+template <typename T, int TPP, bool PAIRED, class Entry, class Sink, class Bar>
 __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry entry,
                                   T* __restrict__ Lout, int lds, T* __restrict__ Dout, Sink sink,
                                   Bar bar, Pair<T>* ub, Pivot<T>* pivs, int* cnt) {
-  const int R = (ext + 3) >> 2, ntile = R * (R + 1) / 2;
+  constexpr int H = PAIRED ? 2 : 1;
+  const int R = (ext + 3) >> 2, npr = PAIRED ? tile_pairs(R) : R * (R + 1) / 2;
   for (int r = tid; r < 2 * RT_UB; r += nt) ub[r] = Pair<T>{T(0), T(0)};
-  int ti[TPT], tj[TPT];
-  T a[TPT][4][4];
+  int ti[TPP], tj0[TPP];
+  bool two[TPP];
+  T a[TPP][H][4][4];
 #pragma unroll
-  for (int j = 0; j < TPT; ++j) {
+  for (int j = 0; j < TPP; ++j) {
     const int t = tid + nt * j;
-    ti[j] = -1; tj[j] = 0;
-    if (t < ntile) tri_tile(t, ti[j], tj[j]);
+    int k = 0;
+    ti[j] = -1;
+    if (PAIRED) {
+      if (t < npr) tile_pair(t, ti[j], k);
+      tj0[j] = 2 * k;
+      two[j] = tj0[j] + 1 <= ti[j];
+    } else {
+      tj0[j] = 0;
+      if (t < npr) tri_tile(t, ti[j], tj0[j]);
+      two[j] = false;
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int h = 0; h < H; ++h)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int r = 4 * ti[j] + u, c = 4 * tj[j] + v;
-        a[j][u][v] = (ti[j] >= 0 && r < ext && c <= r) ? entry(r, c) : T(0);
-      }
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = 4 * ti[j] + u, c = 4 * (tj0[j] + h) + v;
+          a[j][h][u][v] = (ti[j] >= 0 && (h == 0 || two[j]) && r < ext && c <= r) ? entry(r, c)
+                                                                                  : T(0);
+        }
   }
   bar();
   for (int q = 0; q < npairs; ++q) {
@@ -331,17 +362,19 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
     const bool hi = (c0 & 2) != 0;
     Pair<T>* b = ub + (q & 1) * RT_UB;
 #pragma unroll
-    for (int j = 0; j < TPT; ++j)
-      if (ti[j] >= 0 && tj[j] == tq)
+    for (int j = 0; j < TPP; ++j)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = 4 * ti[j] + u;
-          if (r >= c0 && r < ext)
-            b[r] = Pair<T>{hi ? a[j][u][2] : a[j][u][0], hi ? a[j][u][3] : a[j][u][1]};
-        }
+      for (int h = 0; h < H; ++h)
+        if (ti[j] >= 0 && tj0[j] + h == tq && (h == 0 || two[j]))
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * ti[j] + u;
+            if (r >= c0 && r < ext)
+              b[r] = Pair<T>{hi ? a[j][h][u][2] : a[j][h][u][0], hi ? a[j][h][u][3] : a[j][h][u][1]};
+          }
     bar();
     const T pa = b[c0].x, pb = b[c1].x, pd = b[c1].y;
-    const T det = pa * pd - pb * pb;
+    const T det = fma(pa, pd, -(pb * pb));
     T ia, ib, id;
     if (det != T(0) && isfinite(det)) {
       const T inv = recip_rn(det);
@@ -354,17 +387,16 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
       pivs[q] = Pivot<T>{pa, pb, pd};
     }
 #pragma unroll
-    for (int j = 0; j < TPT; ++j) {
+    for (int j = 0; j < TPP; ++j) {
       if (ti[j] < 0 || 4 * ti[j] + 3 <= c1) continue;   // no live row
-      T l0[4], l1[4], y0[4], y1[4], xr0[4], xr1[4];
+      T l0[4], l1[4], xr0[4], xr1[4];
       load4(b + 4 * ti[j], xr0, xr1);
-      load4(b + 4 * tj[j], y0, y1);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        l0[u] = xr0[u] * ia + xr1[u] * ib;
-        l1[u] = xr0[u] * ib + xr1[u] * id;
+        l0[u] = fma(xr0[u], ia, xr1[u] * ib);
+        l1[u] = fma(xr0[u], ib, xr1[u] * id);
       }
-      if (tj[j] == tq)
+      if (tj0[j] == tq || (two[j] && tj0[j] + 1 == tq))
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int r = 4 * ti[j] + u;
@@ -373,25 +405,35 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
             Lout[(size_t)c1 * lds + r] = l1[u];
           }
         }
-      if (4 * tj[j] + 3 <= c1) continue;                 // no live column
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int h = 0; h < H; ++h) {
+        const int tj = tj0[j] + h;
+        if ((h == 1 && !two[j]) || 4 * tj + 3 <= c1) continue;   // no live column
+        T y0[4], y1[4];
+        load4(b + 4 * tj, y0, y1);
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          a[j][u][v] = fma(-l1[u], y1[v], fma(-l0[u], y0[v], a[j][u][v]));
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            a[j][h][u][v] = fma(-l1[u], y1[v], fma(-l0[u], y0[v], a[j][h][u][v]));
+      }
     }
   }
   const int cs = 2 * npairs;
 #pragma unroll
-  for (int j = 0; j < TPT; ++j) {
+  for (int j = 0; j < TPP; ++j) {
     if (ti[j] < 0) continue;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int h = 0; h < H; ++h) {
+      if (h == 1 && !two[j]) continue;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int r = 4 * ti[j] + u, c = 4 * tj[j] + v;
-        if (r < ext && c <= r && c >= cs) sink(r, c, a[j][u][v]);
-      }
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = 4 * ti[j] + u, c = 4 * (tj0[j] + h) + v;
+          if (r < ext && c <= r && c >= cs) sink(r, c, a[j][h][u][v]);
+        }
+    }
   }
   // inertia of the pivots (exact FP64 sign test), off the elimination's
   // critical path: cnt[0..2] = (pos, neg, zero) after the final barrier
@@ -510,7 +552,7 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   auto sink = [&](int r, int c, T val) { blk[tri_at(r, c)] = val; };
   __shared__ Pivot<T> pivs[RT_MAX_PAIRS];
   __shared__ int cnt[3];
-  pair_eliminate_rt<T, TPT>(tid, nt, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+  pair_eliminate_rt<T, TPT, true>(tid, nt, ext, nint, entry, F.Lel + (size_t)e * (2 * nint) * ext, ext,
                             F.Del + (size_t)e * nint * 3, sink, CtaBar{}, ub, pivs, cnt);
   if (tid == 0) {
     F.inert[e * 3 + 0] = cnt[0]; F.inert[e * 3 + 1] = cnt[1]; F.inert[e * 3 + 2] = cnt[2];
@@ -540,17 +582,17 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   }
 }
 
-// Tiles per thread of elem_factor_rt (2) and its block size for an element
+// Tile pairs per thread of elem_factor_rt (1) and its block size for an element
 // of size ext (a multiple of 32 threads covering every tile; 0 when the
 // element is too large and elem_factor_one is used).
 constexpr int RT_MAX_THREADS = 512;
 template <typename T>
-__host__ __device__ constexpr int rt_tpt() { return 2; }
+__host__ __device__ constexpr int rt_tpt() { return 1; }   // tile pairs per thread
 template <typename T>
 __host__ __device__ inline int rt_block_threads(int ext) {
   const int R = (ext + 3) >> 2;
   if (R > RT_MAX_TR) return 0;
-  const int per = (R * (R + 1) / 2 + rt_tpt<T>() - 1) / rt_tpt<T>();
+  const int per = (tile_pairs(R) + rt_tpt<T>() - 1) / rt_tpt<T>();
   const int nt = (per + 31) / 32 * 32;
   return nt < 64 ? 64 : nt;
 }
@@ -701,7 +743,7 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
   // is collected in the staging buffer (the inputs are in registers by now) ...
   const int b2 = 2 * n;
   auto sink = [&](int r, int c, T val) { stage[tri_at(r - b2, c - b2)] = val; };
-  pair_eliminate_rt<T, TPT>(tid, 128, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
+  pair_eliminate_rt<T, TPT, false>(tid, 128, bext, n, entry, F.Lb + (size_t)i * n2 * bext, bext,
                             F.Db + (size_t)i * n * 3, sink, bar, ub, pivs, cnt);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
@@ -747,9 +789,11 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
   bar();   // the buffer is restaged by this half's next block
 }
 
-// Tiles per thread of bcr_factor_rt for P (0: use bcr_factor_one).
+// Tiles per thread of bcr_factor_rt for P (single tiles; 0: use bcr_factor_one).
 __host__ __device__ inline int bcr_rt_tiles(int bext) {
-  const int R = (bext + 3) >> 2, tpt = (R * (R + 1) / 2 + 127) / 128;
+  const int R = (bext + 3) >> 2;
+  if (R > RT_MAX_TR) return 0;
+  const int tpt = (R * (R + 1) / 2 + 127) / 128;
   return tpt <= 2 ? tpt : 0;
 }
 
@@ -896,11 +940,11 @@ constexpr int SOLVE_WARPS = 4;
 
 template <typename T>
 __device__ inline void pair_solve_d(T a, T b, T d, T w0, T w1, T& v0, T& v1) {
-  const T det = a * d - b * b;
-  if (det != T(0) && isfinite((double)det)) {
-    const T inv = T(1) / det;
-    v0 = (d * w0 - b * w1) * inv;
-    v1 = (-b * w0 + a * w1) * inv;
+  const T det = fma(a, d, -(b * b));
+  if (det != T(0) && isfinite(det)) {
+    const T inv = recip_rn(det);
+    v0 = fma(d, w0, -(b * w1)) * inv;
+    v1 = fma(a, w1, -(b * w0)) * inv;
   } else {
     v0 = T(0); v1 = T(0);
   }
@@ -916,7 +960,7 @@ __device__ void warp_forward(T* w, int msz, int npairs, const T* __restrict__ Lc
     const T w0 = w[c0], w1 = w[c1];
     const T* L0 = Lc + (size_t)c0 * lds;
     const T* L1 = Lc + (size_t)c1 * lds;
-    for (int r = c1 + 1 + lane; r < msz; r += 32) w[r] -= L0[r] * w0 + L1[r] * w1;
+    for (int r = c1 + 1 + lane; r < msz; r += 32) w[r] = fma(-L1[r], w1, fma(-L0[r], w0, w[r]));
     __syncwarp();
   }
 }
@@ -934,8 +978,8 @@ __device__ void warp_backward(T* x, const T* v, int msz, int npairs, const T* __
     T s0 = T(0), s1 = T(0);
     for (int r = c1 + 1 + lane; r < msz; r += 32) {
       const T xr = x[r];
-      s0 += L0[r] * xr;
-      s1 += L1[r] * xr;
+      s0 = fma(L0[r], xr, s0);
+      s1 = fma(L1[r], xr, s1);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
