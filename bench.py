@@ -52,6 +52,10 @@ METRIC = "Newton steps/s (mixed-precision continuous-batching IPM path, config 2
 # directions of the objective (same iterations, same objective to 1e-12); at
 # 1e-8 they agree within the 1e-6 parameter criterion.
 TOL = 1e-8
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# element-condensation launch over 64 config-2 instances, from an ncu capture
+# of that launch (--only-elem-phase --slots 64); None once the kernel changes.
+ELEM_TRAFFIC_S64 = 1.0595e9
 
 
 def parse_args():
@@ -74,6 +78,9 @@ def parse_args():
                     help="run one single-instance solve and exit (for profiler launch lists)")
     ap.add_argument("--only-batch", action="store_true",
                     help="run one batched solve and exit (for profiler launch lists)")
+    ap.add_argument("--only-elem-phase", action="store_true",
+                    help="evaluate --slots config-2 problems at their forward-sweep states and "
+                         "launch the batched element condensation twice (ncu capture)")
     ap.add_argument("--phase-profile", action="store_true",
                     help="serve the queue twice with the driver's phase profile on and print it")
     return ap.parse_args()
@@ -347,7 +354,8 @@ def run_ours(args):
     by_e *= S
     ach = fl_e / (ph["factor_fp32_elements"] * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
-            "frac": ach / peak32, "traffic": None,
+            "frac": ach / peak32,
+            "traffic": ELEM_TRAFFIC_S64 * S / 64 if ELEM_TRAFFIC_S64 else None,
             "peak_source": "measured FP32 FFMA throughput of this GPU (collo_alu_peak)",
             "kernel": f"k_elem_factor_rt_b<float> (element condensation, {S} instances)",
             "algorithmic_flops": fl_e, "algorithmic_bytes": by_e,
@@ -605,6 +613,22 @@ def phase_profile(args):
     server.close()
 
 
+def only_elem_phase(S):
+    from paper_2607_12201_gb300 import build as B
+    B.build()
+    from paper_2607_12201_gb300 import collo, workloads
+    inst = workloads.config2()
+    starts = workloads.multistart_thetas(inst, S, seed=2002)
+    probs = [collo.Problem(inst) for _ in range(S)]
+    for p, th in zip(probs, starts):
+        x, _ = p.initial_states(th)
+        p.eval_raw(x.ctypes.data, None)
+    ms = collo.batch_time_phase(probs, 4, collo.MIXED, reps=1)
+    print(json.dumps({"only_elem_phase": S, "elements": S * inst.N, "ms": ms}), flush=True)
+    for p in probs:
+        p.close()
+
+
 def only_batch(nb):
     from paper_2607_12201_gb300 import build as B
     B.build()
@@ -631,6 +655,8 @@ def main():
         only_batch(args.batch)
     elif args.phase_profile:
         phase_profile(args)
+    elif args.only_elem_phase:
+        only_elem_phase(args.slots)
     elif args.impl == "reference":
         run_reference(args)
     else:
