@@ -172,10 +172,11 @@ typedef struct collo_ipm_options {
   int precision;              /* COLLO_PRECISION_*                                 */
   double mixed_mu_switch;     /* MIXED: use FP64 factorization once mu < this
                                  (default 0 = never by mu).  Independently, a MIXED
-                                 solve whose refinement ends above a relative
-                                 residual of 1e-6 after refine_max sweeps redoes
-                                 that step with an FP64 factorization and keeps
-                                 FP64 from then on                               */
+                                 solve whose refinement fails (relative residual
+                                 above 1e-6 after refine_max sweeps, or no longer
+                                 halving above it) redoes that step with an FP64
+                                 factorization and factors in FP64 for the next
+                                 2, 4, 8, ... iterations (doubling per failure)  */
   int refine_max;             /* max iterative-refinement sweeps (default 10)      */
   double refine_tol;          /* stop refining at ||r||/||b|| <= this (1e-10)       */
   int verbose;                /* print an iteration log to stdout                  */

@@ -474,8 +474,15 @@ static collo_status solve_refine(Runner& R, int which, const std::vector<int>& p
       const double* o = R.out(s);
       const double rn = std::max(o[O_RX], o[O_RC]);
       const double r = rn / std::max(1.0, o[O_BMAX]);
+      const double prev = rel[pos[s]];
       rel[pos[s]] = r;
-      if (r > refine_tol && sweeps[pos[s]] < refine_max && std::isfinite(r)) next.push_back(s);
+      // an FP32-factor refinement above ESCALATE_REL that no longer halves its
+      // residual per sweep ends as a failure (the step is redone in FP64):
+      // stop it now instead of after refine_max sweeps
+      const bool stalled = prec_of_slot[s] == COLLO_PRECISION_MIXED && sweeps[pos[s]] >= 2 &&
+                           r > ESCALATE_REL && r > 0.5 * prev;
+      if (r > refine_tol && sweeps[pos[s]] < refine_max && std::isfinite(r) && !stalled)
+        next.push_back(s);
     }
     if (next.empty()) break;
     for (int s : next) sweeps[pos[s]]++;
@@ -567,7 +574,9 @@ struct IpmInst {
   double mu = 0.1, tau = 0.99, dw_last = 0.0, dw = 0.0, dc = 0.0;
   double theta_max = 0, theta_min = 0, err = INFINITY, phi = NAN;
   int acc = 0, it = 0, facs = 0, facs64 = 0, trials_total = 0, prec = 0, refine_total = 0;
-  bool fp64_factor = false;   // MIXED path: refinement failed once, factor in FP64 from now on
+  // MIXED path after a refinement failure: factor in FP64 until iteration
+  // fp64_until, then try FP32 again; each further failure doubles the hold
+  int fp64_until = 0, fp64_hold = 2;
   std::vector<std::pair<double, double>> filt;
   // line-search temporaries
   double theta_k = 0, phi_k = 0, gphi = 0, alpha = 0, alpha_min = 0, alpha_z = 0;
@@ -667,7 +676,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
       I->filt.clear();
     }
     I->theta_k = o[O_C1] > 0 ? o[O_C1] : 0.0;
-    I->prec = (op.precision == COLLO_PRECISION_MIXED && !I->fp64_factor &&
+    I->prec = (op.precision == COLLO_PRECISION_MIXED && I->it >= I->fp64_until &&
                !(op.mixed_mu_switch > 0 && I->mu < op.mixed_mu_switch))
                   ? COLLO_PRECISION_MIXED : COLLO_PRECISION_FP64;
     I->dc = op.dc_coef * std::pow(I->mu, op.dc_exp);
@@ -688,9 +697,10 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
   if ((st = R.resid(0, 1 /* R_RHS */)) != COLLO_OK) return st;
   // 3. factorization with inertia correction (per precision group), then
   // 4. solve with FP64 refinement.  An instance of the MIXED path whose
-  // refinement leaves a relative residual above ESCALATE_REL after refine_max
-  // sweeps is factored and solved again in FP64, and stays in FP64 for the
-  // rest of its solve.
+  // refinement fails (relative residual above ESCALATE_REL after refine_max
+  // sweeps, or stalled above it) is factored and solved again in FP64, and
+  // factors in FP64 for the next 2, 4, 8, ... iterations (doubling after each
+  // failure) before trying FP32 again.
   std::vector<IpmInst*> go;
   auto factor_solve = [&](std::vector<IpmInst*> fac, std::vector<IpmInst*>& redo) -> collo_status {
     std::vector<IpmInst*> list = fac;
@@ -792,7 +802,8 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
       IpmInst* I = run_now[k];
       I->refine_total += sweeps[k];
       if (I->prec == COLLO_PRECISION_MIXED && !(rel[k] <= ESCALATE_REL)) {
-        I->fp64_factor = true;
+        I->fp64_until = I->it + I->fp64_hold;
+        I->fp64_hold *= 2;
         I->prec = COLLO_PRECISION_FP64;
         I->dw = 0.0;
         redo.push_back(I);
