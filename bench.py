@@ -353,10 +353,16 @@ def run_ours(args):
     fl_e *= S
     by_e *= S
     ach = fl_e / (ph["factor_fp32_elements"] * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
-            "frac": ach / peak32,
+    # ALU peak from the unit counts and the clock: SMs x 128 FP32 lanes x 2 flops
+    # (FMA) x maximum SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_alu = sms * 128 * 2 * mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+            "frac": ach / peak_alu,
             "traffic": ELEM_TRAFFIC_S64 * S / 64 if ELEM_TRAFFIC_S64 else None,
-            "peak_source": "measured FP32 FFMA throughput of this GPU (collo_alu_peak)",
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz; measured "
+                           f"FFMA throughput {peak32:.1f} TFLOP/s (collo_alu_peak)",
             "kernel": f"k_elem_factor_rt_b<float> (element condensation, {S} instances)",
             "algorithmic_flops": fl_e, "algorithmic_bytes": by_e,
             "ms": ph["factor_fp32_elements"],

@@ -29,4 +29,8 @@ nodes; row sums / polynomial exactness of the differentiation weights; the
 order; finite-difference Jacobian and Hessian; brute-force dense solves and
 eigenvalue inertia on tiny KKT systems; an independent reduced-space
 Gauss-Newton solve of the linear-cascade estimation problem.
+
+Parity unpinned: the optimum ``ipm.solve`` reaches on the nonlinear random
+mass-action networks has no independent check beyond the KKT conditions at
+the returned point and the linear-cascade analogue above.
 """
