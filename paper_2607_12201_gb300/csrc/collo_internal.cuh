@@ -80,8 +80,8 @@ struct DevEval {
 // Grid barrier state of the persistent cooperative kernels (device memory,
 // zero-initialised; err != 0 records a barrier that gave up waiting).
 struct GridBar {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int count;   // arrivals in the current launch
+  unsigned int exits;   // blocks that have left the current launch
   int err;
   int pad;
 };

@@ -950,44 +950,129 @@ __device__ inline void pair_solve_d(T a, T b, T d, T w0, T w1, T& v0, T& v1) {
   }
 }
 
-// Forward substitution through a block's eliminated pairs: w (length msz)
-// in shared memory, L columns Lc[c * lds + r].
+// Substitutions through a block's eliminated pairs, one warp per block.  The
+// work is a sequence of items: pair q (columns 2q, 2q+1 of L, stored as
+// Lc[c * lds + r]) restricted to one chunk of SUB_J * 32 of its rows below the
+// pair.  The L values of an item do not depend on the vector being solved, so
+// they are loaded SUB_D items ahead into a register ring: each warp keeps
+// several loads in flight instead of waiting a memory latency per pair.  Per
+// row, the arithmetic and its order are those of the plain column loop.
+constexpr int SUB_J = 4;   // rows per lane in one item (chunks of 128 rows)
+constexpr int SUB_D = 2;   // items loaded ahead
+
+__device__ inline int sub_chunks(int msz, int q) {
+  const int rows = msz - 2 * q - 2;
+  return rows > 0 ? (rows + 32 * SUB_J - 1) / (32 * SUB_J) : 0;
+}
+
+template <typename T>
+__device__ inline void sub_fetch(const T* __restrict__ Lc, int lds, int msz, int q, int k, bool ok,
+                                 T (&a)[SUB_J], T (&b)[SUB_J]) {
+  const int lane = threadIdx.x & 31;
+  const T* L0 = Lc + (size_t)(2 * q) * lds;
+  const T* L1 = L0 + lds;
+  const int r0 = 2 * q + 2 + 32 * SUB_J * k + lane;
+#pragma unroll
+  for (int j = 0; j < SUB_J; ++j) {
+    const int r = r0 + 32 * j;
+    const bool in = ok && r < msz;
+    a[j] = in ? L0[r] : T(0);
+    b[j] = in ? L1[r] : T(0);
+  }
+}
+
+// Forward substitution: w (length msz) in shared memory; after the call w
+// holds L^{-1} w.  Items run over pairs ascending, chunks ascending.
 template <typename T>
 __device__ void warp_forward(T* w, int msz, int npairs, const T* __restrict__ Lc, int lds) {
   const int lane = threadIdx.x & 31;
-  for (int q = 0; q < npairs; ++q) {
-    const int c0 = 2 * q, c1 = c0 + 1;
-    const T w0 = w[c0], w1 = w[c1];
-    const T* L0 = Lc + (size_t)c0 * lds;
-    const T* L1 = Lc + (size_t)c1 * lds;
-    for (int r = c1 + 1 + lane; r < msz; r += 32) w[r] = fma(-L1[r], w1, fma(-L0[r], w0, w[r]));
-    __syncwarp();
+  // consumer and prefetch cursors (pair, chunk); a pair without rows below
+  // it ends the sequence, since every later pair has fewer rows
+  int cq = 0, ck = 0, fq = 0, fk = 0;
+  auto valid = [&](int q) { return q < npairs && sub_chunks(msz, q) > 0; };
+  auto advance = [&](int& q, int& k) {
+    if (++k >= sub_chunks(msz, q)) { ++q; k = 0; }
+  };
+  T a[SUB_D][SUB_J], b[SUB_D][SUB_J];
+#pragma unroll
+  for (int s = 0; s < SUB_D; ++s) {
+    const bool ok = valid(fq);
+    sub_fetch<T>(Lc, lds, msz, fq, fk, ok, a[s], b[s]);
+    if (ok) advance(fq, fk);
   }
+  while (valid(cq)) {
+#pragma unroll
+    for (int s = 0; s < SUB_D; ++s) {
+      if (valid(cq)) {
+        __syncwarp();
+        const T w0 = w[2 * cq], w1 = w[2 * cq + 1];
+        const int r0 = 2 * cq + 2 + 32 * SUB_J * ck + lane;
+#pragma unroll
+        for (int j = 0; j < SUB_J; ++j) {
+          const int r = r0 + 32 * j;
+          if (r < msz) w[r] = fma(-b[s][j], w1, fma(-a[s][j], w0, w[r]));
+        }
+        const bool ok = valid(fq);
+        sub_fetch<T>(Lc, lds, msz, fq, fk, ok, a[s], b[s]);
+        if (ok) advance(fq, fk);
+        advance(cq, ck);
+      }
+    }
+  }
+  __syncwarp();
 }
 
 // Back substitution: x (length msz) holds the known tail values; pairs are
 // solved from the last to the first: x_q = v_q - sum_{r > q} L[r][q] x_r.
+// Every pair is at least one item, so that pairs without rows below them
+// are solved too.
 template <typename T>
 __device__ void warp_backward(T* x, const T* v, int msz, int npairs, const T* __restrict__ Lc,
                               int lds) {
   const int lane = threadIdx.x & 31;
-  for (int q = npairs - 1; q >= 0; --q) {
-    const int c0 = 2 * q, c1 = c0 + 1;
-    const T* L0 = Lc + (size_t)c0 * lds;
-    const T* L1 = Lc + (size_t)c1 * lds;
-    T s0 = T(0), s1 = T(0);
-    for (int r = c1 + 1 + lane; r < msz; r += 32) {
-      const T xr = x[r];
-      s0 = fma(L0[r], xr, s0);
-      s1 = fma(L1[r], xr, s1);
-    }
+  auto nitems = [&](int q) { return max(1, sub_chunks(msz, q)); };
+  int cq = npairs - 1, ck = 0, fq = npairs - 1, fk = 0;
+  auto advance = [&](int& q, int& k) {
+    if (++k >= nitems(q)) { --q; k = 0; }
+  };
+  T a[SUB_D][SUB_J], b[SUB_D][SUB_J];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  for (int s = 0; s < SUB_D; ++s) {
+    const bool ok = fq >= 0;
+    sub_fetch<T>(Lc, lds, msz, ok ? fq : 0, fk, ok, a[s], b[s]);
+    if (ok) advance(fq, fk);
+  }
+  T s0 = T(0), s1 = T(0);
+  while (cq >= 0) {
+#pragma unroll
+    for (int s = 0; s < SUB_D; ++s) {
+      if (cq >= 0) {
+        const int r0 = 2 * cq + 2 + 32 * SUB_J * ck + lane;
+#pragma unroll
+        for (int j = 0; j < SUB_J; ++j) {
+          const int r = r0 + 32 * j;
+          if (r < msz) {
+            const T xr = x[r];
+            s0 = fma(a[s][j], xr, s0);
+            s1 = fma(b[s][j], xr, s1);
+          }
+        }
+        const bool ok = fq >= 0;
+        sub_fetch<T>(Lc, lds, msz, ok ? fq : 0, fk, ok, a[s], b[s]);
+        if (ok) advance(fq, fk);
+        if (ck + 1 >= nitems(cq)) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          }
+          if (lane == 0) { x[2 * cq] = v[2 * cq] - s0; x[2 * cq + 1] = v[2 * cq + 1] - s1; }
+          s0 = T(0); s1 = T(0);
+          __syncwarp();
+        }
+        advance(cq, ck);
+      }
     }
-    if (lane == 0) { x[c0] = v[c0] - s0; x[c1] = v[c1] - s1; }
-    __syncwarp();
   }
 }
 
@@ -1188,32 +1273,50 @@ k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
 // A whole factorization or a whole solve in one cooperative launch: the phases
 // of the elimination tree (elements, each cyclic-reduction level, the
 // parameter block) are separated by a grid barrier instead of kernel
-// boundaries.  The barrier's wait is bounded: after GRID_SPIN_LIMIT polls it
-// records an error in GridBar::err and continues, so a fault shows up as a
-// status on the host instead of a hang.
+// boundaries.  Barrier e of a launch completes when the arrival counter
+// reaches (e + 1) * gridDim.x: a block arrives with one release reduction
+// and waits by polling the counter (no returning atomic on the way, nothing
+// to reset between barriers).  The last block to leave the kernel zeroes the
+// counter for the next launch.  The wait is bounded: after GRID_SPIN_LIMIT
+// polls it records an error in GridBar::err and continues, so a fault shows
+// up as a status on the host instead of a hang.
 constexpr long long GRID_SPIN_LIMIT = 20000000;   // ~1-2 s of polling
 
-__device__ void grid_barrier(GridBar* gb) {
+__device__ inline unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// `epoch` counts the barriers this block has passed in the launch.
+__device__ void grid_barrier(GridBar* gb, unsigned int& epoch) {
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &gb->gen;
-    const unsigned int g = *vgen;
+    const unsigned int target = epoch * gridDim.x;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        __nanosleep(40);
-        if (++spins > GRID_SPIN_LIMIT) { atomicExch(&gb->err, 1); break; }
-      }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
+    long long spins = 0;
+    while (ld_acquire_gpu(&gb->count) < target) {
+      __nanosleep(32);
+      if (++spins > GRID_SPIN_LIMIT) { atomicExch(&gb->err, 1); break; }
     }
-    __threadfence();
   }
   __syncthreads();
+}
+
+// Called by every block as its last statement: every block has passed every
+// barrier once the exit count reaches gridDim.x, so the counters can be zeroed.
+__device__ void grid_exit(GridBar* gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int left = atomicAdd(&gb->exits, 1u) + 1u;
+    if (left == gridDim.x) {
+      atomicExch(&gb->count, 0u);
+      atomicExch(&gb->exits, 0u);
+    }
+  }
 }
 
 // ---- batched persistent kernels -------------------------------------------------------
@@ -1256,6 +1359,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
            const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
            const int* __restrict__ flags, GridBar* gb, size_t smem_bytes, int bcr_full) {
   extern __shared__ unsigned char smraw[];
+  unsigned int ep = 0;
   // 1. element condensation
   for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
     const int k = find_item(pre_elem, A, t);
@@ -1268,7 +1372,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     T* Am = (flags[k] & 1) ? (Up + (size_t)ext * PLD) : (F.work + (size_t)blockIdx.x * ld * ext);
     elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, Lp, Up);
   }
-  grid_barrier(gb);
+  grid_barrier(gb, ep);
   // 2. cyclic-reduction levels, then each instance's final block
   for (int lv = 0; lv <= maxL; ++lv) {
     const int* pre = pre_lv + (size_t)lv * (A + 1);
@@ -1306,7 +1410,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, Lp, Up);
       else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, Lp, Up);
     }
-    grid_barrier(gb);
+    grid_barrier(gb, ep);
   }
   // 3. chunk sums of the parameter contributions
   for (int t = blockIdx.x * FBS + threadIdx.x; t < pre_cs[A]; t += gridDim.x * FBS) {
@@ -1317,7 +1421,7 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     const int it = t - pre_cs[k];
     F.chunkS[it] = chunk_sum_item(F.Scon, 2 * I.P.N, L, G, it / L, it % L);
   }
-  grid_barrier(gb);
+  grid_barrier(gb, ep);
   // 4. parameter Schur complement, one block per instance
   for (int k = blockIdx.x; k < A; k += gridDim.x) {
     const DevInst& I = insts[act[k]];
@@ -1330,35 +1434,55 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       o[0] = I.S.inertia[0]; o[1] = I.S.inertia[1]; o[2] = I.S.inertia[2];
     }
   }
+  grid_exit(gb);
 }
 
+// Batched solve.  Levels below `lsplit` run over the whole grid, a grid
+// barrier after each; from level `lsplit` up (few blocks per instance) one
+// block owns an instance and separates its levels by block barriers, and the
+// same block then solves the parameter system and substitutes back down to
+// level `lsplit`.  Every block solve is the same per-warp code as in the
+// single-instance launches, so the result does not depend on the split.
 template <typename T>
 __global__ void __launch_bounds__(FBS)
 k_solve_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
-          const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
+          const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL, int lsplit,
           const int* __restrict__ pre_cs, int ir, int per_warp, GridBar* gb) {
   extern __shared__ unsigned char smraw[];
+  unsigned int ep = 0;
   const int warp = threadIdx.x >> 5, wpb = FBS / 32;
   const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
   T* wv = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp;
+  auto level_blocks = [&](int lv, int k) {
+    const int* pre = pre_lv + (size_t)lv * (A + 1);
+    return lv == maxL ? 1 : pre[k + 1] - pre[k];
+  };
   for (int t = gw; t < pre_elem[A]; t += nw) {
     const int k = find_item(pre_elem, A, t);
     const DevInst& I = insts[act[k]];
     elem_fwd_one<T>(I.P, inst_factor<T>(I), ir ? I.kr : I.ka, t - pre_elem[k], wv);
   }
-  grid_barrier(gb);
-  for (int lv = 0; lv <= maxL; ++lv) {
+  grid_barrier(gb, ep);
+  for (int lv = 0; lv < lsplit; ++lv) {
     const int* pre = pre_lv + (size_t)lv * (A + 1);
-    const bool fin = lv == maxL;
-    const int tot = fin ? A : pre[A];
-    for (int t = gw; t < tot; t += nw) {
-      const int k = fin ? t : find_item(pre, A, t);
+    for (int t = gw; t < pre[A]; t += nw) {
+      const int k = find_item(pre, A, t);
       const DevInst& I = insts[act[k]];
-      if (fin) bcr_fwd_one<T>(I.P, inst_factor<T>(I), 1, 1, 0, wv);
-      else bcr_fwd_one<T>(I.P, inst_factor<T>(I), 1 << lv, 0, t - pre[k], wv);
+      bcr_fwd_one<T>(I.P, inst_factor<T>(I), 1 << lv, 0, t - pre[k], wv);
     }
-    grid_barrier(gb);
+    grid_barrier(gb, ep);
   }
+  for (int k = blockIdx.x; k < A; k += gridDim.x) {
+    const DevInst& I = insts[act[k]];
+    for (int lv = lsplit; lv <= maxL; ++lv) {
+      const bool fin = lv == maxL;
+      const int nb = level_blocks(lv, k);
+      for (int bi = warp; bi < nb; bi += wpb)
+        bcr_fwd_one<T>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0, bi, wv);
+      __syncthreads();
+    }
+  }
+  grid_barrier(gb, ep);
   for (int t = blockIdx.x * FBS + threadIdx.x; t < pre_cs[A]; t += gridDim.x * FBS) {
     const int k = find_item(pre_cs, A, t);
     const DevInst& I = insts[act[k]];
@@ -1367,31 +1491,38 @@ k_solve_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
     const int it = t - pre_cs[k];
     F.chunkR[it] = chunk_sum_item(F.Rth, 2 * I.P.N, L, G, it / L, it % L);
   }
-  grid_barrier(gb);
+  grid_barrier(gb, ep);
   for (int k = blockIdx.x; k < A; k += gridDim.x) {
     const DevInst& I = insts[act[k]];
-    theta_solve_block(I.P, inst_factor<T>(I).chunkR, ir ? I.kr : I.ka, I.S, ir ? I.kc : I.kb,
+    double* sol = ir ? I.kc : I.kb;
+    // theta_solve_block ends with a block barrier: its shared vector and the
+    // per-warp vectors below may overlap
+    theta_solve_block(I.P, inst_factor<T>(I).chunkR, ir ? I.kr : I.ka, I.S, sol,
                       reinterpret_cast<double*>(smraw));
-  }
-  grid_barrier(gb);
-  for (int lv = maxL; lv >= 0; --lv) {
-    const int* pre = pre_lv + (size_t)lv * (A + 1);
-    const bool fin = lv == maxL;
-    const int tot = fin ? A : pre[A];
-    for (int t = gw; t < tot; t += nw) {
-      const int k = fin ? t : find_item(pre, A, t);
-      const DevInst& I = insts[act[k]];
-      double* sol = ir ? I.kc : I.kb;
-      if (fin) bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, sol, 1, 1, 0, wv);
-      else bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, sol, 1 << lv, 0, t - pre[k], wv);
+    for (int lv = maxL; lv >= lsplit; --lv) {
+      const bool fin = lv == maxL;
+      const int nb = level_blocks(lv, k);
+      for (int bi = warp; bi < nb; bi += wpb)
+        bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, sol, fin ? 1 : 1 << lv, fin ? 1 : 0, bi, wv);
+      __syncthreads();
     }
-    grid_barrier(gb);
+  }
+  grid_barrier(gb, ep);
+  for (int lv = lsplit - 1; lv >= 0; --lv) {
+    const int* pre = pre_lv + (size_t)lv * (A + 1);
+    for (int t = gw; t < pre[A]; t += nw) {
+      const int k = find_item(pre, A, t);
+      const DevInst& I = insts[act[k]];
+      bcr_bwd_one<T>(I.P, inst_factor<T>(I), I.S, ir ? I.kc : I.kb, 1 << lv, 0, t - pre[k], wv);
+    }
+    grid_barrier(gb, ep);
   }
   for (int t = gw; t < pre_elem[A]; t += nw) {
     const int k = find_item(pre_elem, A, t);
     const DevInst& I = insts[act[k]];
     elem_bwd_one<T>(I.P, inst_factor<T>(I), I.S, ir ? I.kc : I.kb, t - pre_elem[k], wv);
   }
+  grid_exit(gb);
 }
 
 // ---- host launchers ------------------------------------------------------------------
@@ -1638,7 +1769,8 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
 
 template <typename T>
 cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
-                           const int* pre_lv, int maxL, const int* pre_cs, int ir, int per_warp,
+                           const int* pre_lv, int maxL, int lsplit, const int* pre_cs, int ir,
+                           int per_warp,
                            GridBar* gb, int max_p, int grid_want, cudaStream_t st) {
   if (A == 0) return cudaSuccess;
   size_t smem = std::max(sizeof(T) * (size_t)per_warp * (FBS / 32),
@@ -1647,7 +1779,7 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
   int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
-                  (void*)&pre_cs, &ir, &per_warp, &gb};
+                  &lsplit, (void*)&pre_cs, &ir, &per_warp, &gb};
   count_launch();
   return cudaLaunchCooperativeKernel((void*)k_solve_b<T>, dim3(grid), dim3(FBS), args, smem, st);
 }
@@ -1672,11 +1804,11 @@ int elem_rt_threads(const DevProb& P, bool f32) {
   return f32 ? rt_block_threads<float>(P.ext) : rt_block_threads<double>(P.ext);
 }
 template cudaError_t launch_solve_b<float>(const DevInst*, const int*, int, const int*, const int*,
-                                           int, const int*, int, int, GridBar*, int, int,
+                                           int, int, const int*, int, int, GridBar*, int, int,
                                            cudaStream_t);
 template cudaError_t launch_solve_b<double>(const DevInst*, const int*, int, const int*,
-                                            const int*, int, const int*, int, int, GridBar*, int,
-                                            int, cudaStream_t);
+                                            const int*, int, int, const int*, int, int, GridBar*,
+                                            int, int, cudaStream_t);
 template size_t elem_factor_smem<float>(const DevProb&, bool);
 template size_t elem_factor_smem<double>(const DevProb&, bool);
 template size_t bcr_factor_smem<float>(const DevProb&, bool);

@@ -81,7 +81,8 @@ size_t elem_rt_stage_bytes(const DevProb& P, bool f32);
 size_t bcr_rt_stage_bytes(const DevProb& P, bool f32);
 template <typename T>
 cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
-                           const int* pre_lv, int maxL, const int* pre_cs, int ir, int per_warp,
+                           const int* pre_lv, int maxL, int lsplit, const int* pre_cs, int ir,
+                           int per_warp,
                            GridBar* gb, int max_p, int grid_want, cudaStream_t st);
 template <typename T>
 size_t elem_factor_smem(const DevProb& P, bool full);

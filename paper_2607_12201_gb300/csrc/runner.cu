@@ -27,6 +27,10 @@ namespace collo {
 
 constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
 constexpr size_t KSMEM_LIMIT = FACTOR_SMEM_LIMIT;
+// The batched solve runs the cyclic-reduction levels with at most this many
+// blocks in every instance one block (of FBS / 32 warps) per instance.
+constexpr int SOLVE_TOP_BLOCKS = 8;
+
 // Relative KKT residual above which refinement from an FP32 factorization
 // counts as failed (the step is then redone with an FP64 factorization).
 constexpr double ESCALATE_REL = 1e-6;
@@ -35,6 +39,7 @@ constexpr double ESCALATE_REL = 1e-6;
 struct Plan {
   std::vector<int> slots;
   int A = 0, maxL = 0, tot_elem = 0, max_p = 0;
+  int lsplit = 0;   // first reduction level the solve runs one block per instance
   long long tot_upd = 0;
   int* d_int = nullptr; int* h_int = nullptr; size_t cap_int = 0;
   long long* d_ll = nullptr; long long* h_ll = nullptr; size_t cap_ll = 0;
@@ -193,6 +198,16 @@ struct Runner {
     for (int k = 0; k < A; ++k) h[o + k + 1] = h[o + k] + P(slots[k]).N;
     pl.tot_elem = h[o + A]; o += A + 1;
     pl.off_lv = o;
+    pl.lsplit = maxL;
+    for (int lv = maxL; lv >= 0; --lv) {
+      int most = 0;
+      for (int k = 0; k < A; ++k) {
+        const int N = P(slots[k]).N, st = 1 << lv;
+        most = std::max(most, (lv < maxL && N > st) ? (N - st + 2 * st - 1) / (2 * st) : 0);
+      }
+      if (most > SOLVE_TOP_BLOCKS) break;
+      pl.lsplit = lv;
+    }
     for (int lv = 0; lv <= maxL; ++lv) {
       h[o] = 0;
       for (int k = 0; k < A; ++k) {
@@ -399,10 +414,10 @@ struct Runner {
     cudaError_t e;
     const int want = std::max(pl.A, (pl.tot_elem + 7) / 8);
     if (prec == COLLO_PRECISION_MIXED)
-      e = launch_solve_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+      e = launch_solve_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL, pl.lsplit,
                                 pl.pre_cs_r(), ir, pl.per_warp[1], gbar, pl.max_p, want, stream);
     else
-      e = launch_solve_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
+      e = launch_solve_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL, pl.lsplit,
                                  pl.pre_cs_r(), ir, pl.per_warp[0], gbar, pl.max_p, want, stream);
     COLLO_CUDA(e);
     return COLLO_OK;
