@@ -702,10 +702,54 @@ __host__ __device__ inline size_t bcr_stage_elems(int n, int p) {
   const size_t out = m2 * (m2 + 1) / 2;
   return in > out ? in : out;
 }
+// Asynchronous copies (cp.async, completed by cp_async_wait_all) of single
+// elements from global to shared memory.
+template <typename T>
+__device__ inline void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Starts the staging of cyclic-reduction block bi's inputs into `stage` (one
+// half, tid in [0, 128)); the copies are complete for this thread after
+// cp_async_wait_all and for the half after a barrier that follows it.  A
+// block's inputs are not written by any other block of its level, so they
+// can be staged while the half still works on its previous block.
+template <typename T>
+__device__ void bcr_stage_issue(const DevProb& P, const DevFactor<T>& F, int stride,
+                                int final_level, int bi, int tid, T* stage) {
+  const int n = P.n, p = P.p, N = P.N, n2 = 2 * n;
+  const int i = final_level ? 0 : stride * (2 * bi + 1);
+  const int R = (!final_level && i + stride < N) ? i + stride : -1;
+  T* Ai = stage;
+  T* Ci = Ai + 4 * n * n;
+  T* CR = Ci + n * n;
+  T* Bi = CR + n * n;
+  const T* gA = F.Aif + (size_t)i * n2 * n2;
+  const T* gC = F.Cpl + (size_t)i * n * n;
+  const T* gCR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
+  const T* gB = F.Bif + (size_t)i * n2 * p;
+  for (int k = tid; k < 4 * n * n; k += 128) cp_async_elem(Ai + k, gA + k);
+  for (int k = tid; k < n * n; k += 128) {
+    cp_async_elem(Ci + k, gC + k);
+    if (gCR) cp_async_elem(CR + k, gCR + k);
+    else CR[k] = T(0);
+  }
+  for (int k = tid; k < n2 * p; k += 128) cp_async_elem(Bi + k, gB + k);
+  cp_async_commit();
+}
+
+// Factorization of a block whose inputs are staged (complete and visible to
+// the half).
 template <typename T, int TPT>
-__device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int stride,
-                              int final_level, int bi, int tid, HalfBar bar, Pair<T>* ub,
-                              T* stage, Pivot<T>* pivs, int* cnt) {
+__device__ void bcr_factor_staged(const DevProb& P, const DevFactor<T>& F, int stride,
+                                  int final_level, int bi, int tid, HalfBar bar, Pair<T>* ub,
+                                  T* stage, Pivot<T>* pivs, int* cnt) {
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
@@ -714,22 +758,6 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
   T* Ci = Ai + 4 * n * n;
   T* CR = Ci + n * n;
   T* Bi = CR + n * n;
-  {
-    const T* gA = F.Aif + (size_t)i * n2 * n2;
-    const T* gC = F.Cpl + (size_t)i * n * n;
-    const T* gCR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
-    const T* gB = F.Bif + (size_t)i * n2 * p;
-#pragma unroll 4
-    for (int k = tid; k < 4 * n * n; k += 128) Ai[k] = gA[k];
-#pragma unroll 4
-    for (int k = tid; k < n * n; k += 128) {
-      Ci[k] = gC[k];
-      CR[k] = gCR ? gCR[k] : T(0);
-    }
-#pragma unroll 4
-    for (int k = tid; k < n2 * p; k += 128) Bi[k] = gB[k];
-  }
-  bar();
   auto entry = [&](int a, int b) -> T {
     if (a < n2) return Ai[a * n2 + b];
     if (b >= n2) return T(0);
@@ -787,6 +815,17 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
     Sc[k] = (double)tr(2 * n + q, 2 * n + q2);
   }
   bar();   // the buffer is restaged by this half's next block
+}
+
+// bcr_factor_staged with its staging waited for (no overlap).
+template <typename T, int TPT>
+__device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int stride,
+                              int final_level, int bi, int tid, HalfBar bar, Pair<T>* ub,
+                              T* stage, Pivot<T>* pivs, int* cnt) {
+  bcr_stage_issue<T>(P, F, stride, final_level, bi, tid, stage);
+  cp_async_wait_all();
+  bar();
+  bcr_factor_staged<T, TPT>(P, F, stride, final_level, bi, tid, bar, ub, stage, pivs, cnt);
 }
 
 // Tiles per thread of bcr_factor_rt for P (single tiles; 0: use bcr_factor_one).
@@ -1352,8 +1391,10 @@ k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ ac
                                  t - pre_elem[k], ub.v, reinterpret_cast<T*>(stage_dyn));
 }
 
+// FP32: three blocks per SM (more reduction blocks in flight; the levels are
+// latency bound)
 template <typename T, int BT>
-__global__ void __launch_bounds__(FBS)
+__global__ void __launch_bounds__(FBS, sizeof(T) == 4 ? 3 : 1)
 k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
            const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
            const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
@@ -1383,17 +1424,41 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       __shared__ PivotBuf<T> ubh[2];
       __shared__ Pivot<T> pivh[2][RT_MAX_PAIRS];
       __shared__ int cnth[2][3];
-      const int half = threadIdx.x >> 7;
-      for (int t = 2 * blockIdx.x + half; t < tot; t += 2 * gridDim.x) {
+      const int half = threadIdx.x >> 7, htid = threadIdx.x & 127;
+      const HalfBar hbar{1 + half};
+      // each half owns a fixed half of the dynamic shared memory (instances of
+      // different sizes may share the block), split into two stage buffers:
+      // the next block's inputs are copied into one while the current block
+      // is factored from the other
+      const size_t hb = (smem_bytes / 2) & ~size_t(15), bb = (hb / 2) & ~size_t(15);
+      unsigned char* hbase = smraw + half * hb;
+      auto stage_of = [&](int j) { return reinterpret_cast<T*>(hbase + (j & 1) * bb); };
+      auto next_rt = [&](int t) {
+        for (; t < tot; t += 2 * gridDim.x)
+          if (flags[fin ? t : find_item(pre, A, t)] & 8) break;
+        return t;
+      };
+      auto issue = [&](int t, int j) {
         const int k = fin ? t : find_item(pre, A, t);
-        if (!(flags[k] & 8)) continue;
         const DevInst& I = insts[act[k]];
-        // each half owns a fixed half of the dynamic shared memory (instances
-        // of different sizes may share the block)
-        T* stage = reinterpret_cast<T*>(smraw + half * ((smem_bytes / 2) & ~size_t(15)));
-        bcr_factor_rt<T, BT>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
-                             fin ? 0 : t - pre[k], threadIdx.x & 127, HalfBar{1 + half}, ubh[half].v,
-                             stage, pivh[half], cnth[half]);
+        bcr_stage_issue<T>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
+                           fin ? 0 : t - pre[k], htid, stage_of(j));
+      };
+      int t = next_rt(2 * blockIdx.x + half), j = 0;
+      if (t < tot) issue(t, 0);
+      while (t < tot) {
+        const int tn = next_rt(t + 2 * gridDim.x);
+        cp_async_wait_all();
+        hbar();
+        // the other buffer's last block ended with a half barrier
+        if (tn < tot) issue(tn, j + 1);
+        const int k = fin ? t : find_item(pre, A, t);
+        const DevInst& I = insts[act[k]];
+        bcr_factor_staged<T, BT>(I.P, inst_factor<T>(I), fin ? 1 : 1 << lv, fin ? 1 : 0,
+                                 fin ? 0 : t - pre[k], htid, hbar, ubh[half].v, stage_of(j),
+                                 pivh[half], cnth[half]);
+        t = tn;
+        ++j;
       }
     }
     // the whole-block pass reuses the shared memory the halves staged in
@@ -1798,7 +1863,7 @@ size_t elem_rt_stage_bytes(const DevProb& P, bool f32) {
 }
 size_t bcr_rt_stage_bytes(const DevProb& P, bool f32) {
   const size_t one = (f32 ? sizeof(float) : sizeof(double)) * bcr_stage_elems(P.n, P.p);
-  return 2 * ((one + 15) & ~size_t(15));
+  return 4 * ((one + 15) & ~size_t(15));   // two halves, two stage buffers each
 }
 int elem_rt_threads(const DevProb& P, bool f32) {
   return f32 ? rt_block_threads<float>(P.ext) : rt_block_threads<double>(P.ext);

@@ -77,7 +77,8 @@ int elem_rt_threads(const DevProb& P, bool f32);
 int bcr_rt_tiles_of(const DevProb& P);
 // Dynamic shared memory of the register-tiled element kernel for P.
 size_t elem_rt_stage_bytes(const DevProb& P, bool f32);
-// Dynamic shared memory of the register-tiled reduction blocks (both halves).
+// Dynamic shared memory of the register-tiled reduction blocks (both halves of
+// a block, two stage buffers per half).
 size_t bcr_rt_stage_bytes(const DevProb& P, bool f32);
 template <typename T>
 cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,

@@ -587,6 +587,7 @@ struct IpmInst {
   Opt o;
   int status = RUNNING;
   double mu = 0.1, tau = 0.99, dw_last = 0.0, dw = 0.0, dc = 0.0;
+  bool prev_reg = false;   // the last accepted factorization had dw > 0
   double theta_max = 0, theta_min = 0, err = INFINITY, phi = NAN;
   int acc = 0, it = 0, facs = 0, facs64 = 0, trials_total = 0, prec = 0, refine_total = 0;
   // MIXED path after a refinement failure: factor in FP64 until iteration
@@ -726,8 +727,16 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
     // the inertia is right.  From the second round on, each instance factors two
     // consecutive candidates at once (the second in its shadow slot) and takes
     // the first of the two, in sequence order, whose inertia is right: the same
-    // regularisation as the one-at-a-time sequence, in fewer rounds.
+    // regularisation as the one-at-a-time sequence, in fewer rounds.  An
+    // instance whose last accepted factorization needed dw > 0 is likely to
+    // need it again, so it pairs 0 with its first candidate from the first
+    // round on.
     std::map<int, double> dw2;   // slot -> second candidate of this round (0: none)
+    for (auto* I : fac) {
+      if (!I->prev_reg || I->dw != 0.0 || I->dw_last == 0.0) continue;
+      const double c1 = std::max(I->o.dw_min, I->o.kw_minus * I->dw_last);
+      if (c1 <= I->o.dw_max) dw2[I->slot] = c1;
+    }
     while (!fac.empty()) {
       prof.round(PF_FACTOR);
       std::vector<int> gr[2];
@@ -778,6 +787,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
           I->prob->fac_dw = I->dw;
           I->prob->fac_dc = I->dc;
           if (I->dw > 0) I->dw_last = I->dw;
+          I->prev_reg = I->dw > 0;
           dw2.erase(I->slot);
           continue;
         }
