@@ -316,7 +316,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   pr->kvec_r = A.alloc<double>(nk);
   pr->kvec_c = A.alloc<double>(nk);
   pr->thpart = A.alloc<double>(NN * p + (size_t)CHUNKS * p);
-  pr->npart = A.alloc<double>(NN * 2);
+  pr->npart = A.alloc<double>(NN * 3);
   pr->scal = A.alloc<double>(64);
   pr->red_parts = A.alloc<double>(256);
   pr->x = A.alloc<double>(pr->n_x);

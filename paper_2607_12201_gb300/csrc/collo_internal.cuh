@@ -143,7 +143,7 @@ struct DevInst {
   double* th0;        // [p]  starting parameters
   double* ka, *kb, *kr, *kc;   // [n_x + n_c] rhs, solution, residual, correction
   double* thpart;     // [N][p]
-  double* npart;      // [N][2]
+  double* npart;      // [N][3]
   double* out;        // [64] per-instance scalar outputs of the batched kernels
   int* fails;         // [1]
   float* sweep_work;  // forward-sweep FP32 matrix when 3n is large

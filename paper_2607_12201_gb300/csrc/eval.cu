@@ -353,16 +353,19 @@ k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, d
   resid_elem(P, E, sigma, dw, dc, vx, vl, bx, bxs, bc, bcs, rout, thpart, npart, blockIdx.x, red);
 }
 
-__global__ void __launch_bounds__(EVAL_BS)
+// BS: 64 when every instance of the batch has at most 64 state rows per
+// element (4n), else EVAL_BS; the results do not depend on it.
+template <int BS>
+__global__ void __launch_bounds__(BS)
 k_kkt_resid_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
               const int* __restrict__ pre, const InstParams* __restrict__ prm, int mode) {
-  __shared__ double red[EVAL_BS];
+  __shared__ double red[BS];
   const int t = blockIdx.x;
   const int k = find_item(pre, A, t);
   const DevInst& I = insts[act[k]];
   const ResidArgs a = resid_args(I, prm[k], mode);
-  resid_elem(I.P, I.E, a.sigma, a.dw, a.dc, a.vx, a.vl, a.bx, a.bxs, a.bc, a.bcs, a.rout,
-             I.thpart, I.npart, t - pre[k], red);
+  resid_elem<BS>(I.P, I.E, a.sigma, a.dw, a.dc, a.vx, a.vl, a.bx, a.bxs, a.bc, a.bcs, a.rout,
+                 I.thpart, I.npart, t - pre[k], red);
 }
 
 __global__ void __launch_bounds__(RED_BS)
@@ -494,10 +497,14 @@ cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int
 }
 
 cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
-                           int total_elems, const InstParams* prm, int mode, cudaStream_t st) {
+                           int total_elems, int max_n, const InstParams* prm, int mode,
+                           cudaStream_t st) {
   if (A == 0) return cudaSuccess;
   count_launch();
-  k_kkt_resid_b<<<total_elems, EVAL_BS, 0, st>>>(insts, act, A, pre_elem, prm, mode);
+  if (NP * max_n <= 64)
+    k_kkt_resid_b<64><<<total_elems, 64, 0, st>>>(insts, act, A, pre_elem, prm, mode);
+  else
+    k_kkt_resid_b<EVAL_BS><<<total_elems, EVAL_BS, 0, st>>>(insts, act, A, pre_elem, prm, mode);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launch();

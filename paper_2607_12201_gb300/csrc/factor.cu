@@ -302,6 +302,19 @@ struct Pivot {
 // Correctly rounded reciprocal (the same value as 1 / x).
 __device__ inline float recip_rn(float x) { return __frcp_rn(x); }
 __device__ inline double recip_rn(double x) { return __drcp_rn(x); }
+
+// Asynchronous copies (cp.async, completed by cp_async_wait_all) of single
+// elements from global to shared memory.
+template <typename T>
+__device__ inline void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 constexpr int RT_MAX_PAIRS = 2 * RT_MAX_TR + 2;   // pairs of a block of <= 124 rows
 
 // Tiles are owned in pairs along a tile row: pair t is tiles (ti, 2k) and
@@ -467,8 +480,17 @@ struct HalfBar {
 // threads' register tiles; after the elimination the trailing blocks go back
 // through the same buffer and leave in coalesced stores.
 template <typename T>
+__host__ __device__ inline size_t elem_blk_bytes(const DevProb& P) {
+  return (sizeof(T) * ((size_t)P.ext * (P.ext + 1) / 2) + 15) & ~size_t(15);
+}
+// The element's FP64 derivative blocks (Wzz, JZ: 3 n^2 each; Wzt, JT: 3 n p
+// each; Wobj: 16 n; sigma: 4 n), staged behind the triangle.
+__host__ __device__ inline size_t elem_raw_doubles(const DevProb& P) {
+  return 6 * (size_t)P.n * P.n + 6 * (size_t)P.n * P.p + 20 * (size_t)P.n;
+}
+template <typename T>
 __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
-  return sizeof(T) * ((size_t)P.ext * (P.ext + 1) / 2);
+  return elem_blk_bytes<T>(P) + sizeof(double) * elem_raw_doubles(P);
 }
 __device__ inline int tri_at(int r, int c) { return r * (r + 1) / 2 + c; }
 // i / d and i % d for 0 <= i < 2^22 and 1 <= d <= 4096 through the float
@@ -486,24 +508,47 @@ __device__ inline int loc_dual(int k, int s, int n) { return 2 * ((k == 0 ? 3 : 
 
 // Element condensation (same elimination as elem_factor_one) with
 // pair_eliminate_rt over the nt threads of the block.
-template <typename T, int TPT>
-__device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
-                               const double* __restrict__ sigma, double dw, double dc,
-                               const DevFactor<T>& F, int e, Pair<T>* ub, T* blk) {
+// Assembly of element e's KKT block (packed lower triangle in `blk`, shared
+// memory) from its derivative blocks.  Kept out of line: inlined, it changes
+// how the elimination that follows is compiled (about a quarter more
+// instructions there).
+template <typename T>
+__device__ __noinline__ void elem_assemble_rt(const DevProb& P, const DevEval& E,
+                                              const double* __restrict__ sigma, double dw,
+                                              double dc, int e, T* blk) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
   const int nn = n * n, np = n * p, ntri = ext * (ext + 1) / 2;
   auto put = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] = v; };
   auto add = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] += v; };
+  // the derivative blocks arrive by asynchronous copies issued all at once
+  // (one memory latency per element) while the triangle is cleared
+  double* Wzz = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(blk) +
+                                          elem_blk_bytes<T>(P));
+  double* JZ = Wzz + 3 * nn;
+  double* Wzt = JZ + 3 * nn;
+  double* JT = Wzt + 3 * np;
+  double* Wobj = JT + 3 * np;
+  double* sig = Wobj + 16 * n;
+  {
+    auto stage = [&](double* dst, const double* src, int cnt) {
+      for (int i = tid; i < cnt; i += nt) cp_async_elem(dst + i, src + i);
+    };
+    stage(Wzz, E.Wzz + (size_t)e * 3 * nn, 3 * nn);
+    stage(JZ, E.JZ + (size_t)e * 3 * nn, 3 * nn);
+    stage(Wzt, E.Wzt + (size_t)e * 3 * np, 3 * np);
+    stage(JT, E.JT + (size_t)e * 3 * np, 3 * np);
+    stage(Wobj, E.Wobj + (size_t)e * 16 * n, 16 * n);
+    if (sigma) stage(sig, sigma + (size_t)e * 4 * n, 4 * n);
+    else
+      for (int i = tid; i < 4 * n; i += nt) sig[i] = 0.0;
+    cp_async_commit();
+  }
   for (int i = tid; i < ntri; i += nt) blk[i] = T(0);
+  cp_async_wait_all();
   __syncthreads();
   // 1. disjoint entries: point Hessian blocks, the identity parts of the
   //    collocation rows (D[k][j]), continuity / initial rows, -delta_c, border
-  const double* Wzz = E.Wzz + (size_t)e * 3 * nn;
-  const double* JZ = E.JZ + (size_t)e * 3 * nn;
-  const double* Wzt = E.Wzt + (size_t)e * 3 * np;
-  const double* JT = E.JT + (size_t)e * 3 * np;
   const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
   for (int i = tid; i < 3 * nn; i += nt) {
     const int rs = quot(i, n, inv_n), sb = i - rs * n;   // rs = k n + sa
@@ -529,7 +574,6 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   __syncthreads();
   // 2. sums onto those: objective blocks (same species across points) and the
   //    -h df/dz part of the collocation rows
-  const double* Wobj = E.Wobj + (size_t)e * 16 * n;
   for (int i = tid; i < 16 * n; i += nt) {
     const int s2 = i >> 4, ja = (i >> 2) & 3, jb = i & 3;
     const int a = loc_state(ja, s2, n), b = loc_state(jb, s2, n);
@@ -545,9 +589,20 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   for (int i = tid; i < 4 * n; i += nt) {
     const int j = quot(i, n, inv_n), s2 = i - j * n;
     const int a = loc_state(j, s2, n);
-    add(a, a, (T)((sigma ? sigma[(size_t)e * 4 * n + i] : 0.0) + dw));
+    add(a, a, (T)(sig[i] + dw));
   }
   __syncthreads();
+}
+
+template <typename T, int TPT>
+__device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
+                               const double* __restrict__ sigma, double dw, double dc,
+                               const DevFactor<T>& F, int e, Pair<T>* ub, T* blk) {
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
+  const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
+  elem_assemble_rt<T>(P, E, sigma, dw, dc, e, blk);
   auto entry = [&](int r, int c) -> T { return blk[tri_at(r, c)]; };
   auto sink = [&](int r, int c, T val) { blk[tri_at(r, c)] = val; };
   __shared__ Pivot<T> pivs[RT_MAX_PAIRS];
@@ -702,19 +757,6 @@ __host__ __device__ inline size_t bcr_stage_elems(int n, int p) {
   const size_t out = m2 * (m2 + 1) / 2;
   return in > out ? in : out;
 }
-// Asynchronous copies (cp.async, completed by cp_async_wait_all) of single
-// elements from global to shared memory.
-template <typename T>
-__device__ inline void cp_async_elem(T* dst, const T* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Starts the staging of cyclic-reduction block bi's inputs into `stage` (one
 // half, tid in [0, 128)); the copies are complete for this thread after
 // cp_async_wait_all and for the half after a barrier that follows it.  A
@@ -1630,28 +1672,6 @@ size_t factor_work_elems(const DevProb& P, int n_slabs) {
   return w;
 }
 
-template <typename T>
-cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
-                               double dc, const DevFactor<T>& F, cudaStream_t st) {
-  const int rtn = rt_block_threads<T>(P.ext);
-  if (rtn > 0) {
-    const size_t sm = elem_stage_bytes<T>(P);
-    if (sm > SMEM_OPTIN_ABOVE)
-      cudaFuncSetAttribute(k_elem_factor_rt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    count_launch();
-    k_elem_factor_rt<T><<<P.N, rtn, sm, st>>>(P, E, sigma, dw, dc, F);
-    return cudaGetLastError();
-  }
-  bool es = elem_uses_smem<T>(P);
-  size_t sm = elem_factor_smem<T>(P, es);
-  if (sm > SMEM_OPTIN_ABOVE)
-    cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int grid = es ? P.N : std::min(P.N, F.n_slabs);
-  count_launch();
-  k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0);
-  return cudaGetLastError();
-}
-
 // cudaFuncAttributeMaxDynamicSharedMemorySize, set only when a launch needs
 // more than the kernel's setting so far (per device).
 template <typename KernelT>
@@ -1664,22 +1684,37 @@ static void opt_in_smem(KernelT kern, size_t bytes) {
   std::lock_guard<std::mutex> lk(mu);
   size_t& cur = done[{dev, (const void*)kern}];
   if (bytes <= cur) return;
+  // a kernel that asks for this much shared memory also asks for the largest
+  // shared-memory carveout of the SM's L1: by default the driver may pick a
+  // smaller one that holds fewer of its blocks
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-      cudaSuccess)
+          cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) == cudaSuccess)
     cur = bytes;
   else
     cudaGetLastError();
 }
 
-static int g_coop_checked = -1;   // device supports cooperative launches (-1: unknown)
-static bool coop_supported() {
-  if (g_coop_checked < 0) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev);
-    g_coop_checked = v ? 1 : 0;
+template <typename T>
+cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double* sigma, double dw,
+                               double dc, const DevFactor<T>& F, cudaStream_t st) {
+  const int rtn = rt_block_threads<T>(P.ext);
+  if (rtn > 0) {
+    const size_t sm = elem_stage_bytes<T>(P);
+    opt_in_smem(k_elem_factor_rt<T>, sm);
+    count_launch();
+    k_elem_factor_rt<T><<<P.N, rtn, sm, st>>>(P, E, sigma, dw, dc, F);
+    return cudaGetLastError();
   }
-  return g_coop_checked == 1;
+  bool es = elem_uses_smem<T>(P);
+  size_t sm = elem_factor_smem<T>(P, es);
+  if (sm > SMEM_OPTIN_ABOVE)
+    cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int grid = es ? P.N : std::min(P.N, F.n_slabs);
+  count_launch();
+  k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0);
+  return cudaGetLastError();
 }
 
 template <typename KernelT>

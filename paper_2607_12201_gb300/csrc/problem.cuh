@@ -63,7 +63,8 @@ cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int
                           int total_elems, const InstParams* prm, int xsel, int dxsel, int lsel,
                           bool deriv, size_t smem, cudaStream_t st);
 cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
-                           int total_elems, const InstParams* prm, int mode, cudaStream_t st);
+                           int total_elems, int max_n, const InstParams* prm, int mode,
+                           cudaStream_t st);
 template <typename T>
 cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                             const int* pre_lv, int maxL, const int* pre_cs,
@@ -173,7 +174,7 @@ struct collo_problem {
   double* kvec_r = nullptr;   // [n_x + n_c]  residual
   double* kvec_c = nullptr;   // [n_x + n_c]  correction
   double* thpart = nullptr;   // [N][p] then [CHUNKS][p] chunk sums
-  double* npart = nullptr;    // [N][2]
+  double* npart = nullptr;    // [N][3]
   double* scal = nullptr;     // [64] device scalars
   double* red_parts = nullptr;  // [256] partial sums of two-stage reductions
   double* hscal = nullptr;    // [64] pinned host mirror

@@ -45,8 +45,9 @@ __device__ inline double block_max(double v, double* sh) {
 //   [ W + diag(sigma) + dw I   J^T  ] [vx]
 //   [ J                       -dc I ] [vl]
 // and r = b - y (b may be null: r = -y).  One block per element computes the
-// element's 8n rows and its contribution to the p parameter rows; norms of r
-// per element go to npart[i][0..1] (max |r_x|, max |r_c|).
+// element's 8n rows and its contribution to the p parameter rows; norms per
+// element go to npart[i][0..2] (max |r_x|, max |r_c|, max |b| over the
+// element's rows).
 template <int BS = EVAL_BS>
 __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const double* __restrict__ sigma,
                            double dw, double dc, const double* __restrict__ vx,
@@ -66,7 +67,7 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
   const double* Wzz = E.Wzz + (size_t)i * KC * nn;
   const double* Wzt = E.Wzt + (size_t)i * KC * np_;
   const double* Wob = E.Wobj + (size_t)i * n * NP * NP;
-  double mx = 0.0, mc = 0.0;
+  double mx = 0.0, mc = 0.0, mb = 0.0;
   for (int idx = tid; idx < NP * n; idx += BS) {
     const int j = idx / n, s = idx - j * n;
     // primal row z[i][j][s]
@@ -92,6 +93,8 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
       if (j == 0) y += vl[zoff + s];
       if (j == KC && i + 1 < N) y -= vl[zoff + NP * n + s];
     }
+    if (bx) mb = fmax(mb, fabs(bx[zoff + idx]));
+    if (bc) mb = fmax(mb, fabs(bc[zoff + idx]));
     double rr = (bx ? bxs * bx[zoff + idx] : 0.0) - y;
     if (rout) rout[zoff + idx] = rr;
     mx = fmax(mx, fabs(rr));
@@ -126,7 +129,8 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
   }
   mx = block_max<BS>(mx, red);
   mc = block_max<BS>(mc, red);
-  if (tid == 0) { npart[i * 2 + 0] = mx; npart[i * 2 + 1] = mc; }
+  mb = block_max<BS>(mb, red);
+  if (tid == 0) { npart[i * 3 + 0] = mx; npart[i * 3 + 1] = mc; npart[i * 3 + 2] = mb; }
 }
 
 // Residual modes of the batched product (which vectors of the instance):
@@ -170,7 +174,7 @@ __device__ inline void resid_theta_one(const DevProb& P, const DevEval& E,
                                 double* sh) {
   const int tid = threadIdx.x, p = P.p, N = P.N;
   const int lane = tid & 31, warp = tid >> 5;
-  const size_t nz = (size_t)N * NP * P.n, nx = nz + p;
+  const size_t nz = (size_t)N * NP * P.n;
   double mx = 0.0, mc = 0.0, mb = 0.0;
   for (int q = warp; q < p; q += RED_BS / 32) {
     double y = 0.0;
@@ -185,13 +189,12 @@ __device__ inline void resid_theta_one(const DevProb& P, const DevEval& E,
     }
   }
   for (int i = tid; i < N; i += RED_BS) {
-    mx = fmax(mx, npart[i * 2 + 0]);
-    mc = fmax(mc, npart[i * 2 + 1]);
+    mx = fmax(mx, npart[i * 3 + 0]);
+    mc = fmax(mc, npart[i * 3 + 1]);
+    mb = fmax(mb, npart[i * 3 + 2]);
   }
   if (bx)
-    for (size_t k = tid; k < nx; k += RED_BS) mb = fmax(mb, fabs(bx[k]));
-  if (bc)
-    for (size_t k = tid; k < nz; k += RED_BS) mb = fmax(mb, fabs(bc[k]));
+    for (int q = tid; q < p; q += RED_BS) mb = fmax(mb, fabs(bx[nz + q]));
   mx = block_max<RED_BS>(mx, sh);
   mc = block_max<RED_BS>(mc, sh);
   mb = block_max<RED_BS>(mb, sh);

@@ -38,7 +38,7 @@ constexpr double ESCALATE_REL = 1e-6;
 // ---- plans ---------------------------------------------------------------------------
 struct Plan {
   std::vector<int> slots;
-  int A = 0, maxL = 0, tot_elem = 0, max_p = 0;
+  int A = 0, maxL = 0, tot_elem = 0, max_p = 0, max_n = 0;
   int lsplit = 0;   // first reduction level the solve runs one block per instance
   long long tot_upd = 0;
   int* d_int = nullptr; int* h_int = nullptr; size_t cap_int = 0;
@@ -187,6 +187,8 @@ struct Runner {
     }
     pl.maxL = maxL;
     pl.max_p = maxp;
+    pl.max_n = 0;
+    for (int s : slots) pl.max_n = std::max(pl.max_n, P(s).n);
     const size_t n_int = (size_t)A + (A + 1) * (size_t)(4 + maxL + 1) + 2 * (size_t)A + 2 * (size_t)A;
     cudaError_t e = grow(&pl.d_int, &pl.h_int, &pl.cap_int, n_int);
     if (e == cudaSuccess) e = grow(&pl.d_ll, &pl.h_ll, &pl.cap_ll, (size_t)A + 1);
@@ -369,8 +371,8 @@ struct Runner {
   }
   collo_status resid(int which, int mode) {
     Plan& pl = plans[which];
-    COLLO_CUDA(launch_resid_b(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.tot_elem, pl.d_prm, mode,
-                              stream));
+    COLLO_CUDA(launch_resid_b(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.tot_elem, pl.max_n,
+                              pl.d_prm, mode, stream));
     return COLLO_OK;
   }
   // parts: 1 element condensation (register-tiled kernel), 2 the rest, 3 both
