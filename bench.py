@@ -72,7 +72,7 @@ def parse_args():
                     help="instances of --only-batch")
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--queue", type=int, default=256)
-    ap.add_argument("--admit", type=int, default=24,
+    ap.add_argument("--admit", type=int, default=32,
                     help="admit waiting solves in groups of at least this many free slots")
     ap.add_argument("--only-solve", choices=["mixed", "fp64"], default=None,
                     help="run one single-instance solve and exit (for profiler launch lists)")

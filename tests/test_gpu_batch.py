@@ -71,6 +71,31 @@ def test_batch_equals_alone_bitwise(collo, prec):
         pb.close()
 
 
+def test_full_size_batch_equals_alone_bitwise(collo):
+    # 6 x 400 elements: the first reduction level has more blocks (1200) than the
+    # persistent factor kernel has block halves, so a half factors several blocks
+    # of a level and stages the next one's inputs during the current elimination;
+    # the solve runs its levels 0-4 over the grid and the rest per instance.  The
+    # same starts alone never overlap two blocks.  Iterates must be bitwise equal.
+    inst = W.config2()
+    starts = W.multistart_thetas(inst, 6, seed=2002)
+    alone = []
+    for th in starts:
+        with collo.Problem(inst) as pb:
+            alone.append(pb.ipm_solve(theta0=th, precision=collo.MIXED, max_iter=6))
+    probs = [collo.Problem(inst) for _ in starts]
+    mixed = collo.batch_solve(probs, theta0s=starts, precision=collo.MIXED, max_iter=6,
+                              want_x=True)
+    for a, b in zip(alone, mixed):
+        assert a["iterations"] == b["iterations"]
+        assert a["factorizations"] == b["factorizations"]
+        assert np.array_equal(a["theta"], b["theta"])
+        assert np.array_equal(a["x"], b["x"])
+        assert np.array_equal(a["lam"], b["lam"])
+    for pb in probs:
+        pb.close()
+
+
 def test_batch_multistart_matches_oracle(collo):
     base = W.random_network(4, 8, n_obs=3, M=20, T=5.0, N=40, seed=41, theta0_spread=0.1)
     rng = np.random.default_rng(5)
