@@ -87,6 +87,13 @@ collo_status ensure_spare_storage(collo_problem* pr, int precision) {
   if (s != COLLO_OK || pr->spare_S) return s;
   const size_t p = pr->P.p;
   DevArena& A = pr->arena;
+  pr->c_spare = A.alloc<double>(pr->n_c);
+  pr->part_spare = A.alloc<double>((size_t)pr->P.N * 4);
+  pr->red_spare = A.alloc<double>(8);
+  if (!pr->c_spare || !pr->part_spare || !pr->red_spare) {
+    set_error("device allocation failed for the spare evaluation storage");
+    return COLLO_ERR_OOM;
+  }
   DevSchur& S = pr->S_spare;
   S.S = A.alloc<double>(p * p);
   S.Sd = A.alloc<double>(p);

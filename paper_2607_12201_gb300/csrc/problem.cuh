@@ -162,6 +162,11 @@ struct collo_problem {
   collo::FactorStore<float> f32_spare;
   collo::DevSchur S_spare{};
   bool spare_S = false;
+  // evaluation outputs of a second line-search trial (constraints, element
+  // partials, reduction), written by trial evaluations in the shadow slot
+  double* c_spare = nullptr;
+  double* part_spare = nullptr;
+  double* red_spare = nullptr;
   int factored = -1;          // precision of the current factorization, -1 none
   bool evaluated = false;
   int n_slabs = 0;
