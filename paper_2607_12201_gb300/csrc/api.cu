@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <set>
 
 #include "problem.cuh"
 
@@ -242,6 +243,35 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
       for (int j : pl[q]) pr_r.push_back(j);
     }
   }
+  // structural nonzeros of the derivative blocks (the eval kernels accumulate
+  // JZ / JT over the reactions changing a species, Wzz / Wzt over the
+  // reactions consuming it): sorted index sets per row or column
+  std::vector<std::set<int>> jzr(n), jzc(n), wzr(n), wtr(n), jtr(n), thq(p);
+  for (int j = 0; j < r; ++j) {
+    const int a = net->reactants[2 * j], b = net->reactants[2 * j + 1];
+    const int q = net->param_index[j];
+    std::vector<double> nu(n, 0.0);
+    for (int k = 0; k < 2; ++k) {
+      if (net->reactants[2 * j + k] >= 0) nu[net->reactants[2 * j + k]] -= 1.0;
+      if (net->products[2 * j + k] >= 0) nu[net->products[2 * j + k]] += 1.0;
+    }
+    for (int s2 = 0; s2 < n; ++s2) {
+      if (nu[s2] == 0.0) continue;
+      jzr[s2].insert(a);
+      if (b >= 0) jzr[s2].insert(b);
+      if (q >= 0) { jtr[s2].insert(q); thq[q].insert(s2); }
+    }
+    if (b >= 0) {
+      if (a == b) wzr[a].insert(a);
+      else { wzr[a].insert(b); wzr[b].insert(a); }
+    }
+    if (q >= 0) {
+      wtr[a].insert(q); thq[q].insert(a);
+      if (b >= 0) { wtr[b].insert(q); thq[q].insert(b); }
+    }
+  }
+  for (int s2 = 0; s2 < n; ++s2)
+    for (int t : jzr[s2]) jzc[t].insert(s2);
   // observations: element from the same rule the kernels use, grouped by element
   std::vector<int> oelem(M);
   for (int m = 0; m < M; ++m) {
@@ -289,6 +319,30 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   P.rs_r = up_i(rs_r.data(), rs_r.size());
   P.pr_ptr = up_i(pr_ptr.data(), p + 1);
   P.pr_r = up_i(pr_r.data(), pr_r.size());
+  bool pat_ok = true;
+  auto up_csr = [&](const std::vector<std::set<int>>& sets, const int*& ptr, const int*& idx) {
+    std::vector<int> hp(sets.size() + 1, 0), hi;
+    for (size_t k = 0; k < sets.size(); ++k) {
+      hi.insert(hi.end(), sets[k].begin(), sets[k].end());
+      hp[k + 1] = (int)hi.size();
+    }
+    if (hi.empty()) hi.push_back(0);   // never read: every row range is empty
+    ptr = up_i(hp.data(), hp.size());
+    idx = up_i(hi.data(), hi.size());
+    pat_ok = pat_ok && ptr && idx;
+  };
+  up_csr(jzr, P.jzr_ptr, P.jzr_i);
+  up_csr(jzc, P.jzc_ptr, P.jzc_i);
+  up_csr(wzr, P.wzr_ptr, P.wzr_i);
+  up_csr(wtr, P.wtr_ptr, P.wtr_i);
+  up_csr(jtr, P.jtr_ptr, P.jtr_i);
+  up_csr(thq, P.thq_ptr, P.thq_i);
+  {
+    std::vector<int> osp(n, 0);
+    for (int k = 0; k < M; ++k) osp[obs_s[k]] = 1;
+    P.obs_sp = up_i(osp.data(), n);
+    pat_ok = pat_ok && P.obs_sp;
+  }
   P.obs_ptr = up_i(obs_ptr.data(), N + 1);
   P.obs_s = up_i(obs_s.data(), M);
   P.obs_y = up_d(obs_y.data(), M);
@@ -337,7 +391,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   const bool sweep_global = sweep_dim * (sweep_dim + 1) * sizeof(float) > 160 * 1024;
   if (sweep_global) pr->sweep_work = A.alloc<float>(sweep_dim * (sweep_dim + 1));
   bool ok = P.react && P.prod && P.pidx && P.kfix && P.x0 && P.theta_lo && P.theta_hi &&
-            P.nu_ptr && P.nu_r && P.nu_v && P.rs_ptr && P.rs_r && P.pr_ptr && P.pr_r &&
+            P.nu_ptr && P.nu_r && P.nu_v && P.rs_ptr && P.rs_r && P.pr_ptr && P.pr_r && pat_ok &&
             P.obs_ptr && P.obs_s && P.obs_y && P.obs_sig && d_obs_t && obs_w && obs_elem_chk &&
             E.c && E.grad && E.JZ && E.JT && E.Wzz && E.Wzt && E.Wobj && E.part && E.wtt_part &&
             E.red && E.wtt && S.S && S.Sd && S.xth && S.inertia && S.diag && pr->sigma &&

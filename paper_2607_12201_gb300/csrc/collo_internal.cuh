@@ -54,6 +54,15 @@ struct DevProb {
   const int* rs_ptr; const int* rs_r;
   // parameter -> reactions it drives CSR
   const int* pr_ptr; const int* pr_r;
+  // structural nonzeros of the element derivative blocks (entries outside are
+  // exactly zero at every point), ascending index lists in CSR form
+  const int* jzr_ptr; const int* jzr_i;   // JZ row s -> columns t
+  const int* jzc_ptr; const int* jzc_i;   // JZ column s -> rows t
+  const int* wzr_ptr; const int* wzr_i;   // Wzz row t -> columns u
+  const int* wtr_ptr; const int* wtr_i;   // Wzt row t -> parameters q
+  const int* jtr_ptr; const int* jtr_i;   // JT row s -> parameters q
+  const int* thq_ptr; const int* thq_i;   // parameter q -> rows s of Wzt or JT
+  const int* obs_sp;                       // [n] 1 if species s is observed
   // observations grouped by element: CSR over elements
   const int* obs_ptr;    // [N+1]
   const int* obs_s;      // [M] species

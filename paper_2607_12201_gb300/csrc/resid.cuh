@@ -44,7 +44,10 @@ __device__ inline double block_max(double v, double* sh) {
 // Structured FP64 product y = K v of the regularised KKT matrix
 //   [ W + diag(sigma) + dw I   J^T  ] [vx]
 //   [ J                       -dc I ] [vl]
-// and r = b - y (b may be null: r = -y).  One block per element computes the
+// and r = b - y (b may be null: r = -y).  The derivative blocks are visited
+// only at their structural nonzeros (the pattern lists of DevProb, ascending,
+// so each sum keeps the order of the dense loop; the skipped terms are exact
+// zeros).  One block per element computes the
 // element's 8n rows and its contribution to the p parameter rows; norms per
 // element go to npart[i][0..2] (max |r_x|, max |r_c|, max |b| over the
 // element's rows).
@@ -73,20 +76,30 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
     // primal row z[i][j][s]
     double y = 0.0;
     if (vz) {
+      if (P.obs_sp[s])
 #pragma unroll
-      for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
+        for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
       if (j >= 1) {
         const double* wr = Wzz + (size_t)(j - 1) * nn + (size_t)s * n;
-        for (int t = 0; t < n; ++t) y += wr[t] * vz[zoff + j * n + t];
+        for (int e = P.wzr_ptr[s]; e < P.wzr_ptr[s + 1]; ++e) {
+          const int t = P.wzr_i[e];
+          y += wr[t] * vz[zoff + j * n + t];
+        }
         const double* wt = Wzt + (size_t)(j - 1) * np_ + (size_t)s * p;
-        for (int q = 0; q < p; ++q) y += wt[q] * vt[q];
+        for (int e = P.wtr_ptr[s]; e < P.wtr_ptr[s + 1]; ++e) {
+          const int q = P.wtr_i[e];
+          y += wt[q] * vt[q];
+        }
       }
       y += ((sigma ? sigma[zoff + idx] : 0.0) + dw) * vz[zoff + idx];
     }
     if (vl) {
       if (j >= 1) {
         const double* jz = JZ + (size_t)(j - 1) * nn;
-        for (int t = 0; t < n; ++t) y += jz[(size_t)t * n + s] * vl[zoff + j * n + t];
+        for (int e = P.jzc_ptr[s]; e < P.jzc_ptr[s + 1]; ++e) {
+          const int t = P.jzc_i[e];
+          y += jz[(size_t)t * n + s] * vl[zoff + j * n + t];
+        }
       }
 #pragma unroll
       for (int k = 1; k < NP; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
@@ -107,9 +120,15 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
 #pragma unroll
         for (int l = 0; l < NP; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];
         const double* jz = JZ + (size_t)(j - 1) * nn + (size_t)s * n;
-        for (int t = 0; t < n; ++t) yc += jz[t] * vz[zoff + j * n + t];
+        for (int e = P.jzr_ptr[s]; e < P.jzr_ptr[s + 1]; ++e) {
+          const int t = P.jzr_i[e];
+          yc += jz[t] * vz[zoff + j * n + t];
+        }
         const double* jt = JT + (size_t)(j - 1) * np_ + (size_t)s * p;
-        for (int q = 0; q < p; ++q) yc += jt[q] * vt[q];
+        for (int e = P.jtr_ptr[s]; e < P.jtr_ptr[s + 1]; ++e) {
+          const int q = P.jtr_i[e];
+          yc += jt[q] * vt[q];
+        }
       }
     }
     if (vl) yc -= dc * vl[zoff + idx];
@@ -121,7 +140,8 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
   for (int q = tid; q < p; q += BS) {
     double y = 0.0;
     for (int k = 1; k < NP; ++k)
-      for (int s = 0; s < n; ++s) {
+      for (int e = P.thq_ptr[q]; e < P.thq_ptr[q + 1]; ++e) {
+        const int s = P.thq_i[e];
         if (vz) y += Wzt[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vz[zoff + k * n + s];
         if (vl) y += JT[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vl[zoff + k * n + s];
       }
