@@ -316,19 +316,24 @@ __device__ inline void cp_async_elem(T* dst, const T* src) {
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 constexpr int RT_MAX_PAIRS = 2 * RT_MAX_TR + 2;   // pairs of a block of <= 124 rows
+constexpr int RT_MAX_THREADS = 512;               // threads of a register-tiled block
 
-// Tiles are owned in pairs along a tile row: pair t is tiles (ti, 2k) and
+// Tiles are owned in pairs along a tile row: pair (ti, k) is tiles (ti, 2k) and
 // (ti, 2k + 1) (the second absent when 2k + 1 > ti), so the multipliers of the
-// row are formed once for both.  Row ti holds ceil((ti + 1) / 2) pairs and the
-// rows before it floor((ti + 1)^2 / 4).
+// row are formed once for both.  Pairs are numbered column pair by column pair
+// (k ascending, then ti from 2k to R - 1; R - 2k pairs in column pair k), so
+// that the threads of a warp hold neighbouring column pairs and finish
+// together: a pair has no work left after pair step 4k + 1 (one tile) or
+// 4k + 3 (two tiles), when its columns are eliminated and published.
 __host__ __device__ inline int tile_pairs(int R) { return (R + 1) * (R + 1) / 4; }
-__device__ inline void tile_pair(int t, int& ti, int& k) {
-  int i = (int)(2.f * sqrtf((float)t + 0.25f)) - 1;
-  if (i < 0) i = 0;
-  while (tile_pairs(i + 1) <= t) ++i;
-  while (i > 0 && tile_pairs(i) > t) --i;
-  ti = i;
-  k = t - tile_pairs(i);
+__device__ inline void tile_pair(int t, int R, int& ti, int& k) {
+  // first pair of column pair k: k (R + 1 - k)
+  int c = (int)(0.5f * ((float)(R + 1) - sqrtf((float)((R + 1) * (R + 1) - 4 * t))));
+  if (c < 0) c = 0;
+  while (c > 0 && c * (R + 1 - c) > t) --c;
+  while ((c + 1) * (R - c) <= t) ++c;
+  k = c;
+  ti = 2 * c + (t - c * (R + 1 - c));
 }
 
 // PAIRED: each thread owns TPP row pairs of tiles (above); otherwise TPP
@@ -350,7 +355,7 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
     int k = 0;
     ti[j] = -1;
     if (PAIRED) {
-      if (t < npr) tile_pair(t, ti[j], k);
+      if (t < npr) tile_pair(t, R, ti[j], k);
       tj0[j] = 2 * k;
       two[j] = tj0[j] + 1 <= ti[j];
     } else {
@@ -369,8 +374,44 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
                                                                                   : T(0);
         }
   }
+  // PAIRED: a warp leaves the pair loop once none of its threads has work left
+  // (exit pair = max over its threads of 4k + 2 or 4k + 4); the loop's barrier
+  // (named barrier 1) of pair q counts the warps whose exit pair is >= q: those
+  // still working wait on it, the one leaving at q only arrives, so its reads
+  // of the previous pivot buffer are ordered before that buffer is rewritten.
+  int* s_exit = nullptr;
+  int* s_count = nullptr;
+  int my_exit = npairs;
+  if constexpr (PAIRED) {
+    __shared__ int exit_of_warp[RT_MAX_THREADS / 32];
+    __shared__ int count_of_pair[RT_MAX_PAIRS];
+    s_exit = exit_of_warp;
+    s_count = count_of_pair;
+    int qd = 0;
+#pragma unroll
+    for (int j = 0; j < TPP; ++j)
+      if (ti[j] >= 0) qd = max(qd, min(npairs, two[j] ? 2 * tj0[j] + 4 : 2 * tj0[j] + 2));
+    qd = (int)__reduce_max_sync(0xffffffffu, (unsigned)qd);
+    if ((tid & 31) == 0) s_exit[tid >> 5] = qd;
+  }
   bar();
+  if constexpr (PAIRED) {
+    const int nw = nt >> 5;
+    for (int q = tid; q < npairs; q += nt) {
+      int c = 0;
+      for (int w = 0; w < nw; ++w) c += s_exit[w] >= q ? 32 : 0;
+      s_count[q] = c;
+    }
+    my_exit = s_exit[tid >> 5];
+    bar();
+  }
   for (int q = 0; q < npairs; ++q) {
+    if constexpr (PAIRED) {
+      if (q >= my_exit) {
+        asm volatile("bar.arrive 1, %0;" ::"r"(s_count[q]) : "memory");
+        break;
+      }
+    }
     const int c0 = 2 * q, c1 = c0 + 1, tq = c0 >> 2;
     const bool hi = (c0 & 2) != 0;
     Pair<T>* b = ub + (q & 1) * RT_UB;
@@ -385,7 +426,8 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
             if (r >= c0 && r < ext)
               b[r] = Pair<T>{hi ? a[j][h][u][2] : a[j][h][u][0], hi ? a[j][h][u][3] : a[j][h][u][1]};
           }
-    bar();
+    if constexpr (PAIRED) asm volatile("bar.sync 1, %0;" ::"r"(s_count[q]) : "memory");
+    else bar();
     const T pa = b[c0].x, pb = b[c1].x, pd = b[c1].y;
     const T det = fma(pa, pd, -(pb * pb));
     T ia, ib, id;
@@ -395,7 +437,16 @@ __device__ void pair_eliminate_rt(int tid, int nt, int ext, int npairs, Entry en
     } else {
       ia = ib = id = T(0);
     }
-    if (tid == 0) {
+    // the pivots are recorded by thread 0, or in PAIRED mode by the owner of the
+    // diagonal tile (tq, tq), which works at this step
+    bool writer = tid == 0;
+    if constexpr (PAIRED) {
+      writer = false;
+#pragma unroll
+      for (int j = 0; j < TPP; ++j)
+        writer = writer || (ti[j] == tq && (tj0[j] == tq || (two[j] && tj0[j] + 1 == tq)));
+    }
+    if (writer) {
       Dout[3 * q + 0] = pa; Dout[3 * q + 1] = pb; Dout[3 * q + 2] = pd;
       pivs[q] = Pivot<T>{pa, pb, pd};
     }
@@ -640,7 +691,6 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
 // Tile pairs per thread of elem_factor_rt (1) and its block size for an element
 // of size ext (a multiple of 32 threads covering every tile; 0 when the
 // element is too large and elem_factor_one is used).
-constexpr int RT_MAX_THREADS = 512;
 template <typename T>
 __host__ __device__ constexpr int rt_tpt() { return 1; }   // tile pairs per thread
 template <typename T>
