@@ -266,7 +266,10 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
 //   sink(r, c, v), 2 npairs <= c <= r < ext: the eliminated trailing block;
 //   bar(): barrier over the NT threads; tid in [0, NT).
 // L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
-// Dout[3 q]; thread 0 accumulates the pivots' inertia.
+// Dout[3 q] and pivs[q] (recorded by thread 0, in PAIRED mode by the owner of
+// the diagonal tile); after the loop the threads count the pivots' inertia
+// into cnt[0..2].  In PAIRED mode the loop's barrier is named barrier 1 over
+// the warps that still have work (below); bar() is used outside the loop.
 constexpr int RT_MAX_TR = 31;            // tile rows: ext <= 124
 constexpr int RT_UB = 4 * RT_MAX_TR + 4;  // rows per pivot-column buffer
 
