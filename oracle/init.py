@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 The paper initialises the discretised states from a forward solve of the ODE
 at the nominal parameters (Section "Optimization framework configurations").
 Here the forward solve is the collocation scheme itself, element by element:
-``z[0,0] = x0``; ``z[i,0] = z[i-1,K]``; the interior states
+``z[0,0] = x0``; ``z[i,0] = sum_j b_j z[i-1,j]`` (``z[i-1,K]`` for Radau
+nodes); the interior states
 ``Z = (z[i,1], ..., z[i,K])`` solve the element's K collocation equations
 ``sum_j D[k][j] z[i,j] - h f(z[i,k], theta) = 0`` by Newton's method started
 at ``z[i,k] = z[i,0]``, stopped when ``max|dZ| <= 1e-12 max(1, max|Z|)``
@@ -54,5 +55,5 @@ def forward_sweep(prob, theta, tol: float = 1e-12, max_iter: int = 30):
             failures += 1
             Z = np.tile(start, (K, 1))
         z[i, 1:] = Z
-        start = z[i, K].copy()
+        start = z[i, K].copy() if prob.radau else prob.tab.b @ z[i]
     return z, failures

@@ -9,8 +9,10 @@ the estimated parameters ``theta[q]``.  Flat index of z[i, j, s] is
 
 Constraints ``c[i, k, s]`` (same flat layout as z):
 
-* ``k = 0`` (continuity / initial, Eq. 2c / 2d with Radau ``b_j = delta_jK``):
-  ``c[0,0] = z[0,0] - x0``, ``c[i,0] = z[i,0] - z[i-1,K]`` for i >= 1.
+* ``k = 0`` (continuity / initial, Eq. 2c / 2d):
+  ``c[0,0] = z[0,0] - x0``, ``c[i,0] = z[i,0] - sum_j b_j z[i-1,j]`` for
+  i >= 1, with ``b_j = l_j(1)``; for Radau nodes (``b_j = delta_jK``) this is
+  ``z[i,0] - z[i-1,K]``, computed as such.
 * ``k = 1..K`` (collocation, Eq. 3 with a single experiment):
   ``c[i,k] = sum_j D[k][j] z[i,j] - h f(z[i,k], theta)``.
 
@@ -43,10 +45,12 @@ LN10 = math.log(10.0)
 class Problem:
     """Index bookkeeping and the evaluation routines for one instance."""
 
-    def __init__(self, inst, K: int = 3):
+    def __init__(self, inst, K: int | None = None):
+        K = inst.K if K is None else K
         assert inst.K == K
         self.inst = inst
-        self.tab = Tables(K)
+        self.tab = Tables(K, getattr(inst, "scheme", "radau"))
+        self.radau = self.tab.scheme == "radau"
         self.K = K
         self.n, self.r, self.N, self.p = inst.n, inst.r, inst.N, inst.p
         self.h = inst.T / inst.N
@@ -202,7 +206,10 @@ class Problem:
         D, h, K = self.tab.D, self.h, self.K
         c = np.zeros((self.N, K + 1, self.n))
         c[0, 0] = z[0, 0] - self.inst.x0
-        c[1:, 0] = z[1:, 0] - z[:-1, K]
+        if self.radau:
+            c[1:, 0] = z[1:, 0] - z[:-1, K]
+        else:
+            c[1:, 0] = z[1:, 0] - np.einsum("j,ijs->is", self.tab.b, z[:-1])
         f = self.rhs(z[:, 1:, :], theta)               # [N, K, n]
         for k in range(1, K + 1):
             acc = np.zeros((self.N, self.n))
@@ -221,9 +228,14 @@ class Problem:
         Fz, Ft = self.rhs_jac(z[:, 1:, :], theta)      # [N,K,n,n], [N,K,n,p]
         Z = self._zidx()
         rows, cols, vals = [], [], []
-        # continuity / initial rows: +I on z[i,0], -I on z[i-1,K]
+        # continuity / initial rows: +I on z[i,0], -b_j I on z[i-1,j] (Radau: -I on z[i-1,K])
         rows.append(Z[:, 0].ravel()); cols.append(Z[:, 0].ravel()); vals.append(np.ones(N * n))
-        rows.append(Z[1:, 0].ravel()); cols.append(Z[:-1, K].ravel()); vals.append(-np.ones((N - 1) * n))
+        if self.radau:
+            rows.append(Z[1:, 0].ravel()); cols.append(Z[:-1, K].ravel()); vals.append(-np.ones((N - 1) * n))
+        else:
+            for j in range(K + 1):
+                rows.append(Z[1:, 0].ravel()); cols.append(Z[:-1, j].ravel())
+                vals.append(np.full((N - 1) * n, -self.tab.b[j]))
         for k in range(1, K + 1):
             for j in range(K + 1):
                 if j != k:

@@ -199,6 +199,8 @@ class Problem:
     def __init__(self, inst, precision: int = FP64, stream: int | None = None, device: int = 0,
                  launch_mode: int = 0):
         self.inst = inst
+        if getattr(inst, "scheme", "radau") != "radau" or inst.K != 3:
+            raise ValueError("the library implements Radau IIA collocation with K = 3 only")
         species = np.unique(inst.obs_s)
         obs_index = np.searchsorted(species, inst.obs_s)
         self._keep = dict(

@@ -61,6 +61,8 @@ class Instance:
     obs_y: np.ndarray
     obs_sigma: np.ndarray
     redraws: int = 0
+    # collocation nodes: "radau" (right Radau, tau_K = 1) or "gauss" (Gauss-Legendre)
+    scheme: str = "radau"
 
     @property
     def p(self) -> int:
