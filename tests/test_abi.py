@@ -83,3 +83,14 @@ def test_calls_on_null_problem_fail_cleanly(lib):
     assert L.collo_kkt_factor(None, None, 0.0, 0.0, 0, None) == lib.ERR_INVALID_ARG
     assert L.collo_kkt_solve(None, None, None, 0, 0.0, None) == lib.ERR_INVALID_ARG
     L.collo_problem_destroy(None)
+
+
+def test_binding_refuses_collocation_schemes_the_library_does_not_implement(lib):
+    import dataclasses
+    from paper_2607_12201_gb300 import workloads as W
+    base = W.linear_cascade(N=4)
+    for inst in (dataclasses.replace(base, K=4, scheme="gauss"),
+                 dataclasses.replace(base, scheme="gauss"),
+                 dataclasses.replace(base, K=4)):
+        with pytest.raises(ValueError, match="Radau IIA"):
+            lib.Problem(inst)
