@@ -28,9 +28,10 @@ nodes; row sums / polynomial exactness of the differentiation weights; the
 (2,3) Pade closed form of collocation on linear ODEs; the h^(2K-1) endpoint
 order; finite-difference Jacobian and Hessian; brute-force dense solves and
 eigenvalue inertia on tiny KKT systems; an independent reduced-space
-Gauss-Newton solve of the linear-cascade estimation problem.
-
-Parity unpinned: the optimum ``ipm.solve`` reaches on the nonlinear random
-mass-action networks has no independent check beyond the KKT conditions at
-the returned point and the linear-cascade analogue above.
+Gauss-Newton solve of the linear-cascade estimation problem; and, for small
+nonlinear mass-action networks (n <= 4, N = 12), an independent reduced-space
+Levenberg-Marquardt solve over theta alone (Radau IIA stage equations from the
+published Butcher matrix, Newton per element, a hand-written mass-action
+right-hand side) whose optimum the full-space ``ipm.solve`` reproduces
+(theta to 1e-7 / 1e-6, Phi to 1e-10).  Larger networks run the same code.
 """

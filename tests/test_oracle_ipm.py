@@ -95,3 +95,84 @@ def test_small_random_network_converges():
     inst = W.random_network(4, 6, n_obs=4, M=20, T=5.0, N=20, seed=41, theta0_spread=0.1)
     res = ipm.solve(inst)
     assert res.status in (ipm.SUCCESS, ipm.ACCEPTABLE)
+
+
+# The same reduced-space form for a nonlinear mass-action network: the stage
+# equations Z_k = z0 + h sum_l a_kl f(Z_l) of the published Radau IIA Butcher
+# matrix, solved by Newton's method element by element, with a hand-written
+# mass-action right-hand side f_s = sum_r nu_sr k_r prod_{reactants} z.
+def _rate_constants(theta, inst):
+    k = np.array(inst.kfix, dtype=float)
+    for j in range(inst.r):
+        q = inst.pidx[j]
+        if q >= 0:
+            k[j] = 10.0 ** theta[q] if inst.logscale else theta[q]
+    return k
+
+
+def _mass_action(z, k, inst):
+    n = inst.n
+    f, J = np.zeros(n), np.zeros((n, n))
+    for j in range(inst.r):
+        a, b = inst.react[j]
+        mon = z[a] * (z[b] if b >= 0 else 1.0)
+        dmon = np.zeros(n)
+        dmon[a] += z[b] if b >= 0 else 1.0
+        if b >= 0:
+            dmon[b] += z[a]
+        nu = np.zeros(n)
+        for s in inst.react[j]:
+            if s >= 0:
+                nu[s] -= 1.0
+        for s in inst.prod[j]:
+            if s >= 0:
+                nu[s] += 1.0
+        f += nu * k[j] * mon
+        J += np.outer(nu * k[j], dmon)
+    return f, J
+
+
+def reduced_residuals_network(theta, inst):
+    k = _rate_constants(theta, inst)
+    n, h = inst.n, inst.T / inst.N
+    z0 = np.array(inst.x0, dtype=float)
+    pts = []
+    for _ in range(inst.N):
+        Z = np.tile(z0, (3, 1))
+        for _ in range(50):
+            fj = [_mass_action(Z[l], k, inst) for l in range(3)]
+            F = np.zeros((3, n))
+            Jb = np.zeros((3 * n, 3 * n))
+            for a in range(3):
+                F[a] = Z[a] - z0 - h * sum(A_RADAU[a, l] * fj[l][0] for l in range(3))
+                for l in range(3):
+                    Jb[a * n:(a + 1) * n, l * n:(l + 1) * n] = \
+                        (np.eye(n) if a == l else 0.0) - h * A_RADAU[a, l] * fj[l][1]
+            d = np.linalg.solve(Jb, F.reshape(-1)).reshape(3, n)
+            Z = Z - d
+            if np.max(np.abs(d)) < 1e-15 * max(1.0, np.max(np.abs(Z))):
+                break
+        pts.append((z0.copy(), Z.copy()))
+        z0 = Z[2].copy()
+    res = []
+    for m in range(inst.M):
+        t = inst.obs_t[m]
+        i = min(max(int(math.ceil(t * inst.N / inst.T)) - 1, 0), inst.N - 1)
+        zs, Z = pts[i]
+        s = inst.obs_s[m]
+        vals = np.concatenate([[zs[s]], Z[:, s]])
+        yhat = np.polyval(np.polyfit(h * np.concatenate([[0.0], C_RADAU]), vals, 3), t - i * h)
+        res.append((yhat - inst.obs_y[m]) / inst.obs_sigma[m])
+    return np.array(res)
+
+
+@pytest.mark.parametrize("n,r,seed,theta_rtol", [(3, 4, 7, 1e-7), (4, 6, 41, 1e-6)])
+def test_network_ipm_matches_reduced_space_least_squares(n, r, seed, theta_rtol):
+    inst = W.random_network(n, r, n_obs=n, M=30, T=5.0, N=12, seed=seed, theta0_spread=0.1)
+    ref = least_squares(reduced_residuals_network, inst.theta0, args=(inst,), xtol=1e-15,
+                        ftol=1e-15, gtol=1e-15, method="lm")
+    res = ipm.solve(inst, opt=ipm.Options(tol=1e-10))
+    assert res.status == ipm.SUCCESS
+    th = res.theta(Problem(inst))
+    assert np.max(np.abs(th - ref.x) / np.abs(ref.x)) < theta_rtol, (th, ref.x)
+    assert abs(res.phi - 0.5 * np.sum(ref.fun ** 2)) < 1e-10 * res.phi
