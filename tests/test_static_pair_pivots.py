@@ -12,8 +12,8 @@ system is that plus the inertia of the p x p parameter Schur complement.
 
 This test restates that elimination in dense numpy, applies it to the oracle's
 regularised KKT matrices at interior-point iterates of three problems and three
-regularisations, and checks it against the oracle: Bunch-Kaufman inertia of the
-same matrix, and the oracle's Newton step."""
+regularisations, and checks it against the oracle: the inertia of the same matrix
+(signs of its eigenvalues), and the oracle's Newton step."""
 import numpy as np
 import pytest
 
@@ -35,14 +35,17 @@ def pair_order(prob):
 
 def static_pair_ldlt(A, b, npairs):
     """2x2-pivot elimination of the first npairs pairs in order, then the rest;
-    returns the inertia, the solution and the pivot determinants."""
+    returns the inertia, the solution and the pivot determinants relative to
+    |ad| + b^2 (-1: one positive and one negative eigenvalue, near 0: nearly
+    singular, +1 side: definite)."""
     A, b = A.copy(), b.copy()
     pos = neg = 0
     dets = []
     for q in range(npairs):
         lo, hi = 2 * q, 2 * q + 2
         P = A[lo:hi, lo:hi]
-        dets.append(P[0, 0] * P[1, 1] - P[0, 1] * P[1, 0])
+        dets.append((P[0, 0] * P[1, 1] - P[0, 1] * P[1, 0]) /
+                    (abs(P[0, 0] * P[1, 1]) + P[0, 1] * P[1, 0]))
         ev = np.linalg.eigvalsh(P)
         pos += int(np.sum(ev > 0)); neg += int(np.sum(ev < 0))
         L = A[hi:, lo:hi] @ np.linalg.inv(P)
@@ -87,3 +90,33 @@ def test_static_pair_pivots_match_oracle_inertia_and_step(make):
             assert ins == tuple(kkt.inertia_dense(A))
             sol = np.concatenate([dx, dlam])[perm]
             assert np.max(np.abs(xs - sol)) <= 1e-9 * max(1.0, np.max(np.abs(sol)))
+
+
+def test_static_pair_pivots_on_the_stiff_network():
+    # 30 species, rate constants over six decades: after the Schur updates some
+    # pairs become definite (both eigenvalues of one sign; 6 of 480 at the third
+    # iterate), so the element blocks are not of inertia (4n, 4n) here -- but no
+    # pivot comes near singular and their count is still the exact inertia.  Growth without pivoting costs accuracy (1e-4 relative here), which
+    # the FP64 refinement of the GPU path recovers.
+    inst = W.config3(N=4)
+    prob = Problem(inst)
+    perm = pair_order(prob)
+    npairs = 4 * prob.n * prob.N
+    for iters in (1, 3):
+        r = ipm.solve(inst, opt=ipm.Options(max_iter=iters))
+        ev = prob.evaluate(r.x, r.lam)
+        dc = 1e-8 * r.mu ** 0.25
+        th = r.x[prob.nz:]
+        sl, su = th - inst.theta_lo, inst.theta_hi - th
+        gphi = ev["grad"].copy()
+        gphi[prob.nz:] += -r.mu / sl + r.mu / su
+        rhs = -np.concatenate([gphi + ev["J"].T @ r.lam, ev["c"]])
+        for dw in (0.0, 1.0):
+            dx, dlam, _, _, inertia, K, _ = ipm.newton_direction(prob, ev, r.x, r.lam, r.zl, r.zu,
+                                                                  r.mu, dw, dc, ipm.Options())
+            A = K.toarray()
+            ins, xs, dets = static_pair_ldlt(A[np.ix_(perm, perm)], rhs[perm], npairs)
+            assert np.min(np.abs(dets)) > 1e-6             # no pivot nearly singular
+            assert ins == tuple(kkt.inertia_dense(A)) == tuple(inertia)
+            sol = np.concatenate([dx, dlam])[perm]
+            assert np.max(np.abs(xs - sol)) <= 1e-3 * max(1.0, np.max(np.abs(sol)))
