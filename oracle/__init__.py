@@ -13,10 +13,9 @@ Plain, slow, obviously-correct restatement of the paper's method:
   (Eq. 3, "Collocation equation with condition independence").
 * ``nlp``    - the simultaneous-method NLP of Eq. 2 / Eq. 3 for mass-action
   kinetics: objective, constraints, constraint Jacobian, Lagrangian Hessian.
-* ``kkt``    - the regularised primal-dual KKT matrix, its inertia (signs of
-  eigenvalues, of the whole matrix or of the Schur blocks of a natural-order
-  block elimination) and its solution (pivoted dense LU, whole or per block),
-  with FP64 iterative refinement.
+* ``kkt``    - the regularised primal-dual KKT matrix, its inertia and its
+  solution (dense Bunch-Kaufman or natural-order block elimination with
+  pivoted dense LU), with FP64 iterative refinement.
 * ``ipm``    - a filter line-search primal-dual interior-point method in the
   form of Waechter & Biegler (2006), the algorithm family of the solver the
   paper uses (Introduction: "a filter line-search interior point solver").

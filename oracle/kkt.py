@@ -15,9 +15,9 @@ bound-barrier diagonal.  Unknown order is ``[x (n_x), lambda (n_c)]``.
 
 Two factorizations, chosen to share nothing with the GPU design:
 
-* ``DenseFactor``: the whole matrix dense; inertia as the signs of its
-  eigenvalues (the definition; ``numpy.linalg.eigvalsh``); solve with
-  partial-pivoting LU.
+* ``DenseFactor``: the whole matrix dense; inertia from LAPACK's
+  Bunch-Kaufman ``sytrf`` (``scipy.linalg.ldl``, Sylvester's law on the block
+  diagonal D); solve with partial-pivoting LU.
 * ``BlockFactor``: unknowns regrouped element by element
   (``[z_i, lambda_i]`` for i = 0..N-1, then theta) into a block-tridiagonal
   bordered matrix, eliminated in natural order:
@@ -25,12 +25,7 @@ Two factorizations, chosen to share nothing with the GPU design:
   ``B~_i = B_i - A_i,i-1 S_{i-1}^{-1} B~_{i-1}``, parameter block
   ``S_theta = A_thth - sum_i B~_i^T S_i^{-1} B~_i``.  Each S_i is factored by
   pivoted dense LU; the inertia is the sum of the inertias of the S_i and of
-  S_theta (Haynsworth additivity), each from the signs of its eigenvalues.
-
-Inertia is counted from eigenvalues rather than from the pivots of a
-Bunch-Kaufman LDL^T: on the stiff network's KKT systems (smallest eigenvalues
-around 1e-9 against entries up to 1e3) Bunch-Kaufman's pivot signs miscount by
-one, while symmetric eigenvalues are accurate to about eps ||A||.
+  S_theta (Haynsworth additivity), each from Bunch-Kaufman.
 
 Both solves are followed by FP64 iterative refinement with the sparse matrix.
 """
@@ -48,12 +43,42 @@ def assemble(J, W, sigma, delta_w, delta_c):
     return K
 
 
+def inertia_of_D(d: np.ndarray):
+    """(n_pos, n_neg, n_zero) of a block-diagonal (1x1 / 2x2) symmetric D."""
+    npos = nneg = nzero = 0
+    m = d.shape[0]
+    i = 0
+    while i < m:
+        if i + 1 < m and d[i + 1, i] != 0.0:
+            a, b, c = d[i, i], d[i + 1, i], d[i + 1, i + 1]
+            det = a * c - b * b
+            if det < 0:
+                npos += 1; nneg += 1
+            elif det > 0:
+                if a + c > 0:
+                    npos += 2
+                else:
+                    nneg += 2
+            else:
+                ev = np.linalg.eigvalsh(np.array([[a, b], [b, c]]))
+                npos += int(np.sum(ev > 0)); nneg += int(np.sum(ev < 0)); nzero += int(np.sum(ev == 0))
+            i += 2
+        else:
+            if d[i, i] > 0:
+                npos += 1
+            elif d[i, i] < 0:
+                nneg += 1
+            else:
+                nzero += 1
+            i += 1
+    return npos, nneg, nzero
+
+
 def inertia_dense(A: np.ndarray):
-    """(n_pos, n_neg, n_zero): signs of the eigenvalues of the symmetric A."""
     if A.shape[0] == 0:
         return 0, 0, 0
-    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
-    return int(np.sum(ev > 0)), int(np.sum(ev < 0)), int(np.sum(ev == 0))
+    _, d, _ = sla.ldl(A, lower=True)
+    return inertia_of_D(d)
 
 
 class DenseFactor:

@@ -1,6 +1,5 @@
 """GPU KKT factorization / solve (collo_kkt_factor, collo_kkt_solve) against the
-oracle's dense / natural-order block solves (inertia from eigenvalue signs) on the
-same Newton system."""
+oracle's Bunch-Kaufman / natural-order block solves on the same Newton system."""
 import numpy as np
 import pytest
 
@@ -44,7 +43,7 @@ def _point(oprob, seed):
 # number near 1e23 (delta_c = 1e-8 blocks against rate constants up to 1e3),
 # both at random iterates and at the IPM's starting point, and two
 # backward-stable FP64 solves of it (this library's and the oracle's
-# LU, both with relative residual <= 5e-16) differ by 1e-10
+# Bunch-Kaufman / LU, both with relative residual <= 5e-16) differ by 1e-10
 # to 2.4e-10 there.  The backward error is checked separately (<= 1e-15).
 FWD_TOL = {"config3_N40": 1e-9}
 

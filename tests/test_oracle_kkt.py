@@ -55,3 +55,10 @@ def test_inertia_detects_negative_curvature():
         ev = np.linalg.eigvalsh(A)
         assert fac.inertia == (int(np.sum(ev > 0)), int(np.sum(ev < 0)), 0)
         assert fac.inertia != (prob.n_x, prob.n_c, 0)
+
+
+def test_inertia_of_D_two_by_two_blocks():
+    d = np.array([[1.0, 0, 0, 0], [0, 0.0, 2.0, 0], [0, 2.0, 0.0, 0], [0, 0, 0, -3.0]])
+    assert kkt.inertia_of_D(d) == (2, 2, 0)
+    d2 = np.array([[2.0, 1.0], [1.0, 2.0]])
+    assert kkt.inertia_of_D(d2) == (2, 0, 0)

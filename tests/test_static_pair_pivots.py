@@ -13,7 +13,8 @@ system is that plus the inertia of the p x p parameter Schur complement.
 This test restates that elimination in dense numpy, applies it to the oracle's
 regularised KKT matrices at interior-point iterates of three problems and three
 regularisations, and checks it against the oracle: the inertia of the same matrix
-(signs of its eigenvalues), and the oracle's Newton step."""
+(Bunch-Kaufman) and the oracle's Newton step.  On the stiff network the inertia check
+is against the eigenvalue signs of the whole (small, dense) matrix."""
 import numpy as np
 import pytest
 
@@ -94,10 +95,13 @@ def test_static_pair_pivots_match_oracle_inertia_and_step(make):
 
 def test_static_pair_pivots_on_the_stiff_network():
     # 30 species, rate constants over six decades: after the Schur updates some
-    # pairs become definite (both eigenvalues of one sign; 6 of 480 at the third
+    # pairs become definite (both eigenvalues of one sign; 23 of 480 at the third
     # iterate), so the element blocks are not of inertia (4n, 4n) here -- but no
-    # pivot comes near singular and their count is still the exact inertia.  Growth without pivoting costs accuracy (1e-4 relative here), which
-    # the FP64 refinement of the GPU path recovers.
+    # pivot comes near singular and their count equals the eigenvalue count (where,
+    # at one of these systems, a Bunch-Kaufman LDL^T of the same matrix is off by
+    # one: the smallest eigenvalues are ~1e-9).  Growth without pivoting costs
+    # accuracy (1e-4 relative here), which the FP64 refinement of the GPU path
+    # recovers.
     inst = W.config3(N=4)
     prob = Problem(inst)
     perm = pair_order(prob)
@@ -117,6 +121,7 @@ def test_static_pair_pivots_on_the_stiff_network():
             A = K.toarray()
             ins, xs, dets = static_pair_ldlt(A[np.ix_(perm, perm)], rhs[perm], npairs)
             assert np.min(np.abs(dets)) > 1e-6             # no pivot nearly singular
-            assert ins == tuple(kkt.inertia_dense(A)) == tuple(inertia)
+            eig = np.linalg.eigvalsh(A)
+            assert ins == (int(np.sum(eig > 0)), int(np.sum(eig < 0)), 0)
             sol = np.concatenate([dx, dlam])[perm]
             assert np.max(np.abs(xs - sol)) <= 1e-3 * max(1.0, np.max(np.abs(sol)))
