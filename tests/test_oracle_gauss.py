@@ -137,3 +137,59 @@ def test_gauss_ipm_agrees_with_radau_estimate():
     tr, tg = rr.x[-base.p:], rg.x[-base.p:]
     assert np.max(np.abs(tg - tr) / np.abs(tr)) < 1e-5
     assert np.max(np.abs(tg - tr)) > 0.0
+
+
+# K = 2 Gauss (Hammer-Hollingsworth) Butcher tableau, published in closed form.
+_S3 = math.sqrt(3.0)
+_C2 = np.array([0.5 - _S3 / 6, 0.5 + _S3 / 6])
+_A2 = np.array([[0.25, 0.25 - _S3 / 6], [0.25 + _S3 / 6, 0.25]])
+_B2 = np.array([0.5, 0.5])
+
+
+def _reduced_gauss2(theta, inst):
+    """Weighted misfit of the K = 2 Gauss Runge-Kutta discretisation (stage
+    equations by Newton per element, end value y0 + h sum_j b_j f(Z_j), model
+    output from the quadratic through (0, c_1, c_2))."""
+    from test_oracle_ipm import _mass_action, _rate_constants
+    k = _rate_constants(theta, inst)
+    n, h = inst.n, inst.T / inst.N
+    z0 = np.array(inst.x0, dtype=float)
+    pts = []
+    for _ in range(inst.N):
+        Z = np.tile(z0, (2, 1))
+        for _ in range(50):
+            fj = [_mass_action(Z[l], k, inst) for l in range(2)]
+            F = np.array([Z[a] - z0 - h * sum(_A2[a, l] * fj[l][0] for l in range(2)) for a in range(2)])
+            Jb = np.block([[(np.eye(n) if a == l else 0.0 * np.eye(n)) - h * _A2[a, l] * fj[l][1]
+                            for l in range(2)] for a in range(2)])
+            d = np.linalg.solve(Jb, F.reshape(-1)).reshape(2, n)
+            Z = Z - d
+            if np.max(np.abs(d)) < 1e-15 * max(1.0, np.max(np.abs(Z))):
+                break
+        pts.append((z0.copy(), Z.copy()))
+        fj = [_mass_action(Z[l], k, inst)[0] for l in range(2)]
+        z0 = z0 + h * (_B2[0] * fj[0] + _B2[1] * fj[1])
+    res = []
+    for m in range(inst.M):
+        t = inst.obs_t[m]
+        i = min(max(int(math.ceil(t * inst.N / inst.T)) - 1, 0), inst.N - 1)
+        zs, Z = pts[i]
+        s = inst.obs_s[m]
+        vals = np.array([zs[s], Z[0, s], Z[1, s]])
+        yhat = np.polyval(np.polyfit(h * np.array([0.0, _C2[0], _C2[1]]), vals, 2), t - i * h)
+        res.append((yhat - inst.obs_y[m]) / inst.obs_sigma[m])
+    return np.array(res)
+
+
+def test_gauss_k2_ipm_matches_reduced_space_runge_kutta():
+    from scipy.optimize import least_squares
+    from oracle import ipm as oipm
+    base = W.random_network(3, 4, n_obs=3, M=30, T=5.0, N=12, seed=7, theta0_spread=0.1)
+    inst = dataclasses.replace(base, K=2, scheme="gauss")
+    ref = least_squares(_reduced_gauss2, inst.theta0, args=(inst,), xtol=1e-15, ftol=1e-15,
+                        gtol=1e-15, method="lm")
+    res = oipm.solve(inst, opt=oipm.Options(tol=1e-10))
+    assert res.status == oipm.SUCCESS
+    th = res.x[-inst.p:]
+    assert np.max(np.abs(th - ref.x) / np.abs(ref.x)) < 1e-6, (th, ref.x)
+    assert abs(res.phi - 0.5 * np.sum(ref.fun ** 2)) < 1e-10 * res.phi
