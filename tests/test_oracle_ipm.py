@@ -176,3 +176,21 @@ def test_network_ipm_matches_reduced_space_least_squares(n, r, seed, theta_rtol)
     th = res.theta(Problem(inst))
     assert np.max(np.abs(th - ref.x) / np.abs(ref.x)) < theta_rtol, (th, ref.x)
     assert abs(res.phi - 0.5 * np.sum(ref.fun ** 2)) < 1e-10 * res.phi
+
+
+def test_noise_free_estimate_converges_at_endpoint_order():
+    # With exact data from the closed-form cascade trajectory, the discrete
+    # optimum misses theta_true only by the discretisation error at the
+    # observation times.  For N = 20, 40, 80 (T = 10) every observation time
+    # t_m = m/2 is an element end, where Radau IIA is superconvergent of order
+    # 2K - 1 = 5: halving h divides the parameter error by about 2^5.
+    errs = []
+    for N in (20, 40, 80):
+        inst = W.linear_cascade(N=N, noise=False)
+        res = ipm.solve(inst, opt=ipm.Options(tol=1e-12))
+        assert res.status == ipm.SUCCESS
+        errs.append(res.x[-2:] - np.array([0.7, 0.3]))
+    for coarse, fine in zip(errs, errs[1:]):
+        ratio = np.abs(coarse) / np.abs(fine)
+        assert np.all((ratio > 28.0) & (ratio < 36.0)), ratio
+        assert np.all(np.sign(coarse) == np.sign(fine))
