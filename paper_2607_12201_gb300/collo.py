@@ -193,6 +193,23 @@ def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
 
+def _host_vec(a, size, what):
+    """A host array of exactly ``size`` doubles (converted, length checked: the
+    library reads ``size`` values through the pointer).  ``None``, an int
+    (a raw pointer) or a tensor pass through unchecked: their extent is the
+    caller's responsibility."""
+    if a is None or isinstance(a, int) or hasattr(a, "data_ptr"):
+        return a
+    v = np.ascontiguousarray(a, dtype=np.float64)
+    if v.size != size:
+        raise ValueError(f"{what} has {v.size} values, expected {size}")
+    return v
+
+
+# statuses of a call that failed as a call (not an outcome of the solve)
+_CALL_ERRORS = (ERR_INVALID_ARG, ERR_OOM, ERR_NOT_FACTORED, ERR_DEVICE, ERR_NOT_EVALUATED)
+
+
 class Problem:
     """One estimation problem resident on the GPU (wraps collo_problem)."""
 
@@ -252,8 +269,8 @@ class Problem:
     def eval(self, x, lam=None, obj_factor: float = 1.0, outputs: bool = True):
         """collo_eval on host arrays; returns a dict of host arrays."""
         n, p, N = self.n, self.p, self.N
-        x = _f64(x)
-        lam = None if lam is None else _f64(lam)
+        x = _host_vec(x, self.n_x, "x")
+        lam = _host_vec(lam, self.n_c, "lam")
         out = {}
         eo = EvalOut()
         if outputs:
@@ -286,18 +303,22 @@ class Problem:
     # --- KKT ---------------------------------------------------------------------
     def kkt_factor(self, sigma=None, delta_w=0.0, delta_c=0.0, precision: int = -1):
         inr = Inertia()
-        sig = None if sigma is None else (_f64(sigma) if isinstance(sigma, np.ndarray) else sigma)
+        sig = _host_vec(sigma, self.n_x, "sigma")
         _check(lib.collo_kkt_factor(self.h, _ptr(sig), float(delta_w), float(delta_c),
                                     int(precision), C.byref(inr)))
         return (int(inr.n_pos), int(inr.n_neg), int(inr.n_zero))
 
     def kkt_solve(self, rhs, refine_max: int = 10, refine_tol: float = 1e-12, out=None):
         info = SolveInfo()
+        rhs = _host_vec(rhs, self.n_x + self.n_c, "rhs")
         if isinstance(rhs, np.ndarray):
-            rhs = _f64(rhs)
             sol = np.zeros_like(rhs) if out is None else out
         else:
             sol = out
+        if isinstance(sol, np.ndarray) and (sol.size != self.n_x + self.n_c
+                                            or sol.dtype != np.float64
+                                            or not sol.flags.c_contiguous):
+            raise ValueError("out must be a contiguous float64 array of the rhs's size")
         _check(lib.collo_kkt_solve(self.h, _ptr(rhs), _ptr(sol), int(refine_max),
                                    float(refine_tol), C.byref(info)))
         return sol, dict(sweeps=info.refinement_sweeps, residual=info.residual)
@@ -312,7 +333,7 @@ class Problem:
         return o
 
     def ipm_solve(self, theta0=None, want_x: bool = True, **kw):
-        th0 = _f64(self.inst.theta0 if theta0 is None else theta0)
+        th0 = _host_vec(_f64(self.inst.theta0 if theta0 is None else theta0), self.p, "theta0")
         o = self.ipm_options(**kw)
         res = Result()
         theta = np.zeros(self.p)
@@ -321,7 +342,11 @@ class Problem:
         res.theta = theta.ctypes.data
         res.x = None if x is None else x.ctypes.data
         res.lambda_ = None if lam is None else lam.ctypes.data
-        lib.collo_ipm_solve(self.h, th0.ctypes.data, C.byref(o), C.byref(res))
+        st = lib.collo_ipm_solve(self.h, th0.ctypes.data, C.byref(o), C.byref(res))
+        # the call returns the solve's outcome, which it also stores in the result;
+        # a call that failed before producing a result returns its error only
+        if st in _CALL_ERRORS or st != res.status:
+            raise ColloError(st, last_error())
         return _result_dict(res, theta, x, lam)
 
     def time_phase(self, phase: int, precision: int = -1, reps: int = 20) -> float:
@@ -333,7 +358,8 @@ class Problem:
     def initial_states(self, theta):
         x = np.zeros(self.n_x)
         f = C.c_int(0)
-        _check(lib.collo_initial_states(self.h, _f64(theta).ctypes.data, x.ctypes.data,
+        theta = _host_vec(_f64(theta), self.p, "theta")
+        _check(lib.collo_initial_states(self.h, theta.ctypes.data, x.ctypes.data,
                                         C.byref(f)))
         return x, int(f.value)
 
@@ -350,7 +376,8 @@ def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
     """collo_batch_solve: solve several problems together; list of result dicts."""
     n = len(problems)
     handles = (C.c_void_p * n)(*[p.h.value for p in problems])
-    th = [_f64(p.inst.theta0 if theta0s is None else theta0s[i]) for i, p in enumerate(problems)]
+    th = [_host_vec(_f64(p.inst.theta0 if theta0s is None else theta0s[i]), p.p, f"theta0s[{i}]")
+          for i, p in enumerate(problems)]
     thp = (C.c_void_p * n)(*[t.ctypes.data for t in th])
     res = (Result * n)()
     outs = []
@@ -390,7 +417,8 @@ class Server:
         self._keep = {}
 
     def submit(self, problem, theta0=None) -> int:
-        th = _f64(problem.inst.theta0 if theta0 is None else theta0)
+        th = _host_vec(_f64(problem.inst.theta0 if theta0 is None else theta0), problem.p,
+                       "theta0")
         t = C.c_longlong()
         _check(lib.collo_server_submit(self.h, problem.h, th.ctypes.data, C.byref(t)))
         self._keep[t.value] = (problem, th)

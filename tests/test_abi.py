@@ -94,3 +94,46 @@ def test_binding_refuses_collocation_schemes_the_library_does_not_implement(lib)
                  dataclasses.replace(base, K=4)):
         with pytest.raises(ValueError, match="Radau IIA"):
             lib.Problem(inst)
+
+
+def _unattached_problem(lib, n_x=10, n_c=8, p=2):
+    """A binding Problem with a NULL handle: the library refuses every call on
+    it before touching a device, so the binding's own checks run on the CPU."""
+    pr = object.__new__(lib.Problem)
+    pr.h = C.c_void_p()
+    pr.n, pr.r, pr.p, pr.N = 1, 1, p, 1
+    pr.n_x, pr.n_c = n_x, n_c
+    pr.inst = None
+    return pr
+
+
+def test_binding_checks_host_array_lengths_before_calling(lib):
+    pr = _unattached_problem(lib)
+    with pytest.raises(ValueError, match="x has 9 values, expected 10"):
+        pr.eval(np.zeros(9))
+    with pytest.raises(ValueError, match="lam has 9 values, expected 8"):
+        pr.eval(np.zeros(10), np.zeros(9))
+    with pytest.raises(ValueError, match="sigma"):
+        pr.kkt_factor(np.zeros(11))
+    with pytest.raises(ValueError, match="rhs"):
+        pr.kkt_solve(np.zeros(17))
+    with pytest.raises(ValueError, match="out"):
+        pr.kkt_solve(np.zeros(18), out=np.zeros(17))
+    with pytest.raises(ValueError, match="theta0"):
+        pr.ipm_solve(theta0=np.zeros(3))
+    with pytest.raises(ValueError, match="theta"):
+        pr.initial_states(np.zeros(1))
+    # right lengths reach the library, which refuses the NULL problem
+    with pytest.raises(lib.ColloError) as e:
+        pr.kkt_solve(np.zeros(18))
+    assert e.value.status == lib.ERR_INVALID_ARG
+
+
+def test_ipm_solve_raises_when_the_call_fails_before_a_result(lib):
+    # collo_ipm_solve on a NULL problem returns COLLO_ERR_INVALID_ARG without
+    # writing the result; the binding must not report the untouched result
+    # (status 0, "solved") as an outcome
+    pr = _unattached_problem(lib)
+    with pytest.raises(lib.ColloError) as e:
+        pr.ipm_solve(theta0=np.zeros(2), want_x=False)
+    assert e.value.status == lib.ERR_INVALID_ARG
