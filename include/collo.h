@@ -276,7 +276,9 @@ void collo_ipm_options_default(collo_ipm_options* opts);
  * primal-dual interior-point method (paper Introduction; Waechter & Biegler
  * 2006), all iterates resident on the device.  States start from a
  * collocation forward sweep at theta0.  opts may be NULL (defaults).
- * result->status is the solver outcome; the return value is the same. */
+ * result->status is the solver outcome; the return value is the same.  A call
+ * that fails before the solve starts (INVALID_ARG, OOM, DEVICE) returns its
+ * error and leaves *result unwritten. */
 collo_status collo_ipm_solve(collo_problem* prob, const double* theta0,
                              const collo_ipm_options* opts, collo_result* result);
 
