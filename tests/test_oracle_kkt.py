@@ -1,4 +1,6 @@
 """Pins for the oracle's KKT factorizations: brute-force solves and eigenvalue inertia."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -24,9 +26,13 @@ CASES = [(lambda: W.small_network(n=2, r=3, N=2, seed=21), 0.0, 1e-8),
          (lambda: W.linear_cascade(N=4), 0.0, 1e-8)]
 
 
+@pytest.mark.parametrize("scheme", ["radau3", "gauss4"])
 @pytest.mark.parametrize("make,dw,dc", CASES)
-def test_dense_and_block_match_bruteforce(make, dw, dc):
-    prob = Problem(make())
+def test_dense_and_block_match_bruteforce(make, dw, dc, scheme):
+    inst = make()
+    if scheme == "gauss4":   # continuity couples all K + 1 points of the previous element
+        inst = dataclasses.replace(inst, K=4, scheme="gauss")
+    prob = Problem(inst)
     K = _kkt(prob, 3, dw, dc)
     A = K.toarray()
     rng = np.random.default_rng(4)
