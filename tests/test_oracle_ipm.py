@@ -194,3 +194,36 @@ def test_noise_free_estimate_converges_at_endpoint_order():
         ratio = np.abs(coarse) / np.abs(fine)
         assert np.all((ratio > 28.0) & (ratio < 36.0)), ratio
         assert np.all(np.sign(coarse) == np.sign(fine))
+
+
+def test_inertia_correction_follows_the_published_schedule(monkeypatch):
+    # Waechter & Biegler (2006), inertia correction: try delta_w = 0; then 1e-4
+    # if no earlier iteration needed a correction, else max(delta_min,
+    # delta_last / 3); grow by 100 while no correction has ever succeeded, by 8
+    # after; remember the accepted value.  The wrapper reports a wrong inertia
+    # below a per-iteration threshold and records every delta_w tried.
+    thresholds = [0.5, 0.5, None, 1e-3]
+    calls = []
+    real = ipm.newton_direction
+
+    def fake(prob, ev, x, lam, zl, zu, mu, delta_w, delta_c, opt):
+        if delta_w == 0.0:
+            calls.append([])
+        calls[-1].append(delta_w)
+        out = list(real(prob, ev, x, lam, zl, zu, mu, delta_w, delta_c, opt))
+        thr = thresholds[len(calls) - 1]
+        if thr is not None and delta_w < thr:
+            npos, nneg, nzero = out[4]
+            out[4] = (npos - 1, nneg + 1, nzero)
+        return tuple(out)
+
+    monkeypatch.setattr(ipm, "newton_direction", fake)
+    res = ipm.solve(W.config1(), opt=ipm.Options(max_iter=len(thresholds)))
+    assert res.iterations == len(thresholds)
+    expected = [[0.0, 1e-4, 1e-2, 1.0],                # first correction: x100 from 1e-4
+                [0.0, 1.0 / 3.0, 8.0 / 3.0],           # last/3, then x8
+                [0.0],                                 # no correction: last value kept
+                [0.0, 8.0 / 9.0]]                      # (8/3)/3 suffices
+    assert len(calls) == len(expected)
+    for got, want in zip(calls, expected):
+        assert np.allclose(got, want, rtol=1e-12, atol=0), (got, want)
