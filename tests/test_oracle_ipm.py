@@ -227,3 +227,28 @@ def test_inertia_correction_follows_the_published_schedule(monkeypatch):
     assert len(calls) == len(expected)
     for got, want in zip(calls, expected):
         assert np.allclose(got, want, rtol=1e-12, atol=0), (got, want)
+
+
+def test_barrier_parameter_follows_the_monotone_update():
+    # Waechter & Biegler (2006), monotone barrier update: whenever the barrier
+    # problem is solved to kappa_eps * mu, mu <- max(tol / 10, min(kappa_mu mu,
+    # mu^theta_mu)) with kappa_mu = 0.2, theta_mu = 1.5, possibly several times
+    # in one iteration.  Every change of mu along the history must be such a
+    # chain, mu never grows, and it ends above the floor tol / 10.
+    tol = 1e-8
+    res = ipm.solve(W.config1(), opt=ipm.Options(tol=tol))
+    assert res.status == ipm.SUCCESS
+    mus = [h["mu"] for h in res.history]
+    assert mus[0] == 0.1
+    decreases = 0
+    for a, b in zip(mus, mus[1:]):
+        assert b <= a
+        if b == a:
+            continue
+        m, steps = a, 0
+        while m > b * (1 + 1e-12):
+            m = max(tol / 10.0, min(0.2 * m, m ** 1.5))
+            steps += 1
+        assert abs(m - b) <= 1e-12 * b and steps >= 1, (a, b)
+        decreases += steps
+    assert decreases >= 4 and min(mus) >= tol / 10.0
