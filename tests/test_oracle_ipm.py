@@ -252,3 +252,40 @@ def test_barrier_parameter_follows_the_monotone_update():
         assert abs(m - b) <= 1e-12 * b and steps >= 1, (a, b)
         decreases += steps
     assert decreases >= 4 and min(mus) >= tol / 10.0
+
+
+def test_fraction_to_boundary_is_the_largest_feasible_step():
+    # alpha_max = max{alpha in (0, 1] : v + alpha dv >= (1 - tau) v}, checked
+    # against bisection on random cases and two hand-worked ones
+    assert ipm.fraction_to_boundary(np.array([1.0]), np.array([-2.0]), 0.99) == 0.495
+    assert ipm.fraction_to_boundary(np.array([1.0, 2.0]), np.array([0.5, 3.0]), 0.99) == 1.0
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        k = int(rng.integers(1, 6))
+        v = rng.uniform(1e-3, 2.0, k)
+        dv = rng.normal(0.0, 3.0, k)
+        tau = rng.uniform(0.9, 0.9999)
+        a = ipm.fraction_to_boundary(v, dv, tau)
+        feasible = lambda al: np.all(v + al * dv >= (1 - tau) * v - 1e-14)
+        assert 0.0 < a <= 1.0 and feasible(a)
+        lo, hi = 0.0, 1.0
+        if feasible(1.0):
+            assert a == 1.0
+            continue
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if feasible(mid) else (lo, mid)
+        assert abs(a - lo) <= 1e-12 * max(1.0, lo)
+
+
+def test_initial_parameters_are_pushed_inside_the_bounds():
+    # bound push of Waechter & Biegler (2006), Section 3.6: theta0 is moved to at
+    # least p_L = min(kappa_1 max(1, |lo|), kappa_2 (hi - lo)) inside the lower
+    # bound (p_U likewise), kappa_1 = kappa_2 = 1e-2
+    opt = ipm.Options()
+    lo, hi = np.full(3, -5.0), np.full(3, 5.0)
+    th = ipm.push_into_bounds(np.array([-5.0, 0.3, 7.0]), lo, hi, opt)
+    assert np.allclose(th, [-4.95, 0.3, 4.95], rtol=0, atol=1e-15)
+    lo, hi = np.full(2, 1e-3), np.full(2, 1e2)
+    th = ipm.push_into_bounds(np.array([0.0, 1e3]), lo, hi, opt)
+    assert np.allclose(th, [1e-3 + 1e-2, 1e2 - 0.99999], rtol=0, atol=1e-13)
