@@ -289,3 +289,39 @@ def test_initial_parameters_are_pushed_inside_the_bounds():
     lo, hi = np.full(2, 1e-3), np.full(2, 1e2)
     th = ipm.push_into_bounds(np.array([0.0, 1e3]), lo, hi, opt)
     assert np.allclose(th, [1e-3 + 1e-2, 1e2 - 0.99999], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dw", [0.0, 1e-2])
+def test_condensed_step_solves_the_full_primal_dual_newton_system(dw):
+    # The oracle solves the augmented system in which the bound duals are folded
+    # into Sigma = Z_L / S_L + Z_U / S_U and the barrier gradient; its step, with
+    # the bound-dual steps recovered from it, must satisfy every row of the
+    # unreduced primal-dual Newton system (Waechter & Biegler 2006, Eq. 11):
+    #   (W + dw I) dx + J^T dlam - dzl + dzu = -(grad phi + J^T lam - zl + zu)
+    #   J dx - dc dlam = -c
+    #   Z_L dth + S_L dzl = mu - S_L zl,   -Z_U dth + S_U dzu = mu - S_U zu
+    inst = W.small_network(n=3, r=4, N=5, seed=7)
+    prob = Problem(inst)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.2, 1.0, prob.n_x)
+    x[prob.nz:] = rng.uniform(-1.0, 0.5, prob.p)
+    lam = rng.standard_normal(prob.n_c)
+    zl, zu = rng.uniform(0.5, 2.0, prob.p), rng.uniform(0.5, 2.0, prob.p)
+    mu, dc = 0.05, 1e-6
+    ev = prob.evaluate(x, lam)
+    dx, dlam, dzl, dzu, _, _, _ = ipm.newton_direction(prob, ev, x, lam, zl, zu, mu, dw, dc,
+                                                       ipm.Options())
+    Wm, J = ev["W"].toarray(), ev["J"].toarray()     # W is stored in full (symmetric)
+    assert np.array_equal(Wm, Wm.T)
+    th = x[prob.nz:]
+    sl, su = th - inst.theta_lo, inst.theta_hi - th
+    dth = dx[prob.nz:]
+    E = np.zeros((prob.n_x, prob.p))
+    E[prob.nz:, :] = np.eye(prob.p)
+    stat = (Wm + dw * np.eye(prob.n_x)) @ dx + J.T @ dlam - E @ dzl + E @ dzu \
+        + (ev["grad"] + J.T @ lam - E @ zl + E @ zu)
+    scale = max(1.0, np.max(np.abs(ev["grad"])), np.max(np.abs(J.T @ lam)))
+    assert np.max(np.abs(stat)) <= 1e-10 * scale
+    assert np.max(np.abs(J @ dx - dc * dlam + ev["c"])) <= 1e-10 * max(1.0, np.max(np.abs(ev["c"])))
+    assert np.allclose(zl * dth + sl * dzl, mu - sl * zl, rtol=0, atol=1e-12)
+    assert np.allclose(-zu * dth + su * dzu, mu - su * zu, rtol=0, atol=1e-12)
