@@ -325,3 +325,51 @@ def test_condensed_step_solves_the_full_primal_dual_newton_system(dw):
     assert np.max(np.abs(J @ dx - dc * dlam + ev["c"])) <= 1e-10 * max(1.0, np.max(np.abs(ev["c"])))
     assert np.allclose(zl * dth + sl * dzl, mu - sl * zl, rtol=0, atol=1e-12)
     assert np.allclose(-zu * dth + su * dzu, mu - su * zu, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("make", [lambda: W.config1(),
+                                  lambda: W.small_network(n=3, r=4, N=6, seed=7)],
+                         ids=["cascade", "small_network"])
+def test_every_accepted_step_passes_a_filter_acceptance_test(make, monkeypatch):
+    # Waechter & Biegler (2006), Section 2.3: a trial point is accepted if it
+    # sufficiently reduces the constraint violation theta = ||c||_1 or the
+    # barrier function phi_mu against the current iterate (Eq. 18), or, under the
+    # switching condition, satisfies the Armijo condition phi_mu(x + alpha d) <=
+    # phi_mu(x) + eta_phi alpha grad phi_mu^T d (Eq. 20).  The iterates are taken
+    # from the one evaluation per iteration; theta, phi_mu and the step are
+    # recomputed from them here.
+    inst = make()
+    seen = []
+    real = Problem.evaluate
+
+    def record(self, x, lam, obj_factor=1.0):
+        seen.append(np.array(x, copy=True))
+        return real(self, x, lam, obj_factor)
+
+    monkeypatch.setattr(Problem, "evaluate", record)
+    res = ipm.solve(inst, opt=ipm.Options(tol=1e-8))
+    assert res.status == ipm.SUCCESS
+    assert len(seen) == res.iterations + 1
+    prob = Problem(inst)
+    opt = ipm.Options()
+    nz, lo, hi = prob.nz, inst.theta_lo, inst.theta_hi
+
+    def barrier(x, mu):
+        th = x[nz:]
+        return prob.objective(x)[0] - mu * np.sum(np.log(th - lo)) - mu * np.sum(np.log(hi - th))
+
+    kinds = set()
+    for k, rec in enumerate(res.history):
+        x0, x1, mu, alpha = seen[k], seen[k + 1], rec["mu"], rec["alpha"]
+        th0, th1 = [float(np.sum(np.abs(prob.constraints(v)))) for v in (x0, x1)]
+        ph0, ph1 = barrier(x0, mu), barrier(x1, mu)
+        d = (x1 - x0) / alpha
+        t = x0[nz:]
+        g = float(prob.objective(x0)[1] @ d) + float(np.sum((-mu / (t - lo) + mu / (hi - t)) * d[nz:]))
+        slack = 1e-12 * max(1.0, abs(ph0))
+        by_theta = th1 <= (1 - opt.gamma_theta) * th0 + 1e-14
+        by_phi = ph1 <= ph0 - opt.gamma_phi * th0 + slack
+        armijo = g < 0 and ph1 <= ph0 + opt.eta_phi * alpha * g + slack
+        assert by_theta or by_phi or armijo, k
+        kinds.add("theta/phi" if (by_theta or by_phi) else "armijo")
+    assert kinds
