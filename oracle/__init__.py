@@ -34,7 +34,11 @@ Levenberg-Marquardt solve over theta alone (Radau IIA stage equations from the
 published Butcher matrix, Newton per element, a hand-written mass-action
 right-hand side) whose optimum the full-space ``ipm.solve`` reproduces
 (theta to 1e-7 / 1e-6, Phi to 1e-10); with noise-free cascade data, the
-estimate converging to the true rate constants at the endpoint order h^5.
+estimate converging to the true rate constants at the endpoint order h^5;
+for the interior-point rules of Waechter & Biegler (2006): the inertia-correction
+schedule call by call, the monotone barrier update, the fraction-to-boundary
+step, the initial bound push, the condensed step against the unreduced
+primal-dual Newton system, and filter acceptance of every accepted step.
 Larger networks run the same code.  The Gauss-Legendre option (``radau.Tables``
 with ``scheme="gauss"``) is pinned by closed-form nodes, quadrature and
 polynomial exactness, the diagonal Pade closed form, the h^(2K) endpoint order,
