@@ -80,3 +80,27 @@ def test_mass_action_rhs_on_hand_written_network():
     v = [k[0] * z[0] * z[1], k[1] * z[2], k[2] * z[1] * z[1]]
     f_exp = np.array([-v[0] + v[1], -v[0] - 2 * v[2], v[0] - v[1]])
     np.testing.assert_allclose(prob.rhs(z[None], th)[0], f_exp, rtol=1e-15)
+
+
+def test_observations_on_element_boundaries_use_the_left_element():
+    # Reading of the observation model for times on the mesh: a time on an
+    # element boundary belongs to the element on its left (tau = 1, i.e. its end
+    # state z_iK), t = 0 to the first element's start state z_10.  At a point
+    # that violates continuity the two neighbours disagree, so the choice shows.
+    import dataclasses
+    base = W.small_network(n=3, r=4, N=4, seed=3, M=5, T=2.0)
+    h = base.T / base.N                                   # 0.5, exact in binary
+    times = np.array([0.0, h, 2 * h, 3 * h, base.T])
+    species = np.array([0, 1, 2, 0, 1], dtype=base.obs_s.dtype)
+    y = np.array([0.3, 0.4, 0.5, 0.6, 0.7])
+    sig = np.array([0.1, 0.2, 0.1, 0.3, 0.1])
+    inst = dataclasses.replace(base, obs_t=times, obs_s=species, obs_y=y, obs_sigma=sig)
+    prob = Problem(inst)
+    x, _ = _point(prob, 4)
+    z, _ = prob.split(x)
+    K = prob.K
+    yhat = [z[0, 0, 0], z[0, K, 1], z[1, K, 2], z[2, K, 0], z[3, K, 1]]
+    assert abs(z[0, K, 1] - z[1, 0, 1]) > 1e-3              # the neighbours disagree
+    expected = 0.5 * sum(((yh - yy) / s) ** 2 for yh, yy, s in zip(yhat, y, sig))
+    phi, _ = prob.objective(x)
+    assert abs(phi - expected) <= 1e-13 * max(1.0, expected)
