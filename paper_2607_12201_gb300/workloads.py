@@ -146,9 +146,10 @@ def _observations(times, species, traj, rng, mode):
     """Noisy measurements; returns arrays sorted by (time, species).
 
     ``additive``: y = x + 0.01 eps, sigma = 0.01.  ``multiplicative``:
-    y = x (1 + 0.05 eps), sigma = 0.05 max(|y|, 0.1 max_t |y_s|), i.e. a 5 %
-    error model floored at 10 % of the species' largest measurement so that
-    near-zero readings do not dominate the misfit.
+    y = x (1 + 0.05 eps), sigma = 0.05 max(|y|, 0.1 max_t |y_s|, 1e-6), i.e. a
+    5 % error model floored at 10 % of the species' largest measurement so that
+    near-zero readings do not dominate the misfit (and at 1e-6 for a species
+    that decays to nothing over the horizon).
     """
     t_list, s_list, y_list, sig_list = [], [], [], []
     ys = {}
