@@ -107,3 +107,32 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_0():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check_reference_line(lines[0], 2)
+
+
+def test_clock_sampler_summarises_nvidia_smi_samples(tmp_path):
+    # the median SM clock under load, the maximum clock, and every throttle reason
+    # seen active; malformed and N/A lines are skipped
+    import bench
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    csv = tmp_path / "clocks.csv"
+    csv.write_text(
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+        "0, 2010, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = _Done(), str(csv)
+    out = s.stop()
+    assert out["sm_mhz"] == 2010.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not csv.exists()
+    s2 = bench.ClockSampler(0)
+    assert s2.stop()["reasons"] == ["nvidia-smi unavailable"]
