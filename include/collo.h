@@ -210,8 +210,12 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
                                   const collo_data* data, const collo_mesh* mesh,
                                   const collo_problem_options* opts, collo_problem** out);
 
+/* Wait for the problem's stream, free its device memory (and its stream when
+ * the library created it).  NULL is a no-op. */
 void collo_problem_destroy(collo_problem* prob);
 
+/* Sizes of a created problem (n, r, p, N, K, M, n_x, n_c, the number of
+ * cyclic-reduction levels, device bytes held).  INVALID_ARG on NULL. */
 collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out);
 
 /* The problem's CUDA stream (cudaStream_t), for callers that time or order work. */
@@ -270,6 +274,10 @@ collo_status collo_kkt_factor(collo_problem* prob, const double* sigma, double d
 collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol,
                              int refine_max, double refine_tol, collo_solve_info* info);
 
+/* Defaults: the paper's tolerances (relative KKT error 1e-6, acceptable 1e-4
+ * for 15 iterations; Section "Optimization framework configurations"), 3000
+ * iterations, a 3600 s wall cap, FP64 precision, refinement to 1e-10 in at
+ * most 10 sweeps, no log.  NULL is a no-op. */
 void collo_ipm_options_default(collo_ipm_options* opts);
 
 /* Solve the estimation problem from theta0 [p] with the filter line-search
@@ -316,6 +324,10 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
  * then COLLO_OK with the result (theta copied if result->theta is set).
  * Submitted problems must stay alive until polled as done. */
 typedef struct collo_server collo_server;
+/* create: max_slots >= 1 slots on `device`, opts as for collo_ipm_solve (NULL:
+ * defaults); INVALID_ARG / DEVICE / OOM.  submit: theta0 [p] is copied;
+ * INVALID_ARG on NULL arguments.  step: INVALID_ARG on NULL, DEVICE on a CUDA
+ * error; n_active / n_waiting report the slots in use and the queue. */
 collo_status collo_server_create(int max_slots, int64_t budget_bytes,
                                  const collo_ipm_options* opts, int device, collo_server** out);
 collo_status collo_server_submit(collo_server* server, collo_problem* prob, const double* theta0,
