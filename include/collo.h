@@ -326,8 +326,10 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
 typedef struct collo_server collo_server;
 /* create: max_slots >= 1 slots on `device`, opts as for collo_ipm_solve (NULL:
  * defaults); INVALID_ARG / DEVICE / OOM.  submit: theta0 [p] is copied;
- * INVALID_ARG on NULL arguments.  step: INVALID_ARG on NULL, DEVICE on a CUDA
- * error; n_active / n_waiting report the slots in use and the queue. */
+ * INVALID_ARG on NULL arguments.  step: INVALID_ARG on NULL; OOM when an
+ * admitted problem's storage cannot be allocated; DEVICE on a CUDA error (a
+ * solve's own outcome goes to its result, not to the step's status);
+ * n_active / n_waiting report the slots in use and the queue. */
 collo_status collo_server_create(int max_slots, int64_t budget_bytes,
                                  const collo_ipm_options* opts, int device, collo_server** out);
 collo_status collo_server_submit(collo_server* server, collo_problem* prob, const double* theta0,
