@@ -137,3 +137,16 @@ def test_ipm_solve_raises_when_the_call_fails_before_a_result(lib):
     with pytest.raises(lib.ColloError) as e:
         pr.ipm_solve(theta0=np.zeros(2), want_x=False)
     assert e.value.status == lib.ERR_INVALID_ARG
+
+
+def test_batch_and_server_check_start_lengths(lib):
+    pr = _unattached_problem(lib)
+    with pytest.raises(ValueError, match=r"theta0s\[1\]"):
+        lib.batch_solve([pr, pr], theta0s=[np.zeros(2), np.zeros(5)])
+    sv = object.__new__(lib.Server)
+    sv.h, sv._keep = C.c_void_p(), {}
+    with pytest.raises(ValueError, match="theta0"):
+        sv.submit(pr, theta0=np.zeros(1))
+    with pytest.raises(lib.ColloError) as e:       # right length: the NULL server is refused
+        sv.submit(pr, theta0=np.zeros(2))
+    assert e.value.status == lib.ERR_INVALID_ARG
