@@ -180,7 +180,8 @@ def _ptr(a):
     if isinstance(a, int):
         return a
     if isinstance(a, np.ndarray):
-        assert a.flags.c_contiguous
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays passed to the library must be C-contiguous")
         return a.ctypes.data
     return int(a.data_ptr())
 
