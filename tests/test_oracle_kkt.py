@@ -23,7 +23,9 @@ def _kkt(prob, seed, delta_w, delta_c):
 CASES = [(lambda: W.small_network(n=2, r=3, N=2, seed=21), 0.0, 1e-8),
          (lambda: W.small_network(n=3, r=4, N=3, seed=22), 1e-3, 1e-6),
          (lambda: W.small_network(n=3, r=5, N=4, seed=23), 0.0, 1e-8),
-         (lambda: W.linear_cascade(N=4), 0.0, 1e-8)]
+         (lambda: W.linear_cascade(N=4), 0.0, 1e-8),
+         (lambda: W.small_network(n=2, r=3, N=12, seed=24), 1e-4, 1e-8),
+         (lambda: W.linear_cascade(N=16), 0.0, 1e-8)]
 
 
 @pytest.mark.parametrize("scheme", ["radau3", "gauss4"])
