@@ -104,3 +104,39 @@ def test_observations_on_element_boundaries_use_the_left_element():
     expected = 0.5 * sum(((yh - yy) / s) ** 2 for yh, yy, s in zip(yhat, y, sig))
     phi, _ = prob.objective(x)
     assert abs(phi - expected) <= 1e-13 * max(1.0, expected)
+
+
+@pytest.mark.parametrize("make", [lambda: W.small_network(n=3, r=5, N=3, seed=11),
+                                  lambda: W.small_network(n=4, r=6, N=2, seed=12),
+                                  lambda: W.linear_cascade(N=3)])
+def test_derivatives_by_fourth_order_differences(make):
+    # five-point stencil (f(x-2e) - 8 f(x-e) + 8 f(x+e) - f(x+2e)) / (12 e), truncation
+    # error O(e^4): the constraints are at most quadratic in the states and smooth in
+    # theta, so with e = 1e-3 the differences are accurate to ~1e-11 and pin every
+    # derivative entry to 1e-9 relative -- a missing term far below the size of the
+    # largest entries fails here
+    inst = make()
+    prob = Problem(inst)
+    x, lam = _point(prob, 3)
+    of = 1.3
+    ev = prob.evaluate(x, lam, obj_factor=of)
+    J, Wh, g = ev["J"].toarray(), ev["W"].toarray(), ev["grad"]
+
+    def lag_grad(xx):
+        e = prob.evaluate(xx, lam, obj_factor=of)
+        return e["grad"] + e["J"].T @ lam
+
+    def d5(fun, a, e=1e-3):
+        vals = []
+        for s in (-2, -1, 1, 2):
+            xx = x.copy()
+            xx[a] += s * e
+            vals.append(fun(xx))
+        return (vals[0] - 8 * vals[1] + 8 * vals[2] - vals[3]) / (12 * e)
+
+    Jfd = np.column_stack([d5(prob.constraints, a) for a in range(prob.n_x)])
+    gfd = np.array([of * d5(lambda xx: prob.objective(xx)[0], a) for a in range(prob.n_x)])
+    Wfd = np.column_stack([d5(lag_grad, a) for a in range(prob.n_x)])
+    assert np.max(np.abs(J - Jfd)) <= 1e-9 * max(1.0, np.max(np.abs(J)))
+    assert np.max(np.abs(g - gfd)) <= 1e-9 * max(1.0, np.max(np.abs(g)))
+    assert np.max(np.abs(Wh - Wfd)) <= 1e-9 * max(1.0, np.max(np.abs(Wh)))
