@@ -106,16 +106,20 @@ def test_observations_on_element_boundaries_use_the_left_element():
     assert abs(phi - expected) <= 1e-13 * max(1.0, expected)
 
 
+@pytest.mark.parametrize("scheme", ["radau3", "gauss4"])
 @pytest.mark.parametrize("make", [lambda: W.small_network(n=3, r=5, N=3, seed=11),
                                   lambda: W.small_network(n=4, r=6, N=2, seed=12),
                                   lambda: W.linear_cascade(N=3)])
-def test_derivatives_by_fourth_order_differences(make):
+def test_derivatives_by_fourth_order_differences(make, scheme):
     # five-point stencil (f(x-2e) - 8 f(x-e) + 8 f(x+e) - f(x+2e)) / (12 e), truncation
     # error O(e^4): the constraints are at most quadratic in the states and smooth in
     # theta, so with e = 1e-3 the differences are accurate to ~1e-11 and pin every
     # derivative entry to 1e-9 relative -- a missing term far below the size of the
     # largest entries fails here
+    import dataclasses
     inst = make()
+    if scheme == "gauss4":
+        inst = dataclasses.replace(inst, K=4, scheme="gauss")
     prob = Problem(inst)
     x, lam = _point(prob, 3)
     of = 1.3
