@@ -150,3 +150,77 @@ def test_batch_and_server_check_start_lengths(lib):
     with pytest.raises(lib.ColloError) as e:       # right length: the NULL server is refused
         sv.submit(pr, theta0=np.zeros(2))
     assert e.value.status == lib.ERR_INVALID_ARG
+
+
+class _FakeLib:
+    """Stands in for the loaded library on the CPU: answers the binding's calls
+    the way the C functions do (statuses, outputs written through the result
+    pointers) so that the binding's success paths run without a device.  Calls
+    it does not define go to the real library (host-only ones such as the
+    option defaults)."""
+
+    def __init__(self, real, n_x, n_c, outcome):
+        self.real, self.n_x, self.n_c, self.outcome = real, n_x, n_c, outcome
+        self.tickets = 0
+
+    def __getattr__(self, name):
+        return getattr(self.real, name)
+
+    def collo_eval(self, h, x, lam, of, eo):
+        return 0
+
+    def collo_kkt_factor(self, h, sig, dw, dc, prec, inr):
+        inr._obj.n_pos, inr._obj.n_neg, inr._obj.n_zero = self.n_x, self.n_c, 0
+        return 0
+
+    def collo_kkt_solve(self, h, rhs, sol, rmax, rtol, info):
+        C.memmove(sol, rhs, 8 * (self.n_x + self.n_c))
+        info._obj.refinement_sweeps = 2
+        return 0
+
+    def collo_ipm_solve(self, h, th0, opts, res):
+        res._obj.status, res._obj.iterations = self.outcome, 7
+        return self.outcome
+
+    def collo_initial_states(self, h, th, x, fails):
+        fails._obj.value = 0
+        return 0
+
+    def collo_batch_solve(self, handles, n, thp, opts, res):
+        for i in range(n):
+            res[i].status, res[i].iterations = self.outcome, 5
+        return 0
+
+    def collo_server_submit(self, sv, prob, th, ticket):
+        self.tickets += 1
+        ticket._obj.value = self.tickets
+        return 0
+
+    def collo_server_poll(self, sv, ticket, res):
+        res._obj.status = self.outcome
+        return 0
+
+
+@pytest.mark.parametrize("outcome", [0, 1, -7, -5])
+def test_binding_success_paths(lib, monkeypatch, outcome):
+    pr = _unattached_problem(lib)
+    monkeypatch.setattr(lib, "lib", _FakeLib(lib.lib, pr.n_x, pr.n_c, outcome))
+    pr.eval(np.zeros(10), np.zeros(8), outputs=False)
+    ev = pr.eval(np.zeros(10))
+    assert ev["phi"] == 0.0 and ev["c"].shape == (8,) and ev["jac_theta"].shape == (1, 3, 1, 2)
+    assert pr.kkt_factor(np.zeros(10), 0.0, 1e-8) == (10, 8, 0)
+    rhs = np.arange(18.0)
+    sol, info = pr.kkt_solve(rhs)
+    assert np.array_equal(sol, rhs) and info["sweeps"] == 2
+    out = np.empty(18)
+    assert pr.kkt_solve(rhs, out=out)[0] is out and np.array_equal(out, rhs)
+    r = pr.ipm_solve(theta0=[0.1, 0.2], want_x=True)      # solver outcomes come back as results
+    assert r["status"] == outcome and r["iterations"] == 7 and r["x"].shape == (10,)
+    x, fails = pr.initial_states([0.1, 0.2])
+    assert x.shape == (10,) and fails == 0
+    res = lib.batch_solve([pr, pr], theta0s=[[0.0, 0.0], np.ones(2)])
+    assert [q["status"] for q in res] == [outcome, outcome]
+    sv = object.__new__(lib.Server)
+    sv.h, sv._keep = C.c_void_p(), {}
+    t = sv.submit(pr, theta0=np.zeros(2))
+    assert sv.poll(t)["status"] == outcome
