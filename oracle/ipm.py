@@ -163,6 +163,70 @@ def barrier_value(prob, phi, x, mu):
     return phi - mu * np.sum(np.log(th - inst.theta_lo)) - mu * np.sum(np.log(inst.theta_hi - th))
 
 
+def alpha_min_of(theta_k, gphi, theta_min, opt: Options):
+    """Smallest trial step before the line search gives up (Waechter & Biegler
+    2006, Eq. (23)), from the current infeasibility theta_k = ||c||_1 and the
+    barrier directional derivative gphi."""
+    if gphi < 0:
+        if theta_k <= theta_min:
+            return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta_k / (-gphi),
+                                         opt.delta * theta_k ** opt.s_theta / (-gphi) ** opt.s_phi)
+        return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta_k / (-gphi))
+    return opt.gamma_alpha * opt.gamma_theta
+
+
+def trial_acceptable(theta_t, phib_t, alpha, theta_k, phi_k, gphi, theta_min, theta_max, filt,
+                     opt: Options):
+    """Acceptance of one trial point (theta_t = ||c(x_t)||_1, phib_t its barrier
+    value) at step alpha: (accepted, ftype).
+
+    Waechter & Biegler (2006): the trial must lie below theta_max and outside
+    every filter entry's forbidden region {theta >= theta_f and phi >= phi_f};
+    then, if the switching condition (Eq. (19)) holds at an almost feasible
+    iterate (theta_k <= theta_min), the Armijo condition on the barrier function
+    (Eq. (20); an "f-type" step), else sufficient decrease of either measure
+    (Eq. (18))."""
+    if not (np.isfinite(theta_t) and np.isfinite(phib_t)):
+        return False, False
+    if not theta_t < theta_max:
+        return False, False
+    for (tf, pf) in filt:
+        if theta_t >= tf and phib_t >= pf:
+            return False, False
+    sw = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * theta_k ** opt.s_theta
+    if theta_k <= theta_min and sw:
+        return bool(phib_t <= phi_k + opt.eta_phi * alpha * gphi), True
+    return bool(theta_t <= (1.0 - opt.gamma_theta) * theta_k
+                or phib_t <= phi_k - opt.gamma_phi * theta_k), False
+
+
+def backtrack(trial, alpha_max, theta_k, phi_k, gphi, theta_min, theta_max, filt, opt: Options):
+    """Backtracking filter line search (Waechter & Biegler 2006, Algorithm A,
+    steps A-5.1 to A-5.5, without second-order correction): trial steps
+    alpha_max, alpha_max / 2, ... down to alpha_min (Eq. (23)); trial(alpha)
+    returns (theta_t, phib_t).  Returns (accepted, alpha, ftype, trials); when
+    no trial is accepted alpha is the first step below alpha_min."""
+    a_min = alpha_min_of(theta_k, gphi, theta_min, opt)
+    alpha = alpha_max
+    trials = 0
+    while alpha >= a_min:
+        trials += 1
+        theta_t, phib_t = trial(alpha)
+        ok, ftype = trial_acceptable(theta_t, phib_t, alpha, theta_k, phi_k, gphi, theta_min,
+                                     theta_max, filt, opt)
+        if ok:
+            return True, alpha, ftype, trials
+        alpha *= 0.5
+    return False, alpha, False, trials
+
+
+def reset_bound_duals(z, s, mu, kappa_sigma):
+    """Bound-multiplier safeguard after a step (Waechter & Biegler 2006,
+    Eq. (16)): z is kept within [mu / (kappa_sigma s), kappa_sigma mu / s] for
+    the slack s of its bound."""
+    return np.maximum(np.minimum(z, kappa_sigma * mu / s), mu / (kappa_sigma * s))
+
+
 def solve(inst, theta0=None, opt: Options | None = None, verbose: bool = False,
           on_iter=None) -> Result:
     opt = opt or Options()
@@ -236,45 +300,17 @@ def solve(inst, theta0=None, opt: Options | None = None, verbose: bool = False,
         theta_k = float(np.sum(np.abs(ev["c"])))
         phi_k = barrier_value(prob, ev["phi"], x, mu)
         gphi = float(ev["grad"] @ dx) + float(np.sum((-mu / sl + mu / su) * dth))
-        if gphi < 0:
-            if theta_k <= theta_min:
-                alpha_min = opt.gamma_alpha * min(
-                    opt.gamma_theta, opt.gamma_phi * theta_k / (-gphi),
-                    opt.delta * theta_k ** opt.s_theta / (-gphi) ** opt.s_phi)
-            else:
-                alpha_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta_k / (-gphi))
-        else:
-            alpha_min = opt.gamma_alpha * opt.gamma_theta
-        alpha = alpha_max
-        accepted = False
-        ftype = False
-        trials = 0
-        while alpha >= alpha_min:
-            trials += 1
+
+        def trial(alpha):
             xt = x + alpha * dx
             phit, _ = prob.objective(xt)
-            ct = prob.constraints(xt)
-            thetat = float(np.sum(np.abs(ct)))
-            if np.isfinite(phit) and np.isfinite(thetat):
-                phibt = barrier_value(prob, phit, xt, mu)
-                ok = np.isfinite(phibt) and thetat < theta_max
-                if ok:
-                    for (tf, pf) in filt:
-                        if thetat >= tf and phibt >= pf:
-                            ok = False
-                            break
-                if ok:
-                    sw = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * theta_k ** opt.s_theta
-                    if theta_k <= theta_min and sw:
-                        ftype = True
-                        accepted = phibt <= phi_k + opt.eta_phi * alpha * gphi
-                    else:
-                        ftype = False
-                        accepted = (thetat <= (1.0 - opt.gamma_theta) * theta_k
-                                    or phibt <= phi_k - opt.gamma_phi * theta_k)
-                    if accepted:
-                        break
-            alpha *= 0.5
+            thetat = float(np.sum(np.abs(prob.constraints(xt))))
+            if not (np.isfinite(phit) and np.isfinite(thetat)):
+                return math.nan, math.nan
+            return thetat, barrier_value(prob, phit, xt, mu)
+
+        accepted, alpha, ftype, trials = backtrack(trial, alpha_max, theta_k, phi_k, gphi,
+                                                   theta_min, theta_max, filt, opt)
         if not accepted:
             status = ERR_LINESEARCH
             break
@@ -286,8 +322,8 @@ def solve(inst, theta0=None, opt: Options | None = None, verbose: bool = False,
         zu = zu + alpha_z * dzu
         th = x[prob.nz:]
         sl, su = th - inst.theta_lo, inst.theta_hi - th
-        zl = np.maximum(np.minimum(zl, opt.kappa_sigma * mu / sl), mu / (opt.kappa_sigma * sl))
-        zu = np.maximum(np.minimum(zu, opt.kappa_sigma * mu / su), mu / (opt.kappa_sigma * su))
+        zl = reset_bound_duals(zl, sl, mu, opt.kappa_sigma)
+        zu = reset_bound_duals(zu, su, mu, opt.kappa_sigma)
         rec = dict(it=it, phi=ev["phi"], inf_pr=float(np.max(np.abs(ev["c"]))), err=err,
                    mu=mu, delta_w=delta_w, alpha=alpha, alpha_z=alpha_z, trials=trials)
         history.append(rec)

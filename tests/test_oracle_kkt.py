@@ -70,3 +70,27 @@ def test_inertia_of_D_two_by_two_blocks():
     assert kkt.inertia_of_D(d) == (2, 2, 0)
     d2 = np.array([[2.0, 1.0], [1.0, 2.0]])
     assert kkt.inertia_of_D(d2) == (2, 0, 0)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.random_network(4, 8, n_obs=2, M=20, T=5.0, N=33, seed=19),
+    lambda: W.random_network(12, 24, n_obs=4, M=20, T=5.0, N=10, seed=43, theta0_spread=0.1),
+    lambda: W.linear_cascade(N=50)], ids=["n4_N33", "n12_N10", "cascade_N50"])
+def test_bunch_kaufman_inertia_equals_resolved_eigenvalue_count(make):
+    """The oracle's inertia (Bunch-Kaufman pivots, Sylvester's law; whole matrix
+    or per Schur block, Haynsworth additivity) is the eigenvalue count of the
+    whole KKT matrix wherever that count is resolved: every |eigenvalue| above
+    1000 n eps ||K||_2, so no rounding error of the eigensolver can move one
+    across zero.  The GPU tests compare against the same eigenvalue counts."""
+    prob = Problem(make())
+    resolved = 0
+    for seed, dw in ((3, 0.0), (4, 1e-2), (5, 0.0)):
+        K = _kkt(prob, seed, dw, 1e-8)
+        ev = np.linalg.eigvalsh(K.toarray())
+        if np.min(np.abs(ev)) <= 1000.0 * K.shape[0] * np.finfo(float).eps * np.max(np.abs(ev)):
+            continue
+        resolved += 1
+        want = (int(np.sum(ev > 0)), int(np.sum(ev < 0)), 0)
+        for mode in ["dense", "block"]:
+            assert tuple(kkt.factor(K, prob, mode).inertia) == want
+    assert resolved >= 2
