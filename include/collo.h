@@ -221,6 +221,25 @@ collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out);
 /* The problem's CUDA stream (cudaStream_t), for callers that time or order work. */
 void* collo_problem_stream(const collo_problem* prob);
 
+/* Device bytes the problem holds while an interior-point solve in `precision`
+ * (COLLO_PRECISION_*) runs on it: its own arrays plus the factorization
+ * stores (FP64 and its spare; with MIXED also the FP32 pair) that the solve
+ * allocates, counted exactly as they would be allocated.  The server admits
+ * by this figure.  INVALID_ARG on NULL or a bad precision. */
+collo_status collo_problem_solve_bytes(const collo_problem* prob, int precision, int64_t* bytes);
+
+/* Grid-barrier waits of this problem's own calls (collo_kkt_factor,
+ * collo_kkt_solve, collo_ipm_solve; not batches or servers).  The persistent
+ * kernels separate the phases of the elimination tree by grid barriers whose
+ * waits are bounded: after max_polls polls (0: the default, about 1-2 s) a
+ * wait gives up and the call returns COLLO_ERR_TIMEOUT, the paper's status
+ * "T", with the device still usable.  unreachable != 0 is a failure-test
+ * switch: every barrier then waits for one arrival more than the grid makes,
+ * so every wait runs out (results of such a call are meaningless); set it back
+ * to 0 for normal use.  INVALID_ARG on NULL or max_polls < 0. */
+collo_status collo_problem_set_wait_limit(collo_problem* prob, long long max_polls,
+                                          int unreachable);
+
 /* Evaluate objective, constraints, constraint Jacobian and Lagrangian Hessian
  * at (x, lambda) on every (element, node) pair (the paper's SIMD evaluation of
  * Eq. 3 and its first and second derivatives, Introduction and Section
@@ -230,16 +249,23 @@ void* collo_problem_stream(const collo_problem* prob);
 collo_status collo_eval(collo_problem* prob, const double* x, const double* lambda,
                         double obj_factor, collo_eval_out* out);
 
-/* collo_eval for callers that cannot allocate device memory while they run
- * (inside CUDA graph capture, real-time loops that allocate everything ahead
- * of time, processes whose device allocator belongs to another runtime).  The
- * paper has no counterpart; it computes exactly what collo_eval computes, and
- * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+/* collo_eval for callers that cannot allocate device memory while they run:
+ * real-time loops that allocate everything before they start, so that no
+ * step can fail or stall on an allocation, and processes whose device memory
+ * is owned by another runtime or pool.  The paper has no counterpart.  It
+ * evaluates what collo_eval evaluates and allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library call.
  * x [n_x] and lambda [n_c] (lambda may be NULL) and every pointer of *out
  * (all must be set; hess_thth may be NULL only when p = 0) are DEVICE
- * pointers of the problem's GPU, in the collo_eval layouts.  The kernels are
- * queued on `stream` (a cudaStream_t; NULL: the problem's stream) and the
- * call returns without waiting; *out is valid once the stream reaches it.
+ * pointers of the problem's GPU, in the collo_eval layouts; a host pointer
+ * (pinned or pageable) or memory of another GPU is refused with
+ * COLLO_ERR_INVALID_ARG (checked by cudaPointerGetAttributes, which allocates
+ * nothing).  The kernels are queued on `stream` (a cudaStream_t; NULL: the
+ * problem's stream) and the call returns without waiting; *out is valid once
+ * the stream reaches it.  Because it does not wait, it cannot report
+ * non-finite values as collo_eval does (COLLO_ERR_NUMERIC): check *out->phi
+ * and the constraint values after synchronising.  The caller's current
+ * device is restored before the call returns.
  * Its scratch (per-element partial sums, N (4 + p) + 8 doubles) is a fixed
  * 4 MiB device array of the library (2^19 doubles), held by every GPU that
  * loads the library until the process exits; larger problems are rejected
@@ -247,9 +273,8 @@ collo_status collo_eval(collo_problem* prob, const double* x, const double* lamb
  * overwrites all of it), but every call shares it: calls whose kernels
  * overlap on the GPU race, so issue them on one stream or order them.  The
  * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * The problem's derivative buffers are not touched, so it does not replace
- * collo_eval before collo_kkt_factor. */
+ * (cudaGetSymbolAddress) once.  The problem's derivative buffers are not
+ * touched, so it does not replace collo_eval before collo_kkt_factor. */
 collo_status collo_eval_noalloc(collo_problem* prob, const double* x, const double* lambda,
                                 double obj_factor, const collo_eval_out* out, void* stream);
 
@@ -315,11 +340,17 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
                                     int precision, int reps, double* ms_per_launch);
 
 /* Continuous-batching server.  Problems are submitted at any time; each
- * collo_server_step admits waiting problems into free slots while the device
- * memory held by admitted problems stays within budget_bytes (0: no limit),
- * initialises them, advances every admitted problem by one Newton step in
- * batched launches, and retires finished ones.  Their state (x, lambda, bound
- * duals, barrier parameter, filter) stays on the device between steps.
+ * collo_server_step admits waiting problems, in submission order, into free
+ * slots while the device memory held by admitted problems stays within
+ * budget_bytes (0: no limit), initialises them, advances every admitted
+ * problem by one Newton step in batched launches, and retires finished ones.
+ * A problem's footprint is collo_problem_solve_bytes: its factorization
+ * stores are allocated when it is admitted and freed (stream-ordered) when it
+ * retires, so a retired problem is left unfactored; a problem larger than the
+ * whole budget is not run and its result has status COLLO_ERR_OOM.  Their
+ * state (x, lambda, bound duals, barrier parameter, filter) stays on the
+ * device between steps.  A problem may be submitted again once its previous
+ * ticket is done.
  * collo_server_poll returns COLLO_PENDING until the ticket's solve ended,
  * then COLLO_OK with the result (theta copied if result->theta is set).
  * Submitted problems must stay alive until polled as done. */
@@ -343,6 +374,9 @@ collo_status collo_server_poll(collo_server* server, long long ticket, collo_res
 collo_status collo_server_set_admission(collo_server* server, int min_free_slots);
 /* The CUDA stream (cudaStream_t) all of the server's work is queued on. */
 void* collo_server_stream(collo_server* server);
+/* Device bytes held by the admitted problems now and the most held at once
+ * since the server was created (either pointer may be NULL). */
+collo_status collo_server_memory(collo_server* server, int64_t* active_bytes, int64_t* peak_bytes);
 
 /* Measurement hook: with the environment variable COLLO_PROFILE=1 set before
  * the first solve, the IPM driver synchronises its stream at each phase

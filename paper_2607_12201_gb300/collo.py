@@ -106,6 +106,10 @@ def _load():
     lib.collo_problem_sizes.restype = C.c_int
     lib.collo_problem_stream.argtypes = [P]
     lib.collo_problem_stream.restype = C.c_void_p
+    lib.collo_problem_solve_bytes.argtypes = [P, C.c_int, C.POINTER(C.c_int64)]
+    lib.collo_problem_solve_bytes.restype = C.c_int
+    lib.collo_problem_set_wait_limit.argtypes = [P, C.c_longlong, C.c_int]
+    lib.collo_problem_set_wait_limit.restype = C.c_int
     lib.collo_eval.argtypes = [P, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(EvalOut)]
     lib.collo_eval.restype = C.c_int
     lib.collo_kkt_factor.argtypes = [P, C.c_void_p, C.c_double, C.c_double, C.c_int,
@@ -147,6 +151,8 @@ def _load():
     lib.collo_phase_profile.restype = C.c_int
     lib.collo_server_stream.argtypes = [P]
     lib.collo_server_stream.restype = C.c_void_p
+    lib.collo_server_memory.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.collo_server_memory.restype = C.c_int
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
     lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -265,6 +271,23 @@ class Problem:
     @property
     def stream(self) -> int:
         return lib.collo_problem_stream(self.h)
+
+    def device_bytes(self) -> int:
+        """Device bytes the problem holds now (collo_problem_sizes)."""
+        s = Sizes()
+        _check(lib.collo_problem_sizes(self.h, C.byref(s)))
+        return int(s.device_bytes)
+
+    def solve_bytes(self, precision: int = FP64) -> int:
+        """collo_problem_solve_bytes: device bytes held while a solve runs."""
+        b = C.c_int64()
+        _check(lib.collo_problem_solve_bytes(self.h, int(precision), C.byref(b)))
+        return int(b.value)
+
+    def set_wait_limit(self, max_polls: int = 0, unreachable: bool = False):
+        """collo_problem_set_wait_limit: bound of the grid-barrier waits (0: default)
+        and the failure-test switch that makes every barrier unreachable."""
+        _check(lib.collo_problem_set_wait_limit(self.h, int(max_polls), int(bool(unreachable))))
 
     # --- evaluation ------------------------------------------------------------
     def eval(self, x, lam=None, obj_factor: float = 1.0, outputs: bool = True):
@@ -436,6 +459,12 @@ class Server:
     @property
     def stream(self) -> int:
         return int(lib.collo_server_stream(self.h) or 0)
+
+    def memory(self):
+        """(bytes held by admitted problems now, most held at once so far)."""
+        a, pk = C.c_int64(), C.c_int64()
+        _check(lib.collo_server_memory(self.h, C.byref(a), C.byref(pk)))
+        return int(a.value), int(pk.value)
 
     def poll(self, ticket: int):
         problem, _ = self._keep[ticket]

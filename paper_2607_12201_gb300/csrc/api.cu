@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <set>
+#include <type_traits>
 
 #include "problem.cuh"
 
@@ -41,41 +42,95 @@ static void radau_tables(double tau[NP], double D[NP][NP]) {
   }
 }
 
+// Every device array of a factorization store, in allocation order:
+// fn(pointer member, element count).  Used both to allocate a store and to
+// count its bytes before it exists (admission by memory budget).
+template <typename T, class Fn>
+static void factor_layout(const DevProb& P, int n_slabs, DevFactor<T>& F, Fn&& fn) {
+  const size_t N = P.N, n = P.n, p = P.p;
+  fn(F.Lel, N * 6 * n * P.ext);
+  fn(F.Del, N * 3 * n * 3);
+  fn(F.Aif, N * 4 * n * n);
+  fn(F.Cpl, N * n * n);
+  fn(F.Bif, N * 2 * n * p);
+  fn(F.Lb, N * 2 * n * P.bext);
+  fn(F.Db, N * n * 3);
+  fn(F.Scon, 2 * N * p * p);
+  fn(F.inert, 2 * N * 3);
+  fn(F.Vint, N * 6 * n);
+  fn(F.Rif, N * 2 * n);
+  fn(F.Vb, N * 2 * n);
+  fn(F.Rth, 2 * N * p);
+  fn(F.chunkS, (size_t)CHUNKS * p * p);
+  fn(F.chunkR, (size_t)CHUNKS * p);
+  fn(F.gbar, (size_t)1);
+  const size_t w = factor_work_elems<T>(P, n_slabs);
+  if (w) fn(F.work, w);
+}
+
+template <typename T>
+static int64_t factor_store_bytes(const collo_problem* pr) {
+  DevFactor<T> F{};
+  size_t b = 0;
+  factor_layout<T>(pr->P, pr->n_slabs, F, [&](auto*& ptr, size_t cnt) {
+    using U = std::remove_reference_t<decltype(*ptr)>;
+    b += DevArena::bytes_of<U>(cnt);
+  });
+  return (int64_t)b;
+}
+
 template <typename T>
 static collo_status alloc_factor(collo_problem* pr, FactorStore<T>& fs) {
   if (fs.allocated) return COLLO_OK;
-  const DevProb& P = pr->P;
-  const size_t N = P.N, n = P.n, p = P.p;
-  DevArena& A = pr->arena;
   DevFactor<T>& F = fs.F;
-  F.Lel = A.alloc<T>(N * 6 * n * P.ext);
-  F.Del = A.alloc<T>(N * 3 * n * 3);
-  F.Aif = A.alloc<T>(N * 4 * n * n);
-  F.Cpl = A.alloc<T>(N * n * n);
-  F.Bif = A.alloc<T>(N * 2 * n * p);
-  F.Lb = A.alloc<T>(N * 2 * n * P.bext);
-  F.Db = A.alloc<T>(N * n * 3);
-  F.Scon = A.alloc<double>(2 * N * p * p);
-  F.inert = A.alloc<int>(2 * N * 3);
-  F.Vint = A.alloc<T>(N * 6 * n);
-  F.Rif = A.alloc<T>(N * 2 * n);
-  F.Vb = A.alloc<T>(N * 2 * n);
-  F.Rth = A.alloc<double>(2 * N * p);
-  F.chunkS = A.alloc<double>((size_t)CHUNKS * p * p);
-  F.chunkR = A.alloc<double>((size_t)CHUNKS * p);
-  F.gbar = A.alloc<GridBar>(1);
-  if (F.gbar) cudaMemset(F.gbar, 0, sizeof(GridBar));
-  F.persistent = pr->launch_mode == 0 ? 1 : 0;
-  F.n_slabs = pr->n_slabs;
-  size_t w = factor_work_elems<T>(P, pr->n_slabs);
-  F.work = w ? A.alloc<T>(w) : nullptr;
-  if (!F.Lel || !F.Del || !F.Aif || !F.Cpl || !F.Bif || !F.Lb || !F.Db || !F.Scon || !F.inert ||
-      !F.Vint || !F.Rif || !F.Vb || !F.Rth || !F.chunkS || !F.chunkR || (w && !F.work)) {
+  F = DevFactor<T>{};
+  fs.mem.release(nullptr);
+  fs.mem.stream = pr->stream;
+  bool ok = true;
+  factor_layout<T>(pr->P, pr->n_slabs, F, [&](auto*& ptr, size_t cnt) {
+    using U = std::remove_reference_t<decltype(*ptr)>;
+    ptr = fs.mem.template alloc<U>(cnt);
+    ok = ok && ptr != nullptr;
+  });
+  if (!ok) {
+    fs.mem.release(nullptr);
+    F = DevFactor<T>{};
     set_error("device allocation failed for the factorization storage");
     return COLLO_ERR_OOM;
   }
+  if (cudaMemsetAsync(F.gbar, 0, sizeof(GridBar), pr->stream) != cudaSuccess ||
+      cudaStreamSynchronize(pr->stream) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("initialising the factorization storage failed");
+    return COLLO_ERR_DEVICE;
+  }
+  F.persistent = pr->launch_mode == 0 ? 1 : 0;
+  F.n_slabs = pr->n_slabs;
   fs.allocated = true;
   return COLLO_OK;
+}
+
+template <typename T>
+static void free_factor(FactorStore<T>& fs, cudaStream_t st) {
+  fs.mem.release(st);
+  fs.F = DevFactor<T>{};
+  fs.allocated = false;
+}
+
+// Arrays of the second line-search trial and the spare Schur block (allocated
+// once, with the first spare store): fn(pointer, count).
+template <class Fn>
+static void spare_eval_layout(collo_problem* pr, Fn&& fn) {
+  const size_t p = pr->P.p;
+  fn(pr->c_spare, (size_t)pr->n_c);
+  fn(pr->part_spare, (size_t)pr->P.N * 4);
+  fn(pr->red_spare, (size_t)8);
+  DevSchur& S = pr->S_spare;
+  fn(S.S, schur_doubles((int)p));
+  fn(S.Sd, p);
+  fn(S.xth, p);
+  fn(S.inertia, (size_t)3);
+  fn(S.diag, p);
 }
 
 collo_status ensure_factor_storage(collo_problem* pr, int precision) {
@@ -86,27 +141,54 @@ collo_status ensure_spare_storage(collo_problem* pr, int precision) {
   collo_status s = precision == COLLO_PRECISION_MIXED ? alloc_factor(pr, pr->f32_spare)
                                                        : alloc_factor(pr, pr->f64_spare);
   if (s != COLLO_OK || pr->spare_S) return s;
-  const size_t p = pr->P.p;
   DevArena& A = pr->arena;
-  pr->c_spare = A.alloc<double>(pr->n_c);
-  pr->part_spare = A.alloc<double>((size_t)pr->P.N * 4);
-  pr->red_spare = A.alloc<double>(8);
-  if (!pr->c_spare || !pr->part_spare || !pr->red_spare) {
-    set_error("device allocation failed for the spare evaluation storage");
-    return COLLO_ERR_OOM;
-  }
-  DevSchur& S = pr->S_spare;
-  S.S = A.alloc<double>(p * p);
-  S.Sd = A.alloc<double>(p);
-  S.xth = A.alloc<double>(p);
-  S.inertia = A.alloc<long long>(3);
-  S.diag = A.alloc<double>(p);
-  if (!S.S || !S.Sd || !S.xth || !S.inertia || !S.diag) {
-    set_error("device allocation failed for the spare Schur storage");
+  bool ok = true;
+  spare_eval_layout(pr, [&](auto*& ptr, size_t cnt) {
+    using U = std::remove_reference_t<decltype(*ptr)>;
+    ptr = A.template alloc<U>(cnt);
+    ok = ok && ptr != nullptr;
+  });
+  if (!ok) {
+    set_error("device allocation failed for the spare evaluation / Schur storage");
     return COLLO_ERR_OOM;
   }
   pr->spare_S = true;
   return COLLO_OK;
+}
+
+int64_t problem_held_bytes(const collo_problem* pr) {
+  return (int64_t)(pr->arena.bytes + pr->f64.mem.bytes + pr->f32.mem.bytes +
+                   pr->f64_spare.mem.bytes + pr->f32_spare.mem.bytes);
+}
+
+int64_t problem_solve_bytes(const collo_problem* pr, int precision) {
+  const bool mixed = precision == COLLO_PRECISION_MIXED;
+  int64_t b = (int64_t)pr->arena.bytes;
+  if (!pr->spare_S) {
+    size_t e = 0;
+    // the counting callback reads the sizes only; no pointer is written
+    spare_eval_layout(const_cast<collo_problem*>(pr), [&](auto*& ptr, size_t cnt) {
+      using U = std::remove_reference_t<decltype(*ptr)>;
+      e += DevArena::bytes_of<U>(cnt);
+    });
+    b += (int64_t)e;
+  }
+  const int64_t s64 = factor_store_bytes<double>(pr), s32 = factor_store_bytes<float>(pr);
+  // the FP64 store and its spare always; the FP32 pair for the mixed path
+  b += pr->f64.allocated ? (int64_t)pr->f64.mem.bytes : s64;
+  b += pr->f64_spare.allocated ? (int64_t)pr->f64_spare.mem.bytes : s64;
+  if (mixed || pr->f32.allocated) b += pr->f32.allocated ? (int64_t)pr->f32.mem.bytes : s32;
+  if (mixed || pr->f32_spare.allocated)
+    b += pr->f32_spare.allocated ? (int64_t)pr->f32_spare.mem.bytes : s32;
+  return b;
+}
+
+void release_factor_storage(collo_problem* pr, cudaStream_t st) {
+  free_factor(pr->f64, st);
+  free_factor(pr->f32, st);
+  free_factor(pr->f64_spare, st);
+  free_factor(pr->f32_spare, st);
+  pr->factored = -1;
 }
 
 void swap_spare(collo_problem* pr, int precision) {
@@ -365,7 +447,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   E.red = A.alloc<double>(8);
   E.wtt = A.alloc<double>(p);
   DevSchur& S = pr->S;
-  S.S = A.alloc<double>((size_t)p * p);
+  S.S = A.alloc<double>(schur_doubles(p));
   S.Sd = A.alloc<double>(p);
   S.xth = A.alloc<double>(p);
   S.inertia = A.alloc<long long>(3);
@@ -435,11 +517,20 @@ collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out) {
   out->n = prob->P.n; out->r = prob->P.r; out->p = prob->P.p; out->N = prob->P.N;
   out->K = KC; out->M = prob->P.M; out->n_x = prob->n_x; out->n_c = prob->n_c;
   out->levels = bcr_levels(prob->P.N);
-  out->device_bytes = (int64_t)prob->arena.bytes;
+  out->device_bytes = problem_held_bytes(prob);
   return COLLO_OK;
 }
 
 void* collo_problem_stream(const collo_problem* prob) { return prob ? (void*)prob->stream : nullptr; }
+
+collo_status collo_problem_solve_bytes(const collo_problem* prob, int precision, int64_t* bytes) {
+  if (!prob || !bytes) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  if (precision != COLLO_PRECISION_FP64 && precision != COLLO_PRECISION_MIXED) {
+    set_error("bad precision"); return COLLO_ERR_INVALID_ARG;
+  }
+  *bytes = problem_solve_bytes(prob, precision);
+  return COLLO_OK;
+}
 
 collo_status collo_eval(collo_problem* prob, const double* x, const double* lambda,
                         double obj_factor, collo_eval_out* out) {

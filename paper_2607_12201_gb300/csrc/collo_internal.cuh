@@ -92,7 +92,10 @@ struct GridBar {
   unsigned int count;   // arrivals in the current launch
   unsigned int exits;   // blocks that have left the current launch
   int err;
-  int pad;
+  // arrivals each barrier waits for beyond the grid's own (0; a failure test
+  // sets 1 so that no barrier can complete and every wait runs out)
+  unsigned int extra;
+  long long spin_limit; // polls before a wait gives up (0: GRID_SPIN_LIMIT)
 };
 
 // Factorization storage (T = double or float).
@@ -127,12 +130,18 @@ constexpr int CHUNKS = 64;
 __host__ __device__ inline int n_chunks(int C) { return C < CHUNKS ? (C > 0 ? C : 1) : CHUNKS; }
 
 struct DevSchur {
-  double* S;       // [p][p] assembled, then overwritten by L (unit lower) and D
+  double* S;       // [p][p] assembled, then overwritten by L (unit lower) and D;
+                   // followed by [p] of scratch (schur_doubles), the multiplier
+                   // row of the factorization when it runs in global memory
   double* Sd;      // [p] pivots
   double* xth;     // [p] parameter solution
   long long* inertia;  // [3] total inertia
   double* diag;    // [p] W_thth + sigma_theta + delta_w (assembled by host-side launch)
 };
+
+// Doubles of DevSchur::S: the p x p block and the p-entry multiplier row the
+// factorization uses when the block does not fit in shared memory.
+inline size_t schur_doubles(int p) { return (size_t)p * p + (size_t)p; }
 
 // ---- batched execution ------------------------------------------------------------
 // Everything one instance owns on the device, gathered for batched kernels.

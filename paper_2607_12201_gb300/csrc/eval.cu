@@ -444,9 +444,10 @@ cudaError_t launch_kkt_resid(const DevProb& P, const DevEval& E, const double* s
 }
 
 // ---- evaluation without allocation ------------------------------------------------
-// Callers that cannot allocate device memory while running (code inside a CUDA
-// graph capture, real-time control loops that allocate everything up front,
-// hosts whose allocator is owned by another runtime) use collo_eval_noalloc.
+// Callers that cannot allocate device memory while running (real-time control
+// loops that allocate everything up front so that no call can fail or stall on
+// an allocation, hosts whose device allocator is owned by another runtime or
+// memory pool) use collo_eval_noalloc.
 // Its only scratch, the per-element partial sums of the objective, of the
 // constraint norms and of the parameter-parameter Hessian, lives in this
 // fixed device array instead of problem-owned buffers.  Every GPU that loads
@@ -516,6 +517,29 @@ cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const in
 
 // ---- C ABI: evaluation without allocation -------------------------------------------
 
+namespace {
+// Restores the caller's current device when the call returns.
+struct DeviceRestore {
+  int dev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = -1; }
+  }
+  ~DeviceRestore() {
+    if (dev >= 0) cudaSetDevice(dev);
+  }
+};
+// True when p is device (or managed) memory of device `dev`; a host pointer,
+// pinned or pageable, or memory of another GPU is refused.  Allocates nothing.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+}  // namespace
+
 extern "C" collo_status collo_eval_noalloc(collo_problem* prob, const double* x,
                                            const double* lambda, double obj_factor,
                                            const collo_eval_out* out, void* stream) {
@@ -525,6 +549,21 @@ extern "C" collo_status collo_eval_noalloc(collo_problem* prob, const double* x,
       (prob->P.p > 0 && !out->hess_thth)) {
     set_error("collo_eval_noalloc: x and every output must be device pointers (lambda may be NULL)");
     return COLLO_ERR_INVALID_ARG;
+  }
+  DeviceRestore restore;
+  {
+    const void* ptrs[] = {x, lambda, out->phi, out->c, out->grad, out->jac_z, out->jac_theta,
+                          out->hess_zz, out->hess_ztheta, out->hess_obj, out->hess_thth};
+    const char* names[] = {"x", "lambda", "phi", "c", "grad", "jac_z", "jac_theta", "hess_zz",
+                           "hess_ztheta", "hess_obj", "hess_thth"};
+    for (int k = 0; k < 11; ++k) {
+      if (!ptrs[k]) continue;   // lambda, or hess_thth with p = 0
+      if (!on_device(ptrs[k], prob->device)) {
+        set_error(std::string("collo_eval_noalloc: ") + names[k] +
+                  " is not device memory of the problem's GPU");
+        return COLLO_ERR_INVALID_ARG;
+      }
+    }
   }
   const DevProb& P = prob->P;
   const size_t need = (size_t)P.N * (4 + (size_t)P.p) + 8;

@@ -1009,7 +1009,9 @@ __device__ inline double sum_chunks(const double* __restrict__ part, int G, int 
 
 constexpr int SBS = 256;
 // One block: S = (chunk sums of all contributions) + diag(W_thth + sigma + dw),
-// FP64 LDL^T with 1x1 pivots, total inertia.  sS: dynamic shared [p][p] + [p].
+// FP64 LDL^T with 1x1 pivots, total inertia.  sS: [p][p] followed by a
+// p-entry multiplier row, in dynamic shared memory, or S.S itself when that
+// does not fit (S.S holds p p + p doubles for this).
 __device__ void schur_block(const DevProb& P, const int* __restrict__ inert,
                             const double* __restrict__ chunkS, const double* __restrict__ wtt,
                             const double* __restrict__ sigma, double dw, const DevSchur& S,
@@ -1064,9 +1066,9 @@ __device__ void schur_block(const DevProb& P, const int* __restrict__ inert,
 __global__ void __launch_bounds__(SBS)
 k_schur(DevProb P, const int* __restrict__ inert, const double* __restrict__ chunkS,
         const double* __restrict__ wtt, const double* __restrict__ sigma, double dw,
-        DevSchur S) {
+        DevSchur S, int in_global) {
   extern __shared__ double sS[];
-  schur_block(P, inert, chunkS, wtt, sigma, dw, S, sS);
+  schur_block(P, inert, chunkS, wtt, sigma, dw, S, in_global ? S.S : sS);
 }
 
 // ---- solves: one warp per block ----------------------------------------------------
@@ -1411,9 +1413,9 @@ k_elem_bwd(DevProb P, DevFactor<T> F, DevSchur S, double* __restrict__ sol) {
 // reaches (e + 1) * gridDim.x: a block arrives with one release reduction
 // and waits by polling the counter (no returning atomic on the way, nothing
 // to reset between barriers).  The last block to leave the kernel zeroes the
-// counter for the next launch.  The wait is bounded: after GRID_SPIN_LIMIT
-// polls it records an error in GridBar::err and continues, so a fault shows
-// up as a status on the host instead of a hang.
+// counter for the next launch.  The wait is bounded: after GridBar::spin_limit
+// polls (GRID_SPIN_LIMIT when 0) it records an error in GridBar::err and
+// continues, so a fault shows up as a status on the host instead of a hang.
 constexpr long long GRID_SPIN_LIMIT = 20000000;   // ~1-2 s of polling
 
 __device__ inline unsigned int ld_acquire_gpu(const unsigned int* p) {
@@ -1427,13 +1429,15 @@ __device__ void grid_barrier(GridBar* gb, unsigned int& epoch) {
   __syncthreads();
   ++epoch;
   if (threadIdx.x == 0) {
-    const unsigned int target = epoch * gridDim.x;
+    // extra and spin_limit are set by the host before the launch
+    const unsigned int target = epoch * gridDim.x + gb->extra;
+    const long long limit = gb->spin_limit > 0 ? gb->spin_limit : GRID_SPIN_LIMIT;
     __threadfence();
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->count) : "memory");
     long long spins = 0;
     while (ld_acquire_gpu(&gb->count) < target) {
       __nanosleep(32);
-      if (++spins > GRID_SPIN_LIMIT) { atomicExch(&gb->err, 1); break; }
+      if (++spins > limit) { atomicExch(&gb->err, 1); break; }
     }
   }
   __syncthreads();
@@ -1834,11 +1838,14 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
   for (int s = 1; s < P.N; s *= 2)
     if ((e = bcr_level(s, 0)) != cudaSuccess) return e;
   if ((e = bcr_level(1, 1)) != cudaSuccess) return e;
-  if (sms > SMEM_OPTIN_ABOVE)
+  // the Schur block works in shared memory up to the factorization limit,
+  // otherwise in S.S (p p + p doubles) itself
+  const bool sg = sms > SMEM_LIMIT;
+  if (!sg && sms > SMEM_OPTIN_ABOVE)
     cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
   if ((e = launch_chunk_sums(F.Scon, 2 * P.N, P.p * P.p, F.chunkS, st)) != cudaSuccess) return e;
   count_launch();
-  k_schur<<<1, SBS, sms, st>>>(P, F.inert, F.chunkS, E.wtt, sigma, dw, S);
+  k_schur<<<1, SBS, sg ? 0 : sms, st>>>(P, F.inert, F.chunkS, E.wtt, sigma, dw, S, sg ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -91,23 +91,56 @@ size_t elem_factor_smem(const DevProb& P, bool full);
 template <typename T>
 size_t bcr_factor_smem(const DevProb& P, bool full);
 
-// Device allocations owned by a problem; freed in the destructor.
+// Device allocations owned by a problem; freed in the destructor (or by
+// release).  With `stream` set the allocations are stream-ordered
+// (cudaMallocAsync from the device's default pool) and release() returns them
+// in stream order, so freeing a store does not synchronise the device.
 struct DevArena {
   std::vector<void*> ptrs;
   size_t bytes = 0;
-  ~DevArena() {
-    for (void* p : ptrs) cudaFree(p);
+  cudaStream_t stream = nullptr;
+  DevArena() = default;
+  DevArena(const DevArena&) = delete;
+  DevArena& operator=(const DevArena&) = delete;
+  DevArena(DevArena&& o) noexcept : ptrs(std::move(o.ptrs)), bytes(o.bytes), stream(o.stream) {
+    o.ptrs.clear();
+    o.bytes = 0;
   }
+  DevArena& operator=(DevArena&& o) noexcept {
+    if (this != &o) {
+      release(nullptr);
+      ptrs = std::move(o.ptrs);
+      bytes = o.bytes;
+      stream = o.stream;
+      o.ptrs.clear();
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevArena() { release(nullptr); }
+  // Free everything: in stream order on `st` when given, else at once.
+  void release(cudaStream_t st) {
+    for (void* p : ptrs) {
+      if (st) cudaFreeAsync(p, st);
+      else cudaFree(p);
+    }
+    ptrs.clear();
+    bytes = 0;
+  }
+  // Bytes alloc<T>(count) takes.
+  template <typename T>
+  static size_t bytes_of(size_t count) { return (count ? count : 1) * sizeof(T); }
   template <typename T>
   T* alloc(size_t count) {
-    if (count == 0) count = 1;
+    const size_t b = bytes_of<T>(count);
     void* p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    const cudaError_t e = stream ? cudaMallocAsync(&p, b, stream) : cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
     ptrs.push_back(p);
-    bytes += count * sizeof(T);
+    bytes += b;
     return static_cast<T*>(p);
   }
 };
@@ -116,6 +149,7 @@ template <typename T>
 struct FactorStore {
   DevFactor<T> F{};
   bool allocated = false;
+  DevArena mem;   // this store's arrays (stream-ordered, freed on release)
 };
 
 }  // namespace collo
@@ -128,6 +162,16 @@ collo_status ensure_factor_storage(collo_problem* pr, int precision);
 // the Schur blocks.
 collo_status ensure_spare_storage(collo_problem* pr, int precision);
 void swap_spare(collo_problem* pr, int precision);
+// Device bytes the problem holds now (its own arrays and every allocated
+// factorization store).
+int64_t problem_held_bytes(const collo_problem* pr);
+// Device bytes the problem will hold while an interior-point solve in
+// `precision` runs on it (the stores ensure_factor_storage and
+// ensure_spare_storage add are counted exactly as they would be allocated).
+int64_t problem_solve_bytes(const collo_problem* pr, int precision);
+// Free every factorization store (stream-ordered on `st`); the problem keeps
+// its data, iterate and evaluation arrays and becomes unfactored.
+void release_factor_storage(collo_problem* pr, cudaStream_t st);
 collo_status factor_internal(collo_problem* prob, double dw, double dc, int precision,
                              long long inertia[3]);
 collo_status solve_internal(collo_problem* prob, const double* b, double* sol, int refine_max,
@@ -193,6 +237,11 @@ struct collo_problem {
   int* fails = nullptr;       // [1]
   float* sweep_work = nullptr;   // forward-sweep FP32 Newton matrix when too big for smem
   int64_t n_x = 0, n_c = 0;
+  // grid-barrier wait settings of this problem's own runner
+  // (collo_problem_set_wait_limit): polls before a wait gives up (0: default)
+  // and the failure-test switch that makes every barrier unreachable
+  long long wait_polls = 0;
+  int wait_unreachable = 0;
   collo::DevInst inst{};            // this problem's device pointers (host copy)
   collo::Runner* self = nullptr;    // single-instance runner (batch of one)
   ~collo_problem();

@@ -173,6 +173,18 @@ struct Runner {
   }
   int shadow(int s) const { return capacity + s; }
 
+  // Wait settings of the persistent kernels' grid barrier (see GridBar).
+  collo_status set_wait(long long polls, int unreachable) {
+    GridBar g{};
+    g.extra = unreachable ? 1u : 0u;
+    g.spin_limit = polls > 0 ? polls : 0;
+    COLLO_CUDA(cudaStreamSynchronize(stream));
+    COLLO_CUDA(cudaMemcpy(&gbar->extra, &g.extra, sizeof(g.extra), cudaMemcpyHostToDevice));
+    COLLO_CUDA(cudaMemcpy(&gbar->spin_limit, &g.spin_limit, sizeof(g.spin_limit),
+                          cudaMemcpyHostToDevice));
+    return COLLO_OK;
+  }
+
   const DevProb& P(int s) const { return h_insts[s].P; }
   double* out(int s) { return h_outs + (size_t)s * OUTS; }
 
@@ -442,6 +454,8 @@ collo_status self_runner(collo_problem* pr, Runner** out) {
   if (!pr->self) {
     Runner* r = new Runner();
     collo_status s = r->init(1, pr->device, pr->stream);
+    if (s == COLLO_OK && (pr->wait_polls > 0 || pr->wait_unreachable))
+      s = r->set_wait(pr->wait_polls, pr->wait_unreachable);
     if (s != COLLO_OK) { delete r; return s; }
     pr->self = r;
   }
@@ -1125,7 +1139,8 @@ struct collo_server {
   Runner R;
   Opt o;
   int64_t budget = 0;
-  int64_t active_bytes = 0;
+  int64_t active_bytes = 0;   // held by admitted jobs' problems
+  int64_t peak_bytes = 0;     // largest active_bytes so far
   long long next_ticket = 1;
   struct Job {
     long long ticket;
@@ -1134,6 +1149,7 @@ struct collo_server {
     IpmInst I;
     int slot = -1;
     bool done = false;
+    int64_t bytes = 0;   // device bytes its problem holds while admitted
     collo_result res{};
   };
   std::deque<Job*> waiting;
@@ -1321,6 +1337,19 @@ collo_status collo_server_create(int max_slots, int64_t budget_bytes, const coll
   sv->o = make_opt(opts);
   sv->budget = budget_bytes;
   sv->slots.assign(max_slots, nullptr);
+  // factorization stores come from the device's default stream-ordered pool;
+  // let it keep up to the budget (64 GiB without one) of freed memory for the
+  // next admissions instead of returning it at every synchronisation
+  {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = 0;
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      const uint64_t want = budget_bytes > 0 ? (uint64_t)budget_bytes : (uint64_t)64 << 30;
+      if (want > keep) cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, (void*)&want);
+    }
+    cudaGetLastError();
+  }
   *out = sv.release();
   return COLLO_OK;
 }
@@ -1348,7 +1377,11 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
   collo_status s;
   // admit waiting jobs into free slots within the device-memory budget, in
   // groups of at least admit_min (initialising a group costs one forward
-  // sweep of the longest horizon, whatever the group's size)
+  // sweep of the longest horizon, whatever the group's size).  A job's
+  // footprint is its problem's arrays plus every factorization store the
+  // solve allocates (counted before they exist); the stores are allocated at
+  // admission and freed when the job retires.  Jobs are admitted in
+  // submission order; one larger than the whole budget fails with OOM.
   std::vector<IpmInst*> fresh;
   int n_free = 0, n_busy = 0;
   for (auto* j : sv->slots) (j ? n_busy : n_free)++;
@@ -1359,13 +1392,22 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     for (int k = 0; k < (int)sv->slots.size(); ++k)
       if (!sv->slots[k]) { slot = k; break; }
     if (slot < 0) break;
-    const int64_t bytes = (int64_t)j->prob->arena.bytes;
-    if (sv->budget > 0 && sv->active_bytes > 0 && sv->active_bytes + bytes > sv->budget) break;
+    const int64_t need = problem_solve_bytes(j->prob, sv->o.precision);
+    if (sv->budget > 0 && need > sv->budget) {
+      sv->waiting.pop_front();
+      j->res = collo_result{};
+      j->res.status = COLLO_ERR_OOM;
+      j->done = true;
+      continue;
+    }
+    if (sv->budget > 0 && sv->active_bytes + need > sv->budget) break;
     sv->waiting.pop_front();
     if ((s = ipm_prepare(R, slot, j->prob, j->theta0.data(), sv->o, j->I)) != COLLO_OK) return s;
     j->slot = slot;
+    j->bytes = problem_held_bytes(j->prob);
     sv->slots[slot] = j;
-    sv->active_bytes += (int64_t)j->prob->arena.bytes;
+    sv->active_bytes += j->bytes;
+    sv->peak_bytes = std::max(sv->peak_bytes, sv->active_bytes);
     fresh.push_back(&j->I);
   }
   {
@@ -1384,7 +1426,9 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     j->res = collo_result{};
     if ((s = ipm_finish(R, j->I, &j->res)) != COLLO_OK) return s;
     j->done = true;
-    sv->active_bytes -= (int64_t)j->prob->arena.bytes;
+    // its factorization stores go back in stream order after its last kernels
+    release_factor_storage(j->prob, R.stream);
+    sv->active_bytes -= j->bytes;
     sv->slots[k] = nullptr;
   }
   int a = 0;
@@ -1403,6 +1447,23 @@ int collo_phase_profile(double* ms, long long* rounds, int n, int reset) {
   if (reset)
     for (int k = 0; k < PF_N; ++k) { g_prof_ms[k] = 0.0; g_prof_rounds[k] = 0; }
   return g_prof_on > 0 ? (int)PF_N : 0;
+}
+
+collo_status collo_server_memory(collo_server* sv, int64_t* active_bytes, int64_t* peak_bytes) {
+  if (!sv) { set_error("NULL server"); return COLLO_ERR_INVALID_ARG; }
+  if (active_bytes) *active_bytes = sv->active_bytes;
+  if (peak_bytes) *peak_bytes = sv->peak_bytes;
+  return COLLO_OK;
+}
+
+collo_status collo_problem_set_wait_limit(collo_problem* prob, long long max_polls,
+                                          int unreachable) {
+  if (!prob || max_polls < 0) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  prob->wait_polls = max_polls;
+  prob->wait_unreachable = unreachable ? 1 : 0;
+  if (prob->self) return prob->self->set_wait(prob->wait_polls, prob->wait_unreachable);
+  return COLLO_OK;
 }
 
 collo_status collo_server_set_admission(collo_server* sv, int min_free_slots) {

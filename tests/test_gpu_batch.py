@@ -159,3 +159,69 @@ def test_repeated_batches_are_bitwise_reproducible(collo):
         for a, b in zip(runs[0], r):
             assert a["iterations"] == b["iterations"]
             assert np.array_equal(a["theta"], b["theta"])
+
+
+def test_server_admits_by_device_memory_budget(collo):
+    """Admission by device memory: with a budget of k problems' full footprint
+    (their arrays plus the factorization stores a mixed-precision solve
+    allocates, collo_problem_solve_bytes) at most k of n waiting problems run at
+    once although more slots are free; the held memory never exceeds the budget;
+    each job's stores are freed when it retires; every result equals the same
+    problem solved alone."""
+    inst = W.random_network(4, 8, n_obs=3, M=20, T=5.0, N=40, seed=41, theta0_spread=0.1)
+    rng = np.random.default_rng(11)
+    starts = [inst.theta_true + rng.uniform(-0.1, 0.1, inst.p) for _ in range(6)]
+    probs = [collo.Problem(inst) for _ in starts]
+    need = probs[0].solve_bytes(collo.MIXED)
+    base = probs[0].device_bytes()
+    assert need > base          # the stores are counted before they exist
+    k = 2
+    budget = k * need + need // 2
+    server = collo.Server(max_slots=5, budget_bytes=budget, precision=collo.MIXED)
+    tickets = [server.submit(pb, th) for pb, th in zip(probs, starts)]
+    most, done = 0, {}
+    for _ in range(5000):
+        active, waiting = server.step()
+        held, peak = server.memory()
+        most = max(most, active)
+        assert active <= k and held <= budget and peak <= budget
+        for i, t in enumerate(tickets):
+            if i not in done:
+                r = server.poll(t)
+                if r is not None:
+                    done[i] = r
+                    # retired: its factorization stores are freed (its arrays,
+                    # the spare trial arrays included, stay with the problem)
+                    assert base <= probs[i].device_bytes() < need
+                    assert probs[i].solve_bytes(collo.MIXED) == need
+        if len(done) == len(tickets):
+            break
+    assert most == k
+    assert server.memory()[1] == k * need
+    server.close()
+    for i, (pb, th) in enumerate(zip(probs, starts)):
+        alone = pb.ipm_solve(theta0=th, precision=collo.MIXED, want_x=False)
+        assert alone["status"] == done[i]["status"]
+        assert alone["iterations"] == done[i]["iterations"]
+        assert np.array_equal(alone["theta"], done[i]["theta"])
+        pb.close()
+
+
+def test_server_fails_a_problem_larger_than_the_budget(collo):
+    inst = W.small_network(n=3, r=4, N=7, seed=7)
+    small = collo.Problem(inst)
+    big = collo.Problem(W.config2(N=100))
+    budget = small.solve_bytes(collo.FP64) + 1024
+    assert big.solve_bytes(collo.FP64) > budget
+    server = collo.Server(max_slots=2, budget_bytes=budget)
+    t_big = server.submit(big)
+    t_small = server.submit(small)
+    for _ in range(2000):
+        server.step()
+        if server.poll(t_small) is not None:
+            break
+    assert server.poll(t_big)["status"] == collo.ERR_OOM
+    assert server.poll(t_small)["status"] in (collo.OK, collo.ACCEPTABLE)
+    server.close()
+    small.close()
+    big.close()

@@ -38,6 +38,16 @@ def _point(oprob, seed):
     return x, lam, zl, zu
 
 
+# Systems whose inertia no FP64 method can count reliably: on the stiff
+# network the KKT matrix has a 2-norm near 2.5e15 (objective weights 1/sigma^2
+# of species that nearly vanish, sigma floored at 5e-8) against smallest
+# eigenvalue magnitudes near 5e-9, a condition number near 1e24 > 1 / eps, so
+# Bunch-Kaufman, eigenvalue counts and the static pivots may all differ by a
+# few.  There the step is checked by its backward error and forward agreement;
+# inertia is compared only where the whole matrix's eigenvalues resolve it
+# (test_inertia_matches_whole_matrix_eigenvalues).
+UNRESOLVED_INERTIA = {"config3_N40"}
+
 # Forward tolerance on the Newton step (relative 2-norm).  1e-10 everywhere
 # except the stiff config-3 network: its KKT matrix has a 2-norm condition
 # number near 1e23 (delta_c = 1e-8 blocks against rate constants up to 1e3),
@@ -66,7 +76,8 @@ def test_newton_step_matches_oracle_fp64(collo, name, dw):
     with collo.Problem(inst) as prob:
         prob.eval(x, lam)
         inertia = prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.FP64)
-        assert inertia == ref["inertia"]
+        if name not in UNRESOLVED_INERTIA:
+            assert inertia == ref["inertia"]
         sol, info = prob.kkt_solve(ref["rhs"], refine_max=3, refine_tol=1e-14)
     err = np.linalg.norm(sol - ref["sol"]) / np.linalg.norm(ref["sol"])
     assert backward_error(ref["K"], sol, ref["rhs"]) <= 1e-15
@@ -85,7 +96,9 @@ def test_newton_step_at_ipm_start_fp64(collo, name):
     ref = newton_system(oprob, x, lam, zl, zu, mu, 0.0, dc)
     with collo.Problem(inst) as prob:
         prob.eval(x, lam)
-        assert prob.kkt_factor(ref["sigma"], 0.0, dc, precision=collo.FP64) == ref["inertia"]
+        inertia = prob.kkt_factor(ref["sigma"], 0.0, dc, precision=collo.FP64)
+        if name not in UNRESOLVED_INERTIA:
+            assert inertia == ref["inertia"]
         sol, info = prob.kkt_solve(ref["rhs"], refine_max=3, refine_tol=1e-14)
     err = np.linalg.norm(sol - ref["sol"]) / np.linalg.norm(ref["sol"])
     assert backward_error(ref["K"], sol, ref["rhs"]) <= 1e-15
@@ -157,3 +170,144 @@ def test_persistent_and_per_level_launches_agree_bitwise(collo, prec):
             sols.append((inertia, sol))
     assert sols[0][0] == sols[1][0] == ref["inertia"]
     assert np.array_equal(sols[0][1], sols[1][1])
+
+
+# ---- inertia against the whole matrix's eigenvalues -------------------------------------
+
+RESOLVED_CASES = {
+    "cascade_N50": lambda: W.config1(),
+    "n4_N33": lambda: W.random_network(4, 8, n_obs=2, M=20, T=5.0, N=33, seed=19),
+    "n12_N10": lambda: W.random_network(12, 24, n_obs=4, M=20, T=5.0, N=10, seed=43,
+                                        theta0_spread=0.1),
+}
+
+
+def eigen_inertia(K):
+    """(n_pos, n_neg, n_zero) of the dense symmetric K from its eigenvalues, and
+    whether the count is resolved: every |eigenvalue| above 1000 n eps ||K||_2,
+    far beyond the eigensolver's backward error, so no rounding can move an
+    eigenvalue across zero."""
+    ev = np.linalg.eigvalsh(K.toarray())
+    tau = 1000.0 * K.shape[0] * np.finfo(np.float64).eps * np.max(np.abs(ev))
+    return (int(np.sum(ev > 0)), int(np.sum(ev < 0)), 0), bool(np.min(np.abs(ev)) > tau)
+
+
+@pytest.mark.parametrize("name", list(RESOLVED_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inertia_matches_whole_matrix_eigenvalues(collo, name, prec):
+    """Sylvester's law: the inertia counted from the static 2x2 pivots equals the
+    eigenvalue signs of the whole assembled KKT matrix (an independent count,
+    not a factorization), at random iterates and at the IPM start, with and
+    without regularisation, wherever that count is resolved."""
+    inst = RESOLVED_CASES[name]()
+    oprob = OProblem(inst)
+    pts = [_point(oprob, 21), _point(oprob, 5)]
+    x0, l0, zl0, zu0, _ = oipm.initial_point(oprob, inst.theta0, oipm.Options())
+    pts.append((x0, l0, zl0, zu0))
+    P = collo.MIXED if prec == "mixed" else collo.FP64
+    resolved = 0
+    with collo.Problem(inst) as prob:
+        for x, lam, zl, zu in pts:
+            for dw in (0.0, 1e-2):
+                dc = 1e-8 * 0.05 ** 0.25
+                ref = newton_system(oprob, x, lam, zl, zu, 0.05, dw, dc)
+                want, ok = eigen_inertia(ref["K"])
+                if not ok:
+                    continue
+                resolved += 1
+                prob.eval(x, lam)
+                assert prob.kkt_factor(ref["sigma"], dw, dc, precision=P) == want
+    assert resolved >= 4
+
+
+# ---- large element blocks in the mixed path ----------------------------------------------
+
+LARGE_BLOCKS = {
+    # 8n + p = 130: shared-memory panel elimination in FP32
+    "n13_N20": lambda: W.random_network(13, 26, n_obs=4, M=20, T=5.0, N=20, seed=52,
+                                        theta0_spread=0.1),
+    # 8n + p = 250: FP32 element blocks in global slabs, reduction blocks of 150
+    "n25_N12": lambda: W.random_network(25, 50, n_obs=4, M=20, T=5.0, N=12, seed=61,
+                                        theta0_spread=0.1),
+    # config-4 shape at its largest species count: 8n + p = 500
+    "n50_N6": lambda: W.random_network(50, 100, n_obs=4, M=20, T=5.0, N=6, seed=62,
+                                       theta0_spread=0.1),
+}
+
+
+@pytest.mark.parametrize("name", list(LARGE_BLOCKS))
+def test_mixed_step_on_large_blocks_matches_oracle(collo, name):
+    """FP32 panel eliminations of blocks above the register-tile limit (124 rows),
+    refined in FP64, reach the oracle's FP64 Newton step."""
+    inst = LARGE_BLOCKS[name]()
+    oprob = OProblem(inst)
+    opt = oipm.Options()
+    x, lam, zl, zu, _ = oipm.initial_point(oprob, inst.theta0, opt)
+    mu, dw = 0.1, 1e-3
+    dc = 1e-8 * mu ** 0.25
+    ref = newton_system(oprob, x, lam, zl, zu, mu, dw, dc)
+    with collo.Problem(inst) as prob:
+        prob.eval(x, lam)
+        inertia = prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.MIXED)
+        sol, info = prob.kkt_solve(ref["rhs"], refine_max=40, refine_tol=1e-14)
+        inertia64 = prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.FP64)
+        sol64, _ = prob.kkt_solve(ref["rhs"], refine_max=3, refine_tol=1e-14)
+    assert inertia == inertia64 == ref["inertia"]
+    err = np.linalg.norm(sol - ref["sol"]) / np.linalg.norm(ref["sol"])
+    err64 = np.linalg.norm(sol64 - ref["sol"]) / np.linalg.norm(ref["sol"])
+    assert err <= 1e-10, (err, info)
+    assert err64 <= 1e-10
+    assert backward_error(ref["K"], sol64, ref["rhs"]) <= 1e-15
+
+
+# ---- parameter Schur complement larger than shared memory ---------------------------
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_parameter_schur_block_in_global_memory(collo, mode):
+    """p = 200 (the serving stream's largest networks): the p x p Schur block and
+    its multiplier row (8 (p^2 + p) bytes = 321.6 KB) exceed shared memory and
+    are factored in the problem's own S storage, in the persistent kernel
+    (mode 0) and in the per-level launches (mode 1)."""
+    inst = W.random_network(100, 200, n_obs=4, M=20, T=5.0, N=3, seed=71, theta0_spread=0.1)
+    assert inst.p == 200
+    oprob = OProblem(inst)
+    x, lam, zl, zu = _point(oprob, 21)
+    mu, dw = 0.05, 1e-2
+    dc = 1e-8 * mu ** 0.25
+    ref = newton_system(oprob, x, lam, zl, zu, mu, dw, dc)
+    with collo.Problem(inst, launch_mode=mode) as prob:
+        prob.eval(x, lam)
+        inertia = prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.FP64)
+        sol, info = prob.kkt_solve(ref["rhs"], refine_max=3, refine_tol=1e-14)
+    assert inertia == ref["inertia"]
+    err = np.linalg.norm(sol - ref["sol"]) / np.linalg.norm(ref["sol"])
+    assert err <= 1e-10, (err, info)
+    assert backward_error(ref["K"], sol, ref["rhs"]) <= 1e-15
+
+
+# ---- a device-side wait that runs out ------------------------------------------------
+
+def test_grid_barrier_wait_runs_out_and_the_problem_recovers(collo):
+    """The failure-test switch makes every grid barrier of the persistent kernels
+    wait for one arrival that never comes: each wait gives up after 2000 polls,
+    the factorization returns COLLO_ERR_TIMEOUT (the paper's "T") instead of
+    hanging, and the next factorization on the same problem, with the switch
+    off, is correct."""
+    inst = CASES["n4_N33"]()
+    oprob = OProblem(inst)
+    x, lam, zl, zu = _point(oprob, 21)
+    mu, dw = 0.05, 1e-2
+    dc = 1e-8 * mu ** 0.25
+    ref = newton_system(oprob, x, lam, zl, zu, mu, dw, dc)
+    with collo.Problem(inst) as prob:
+        prob.eval(x, lam)
+        prob.set_wait_limit(2000, unreachable=True)
+        with pytest.raises(collo.ColloError) as e:
+            prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.FP64)
+        assert e.value.status == collo.ERR_TIMEOUT
+        assert "timed out" in collo.last_error()
+        prob.set_wait_limit(0, unreachable=False)
+        assert prob.kkt_factor(ref["sigma"], dw, dc, precision=collo.FP64) == ref["inertia"]
+        sol, _ = prob.kkt_solve(ref["rhs"], refine_max=3, refine_tol=1e-14)
+    err = np.linalg.norm(sol - ref["sol"]) / np.linalg.norm(ref["sol"])
+    assert err <= 1e-10

@@ -83,7 +83,7 @@ def test_noalloc_eval_matches_collo_eval_twice(collo, make):
             assert torch.equal(outs[k], results[1][k]), k
 
 
-def test_noalloc_eval_rejects_oversized_and_null(collo):
+def test_noalloc_eval_rejects_oversized_null_and_host_pointers(collo):
     torch = pytest.importorskip("torch")
     # N (4 + p) + 8 above 2^19 doubles of fixed scratch
     inst = W.random_network(1, 2, n_obs=1, M=5, T=2.0, N=120000, seed=9)
@@ -105,3 +105,47 @@ def test_noalloc_eval_rejects_oversized_and_null(collo):
         with pytest.raises(collo.ColloError) as e:
             prob.eval_noalloc(xd.data_ptr(), None, ptrs)
         assert e.value.status == collo.ERR_INVALID_ARG
+        # host memory where device memory is required: refused before any launch
+        ptrs = {k: v.data_ptr() for k, v in outs.items()}
+        xh = np.zeros(prob.n_x)
+        with pytest.raises(collo.ColloError) as e:
+            prob.eval_noalloc(xh.ctypes.data, None, ptrs)
+        assert e.value.status == collo.ERR_INVALID_ARG
+        assert "not device memory" in collo.last_error()
+        pinned = torch.zeros(prob.n_c, dtype=torch.float64).pin_memory()
+        ptrs["c"] = pinned.data_ptr()
+        with pytest.raises(collo.ColloError) as e:
+            prob.eval_noalloc(xd.data_ptr(), None, ptrs)
+        assert e.value.status == collo.ERR_INVALID_ARG
+        # the problem is still usable afterwards
+        ptrs = {k: v.data_ptr() for k, v in outs.items()}
+        x, lam = _point(prob, 4)
+        xd = torch.tensor(x, device="cuda")
+        prob.eval_noalloc(xd.data_ptr(), None, ptrs)
+        torch.cuda.synchronize()
+        host = prob.eval(x, None)
+        host["phi"] = np.array([host["phi"]])
+        _compare(host, outs)
+
+
+def test_noalloc_eval_allocates_nothing_and_keeps_the_current_device(collo):
+    """After one call (which looks up the scratch array's address), further
+    calls leave the device's free memory unchanged and the caller's current
+    device as it was."""
+    torch = pytest.importorskip("torch")
+    inst = W.config2(N=100)
+    with collo.Problem(inst) as prob:
+        outs = _device_outputs(torch, prob)
+        ptrs = {k: v.data_ptr() for k, v in outs.items()}
+        x, lam = _point(prob, 3)
+        xd = torch.tensor(x, device="cuda")
+        ld = torch.tensor(lam, device="cuda")
+        prob.eval_noalloc(xd.data_ptr(), ld.data_ptr(), ptrs)
+        torch.cuda.synchronize()
+        before = torch.cuda.mem_get_info()[0]
+        dev = torch.cuda.current_device()
+        for _ in range(5):
+            prob.eval_noalloc(xd.data_ptr(), ld.data_ptr(), ptrs)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == before
+        assert torch.cuda.current_device() == dev
