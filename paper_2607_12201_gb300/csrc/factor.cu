@@ -191,6 +191,19 @@ __device__ inline double elem_entry(const DevProb& P, const DevEval& E, int e, i
 
 __host__ __device__ inline int odd_ld(int m) { return (m & 1) ? m : m + 1; }
 
+// Where pair_eliminate works on a block of msz rows that does not fit in shared
+// memory: the block itself in a per-CUDA-block global slab (L2-resident), and
+// its two panel buffers Lp, Up (msz x PLD each) in shared memory when they fit
+// the factorization limit, otherwise in the slab behind the block.
+template <typename T>
+__host__ __device__ inline bool panel_in_global(int msz) {
+  return sizeof(T) * 2 * (size_t)msz * PLD > FACTOR_SMEM_LIMIT;
+}
+template <typename T>
+__host__ __device__ inline size_t slab_elems(int msz) {
+  return (size_t)odd_ld(msz) * msz + (panel_in_global<T>(msz) ? 2 * (size_t)msz * PLD : 0);
+}
+
 // ---- 1. element condensation --------------------------------------------------
 // One CUDA block condenses element e: assemble the bordered (8n + p) block,
 // eliminate the 3n interior pairs, write L, pivots, the 2n x 2n interface
@@ -243,9 +256,10 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
               DevFactor<T> F, int use_smem) {
   extern __shared__ unsigned char smraw[];
   const int ext = P.ext, ld = odd_ld(ext);
-  T* Lp = reinterpret_cast<T*>(smraw);
+  T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(ext);
+  T* Lp = (!use_smem && panel_in_global<T>(ext)) ? slab + (size_t)ld * ext : reinterpret_cast<T*>(smraw);
   T* Up = Lp + (size_t)ext * PLD;
-  T* A = use_smem ? (Up + (size_t)ext * PLD) : (F.work + (size_t)blockIdx.x * ld * ext);
+  T* A = use_smem ? (Up + (size_t)ext * PLD) : slab;
   for (int e = blockIdx.x; e < P.N; e += gridDim.x)
     elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, Lp, Up);
 }
@@ -952,9 +966,11 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
                            ub[half].v, stage, pivs[half], cnt[half]);
   } else {
     const int bext = P.bext, ld = odd_ld(bext);
-    T* Lp = reinterpret_cast<T*>(smraw);
+    T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(bext);
+    T* Lp = (!use_smem && panel_in_global<T>(bext)) ? slab + (size_t)ld * bext
+                                                    : reinterpret_cast<T*>(smraw);
     T* Up = Lp + (size_t)bext * PLD;
-    T* A = use_smem ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
+    T* A = use_smem ? (Up + (size_t)bext * PLD) : slab;
     for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
       bcr_factor_one<T>(P, F, stride, final_level, bi, A, Lp, Up);
   }
@@ -1507,9 +1523,11 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     const DevInst& I = insts[act[k]];
     const DevFactor<T>& F = inst_factor<T>(I);
     const int ext = I.P.ext, ld = odd_ld(ext);
-    T* Lp = reinterpret_cast<T*>(smraw);
+    const bool sm = flags[k] & 1;
+    T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(ext);
+    T* Lp = (!sm && panel_in_global<T>(ext)) ? slab + (size_t)ld * ext : reinterpret_cast<T*>(smraw);
     T* Up = Lp + (size_t)ext * PLD;
-    T* Am = (flags[k] & 1) ? (Up + (size_t)ext * PLD) : (F.work + (size_t)blockIdx.x * ld * ext);
+    T* Am = sm ? (Up + (size_t)ext * PLD) : slab;
     elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, Lp, Up);
   }
   grid_barrier(gb, ep);
@@ -1568,9 +1586,12 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       const DevInst& I = insts[act[k]];
       const DevFactor<T>& F = inst_factor<T>(I);
       const int bext = I.P.bext, ld = odd_ld(bext);
-      T* Lp = reinterpret_cast<T*>(smraw);
+      const bool sm = flags[k] & 2;
+      T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(bext);
+      T* Lp = (!sm && panel_in_global<T>(bext)) ? slab + (size_t)ld * bext
+                                                : reinterpret_cast<T*>(smraw);
       T* Up = Lp + (size_t)bext * PLD;
-      T* Am = (flags[k] & 2) ? (Up + (size_t)bext * PLD) : (F.work + (size_t)blockIdx.x * ld * bext);
+      T* Am = sm ? (Up + (size_t)bext * PLD) : slab;
       if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, Lp, Up);
       else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, Lp, Up);
     }
@@ -1696,18 +1717,19 @@ int bcr_levels(int N) {
   return lv;
 }
 
+// Dynamic shared memory of a panel-eliminated block: everything (full), or
+// the panel buffers only when the block is in a global slab (none when they
+// are in the slab too).
 template <typename T>
-size_t elem_factor_smem(const DevProb& P, bool full) {
-  size_t v = sizeof(T) * 2 * (size_t)P.ext * PLD;
-  if (full) v += sizeof(T) * (size_t)odd_ld(P.ext) * P.ext;
-  return v;
+static size_t panel_smem(int msz, bool full) {
+  const size_t panel = sizeof(T) * 2 * (size_t)msz * PLD;
+  if (full) return panel + sizeof(T) * (size_t)odd_ld(msz) * msz;
+  return panel_in_global<T>(msz) ? 0 : panel;
 }
 template <typename T>
-size_t bcr_factor_smem(const DevProb& P, bool full) {
-  size_t v = sizeof(T) * 2 * (size_t)P.bext * PLD;
-  if (full) v += sizeof(T) * (size_t)odd_ld(P.bext) * P.bext;
-  return v;
-}
+size_t elem_factor_smem(const DevProb& P, bool full) { return panel_smem<T>(P.ext, full); }
+template <typename T>
+size_t bcr_factor_smem(const DevProb& P, bool full) { return panel_smem<T>(P.bext, full); }
 
 // Largest dynamic shared memory of a factorization block.  One limit decides
 // both whether a block is factored in shared memory (here and in the batched
@@ -1724,8 +1746,8 @@ bool bcr_uses_smem(const DevProb& P) { return bcr_factor_smem<T>(P, true) <= SME
 template <typename T>
 size_t factor_work_elems(const DevProb& P, int n_slabs) {
   size_t w = 0;
-  if (!elem_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.ext) * P.ext * n_slabs);
-  if (!bcr_uses_smem<T>(P)) w = std::max(w, (size_t)odd_ld(P.bext) * P.bext * n_slabs);
+  if (!elem_uses_smem<T>(P)) w = std::max(w, slab_elems<T>(P.ext) * n_slabs);
+  if (!bcr_uses_smem<T>(P)) w = std::max(w, slab_elems<T>(P.bext) * n_slabs);
   return w;
 }
 
