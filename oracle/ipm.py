@@ -325,7 +325,8 @@ def solve(inst, theta0=None, opt: Options | None = None, verbose: bool = False,
         zl = reset_bound_duals(zl, sl, mu, opt.kappa_sigma)
         zu = reset_bound_duals(zu, su, mu, opt.kappa_sigma)
         rec = dict(it=it, phi=ev["phi"], inf_pr=float(np.max(np.abs(ev["c"]))), err=err,
-                   mu=mu, delta_w=delta_w, alpha=alpha, alpha_z=alpha_z, trials=trials)
+                   mu=mu, delta_w=delta_w, alpha=alpha, alpha_z=alpha_z, trials=trials,
+                   theta=x[prob.nz:].copy())
         history.append(rec)
         if verbose:
             print(rec)

@@ -43,17 +43,10 @@ __device__ inline void pivot_inertia(double a, double b, double d, int& pos, int
   if (a + d > 0) pos += 2; else neg += 2;
 }
 
-// Eliminate the first npairs (state, multiplier) pairs of the symmetric
-// matrix A (size msz, leading dimension ld, lower triangle valid), blocked
-// right-looking: pairs are taken in panels of PB; inside a panel each pair's
-// multipliers are formed and only the panel's remaining columns are updated;
-// then the trailing matrix receives one rank-2PB update, computed in 4 x 4
-// register tiles from the panel's multipliers Lp and unscaled columns Up.
-// L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
-// Dout[3 q].  Scratch Lp, Up: msz x (2 PB + 1) each (shared memory).
-constexpr int PB = 8;
-constexpr int PLD = 2 * PB + 1;
+// Packed lower triangle: entry (r, c), c <= r, at r (r + 1) / 2 + c.
+__host__ __device__ inline int tri_at(int r, int c) { return r * (r + 1) / 2 + c; }
 
+// Tile t of a lower triangle of tiles, numbered row by row: (ti, tj), tj <= ti.
 __device__ inline void tri_tile(int t, int& ti, int& tj) {
   int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= t) ++i;
@@ -62,61 +55,81 @@ __device__ inline void tri_tile(int t, int& ti, int& tj) {
   tj = t - i * (i + 1) / 2;
 }
 
+// Eliminate the first npairs (state, multiplier) pairs of the symmetric msz x
+// msz matrix A, stored as a packed lower triangle (shared or global memory),
+// blocked right-looking: pairs are taken in panels of PB.  A panel's 2 PB
+// columns (rows >= the panel) are copied into W[j][r] (leading dimension
+// ldw = msz | 1); its pairs are eliminated one after another by all threads of
+// the block, each pair forming the multipliers of every row below it (into
+// Lp[j][r] and Lout) and updating the panel's remaining columns, one barrier
+// per pair; then the trailing matrix receives one rank-2PB update, in 4 x 4
+// register tiles, from the multipliers Lp and the unscaled columns W.  The
+// arithmetic of every entry, and its order, is that of the pair-by-pair
+// elimination: the pivot inverse ia = d / det, ib = -b / det, id = a / det;
+// multipliers l0 = x0 ia + x1 ib, l1 = x0 ib + x1 id; panel entries updated
+// pair by pair; trailing entries by the sum over the panel's 2 PB columns in
+// ascending order, subtracted once.
+// L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
+// Dout[3 q]; pivot inertia is counted by thread 0.  The trailing block (rows
+// and columns >= 2 npairs) is left in A.
+constexpr int PB = 8;
+constexpr int PW = 2 * PB;   // columns of a panel
+
+__host__ __device__ inline int panel_ld(int msz) { return msz | 1; }
+
 template <typename T>
-__device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict__ Lout, int lds,
-                               T* __restrict__ Dout, T* Lp, T* Up, int& pos, int& neg, int& zero) {
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
+__device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__ Lout, int lds,
+                                      T* __restrict__ Dout, T* Lp, T* W, int& pos, int& neg,
+                                      int& zero) {
+  const int tid = threadIdx.x, nt = blockDim.x, ldw = panel_ld(msz);
   for (int q0 = 0; q0 < npairs; q0 += PB) {
     const int pe = min(q0 + PB, npairs);
-    const int cend = 2 * pe;
-    // panel: warp 0 alone, warp-synchronous
-    if (warp == 0) {
-      for (int q = q0; q < pe; ++q) {
-        const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
-        const T a = A[c0 * ld + c0], b = A[c1 * ld + c0], d = A[c1 * ld + c1];
-        const T det = fma(a, d, -(b * b));
-        T ia, ib, id;
-        if (det != T(0) && isfinite(det)) {
-          const T inv = T(1) / det;
-          ia = d * inv; ib = -b * inv; id = a * inv;
-        } else {
-          ia = ib = id = T(0);
-        }
-        for (int r = c1 + 1 + lane; r < msz; r += 32) {
-          const T x0 = A[r * ld + c0], x1 = A[r * ld + c1];
-          const T l0 = fma(x0, ia, x1 * ib);
-          const T l1 = fma(x0, ib, x1 * id);
-          Up[r * PLD + kk] = x0; Up[r * PLD + kk + 1] = x1;
-          Lp[r * PLD + kk] = l0; Lp[r * PLD + kk + 1] = l1;
-          Lout[(size_t)c0 * lds + r] = l0;
-          Lout[(size_t)c1 * lds + r] = l1;
-        }
-        if (lane == 0) {
-          Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
-          pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
-        }
-        __syncwarp();
-        // remaining panel columns c in (c1, cend), rows r >= c
-        if (c1 + 1 < cend)
-          for (int r = c1 + 1 + lane; r < msz; r += 32) {
-            const T l0 = Lp[r * PLD + kk], l1 = Lp[r * PLD + kk + 1];
-            T* Ar = A + (size_t)r * ld;
-            const int cmax = min(cend - 1, r);
-            for (int c = c1 + 1; c <= cmax; ++c)
-              Ar[c] = fma(-l1, Up[c * PLD + kk + 1], fma(-l0, Up[c * PLD + kk], Ar[c]));
-          }
-        __syncwarp();
-      }
+    const int cp = 2 * q0, cend = 2 * pe, K = cend - cp, rows = msz - cp;
+    // panel columns cp .. cend-1 for rows >= cp (the lower triangle; the
+    // entries above the diagonal are never read)
+    for (int idx = tid; idx < K * rows; idx += nt) {
+      const int r = cp + idx / K, j = idx - (r - cp) * K, c = cp + j;
+      if (c <= r) W[j * ldw + r] = A[tri_at(r, c)];
     }
     __syncthreads();
-    // trailing rank-2PB update of rows / columns >= cend (lower part), all warps
-    const int K = 2 * (pe - q0);
+    for (int q = q0; q < pe; ++q) {
+      const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
+      const T a = W[kk * ldw + c0], b = W[kk * ldw + c1], d = W[(kk + 1) * ldw + c1];
+      const T det = fma(a, d, -(b * b));
+      T ia, ib, id;
+      if (det != T(0) && isfinite(det)) {
+        const T inv = T(1) / det;
+        ia = d * inv; ib = -b * inv; id = a * inv;
+      } else {
+        ia = ib = id = T(0);
+      }
+      if (tid == 0) {
+        Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
+        pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
+      }
+      for (int r = c1 + 1 + tid; r < msz; r += nt) {
+        const T x0 = W[kk * ldw + r], x1 = W[(kk + 1) * ldw + r];
+        const T l0 = fma(x0, ia, x1 * ib);
+        const T l1 = fma(x0, ib, x1 * id);
+        Lp[kk * ldw + r] = l0;
+        Lp[(kk + 1) * ldw + r] = l1;
+        Lout[(size_t)c0 * lds + r] = l0;
+        Lout[(size_t)c1 * lds + r] = l1;
+        // remaining panel columns c in (c1, cend), c <= r
+        const int cmax = min(cend - 1, r);
+        for (int c = c1 + 1; c <= cmax; ++c) {
+          T& w = W[(c - cp) * ldw + r];
+          w = fma(-l1, W[(kk + 1) * ldw + c], fma(-l0, W[kk * ldw + c], w));
+        }
+      }
+      __syncthreads();
+    }
+    // trailing rank-K update of rows / columns >= cend (lower part)
     const int Tn = msz - cend;
     if (Tn > 0) {
-      const int nt = (Tn + 3) >> 2;
-      const int ntiles = nt * (nt + 1) / 2;
-      for (int t = tid; t < ntiles; t += FBS) {
+      const int ntr = (Tn + 3) >> 2;
+      const int ntiles = ntr * (ntr + 1) / 2;
+      for (int t = tid; t < ntiles; t += nt) {
         int ti, tj;
         tri_tile(t, ti, tj);
         const int r0 = cend + 4 * ti, cb = cend + 4 * tj;
@@ -129,8 +142,8 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
           T lr[4], uc[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            lr[u] = (r0 + u < msz) ? Lp[(r0 + u) * PLD + k] : T(0);
-            uc[u] = (cb + u < msz) ? Up[(cb + u) * PLD + k] : T(0);
+            lr[u] = (r0 + u < msz) ? Lp[k * ldw + r0 + u] : T(0);
+            uc[u] = (cb + u < msz) ? W[k * ldw + cb + u] : T(0);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -144,7 +157,7 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const int c = cb + v;
-            if (c <= r && c < msz) A[r * ld + c] -= acc[u][v];
+            if (c <= r) A[tri_at(r, c)] -= acc[u][v];
           }
         }
       }
@@ -153,99 +166,103 @@ __device__ void pair_eliminate(T* A, int ld, int msz, int npairs, T* __restrict_
   }
 }
 
-// Entry (a, b), a >= b, of element e's bordered KKT block in local order.
-__device__ inline double elem_entry(const DevProb& P, const DevEval& E, int e, int a, int b,
-                                    const double* __restrict__ sigma, double dw, double dc) {
-  const int n = P.n, m = P.m, p = P.p;
-  if (a >= m) {
-    if (b >= m) return 0.0;
-    const int q = a - m;
-    const int pr = b >> 1, g = pr / n, s = pr - g * n;
-    if ((b & 1) == 0) {
-      const int j = grp_point(g);
-      return j >= 1 ? E.Wzt[(((size_t)e * KC + (j - 1)) * n + s) * p + q] : 0.0;
-    }
-    const int k = grp_con(g);
-    return k >= 1 ? E.JT[(((size_t)e * KC + (k - 1)) * n + s) * p + q] : 0.0;
-  }
-  const int pa = a >> 1, ga = pa / n, sa = pa - ga * n;
-  const int pb = b >> 1, gb = pb / n, sb = pb - gb * n;
-  const bool adual = a & 1, bdual = b & 1;
-  if (!adual && !bdual) {
-    const int ja = grp_point(ga), jb = grp_point(gb);
-    double v = 0.0;
-    if (sa == sb) v += E.Wobj[(((size_t)e * n + sa) * NP + ja) * NP + jb];
-    if (ja == jb && ja >= 1) v += E.Wzz[(((size_t)e * KC + (ja - 1)) * n + sa) * n + sb];
-    if (a == b) v += (sigma ? sigma[((size_t)e * NP + ja) * n + sa] : 0.0) + dw;
-    return v;
-  }
-  if (adual && bdual) return a == b ? -dc : 0.0;
-  int kd, sd, jp, sp;
-  if (adual) { kd = grp_con(ga); sd = sa; jp = grp_point(gb); sp = sb; }
-  else { kd = grp_con(gb); sd = sb; jp = grp_point(ga); sp = sa; }
-  if (kd == 0) return (jp == 0 && sd == sp) ? 1.0 : 0.0;
-  double v = (sd == sp) ? P.D[kd][jp] : 0.0;
-  if (jp == kd) v += E.JZ[(((size_t)e * KC + (kd - 1)) * n + sd) * n + sp];
-  return v;
+// Storage of a block of msz rows factored by pair_eliminate_packed: the two
+// panel buffers Lp, W (PW x panel_ld(msz) each) and the packed triangle
+// (msz (msz + 1) / 2).  Everything in shared memory when it fits the
+// factorization limit; otherwise the triangle in a per-CUDA-block global slab
+// (L2-resident) and the panel buffers in shared memory, or, when even they do
+// not fit, in the slab behind the triangle.
+template <typename T>
+__host__ __device__ inline size_t big_panel_elems(int msz) { return 2 * (size_t)PW * panel_ld(msz); }
+__host__ __device__ inline size_t big_tri_elems(int msz) {
+  return ((size_t)msz * (msz + 1) / 2 + 1) & ~size_t(1);
 }
-
-__host__ __device__ inline int odd_ld(int m) { return (m & 1) ? m : m + 1; }
-
-// Where pair_eliminate works on a block of msz rows that does not fit in shared
-// memory: the block itself in a per-CUDA-block global slab (L2-resident), and
-// its two panel buffers Lp, Up (msz x PLD each) in shared memory when they fit
-// the factorization limit, otherwise in the slab behind the block.
 template <typename T>
 __host__ __device__ inline bool panel_in_global(int msz) {
-  return sizeof(T) * 2 * (size_t)msz * PLD > FACTOR_SMEM_LIMIT;
+  return sizeof(T) * big_panel_elems<T>(msz) > FACTOR_SMEM_LIMIT;
 }
 template <typename T>
 __host__ __device__ inline size_t slab_elems(int msz) {
-  return (size_t)odd_ld(msz) * msz + (panel_in_global<T>(msz) ? 2 * (size_t)msz * PLD : 0);
+  return big_tri_elems(msz) + (panel_in_global<T>(msz) ? big_panel_elems<T>(msz) : 0);
 }
+template <typename T>
+struct BigPlace {
+  T* A;
+  T* Lp;
+  T* W;
+};
+// Pointers of block storage for this CUDA block (full: all in shared memory).
+template <typename T>
+__device__ inline BigPlace<T> big_place(unsigned char* smraw, T* work, int msz, bool full) {
+  const size_t pn = (size_t)PW * panel_ld(msz);
+  T* slab = work + (size_t)blockIdx.x * slab_elems<T>(msz);
+  const bool pg = !full && panel_in_global<T>(msz);
+  T* Lp = pg ? slab + big_tri_elems(msz) : reinterpret_cast<T*>(smraw);
+  T* A = full ? Lp + 2 * pn : slab;
+  return {A, Lp, Lp + pn};
+}
+
+// Scatter assembly of element e's KKT block (packed lower triangle blk, zeroed)
+// from its FP64 derivative blocks Wzz, JZ (3 n^2), Wzt, JT (3 n p), Wobj
+// (16 n) and the barrier diagonal sig (4 n, or NULL: zero), which may be in
+// shared or global memory.  Three passes separated by barriers over the nt
+// threads of the block: disjoint entries (point Hessian blocks, the identity
+// parts of the collocation rows D[k][j], continuity / initial rows, -delta_c,
+// border), sums onto those (objective blocks, -h df/dz), then the diagonal.
+template <typename T>
+__device__ inline void elem_scatter(const DevProb& P, const double* Wzz, const double* JZ,
+                                    const double* Wzt, const double* JT, const double* Wobj,
+                                    const double* sig, double dw, double dc, T* blk);
 
 // ---- 1. element condensation --------------------------------------------------
 // One CUDA block condenses element e: assemble the bordered (8n + p) block,
 // eliminate the 3n interior pairs, write L, pivots, the 2n x 2n interface
-// block, its border, the p x p Schur contribution and the coupling -I.
+// block, its border, the p x p Schur contribution and the coupling -I.  For
+// blocks above the register-tile limit (elem_factor_rt below).
 template <typename T>
-__device__ void elem_factor_one(const DevProb& P, const DevEval& E,
+__device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                                 const double* __restrict__ sigma, double dw, double dc,
-                                const DevFactor<T>& F, int e, T* A, T* Lp, T* Up) {
-  const int n = P.n, p = P.p, m = P.m, ext = P.ext, ld = odd_ld(ext);
-  const int tid = threadIdx.x;
+                                const DevFactor<T>& F, int e, const BigPlace<T>& pl) {
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nint = 3 * n;          // interior pairs
   const int i0 = 2 * nint;         // first interface row (6n)
-  for (int a = tid >> 5; a < ext; a += FTY)
-    for (int b = tid & 31; b <= a; b += 32)
-      A[a * ld + b] = (T)elem_entry(P, E, e, a, b, sigma, dw, dc);
+  const size_t nn = (size_t)n * n, np = (size_t)n * p;
+  T* A = pl.A;
+  const int ntri = ext * (ext + 1) / 2;
+  for (int i = tid; i < ntri; i += nt) A[i] = T(0);
   __syncthreads();
+  elem_scatter<T>(P, E.Wzz + (size_t)e * 3 * nn, E.JZ + (size_t)e * 3 * nn,
+                  E.Wzt + (size_t)e * 3 * np, E.JT + (size_t)e * 3 * np,
+                  E.Wobj + (size_t)e * 16 * n, sigma ? sigma + (size_t)e * 4 * n : nullptr, dw,
+                  dc, A);
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate<T>(A, ld, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                    F.Del + (size_t)e * nint * 3, Lp, Up, pos, neg, zero);
+  pair_eliminate_packed<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+                           F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
   }
   const int n2 = 2 * n;
+  auto tr = [&](int a, int b) { return a >= b ? A[tri_at(a, b)] : A[tri_at(b, a)]; };
   T* Aif = F.Aif + (size_t)e * n2 * n2;
-  for (int idx = tid; idx < n2 * n2; idx += FBS) {
+  for (int idx = tid; idx < n2 * n2; idx += nt) {
     const int u = idx / n2, v = idx - u * n2;
-    Aif[idx] = u >= v ? A[(i0 + u) * ld + i0 + v] : A[(i0 + v) * ld + i0 + u];
+    Aif[idx] = tr(i0 + u, i0 + v);
   }
   T* Bif = F.Bif + (size_t)e * n2 * p;
-  for (int idx = tid; idx < n2 * p; idx += FBS) {
+  for (int idx = tid; idx < n2 * p; idx += nt) {
     const int u = idx / p, q = idx - u * p;
-    Bif[idx] = A[(m + q) * ld + i0 + u];
+    Bif[idx] = A[tri_at(m + q, i0 + u)];
   }
   double* Sc = F.Scon + (size_t)e * p * p;
-  for (int idx = tid; idx < p * p; idx += FBS) {
+  for (int idx = tid; idx < p * p; idx += nt) {
     const int q = idx / p, q2 = idx - q * p;
-    Sc[idx] = (double)(q >= q2 ? A[(m + q) * ld + m + q2] : A[(m + q2) * ld + m + q]);
+    Sc[idx] = (double)tr(m + q, m + q2);
   }
   T* C = F.Cpl + (size_t)e * n * n;
-  for (int idx = tid; idx < n * n; idx += FBS) {
-    const int s = idx / n, t = idx - s * n;
-    C[idx] = (e > 0 && s == t) ? T(-1) : T(0);
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int s2 = idx / n, t = idx - s2 * n;
+    C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
   }
   __syncthreads();
 }
@@ -255,13 +272,9 @@ __global__ void __launch_bounds__(FBS)
 k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
               DevFactor<T> F, int use_smem) {
   extern __shared__ unsigned char smraw[];
-  const int ext = P.ext, ld = odd_ld(ext);
-  T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(ext);
-  T* Lp = (!use_smem && panel_in_global<T>(ext)) ? slab + (size_t)ld * ext : reinterpret_cast<T*>(smraw);
-  T* Up = Lp + (size_t)ext * PLD;
-  T* A = use_smem ? (Up + (size_t)ext * PLD) : slab;
+  const BigPlace<T> pl = big_place<T>(smraw, F.work, P.ext, use_smem != 0);
   for (int e = blockIdx.x; e < P.N; e += gridDim.x)
-    elem_factor_one<T>(P, E, sigma, dw, dc, F, e, A, Lp, Up);
+    elem_factor_big<T>(P, E, sigma, dw, dc, F, e, pl);
 }
 
 // ---- 1'. pair elimination with the block held in registers -------------------------
@@ -560,7 +573,6 @@ template <typename T>
 __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
   return elem_blk_bytes<T>(P) + sizeof(double) * elem_raw_doubles(P);
 }
-__device__ inline int tri_at(int r, int c) { return r * (r + 1) / 2 + c; }
 // i / d and i % d for 0 <= i < 2^22 and 1 <= d <= 4096 through the float
 // reciprocal inv = 1 / d: (i + 0.5) / d lies at least 0.5 / d from an integer,
 // far more than the float rounding of the product, so the truncation is exact.
@@ -574,7 +586,7 @@ __device__ inline int loc_state(int j, int s, int n) {
 }
 __device__ inline int loc_dual(int k, int s, int n) { return 2 * ((k == 0 ? 3 : k - 1) * n + s) + 1; }
 
-// Element condensation (same elimination as elem_factor_one) with
+// Element condensation (same elimination as elem_factor_big) with
 // pair_eliminate_rt over the nt threads of the block.
 // Assembly of element e's KKT block (packed lower triangle in `blk`, shared
 // memory) from its derivative blocks.  Kept out of line: inlined, it changes
@@ -584,11 +596,9 @@ template <typename T>
 __device__ __noinline__ void elem_assemble_rt(const DevProb& P, const DevEval& E,
                                               const double* __restrict__ sigma, double dw,
                                               double dc, int e, T* blk) {
-  const int n = P.n, p = P.p, m = P.m, ext = P.ext;
+  const int n = P.n, p = P.p, ext = P.ext;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nn = n * n, np = n * p, ntri = ext * (ext + 1) / 2;
-  auto put = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] = v; };
-  auto add = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] += v; };
   // the derivative blocks arrive by asynchronous copies issued all at once
   // (one memory latency per element) while the triangle is cleared
   double* Wzz = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(blk) +
@@ -615,6 +625,18 @@ __device__ __noinline__ void elem_assemble_rt(const DevProb& P, const DevEval& E
   for (int i = tid; i < ntri; i += nt) blk[i] = T(0);
   cp_async_wait_all();
   __syncthreads();
+  elem_scatter<T>(P, Wzz, JZ, Wzt, JT, Wobj, sig, dw, dc, blk);
+}
+
+template <typename T>
+__device__ inline void elem_scatter(const DevProb& P, const double* Wzz, const double* JZ,
+                                    const double* Wzt, const double* JT, const double* Wobj,
+                                    const double* sig, double dw, double dc, T* blk) {
+  const int n = P.n, p = P.p, m = P.m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nn = n * n, np = n * p;
+  auto put = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] = v; };
+  auto add = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] += v; };
   // 1. disjoint entries: point Hessian blocks, the identity parts of the
   //    collocation rows (D[k][j]), continuity / initial rows, -delta_c, border
   const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
@@ -657,7 +679,7 @@ __device__ __noinline__ void elem_assemble_rt(const DevProb& P, const DevEval& E
   for (int i = tid; i < 4 * n; i += nt) {
     const int j = quot(i, n, inv_n), s2 = i - j * n;
     const int a = loc_state(j, s2, n);
-    add(a, a, (T)(sig[i] + dw));
+    add(a, a, (T)((sig ? sig[i] : 0.0) + dw));
   }
   __syncthreads();
 }
@@ -707,7 +729,7 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
 
 // Tile pairs per thread of elem_factor_rt (1) and its block size for an element
 // of size ext (a multiple of 32 threads covering every tile; 0 when the
-// element is too large and elem_factor_one is used).
+// element is too large and elem_factor_big is used).
 template <typename T>
 __host__ __device__ constexpr int rt_tpt() { return 1; }   // tile pairs per thread
 template <typename T>
@@ -739,10 +761,10 @@ k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double 
 // Local order of the extended block: [interface of block i (2n) | z3 of the
 // left neighbour (n) | c0 of the right neighbour (n) | theta (p)].
 template <typename T>
-__device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stride,
-                               int final_level, int bi, T* A, T* Lp, T* Up) {
-  const int n = P.n, p = P.p, N = P.N, bext = P.bext, ld = odd_ld(bext), n2 = 2 * n;
-  const int tid = threadIdx.x;
+__device__ void bcr_factor_big(const DevProb& P, const DevFactor<T>& F, int stride,
+                               int final_level, int bi, const BigPlace<T>& pl) {
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
   const int R = (!final_level && i + stride < N) ? i + stride : -1;
@@ -750,7 +772,8 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
   const T* Ci = F.Cpl + (size_t)i * n * n;
   const T* CR = R >= 0 ? F.Cpl + (size_t)R * n * n : nullptr;
   const T* Bi = F.Bif + (size_t)i * n2 * p;
-  for (int a = tid >> 5; a < bext; a += FTY)
+  T* A = pl.A;
+  for (int a = tid >> 5; a < bext; a += nt >> 5)
     for (int b = tid & 31; b <= a; b += 32) {
       T v = T(0);
       if (a < n2) {
@@ -764,55 +787,53 @@ __device__ void bcr_factor_one(const DevProb& P, const DevFactor<T>& F, int stri
           v = Bi[b * p + (a - 4 * n)];
         }
       }
-      A[a * ld + b] = v;
+      A[tri_at(a, b)] = v;
     }
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate<T>(A, ld, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
-                    F.Db + (size_t)i * n * 3, Lp, Up, pos, neg, zero);
+  pair_eliminate_packed<T>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
+                           F.Db + (size_t)i * n * 3, pl.Lp, pl.W, pos, neg, zero);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
     in[0] = pos; in[1] = neg; in[2] = zero;
   }
   // scatter the trailing (Schur) block into the neighbours
+  auto tr = [&](int a, int b) { return a >= b ? A[tri_at(a, b)] : A[tri_at(b, a)]; };
   if (L >= 0) {
     T* AL = F.Aif + (size_t)L * n2 * n2;
-    for (int idx = tid; idx < n * n; idx += FBS) {
+    for (int idx = tid; idx < n * n; idx += nt) {
       const int t = idx / n, t2 = idx - t * n;
-      const int ra = n2 + t, rb = n2 + t2;
-      AL[(2 * t) * n2 + 2 * t2] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
+      AL[(2 * t) * n2 + 2 * t2] += tr(n2 + t, n2 + t2);
     }
     T* BL = F.Bif + (size_t)L * n2 * p;
-    for (int idx = tid; idx < n * p; idx += FBS) {
+    for (int idx = tid; idx < n * p; idx += nt) {
       const int t = idx / p, q = idx - t * p;
-      BL[(2 * t) * p + q] += A[(4 * n + q) * ld + n2 + t];
+      BL[(2 * t) * p + q] += A[tri_at(4 * n + q, n2 + t)];
     }
   }
   if (R >= 0) {
     T* AR = F.Aif + (size_t)R * n2 * n2;
     T* CRw = F.Cpl + (size_t)R * n * n;
-    for (int idx = tid; idx < n * n; idx += FBS) {
-      const int s = idx / n, s2 = idx - s * n;
-      const int ra = 3 * n + s, rb = 3 * n + s2;
-      AR[(2 * s + 1) * n2 + 2 * s2 + 1] += ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra];
-      CRw[idx] = (L >= 0) ? A[(3 * n + s) * ld + n2 + s2] : T(0);
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int s2 = idx / n, s3 = idx - s2 * n;
+      AR[(2 * s2 + 1) * n2 + 2 * s3 + 1] += tr(3 * n + s2, 3 * n + s3);
+      CRw[idx] = (L >= 0) ? A[tri_at(3 * n + s2, n2 + s3)] : T(0);
     }
     T* BR = F.Bif + (size_t)R * n2 * p;
-    for (int idx = tid; idx < n * p; idx += FBS) {
-      const int s = idx / p, q = idx - s * p;
-      BR[(2 * s + 1) * p + q] += A[(4 * n + q) * ld + 3 * n + s];
+    for (int idx = tid; idx < n * p; idx += nt) {
+      const int s2 = idx / p, q = idx - s2 * p;
+      BR[(2 * s2 + 1) * p + q] += A[tri_at(4 * n + q, 3 * n + s2)];
     }
   }
   double* Sc = F.Scon + (size_t)(N + i) * p * p;
-  for (int idx = tid; idx < p * p; idx += FBS) {
+  for (int idx = tid; idx < p * p; idx += nt) {
     const int q = idx / p, q2 = idx - q * p;
-    const int ra = 4 * n + q, rb = 4 * n + q2;
-    Sc[idx] = (double)(ra >= rb ? A[ra * ld + rb] : A[rb * ld + ra]);
+    Sc[idx] = (double)tr(4 * n + q, 4 * n + q2);
   }
   __syncthreads();
 }
 
-// Cyclic-reduction block (same result as bcr_factor_one) with
+// Cyclic-reduction block (same result as bcr_factor_big) with
 // pair_eliminate_rt on one half (128 threads) of the block: tid in [0, 128).
 // Its inputs are first staged in `stage` (T elements, bcr_stage_elems):
 // the block's interface block [2n][2n], its coupling [n][n], the right
@@ -937,7 +958,7 @@ __device__ void bcr_factor_rt(const DevProb& P, const DevFactor<T>& F, int strid
   bcr_factor_staged<T, TPT>(P, F, stride, final_level, bi, tid, bar, ub, stage, pivs, cnt);
 }
 
-// Tiles per thread of bcr_factor_rt for P (single tiles; 0: use bcr_factor_one).
+// Tiles per thread of bcr_factor_rt for P (single tiles; 0: use bcr_factor_big).
 __host__ __device__ inline int bcr_rt_tiles(int bext) {
   const int R = (bext + 3) >> 2;
   if (R > RT_MAX_TR) return 0;
@@ -965,14 +986,9 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
       bcr_factor_rt<T, BT>(P, F, stride, final_level, bi, threadIdx.x & 127, HalfBar{1 + half},
                            ub[half].v, stage, pivs[half], cnt[half]);
   } else {
-    const int bext = P.bext, ld = odd_ld(bext);
-    T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(bext);
-    T* Lp = (!use_smem && panel_in_global<T>(bext)) ? slab + (size_t)ld * bext
-                                                    : reinterpret_cast<T*>(smraw);
-    T* Up = Lp + (size_t)bext * PLD;
-    T* A = use_smem ? (Up + (size_t)bext * PLD) : slab;
+    const BigPlace<T> pl = big_place<T>(smraw, F.work, P.bext, use_smem != 0);
     for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-      bcr_factor_one<T>(P, F, stride, final_level, bi, A, Lp, Up);
+      bcr_factor_big<T>(P, F, stride, final_level, bi, pl);
   }
 }
 
@@ -1522,13 +1538,8 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
     if (flags[k] & 4) continue;   // condensed by k_elem_factor_rt_b
     const DevInst& I = insts[act[k]];
     const DevFactor<T>& F = inst_factor<T>(I);
-    const int ext = I.P.ext, ld = odd_ld(ext);
-    const bool sm = flags[k] & 1;
-    T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(ext);
-    T* Lp = (!sm && panel_in_global<T>(ext)) ? slab + (size_t)ld * ext : reinterpret_cast<T*>(smraw);
-    T* Up = Lp + (size_t)ext * PLD;
-    T* Am = sm ? (Up + (size_t)ext * PLD) : slab;
-    elem_factor_one<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], Am, Lp, Up);
+    const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, (flags[k] & 1) != 0);
+    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl);
   }
   grid_barrier(gb, ep);
   // 2. cyclic-reduction levels, then each instance's final block
@@ -1585,15 +1596,9 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       if (BT > 0 && (flags[k] & 8)) continue;
       const DevInst& I = insts[act[k]];
       const DevFactor<T>& F = inst_factor<T>(I);
-      const int bext = I.P.bext, ld = odd_ld(bext);
-      const bool sm = flags[k] & 2;
-      T* slab = F.work + (size_t)blockIdx.x * slab_elems<T>(bext);
-      T* Lp = (!sm && panel_in_global<T>(bext)) ? slab + (size_t)ld * bext
-                                                : reinterpret_cast<T*>(smraw);
-      T* Up = Lp + (size_t)bext * PLD;
-      T* Am = sm ? (Up + (size_t)bext * PLD) : slab;
-      if (fin) bcr_factor_one<T>(I.P, F, 1, 1, 0, Am, Lp, Up);
-      else bcr_factor_one<T>(I.P, F, 1 << lv, 0, t - pre[k], Am, Lp, Up);
+      const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.bext, (flags[k] & 2) != 0);
+      if (fin) bcr_factor_big<T>(I.P, F, 1, 1, 0, pl);
+      else bcr_factor_big<T>(I.P, F, 1 << lv, 0, t - pre[k], pl);
     }
     grid_barrier(gb, ep);
   }
@@ -1722,8 +1727,8 @@ int bcr_levels(int N) {
 // are in the slab too).
 template <typename T>
 static size_t panel_smem(int msz, bool full) {
-  const size_t panel = sizeof(T) * 2 * (size_t)msz * PLD;
-  if (full) return panel + sizeof(T) * (size_t)odd_ld(msz) * msz;
+  const size_t panel = sizeof(T) * big_panel_elems<T>(msz);
+  if (full) return panel + sizeof(T) * big_tri_elems(msz);
   return panel_in_global<T>(msz) ? 0 : panel;
 }
 template <typename T>

@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 
 OUT = os.path.join(HERE, "oracle_optima_large.json")
 TOL = 1e-8
+CHECK_BACK = 5
 
 
 def cases():
@@ -64,13 +65,20 @@ def solve_case(name):
     inst = make()
     t0 = time.time()
     res = ipm.solve(inst, opt=ipm.Options(tol=TOL))
+    extra = {}
+    if res.status not in (ipm.SUCCESS, ipm.ACCEPTABLE) and res.iterations > 1:
+        # a failed solve's last steps are taken near alpha_min, where rounding
+        # decides ties in the filter tests: the parity point is the iterate
+        # CHECK_BACK iterations before the failure
+        m = max(1, res.iterations - CHECK_BACK)
+        extra = {"checkpoint_iter": m, "checkpoint_theta": res.history[m - 1]["theta"].tolist()}
     return {
         "cite": "Eq. 2 NLP solved by the filter line-search interior-point method "
                 "(Introduction; tolerances of Section \"Optimization framework configurations\")",
         "description": desc, "instance": inst.name, "n": inst.n, "p": inst.p, "N": inst.N,
         "tol": TOL, "status": int(res.status), "iterations": int(res.iterations),
         "theta": res.x[-inst.p:].tolist(), "phi": float(res.phi),
-        "kkt_error": float(res.kkt_error), "cpu_seconds": round(time.time() - t0, 1)}
+        "kkt_error": float(res.kkt_error), "cpu_seconds": round(time.time() - t0, 1), **extra}
 
 
 def merge(name, rec):
