@@ -1,31 +1,37 @@
 #!/usr/bin/env python
 """Benchmark of the GPU Radau-collocation interior-point path.
 
-Workload: the 10-species / 20-reaction random mass-action network on
-N = 400 Radau elements (K = 3), 4 observed species x 50 times, T = 20,
-seed 3 (``workloads.config2()``): 16 020 primal unknowns, 16 000 constraints,
-20 log10 rate constants, solved from Q seeded starting points
-theta_true + U[-0.1, 0.1] (a multistart run; ``--queue``, default 256).
+Workload (the uneven multistart batch at its stated size,
+``workloads.multistart_batch()``): 256 seeded mass-action networks, species
+n ~ U{5..50}, reactions r = 2n (all rate constants estimated, p = 2n),
+N log-uniform on [100, 2000] Radau elements (K = 3), 4 observed species x 50
+times, T = 20, starts theta0 within +-1 decade of the true log10 rate
+constants: 40.2 M KKT unknowns in all, 157 k per instance on average.
 
-A timed step serves the Q starts through the continuous-batching server
-(``collo_server_*``) with ``--slots`` (default 64) slots: all Q are submitted
-at once, admitted as slots free up (in groups of ``--admit``), and every
-server step advances all admitted solves by one Newton step in batched
-launches, in the mixed-precision path (FP32 element factorization and block
-cyclic reduction, FP64 parameter Schur complement, residuals and refinement,
-FP64 factorization where refinement from FP32 fails).  ``value`` = Newton steps per second over
-all Q solves.  Beside it: one lock-step batch of ``--slots`` starts (no
-refill), the same path and the plain FP64 path on a single instance,
-per-solve latency percentiles, the parameter agreement with FP64 solves, an
-end-to-end number through host buffers, the dominant kernel's roofline and
-the CPU oracle.  Between timed steps the L2 cache is flushed (256 MiB write).
+The instances are served through the continuous-batching server
+(``collo_server_*``) with ``--slots`` slots (default 64) inside a device-memory
+budget (default 180 GiB), in the mixed-precision path (FP32 element and
+cyclic-reduction factors, FP64 parameter Schur complement, residuals and
+refinement, FP64 factorization where refinement from FP32 fails), every solve
+to KKT tolerance 1e-8.  Every instance that reaches a final status is
+submitted again from the same start, so the server runs a steady multistart
+stream.  One benchmark step is ``--slice`` server steps (default 8), each
+advancing every admitted solve by one Newton step in batched launches;
+``value`` = Newton steps per second over all solves.  Beside it: solves that
+reached a final status per second (all, and converged), their service-time
+percentiles, the plain FP64 single-instance path on a stratified subsample of
+the same instances, the parameter agreement of converged served solves with
+FP64 solves of the same starts, per-kernel timings and rooflines, an
+end-to-end number through host buffers, the previous config-2 multistart
+workload, a Poisson stream of the serving-stream shape, and the CPU oracle.
 
 ``--impl reference`` times the CPU oracle instead (a bounded sample: each step
-is the oracle's initial point plus two Newton iterations of one instance).
+is the oracle's initial point plus two Newton iterations of one instance of
+the batch).
 
-Multi-GPU (torchrun, one process per GPU): each rank serves its own queue
-with no collective on the data path (weak scaling); the timed region is
-bracketed by barriers and the slowest rank's time is used.
+Multi-GPU (torchrun, one process per GPU): each rank serves its own copy of
+the stream with no collective on the data path (weak scaling); the timed
+region is bracketed by barriers and the slowest rank's time is used.
 """
 from __future__ import annotations
 
@@ -39,23 +45,31 @@ import sys
 import tempfile
 import time
 
+# the oracle (cpu_baseline and the reference arm) makes thousands of small
+# LAPACK calls; one BLAS thread is its fastest setting here
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = ("massaction_n10_r20_N400_K3 x {Q} multistart solves served with {S} slots "
-            "(config 2: 10 species, 20 reactions, N=400, T=20, seed 3; "
-            "starts theta_true + U[-0.1,0.1])")
-METRIC = "Newton steps/s (mixed-precision continuous-batching IPM path, config 2 multistart)"
+WORKLOAD = ("uneven multistart batch at its stated size: 256 mass-action networks, "
+            "n ~ U{{5..50}} species, r = p = 2n, N log-uniform [100, 2000], K = 3, "
+            "4 observed x 50 times, T = 20, starts within +-1 decade (seed 1004); served "
+            "as a steady multistart stream (finished instances resubmitted) through {S} "
+            "slots within a {B} GiB device-memory budget")
+METRIC = ("Newton steps/s (mixed-precision continuous-batching IPM path, uneven multistart "
+          "batch at its stated size)")
 # KKT tolerance of every solve in the benchmark: at the paper's 1e-6 the mixed
 # and FP64 paths stop at points up to 4e-3 apart in rate constants along flat
 # directions of the objective (same iterations, same objective to 1e-12); at
 # 1e-8 they agree within the 1e-6 parameter criterion.
 TOL = 1e-8
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# element-condensation launch over 64 config-2 instances, from an ncu capture
-# of that launch (--only-elem-phase --slots 64); None once the kernel changes.
-ELEM_TRAFFIC_S64 = 1.0576e9
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel over the first 64 instances of the batch at their initial points,
+# from one ncu capture of that launch (--only-phase); None until captured or
+# once the kernel changes.
+TRAFFIC_C4_64 = {}
 
 
 def parse_args():
@@ -64,25 +78,26 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--slice", type=int, default=8, help="server steps per benchmark step")
+    ap.add_argument("--admit", type=int, default=16,
+                    help="admit waiting solves in groups of at least this many free slots")
+    ap.add_argument("--budget-gib", type=float, default=180.0)
+    ap.add_argument("--fp64-sample", type=int, default=8,
+                    help="instances of the stratified subsample run on the plain FP64 path")
+    ap.add_argument("--fp64-steps", type=int, default=20,
+                    help="Newton steps of each FP64 single-instance run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the reduced uneven-batch and Poisson-stream measurements")
-    ap.add_argument("--batch", type=int, default=64,
-                    help="instances of --only-batch")
-    ap.add_argument("--slots", type=int, default=64)
-    ap.add_argument("--queue", type=int, default=256)
-    ap.add_argument("--admit", type=int, default=32,
-                    help="admit waiting solves in groups of at least this many free slots")
-    ap.add_argument("--only-solve", choices=["mixed", "fp64"], default=None,
-                    help="run one single-instance solve and exit (for profiler launch lists)")
-    ap.add_argument("--only-batch", action="store_true",
-                    help="run one batched solve and exit (for profiler launch lists)")
-    ap.add_argument("--only-elem-phase", action="store_true",
-                    help="evaluate --slots config-2 problems at their forward-sweep states and "
-                         "launch the batched element condensation twice (ncu capture)")
+                    help="skip the config-2 multistart and Poisson-stream measurements")
+    ap.add_argument("--only-phase", type=int, default=0,
+                    help="time one batched phase (1..7 of collo_batch_time_phase) over the "
+                         "first --slots instances at their initial points and exit (ncu)")
+    ap.add_argument("--only-serve", type=int, default=0,
+                    help="run this many server steps of the stream and exit (ncu launch list)")
     ap.add_argument("--phase-profile", action="store_true",
-                    help="serve the queue twice with the driver's phase profile on and print it")
+                    help="print the driver's per-phase wall time over --slice server steps")
     return ap.parse_args()
 
 
@@ -191,8 +206,13 @@ def _pair_flops(msz: int, pairs: int) -> int:
     return fl
 
 
+def _pair_l_entries(msz: int, pairs: int) -> int:
+    """Entries of the L columns of `pairs` eliminated 2x2 pivots (rows below each pair)."""
+    return sum(2 * (msz - 2 * q - 2) for q in range(pairs))
+
+
 def elem_factor_work(n: int, p: int, N: int, bytes_per: int):
-    """Algorithmic flops and bytes of one element-condensation launch.
+    """Algorithmic flops and bytes of the element condensation of one instance.
 
     Per element: eliminating the 3n interior pairs of the symmetric (8n + p)
     block.  Bytes: FP64 derivative blocks read (jac_z, hess_zz at 3 n^2,
@@ -206,19 +226,38 @@ def elem_factor_work(n: int, p: int, N: int, bytes_per: int):
     return fl * N, (rd + wr) * N
 
 
-def factor_work(n: int, p: int, N: int, bytes_per: int):
-    """Algorithmic flops and bytes of one whole factorization of one instance:
-    element condensation (above), the N eliminations of the cyclic reduction
-    (n pairs of a (4n + p) block each: interface block, neighbour couplings
-    and border read, L columns written), the parameter Schur complement
-    (2N p^2 FP64 contributions summed, p^3/3 for its LDL^T)."""
-    fl_e, by_e = elem_factor_work(n, p, N, bytes_per)
+def reduction_work(n: int, p: int, N: int, bytes_per: int):
+    """Algorithmic flops and bytes of the cyclic reduction and the parameter
+    Schur complement of one instance: N eliminations of n pairs of a (4n + p)
+    block (interface block, two couplings and border read, L columns and pivots
+    written, the neighbours' blocks and borders updated), the 2N p^2 FP64
+    contributions summed and the p^3 / 3 of the Schur block's LDL^T."""
     bext = 4 * n + p
-    fl_b = _pair_flops(bext, n) * N
-    by_b = bytes_per * N * (4 * n * n + 2 * n * n + 2 * n * p + 2 * n * bext + 3 * n)
-    fl_s = p ** 3 // 3 + 2 * N * p * p
-    by_s = 8 * 2 * N * p * p
-    return fl_e + fl_b + fl_s, by_e + by_b + by_s
+    fl = _pair_flops(bext, n) * N + p ** 3 // 3 + 2 * N * p * p
+    by = bytes_per * N * (4 * n * n + 2 * n * n + 2 * n * p + 2 * n * bext + 3 * n
+                          + 2 * (n * n + n * p)) + 8 * 2 * N * p * p
+    return fl, by
+
+
+def solve_bytes(n: int, p: int, N: int, bytes_per: int):
+    """Algorithmic bytes of one solve (no refinement): the used entries of the
+    element and reduction L columns and their pivots read twice (forward and
+    back substitution), the right-hand side read and the solution written in
+    FP64, the per-block intermediate vectors written and read once."""
+    ext, bext = 8 * n + p, 4 * n + p
+    lent = N * (_pair_l_entries(ext, 3 * n) + _pair_l_entries(bext, n))
+    piv = N * 3 * (3 * n + n)
+    nk = 8 * n * N + p
+    inter = N * (6 * n + 2 * n + 2 * n)
+    return 2 * bytes_per * (lent + piv) + 8 * 2 * nk + 2 * bytes_per * inter
+
+
+def eval_bytes(n: int, p: int, N: int):
+    """Algorithmic bytes of one evaluation with derivatives: x and lambda read,
+    constraints, gradient, the Jacobian and Hessian blocks (3 n^2 and 3 n p per
+    element each, 16 n objective entries) and per-element partial sums written."""
+    nk = 8 * n * N + p
+    return 8 * (nk + N * (2 * 3 * n * n + 2 * 3 * n * p + 16 * n + 4 + p))
 
 
 def measured_peaks():
@@ -234,6 +273,55 @@ def rate_rel_err(theta, theta_ref):
     return float(np.max(np.abs(np.expm1(np.log(10.0) * (np.asarray(theta) - theta_ref)))))
 
 
+class Stream:
+    """A steady multistart stream through a server: every instance that
+    reaches a final status is submitted again from the same start.  With
+    `recreate` each resubmission first builds a new problem from the
+    instance's host arrays (and frees the finished one), the end-to-end form."""
+
+    def __init__(self, collo, server, insts, probs, device):
+        self.collo, self.server, self.insts, self.probs = collo, server, insts, probs
+        self.device = device
+        self.recreate = False
+        self.h2d = 0
+        self.d2h = 0
+        self.tk = {server.submit(p): i for i, p in enumerate(probs)}
+
+    def step(self, m):
+        """m server steps; the (instance, result) pairs that finished in them."""
+        fin = []
+        for _ in range(m):
+            self.server.step()
+            for t in list(self.tk):
+                r = self.server.poll(t)
+                if r is None:
+                    continue
+                i = self.tk.pop(t)
+                fin.append((i, r))
+                self.d2h += 8 * self.insts[i].p
+                if self.recreate:
+                    self.probs[i].close()
+                    self.probs[i] = self.collo.Problem(self.insts[i], device=self.device)
+                    self.h2d += host_bytes(self.insts[i])
+                self.tk[self.server.submit(self.probs[i])] = i
+        return fin
+
+
+def host_bytes(inst):
+    """Bytes of an instance's host arrays that collo_problem_create copies to the device."""
+    import numpy as np
+    keep = [inst.react, inst.prod, inst.pidx, inst.kfix, inst.x0, inst.theta_lo, inst.theta_hi,
+            inst.obs_t, inst.obs_s, inst.obs_y, inst.obs_sigma, inst.theta0]
+    return int(sum(np.asarray(a).nbytes for a in keep))
+
+
+def stratified(insts, k):
+    """k instances spread over the batch by the work of one factorization
+    (N (8n + p)^3): the middles of k equal strata of the sorted list."""
+    order = sorted(range(len(insts)), key=lambda i: insts[i].N * (8 * insts[i].n + insts[i].p) ** 3)
+    return [order[int((j + 0.5) * len(order) / k)] for j in range(k)]
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -245,213 +333,249 @@ def run_ours(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     init_dist(world, "nccl")
-    inst = workloads.config2()
-    S, Q = args.slots, args.queue
-    starts = workloads.multistart_thetas(inst, Q, seed=2002 + rank)
-    probs = [collo.Problem(inst, device=local) for _ in range(Q)]
-    server = collo.Server(S, device=local, precision=collo.MIXED, tol=TOL)
+    S, M = args.slots, args.slice
+    budget = int(args.budget_gib * (1 << 30))
+    insts = workloads.multistart_batch()
+    probs = [collo.Problem(i, device=local) for i in insts]
+    server = collo.Server(S, budget_bytes=budget, device=local, precision=collo.MIXED, tol=TOL)
     server.set_admission(args.admit)
     sstream = torch.cuda.ExternalStream(server.stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = Stream(collo, server, insts, probs, local)
 
-    def flush_l2(i):
+    def timed_slice(i):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
-
-    def timed_serve():
+        c0 = server.counters()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(sstream)
-        tickets = [server.submit(p, theta0=th) for p, th in zip(probs, starts)]
-        while True:
-            act, wait = server.step()
-            if act == 0 and wait == 0:
-                break
+        fin = st.step(M)
         e1.record(sstream)
         e1.synchronize()
-        return [server.poll(t) for t in tickets], e0.elapsed_time(e1)
+        c1 = server.counters()
+        return e0.elapsed_time(e1), [b - a for a, b in zip(c0, c1)], fin
 
+    warm_fin = []
     for i in range(args.warmup):
-        flush_l2(i)
-        timed_serve()
+        warm_fin += timed_slice(i)[2]
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     l0 = collo.launch_count()
-    its, ms_list, statuses, lat, last = 0, [], [], [], None
+    ms_list, its, done, conv, fin_all = [], 0, 0, 0, []
     for i in range(args.steps):
-        flush_l2(i)
-        res, ms = timed_serve()
-        its += sum(r["iterations"] for r in res)
+        ms, d, fin = timed_slice(i)
         ms_list.append(ms)
-        statuses += [r["status"] for r in res]
-        lat += [1e3 * r["wall"] for r in res]
-        last = res
+        its += d[0]
+        done += d[1]
+        conv += d[2]
+        fin_all += fin
     launches = collo.launch_count() - l0
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     t_total = reduce_max(sum(ms_list), world)
     its_total = reduce_sum(float(its), world)
-    solves_total = reduce_sum(float(args.steps * Q), world)
-    conv_total = reduce_sum(float(sum(1 for s_ in statuses if s_ in (collo.OK, collo.ACCEPTABLE))),
-                            world)
+    done_total = reduce_sum(float(done), world)
+    conv_total = reduce_sum(float(conv), world)
     value = its_total / (t_total * 1e-3)
-
-    # one lock-step batch of S starts (no refill), on the problems' own streams
-    bstream = torch.cuda.ExternalStream(probs[0].stream)
-    flush_l2(0)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(bstream)
-    bres = collo.batch_solve(probs[:S], theta0s=starts[:S], precision=collo.MIXED, tol=TOL)
-    e1.record(bstream)
-    e1.synchronize()
-    b_ms = e0.elapsed_time(e1)
-    b_its = sum(r["iterations"] for r in bres)
-
-    # single-instance paths on the same GPU: mixed and the plain FP64 path
-    one = probs[0]
-    single = {}
-    for name, prec in [("mixed", collo.MIXED), ("fp64", collo.FP64)]:
-        one.ipm_solve(theta0=starts[0], precision=prec, want_x=False, tol=TOL)
-        ms_s, its_s = [], 0
-        for i in range(3):
-            flush_l2(i)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(bstream)
-            r = one.ipm_solve(theta0=starts[0], precision=prec, want_x=False, tol=TOL)
-            e1.record(bstream)
-            e1.synchronize()
-            ms_s.append(e0.elapsed_time(e1))
-            its_s += r["iterations"]
-        single[name] = {"newton_steps_per_s": its_s / (sum(ms_s) * 1e-3),
-                        "solves_per_s": len(ms_s) / (sum(ms_s) * 1e-3),
-                        "ms_per_solve": sum(ms_s) / len(ms_s)}
-    # parameter agreement of the served mixed solves with single FP64 solves
-    perr, n_cmp = 0.0, 0
-    for j in range(min(8, Q)):
-        if last[j]["status"] not in (collo.OK, collo.ACCEPTABLE):
-            continue
-        r64 = one.ipm_solve(theta0=starts[j], precision=collo.FP64, want_x=False, tol=TOL)
-        if r64["status"] in (collo.OK, collo.ACCEPTABLE):
-            perr = max(perr, rate_rel_err(last[j]["theta"], r64["theta"]))
-            n_cmp += 1
-
-    # phase timings at S instances (CUDA events inside the library)
-    ph = {"factor_fp32": collo.batch_time_phase(probs[:S], 1, collo.MIXED, reps=5),
-          "factor_fp32_elements": collo.batch_time_phase(probs[:S], 4, collo.MIXED, reps=5),
-          "factor_fp32_reduction_schur": collo.batch_time_phase(probs[:S], 5, collo.MIXED, reps=5),
-          "solve_fp32": collo.batch_time_phase(probs[:S], 2, collo.MIXED, reps=5),
-          "eval": collo.batch_time_phase(probs[:S], 3, collo.MIXED, reps=5)}
-    peak32 = collo.alu_peak(collo.MIXED)
-    peak64 = collo.alu_peak(collo.FP64)
-    # dominant kernel: the FP32 element condensation (FP32 FMA bound)
-    fl_e, by_e = elem_factor_work(inst.n, inst.p, inst.N, 4)
-    fl_e *= S
-    by_e *= S
-    ach = fl_e / (ph["factor_fp32_elements"] * 1e-3) / 1e12
-    # ALU peak from the unit counts and the clock: SMs x 128 FP32 lanes x 2 flops
-    # (FMA) x maximum SM clock
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_alu = sms * 128 * 2 * mhz * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
-            "frac": ach / peak_alu,
-            "traffic": ELEM_TRAFFIC_S64 * S / 64 if ELEM_TRAFFIC_S64 else None,
-            "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz; measured "
-                           f"FFMA throughput {peak32:.1f} TFLOP/s (collo_alu_peak)",
-            "kernel": f"k_elem_factor_rt_b<float> (element condensation, {S} instances)",
-            "algorithmic_flops": fl_e, "algorithmic_bytes": by_e,
-            "ms": ph["factor_fp32_elements"],
-            "hbm": {"achieved_gbs": by_e / (ph["factor_fp32_elements"] * 1e-3) / 1e9,
-                    "peak_gbs": measured_peaks().get("hbm_gbs")}}
+    held, peak = server.memory()
+    statuses = [r["status"] for _, r in fin_all]
+    lat = [1e3 * r["wall"] for _, r in fin_all]
+    its_fin = sum(r["iterations"] for _, r in fin_all) or 1
+    per_step = {"factorizations": sum(r["factorizations"] for _, r in fin_all) / its_fin,
+                "fp64_factorizations": sum(r["fp64_facs"] for _, r in fin_all) / its_fin,
+                "solves": 1.0 + sum(r["refine"] for _, r in fin_all) / its_fin,
+                "evaluations": 1.0 + sum(r["trials"] for _, r in fin_all) / its_fin}
 
     out = {
         "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32 factor + fp64 residual/refinement",
-        "data": "synthetic (seeded mass-action network, noisy observations, seeded starts)",
-        "config": {"workload": WORKLOAD.format(Q=Q, S=S), "queue": Q, "slots": S, "tol": TOL,
+        "data": "synthetic (seeded mass-action networks, noisy observations, seeded starts)",
+        "config": {"workload": WORKLOAD.format(S=S, B=args.budget_gib), "instances": len(insts),
+                   "kkt_unknowns_total": int(sum(8 * i.n * i.N + i.p for i in insts)),
+                   "slots": S, "budget_gib": args.budget_gib, "tol": TOL,
                    "admit_group": args.admit,
-                   "step": f"serve {Q} starts from theta0 to a final status",
+                   "step": f"{M} server steps of the steady stream (each advances every "
+                           "admitted solve by one Newton step)",
                    "newton_steps_per_step": its / max(args.steps, 1),
-                   "n_x_per_instance": one.n_x, "n_c_per_instance": one.n_c, "p": inst.p,
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world} (independent queues)"},
-        "solves_per_s": solves_total / (t_total * 1e-3),
+                   "l2": "inputs larger than L2 (factor stores of tens of GB per step); "
+                         "also flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (independent streams)"},
+        "solves_per_s": done_total / (t_total * 1e-3),
         "converged_solves_per_s": conv_total / (t_total * 1e-3),
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "what": "per-solve service time, admission to final status"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
+                       "p99": float(np.percentile(lat, 99)) if lat else None,
+                       "count": len(lat),
+                       "what": "service time (admission to final status) of the solves "
+                               "that finished in the timed steps"},
         "status_counts": {str(s_): statuses.count(s_) for s_ in sorted(set(statuses))},
-        "lockstep_batch": {"instances": S, "newton_steps_per_s": b_its / (b_ms * 1e-3),
-                           "ms": b_ms, "what": f"one collo_batch_solve of {S} starts, no refill"},
-        "single_instance": single,
-        "speedup_vs_fp64_single": value / single["fp64"]["newton_steps_per_s"],
-        "solves_speedup_vs_fp64_single": (solves_total / (t_total * 1e-3))
-                                         / single["fp64"]["solves_per_s"],
-        "param_rel_err_vs_fp64": {"value": perr, "compared": n_cmp,
-                                  "what": "max |k_mixed/k_fp64 - 1| over rate constants "
-                                          "k = 10^theta, starts where both paths converged"},
-        "phases_ms": ph, "roofline": roof,
-        "peaks_tflops": {"fp32_ffma": peak32, "fp64_dfma": peak64},
+        "per_newton_step": per_step,
+        "memory_gib": {"held_at_end": held / 2 ** 30, "peak": peak / 2 ** 30},
         "gpu_launches": launches, "clocks": clk,
     }
+
+    # end to end through host buffers: the same stream, each resubmission a new
+    # problem created from the instance's host arrays, every result read back
     if not args.no_e2e:
-        keep = [inst.react, inst.prod, inst.pidx, inst.kfix, inst.x0, inst.theta_lo,
-                inst.theta_hi, inst.obs_t, inst.obs_s, inst.obs_y, inst.obs_sigma]
-        h2d = Q * int(sum(np.asarray(a).nbytes for a in keep)) + 8 * inst.p * Q
-        tot, its_e = 0.0, 0
+        st.recreate = True
+        st.h2d = st.d2h = 0
         k_e = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        c0 = server.counters()
+        t0 = time.perf_counter()
         for i in range(k_e):
-            flush_l2(i)
-            t0 = time.perf_counter()
-            ps = [collo.Problem(inst, device=local) for _ in range(Q)]
-            tk = [server.submit(p, theta0=th) for p, th in zip(ps, starts)]
-            while True:
-                act, wait = server.step()
-                if act == 0 and wait == 0:
-                    break
-            res = [server.poll(t) for t in tk]
-            for pb in ps:
-                pb.close()
-            t1 = time.perf_counter()
-            tot += t1 - t0
-            its_e += sum(r["iterations"] for r in res)
-        tot = reduce_max(tot, world)
-        its_e = reduce_sum(float(its_e), world)
-        out["e2e"] = {"value": its_e / tot, "unit": "Newton steps/s",
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": Q * (8 * inst.p + 64),
-                      "what": f"{Q} x collo_problem_create from host arrays + serving + "
-                              "theta* read back, per step", "steps": k_e}
+            st.step(M)
+        torch.cuda.synchronize()
+        dt = reduce_max(time.perf_counter() - t0, world)
+        c1 = server.counters()
+        out["e2e"] = {"value": reduce_sum(float(c1[0] - c0[0]), world) / dt,
+                      "unit": "Newton steps/s",
+                      "h2d_bytes_per_step": st.h2d / k_e, "d2h_bytes_per_step": st.d2h / k_e,
+                      "what": "the same stream, host clock; every resubmitted instance is a new "
+                              "collo_problem_create from host arrays (the finished problem is "
+                              "destroyed) and every result's theta is read back",
+                      "steps": k_e}
+    server.close()
+    for pb in st.probs:
+        pb.close()
+    del probs
+
+    # the plain FP64 single-instance path on a stratified subsample
+    sample = stratified(insts, args.fp64_sample)
+    ms64, its64 = 0.0, 0
+    for i in sample:
+        with collo.Problem(insts[i], device=local) as pb:
+            pst = torch.cuda.ExternalStream(pb.stream)
+            pb.ipm_solve(precision=collo.FP64, want_x=False, tol=TOL, max_iter=1)   # allocation
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(pst)
+            r = pb.ipm_solve(precision=collo.FP64, want_x=False, tol=TOL,
+                             max_iter=args.fp64_steps)
+            e1.record(pst)
+            e1.synchronize()
+            ms64 += e0.elapsed_time(e1)
+            its64 += r["iterations"]
+    fp64_rate = its64 / (ms64 * 1e-3)
+    mean_its = its_fin / max(len(fin_all), 1)
+    out["fp64_single"] = {
+        "newton_steps_per_s": fp64_rate,
+        "solves_per_s_derived": fp64_rate / mean_its,
+        "instances": [[insts[i].n, insts[i].N] for i in sample],
+        "what": f"plain FP64 path, one instance at a time (collo_ipm_solve), on a stratified "
+                f"subsample of {len(sample)} instances (middles of equal strata of the batch "
+                f"sorted by factorization work), first {args.fp64_steps} Newton steps of each; "
+                "solves/s derived with the served solves' mean Newton steps per solve "
+                f"({mean_its:.1f})"}
+    out["speedup_vs_fp64_single"] = value / fp64_rate
+    out["solves_speedup_vs_fp64_single"] = (done_total / (t_total * 1e-3)) / (fp64_rate / mean_its)
+
+    # parameter agreement: converged served solves against FP64 solves of the same start
+    perr, n_cmp = 0.0, 0
+    seen = set()
+    for i, r in warm_fin + fin_all:
+        if r["status"] not in (collo.OK, collo.ACCEPTABLE) or i in seen or n_cmp >= 6:
+            continue
+        seen.add(i)
+        with collo.Problem(insts[i], device=local) as pb:
+            r64 = pb.ipm_solve(precision=collo.FP64, want_x=False, tol=TOL, max_wall_time=60.0)
+        if r64["status"] in (collo.OK, collo.ACCEPTABLE):
+            perr = max(perr, rate_rel_err(r["theta"], r64["theta"]))
+            n_cmp += 1
+    out["param_rel_err_vs_fp64"] = {
+        "value": perr if n_cmp else None, "compared": n_cmp,
+        "what": "max |k_mixed/k_fp64 - 1| over rate constants k = 10^theta, served solves "
+                "that converged (warm-up and timed steps) against FP64 single solves of the "
+                "same instance and start"}
+
+    # per-kernel timings (CUDA events inside the library) over the first S
+    # instances at their initial points, and their rooflines
+    out.update(kernel_rooflines(collo, insts[:S], local, per_step, clk))
     if not args.no_extra:
-        out.update(uneven_and_stream(collo, workloads, local))
+        out.update(config2_multistart(collo, workloads, local))
+        out.update(poisson_stream(collo, workloads, local, budget))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(inst, iters=6)
+        out["cpu_baseline"] = cpu_baseline(insts)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    server.close()
-    for pb in probs:
-        pb.close()
 
 
-def uneven_and_stream(collo, workloads, device):
-    """Reduced-size versions of the uneven multistart batch and the Poisson
-    serving stream (species 5-15, 100-800 elements): mixed path through the
-    server, against the plain FP64 path solving the same instances one by one."""
-    import numpy as np
-    out = {}
-    # uneven batch: all submitted at once, served through 16 slots
-    insts = workloads.multistart_batch(count=48, n_range=(5, 15), N_range=(100, 400))
+def kernel_rooflines(collo, insts, device, per_step, clk):
+    import torch
     probs = [collo.Problem(i, device=device) for i in insts]
-    srv = collo.Server(16, device=device, precision=collo.MIXED, tol=TOL)
-    srv.set_admission(4)
-    for rep in range(2):   # the first pass allocates the factor storage
+    for p, i in zip(probs, insts):
+        x, _ = p.initial_states(i.theta0)
+        p.eval_raw(x.ctypes.data, None)
+    F = collo.MIXED
+    ms = {"elem_big": collo.batch_time_phase(probs, 6, F, reps=3),
+          "elem_rt": collo.batch_time_phase(probs, 7, F, reps=3),
+          "reduction_schur": collo.batch_time_phase(probs, 5, F, reps=3),
+          "solve": collo.batch_time_phase(probs, 2, F, reps=3),
+          "eval": collo.batch_time_phase(probs, 3, F, reps=3)}
+    for p in probs:
+        p.close()
+    big = [i for i in insts if 8 * i.n + i.p > 124]
+    small = [i for i in insts if 8 * i.n + i.p <= 124]
+    w = {"elem_big": sum(elem_factor_work(i.n, i.p, i.N, 4)[0] for i in big),
+         "elem_rt": sum(elem_factor_work(i.n, i.p, i.N, 4)[0] for i in small),
+         "reduction_schur": sum(reduction_work(i.n, i.p, i.N, 4)[0] for i in insts),
+         "solve": sum(solve_bytes(i.n, i.p, i.N, 4) for i in insts),
+         "eval": sum(eval_bytes(i.n, i.p, i.N) for i in insts)}
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_alu = sms * 128 * 2 * mhz * 1e6 / 1e12
+    peak_hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    kern = {"elem_big": "k_elem_factor_big_b<float>", "elem_rt": "k_elem_factor_rt_b<float>",
+            "reduction_schur": "k_factor_b<float> (cyclic reduction + parameter Schur)",
+            "solve": "k_solve_b<float>", "eval": "k_eval_b<1> + k_eval_reduce_b"}
+    roofs = {}
+    for k, t in ms.items():
+        if t <= 0:
+            continue
+        if k in ("solve", "eval"):
+            ach = w[k] / (t * 1e-3) / 1e9
+            roofs[k] = {"bound": "hbm", "achieved": ach, "peak": peak_hbm, "unit": "GB/s",
+                        "frac": ach / peak_hbm, "traffic": TRAFFIC_C4_64.get(k),
+                        "algorithmic": w[k], "ms": t, "kernel": kern[k]}
+        else:
+            ach = w[k] / (t * 1e-3) / 1e12
+            roofs[k] = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+                        "frac": ach / peak_alu, "traffic": TRAFFIC_C4_64.get(k),
+                        "algorithmic": w[k], "ms": t, "kernel": kern[k]}
+    # time per Newton step of the batch: each factorization runs the three
+    # factorization kernels, each solve round the solve, each evaluation the eval
+    share = {k: ms[k] * per_step["factorizations"] for k in ("elem_big", "elem_rt",
+                                                               "reduction_schur")}
+    share["solve"] = ms["solve"] * per_step["solves"]
+    share["eval"] = ms["eval"] * per_step["evaluations"]
+    dom = max((k for k in share if k in roofs), key=lambda k: share[k])
+    tot = sum(share.values()) or 1.0
+    roof = dict(roofs[dom])
+    roof["peak_source"] = (f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"
+                           if roof["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs")
+    roof["share_of_kernel_time"] = share[dom] / tot
+    return {"roofline": roof,
+            "kernels": {k: dict(roofs[k], share_of_kernel_time=share[k] / tot) for k in roofs},
+            "kernels_what": f"CUDA-event time per batched launch over the first {len(insts)} "
+                            "instances at their initial points (collo_batch_time_phase); share = "
+                            "that time x launches per Newton step of the served stream"}
+
+
+def config2_multistart(collo, workloads, device):
+    """The earlier config-2 workload: 256 starts of one 10-species network, served."""
+    inst = workloads.config2()
+    starts = workloads.multistart_thetas(inst, 256, seed=2002)
+    probs = [collo.Problem(inst, device=device) for _ in starts]
+    srv = collo.Server(64, device=device, precision=collo.MIXED, tol=TOL)
+    srv.set_admission(32)
+    for rep in range(2):
         t0 = time.perf_counter()
-        tk = [srv.submit(p) for p in probs]
+        tk = [srv.submit(p, theta0=th) for p, th in zip(probs, starts)]
         while True:
             act, wait = srv.step()
             if act == 0 and wait == 0:
@@ -459,75 +583,80 @@ def uneven_and_stream(collo, workloads, device):
         dt = time.perf_counter() - t0
         res = [srv.poll(t) for t in tk]
     srv.close()
-    t64 = 0.0
-    for p in probs:
-        t1 = time.perf_counter()
-        p.ipm_solve(precision=collo.FP64, want_x=False, tol=TOL)
-        t64 += time.perf_counter() - t1
-    lat = [1e3 * r["wall"] for r in res]
-    out["uneven_batch"] = {
-        "instances": len(probs), "slots": 16, "species": [5, 15], "elements": [100, 400],
-        "sizes_n_N": [[i.n, i.N] for i in insts],
-        "newton_steps_per_s": sum(r["iterations"] for r in res) / dt,
-        "solves_per_s": len(res) / dt,
-        "fp64_single_solves_per_s": len(probs) / t64,
-        "solves_speedup_vs_fp64_single": (len(res) / dt) / (len(probs) / t64),
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "status_counts": {str(s_): sum(1 for r in res if r["status"] == s_)
-                          for s_ in sorted(set(r["status"] for r in res))},
-        "what": "config-4 shape at reduced sizes, served through 16 slots (admission groups "
-                "of 4); fp64 single = the same instances solved one after another on the plain "
-                "FP64 path"}
     for p in probs:
         p.close()
-    # Poisson stream: requests submitted at their arrival times (host clock)
-    stream = workloads.serving_stream(count=48, rate_hz=200.0, n_range=(5, 15),
-                                      N_range=(200, 800))
+    its = sum(r["iterations"] for r in res)
+    conv = sum(1 for r in res if r["status"] in (collo.OK, collo.ACCEPTABLE))
+    return {"config2_multistart": {
+        "newton_steps_per_s": its / dt, "solves_per_s": len(res) / dt,
+        "converged_solves_per_s": conv / dt, "wall_s": dt,
+        "what": "256 starts (theta_true + U[-0.1, 0.1]) of the 10-species / 20-reaction "
+                "network on N = 400 served through 64 slots, host clock, second pass"}}
+
+
+def poisson_stream(collo, workloads, device, budget):
+    """Requests of the serving-stream shape at their stated sizes (n log-uniform
+    on [5, 100], N on [200, 5000]) arriving at 200 per second, served for a
+    bounded time."""
+    import numpy as np
+    stream = workloads.serving_stream(count=16, rate_hz=200.0)
     probs = [collo.Problem(i, device=device) for _, i in stream]
-    srv = collo.Server(64, device=device, precision=collo.MIXED, tol=TOL)
+    srv = collo.Server(16, budget_bytes=budget, device=device, precision=collo.MIXED, tol=TOL)
     srv.set_admission(1)
-    for rep in range(2):
-        t0 = time.perf_counter()
-        nxt, tk, done_at = 0, {}, {}
-        while len(done_at) < len(stream):
-            now = time.perf_counter() - t0
-            while nxt < len(stream) and stream[nxt][0] <= now:
-                tk[nxt] = srv.submit(probs[nxt])
-                nxt += 1
-            act, wait = srv.step()
-            for j, t in tk.items():
-                if j not in done_at and srv.poll(t) is not None:
-                    done_at[j] = time.perf_counter() - t0
-            if act == 0 and wait == 0 and nxt < len(stream):
-                time.sleep(max(0.0, stream[nxt][0] - (time.perf_counter() - t0)))
-        dt = time.perf_counter() - t0
-        res = [srv.poll(tk[j]) for j in range(len(stream))]
+    limit = 60.0
+    t0 = time.perf_counter()
+    nxt, tk, done_at = 0, {}, {}
+    c0 = srv.counters()
+    while len(done_at) < len(stream) and time.perf_counter() - t0 < limit:
+        now = time.perf_counter() - t0
+        while nxt < len(stream) and stream[nxt][0] <= now:
+            tk[nxt] = srv.submit(probs[nxt])
+            nxt += 1
+        act, wait = srv.step()
+        for j, t in tk.items():
+            if j not in done_at and srv.poll(t) is not None:
+                done_at[j] = time.perf_counter() - t0
+        if act == 0 and wait == 0 and nxt < len(stream):
+            time.sleep(max(0.0, stream[nxt][0] - (time.perf_counter() - t0)))
+    dt = time.perf_counter() - t0
+    c1 = srv.counters()
+    res = {j: srv.poll(tk[j]) for j in done_at}
     srv.close()
-    lat = [1e3 * (done_at[j] - stream[j][0]) for j in range(len(stream))]
-    out["poisson_stream"] = {
-        "requests": len(stream), "rate_hz": 200.0, "species": [5, 15], "elements": [200, 800],
-        "newton_steps_per_s": sum(r["iterations"] for r in res) / dt,
-        "solves_per_s": len(res) / dt,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "status_counts": {str(s_): sum(1 for r in res if r["status"] == s_)
-                          for s_ in sorted(set(r["status"] for r in res))},
-        "what": "config-5 shape at reduced sizes: seeded exponential gaps, each request "
-                "submitted at its arrival time; latency = arrival to result (host clock)"}
     for p in probs:
         p.close()
-    return out
+    lat = [1e3 * (done_at[j] - stream[j][0]) for j in done_at]
+    return {"poisson_stream": {
+        "requests": len(stream), "finished": len(done_at), "wall_s": dt, "limit_s": limit,
+        "sizes_n_N": [[i.n, i.N] for _, i in stream],
+        "newton_steps_per_s": (c1[0] - c0[0]) / dt,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
+                       "p99": float(np.percentile(lat, 99)) if lat else None},
+        "status_counts": {str(s_): sum(1 for r in res.values() if r["status"] == s_)
+                          for s_ in sorted(set(r["status"] for r in res.values()))},
+        "what": "serving-stream shape at its stated sizes: 16 requests, seeded exponential "
+                "gaps at 200/s, each submitted at its arrival time, served for at most "
+                f"{limit:.0f} s; latency = arrival to result (host clock)"}}
 
 
-def cpu_baseline(inst, iters):
+def cpu_sample(insts):
+    """The oracle's bounded sample: the median instance of the batch by
+    factorization work."""
+    order = sorted(range(len(insts)), key=lambda i: insts[i].N * (8 * insts[i].n + insts[i].p) ** 3)
+    return insts[order[len(order) // 2]]
+
+
+def cpu_baseline(insts):
     from oracle import ipm as oipm
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    inst = cpu_sample(insts)
     t0 = time.perf_counter()
-    r = oipm.solve(inst, opt=oipm.Options(max_iter=iters))
+    r = oipm.solve(inst, opt=oipm.Options(max_iter=2))
     dt = time.perf_counter() - t0
-    return {"value": r.iterations / dt, "unit": "Newton steps/s", "cores": cores,
+    return {"value": r.iterations / dt, "unit": "Newton steps/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"oracle IPM on the same config-2 instance: initial point + {r.iterations} "
-                      f"Newton iterations ({dt:.1f} s, numpy/scipy FP64, block KKT mode)"}
+            "sample": f"oracle IPM on one instance of the batch (n = {inst.n}, N = {inst.N}, "
+                      f"the median by factorization work): initial point + "
+                      f"{r.iterations} Newton iterations ({dt:.1f} s, numpy/scipy FP64, one BLAS "
+                      "thread, block KKT mode)"}
 
 
 def run_reference(args):
@@ -538,9 +667,7 @@ def run_reference(args):
             return
     from oracle import ipm as oipm
     from paper_2607_12201_gb300 import workloads
-    inst = workloads.config2()
-    inst = inst.with_theta0(workloads.multistart_thetas(inst, 1, seed=2002)[0])
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    inst = cpu_sample(workloads.multistart_batch())
     per = 2
     for _ in range(args.warmup):
         oipm.solve(inst, opt=oipm.Options(max_iter=per))
@@ -554,115 +681,94 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
-           "config": {"workload": WORKLOAD.format(Q=args.queue, S=args.slots),
-                      "step": f"oracle initial point + {per} Newton iterations of one start"},
-           "cpu_baseline": {"value": v, "unit": "Newton steps/s", "cores": cores,
-                            "kind": "oracle",
+           "config": {"workload": WORKLOAD.format(S=args.slots, B=args.budget_gib),
+                      "step": f"oracle initial point + {per} Newton iterations of one instance "
+                              f"(n = {inst.n}, N = {inst.N})"},
+           "cpu_baseline": {"value": v, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                             "sample": f"{args.steps} x (initial point + {per} Newton iterations)"},
            "e2e": {"value": v, "unit": "Newton steps/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def only_solve(prec_name):
+def only_phase(args):
     from paper_2607_12201_gb300 import build as B
     B.build()
     from paper_2607_12201_gb300 import collo, workloads
-    inst = workloads.config2()
-    prec = collo.MIXED if prec_name == "mixed" else collo.FP64
-    with collo.Problem(inst) as prob:
-        l0 = collo.launch_count()
-        r = prob.ipm_solve(precision=prec, want_x=False)
-        print(json.dumps({"only_solve": prec_name, "status": r["status"],
-                          "iterations": r["iterations"], "wall_s": r["wall"],
-                          "launches": collo.launch_count() - l0}), flush=True)
-        if r["status"] not in (collo.OK, collo.ACCEPTABLE):
-            sys.exit(1)
-
-
-def phase_profile(args):
-    """Per-phase host wall time of the IPM driver while serving (COLLO_PROFILE=1:
-    the driver synchronises at each phase boundary, so the total is a little
-    above an unprofiled run)."""
-    os.environ["COLLO_PROFILE"] = "1"
-    from paper_2607_12201_gb300 import build as B
-    B.build()
-    from paper_2607_12201_gb300 import collo, workloads
-    inst = workloads.config2()
-    S, Q = args.slots, args.queue
-    starts = workloads.multistart_thetas(inst, Q, seed=2002)
-    probs = [collo.Problem(inst) for _ in range(Q)]
-    server = collo.Server(S, precision=collo.MIXED, tol=TOL)
-    server.set_admission(args.admit)
-    for rep in range(2):
-        collo.phase_profile(reset=True)
-        t0 = time.perf_counter()
-        tk = [server.submit(p, theta0=th) for p, th in zip(probs, starts)]
-        n_steps = 0
-        while True:
-            act, wait = server.step()
-            n_steps += 1
-            if act == 0 and wait == 0:
-                break
-        wall = time.perf_counter() - t0
-        res = [server.poll(t) for t in tk]
-        prof = collo.phase_profile(reset=True)
-    print(json.dumps({"phase_profile": {k: {"ms": round(v[0], 1), "rounds": v[1]}
-                                        for k, v in prof.items()},
-                      "wall_s": round(wall, 3), "server_steps": n_steps,
-                      "newton_steps": sum(r["iterations"] for r in res),
-                      "factorizations": sum(r["factorizations"] for r in res),
-                      "fp64_factorizations": sum(r["fp64_facs"] for r in res),
-                      "refinement_sweeps": sum(r["refine"] for r in res),
-                      "line_search_trials": sum(r["trials"] for r in res),
-                      "queue": Q, "slots": S, "admit_group": args.admit, "tol": TOL}), flush=True)
-    server.close()
-
-
-def only_elem_phase(S):
-    from paper_2607_12201_gb300 import build as B
-    B.build()
-    from paper_2607_12201_gb300 import collo, workloads
-    inst = workloads.config2()
-    starts = workloads.multistart_thetas(inst, S, seed=2002)
-    probs = [collo.Problem(inst) for _ in range(S)]
-    for p, th in zip(probs, starts):
-        x, _ = p.initial_states(th)
+    insts = workloads.multistart_batch()[:args.slots]
+    probs = [collo.Problem(i) for i in insts]
+    for p, i in zip(probs, insts):
+        x, _ = p.initial_states(i.theta0)
         p.eval_raw(x.ctypes.data, None)
-    ms = collo.batch_time_phase(probs, 4, collo.MIXED, reps=1)
-    print(json.dumps({"only_elem_phase": S, "elements": S * inst.N, "ms": ms}), flush=True)
+    ms = collo.batch_time_phase(probs, args.only_phase, collo.MIXED, reps=1)
+    print(json.dumps({"only_phase": args.only_phase, "instances": len(insts), "ms": ms}),
+          flush=True)
     for p in probs:
         p.close()
 
 
-def only_batch(nb):
+def only_serve(args):
     from paper_2607_12201_gb300 import build as B
     B.build()
     from paper_2607_12201_gb300 import collo, workloads
-    inst = workloads.config2()
-    starts = workloads.multistart_thetas(inst, nb, seed=2002)
-    probs = [collo.Problem(inst) for _ in range(nb)]
+    insts = workloads.multistart_batch()
+    probs = [collo.Problem(i) for i in insts]
+    srv = collo.Server(args.slots, budget_bytes=int(args.budget_gib * (1 << 30)),
+                       precision=collo.MIXED, tol=TOL)
+    srv.set_admission(args.admit)
+    st = Stream(collo, srv, insts, probs, 0)
     l0 = collo.launch_count()
     t0 = time.perf_counter()
-    res = collo.batch_solve(probs, theta0s=starts, precision=collo.MIXED)
-    print(json.dumps({"only_batch": nb, "wall_s": time.perf_counter() - t0,
-                      "iterations": sum(r["iterations"] for r in res),
-                      "status": sorted(set(r["status"] for r in res)),
-                      "launches": collo.launch_count() - l0}), flush=True)
-    for pb in probs:
-        pb.close()
+    st.step(args.only_serve)
+    print(json.dumps({"only_serve": args.only_serve, "wall_s": time.perf_counter() - t0,
+                      "counters": srv.counters(), "launches": collo.launch_count() - l0}),
+          flush=True)
+    srv.close()
+    for p in probs:
+        p.close()
+
+
+def phase_profile(args):
+    """Per-phase host wall time of the IPM driver over --slice server steps of the
+    stream after --warmup slices (COLLO_PROFILE=1: the driver synchronises at
+    each phase boundary)."""
+    os.environ["COLLO_PROFILE"] = "1"
+    from paper_2607_12201_gb300 import build as B
+    B.build()
+    from paper_2607_12201_gb300 import collo, workloads
+    insts = workloads.multistart_batch()
+    probs = [collo.Problem(i) for i in insts]
+    srv = collo.Server(args.slots, budget_bytes=int(args.budget_gib * (1 << 30)),
+                       precision=collo.MIXED, tol=TOL)
+    srv.set_admission(args.admit)
+    st = Stream(collo, srv, insts, probs, 0)
+    for _ in range(args.warmup):
+        st.step(args.slice)
+    collo.phase_profile(reset=True)
+    c0 = srv.counters()
+    t0 = time.perf_counter()
+    st.step(args.slice)
+    wall = time.perf_counter() - t0
+    prof = collo.phase_profile(reset=True)
+    c1 = srv.counters()
+    print(json.dumps({"phase_profile": {k: {"ms": round(v[0], 1), "rounds": v[1]}
+                                        for k, v in prof.items()},
+                      "wall_s": round(wall, 3), "server_steps": args.slice,
+                      "newton_steps": c1[0] - c0[0], "slots": args.slots,
+                      "admit_group": args.admit, "tol": TOL}), flush=True)
+    srv.close()
+    for p in probs:
+        p.close()
 
 
 def main():
     args = parse_args()
-    if args.only_solve:
-        only_solve(args.only_solve)
-    elif args.only_batch:
-        only_batch(args.batch)
+    if args.only_phase:
+        only_phase(args)
+    elif args.only_serve:
+        only_serve(args)
     elif args.phase_profile:
         phase_profile(args)
-    elif args.only_elem_phase:
-        only_elem_phase(args.slots)
     elif args.impl == "reference":
         run_reference(args)
     else:

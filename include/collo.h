@@ -333,9 +333,10 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
  * regularisation, 2 solve without refinement, 3 evaluation with derivatives at
  * each problem's current iterate, 4 the element-condensation part of phase 1
  * alone, 5 the rest of phase 1: cyclic reduction and parameter Schur
- * complement) reps times between CUDA events and returns
- * the average milliseconds per launch.  Problems must have been evaluated
- * (e.g. by a solve). */
+ * complement, 6 the condensation of element blocks above 124 rows alone,
+ * 7 that of the smaller, register-tiled element blocks alone) reps times
+ * between CUDA events and returns the average milliseconds per launch.
+ * Problems must have been evaluated (e.g. by a solve). */
 collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
                                     int precision, int reps, double* ms_per_launch);
 
@@ -377,6 +378,11 @@ void* collo_server_stream(collo_server* server);
 /* Device bytes held by the admitted problems now and the most held at once
  * since the server was created (either pointer may be NULL). */
 collo_status collo_server_memory(collo_server* server, int64_t* active_bytes, int64_t* peak_bytes);
+/* Totals since the server was created: Newton steps taken by all jobs, jobs
+ * that reached a final status, and of those the ones solved (COLLO_OK or
+ * COLLO_ACCEPTABLE).  Any pointer may be NULL. */
+collo_status collo_server_counters(collo_server* server, long long* newton_steps,
+                                   long long* finished, long long* converged);
 
 /* Measurement hook: with the environment variable COLLO_PROFILE=1 set before
  * the first solve, the IPM driver synchronises its stream at each phase

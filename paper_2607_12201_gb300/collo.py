@@ -153,6 +153,9 @@ def _load():
     lib.collo_server_stream.restype = C.c_void_p
     lib.collo_server_memory.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.collo_server_memory.restype = C.c_int
+    lib.collo_server_counters.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                          C.POINTER(C.c_longlong)]
+    lib.collo_server_counters.restype = C.c_int
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
     lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -419,8 +422,9 @@ def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
 
 
 def batch_time_phase(problems, phase: int, precision: int, reps: int = 10) -> float:
-    """collo_batch_time_phase: ms per batched launch of phase 1..5 (factor, solve,
-    eval, element condensation alone, reduction + Schur alone)."""
+    """collo_batch_time_phase: ms per batched launch of phase 1..7 (factor, solve,
+    eval, element condensation alone, reduction + Schur alone, large element
+    blocks alone, register-tiled element blocks alone)."""
     n = len(problems)
     handles = (C.c_void_p * n)(*[p.h.value for p in problems])
     ms = C.c_double()
@@ -459,6 +463,12 @@ class Server:
     @property
     def stream(self) -> int:
         return int(lib.collo_server_stream(self.h) or 0)
+
+    def counters(self):
+        """(Newton steps taken, jobs finished, jobs solved) since creation."""
+        a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(lib.collo_server_counters(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
 
     def memory(self):
         """(bytes held by admitted problems now, most held at once so far)."""

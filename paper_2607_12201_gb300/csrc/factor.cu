@@ -59,16 +59,17 @@ __device__ inline void tri_tile(int t, int& ti, int& tj) {
 // msz matrix A, stored as a packed lower triangle (shared or global memory),
 // blocked right-looking: pairs are taken in panels of PB.  A panel's 2 PB
 // columns (rows >= the panel) are copied into W[j][r] (leading dimension
-// ldw = msz | 1); its pairs are eliminated one after another by all threads of
-// the block, each pair forming the multipliers of every row below it (into
-// Lp[j][r] and Lout) and updating the panel's remaining columns, one barrier
-// per pair; then the trailing matrix receives one rank-2PB update, in 4 x 4
-// register tiles, from the multipliers Lp and the unscaled columns W.  The
-// arithmetic of every entry, and its order, is that of the pair-by-pair
-// elimination: the pivot inverse ia = d / det, ib = -b / det, id = a / det;
-// multipliers l0 = x0 ia + x1 ib, l1 = x0 ib + x1 id; panel entries updated
-// pair by pair; trailing entries by the sum over the panel's 2 PB columns in
-// ascending order, subtracted once.
+// ldw = msz | 1).  One warp eliminates the panel's pairs on its own 2 PB rows
+// (the diagonal block), recording each pair's pivot inverse; then every
+// thread replays the same eliminations on the rows below, one row at a time
+// in registers (a row's multipliers depend only on the diagonal block), with
+// no barrier between pairs; then the trailing matrix receives one rank-2PB
+// update, in 4 x 4 register tiles, from the multipliers Lp[j][r] and the
+// unscaled columns W.  Every entry sees the arithmetic, in the order, of the
+// pair-by-pair elimination: the pivot inverse ia = d / det, ib = -b / det,
+// id = a / det; multipliers l0 = x0 ia + x1 ib, l1 = x0 ib + x1 id; the
+// panel's remaining columns updated pair by pair; trailing entries by the sum
+// over the panel's 2 PB columns in ascending order, subtracted once.
 // L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
 // Dout[3 q]; pivot inertia is counted by thread 0.  The trailing block (rows
 // and columns >= 2 npairs) is left in A.
@@ -82,6 +83,7 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
                                       T* __restrict__ Dout, T* Lp, T* W, int& pos, int& neg,
                                       int& zero) {
   const int tid = threadIdx.x, nt = blockDim.x, ldw = panel_ld(msz);
+  __shared__ T pinv[PB][3];   // pivot inverse (ia, ib, id) of the panel's pairs
   for (int q0 = 0; q0 < npairs; q0 += PB) {
     const int pe = min(q0 + PB, npairs);
     const int cp = 2 * q0, cend = 2 * pe, K = cend - cp, rows = msz - cp;
@@ -92,38 +94,63 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
       if (c <= r) W[j * ldw + r] = A[tri_at(r, c)];
     }
     __syncthreads();
-    for (int q = q0; q < pe; ++q) {
-      const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
-      const T a = W[kk * ldw + c0], b = W[kk * ldw + c1], d = W[(kk + 1) * ldw + c1];
-      const T det = fma(a, d, -(b * b));
-      T ia, ib, id;
-      if (det != T(0) && isfinite(det)) {
-        const T inv = T(1) / det;
-        ia = d * inv; ib = -b * inv; id = a * inv;
-      } else {
-        ia = ib = id = T(0);
+    // 1. the diagonal block (rows cp .. cend-1), pair by pair, by warp 0
+    if (tid < 32) {
+      const int lane = tid;
+      for (int q = q0; q < pe; ++q) {
+        const int c0 = 2 * q, c1 = c0 + 1, kk = 2 * (q - q0);
+        const T a = W[kk * ldw + c0], b = W[kk * ldw + c1], d = W[(kk + 1) * ldw + c1];
+        const T det = fma(a, d, -(b * b));
+        T ia, ib, id;
+        if (det != T(0) && isfinite(det)) {
+          const T inv = T(1) / det;
+          ia = d * inv; ib = -b * inv; id = a * inv;
+        } else {
+          ia = ib = id = T(0);
+        }
+        if (lane == 0) {
+          Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
+          pinv[q - q0][0] = ia; pinv[q - q0][1] = ib; pinv[q - q0][2] = id;
+          pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
+        }
+        const int r = c1 + 1 + lane;
+        if (r < cend) {
+          const T x0 = W[kk * ldw + r], x1 = W[(kk + 1) * ldw + r];
+          const T l0 = fma(x0, ia, x1 * ib);
+          const T l1 = fma(x0, ib, x1 * id);
+          Lout[(size_t)c0 * lds + r] = l0;
+          Lout[(size_t)c1 * lds + r] = l1;
+          for (int c = c1 + 1; c <= r; ++c) {   // remaining panel columns, c <= r
+            T& w = W[(c - cp) * ldw + r];
+            w = fma(-l1, W[(kk + 1) * ldw + c], fma(-l0, W[kk * ldw + c], w));
+          }
+        }
+        __syncwarp();
       }
-      if (tid == 0) {
-        Dout[3 * q + 0] = a; Dout[3 * q + 1] = b; Dout[3 * q + 2] = d;
-        pivot_inertia((double)a, (double)b, (double)d, pos, neg, zero);
-      }
-      for (int r = c1 + 1 + tid; r < msz; r += nt) {
+    }
+    __syncthreads();
+    // 2. rows below the panel: the same eliminations, each thread on its own
+    // rows (entries of row r are updated in place in W; the diagonal block's
+    // columns are read through a volatile view, loaded where used)
+    const volatile T* U = W;
+    for (int r = cend + tid; r < msz; r += nt) {
+      for (int kk = 0; kk < K; kk += 2) {
+        const T ia = pinv[kk >> 1][0], ib = pinv[kk >> 1][1], id = pinv[kk >> 1][2];
         const T x0 = W[kk * ldw + r], x1 = W[(kk + 1) * ldw + r];
         const T l0 = fma(x0, ia, x1 * ib);
         const T l1 = fma(x0, ib, x1 * id);
         Lp[kk * ldw + r] = l0;
         Lp[(kk + 1) * ldw + r] = l1;
-        Lout[(size_t)c0 * lds + r] = l0;
-        Lout[(size_t)c1 * lds + r] = l1;
-        // remaining panel columns c in (c1, cend), c <= r
-        const int cmax = min(cend - 1, r);
-        for (int c = c1 + 1; c <= cmax; ++c) {
-          T& w = W[(c - cp) * ldw + r];
-          w = fma(-l1, W[(kk + 1) * ldw + c], fma(-l0, W[kk * ldw + c], w));
+        Lout[(size_t)(cp + kk) * lds + r] = l0;
+        Lout[(size_t)(cp + kk + 1) * lds + r] = l1;
+        for (int j = kk + 2; j < K; ++j) {
+          const int c = cp + j;
+          T& w = W[j * ldw + r];
+          w = fma(-l1, U[(kk + 1) * ldw + c], fma(-l0, U[kk * ldw + c], w));
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
     // trailing rank-K update of rows / columns >= cend (lower part)
     const int Tn = msz - cend;
     if (Tn > 0) {
@@ -133,6 +160,16 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
         int ti, tj;
         tri_tile(t, ti, tj);
         const int r0 = cend + 4 * ti, cb = cend + 4 * tj;
+        // the tile's entries are loaded first, so that their latency (the
+        // triangle may be in global memory) overlaps the products below
+        T cur[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int r = r0 + u, c = cb + v;
+            cur[u][v] = (r < msz && c <= r) ? A[tri_at(r, c)] : T(0);
+          }
         T acc[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -157,7 +194,7 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const int c = cb + v;
-            if (c <= r) A[tri_at(r, c)] -= acc[u][v];
+            if (c <= r) A[tri_at(r, c)] = cur[u][v] - acc[u][v];
           }
         }
       }
@@ -760,9 +797,12 @@ k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double 
 // Eliminates the blocks at odd multiples of `stride` (final = 1: block 0 alone).
 // Local order of the extended block: [interface of block i (2n) | z3 of the
 // left neighbour (n) | c0 of the right neighbour (n) | theta (p)].
+// Kept out of line: inside the cooperative kernel (80 registers per thread for
+// the latency-bound register-tiled reduction blocks) its register demand would
+// otherwise shape the whole kernel.
 template <typename T>
-__device__ void bcr_factor_big(const DevProb& P, const DevFactor<T>& F, int stride,
-                               int final_level, int bi, const BigPlace<T>& pl) {
+__device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>& F, int stride,
+                                            int final_level, int bi, const BigPlace<T> pl) {
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
@@ -1522,6 +1562,26 @@ k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ ac
                                  t - pre_elem[k], ub.v, reinterpret_cast<T*>(stage_dyn));
 }
 
+// Element condensation of a batch for the instances whose element blocks are
+// above the register-tile limit (without flag 4): elements of the work list
+// taken in turn by the CUDA blocks of the grid (at most one global slab per
+// CUDA block), block storage in shared memory (flag 1) or in the slab.
+template <typename T>
+__global__ void __launch_bounds__(FBS, 1)
+k_elem_factor_big_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
+                    const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
+                    const int* __restrict__ flags) {
+  extern __shared__ unsigned char smraw[];
+  for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
+    const int k = find_item(pre_elem, A, t);
+    if (flags[k] & 4) continue;   // condensed by k_elem_factor_rt_b
+    const DevInst& I = insts[act[k]];
+    const DevFactor<T>& F = inst_factor<T>(I);
+    const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, (flags[k] & 1) != 0);
+    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl);
+  }
+}
+
 // FP32: three blocks per SM (more reduction blocks in flight; the levels are
 // latency bound)
 template <typename T, int BT>
@@ -1532,16 +1592,8 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
            const int* __restrict__ flags, GridBar* gb, size_t smem_bytes, int bcr_full) {
   extern __shared__ unsigned char smraw[];
   unsigned int ep = 0;
-  // 1. element condensation
-  for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
-    const int k = find_item(pre_elem, A, t);
-    if (flags[k] & 4) continue;   // condensed by k_elem_factor_rt_b
-    const DevInst& I = insts[act[k]];
-    const DevFactor<T>& F = inst_factor<T>(I);
-    const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, (flags[k] & 1) != 0);
-    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl);
-  }
-  grid_barrier(gb, ep);
+  // 1. element condensation: done by k_elem_factor_rt_b / k_elem_factor_big_b
+  // before this launch
   // 2. cyclic-reduction levels, then each instance's final block
   for (int lv = 0; lv <= maxL; ++lv) {
     const int* pre = pre_lv + (size_t)lv * (A + 1);
@@ -1926,13 +1978,16 @@ cudaError_t launch_solve(const DevProb& P, const DevFactor<T>& F, const DevSchur
 }
 
 // Batched launchers.  `grid_cap` limits the grid when some instance uses its
-// global slabs (at most n_slabs blocks may run).
+// global slabs (at most n_slabs blocks may run).  Factorization parts: 1 the
+// register-tiled element kernel, 4 the large-element kernel, 2 the rest (cyclic
+// reduction and parameter Schur complement in the cooperative kernel).
 template <typename T>
 cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                             const int* pre_lv, int maxL, const int* pre_cs,
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
                             int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
-                            int bcr_tpt, int bcr_full, int parts, cudaStream_t st) {
+                            int big_grid, size_t big_smem, int bcr_tpt, int bcr_full, int parts,
+                            cudaStream_t st) {
   if (A == 0) return cudaSuccess;
   if ((parts & 1) && rt_threads > 0 && tot_elem > 0) {
     if (rt_threads > RT_MAX_THREADS) return cudaErrorInvalidValue;
@@ -1940,6 +1995,13 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
     count_launch();
     k_elem_factor_rt_b<T><<<tot_elem, rt_threads, rt_smem, st>>>(insts, act, A, pre_elem, prm,
                                                                  flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if ((parts & 4) && big_grid > 0) {
+    opt_in_smem(k_elem_factor_big_b<T>, big_smem);
+    count_launch();
+    k_elem_factor_big_b<T><<<big_grid, FBS, big_smem, st>>>(insts, act, A, pre_elem, prm, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1974,11 +2036,11 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
 template cudaError_t launch_factor_b<float>(const DevInst*, const int*, int, const int*,
                                             const int*, int, const int*, const InstParams*,
                                             const int*, GridBar*, size_t, int, int, size_t, int,
-                                            int, int, int, cudaStream_t);
+                                            int, size_t, int, int, int, cudaStream_t);
 template cudaError_t launch_factor_b<double>(const DevInst*, const int*, int, const int*,
                                              const int*, int, const int*, const InstParams*,
                                              const int*, GridBar*, size_t, int, int, size_t, int,
-                                             int, int, int, cudaStream_t);
+                                             int, size_t, int, int, int, cudaStream_t);
 int bcr_rt_tiles_of(const DevProb& P) { return bcr_rt_tiles(P.bext); }
 size_t elem_rt_stage_bytes(const DevProb& P, bool f32) {
   return f32 ? elem_stage_bytes<float>(P) : elem_stage_bytes<double>(P);

@@ -70,7 +70,8 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
                             const int* pre_lv, int maxL, const int* pre_cs,
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
                             int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
-                            int bcr_tpt, int bcr_full, int parts, cudaStream_t st);
+                            int big_grid, size_t big_smem, int bcr_tpt, int bcr_full, int parts,
+                            cudaStream_t st);
 // Block size of the register-tiled element condensation for P (0: the
 // element does not fit it).
 int elem_rt_threads(const DevProb& P, bool f32);

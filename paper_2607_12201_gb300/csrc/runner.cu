@@ -54,6 +54,8 @@ struct Plan {
   int per_warp[2] = {0, 0};
   int rt_threads[2] = {0, 0};   // block size of the register-tiled element kernel
   size_t rt_smem[2] = {0, 0};   // its dynamic shared memory
+  int big_grid[2] = {0, 0};     // grid of the large-element kernel (0: no such element)
+  size_t big_smem[2] = {0, 0};  // its dynamic shared memory
   int bcr_tpt = 0;          // ... of the register-tiled cyclic-reduction blocks
   int bcr_full = 0;         // some instance's reduction blocks use the whole-block path
 
@@ -254,7 +256,8 @@ struct Runner {
       const size_t off = o;
       size_t smem = 0;
       int cap = 1 << 30, pw = 0, tpt = 0, btpt = 0, bfull = 0;
-      size_t rts = 0;
+      size_t rts = 0, bsm = 0;
+      int bcap = 1 << 30, nbig = 0;
       for (int k = 0; k < A; ++k) {
         const DevProb& Q = P(slots[k]);
         const size_t se = f32 ? elem_factor_smem<float>(Q, true) : elem_factor_smem<double>(Q, true);
@@ -268,9 +271,10 @@ struct Runner {
           fl |= 1 | 4;
           tpt = std::max(tpt, rt);
           rts = std::max(rts, elem_rt_stage_bytes(Q, f32));
-        } else {
-          need = std::max(need, ve);
-          if (se <= KSMEM_LIMIT) { fl |= 1; need = std::max(need, se); }
+        } else {                       // ... or by the large-element kernel
+          if (se <= KSMEM_LIMIT) { fl |= 1; bsm = std::max(bsm, se); }
+          else { bsm = std::max(bsm, ve); bcap = std::min(bcap, probs[slots[k]]->n_slabs); }
+          nbig += Q.N;
         }
         if (brt > 0) {                 // register-tiled reduction blocks
           fl |= 2 | 8;
@@ -283,7 +287,8 @@ struct Runner {
         }
         const size_t ss = sizeof(double) * ((size_t)Q.p * Q.p + Q.p);
         if (ss <= KSMEM_LIMIT) need = std::max(need, ss);
-        if ((fl & 3) != 3) cap = std::min(cap, probs[slots[k]]->n_slabs);
+        // the cooperative kernel uses a global slab only for reduction blocks
+        if (!(fl & 2)) cap = std::min(cap, probs[slots[k]]->n_slabs);
         smem = std::max(smem, need);
         h[off + k] = fl;
         pw = std::max(pw, std::max(Q.ext, Q.bext));
@@ -295,6 +300,8 @@ struct Runner {
       pl.per_warp[prec] = pw;
       pl.rt_threads[prec] = tpt;
       pl.rt_smem[prec] = rts;
+      pl.big_grid[prec] = nbig > 0 ? std::min(bcap, pl.tot_elem) : 0;
+      pl.big_smem[prec] = bsm;
       pl.bcr_tpt = btpt;
       pl.bcr_full = bfull;
     }
@@ -392,8 +399,9 @@ struct Runner {
                               pl.d_prm, mode, stream));
     return COLLO_OK;
   }
-  // parts: 1 element condensation (register-tiled kernel), 2 the rest, 3 both
-  collo_status factor(int which, int prec, int parts = 3) {
+  // parts: 1 register-tiled element condensation, 4 large-element condensation,
+  // 2 the rest (cyclic reduction, parameter Schur complement); 7 all
+  collo_status factor(int which, int prec, int parts = 7) {
     Plan& pl = plans[which];
     err_fresh = false;
     {
@@ -416,14 +424,14 @@ struct Runner {
       e = launch_factor_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                  pl.pre_cs_s(), pl.d_prm, pl.flags(1), gbar, pl.smem_f[1],
                                  std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)),
-                                 pl.rt_threads[1], pl.rt_smem[1], pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
-                                 parts, stream);
+                                 pl.rt_threads[1], pl.rt_smem[1], pl.tot_elem, pl.big_grid[1],
+                                 pl.big_smem[1], pl.bcr_tpt, pl.bcr_full, parts, stream);
     else
       e = launch_factor_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                   pl.pre_cs_s(), pl.d_prm, pl.flags(0), gbar, pl.smem_f[0],
                                   std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)),
-                                  pl.rt_threads[0], pl.rt_smem[0], pl.tot_elem, pl.bcr_tpt, pl.bcr_full,
-                                  parts, stream);
+                                  pl.rt_threads[0], pl.rt_smem[0], pl.tot_elem, pl.big_grid[0],
+                                  pl.big_smem[0], pl.bcr_tpt, pl.bcr_full, parts, stream);
     COLLO_CUDA(e);
     return COLLO_OK;
   }
@@ -1141,6 +1149,9 @@ struct collo_server {
   int64_t budget = 0;
   int64_t active_bytes = 0;   // held by admitted jobs' problems
   int64_t peak_bytes = 0;     // largest active_bytes so far
+  long long newton_steps = 0; // Newton steps taken by all jobs
+  long long finished = 0;     // jobs with a final status
+  long long converged = 0;    // ... of them solved (COLLO_OK or COLLO_ACCEPTABLE)
   long long next_ticket = 1;
   struct Job {
     long long ticket;
@@ -1274,7 +1285,7 @@ collo_status collo_batch_solve(collo_problem* const* probs, int count, const dou
 // phase 1 factorization, 2 solve (no refinement), 3 evaluation.
 collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int phase,
                                     int precision, int reps, double* ms_per_launch) {
-  if (!probs || count < 1 || reps < 1 || !ms_per_launch || phase < 1 || phase > 5) {
+  if (!probs || count < 1 || reps < 1 || !ms_per_launch || phase < 1 || phase > 7) {
     set_error("bad argument");
     return COLLO_ERR_INVALID_ARG;
   }
@@ -1297,11 +1308,14 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
   auto run = [&]() -> collo_status {
     if (phase == 1) return R.factor(0, precision);
     if (phase == 2) return R.solve(0, precision, 0);
-    if (phase == 4) return R.factor(0, precision, 1);
+    if (phase == 4) return R.factor(0, precision, 1 | 4);
     if (phase == 5) return R.factor(0, precision, 2);
+    if (phase == 6) return R.factor(0, precision, 4);
+    if (phase == 7) return R.factor(0, precision, 1);
     return R.eval(0, 1, 0, 2, true);
   };
   if ((phase == 2 || phase == 5) && (s = R.factor(0, precision)) != COLLO_OK) return s;
+  if ((phase == 6 || phase == 7) && (s = R.factor(0, precision)) != COLLO_OK) return s;
   if ((s = run()) != COLLO_OK) return s;
   cudaEvent_t e0, e1;
   COLLO_CUDA(cudaEventCreate(&e0));
@@ -1317,7 +1331,7 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
   cudaEventDestroy(e1);
   *ms_per_launch = t / reps;
   for (int i = 0; i < count; ++i)
-    if (phase <= 2 || phase == 5) probs[i]->factored = precision;
+    if (phase <= 2 || phase >= 5) probs[i]->factored = precision;
   return R.check_barrier();
 }
 
@@ -1398,6 +1412,7 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
       j->res = collo_result{};
       j->res.status = COLLO_ERR_OOM;
       j->done = true;
+      sv->finished++;
       continue;
     }
     if (sv->budget > 0 && sv->active_bytes + need > sv->budget) break;
@@ -1416,9 +1431,12 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     if ((s = ipm_begin(R, fresh)) != COLLO_OK) return s;
   }
   std::vector<IpmInst*> act;
+  long long its0 = 0, its1 = 0;
   for (auto* j : sv->slots)
-    if (j) act.push_back(&j->I);
+    if (j) { act.push_back(&j->I); its0 += j->I.it; }
   if ((s = ipm_iteration(R, act)) != COLLO_OK) return s;
+  for (auto* I : act) its1 += I->it;
+  sv->newton_steps += its1 - its0;
   // retire finished jobs
   for (int k = 0; k < (int)sv->slots.size(); ++k) {
     auto* j = sv->slots[k];
@@ -1426,6 +1444,8 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     j->res = collo_result{};
     if ((s = ipm_finish(R, j->I, &j->res)) != COLLO_OK) return s;
     j->done = true;
+    sv->finished++;
+    if (j->res.status == COLLO_OK || j->res.status == COLLO_ACCEPTABLE) sv->converged++;
     // its factorization stores go back in stream order after its last kernels
     release_factor_storage(j->prob, R.stream);
     sv->active_bytes -= j->bytes;
@@ -1453,6 +1473,15 @@ collo_status collo_server_memory(collo_server* sv, int64_t* active_bytes, int64_
   if (!sv) { set_error("NULL server"); return COLLO_ERR_INVALID_ARG; }
   if (active_bytes) *active_bytes = sv->active_bytes;
   if (peak_bytes) *peak_bytes = sv->peak_bytes;
+  return COLLO_OK;
+}
+
+collo_status collo_server_counters(collo_server* sv, long long* newton_steps, long long* finished,
+                                   long long* converged) {
+  if (!sv) { set_error("NULL server"); return COLLO_ERR_INVALID_ARG; }
+  if (newton_steps) *newton_steps = sv->newton_steps;
+  if (finished) *finished = sv->finished;
+  if (converged) *converged = sv->converged;
   return COLLO_OK;
 }
 

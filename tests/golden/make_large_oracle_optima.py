@@ -71,7 +71,8 @@ def solve_case(name):
         # decides ties in the filter tests: the parity point is the iterate
         # CHECK_BACK iterations before the failure
         m = max(1, res.iterations - CHECK_BACK)
-        extra = {"checkpoint_iter": m, "checkpoint_theta": res.history[m - 1]["theta"].tolist()}
+        extra = {"checkpoint_iter": m, "checkpoint_theta": res.history[m - 1]["theta"].tolist(),
+                 "trajectory": [h["theta"].tolist() for h in res.history]}
     return {
         "cite": "Eq. 2 NLP solved by the filter line-search interior-point method "
                 "(Introduction; tolerances of Section \"Optimization framework configurations\")",
