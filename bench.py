@@ -94,6 +94,10 @@ def parse_args():
     ap.add_argument("--only-phase", type=int, default=0,
                     help="time one batched phase (1..7 of collo_batch_time_phase) over the "
                          "first --slots instances at their initial points and exit (ncu)")
+    ap.add_argument("--phase-case", default="batch", choices=["batch", "large"],
+                    help="--only-phase instances: the first --slots of the batch, or --slots "
+                         "copies of one 45-species network on N = 150 (element blocks of 450 "
+                         "rows, factored in the global slab)")
     ap.add_argument("--only-serve", type=int, default=0,
                     help="run this many server steps of the stream and exit (ncu launch list)")
     ap.add_argument("--phase-profile", action="store_true",
@@ -695,13 +699,19 @@ def only_phase(args):
     from paper_2607_12201_gb300 import build as B
     B.build()
     from paper_2607_12201_gb300 import collo, workloads
-    insts = workloads.multistart_batch()[:args.slots]
+    if args.phase_case == "large":
+        one = workloads.random_network(45, 90, log10k=(-2.0, 1.0), n_obs=4, M=50, T=20.0, N=150,
+                                       seed=4501, theta0_spread=1.0)
+        insts = [one] * args.slots
+    else:
+        insts = workloads.multistart_batch()[:args.slots]
     probs = [collo.Problem(i) for i in insts]
     for p, i in zip(probs, insts):
         x, _ = p.initial_states(i.theta0)
         p.eval_raw(x.ctypes.data, None)
     ms = collo.batch_time_phase(probs, args.only_phase, collo.MIXED, reps=1)
-    print(json.dumps({"only_phase": args.only_phase, "instances": len(insts), "ms": ms}),
+    print(json.dumps({"only_phase": args.only_phase, "case": args.phase_case,
+                      "instances": len(insts), "elements": sum(i.N for i in insts), "ms": ms}),
           flush=True)
     for p in probs:
         p.close()

@@ -73,12 +73,12 @@ __device__ inline void tri_tile(int t, int& ti, int& tj) {
 // L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
 // Dout[3 q]; pivot inertia is counted by thread 0.  The trailing block (rows
 // and columns >= 2 npairs) is left in A.
-constexpr int PB = 8;
-constexpr int PW = 2 * PB;   // columns of a panel
-
+// PB is 8 for blocks held in shared memory and 16 for blocks in the global
+// slab (half the trailing passes over global memory, twice the arithmetic per
+// entry read and written).
 __host__ __device__ inline int panel_ld(int msz) { return msz | 1; }
 
-template <typename T>
+template <typename T, int PB>
 __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__ Lout, int lds,
                                       T* __restrict__ Dout, T* Lp, T* W, int& pos, int& neg,
                                       int& zero) {
@@ -204,15 +204,32 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
 }
 
 // Storage of a block of msz rows factored by pair_eliminate_packed: the two
-// panel buffers Lp, W (PW x panel_ld(msz) each) and the packed triangle
-// (msz (msz + 1) / 2).  Everything in shared memory when it fits the
-// factorization limit; otherwise the triangle in a per-CUDA-block global slab
-// (L2-resident) and the panel buffers in shared memory, or, when even they do
-// not fit, in the slab behind the triangle.
-template <typename T>
-__host__ __device__ inline size_t big_panel_elems(int msz) { return 2 * (size_t)PW * panel_ld(msz); }
+// panel buffers Lp, W (2 PB x panel_ld(msz) each) and the packed triangle
+// (msz (msz + 1) / 2).  Everything in shared memory (PB = 8) when it fits the
+// factorization limit; otherwise (PB = 16) the triangle in a per-CUDA-block
+// global slab (L2-resident) and the panel buffers in shared memory, or, when
+// even they do not fit, in the slab behind the triangle.
 __host__ __device__ inline size_t big_tri_elems(int msz) {
   return ((size_t)msz * (msz + 1) / 2 + 1) & ~size_t(1);
+}
+template <typename T>
+__host__ __device__ inline int big_pb(int msz) {
+  const size_t full8 = sizeof(T) * (2 * (size_t)16 * panel_ld(msz) + big_tri_elems(msz));
+  return full8 <= FACTOR_SMEM_LIMIT ? 8 : 16;
+}
+template <typename T>
+__host__ __device__ inline size_t big_panel_elems(int msz) {
+  return 2 * (size_t)(2 * big_pb<T>(msz)) * panel_ld(msz);
+}
+// pair_eliminate_packed with the panel width of the block's storage
+template <typename T>
+__device__ inline void pair_eliminate_big(T* A, int msz, int npairs, T* __restrict__ Lout,
+                                          int lds, T* __restrict__ Dout, T* Lp, T* W, int& pos,
+                                          int& neg, int& zero) {
+  if (big_pb<T>(msz) == 16)
+    pair_eliminate_packed<T, 16>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
+  else
+    pair_eliminate_packed<T, 8>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
 }
 template <typename T>
 __host__ __device__ inline bool panel_in_global(int msz) {
@@ -231,7 +248,7 @@ struct BigPlace {
 // Pointers of block storage for this CUDA block (full: all in shared memory).
 template <typename T>
 __device__ inline BigPlace<T> big_place(unsigned char* smraw, T* work, int msz, bool full) {
-  const size_t pn = (size_t)PW * panel_ld(msz);
+  const size_t pn = big_panel_elems<T>(msz) / 2;
   T* slab = work + (size_t)blockIdx.x * slab_elems<T>(msz);
   const bool pg = !full && panel_in_global<T>(msz);
   T* Lp = pg ? slab + big_tri_elems(msz) : reinterpret_cast<T*>(smraw);
@@ -274,7 +291,7 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                   E.Wobj + (size_t)e * 16 * n, sigma ? sigma + (size_t)e * 4 * n : nullptr, dw,
                   dc, A);
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_packed<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+  pair_eliminate_big<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
                            F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
@@ -831,7 +848,7 @@ __device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>
     }
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_packed<T>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
+  pair_eliminate_big<T>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
                            F.Db + (size_t)i * n * 3, pl.Lp, pl.W, pos, neg, zero);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
@@ -1566,8 +1583,9 @@ k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ ac
 // above the register-tile limit (without flag 4): elements of the work list
 // taken in turn by the CUDA blocks of the grid (at most one global slab per
 // CUDA block), block storage in shared memory (flag 1) or in the slab.
+constexpr int BIG_BS = 512;   // threads of the large-element kernel
 template <typename T>
-__global__ void __launch_bounds__(FBS, 1)
+__global__ void __launch_bounds__(BIG_BS, 1)
 k_elem_factor_big_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
                     const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
                     const int* __restrict__ flags) {
@@ -2001,7 +2019,8 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
   if ((parts & 4) && big_grid > 0) {
     opt_in_smem(k_elem_factor_big_b<T>, big_smem);
     count_launch();
-    k_elem_factor_big_b<T><<<big_grid, FBS, big_smem, st>>>(insts, act, A, pre_elem, prm, flags);
+    k_elem_factor_big_b<T><<<big_grid, BIG_BS, big_smem, st>>>(insts, act, A, pre_elem, prm,
+                                                                flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
