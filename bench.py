@@ -87,6 +87,9 @@ def parse_args():
                     help="instances of the stratified subsample run on the plain FP64 path")
     ap.add_argument("--fp64-steps", type=int, default=20,
                     help="Newton steps of each FP64 single-instance run")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default schedule")
+    ap.add_argument("--schedule-cache", default=None,
+                    help="JSON file caching autotuned schedules per batch shape and device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -340,6 +343,7 @@ def run_ours(args):
     S, M = args.slots, args.slice
     budget = int(args.budget_gib * (1 << 30))
     insts = workloads.multistart_batch()
+    tune = autotune_schedule(collo, insts[:S], local, args) if not args.no_tune else None
     probs = [collo.Problem(i, device=local) for i in insts]
     server = collo.Server(S, budget_bytes=budget, device=local, precision=collo.MIXED, tol=TOL)
     server.set_admission(args.admit)
@@ -419,6 +423,7 @@ def run_ours(args):
                                "that finished in the timed steps"},
         "status_counts": {str(s_): statuses.count(s_) for s_ in sorted(set(statuses))},
         "per_newton_step": per_step,
+        "autotune": tune,
         "memory_gib": {"held_at_end": held / 2 ** 30, "peak": peak / 2 ** 30},
         "gpu_launches": launches, "clocks": clk,
     }
@@ -507,6 +512,29 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(insts)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def autotune_schedule(collo, insts, device, args):
+    """The launch schedule for this workload: collo_autotune over the first
+    --slots instances at their initial points (cached per batch shape and
+    device in --schedule-cache)."""
+    import torch
+    probs = [collo.Problem(i, device=device) for i in insts]
+    for p, i in zip(probs, insts):
+        x, _ = p.initial_states(i.theta0)
+        p.eval_raw(x.ctypes.data, None)
+    name = torch.cuda.get_device_name(device)
+    best, before, after, hit = collo.autotune(probs, collo.MIXED, reps=2,
+                                              cache=args.schedule_cache, device_name=name)
+    for p in probs:
+        p.close()
+    return {"schedule": best, "default_ms": before, "tuned_ms": after,
+            "gain": before / after if after > 0 else None, "from_cache": hit,
+            "what": "collo_autotune over the first instances at their initial points: the "
+                    "large-element kernel (threads per block, pairs per panel of slab blocks) "
+                    "and the solve (per-instance top levels, elements per block) timed per "
+                    "candidate; ms = the two phases' time per launch under the default and "
+                    "the tuned schedule"}
 
 
 def kernel_rooflines(collo, insts, device, per_step, clk):

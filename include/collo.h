@@ -417,6 +417,38 @@ collo_status collo_initial_states(collo_problem* prob, const double* theta, doub
 collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int reps,
                               double* ms_per_launch);
 
+/* Launch schedule of the batched kernels, process-wide (the paper has no
+ * counterpart; it sets how the work is laid out on the GPU, not what is
+ * computed).  Results are bitwise reproducible for a fixed schedule;
+ * slab_pairs changes the rounding order of element and reduction blocks held
+ * in the global slab.  Change it only while no solve is running. */
+typedef struct collo_schedule {
+  int big_threads;            /* threads per block of the condensation of element
+                                 blocks above 124 rows: 256 or 512 (default 512) */
+  int slab_pairs;             /* pairs per panel of blocks whose packed triangle is
+                                 held in the global slab: 8 or 16 (default 16) */
+  int solve_top_blocks;       /* the batched solve runs the reduction levels with
+                                 at most this many blocks per instance in one CUDA
+                                 block per instance (default 8) */
+  int solve_elems_per_block;  /* elements per 8-warp block of the solve's grid
+                                 (default 8) */
+  int reserved[4];
+} collo_schedule;
+collo_status collo_get_schedule(collo_schedule* out);
+/* INVALID_ARG when a field is outside the values above (1..4096 for
+ * solve_top_blocks, 1..1024 for solve_elems_per_block). */
+collo_status collo_set_schedule(const collo_schedule* s);
+/* Autotuner: on `count` evaluated problems (as for collo_batch_time_phase),
+ * times the large-element condensation (phase 6) for each (big_threads,
+ * slab_pairs) and then the solve (phase 2) for each (solve_top_blocks in
+ * 2..32, solve_elems_per_block in 4..32), reps launches each between CUDA
+ * events, keeps the fastest of each, sets it as the schedule and returns it
+ * in *best, with the two phases' milliseconds per launch under the schedule
+ * it started from and under the chosen one (either pointer may be NULL).  On
+ * error the schedule it started from is restored. */
+collo_status collo_autotune(collo_problem* const* probs, int count, int precision, int reps,
+                            collo_schedule* best, double* ms_before, double* ms_after);
+
 /* Fused multiply-add throughput of the current device in TFLOP/s (2 flops
  * per FMA), for precision COLLO_PRECISION_FP64 (DFMA) or _MIXED (FFMA):
  * the arithmetic roof of the element factorization.  Allocates a small

@@ -83,6 +83,11 @@ class IpmOptions(C.Structure):
                 ("refine_tol", C.c_double), ("verbose", C.c_int), ("reserved", C.c_int * 8)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("big_threads", C.c_int), ("slab_pairs", C.c_int), ("solve_top_blocks", C.c_int),
+                ("solve_elems_per_block", C.c_int), ("reserved", C.c_int * 4)]
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("factorizations", C.c_int),
                 ("line_search_trials", C.c_int), ("refinement_sweeps", C.c_int),
@@ -158,6 +163,13 @@ def _load():
     lib.collo_server_counters.restype = C.c_int
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
+    lib.collo_get_schedule.argtypes = [C.POINTER(Schedule)]
+    lib.collo_get_schedule.restype = C.c_int
+    lib.collo_set_schedule.argtypes = [C.POINTER(Schedule)]
+    lib.collo_set_schedule.restype = C.c_int
+    lib.collo_autotune.argtypes = [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.POINTER(Schedule),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.collo_autotune.restype = C.c_int
     lib.collo_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     lib.collo_alu_peak.restype = C.c_int
     lib.collo_launch_count.argtypes = []
@@ -431,6 +443,63 @@ def batch_time_phase(problems, phase: int, precision: int, reps: int = 10) -> fl
     _check(lib.collo_batch_time_phase(handles, n, int(phase), int(precision), int(reps),
                                       C.byref(ms)))
     return ms.value
+
+
+SCHEDULE_FIELDS = ["big_threads", "slab_pairs", "solve_top_blocks", "solve_elems_per_block"]
+
+
+def get_schedule() -> dict:
+    """collo_get_schedule: the process-wide launch schedule."""
+    sc = Schedule()
+    _check(lib.collo_get_schedule(C.byref(sc)))
+    return {k: int(getattr(sc, k)) for k in SCHEDULE_FIELDS}
+
+
+def set_schedule(sched: dict):
+    """collo_set_schedule from a dict with the fields of collo_schedule."""
+    sc = Schedule()
+    for k in SCHEDULE_FIELDS:
+        setattr(sc, k, int(sched[k]))
+    _check(lib.collo_set_schedule(C.byref(sc)))
+
+
+def shape_key(problems, precision: int, device_name: str = "") -> str:
+    """Cache key of a batch for the autotuner: the device, the precision and
+    the sorted (n, p, N) shapes of its problems."""
+    import hashlib
+    shapes = sorted((p.n, p.p, p.N) for p in problems)
+    h = hashlib.sha1(repr((device_name, int(precision), shapes)).encode()).hexdigest()[:16]
+    return f"{device_name}|{int(precision)}|{len(shapes)}|{h}"
+
+
+def autotune(problems, precision: int = MIXED, reps: int = 2, cache: str | None = None,
+             device_name: str = ""):
+    """collo_autotune over evaluated problems; with `cache` (a JSON file path)
+    a batch already tuned on this device reuses the stored schedule.  Returns
+    (schedule dict, ms before, ms after, from_cache)."""
+    import json
+    key = shape_key(problems, precision, device_name)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            ent = table[key]
+            set_schedule(ent["schedule"])
+            return ent["schedule"], ent["ms_before"], ent["ms_after"], True
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p.h.value for p in problems])
+    sc = Schedule()
+    b, a = C.c_double(), C.c_double()
+    _check(lib.collo_autotune(handles, n, int(precision), int(reps), C.byref(sc), C.byref(b),
+                              C.byref(a)))
+    best = {k: int(getattr(sc, k)) for k in SCHEDULE_FIELDS}
+    if cache:
+        table[key] = {"schedule": best, "ms_before": b.value, "ms_after": a.value}
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return best, b.value, a.value, False
 
 
 class Server:

@@ -15,6 +15,10 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<long long> g_launches{0};
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+Schedule& schedule() {
+  static Schedule s;
+  return s;
+}
 
 // Radau IIA points for K = 3 (closed form) and D[k][j] = l_j'(tau_k) from the
 // barycentric weights w_j = 1 / prod_{l != j} (tau_j - tau_l):

@@ -218,6 +218,17 @@ void set_error(const std::string& msg);
 // Count of kernels this library has launched (all threads, all problems).
 void count_launch(int k = 1);
 
+// Launch schedule of the batched kernels (process-wide; collo_set_schedule,
+// collo_autotune).  Results are bitwise reproducible for a fixed schedule;
+// slab_pairs changes the rounding of blocks held in the global slab.
+struct Schedule {
+  int big_threads = 512;   // threads per block of the large-element kernel (256 | 512)
+  int slab_pairs = 16;     // pairs per panel of blocks in the global slab (8 | 16)
+  int solve_top = 8;       // the solve's per-instance top levels: at most this many blocks
+  int solve_elems = 8;     // elements per 8-warp block of the solve's grid
+};
+Schedule& schedule();
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace collo

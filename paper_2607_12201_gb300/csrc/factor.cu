@@ -221,12 +221,13 @@ template <typename T>
 __host__ __device__ inline size_t big_panel_elems(int msz) {
   return 2 * (size_t)(2 * big_pb<T>(msz)) * panel_ld(msz);
 }
-// pair_eliminate_packed with the panel width of the block's storage
+// pair_eliminate_packed with PB = pb (8, or 16 for a block in the global slab,
+// whose panel buffers are sized for 16)
 template <typename T>
 __device__ inline void pair_eliminate_big(T* A, int msz, int npairs, T* __restrict__ Lout,
                                           int lds, T* __restrict__ Dout, T* Lp, T* W, int& pos,
-                                          int& neg, int& zero) {
-  if (big_pb<T>(msz) == 16)
+                                          int& neg, int& zero, int pb) {
+  if (pb == 16)
     pair_eliminate_packed<T, 16>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
   else
     pair_eliminate_packed<T, 8>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
@@ -276,7 +277,7 @@ __device__ inline void elem_scatter(const DevProb& P, const double* Wzz, const d
 template <typename T>
 __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                                 const double* __restrict__ sigma, double dw, double dc,
-                                const DevFactor<T>& F, int e, const BigPlace<T>& pl) {
+                                const DevFactor<T>& F, int e, const BigPlace<T>& pl, int pb) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nint = 3 * n;          // interior pairs
@@ -292,7 +293,7 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                   dc, A);
   int pos = 0, neg = 0, zero = 0;
   pair_eliminate_big<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
-                           F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero);
+                        F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero, pb);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
   }
@@ -324,11 +325,11 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
 template <typename T>
 __global__ void __launch_bounds__(FBS)
 k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, double dc,
-              DevFactor<T> F, int use_smem) {
+              DevFactor<T> F, int use_smem, int slab_pb) {
   extern __shared__ unsigned char smraw[];
   const BigPlace<T> pl = big_place<T>(smraw, F.work, P.ext, use_smem != 0);
   for (int e = blockIdx.x; e < P.N; e += gridDim.x)
-    elem_factor_big<T>(P, E, sigma, dw, dc, F, e, pl);
+    elem_factor_big<T>(P, E, sigma, dw, dc, F, e, pl, use_smem ? 8 : slab_pb);
 }
 
 // ---- 1'. pair elimination with the block held in registers -------------------------
@@ -819,7 +820,8 @@ k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double 
 // otherwise shape the whole kernel.
 template <typename T>
 __device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>& F, int stride,
-                                            int final_level, int bi, const BigPlace<T> pl) {
+                                            int final_level, int bi, const BigPlace<T> pl,
+                                            int pb) {
   const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
@@ -849,7 +851,7 @@ __device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
   pair_eliminate_big<T>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
-                           F.Db + (size_t)i * n * 3, pl.Lp, pl.W, pos, neg, zero);
+                        F.Db + (size_t)i * n * 3, pl.Lp, pl.W, pos, neg, zero, pb);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
     in[0] = pos; in[1] = neg; in[2] = zero;
@@ -1029,7 +1031,7 @@ __host__ __device__ inline int bcr_level_blocks(int N, int stride) {
 
 template <typename T, int BT>
 __global__ void __launch_bounds__(FBS)
-k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem) {
+k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_smem, int slab_pb) {
   extern __shared__ unsigned char smraw[];
   const int nblk = final_level ? 1 : bcr_level_blocks(P.N, stride);
   if constexpr (BT > 0) {
@@ -1045,7 +1047,7 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
   } else {
     const BigPlace<T> pl = big_place<T>(smraw, F.work, P.bext, use_smem != 0);
     for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-      bcr_factor_big<T>(P, F, stride, final_level, bi, pl);
+      bcr_factor_big<T>(P, F, stride, final_level, bi, pl, use_smem ? 8 : slab_pb);
   }
 }
 
@@ -1583,20 +1585,22 @@ k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ ac
 // above the register-tile limit (without flag 4): elements of the work list
 // taken in turn by the CUDA blocks of the grid (at most one global slab per
 // CUDA block), block storage in shared memory (flag 1) or in the slab.
-constexpr int BIG_BS = 512;   // threads of the large-element kernel
-template <typename T>
-__global__ void __launch_bounds__(BIG_BS, 1)
+// BS threads per block (256 or 512: Schedule::big_threads).
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS, 1)
 k_elem_factor_big_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
                     const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
-                    const int* __restrict__ flags) {
+                    const int* __restrict__ flags, int slab_pb) {
   extern __shared__ unsigned char smraw[];
   for (int t = blockIdx.x; t < pre_elem[A]; t += gridDim.x) {
     const int k = find_item(pre_elem, A, t);
     if (flags[k] & 4) continue;   // condensed by k_elem_factor_rt_b
     const DevInst& I = insts[act[k]];
     const DevFactor<T>& F = inst_factor<T>(I);
-    const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, (flags[k] & 1) != 0);
-    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl);
+    const bool full = (flags[k] & 1) != 0;
+    const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, full);
+    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl,
+                       full ? 8 : slab_pb);
   }
 }
 
@@ -1607,7 +1611,8 @@ __global__ void __launch_bounds__(FBS, sizeof(T) == 4 ? 3 : 1)
 k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
            const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
            const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
-           const int* __restrict__ flags, GridBar* gb, size_t smem_bytes, int bcr_full) {
+           const int* __restrict__ flags, GridBar* gb, size_t smem_bytes, int bcr_full,
+           int slab_pb) {
   extern __shared__ unsigned char smraw[];
   unsigned int ep = 0;
   // 1. element condensation: done by k_elem_factor_rt_b / k_elem_factor_big_b
@@ -1666,9 +1671,11 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       if (BT > 0 && (flags[k] & 8)) continue;
       const DevInst& I = insts[act[k]];
       const DevFactor<T>& F = inst_factor<T>(I);
-      const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.bext, (flags[k] & 2) != 0);
-      if (fin) bcr_factor_big<T>(I.P, F, 1, 1, 0, pl);
-      else bcr_factor_big<T>(I.P, F, 1 << lv, 0, t - pre[k], pl);
+      const bool full = (flags[k] & 2) != 0;
+      const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.bext, full);
+      const int pb = full ? 8 : slab_pb;
+      if (fin) bcr_factor_big<T>(I.P, F, 1, 1, 0, pl, pb);
+      else bcr_factor_big<T>(I.P, F, 1 << lv, 0, t - pre[k], pl, pb);
     }
     grid_barrier(gb, ep);
   }
@@ -1867,7 +1874,8 @@ cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double*
     cudaFuncSetAttribute(k_elem_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int grid = es ? P.N : std::min(P.N, F.n_slabs);
   count_launch();
-  k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0);
+  k_elem_factor<T><<<grid, FBS, sm, st>>>(P, E, sigma, dw, dc, F, es ? 1 : 0,
+                                           schedule().slab_pairs);
   return cudaGetLastError();
 }
 
@@ -1922,13 +1930,13 @@ cudaError_t launch_factor(const DevProb& P, const DevEval& E, const double* sigm
       auto kern = bt == 1 ? k_bcr_factor<T, 1> : k_bcr_factor<T, 2>;
       if (smr > SMEM_OPTIN_ABOVE)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-      kern<<<(nblk + 1) / 2, FBS, smr, st>>>(P, F, s, fin, 1);
+      kern<<<(nblk + 1) / 2, FBS, smr, st>>>(P, F, s, fin, 1, schedule().slab_pairs);
     } else {
       if (smb > SMEM_OPTIN_ABOVE)
         cudaFuncSetAttribute(k_bcr_factor<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smb);
       const int g = bs ? nblk : std::min(nblk, F.n_slabs);
-      k_bcr_factor<T, 0><<<g, FBS, smb, st>>>(P, F, s, fin, bs ? 1 : 0);
+      k_bcr_factor<T, 0><<<g, FBS, smb, st>>>(P, F, s, fin, bs ? 1 : 0, schedule().slab_pairs);
     }
     return cudaGetLastError();
   };
@@ -2016,11 +2024,18 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  const Schedule sch = schedule();
   if ((parts & 4) && big_grid > 0) {
-    opt_in_smem(k_elem_factor_big_b<T>, big_smem);
     count_launch();
-    k_elem_factor_big_b<T><<<big_grid, BIG_BS, big_smem, st>>>(insts, act, A, pre_elem, prm,
-                                                                flags);
+    if (sch.big_threads == 256) {
+      opt_in_smem(k_elem_factor_big_b<T, 256>, big_smem);
+      k_elem_factor_big_b<T, 256><<<big_grid, 256, big_smem, st>>>(insts, act, A, pre_elem, prm,
+                                                                   flags, sch.slab_pairs);
+    } else {
+      opt_in_smem(k_elem_factor_big_b<T, 512>, big_smem);
+      k_elem_factor_big_b<T, 512><<<big_grid, 512, big_smem, st>>>(insts, act, A, pre_elem, prm,
+                                                                   flags, sch.slab_pairs);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -2029,8 +2044,9 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
   opt_in_smem(kern, smem);
   int grid = coop_grid(kern, FBS, smem, grid_cap);
   if (grid < 1) return cudaErrorInvalidConfiguration;
+  int slab_pb = sch.slab_pairs;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
-                  (void*)&pre_cs, (void*)&prm, (void*)&flags, &gb, &smem, &bcr_full};
+                  (void*)&pre_cs, (void*)&prm, (void*)&flags, &gb, &smem, &bcr_full, &slab_pb};
   count_launch();
   return cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(FBS), args, smem, st);
 }

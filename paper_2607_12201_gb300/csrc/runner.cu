@@ -27,9 +27,6 @@ namespace collo {
 
 constexpr int OUTS = 32;                  // doubles of DevInst::out per instance
 constexpr size_t KSMEM_LIMIT = FACTOR_SMEM_LIMIT;
-// The batched solve runs the cyclic-reduction levels with at most this many
-// blocks in every instance one block (of FBS / 32 warps) per instance.
-constexpr int SOLVE_TOP_BLOCKS = 8;
 
 // Relative KKT residual above which refinement from an FP32 factorization
 // counts as failed (the step is then redone with an FP64 factorization).
@@ -226,7 +223,7 @@ struct Runner {
         const int N = P(slots[k]).N, st = 1 << lv;
         most = std::max(most, (lv < maxL && N > st) ? (N - st + 2 * st - 1) / (2 * st) : 0);
       }
-      if (most > SOLVE_TOP_BLOCKS) break;
+      if (most > schedule().solve_top) break;
       pl.lsplit = lv;
     }
     for (int lv = 0; lv <= maxL; ++lv) {
@@ -439,7 +436,8 @@ struct Runner {
     Plan& pl = plans[which];
     err_fresh = false;
     cudaError_t e;
-    const int want = std::max(pl.A, (pl.tot_elem + 7) / 8);
+    const int per = std::max(1, schedule().solve_elems);
+    const int want = std::max(pl.A, (pl.tot_elem + per - 1) / per);
     if (prec == COLLO_PRECISION_MIXED)
       e = launch_solve_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL, pl.lsplit,
                                 pl.pre_cs_r(), ir, pl.per_warp[1], gbar, pl.max_p, want, stream);
@@ -1473,6 +1471,81 @@ collo_status collo_server_memory(collo_server* sv, int64_t* active_bytes, int64_
   if (!sv) { set_error("NULL server"); return COLLO_ERR_INVALID_ARG; }
   if (active_bytes) *active_bytes = sv->active_bytes;
   if (peak_bytes) *peak_bytes = sv->peak_bytes;
+  return COLLO_OK;
+}
+
+static bool valid_schedule(const collo_schedule* s) {
+  return s && (s->big_threads == 256 || s->big_threads == 512) &&
+         (s->slab_pairs == 8 || s->slab_pairs == 16) && s->solve_top_blocks >= 1 &&
+         s->solve_top_blocks <= 4096 && s->solve_elems_per_block >= 1 &&
+         s->solve_elems_per_block <= 1024;
+}
+
+collo_status collo_get_schedule(collo_schedule* out) {
+  if (!out) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  const Schedule& g = schedule();
+  out->big_threads = g.big_threads;
+  out->slab_pairs = g.slab_pairs;
+  out->solve_top_blocks = g.solve_top;
+  out->solve_elems_per_block = g.solve_elems;
+  return COLLO_OK;
+}
+
+collo_status collo_set_schedule(const collo_schedule* s) {
+  if (!valid_schedule(s)) { set_error("bad schedule"); return COLLO_ERR_INVALID_ARG; }
+  Schedule& g = schedule();
+  g.big_threads = s->big_threads;
+  g.slab_pairs = s->slab_pairs;
+  g.solve_top = s->solve_top_blocks;
+  g.solve_elems = s->solve_elems_per_block;
+  return COLLO_OK;
+}
+
+collo_status collo_autotune(collo_problem* const* probs, int count, int precision, int reps,
+                            collo_schedule* best, double* ms_before, double* ms_after) {
+  if (!probs || count < 1 || reps < 1 || !best ||
+      (precision != COLLO_PRECISION_FP64 && precision != COLLO_PRECISION_MIXED)) {
+    set_error("bad argument");
+    return COLLO_ERR_INVALID_ARG;
+  }
+  collo_schedule cur;
+  collo_get_schedule(&cur);
+  // the large-element kernel (phase 6) and the solve (phase 2) are timed
+  // apart: their knobs do not interact
+  auto timed = [&](const collo_schedule& c, int phase, double* ms) -> collo_status {
+    collo_status s = collo_set_schedule(&c);
+    if (s != COLLO_OK) return s;
+    return collo_batch_time_phase(probs, count, phase, precision, reps, ms);
+  };
+  double f0 = 0, s0 = 0;
+  collo_status st;
+  if ((st = timed(cur, 6, &f0)) != COLLO_OK) { collo_set_schedule(&cur); return st; }
+  if ((st = timed(cur, 2, &s0)) != COLLO_OK) { collo_set_schedule(&cur); return st; }
+  collo_schedule b = cur;
+  double fb = f0, sb = s0;
+  for (int bt : {256, 512})
+    for (int sp : {8, 16}) {
+      collo_schedule c = b;
+      c.big_threads = bt;
+      c.slab_pairs = sp;
+      double ms = 0;
+      if ((st = timed(c, 6, &ms)) != COLLO_OK) { collo_set_schedule(&cur); return st; }
+      if (ms < fb) { fb = ms; b.big_threads = bt; b.slab_pairs = sp; }
+    }
+  for (int top : {2, 4, 8, 16, 32})
+    for (int per : {4, 8, 16, 32}) {
+      collo_schedule c = b;
+      c.solve_top_blocks = top;
+      c.solve_elems_per_block = per;
+      double ms = 0;
+      if ((st = timed(c, 2, &ms)) != COLLO_OK) { collo_set_schedule(&cur); return st; }
+      if (ms < sb) { sb = ms; b.solve_top_blocks = top; b.solve_elems_per_block = per; }
+    }
+  collo_set_schedule(&b);
+  *best = b;
+  if (ms_before) *ms_before = f0 + s0;
+  if (ms_after) *ms_after = fb + sb;
   return COLLO_OK;
 }
 

@@ -224,3 +224,34 @@ def test_binding_success_paths(lib, monkeypatch, outcome):
     sv.h, sv._keep = C.c_void_p(), {}
     t = sv.submit(pr, theta0=np.zeros(2))
     assert sv.poll(t)["status"] == outcome
+
+
+def test_schedule_get_set_and_validation(lib):
+    """collo_get_schedule / collo_set_schedule are host-side (no GPU): values
+    outside the documented sets are refused and the schedule is unchanged."""
+    before = lib.get_schedule()
+    assert before["big_threads"] in (256, 512) and before["slab_pairs"] in (8, 16)
+    try:
+        for bad in (dict(before, big_threads=384), dict(before, slab_pairs=12),
+                    dict(before, solve_top_blocks=0), dict(before, solve_elems_per_block=0)):
+            with pytest.raises(lib.ColloError) as e:
+                lib.set_schedule(bad)
+            assert e.value.status == lib.ERR_INVALID_ARG
+            assert lib.get_schedule() == before
+        other = dict(big_threads=256, slab_pairs=8, solve_top_blocks=16, solve_elems_per_block=4)
+        lib.set_schedule(other)
+        assert lib.get_schedule() == other
+    finally:
+        lib.set_schedule(before)
+
+
+def test_autotune_cache_key_depends_on_shapes_and_device(lib):
+    class P:
+        def __init__(self, n, p, N):
+            self.n, self.p, self.N = n, p, N
+    a = [P(5, 10, 100), P(20, 40, 300)]
+    b = [P(20, 40, 300), P(5, 10, 100)]
+    assert lib.shape_key(a, lib.MIXED, "gpu") == lib.shape_key(b, lib.MIXED, "gpu")
+    assert lib.shape_key(a, lib.MIXED, "gpu") != lib.shape_key(a, lib.FP64, "gpu")
+    assert lib.shape_key(a, lib.MIXED, "gpu") != lib.shape_key(a, lib.MIXED, "other")
+    assert lib.shape_key(a, lib.MIXED, "gpu") != lib.shape_key(a[:1], lib.MIXED, "gpu")

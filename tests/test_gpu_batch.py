@@ -225,3 +225,32 @@ def test_server_fails_a_problem_larger_than_the_budget(collo):
     server.close()
     small.close()
     big.close()
+
+
+def test_autotuner_picks_a_schedule_and_results_stay_correct(collo, tmp_path):
+    """collo_autotune times the large-element kernel and the solve under each
+    candidate schedule on an uneven batch, keeps the fastest (no slower than the
+    schedule it started from), and caches it; solves under the tuned schedule
+    are bitwise reproducible and agree with the default schedule's within the
+    parity tolerance (the panel width changes the rounding of slab blocks)."""
+    insts = [W.random_network(n, 2 * n, n_obs=4, M=20, T=5.0, N=N, seed=70 + n,
+                              theta0_spread=0.1) for n, N in ((6, 40), (20, 30), (36, 20))]
+    default = collo.get_schedule()
+    probs = [collo.Problem(i) for i in insts]
+    ref = collo.batch_solve(probs, precision=collo.MIXED, max_iter=8)
+    try:
+        cache = str(tmp_path / "sched.json")
+        best, before, after, hit = collo.autotune(probs, collo.MIXED, reps=2, cache=cache)
+        assert not hit and after <= before
+        assert best == collo.get_schedule()
+        again = collo.autotune(probs, collo.MIXED, reps=2, cache=cache)
+        assert again[3] and again[0] == best
+        runs = [collo.batch_solve(probs, precision=collo.MIXED, max_iter=8) for _ in range(2)]
+        for a, b, r in zip(runs[0], runs[1], ref):
+            assert np.array_equal(a["theta"], b["theta"])
+            assert a["iterations"] == r["iterations"]
+            assert np.max(np.abs(a["theta"] - r["theta"])) <= 1e-6 * max(1.0, np.max(np.abs(r["theta"])))
+    finally:
+        collo.set_schedule(default)
+        for pb in probs:
+            pb.close()
