@@ -395,6 +395,58 @@ collo_status collo_server_counters(collo_server* server, long long* newton_steps
 int collo_phase_profile(double* ms, long long* rounds, int n, int reset);
 void collo_server_destroy(collo_server* server);
 
+/* ---- Mesh refinement (paper Section "Static collocation mesh limitations"
+ * and Conclusion: a mesh fixed at the nominal parameters may be too coarse
+ * near the optimum; refine the interval width in an outer loop).  The loop
+ * here is batched on the GPU. */
+
+/* A new problem with coarse's network, observables and data on a uniform
+ * mesh of N elements (same horizon, K = 3).  The caller owns *out. */
+collo_status collo_problem_create_refined(const collo_problem* coarse, int N,
+                                          collo_problem** out);
+
+/* Collocation defect of x [n_x] (host or device): for element i, the
+ * collocation polynomial z_i(tau) = sum_j l_j(tau) z_ij leaves at the
+ * midpoints tau*_m = (tau_(m-1) + tau_m) / 2, m = 1..K, of consecutive
+ * interpolation points the residual d_ims = sum_j l_j'(tau*_m) z_ijs
+ * - h f_s(z_i(tau*_m), theta) (h times the ODE residual); per_element [N]
+ * (host or device, may be NULL) receives max_{m,s} |d_ims| and *max_defect
+ * (may be NULL) the maximum over elements. */
+collo_status collo_defect(collo_problem* prob, const double* x, double* per_element,
+                          double* max_defect);
+
+/* Interpolates the coarse solution x_coarse [n_x of coarse] onto fine's mesh:
+ * the states at fine's interpolation points t = (i + tau_j) h_f from the
+ * coarse collocation polynomial of the element holding t (a time on a coarse
+ * element boundary from the left element, t = 0 from the first), theta
+ * copied; x_fine [n_x of fine].  Both problems must differ only in their
+ * meshes, with fine at least half as many elements as coarse. */
+collo_status collo_interpolate(collo_problem* coarse, const double* x_coarse,
+                               collo_problem* fine, double* x_fine);
+
+/* Warm start: the next interior-point solve of prob (collo_ipm_solve,
+ * collo_batch_solve or the server) starts from x [n_x] (states and theta,
+ * theta pushed into its bounds as a theta0 would be) and lambda [n_c] (NULL:
+ * zero) instead of the forward sweep at theta0, whose theta0 argument is then
+ * ignored; bound duals and the barrier parameter start as usual.  The start
+ * is consumed by that solve; x = NULL clears it. */
+collo_status collo_problem_set_start(collo_problem* prob, const double* x, const double* lambda);
+
+/* Batched refinement: solves probs from theta0 as collo_batch_solve does;
+ * then, up to max_levels times, every problem whose last solve ended in
+ * COLLO_OK or COLLO_ACCEPTABLE with a defect (collo_defect of its solution)
+ * above defect_tol is re-created on twice as many elements (at most
+ * max_elements; 0: no limit), warm-started from its interpolated solution,
+ * and all of them are solved again together.  finals[i] is the problem of
+ * problem i's last solve: probs[i] or a problem this call created, which the
+ * caller then destroys (intermediate ones are destroyed here); results[i] its
+ * result (theta honoured at every level, x and lambda only when no refinement
+ * happened); levels[i] how many times it was refined. */
+collo_status collo_refine_solve(collo_problem* const* probs, int count, const double* const* theta0,
+                                const collo_ipm_options* opts, double defect_tol, int max_levels,
+                                int max_elements, collo_problem** finals, collo_result* results,
+                                int* levels);
+
 /* Collocation forward sweep at theta (the IPM's initial states): writes
  * z [N][K+1][n] into x_out [n_x] (theta copied into its tail).  Returns the
  * number of elements whose Newton iteration failed in *failures. */

@@ -99,12 +99,19 @@ def push_into_bounds(theta, lo, hi, opt: Options):
     return np.minimum(np.maximum(theta, lo + pl), hi - pu)
 
 
-def initial_point(prob: Problem, theta0, opt: Options):
+def initial_point(prob: Problem, theta0, opt: Options, x_start=None, lam_start=None):
+    """theta0 pushed into the bounds and the forward sweep's states; with a warm
+    start x_start the states are its own and theta0 is its theta (pushed)."""
     inst = prob.inst
+    if x_start is not None:
+        theta0 = np.asarray(x_start, dtype=np.float64)[prob.nz:]
     th = push_into_bounds(np.asarray(theta0, dtype=np.float64), inst.theta_lo, inst.theta_hi, opt)
-    z, fails = forward_sweep(prob, th)
+    if x_start is not None:
+        z, fails = np.asarray(x_start, dtype=np.float64)[:prob.nz].copy(), 0
+    else:
+        z, fails = forward_sweep(prob, th)
     x = np.concatenate([z.reshape(-1), th])
-    lam = np.zeros(prob.n_c)
+    lam = np.zeros(prob.n_c) if lam_start is None else np.array(lam_start, dtype=np.float64)
     zl = np.ones(prob.p)
     zu = np.ones(prob.p)
     return x, lam, zl, zu, fails
@@ -228,10 +235,13 @@ def reset_bound_duals(z, s, mu, kappa_sigma):
 
 
 def solve(inst, theta0=None, opt: Options | None = None, verbose: bool = False,
-          on_iter=None) -> Result:
+          on_iter=None, x_start=None, lam_start=None) -> Result:
+    """x_start / lam_start: a warm start (states and theta, multipliers) in
+    place of the forward sweep at theta0."""
     opt = opt or Options()
     prob = Problem(inst)
-    x, lam, zl, zu, fails = initial_point(prob, inst.theta0 if theta0 is None else theta0, opt)
+    x, lam, zl, zu, fails = initial_point(prob, inst.theta0 if theta0 is None else theta0, opt,
+                                          x_start, lam_start)
     mu = opt.mu_init
     tau = max(opt.tau_min, 1.0 - mu)
     filt = []

@@ -163,6 +163,18 @@ def _load():
     lib.collo_server_counters.restype = C.c_int
     lib.collo_time_phase.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.collo_time_phase.restype = C.c_int
+    lib.collo_problem_create_refined.argtypes = [P, C.c_int, C.POINTER(P)]
+    lib.collo_problem_create_refined.restype = C.c_int
+    lib.collo_defect.argtypes = [P, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+    lib.collo_defect.restype = C.c_int
+    lib.collo_interpolate.argtypes = [P, C.c_void_p, P, C.c_void_p]
+    lib.collo_interpolate.restype = C.c_int
+    lib.collo_problem_set_start.argtypes = [P, C.c_void_p, C.c_void_p]
+    lib.collo_problem_set_start.restype = C.c_int
+    lib.collo_refine_solve.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_void_p),
+                                       C.POINTER(IpmOptions), C.c_double, C.c_int, C.c_int,
+                                       C.POINTER(P), C.POINTER(Result), C.POINTER(C.c_int)]
+    lib.collo_refine_solve.restype = C.c_int
     lib.collo_get_schedule.argtypes = [C.POINTER(Schedule)]
     lib.collo_get_schedule.restype = C.c_int
     lib.collo_set_schedule.argtypes = [C.POINTER(Schedule)]
@@ -265,6 +277,40 @@ class Problem:
         self.sizes = s
         self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
         self.n_x, self.n_c = int(s.n_x), int(s.n_c)
+
+    @classmethod
+    def _adopt(cls, handle, inst):
+        """Wrap a problem the library created (the wrapper owns it)."""
+        self = cls.__new__(cls)
+        self.inst = inst
+        self._keep = {}
+        self.h = C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle
+        s = Sizes()
+        _check(lib.collo_problem_sizes(self.h, C.byref(s)))
+        self.sizes = s
+        self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.n_x, self.n_c = int(s.n_x), int(s.n_c)
+        return self
+
+    def refined(self, N: int) -> "Problem":
+        """collo_problem_create_refined: the same problem on N elements."""
+        h = C.c_void_p()
+        _check(lib.collo_problem_create_refined(self.h, int(N), C.byref(h)))
+        return Problem._adopt(h, self.inst.with_mesh(N))
+
+    def defect(self, x):
+        """collo_defect: (per-element defects [N], their maximum)."""
+        x = _host_vec(x, self.n_x, "x")
+        d = np.zeros(self.N)
+        mx = C.c_double()
+        _check(lib.collo_defect(self.h, _ptr(x), d.ctypes.data, C.byref(mx)))
+        return d, mx.value
+
+    def set_start(self, x, lam=None):
+        """collo_problem_set_start: warm start of the next solve (x = None clears)."""
+        x = _host_vec(x, self.n_x, "x") if x is not None else None
+        lam = _host_vec(lam, self.n_c, "lam") if lam is not None else None
+        _check(lib.collo_problem_set_start(self.h, _ptr(x), _ptr(lam)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -431,6 +477,48 @@ def batch_solve(problems, theta0s=None, want_x: bool = False, **kw):
     o = Problem.ipm_options(**kw)
     _check(lib.collo_batch_solve(handles, n, thp, C.byref(o), res))
     return [_result_dict(res[i], *outs[i]) for i in range(n)]
+
+
+def interpolate(coarse, x_coarse, fine):
+    """collo_interpolate: the coarse solution on fine's mesh (host array)."""
+    xc = _host_vec(x_coarse, coarse.n_x, "x_coarse")
+    xf = np.zeros(fine.n_x)
+    _check(lib.collo_interpolate(coarse.h, _ptr(xc), fine.h, xf.ctypes.data))
+    return xf
+
+
+def refine_solve(problems, theta0s=None, defect_tol: float = 1e-6, max_levels: int = 3,
+                 max_elements: int = 0, **kw):
+    """collo_refine_solve: batched solve, then refine the converged problems whose
+    defect exceeds defect_tol (twice the elements, warm start) up to max_levels
+    times.  Returns (results, final problems, levels); a final problem the
+    library created is wrapped (and owned) here."""
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p.h.value for p in problems])
+    th = [_host_vec(_f64(p.inst.theta0 if theta0s is None else theta0s[i]), p.p, f"theta0s[{i}]")
+          for i, p in enumerate(problems)]
+    thp = (C.c_void_p * n)(*[t.ctypes.data for t in th])
+    res = (Result * n)()
+    thetas = []
+    for i, p in enumerate(problems):
+        theta = np.zeros(p.p)
+        res[i].theta = theta.ctypes.data
+        thetas.append(theta)
+    finals = (C.c_void_p * n)()
+    levels = (C.c_int * n)()
+    o = Problem.ipm_options(**kw)
+    _check(lib.collo_refine_solve(handles, n, thp, C.byref(o), float(defect_tol), int(max_levels),
+                                  int(max_elements), finals, res, levels))
+    out_probs = []
+    for i, p in enumerate(problems):
+        if finals[i] == p.h.value:
+            out_probs.append(p)
+        else:
+            size = Sizes()
+            _check(lib.collo_problem_sizes(C.c_void_p(finals[i]), C.byref(size)))
+            out_probs.append(Problem._adopt(finals[i], p.inst.with_mesh(size.N)))
+    return ([_result_dict(res[i], thetas[i], None, None) for i in range(n)], out_probs,
+            [int(levels[i]) for i in range(n)])
 
 
 def batch_time_phase(problems, phase: int, precision: int, reps: int = 10) -> float:

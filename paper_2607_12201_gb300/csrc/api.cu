@@ -272,6 +272,25 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   }
   std::unique_ptr<collo_problem> pr(new collo_problem());
   pr->device = dev;
+  {
+    HostInputs& h = pr->host;
+    h.react.assign(net->reactants, net->reactants + 2 * r);
+    h.prod.assign(net->products, net->products + 2 * r);
+    h.pidx.assign(net->param_index, net->param_index + r);
+    h.kfix.assign(net->k_fixed, net->k_fixed + r);
+    h.x0.assign(net->x0, net->x0 + n);
+    if (p > 0) {
+      h.lo.assign(net->theta_lo, net->theta_lo + p);
+      h.hi.assign(net->theta_hi, net->theta_hi + p);
+    }
+    if (M > 0) {
+      h.species.assign(obs->species, obs->species + obs->n_observables);
+      h.t.assign(data->t, data->t + M);
+      h.observable.assign(data->observable, data->observable + M);
+      h.y.assign(data->y, data->y + M);
+      h.sigma.assign(data->sigma, data->sigma + M);
+    }
+  }
   pr->precision = opts ? opts->precision : 0;
   pr->launch_mode = opts ? opts->launch_mode : 0;
   if (pr->launch_mode != 0 && pr->launch_mode != 1) {

@@ -157,6 +157,11 @@ struct FactorStore {
 
 struct collo_problem;
 namespace collo {
+// Host copies of a problem's inputs (for re-creating it on another mesh).
+struct HostInputs {
+  std::vector<int> react, prod, pidx, species, observable;
+  std::vector<double> kfix, x0, lo, hi, t, y, sigma;
+};
 collo_status ensure_factor_storage(collo_problem* pr, int precision);
 // Spare storage of `precision` (and the spare Schur block); swap_spare
 // exchanges the primary and spare factorization of `precision` together with
@@ -243,6 +248,14 @@ struct collo_problem {
   // and the failure-test switch that makes every barrier unreachable
   long long wait_polls = 0;
   int wait_unreachable = 0;
+  // inputs as given (collo_problem_create_refined)
+  collo::HostInputs host;
+  // warm start of the next solve (collo_problem_set_start): states and theta,
+  // multipliers
+  bool has_start = false;
+  double* start_x = nullptr;   // [n_x]
+  double* start_lam = nullptr; // [n_c]
+  double* refine_buf = nullptr;  // [N + 8] defects and their maximum
   collo::DevInst inst{};            // this problem's device pointers (host copy)
   collo::Runner* self = nullptr;    // single-instance runner (batch of one)
   ~collo_problem();

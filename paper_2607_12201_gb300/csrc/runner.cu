@@ -645,6 +645,18 @@ static collo_status ipm_begin(Runner& R, std::vector<IpmInst*>& ins) {
   if (s != COLLO_OK) return s;
   COLLO_CUDA(launch_sweep_b(R.d_insts, pl.d_int + pl.off_sw_w, pl.n_sw_w, pl.smem_sw_w,
                             pl.d_int + pl.off_sw_c, pl.n_sw_c, pl.smem_sw_c, R.stream));
+  // warm starts: the given states and multipliers replace the sweep's (theta
+  // was pushed into its bounds from the start's values by the initial point)
+  for (auto* I : ins) {
+    collo_problem* pr = I->prob;
+    if (!pr->has_start) continue;
+    const size_t nz = (size_t)(pr->n_x - pr->P.p);
+    COLLO_CUDA(cudaMemcpyAsync(pr->x, pr->start_x, nz * sizeof(double), cudaMemcpyDeviceToDevice,
+                               R.stream));
+    COLLO_CUDA(cudaMemcpyAsync(pr->lam, pr->start_lam, pr->n_c * sizeof(double),
+                               cudaMemcpyDeviceToDevice, R.stream));
+    pr->has_start = false;
+  }
   s = R.eval(3, 1 /* V_X */, 0, 0, false);
   if (s != COLLO_OK) return s;
   s = R.read_outs();
@@ -1044,8 +1056,10 @@ static collo_status ipm_prepare(Runner& R, int slot, collo_problem* pr, const do
     if ((s = ensure_spare_storage(pr, COLLO_PRECISION_MIXED)) != COLLO_OK) return s;
   }
   if ((s = R.attach(slot, pr)) != COLLO_OK) return s;
+  // a warm start (collo_problem_set_start) supplies theta0 from its x
+  const double* th = pr->has_start ? pr->start_x + (pr->n_x - pr->P.p) : theta0;
   if (pr->P.p)
-    COLLO_CUDA(cudaMemcpyAsync(pr->inst.th0, theta0, pr->P.p * sizeof(double), cudaMemcpyDefault,
+    COLLO_CUDA(cudaMemcpyAsync(pr->inst.th0, th, pr->P.p * sizeof(double), cudaMemcpyDefault,
                                R.stream));
   I = IpmInst();
   I.slot = slot;
