@@ -8,7 +8,8 @@
  * points each, and the ODE becomes the collocation equations of Eq. 3.
  * Interpolation points are right Radau (Radau IIA) roots with tau_0 = 0,
  * so the continuity weights of Eq. 2c are b_j = delta_jK.  Only K = 3 is
- * built.  One experiment (N_c = 1 in Eq. 1d / 2e).
+ * built.  One experiment (N_c = 1 in Eq. 1d / 2e) unless the problem is
+ * created with collo_problem_create_conditions.
  *
  * ---- Layouts (all arrays are C-contiguous, 0-based) ----------------------
  *   n species, r reactions, p estimated parameters, N elements, K = 3,
@@ -113,6 +114,21 @@ typedef struct collo_mesh {
   int K;                      /* interior collocation points; must be 3 */
 } collo_mesh;
 
+/* Experimental conditions (paper Eq. 1d / 2e: c = 1..N_c, each with its own
+ * state profile z^c and initial condition z^c(0), Eq. 1c / 2d; all share
+ * theta).  The condition-dependent variables p^c of Eq. 3 are lifted to inputs
+ * of the right-hand side: condition c multiplies each rate constant k_r by
+ * rate_scale[c][r], so f(z, theta; p^c) keeps one expression per species.
+ * Layout: the conditions' meshes one after another, z[c N + i][j][s] for
+ * condition c, element i of its N (mesh->N), and c[c N + i][0] is
+ * condition c's initial condition when i = 0, else continuity. */
+typedef struct collo_conditions {
+  int n_conditions;           /* N_c >= 1                                        */
+  const double* x0;           /* [N_c][n] initial state of each condition        */
+  const double* rate_scale;   /* [N_c][r] finite, > 0 (NULL: all 1)               */
+  const int* obs_condition;   /* [M] condition of each measurement (NULL: all 0) */
+} collo_conditions;
+
 typedef struct collo_problem_options {
   int precision;              /* COLLO_PRECISION_*, default for factor/solve */
   void* stream;               /* cudaStream_t to run on, or NULL for an own stream */
@@ -127,10 +143,12 @@ typedef struct collo_problem_options {
 typedef struct collo_problem collo_problem;
 
 typedef struct collo_sizes {
-  int n, r, p, N, K, M;
+  int n, r, p, N, K, M;       /* N: elements of all conditions (N_c x mesh->N) */
   int64_t n_x, n_c;
   int levels;                 /* block cyclic reduction levels */
   int64_t device_bytes;       /* device memory held by the problem */
+  int n_conditions;           /* N_c */
+  int elements_per_condition; /* mesh->N */
 } collo_sizes;
 
 /* Outputs of collo_eval.  Any pointer may be NULL (not wanted).
@@ -209,6 +227,16 @@ typedef struct collo_result {
 collo_status collo_problem_create(const collo_network* net, const collo_observables* obs,
                                   const collo_data* data, const collo_mesh* mesh,
                                   const collo_problem_options* opts, collo_problem** out);
+
+/* collo_problem_create for N_c experimental conditions (above); net->x0 is
+ * not used (each condition has its own).  conds = NULL or n_conditions = 1
+ * with the network's x0 is collo_problem_create.  INVALID_ARG on a bad
+ * condition index, non-finite initial states or scales <= 0. */
+collo_status collo_problem_create_conditions(const collo_network* net,
+                                             const collo_observables* obs, const collo_data* data,
+                                             const collo_mesh* mesh, const collo_conditions* conds,
+                                             const collo_problem_options* opts,
+                                             collo_problem** out);
 
 /* Wait for the problem's stream, free its device memory (and its stream when
  * the library created it).  NULL is a no-op. */

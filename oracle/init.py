@@ -5,8 +5,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 The paper initialises the discretised states from a forward solve of the ODE
 at the nominal parameters (Section "Optimization framework configurations").
 Here the forward solve is the collocation scheme itself, element by element:
-``z[0,0] = x0``; ``z[i,0] = sum_j b_j z[i-1,j]`` (``z[i-1,K]`` for Radau
-nodes); the interior states
+``z[0,0] = x0`` (with several experimental conditions, each condition's first
+element starts from that condition's x0); ``z[i,0] = sum_j b_j z[i-1,j]``
+(``z[i-1,K]`` for Radau nodes); the interior states
 ``Z = (z[i,1], ..., z[i,K])`` solve the element's K collocation equations
 ``sum_j D[k][j] z[i,j] - h f(z[i,k], theta) = 0`` by Newton's method started
 at ``z[i,k] = z[i,0]``, stopped when ``max|dZ| <= 1e-12 max(1, max|Z|)``
@@ -22,15 +23,16 @@ def forward_sweep(prob, theta, tol: float = 1e-12, max_iter: int = 30):
     n, N, K = prob.n, prob.N, prob.K
     D, h = prob.tab.D, prob.h
     z = np.zeros((N, K + 1, n))
-    start = np.array(prob.inst.x0, dtype=np.float64)
     failures = 0
     for i in range(N):
+        if i % prob.Nch == 0:   # a condition's first element starts from its x0
+            start = prob.x0c[i // prob.Nch].copy()
         z[i, 0] = start
         Z = np.tile(start, (K, 1))                       # [K, n]
         ok = False
         for _ in range(max_iter):
-            f = prob.rhs(Z, theta)                        # [K, n]
-            Fz, _ = prob.rhs_jac(Z, theta)                # [K, n, n]
+            f = prob.rhs(Z, theta, prob.escale[i])        # [K, n]
+            Fz, _ = prob.rhs_jac(Z, theta, prob.escale[i])  # [K, n, n]
             G = np.zeros((K, n))
             Jm = np.zeros((K * n, K * n))
             for k in range(1, K + 1):

@@ -52,8 +52,22 @@ class Problem:
         self.tab = Tables(K, getattr(inst, "scheme", "radau"))
         self.radau = self.tab.scheme == "radau"
         self.K = K
-        self.n, self.r, self.N, self.p = inst.n, inst.r, inst.N, inst.p
+        self.n, self.r, self.p = inst.n, inst.r, inst.p
+        # experimental conditions (Eq. 1d / 2e): condition c's chain of Nch
+        # elements is elements c Nch .. (c + 1) Nch - 1; shared theta
+        self.Nc = getattr(inst, "Nc", 1)
+        self.Nch = inst.N
+        self.N = self.Nc * self.Nch
         self.h = inst.T / inst.N
+        cx0 = getattr(inst, "cond_x0", None)
+        self.x0c = np.asarray(inst.x0 if cx0 is None else cx0, dtype=np.float64).reshape(
+            self.Nc, self.n)
+        # condition inputs (the lifted p^c of Eq. 3) multiplying each rate
+        # constant, per element
+        sc = getattr(inst, "cond_scale", None)
+        sc = np.ones((self.Nc, self.r)) if sc is None else np.asarray(sc, dtype=np.float64)
+        self.escale = np.repeat(sc.reshape(self.Nc, self.r), self.Nch, axis=0)   # [N, r]
+        self.starts = np.arange(0, self.N, self.Nch)
         self.nz = self.n * self.N * (K + 1)
         self.n_x = self.nz + self.p
         self.n_c = self.nz
@@ -69,11 +83,12 @@ class Problem:
         # observation -> (element, tau, basis weights)
         self.obs_elem = np.zeros(inst.M, dtype=np.int64)
         self.obs_w = np.zeros((inst.M, K + 1))
+        ocond = getattr(inst, "obs_cond", None)
         for m in range(inst.M):
             u = inst.obs_t[m] * inst.N / inst.T
             i = int(math.ceil(u)) - 1
             i = min(max(i, 0), inst.N - 1)
-            self.obs_elem[m] = i
+            self.obs_elem[m] = (0 if ocond is None else int(ocond[m])) * self.Nch + i
             self.obs_w[m] = basis(self.tab.tau, u - i)
 
     # -- index helpers ------------------------------------------------------
@@ -130,16 +145,21 @@ class Problem:
             hess.append((b, a, 1.0))
         return mon, grads, hess
 
-    def rhs(self, zn, theta):
-        """f(z, theta) for zn [..., n] -> [..., n]."""
+    def _scaled(self, k, scale, j):
+        """Rate constant k[j] times the condition input of reaction j (scale
+        [..., r] broadcast against the node shape, or None: 1)."""
+        return k[j] if scale is None else k[j] * scale[..., j]
+
+    def rhs(self, zn, theta, scale=None):
+        """f(z, theta) for zn [..., n] -> [..., n]; scale [..., r]: condition inputs."""
         k, _, _ = self.rate_constants(theta)
         f = np.zeros(zn.shape)
         for j in range(self.r):
             mon, _, _ = self.monomial(zn, j)
-            f += (k[j] * mon)[..., None] * self.nu[:, j]
+            f += (self._scaled(k, scale, j) * mon)[..., None] * self.nu[:, j]
         return f
 
-    def rhs_jac(self, zn, theta):
+    def rhs_jac(self, zn, theta, scale=None):
         """df/dz [..., n, n] and df/dtheta [..., n, p]."""
         k, dk, _ = self.rate_constants(theta)
         Fz = np.zeros(zn.shape + (self.n,))
@@ -147,13 +167,13 @@ class Problem:
         for j in range(self.r):
             mon, grads, _ = self.monomial(zn, j)
             for (t, g) in grads:
-                Fz[..., :, t] += (k[j] * g)[..., None] * self.nu[:, j]
+                Fz[..., :, t] += (self._scaled(k, scale, j) * g)[..., None] * self.nu[:, j]
             q = self.inst.pidx[j]
             if q >= 0:
-                Ft[..., :, q] += (dk[j] * mon)[..., None] * self.nu[:, j]
+                Ft[..., :, q] += (self._scaled(dk, scale, j) * mon)[..., None] * self.nu[:, j]
         return Fz, Ft
 
-    def rhs_hess(self, zn, theta, lam):
+    def rhs_hess(self, zn, theta, lam, scale=None):
         """Weighted second derivatives of sum_s lam[..., s] f_s:
         Hzz [..., n, n], Hzt [..., n, p], Htt [p, p] (summed over nodes)."""
         k, dk, d2k = self.rate_constants(theta)
@@ -164,13 +184,17 @@ class Problem:
             omega = lam @ self.nu[:, j]          # [...]
             mon, grads, hess = self.monomial(zn, j)
             for (a, b, v) in hess:
-                Hzz[..., a, b] += omega * k[j] * v
+                Hzz[..., a, b] += omega * self._scaled(k, scale, j) * v
             q = self.inst.pidx[j]
             if q >= 0:
                 for (t, g) in grads:
-                    Hzt[..., t, q] += omega * dk[j] * g
-                Htt[q, q] += np.sum(omega * d2k[j] * mon)
+                    Hzt[..., t, q] += omega * self._scaled(dk, scale, j) * g
+                Htt[q, q] += np.sum(omega * self._scaled(d2k, scale, j) * mon)
         return Hzz, Hzt, Htt
+
+    def node_scale(self):
+        """Condition inputs broadcast over the K collocation nodes: [N, 1, r]."""
+        return self.escale[:, None, :]
 
     # -- objective ------------------------------------------------------------
     def objective(self, x):
@@ -205,12 +229,13 @@ class Problem:
         z, theta = self.split(x)
         D, h, K = self.tab.D, self.h, self.K
         c = np.zeros((self.N, K + 1, self.n))
-        c[0, 0] = z[0, 0] - self.inst.x0
         if self.radau:
             c[1:, 0] = z[1:, 0] - z[:-1, K]
         else:
             c[1:, 0] = z[1:, 0] - np.einsum("j,ijs->is", self.tab.b, z[:-1])
-        f = self.rhs(z[:, 1:, :], theta)               # [N, K, n]
+        # each condition's first element: its initial condition (Eq. 2d)
+        c[self.starts, 0] = z[self.starts, 0] - self.x0c
+        f = self.rhs(z[:, 1:, :], theta, self.node_scale())   # [N, K, n]
         for k in range(1, K + 1):
             acc = np.zeros((self.N, self.n))
             for j in range(K + 1):
@@ -225,17 +250,20 @@ class Problem:
     def jacobian(self, x):
         z, theta = self.split(x)
         D, h, K, n, N, p = self.tab.D, self.h, self.K, self.n, self.N, self.p
-        Fz, Ft = self.rhs_jac(z[:, 1:, :], theta)      # [N,K,n,n], [N,K,n,p]
+        Fz, Ft = self.rhs_jac(z[:, 1:, :], theta, self.node_scale())   # [N,K,n,n], [N,K,n,p]
         Z = self._zidx()
         rows, cols, vals = [], [], []
-        # continuity / initial rows: +I on z[i,0], -b_j I on z[i-1,j] (Radau: -I on z[i-1,K])
+        # continuity / initial rows: +I on z[i,0], -b_j I on z[i-1,j] (Radau: -I on
+        # z[i-1,K]) except at each condition's first element (initial condition)
         rows.append(Z[:, 0].ravel()); cols.append(Z[:, 0].ravel()); vals.append(np.ones(N * n))
+        cont = np.array([i for i in range(1, N) if i % self.Nch != 0], dtype=np.int64)
         if self.radau:
-            rows.append(Z[1:, 0].ravel()); cols.append(Z[:-1, K].ravel()); vals.append(-np.ones((N - 1) * n))
+            rows.append(Z[cont, 0].ravel()); cols.append(Z[cont - 1, K].ravel())
+            vals.append(-np.ones(len(cont) * n))
         else:
             for j in range(K + 1):
-                rows.append(Z[1:, 0].ravel()); cols.append(Z[:-1, j].ravel())
-                vals.append(np.full((N - 1) * n, -self.tab.b[j]))
+                rows.append(Z[cont, 0].ravel()); cols.append(Z[cont - 1, j].ravel())
+                vals.append(np.full(len(cont) * n, -self.tab.b[j]))
         for k in range(1, K + 1):
             for j in range(K + 1):
                 if j != k:
@@ -258,7 +286,7 @@ class Problem:
         z, theta = self.split(x)
         lamr = lam.reshape(self.N, self.K + 1, self.n)
         h, K, n, N, p = self.h, self.K, self.n, self.N, self.p
-        Hzz, Hzt, Htt = self.rhs_hess(z[:, 1:, :], theta, lamr[:, 1:, :])
+        Hzz, Hzt, Htt = self.rhs_hess(z[:, 1:, :], theta, lamr[:, 1:, :], self.node_scale())
         Z = self._zidx()
         r0, c0, v0 = self.objective_hessian_entries()
         rows = [np.array(r0, dtype=np.int64)]

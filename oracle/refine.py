@@ -58,7 +58,7 @@ def residual_at(prob: Problem, x, points):
         db = basis_derivative(tau, t)
         zt = np.einsum("j,ijs->is", lb, z)
         dz = np.einsum("j,ijs->is", db, z)
-        out[:, m, :] = np.abs(dz - prob.h * prob.rhs(zt, theta))
+        out[:, m, :] = np.abs(dz - prob.h * prob.rhs(zt, theta, prob.escale))
     return out
 
 
@@ -74,12 +74,13 @@ def interpolate(coarse: Problem, x, fine: Problem):
     """Fine-mesh x from the coarse solution x (above)."""
     zc, theta = coarse.split(np.asarray(x, dtype=np.float64))
     zf = np.zeros((fine.N, fine.K + 1, fine.n))
-    for i in range(fine.N):
+    for e in range(fine.N):
+        c, i = divmod(e, fine.Nch)   # experimental condition, element within it
         for j in range(fine.K + 1):
             t = (i + fine.tab.tau[j]) * fine.h
             u = t / coarse.h
-            ic = min(max(int(math.ceil(u)) - 1, 0), coarse.N - 1)
-            zf[i, j] = basis(coarse.tab.tau, u - ic) @ zc[ic]
+            ic = min(max(int(math.ceil(u)) - 1, 0), coarse.Nch - 1)
+            zf[e, j] = basis(coarse.tab.tau, u - ic) @ zc[c * coarse.Nch + ic]
     return np.concatenate([zf.reshape(-1), theta])
 
 

@@ -51,6 +51,11 @@ class Mesh(C.Structure):
     _fields_ = [("T", C.c_double), ("N", C.c_int), ("K", C.c_int)]
 
 
+class Conditions(C.Structure):
+    _fields_ = [("n_conditions", C.c_int), ("x0", _dp), ("rate_scale", _dp),
+                ("obs_condition", _ip)]
+
+
 class ProblemOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("device", C.c_int),
                 ("launch_mode", C.c_int), ("reserved", C.c_int * 6)]
@@ -59,7 +64,8 @@ class ProblemOptions(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("n", C.c_int), ("r", C.c_int), ("p", C.c_int), ("N", C.c_int), ("K", C.c_int),
                 ("M", C.c_int), ("n_x", C.c_int64), ("n_c", C.c_int64), ("levels", C.c_int),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("n_conditions", C.c_int),
+                ("elements_per_condition", C.c_int)]
 
 
 class EvalOut(C.Structure):
@@ -105,6 +111,10 @@ def _load():
                                          C.POINTER(Data), C.POINTER(Mesh),
                                          C.POINTER(ProblemOptions), C.POINTER(P)]
     lib.collo_problem_create.restype = C.c_int
+    lib.collo_problem_create_conditions.argtypes = [
+        C.POINTER(Network), C.POINTER(Observables), C.POINTER(Data), C.POINTER(Mesh),
+        C.POINTER(Conditions), C.POINTER(ProblemOptions), C.POINTER(P)]
+    lib.collo_problem_create_conditions.restype = C.c_int
     lib.collo_problem_destroy.argtypes = [P]
     lib.collo_problem_destroy.restype = None
     lib.collo_problem_sizes.argtypes = [P, C.POINTER(Sizes)]
@@ -269,13 +279,27 @@ class Problem:
         mesh = Mesh(float(inst.T), int(inst.N), int(inst.K))
         opt = ProblemOptions(precision, stream, device, launch_mode)
         h = C.c_void_p()
-        _check(lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh),
-                                        C.byref(opt), C.byref(h)))
+        if getattr(inst, "cond_x0", None) is not None:
+            k["cx0"] = _f64(inst.cond_x0).reshape(-1)
+            k["csc"] = (_f64(inst.cond_scale).reshape(-1)
+                        if getattr(inst, "cond_scale", None) is not None else None)
+            k["oc"] = (_i32(inst.obs_cond) if getattr(inst, "obs_cond", None) is not None
+                       else None)
+            cond = Conditions(inst.Nc, dp(k["cx0"]),
+                              dp(k["csc"]) if k["csc"] is not None else None,
+                              ip(k["oc"]) if k["oc"] is not None else None)
+            _check(lib.collo_problem_create_conditions(
+                C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh), C.byref(cond),
+                C.byref(opt), C.byref(h)))
+        else:
+            _check(lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data),
+                                            C.byref(mesh), C.byref(opt), C.byref(h)))
         self.h = h
         s = Sizes()
         _check(lib.collo_problem_sizes(self.h, C.byref(s)))
         self.sizes = s
         self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.Nc, self.Nch = s.n_conditions, s.elements_per_condition
         self.n_x, self.n_c = int(s.n_x), int(s.n_c)
 
     @classmethod
@@ -289,6 +313,7 @@ class Problem:
         _check(lib.collo_problem_sizes(self.h, C.byref(s)))
         self.sizes = s
         self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.Nc, self.Nch = s.n_conditions, s.elements_per_condition
         self.n_x, self.n_c = int(s.n_x), int(s.n_c)
         return self
 
@@ -516,7 +541,8 @@ def refine_solve(problems, theta0s=None, defect_tol: float = 1e-6, max_levels: i
         else:
             size = Sizes()
             _check(lib.collo_problem_sizes(C.c_void_p(finals[i]), C.byref(size)))
-            out_probs.append(Problem._adopt(finals[i], p.inst.with_mesh(size.N)))
+            out_probs.append(Problem._adopt(finals[i],
+                                            p.inst.with_mesh(size.elements_per_condition)))
     return ([_result_dict(res[i], thetas[i], None, None) for i in range(n)], out_probs,
             [int(levels[i]) for i in range(n)])
 

@@ -221,15 +221,45 @@ long long collo_launch_count(void) { return g_launches.load(); }
 collo_status collo_problem_create(const collo_network* net, const collo_observables* obs,
                                   const collo_data* data, const collo_mesh* mesh,
                                   const collo_problem_options* opts, collo_problem** out) {
+  return collo_problem_create_conditions(net, obs, data, mesh, nullptr, opts, out);
+}
+
+collo_status collo_problem_create_conditions(const collo_network* net,
+                                             const collo_observables* obs, const collo_data* data,
+                                             const collo_mesh* mesh, const collo_conditions* conds,
+                                             const collo_problem_options* opts,
+                                             collo_problem** out) {
   if (!out) { set_error("out is NULL"); return COLLO_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!net || !mesh || !data || !obs) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
   const int n = net->n_species, r = net->n_reactions, p = net->n_params;
-  const int N = mesh->N, M = data->n_obs;
-  if (n < 1 || r < 1 || p < 0 || N < 1 || M < 0) { set_error("bad sizes"); return COLLO_ERR_INVALID_ARG; }
+  const int Nch = mesh->N, M = data->n_obs;
+  const int Nc = conds ? conds->n_conditions : 1;
+  if (n < 1 || r < 1 || p < 0 || Nch < 1 || M < 0 || Nc < 1) {
+    set_error("bad sizes"); return COLLO_ERR_INVALID_ARG;
+  }
+  if ((long long)Nc * Nch > (1 << 30)) { set_error("too many elements"); return COLLO_ERR_INVALID_ARG; }
+  const int N = Nc * Nch;   // elements of all conditions
+  if (conds) {
+    if (!conds->x0) { set_error("NULL condition initial states"); return COLLO_ERR_INVALID_ARG; }
+    if (!finite_all(conds->x0, Nc * n)) {
+      set_error("non-finite condition initial state"); return COLLO_ERR_INVALID_ARG;
+    }
+    if (conds->rate_scale)
+      for (int k = 0; k < Nc * r; ++k)
+        if (!std::isfinite(conds->rate_scale[k]) || !(conds->rate_scale[k] > 0)) {
+          set_error("condition rate scales must be finite and > 0"); return COLLO_ERR_INVALID_ARG;
+        }
+    if (conds->obs_condition)
+      for (int m = 0; m < M; ++m)
+        if (conds->obs_condition[m] < 0 || conds->obs_condition[m] >= Nc) {
+          set_error("bad measurement condition"); return COLLO_ERR_INVALID_ARG;
+        }
+  }
   if (mesh->K != KC) { set_error("only K = 3 (Radau IIA) is built"); return COLLO_ERR_INVALID_ARG; }
   if (!(mesh->T > 0) || !std::isfinite(mesh->T)) { set_error("T must be positive"); return COLLO_ERR_INVALID_ARG; }
-  if (!net->reactants || !net->products || !net->param_index || !net->k_fixed || !net->x0 ||
+  if (!net->reactants || !net->products || !net->param_index || !net->k_fixed ||
+      (!conds && !net->x0) ||
       (p > 0 && (!net->theta_lo || !net->theta_hi))) {
     set_error("NULL network array"); return COLLO_ERR_INVALID_ARG;
   }
@@ -247,7 +277,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
     if (q < -1 || q >= p) { set_error("bad parameter index"); return COLLO_ERR_INVALID_ARG; }
     if (q < 0 && !std::isfinite(net->k_fixed[j])) { set_error("non-finite fixed rate"); return COLLO_ERR_INVALID_ARG; }
   }
-  if (!finite_all(net->x0, n)) { set_error("non-finite x0"); return COLLO_ERR_INVALID_ARG; }
+  if (!conds && !finite_all(net->x0, n)) { set_error("non-finite x0"); return COLLO_ERR_INVALID_ARG; }
   for (int q = 0; q < p; ++q)
     if (!std::isfinite(net->theta_lo[q]) || !std::isfinite(net->theta_hi[q]) ||
         !(net->theta_lo[q] < net->theta_hi[q])) {
@@ -278,7 +308,14 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
     h.prod.assign(net->products, net->products + 2 * r);
     h.pidx.assign(net->param_index, net->param_index + r);
     h.kfix.assign(net->k_fixed, net->k_fixed + r);
-    h.x0.assign(net->x0, net->x0 + n);
+    if (conds) h.cond_x0.assign(conds->x0, conds->x0 + (size_t)Nc * n);
+    else h.cond_x0.assign(net->x0, net->x0 + n);
+    h.x0 = std::vector<double>(h.cond_x0.begin(), h.cond_x0.begin() + n);
+    h.n_conditions = Nc;
+    if (conds && conds->rate_scale)
+      h.cond_scale.assign(conds->rate_scale, conds->rate_scale + (size_t)Nc * r);
+    if (conds && conds->obs_condition && M > 0)
+      h.obs_cond.assign(conds->obs_condition, conds->obs_condition + M);
     if (p > 0) {
       h.lo.assign(net->theta_lo, net->theta_lo + p);
       h.hi.assign(net->theta_hi, net->theta_hi + p);
@@ -305,9 +342,10 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   }
   DevProb& P = pr->P;
   P.n = n; P.r = r; P.p = p; P.N = N; P.M = M;
+  P.Nc = Nc; P.Nch = Nch;
   P.m = 8 * n; P.ext = 8 * n + p; P.bext = 4 * n + p;
   P.logscale = net->log10_params ? 1 : 0;
-  P.T = mesh->T; P.h = mesh->T / N;
+  P.T = mesh->T; P.h = mesh->T / Nch;
   radau_tables(P.tau, P.D);
   pr->n_x = (int64_t)n * N * NP + p;
   pr->n_c = (int64_t)n * N * NP;
@@ -380,9 +418,10 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   // observations: element from the same rule the kernels use, grouped by element
   std::vector<int> oelem(M);
   for (int m = 0; m < M; ++m) {
-    double u = data->t[m] * N / mesh->T;
+    double u = data->t[m] * Nch / mesh->T;
     int i = (int)std::ceil(u) - 1;
-    oelem[m] = std::min(std::max(i, 0), N - 1);
+    const int c = (conds && conds->obs_condition) ? conds->obs_condition[m] : 0;
+    oelem[m] = c * Nch + std::min(std::max(i, 0), Nch - 1);
   }
   std::vector<int> order(M);
   for (int m = 0; m < M; ++m) order[m] = m;
@@ -414,7 +453,9 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   P.prod = up_i(net->products, 2 * (size_t)r);
   P.pidx = up_i(net->param_index, r);
   P.kfix = up_d(net->k_fixed, r);
-  P.x0 = up_d(net->x0, n);
+  P.x0 = up_d(pr->host.cond_x0.data(), (size_t)Nc * n);
+  P.kscale = pr->host.cond_scale.empty() ? nullptr
+                                          : up_d(pr->host.cond_scale.data(), (size_t)Nc * r);
   P.theta_lo = up_d(p ? net->theta_lo : nullptr, p);
   P.theta_hi = up_d(p ? net->theta_hi : nullptr, p);
   P.nu_ptr = up_i(nu_ptr.data(), n + 1);
@@ -496,6 +537,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
   const bool sweep_global = sweep_dim * (sweep_dim + 1) * sizeof(float) > 160 * 1024;
   if (sweep_global) pr->sweep_work = A.alloc<float>(sweep_dim * (sweep_dim + 1));
   bool ok = P.react && P.prod && P.pidx && P.kfix && P.x0 && P.theta_lo && P.theta_hi &&
+            (pr->host.cond_scale.empty() || P.kscale) &&
             P.nu_ptr && P.nu_r && P.nu_v && P.rs_ptr && P.rs_r && P.pr_ptr && P.pr_r && pat_ok &&
             P.obs_ptr && P.obs_s && P.obs_y && P.obs_sig && d_obs_t && obs_w && obs_elem_chk &&
             E.c && E.grad && E.JZ && E.JT && E.Wzz && E.Wzt && E.Wobj && E.part && E.wtt_part &&
@@ -519,7 +561,7 @@ collo_status collo_problem_create(const collo_network* net, const collo_observab
     I.n_x = pr->n_x; I.n_c = pr->n_c;
   }
   COLLO_CUDA(cudaMemsetAsync(pr->sigma, 0, pr->n_x * sizeof(double), pr->stream));
-  COLLO_CUDA(launch_obs_weights(P, M, N, mesh->T, d_obs_t, obs_elem_chk, obs_w, pr->stream));
+  COLLO_CUDA(launch_obs_weights(P, M, Nch, mesh->T, d_obs_t, obs_elem_chk, obs_w, pr->stream));
   COLLO_CUDA(cudaStreamSynchronize(pr->stream));
   COLLO_CUDA(cudaGetLastError());
   *out = pr.release();
@@ -541,6 +583,8 @@ collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out) {
   out->K = KC; out->M = prob->P.M; out->n_x = prob->n_x; out->n_c = prob->n_c;
   out->levels = bcr_levels(prob->P.N);
   out->device_bytes = problem_held_bytes(prob);
+  out->n_conditions = prob->P.Nc;
+  out->elements_per_condition = prob->P.Nch;
   return COLLO_OK;
 }
 

@@ -32,7 +32,8 @@ __host__ __device__ inline int grp_con(int g) { return g == 0 ? 1 : (g == 1 ? 2 
 
 // Plain-old-data view of one problem's device arrays, passed by value.
 struct DevProb {
-  int n, r, p, N, M;
+  int n, r, p, N, M;   // N: elements of all conditions (Nc x Nch)
+  int Nc, Nch;         // experimental conditions, elements per condition
   int m;        // 8 n: element unknowns
   int ext;      // 8 n + p: element block plus parameter border
   int bext;     // 4 n + p: cyclic-reduction block (2n) + two neighbour slices + border
@@ -46,7 +47,8 @@ struct DevProb {
   const int* prod;       // [r][2]
   const int* pidx;       // [r]
   const double* kfix;    // [r]
-  const double* x0;      // [n]
+  const double* x0;      // [Nc][n] initial state of each condition
+  const double* kscale;  // [Nc][r] condition multipliers of the rate constants, or null
   const double* theta_lo, *theta_hi;  // [p]
   // species -> (reaction, stoichiometric coefficient) CSR
   const int* nu_ptr; const int* nu_r; const double* nu_v;
@@ -184,6 +186,9 @@ enum OutSlot {
   O_INERT = 24,                               // 3 x long long (24..26)
   O_BERR = 28,                                // grid barrier error flag (as double)
 };
+
+// Element i starts its condition's chain (its row 0 is an initial condition).
+__host__ __device__ inline bool chain_start(const DevProb& P, int i) { return i % P.Nch == 0; }
 
 // Find k with pre[k] <= t < pre[k+1] (pre[0] = 0, A + 1 entries).
 __device__ inline int find_item(const int* __restrict__ pre, int A, int t) {

@@ -95,7 +95,13 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
     ze[t] = v;
     le[t] = (DERIV && lam) ? lam[zoff + t] : 0.0;
   }
-  for (int j = tid; j < r; j += EVAL_BS) rate_const(P, j, x, dx, alpha, kr[j], dkr[j], d2kr[j]);
+  for (int j = tid; j < r; j += EVAL_BS) {
+    rate_const(P, j, x, dx, alpha, kr[j], dkr[j], d2kr[j]);
+    if (P.kscale) {   // the element's condition input (lifted p^c, Eq. 3)
+      const double u = P.kscale[(size_t)(i / P.Nch) * r + j];
+      kr[j] *= u; dkr[j] *= u; d2kr[j] *= u;
+    }
+  }
   __syncthreads();
   for (int idx = tid; idx < KC * r; idx += EVAL_BS) {
     const int k = idx / r + 1, j = idx - (idx / r) * r;
@@ -123,11 +129,11 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
     double c;
     if (j == 0) {
       double prev;
-      if (i > 0) {
+      if (!chain_start(P, i)) {
         prev = x[zoff - n + s];
         if (dx) prev += alpha * dx[zoff - n + s];
-      } else {
-        prev = P.x0[s];
+      } else {   // initial condition of the element's experimental condition
+        prev = P.x0[(size_t)(i / P.Nch) * n + s];
       }
       c = ze[s] - prev;
     } else {

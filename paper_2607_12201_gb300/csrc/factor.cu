@@ -317,7 +317,7 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
   T* C = F.Cpl + (size_t)e * n * n;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int s2 = idx / n, t = idx - s2 * n;
-    C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
+    C[idx] = (!chain_start(P, e) && s2 == t) ? T(-1) : T(0);
   }
   __syncthreads();
 }
@@ -778,7 +778,7 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   T* C = F.Cpl + (size_t)e * n * n;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int s2 = quot(idx, n, inv_n), t = idx - s2 * n;
-    C[idx] = (e > 0 && s2 == t) ? T(-1) : T(0);
+    C[idx] = (!chain_start(P, e) && s2 == t) ? T(-1) : T(0);
   }
 }
 

@@ -140,15 +140,19 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
   double* dZ = Z + dim;            // [3n]
   float* Jm = gwork ? gwork : reinterpret_cast<float*>(dZ + dim);  // [dim][dim+1]
   const size_t nz = (size_t)P.N * NP * n;
-  for (int j = tid; j < r; j += SWEEP_BS) {
-    const int q = P.pidx[j];
-    if (q < 0) kr[j] = P.kfix[j];
-    else kr[j] = P.logscale ? exp10(x[nz + q]) : x[nz + q];
-  }
-  for (int s = tid; s < n; s += SWEEP_BS) z0[s] = P.x0[s];
-  __syncthreads();
   int nfail = 0;
   for (int i = 0; i < P.N; ++i) {
+    if (chain_start(P, i)) {   // a condition's first element: its rates and x0
+      const int c = i / P.Nch;
+      for (int j = tid; j < r; j += SWEEP_BS) {
+        const int q = P.pidx[j];
+        double k = q < 0 ? P.kfix[j] : (P.logscale ? exp10(x[nz + q]) : x[nz + q]);
+        if (P.kscale) k *= P.kscale[(size_t)c * r + j];
+        kr[j] = k;
+      }
+      for (int s = tid; s < n; s += SWEEP_BS) z0[s] = P.x0[(size_t)c * n + s];
+      __syncthreads();
+    }
     for (int t = tid; t < dim; t += SWEEP_BS) Z[t] = z0[t % n];
     __syncthreads();
     bool ok = false;
@@ -304,13 +308,6 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
   double* z0 = reinterpret_cast<double*>(rows + WSWEEP * (WSWEEP + 1));  // [n]
   double* Z = z0 + n;              // [3n]
   const size_t nz = (size_t)P.N * NP * n;
-  for (int j = lane; j < r; j += 32) {
-    const int q = P.pidx[j];
-    if (q < 0) kr[j] = P.kfix[j];
-    else kr[j] = P.logscale ? exp10(x[nz + q]) : x[nz + q];
-  }
-  for (int s = lane; s < n; s += 32) z0[s] = P.x0[s];
-  __syncwarp();
   const int rk = lane < dim ? lane / n + 1 : 1;
   const int rs = lane < dim ? lane - (rk - 1) * n : 0;
   int nfail = 0;
@@ -318,6 +315,18 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
   int piv[WSWEEP];
   double dZ = 0.0;                 // lane's stage increment in the previous element
   for (int i = 0; i < P.N; ++i) {
+    if (chain_start(P, i)) {   // a condition's first element: its rates and x0
+      const int c = i / P.Nch;
+      for (int j = lane; j < r; j += 32) {
+        const int q = P.pidx[j];
+        double k = q < 0 ? P.kfix[j] : (P.logscale ? exp10(x[nz + q]) : x[nz + q]);
+        if (P.kscale) k *= P.kscale[(size_t)c * r + j];
+        kr[j] = k;
+      }
+      for (int s = lane; s < n; s += 32) z0[s] = P.x0[(size_t)c * n + s];
+      dZ = 0.0;
+      __syncwarp();
+    }
     if (lane < dim) Z[lane] = z0[rs] + dZ;
     __syncwarp();
     bool ok = false, have_lu = false;

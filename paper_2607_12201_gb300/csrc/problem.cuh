@@ -159,8 +159,9 @@ struct collo_problem;
 namespace collo {
 // Host copies of a problem's inputs (for re-creating it on another mesh).
 struct HostInputs {
-  std::vector<int> react, prod, pidx, species, observable;
-  std::vector<double> kfix, x0, lo, hi, t, y, sigma;
+  std::vector<int> react, prod, pidx, species, observable, obs_cond;
+  std::vector<double> kfix, x0, lo, hi, t, y, sigma, cond_x0, cond_scale;
+  int n_conditions = 1;
 };
 collo_status ensure_factor_storage(collo_problem* pr, int precision);
 // Spare storage of `precision` (and the spare Schur block); swap_spare

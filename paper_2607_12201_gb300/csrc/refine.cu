@@ -60,7 +60,9 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
   for (int t = tid; t < NP * n; t += DEF_BS) ze[t] = x[zoff + t];
   for (int j = tid; j < r; j += DEF_BS) {
     const int q = P.pidx[j];
-    kr[j] = q < 0 ? P.kfix[j] : (P.logscale ? exp10(x[nz + q]) : x[nz + q]);
+    double k = q < 0 ? P.kfix[j] : (P.logscale ? exp10(x[nz + q]) : x[nz + q]);
+    if (P.kscale) k *= P.kscale[(size_t)(i / P.Nch) * r + j];
+    kr[j] = k;
   }
   __syncthreads();
   for (int idx = tid; idx < KC * n; idx += DEF_BS) {
@@ -101,7 +103,8 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
 }
 
 // Fine-mesh states from the coarse solution: one thread per (fine element,
-// point, species).  Time t = (i + tau_j) h_f lies in coarse element
+// point, species).  In each experimental condition, time t = (i + tau_j) h_f
+// (i the element within the condition) lies in the condition's coarse element
 // ceil(t / h_c) - 1 (clamped; a time on a coarse boundary belongs to the left
 // element, t = 0 to the first), at tau_c = t / h_c - i_c.
 __global__ void k_interp(DevProb C, const double* __restrict__ xc, DevProb F,
@@ -115,16 +118,18 @@ __global__ void k_interp(DevProb C, const double* __restrict__ xc, DevProb F,
   }
   const int n = F.n, s = (int)(idx % n);
   const size_t ij = idx / n;
-  const int j = (int)(ij % NP), i = (int)(ij / NP);
+  const int j = (int)(ij % NP), ie = (int)(ij / NP);
+  const int cond = ie / F.Nch, i = ie - cond * F.Nch;
   const double t = ((double)i + F.tau[j]) * F.h;
   const double u = t / C.h;
   int ic = (int)ceil(u) - 1;
-  ic = ic < 0 ? 0 : (ic > C.N - 1 ? C.N - 1 : ic);
+  ic = ic < 0 ? 0 : (ic > C.Nch - 1 ? C.Nch - 1 : ic);
   const double tc = u - ic;
   double l[NP];
   lagrange(C, tc, l, nullptr);
+  const size_t ec = (size_t)cond * C.Nch + ic;
   double v = 0.0;
-  for (int a = 0; a < NP; ++a) v += l[a] * xc[((size_t)ic * NP + a) * n + s];
+  for (int a = 0; a < NP; ++a) v += l[a] * xc[(ec * NP + a) * n + s];
   xf[idx] = v;
 }
 
@@ -193,7 +198,10 @@ collo_status collo_problem_create_refined(const collo_problem* coarse, int N,
   o.precision = coarse->precision;
   o.device = coarse->device;
   o.launch_mode = coarse->launch_mode;
-  return collo_problem_create(&net, &obs, &data, &mesh, &o, out);
+  collo_conditions cond{h.n_conditions, h.cond_x0.data(),
+                        h.cond_scale.empty() ? nullptr : h.cond_scale.data(),
+                        h.obs_cond.empty() ? nullptr : h.obs_cond.data()};
+  return collo_problem_create_conditions(&net, &obs, &data, &mesh, &cond, &o, out);
 }
 
 collo_status collo_defect(collo_problem* prob, const double* x, double* per_element,
@@ -223,7 +231,7 @@ collo_status collo_interpolate(collo_problem* coarse, const double* x_coarse, co
     return COLLO_ERR_INVALID_ARG;
   }
   if (coarse->device != fine->device || coarse->P.n != fine->P.n || coarse->P.p != fine->P.p ||
-      coarse->P.T != fine->P.T) {
+      coarse->P.T != fine->P.T || coarse->P.Nc != fine->P.Nc) {
     set_error("coarse and fine problems differ in more than their meshes");
     return COLLO_ERR_INVALID_ARG;
   }
@@ -294,7 +302,7 @@ collo_status collo_refine_solve(collo_problem* const* probs, int count, const do
       const int st = results[i].status;
       if (st != COLLO_OK && st != COLLO_ACCEPTABLE) continue;
       collo_problem* c = cur[i];
-      const int Nf = 2 * c->P.N;
+      const int Nf = 2 * c->P.Nch;   // elements per condition
       if (max_elements > 0 && Nf > max_elements) continue;
       double mx = 0.0;
       if ((s = collo_defect(c, c->x, nullptr, &mx)) != COLLO_OK) { cleanup(); return s; }

@@ -104,7 +104,7 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
 #pragma unroll
       for (int k = 1; k < NP; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
       if (j == 0) y += vl[zoff + s];
-      if (j == KC && i + 1 < N) y -= vl[zoff + NP * n + s];
+      if (j == KC && i + 1 < N && !chain_start(P, i + 1)) y -= vl[zoff + NP * n + s];
     }
     if (bx) mb = fmax(mb, fabs(bx[zoff + idx]));
     if (bc) mb = fmax(mb, fabs(bc[zoff + idx]));
@@ -115,7 +115,7 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
     double yc = 0.0;
     if (vz) {
       if (j == 0) {
-        yc = vz[zoff + s] - (i > 0 ? vz[zoff - n + s] : 0.0);
+        yc = vz[zoff + s] - (!chain_start(P, i) ? vz[zoff - n + s] : 0.0);
       } else {
 #pragma unroll
         for (int l = 0; l < NP; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];

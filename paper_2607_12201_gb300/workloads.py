@@ -63,6 +63,13 @@ class Instance:
     redraws: int = 0
     # collocation nodes: "radau" (right Radau, tau_K = 1) or "gauss" (Gauss-Legendre)
     scheme: str = "radau"
+    # experimental conditions (Eq. 1d): each condition's initial state and its
+    # inputs multiplying the rate constants, and the condition of each
+    # measurement; None: one condition starting from x0.  N is the number of
+    # elements of each condition's mesh.
+    cond_x0: np.ndarray | None = None      # [Nc][n]
+    cond_scale: np.ndarray | None = None   # [Nc][r]
+    obs_cond: np.ndarray | None = None     # [M]
 
     @property
     def p(self) -> int:
@@ -73,12 +80,16 @@ class Instance:
         return int(self.obs_t.shape[0])
 
     @property
+    def Nc(self) -> int:
+        return 1 if self.cond_x0 is None else int(np.asarray(self.cond_x0).shape[0])
+
+    @property
     def n_x(self) -> int:
-        return self.n * self.N * (self.K + 1) + self.p
+        return self.n * self.N * self.Nc * (self.K + 1) + self.p
 
     @property
     def n_c(self) -> int:
-        return self.n * self.N * (self.K + 1)
+        return self.n * self.N * self.Nc * (self.K + 1)
 
     def with_mesh(self, N: int) -> "Instance":
         return dataclasses.replace(self, N=int(N))
@@ -99,12 +110,15 @@ def _rate_constants(react, pidx, kfix, logscale, theta):
     return k
 
 
-def _simulate(inst_fields, theta, times):
-    """Integrate the mass-action ODE with scipy (data source only)."""
+def _simulate(inst_fields, theta, times, scale=None):
+    """Integrate the mass-action ODE with scipy (data source only); scale [r]
+    multiplies the rate constants (an experimental condition's inputs)."""
     from scipy.integrate import solve_ivp
 
     react, prod, pidx, kfix, logscale, x0, T = inst_fields
     k = _rate_constants(react, pidx, kfix, logscale, theta)
+    if scale is not None:
+        k = k * scale
     n = x0.shape[0]
     r = react.shape[0]
     stoich = np.zeros((n, r))
@@ -326,6 +340,51 @@ def serving_stream(count: int = 64, seed: int = 1005, rate_hz: float = 200.0,
                               name=f"request{j}_n{n}_N{N}")
         out.append((t, inst))
     return out
+
+
+def multi_condition(n: int = 6, r: int = 12, Nc: int = 3, N: int = 30, M: int = 20,
+                    T: float = 10.0, seed: int = 1006, theta0_spread: float = 0.1,
+                    n_inputs: int = 2, max_redraw: int = 50) -> Instance:
+    """A random mass-action network measured under Nc experimental conditions
+    (Eq. 1d): condition 0 is the network's own draw; every other condition has
+    its own initial state x0^c ~ U[0.1, 1] and scales n_inputs of the rate
+    constants by 10^U[-0.7, 0.7] (the condition-dependent inputs p^c of Eq. 3,
+    lifted to multipliers of the rate constants).  Each condition is simulated
+    and measured like the single network (same observed species and times,
+    5 % multiplicative noise); the measurements are concatenated with their
+    condition index."""
+    base = random_network(n, r, n_obs=min(4, n), M=M, T=T, N=N, seed=seed,
+                          theta0_spread=theta0_spread, name=f"conditions{Nc}_n{n}_r{r}_N{N}")
+    species = np.unique(base.obs_s)
+    times = np.array([m * T / M for m in range(1, M + 1)])
+    fields = (base.react, base.prod, base.pidx, base.kfix, 1, base.x0, T)
+    for attempt in range(max_redraw):
+        rng = _rng(seed, 271828, attempt)
+        x0s = [base.x0] + [rng.uniform(0.1, 1.0, size=n) for _ in range(Nc - 1)]
+        scale = np.ones((Nc, r))
+        for c in range(1, Nc):
+            for j in rng.choice(r, size=min(n_inputs, r), replace=False):
+                scale[c, j] = 10.0 ** rng.uniform(-0.7, 0.7)
+        ts, ss, ys, sg, oc = [], [], [], [], []
+        ok = True
+        for c in range(Nc):
+            fc = fields[:5] + (x0s[c], T)
+            dense = _simulate(fc, base.theta_true, np.linspace(0.0, T, 201), scale[c])
+            traj = _simulate(fc, base.theta_true, times, scale[c])
+            if (dense is None or traj is None or not np.all(np.isfinite(dense))
+                    or dense.max() > 1e3 or dense.min() < -1e-6):
+                ok = False
+                break
+            t_, s_, y_, g_ = _observations(times, species, traj, rng, "multiplicative")
+            ts.append(t_); ss.append(s_); ys.append(y_); sg.append(g_)
+            oc.append(np.full(len(t_), c, dtype=np.int32))
+        if not ok:
+            continue
+        return dataclasses.replace(
+            base, obs_t=np.concatenate(ts), obs_s=np.concatenate(ss), obs_y=np.concatenate(ys),
+            obs_sigma=np.concatenate(sg), cond_x0=np.array(x0s), cond_scale=scale,
+            obs_cond=np.concatenate(oc), redraws=base.redraws + attempt)
+    raise RuntimeError("no admissible conditions drawn")
 
 
 def small_network(n: int = 3, r: int = 4, N: int = 4, seed: int = 7, M: int = 6,

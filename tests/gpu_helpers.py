@@ -23,8 +23,10 @@ def assemble_J(oprob, out):
     n, N, p, K = oprob.n, oprob.N, oprob.p, 3
     D, h = oprob.tab.D, oprob.h
     Z = np.arange(oprob.nz).reshape(N, 4, n)
-    rows, cols, vals = [Z[:, 0].ravel(), Z[1:, 0].ravel()], [Z[:, 0].ravel(), Z[:-1, 3].ravel()], \
-        [np.ones(N * n), -np.ones((N - 1) * n)]
+    # continuity rows of every element but each experimental condition's first
+    cont = np.array([i for i in range(1, N) if i % oprob.Nch != 0], dtype=np.int64)
+    rows, cols, vals = [Z[:, 0].ravel(), Z[cont, 0].ravel()], [Z[:, 0].ravel(), Z[cont - 1, 3].ravel()], \
+        [np.ones(N * n), -np.ones(len(cont) * n)]
     for k in range(1, 4):
         for j in range(4):
             if j != k:

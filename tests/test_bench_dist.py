@@ -55,9 +55,16 @@ def test_factor_work_counts():
     import bench
     # one 2x2 pivot of a 4x4 block: t = 2 trailing rows -> 2*2*3 + 8*2 flops
     assert bench._pair_flops(4, 1) == 2 * 2 * 3 + 8 * 2
-    fl, by = bench.factor_work(10, 20, 400, 4)
+    # its L columns have 2 rows each below the pair
+    assert bench._pair_l_entries(4, 1) == 4
+    # one species, no parameter, one element: element block 8 rows (3 pairs:
+    # 2 (6 + 4 + 2) = 24 L entries), reduction block 4 rows (1 pair: 4 entries),
+    # 12 pivot values, 8 KKT unknowns, 10 intermediate values; FP32 factors:
+    # 2*4*(28 + 12) + 8*2*8 + 2*4*10 = 528 bytes
+    assert bench.solve_bytes(1, 0, 1, 4) == 528
     fe, be = bench.elem_factor_work(10, 20, 400, 4)
-    assert fl > fe and by > be
+    fr, br = bench.reduction_work(10, 20, 400, 4)
+    assert fe > fr > 0 and be > 0 and br > 0
 
 
 REQUIRED = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
