@@ -351,7 +351,10 @@ collo_status collo_problem_create_conditions(const collo_network* net,
   pr->n_c = (int64_t)n * N * NP;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  pr->n_slabs = std::max(1, std::min(N, 2 * std::max(1, sms)));
+  // global slabs of the blocks too large for shared memory: one per CUDA block
+  // that may run at once, two per SM; not limited by N, since a batch's
+  // kernels take their grid from the smallest slab count of its members
+  pr->n_slabs = 2 * std::max(1, sms);
 
   // host-side CSR structures (index bookkeeping only)
   std::vector<int> nu_ptr(n + 1, 0), nu_r, rs_ptr(n + 1, 0), rs_r, pr_ptr(p + 1, 0), pr_r;
