@@ -116,5 +116,6 @@ def test_interpolation_and_defect_with_conditions(collo):
         with pc.refined(45) as pf:
             assert pf.Nc == inst.Nc and pf.Nch == 45
             xf = collo.interpolate(pc, x, pf)
-    assert np.max(np.abs(xf - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+    # the two sides form the Lagrange basis in different orders
+    assert np.max(np.abs(xf - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
     assert np.max(np.abs(d - d_ref)) <= 1e-12 * max(1.0, m_ref)
