@@ -6,17 +6,21 @@
  * <= theta_hi) by the simultaneous method of Eq. 2: the states are kept as
  * NLP variables on a collocation mesh of N elements with K + 1 interpolation
  * points each, and the ODE becomes the collocation equations of Eq. 3.
- * Interpolation points are right Radau (Radau IIA) roots with tau_0 = 0,
- * so the continuity weights of Eq. 2c are b_j = delta_jK.  Only K = 3 is
- * built.  One experiment (N_c = 1 in Eq. 1d / 2e) unless the problem is
- * created with collo_problem_create_conditions.
+ * Two sets of interpolation points, both with tau_0 = 0 (collo_mesh.scheme):
+ * right Radau (Radau IIA) roots with K = 3, whose continuity weights in
+ * Eq. 2c are b_j = delta_jK, and the paper's own Gauss-Legendre roots with
+ * K = 4 (section "Collocation equation with condition independence";
+ * "Optimization framework configurations"), whose continuity goes through the
+ * extrapolated end value, b_j = l_j(1).  One experiment (N_c = 1 in Eq. 1d /
+ * 2e) unless the problem is created with collo_problem_create_conditions.
  *
  * ---- Layouts (all arrays are C-contiguous, 0-based) ----------------------
- *   n species, r reactions, p estimated parameters, N elements, K = 3,
+ *   n species, r reactions, p estimated parameters, N elements, K = 3 or 4,
  *   n_x = n N (K+1) + p primal unknowns, n_c = n N (K+1) constraints.
  *   x      = [ z[N][K+1][n], theta[p] ]       (z[i][j][s]: element i, point j)
  *   lambda = c = [N][K+1][n]:
- *            c[i][0][s]  continuity z[i][0][s] - z[i-1][K][s]  (Eq. 2c), or
+ *            c[i][0][s]  continuity z[i][0][s] - sum_j b_j z[i-1][j][s]
+ *                        (Eq. 2c; Radau: z[i][0][s] - z[i-1][K][s]), or
  *                        the initial condition z[0][0][s] - x0[s]  (Eq. 2d);
  *            c[i][k][s]  collocation sum_j D[k][j] z[i][j][s] - h f_s(z[i][k], theta)
  *                        for k = 1..K  (Eq. 3), h = T / N.
@@ -107,11 +111,19 @@ typedef struct collo_data {
   const double* sigma;        /* [M] > 0 */
 } collo_data;
 
-/* Uniform collocation mesh, paper "collocation mesh t_ij = t_(i-1)0 + h_i tau_j". */
+/* Interpolation points of an element (collo_mesh.scheme). */
+enum {
+  COLLO_SCHEME_RADAU = 0,     /* Radau IIA roots, K = 3 */
+  COLLO_SCHEME_GAUSS = 1      /* Gauss-Legendre roots, K = 4 (the paper's choice) */
+};
+
+/* Uniform collocation mesh, paper "collocation mesh t_ij = t_(i-1)0 + h_i tau_j".
+ * A zero-initialised scheme is Radau.  INVALID_ARG for another (scheme, K). */
 typedef struct collo_mesh {
   double T;                   /* horizon > 0 */
   int N;                      /* elements >= 1 */
-  int K;                      /* interior collocation points; must be 3 */
+  int K;                      /* collocation points: 3 (Radau) or 4 (Gauss) */
+  int scheme;                 /* COLLO_SCHEME_* */
 } collo_mesh;
 
 /* Experimental conditions (paper Eq. 1d / 2e: c = 1..N_c, each with its own
@@ -429,7 +441,7 @@ void collo_server_destroy(collo_server* server);
  * here is batched on the GPU. */
 
 /* A new problem with coarse's network, observables and data on a uniform
- * mesh of N elements (same horizon, K = 3).  The caller owns *out. */
+ * mesh of N elements (same horizon and collocation scheme).  The caller owns *out. */
 collo_status collo_problem_create_refined(const collo_problem* coarse, int N,
                                           collo_problem** out);
 

@@ -47,8 +47,12 @@ class Data(C.Structure):
     _fields_ = [("n_obs", C.c_int), ("t", _dp), ("observable", _ip), ("y", _dp), ("sigma", _dp)]
 
 
+SCHEME_RADAU, SCHEME_GAUSS = 0, 1
+_SCHEMES = {"radau": SCHEME_RADAU, "gauss": SCHEME_GAUSS}
+
+
 class Mesh(C.Structure):
-    _fields_ = [("T", C.c_double), ("N", C.c_int), ("K", C.c_int)]
+    _fields_ = [("T", C.c_double), ("N", C.c_int), ("K", C.c_int), ("scheme", C.c_int)]
 
 
 class Conditions(C.Structure):
@@ -260,8 +264,9 @@ class Problem:
     def __init__(self, inst, precision: int = FP64, stream: int | None = None, device: int = 0,
                  launch_mode: int = 0):
         self.inst = inst
-        if getattr(inst, "scheme", "radau") != "radau" or inst.K != 3:
-            raise ValueError("the library implements Radau IIA collocation with K = 3 only")
+        scheme = getattr(inst, "scheme", "radau")
+        if scheme not in _SCHEMES:
+            raise ValueError(f"unknown collocation scheme {scheme!r}")
         species = np.unique(inst.obs_s)
         obs_index = np.searchsorted(species, inst.obs_s)
         self._keep = dict(
@@ -276,7 +281,7 @@ class Problem:
                       int(inst.logscale), dp(k["x0"]), inst.p, dp(k["lo"]), dp(k["hi"]))
         obs = Observables(len(species), ip(k["species"]))
         data = Data(inst.M, dp(k["t"]), ip(k["obs"]), dp(k["y"]), dp(k["sig"]))
-        mesh = Mesh(float(inst.T), int(inst.N), int(inst.K))
+        mesh = Mesh(float(inst.T), int(inst.N), int(inst.K), _SCHEMES[scheme])
         opt = ProblemOptions(precision, stream, device, launch_mode)
         h = C.c_void_p()
         if getattr(inst, "cond_x0", None) is not None:
@@ -298,7 +303,7 @@ class Problem:
         s = Sizes()
         _check(lib.collo_problem_sizes(self.h, C.byref(s)))
         self.sizes = s
-        self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.n, self.r, self.p, self.N, self.K = s.n, s.r, s.p, s.N, s.K
         self.Nc, self.Nch = s.n_conditions, s.elements_per_condition
         self.n_x, self.n_c = int(s.n_x), int(s.n_c)
 
@@ -312,7 +317,7 @@ class Problem:
         s = Sizes()
         _check(lib.collo_problem_sizes(self.h, C.byref(s)))
         self.sizes = s
-        self.n, self.r, self.p, self.N = s.n, s.r, s.p, s.N
+        self.n, self.r, self.p, self.N, self.K = s.n, s.r, s.p, s.N, s.K
         self.Nc, self.Nch = s.n_conditions, s.elements_per_condition
         self.n_x, self.n_c = int(s.n_x), int(s.n_c)
         return self
@@ -378,15 +383,16 @@ class Problem:
     # --- evaluation ------------------------------------------------------------
     def eval(self, x, lam=None, obj_factor: float = 1.0, outputs: bool = True):
         """collo_eval on host arrays; returns a dict of host arrays."""
-        n, p, N = self.n, self.p, self.N
+        n, p, N, K = self.n, self.p, self.N, self.K
         x = _host_vec(x, self.n_x, "x")
         lam = _host_vec(lam, self.n_c, "lam")
         out = {}
         eo = EvalOut()
         if outputs:
-            shapes = dict(phi=(1,), c=(self.n_c,), grad=(self.n_x,), jac_z=(N, 3, n, n),
-                          jac_theta=(N, 3, n, p), hess_zz=(N, 3, n, n),
-                          hess_ztheta=(N, 3, n, p), hess_thth=(p,), hess_obj=(N, n, 4, 4))
+            shapes = dict(phi=(1,), c=(self.n_c,), grad=(self.n_x,), jac_z=(N, K, n, n),
+                          jac_theta=(N, K, n, p), hess_zz=(N, K, n, n),
+                          hess_ztheta=(N, K, n, p), hess_thth=(p,),
+                          hess_obj=(N, n, K + 1, K + 1))
             for name, shp in shapes.items():
                 out[name] = np.zeros(shp)
                 setattr(eo, name, out[name].ctypes.data)

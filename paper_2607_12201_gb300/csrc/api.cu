@@ -20,29 +20,56 @@ Schedule& schedule() {
   return s;
 }
 
-// Radau IIA points for K = 3 (closed form) and D[k][j] = l_j'(tau_k) from the
-// barycentric weights w_j = 1 / prod_{l != j} (tau_j - tau_l):
-//   D[k][j] = (w_j / w_k) / (tau_k - tau_j),  D[k][k] = -sum_{j != k} D[k][j].
-static void radau_tables(double tau[NP], double D[NP][NP]) {
-  const double s6 = std::sqrt(6.0);
+// Collocation tables (Eq. 2b, 2c).  Points: Radau IIA for K = 3, the
+// roots of P_3 - P_2 on [0, 1] in closed form, tau = (4 -+ sqrt 6) / 10 and 1;
+// Gauss-Legendre for K = 4, the roots of P_4 mapped from [-1, 1],
+// x = +-sqrt(3/7 -+ (2/7) sqrt(6/5)), tau = (1 + x) / 2.  tau_0 = 0 in both.
+// D[k][j] = l_j'(tau_k) from the barycentric weights
+// w_j = 1 / prod_{l != j} (tau_j - tau_l):
+//   D[k][j] = (w_j / w_k) / (tau_k - tau_j),  D[k][k] = -sum_{j != k} D[k][j];
+// continuity weights b_j = l_j(1) (Radau: exactly delta_jK, as tau_K = 1).
+static void colloc_tables(int gauss, double tau[NPMAX], double D[NPMAX][NPMAX],
+                          double bw[NPMAX]) {
+  const int np = gauss ? 5 : 4;
   tau[0] = 0.0;
-  tau[1] = (4.0 - s6) / 10.0;
-  tau[2] = (4.0 + s6) / 10.0;
-  tau[3] = 1.0;
-  double w[NP];
-  for (int j = 0; j < NP; ++j) {
+  if (gauss) {
+    const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+    const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+    tau[1] = 0.5 * (1.0 - b);
+    tau[2] = 0.5 * (1.0 - a);
+    tau[3] = 0.5 * (1.0 + a);
+    tau[4] = 0.5 * (1.0 + b);
+  } else {
+    const double s6 = std::sqrt(6.0);
+    tau[1] = (4.0 - s6) / 10.0;
+    tau[2] = (4.0 + s6) / 10.0;
+    tau[3] = 1.0;
+  }
+  double w[NPMAX];
+  for (int j = 0; j < np; ++j) {
     w[j] = 1.0;
-    for (int l = 0; l < NP; ++l)
+    for (int l = 0; l < np; ++l)
       if (l != j) w[j] /= (tau[j] - tau[l]);
   }
-  for (int k = 0; k < NP; ++k) {
+  for (int k = 0; k < np; ++k) {
     double sum = 0.0;
-    for (int j = 0; j < NP; ++j) {
+    for (int j = 0; j < np; ++j) {
       if (j == k) continue;
       D[k][j] = (w[j] / w[k]) / (tau[k] - tau[j]);
       sum += D[k][j];
     }
     D[k][k] = -sum;
+  }
+  for (int j = 0; j < np; ++j) {
+    if (!gauss) { bw[j] = j == np - 1 ? 1.0 : 0.0; continue; }
+    double v = 1.0;
+    for (int l = 0; l < np; ++l)
+      if (l != j) v *= (1.0 - tau[l]) / (tau[j] - tau[l]);
+    bw[j] = v;
+  }
+  for (int j = np; j < NPMAX; ++j) {
+    tau[j] = 0.0; bw[j] = 0.0;
+    for (int k = 0; k < NPMAX; ++k) D[j][k] = D[k][j] = 0.0;
   }
 }
 
@@ -52,8 +79,9 @@ static void radau_tables(double tau[NP], double D[NP][NP]) {
 template <typename T, class Fn>
 static void factor_layout(const DevProb& P, int n_slabs, DevFactor<T>& F, Fn&& fn) {
   const size_t N = P.N, n = P.n, p = P.p;
-  fn(F.Lel, N * 6 * n * P.ext);
-  fn(F.Del, N * 3 * n * 3);
+  const size_t K = P.K;
+  fn(F.Lel, N * 2 * K * n * P.ext);
+  fn(F.Del, N * K * n * 3);
   fn(F.Aif, N * 4 * n * n);
   fn(F.Cpl, N * n * n);
   fn(F.Bif, N * 2 * n * p);
@@ -61,7 +89,7 @@ static void factor_layout(const DevProb& P, int n_slabs, DevFactor<T>& F, Fn&& f
   fn(F.Db, N * n * 3);
   fn(F.Scon, 2 * N * p * p);
   fn(F.inert, 2 * N * 3);
-  fn(F.Vint, N * 6 * n);
+  fn(F.Vint, N * 2 * K * n);
   fn(F.Rif, N * 2 * n);
   fn(F.Vb, N * 2 * n);
   fn(F.Rth, 2 * N * p);
@@ -256,7 +284,14 @@ collo_status collo_problem_create_conditions(const collo_network* net,
           set_error("bad measurement condition"); return COLLO_ERR_INVALID_ARG;
         }
   }
-  if (mesh->K != KC) { set_error("only K = 3 (Radau IIA) is built"); return COLLO_ERR_INVALID_ARG; }
+  if (mesh->scheme != COLLO_SCHEME_RADAU && mesh->scheme != COLLO_SCHEME_GAUSS) {
+    set_error("unknown collocation scheme"); return COLLO_ERR_INVALID_ARG;
+  }
+  const int gauss = mesh->scheme == COLLO_SCHEME_GAUSS ? 1 : 0;
+  if (mesh->K != (gauss ? 4 : 3)) {
+    set_error("K must be 3 with Radau IIA points and 4 with Gauss-Legendre points");
+    return COLLO_ERR_INVALID_ARG;
+  }
   if (!(mesh->T > 0) || !std::isfinite(mesh->T)) { set_error("T must be positive"); return COLLO_ERR_INVALID_ARG; }
   if (!net->reactants || !net->products || !net->param_index || !net->k_fixed ||
       (!conds && !net->x0) ||
@@ -343,12 +378,13 @@ collo_status collo_problem_create_conditions(const collo_network* net,
   DevProb& P = pr->P;
   P.n = n; P.r = r; P.p = p; P.N = N; P.M = M;
   P.Nc = Nc; P.Nch = Nch;
-  P.m = 8 * n; P.ext = 8 * n + p; P.bext = 4 * n + p;
+  P.K = mesh->K; P.np = P.K + 1; P.gauss = gauss; P.cpt = gauss ? 0 : P.K;
+  P.m = 2 * P.np * n; P.ext = P.m + p; P.bext = 4 * n + p;
   P.logscale = net->log10_params ? 1 : 0;
   P.T = mesh->T; P.h = mesh->T / Nch;
-  radau_tables(P.tau, P.D);
-  pr->n_x = (int64_t)n * N * NP + p;
-  pr->n_c = (int64_t)n * N * NP;
+  colloc_tables(gauss, P.tau, P.D, P.bw);
+  pr->n_x = (int64_t)n * N * P.np + p;
+  pr->n_c = (int64_t)n * N * P.np;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // global slabs of the blocks too large for shared memory: one per CUDA block
@@ -497,18 +533,18 @@ collo_status collo_problem_create_conditions(const collo_network* net,
   P.obs_y = up_d(obs_y.data(), M);
   P.obs_sig = up_d(obs_sig.data(), M);
   const double* d_obs_t = up_d(obs_t.data(), M);
-  double* obs_w = A.alloc<double>((size_t)M * NP);
+  double* obs_w = A.alloc<double>((size_t)M * P.np);
   int* obs_elem_chk = A.alloc<int>(M);
   P.obs_w = obs_w;
   const size_t NN = (size_t)N, nn = (size_t)n * n, np_ = (size_t)n * p;
   DevEval& E = pr->E;
   E.c = A.alloc<double>(pr->n_c);
   E.grad = A.alloc<double>(pr->n_x);
-  E.JZ = A.alloc<double>(NN * KC * nn);
-  E.JT = A.alloc<double>(NN * KC * np_);
-  E.Wzz = A.alloc<double>(NN * KC * nn);
-  E.Wzt = A.alloc<double>(NN * KC * np_);
-  E.Wobj = A.alloc<double>(NN * n * NP * NP);
+  E.JZ = A.alloc<double>(NN * P.K * nn);
+  E.JT = A.alloc<double>(NN * P.K * np_);
+  E.Wzz = A.alloc<double>(NN * P.K * nn);
+  E.Wzt = A.alloc<double>(NN * P.K * np_);
+  E.Wobj = A.alloc<double>(NN * n * P.np * P.np);
   E.part = A.alloc<double>(NN * 4);
   E.wtt_part = A.alloc<double>(NN * p);
   E.red = A.alloc<double>(8);
@@ -536,7 +572,7 @@ collo_status collo_problem_create_conditions(const collo_network* net,
   pr->dz = A.alloc<double>(2 * (size_t)p);
   pr->thx = A.alloc<double>(8 * (size_t)p + 8);
   pr->fails = A.alloc<int>(1);
-  const size_t sweep_dim = 3 * (size_t)n;
+  const size_t sweep_dim = (size_t)P.K * n;
   const bool sweep_global = sweep_dim * (sweep_dim + 1) * sizeof(float) > 160 * 1024;
   if (sweep_global) pr->sweep_work = A.alloc<float>(sweep_dim * (sweep_dim + 1));
   bool ok = P.react && P.prod && P.pidx && P.kfix && P.x0 && P.theta_lo && P.theta_hi &&
@@ -583,7 +619,7 @@ void collo_problem_destroy(collo_problem* prob) {
 collo_status collo_problem_sizes(const collo_problem* prob, collo_sizes* out) {
   if (!prob || !out) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
   out->n = prob->P.n; out->r = prob->P.r; out->p = prob->P.p; out->N = prob->P.N;
-  out->K = KC; out->M = prob->P.M; out->n_x = prob->n_x; out->n_c = prob->n_c;
+  out->K = prob->P.K; out->M = prob->P.M; out->n_x = prob->n_x; out->n_c = prob->n_c;
   out->levels = bcr_levels(prob->P.N);
   out->device_bytes = problem_held_bytes(prob);
   out->n_conditions = prob->P.Nc;
@@ -631,12 +667,12 @@ collo_status collo_eval(collo_problem* prob, const double* x, const double* lamb
     COLLO_CUDA(cp(out->phi, E.red, 1));
     COLLO_CUDA(cp(out->c, E.c, prob->n_c));
     COLLO_CUDA(cp(out->grad, E.grad, prob->n_x));
-    COLLO_CUDA(cp(out->jac_z, E.JZ, NN * KC * nn));
-    COLLO_CUDA(cp(out->jac_theta, E.JT, NN * KC * np_));
-    COLLO_CUDA(cp(out->hess_zz, E.Wzz, NN * KC * nn));
-    COLLO_CUDA(cp(out->hess_ztheta, E.Wzt, NN * KC * np_));
+    COLLO_CUDA(cp(out->jac_z, E.JZ, NN * P.K * nn));
+    COLLO_CUDA(cp(out->jac_theta, E.JT, NN * P.K * np_));
+    COLLO_CUDA(cp(out->hess_zz, E.Wzz, NN * P.K * nn));
+    COLLO_CUDA(cp(out->hess_ztheta, E.Wzt, NN * P.K * np_));
     COLLO_CUDA(cp(out->hess_thth, E.wtt, P.p));
-    COLLO_CUDA(cp(out->hess_obj, E.Wobj, NN * P.n * NP * NP));
+    COLLO_CUDA(cp(out->hess_obj, E.Wobj, NN * P.n * P.np * P.np));
   }
   COLLO_CUDA(cudaMemcpyAsync(prob->hscal, E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   COLLO_CUDA(cudaStreamSynchronize(st));

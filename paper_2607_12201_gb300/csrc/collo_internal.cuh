@@ -1,7 +1,9 @@
 // Internal definitions shared by the CUDA translation units of libcollo.
 //
 // Notation follows the paper's Eq. 2 / Eq. 3: element i = 0..N-1, interpolation
-// point j = 0..K (K = 3, Radau IIA), species s, parameter q, h = T / N.
+// point j = 0..K, species s, parameter q, h = T / N.  Two collocation schemes:
+// Radau IIA with K = 3 (tau_K = 1, continuity weights b_j = delta_jK) and
+// Gauss-Legendre with K = 4 (interior roots, b_j = l_j(1)), Eq. 2c.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,33 +17,54 @@
 
 namespace collo {
 
-constexpr int KC = 3;        // collocation points per element
-constexpr int NP = KC + 1;   // interpolation points per element
+constexpr int KMAX = 4;          // most collocation points per element
+constexpr int NPMAX = KMAX + 1;  // most interpolation points per element
 
 // ---- element-local ordering of the KKT unknowns -----------------------------
-// The 8n unknowns of element i are grouped into 4 groups of n (state,
-// multiplier) pairs.  Group g pairs state z[i][pt(g)][s] with the multiplier
-// of constraint c[i][con(g)][s]:
-//   g = 0: (z1, c1)   g = 1: (z2, c2)   g = 2: (z0, c3)   g = 3: (z3, c0)
-// Groups 0..2 are the element interior (eliminated locally); group 3 is the
-// interface (z3 couples forward to the next element's continuity row c0,
-// c0 couples back to the previous element's z3).  Local index of the state of
-// pair (g, s) is 2 (g n + s), of the multiplier 2 (g n + s) + 1.
-__host__ __device__ inline int grp_point(int g) { return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 0 : 3)); }
-__host__ __device__ inline int grp_con(int g) { return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 0)); }
+// The 2 (K+1) n unknowns of element i's block are grouped into K + 1 groups of
+// n (state, multiplier) pairs.  Group g pairs state z[i][pt(g)][s] with the
+// multiplier of constraint con(g):
+//   Radau K = 3:  (z1, c1) (z2, c2) (z0, c3) | (z3, c0)
+//   Gauss K = 4:  (z1, c1) (z2, c2) (z3, c3) (z4, c4) | (z0, c0 of element i+1)
+// The first K groups are the element interior (eliminated locally); the last
+// is the chain group.  Radau: z3 couples forward to the next element's
+// continuity row c0 and c0 back to the previous element's z3, so the chain
+// block of element i is (z_i3, c_i0).  Gauss: the outgoing continuity row
+// c_(i+1)0 = z_(i+1)0 - sum_j b_j z_ij touches every point of element i, so
+// it joins element i's block; the chain block of element i is (z_i0, c_i0),
+// whose (c_i0, z_i0) entry is the constant identity, and element i's
+// condensation writes the z part of chain block i and the c part of chain
+// block i + 1.  Local index of the state of pair (g, s) is 2 (g n + s), of the
+// multiplier 2 (g n + s) + 1.
+__host__ __device__ inline int grp_point(int gauss, int K, int g) {
+  if (gauss) return g < K ? g + 1 : 0;
+  return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 0 : 3));
+}
+// constraint point of group g's multiplier; Gauss's chain group holds the
+// next element's c0 (returned as K + 1)
+__host__ __device__ inline int grp_con(int gauss, int K, int g) {
+  if (gauss) return g < K ? g + 1 : K + 1;
+  return g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 0));
+}
 
 // Plain-old-data view of one problem's device arrays, passed by value.
 struct DevProb {
   int n, r, p, N, M;   // N: elements of all conditions (Nc x Nch)
   int Nc, Nch;         // experimental conditions, elements per condition
-  int m;        // 8 n: element unknowns
-  int ext;      // 8 n + p: element block plus parameter border
+  int K;        // collocation points per element (3 Radau, 4 Gauss)
+  int np;       // K + 1 interpolation points
+  int gauss;    // 1: Gauss-Legendre points, 0: Radau IIA
+  int cpt;      // point of the chain block's state: K (Radau) or 0 (Gauss)
+  int m;        // 2 (K + 1) n: element unknowns
+  int ext;      // m + p: element block plus parameter border
   int bext;     // 4 n + p: cyclic-reduction block (2n) + two neighbour slices + border
   int logscale;
   double h, T;
-  // Radau IIA tables (kernel-parameter space): tau[j], D[k][j] = l_j'(tau_k)
-  double tau[NP];
-  double D[NP][NP];
+  // collocation tables (kernel-parameter space): tau[j], D[k][j] = l_j'(tau_k),
+  // continuity weights bw[j] (Eq. 2c)
+  double tau[NPMAX];
+  double D[NPMAX][NPMAX];
+  double bw[NPMAX];
   // network
   const int* react;      // [r][2]
   const int* prod;       // [r][2]
@@ -70,18 +93,18 @@ struct DevProb {
   const int* obs_s;      // [M] species
   const double* obs_y;   // [M]
   const double* obs_sig; // [M]
-  const double* obs_w;   // [M][4] Lagrange weights l_j(tau_m)
+  const double* obs_w;   // [M][K+1] Lagrange weights l_j(tau_m)
 };
 
 // Evaluation outputs kept in the problem (FP64).
 struct DevEval {
-  double* c;        // [N][4][n]
+  double* c;        // [N][K+1][n]
   double* grad;     // [n_x]
-  double* JZ;       // [N][3][n][n]
-  double* JT;       // [N][3][n][p]
-  double* Wzz;      // [N][3][n][n]
-  double* Wzt;      // [N][3][n][p]
-  double* Wobj;     // [N][n][4][4]
+  double* JZ;       // [N][K][n][n]
+  double* JT;       // [N][K][n][p]
+  double* Wzz;      // [N][K][n][n]
+  double* Wzt;      // [N][K][n][p]
+  double* Wobj;     // [N][n][K+1][K+1]
   double* part;     // [N][4] per element: phi, sum|c|, max|c|, unused
   double* wtt_part; // [N][p]
   double* red;      // [8]: phi, |c|_1, |c|_inf, ...
@@ -103,10 +126,10 @@ struct GridBar {
 // Factorization storage (T = double or float).
 template <typename T>
 struct DevFactor {
-  T* Lel;        // [N][6n][ext]   element interior L columns (column-major)
-  T* Del;        // [N][3n][3]     element interior 2x2 pivots (a, b, d)
-  T* Aif;        // [N][2n][2n]    interface blocks (full symmetric)
-  T* Cpl;        // [N][n][n]      coupling K[c0 of block, z3 of left neighbour]
+  T* Lel;        // [N][2Kn][ext]  element interior L columns (column-major)
+  T* Del;        // [N][Kn][3]     element interior 2x2 pivots (a, b, d)
+  T* Aif;        // [N][2n][2n]    chain blocks (full symmetric)
+  T* Cpl;        // [N][n][n]      coupling K[c0 of block, chain state of left neighbour]
   T* Bif;        // [N][2n][p]     interface border
   T* Lb;         // [N][2n][bext]  cyclic-reduction L columns
   T* Db;         // [N][n][3]      cyclic-reduction 2x2 pivots
@@ -115,7 +138,7 @@ struct DevFactor {
   T* work;       // global slab workspace for element blocks too large for smem
   int n_slabs;
   // solve vectors
-  T* Vint;       // [N][6n]  D^-1 L^-1 rhs of the interior
+  T* Vint;       // [N][2Kn] D^-1 L^-1 rhs of the interior
   T* Rif;        // [N][2n]  interface rhs (updated through the reduction)
   T* Vb;         // [N][2n]  D^-1 L^-1 rhs of each reduced block
   double* Rth;   // [2N][p]  parameter rhs contributions
@@ -166,7 +189,7 @@ struct DevInst {
   double* npart;      // [N][3]
   double* out;        // [64] per-instance scalar outputs of the batched kernels
   int* fails;         // [1]
-  float* sweep_work;  // forward-sweep FP32 matrix when 3n is large
+  float* sweep_work;  // forward-sweep FP32 matrix when Kn is large
   long long n_x, n_c;
 };
 
@@ -189,6 +212,10 @@ enum OutSlot {
 
 // Element i starts its condition's chain (its row 0 is an initial condition).
 __host__ __device__ inline bool chain_start(const DevProb& P, int i) { return i % P.Nch == 0; }
+// Element i has a successor in its chain (whose row 0 is a continuity row).
+__host__ __device__ inline bool chain_next(const DevProb& P, int i) {
+  return i + 1 < P.N && !chain_start(P, i + 1);
+}
 
 // Find k with pre[k] <= t < pre[k+1] (pre[0] = 0, A + 1 entries).
 __device__ inline int find_item(const int* __restrict__ pre, int A, int t) {

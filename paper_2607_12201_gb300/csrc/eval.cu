@@ -29,8 +29,9 @@ __device__ inline double sum_chunks(const double* __restrict__ part, int G, int 
   return (a0 + a1) + (a2 + a3);
 }
 
-// Observation weights l_j(tau_m) (Lagrange basis on the Radau points) and
-// the observation's element; one thread per observation.
+// Observation weights l_j(tau_m) (Lagrange basis on the element's
+// interpolation points) and the observation's element; one thread per
+// observation.
 __global__ void k_obs_weights(DevProb P, int M, int N, double T, const double* __restrict__ t,
                               int* __restrict__ elem, double* __restrict__ w) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,11 +41,12 @@ __global__ void k_obs_weights(DevProb P, int M, int N, double T, const double* _
   i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
   double tau = u - i;
   elem[m] = i;
-  for (int j = 0; j < NP; ++j) {
+  const int np = P.np;
+  for (int j = 0; j < np; ++j) {
     double v = 1.0;
-    for (int l = 0; l < NP; ++l)
+    for (int l = 0; l < np; ++l)
       if (l != j) v *= (tau - P.tau[l]) / (P.tau[j] - P.tau[l]);
-    w[m * NP + j] = v;
+    w[m * np + j] = v;
   }
 }
 
@@ -56,7 +58,7 @@ __device__ inline void rate_const(const DevProb& P, int j, const double* x, cons
     k = P.kfix[j]; dk = 0.0; d2k = 0.0;
     return;
   }
-  size_t o = (size_t)P.N * NP * P.n + q;
+  size_t o = (size_t)P.N * P.np * P.n + q;
   double th = x[o];
   if (dx) th += alpha * dx[o];
   if (P.logscale) {
@@ -76,20 +78,20 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
                           const double* __restrict__ dx, double alpha,
                           const double* __restrict__ lam, double obj_factor, const DevEval& E,
                           int i, double* sm, double* red) {
-  const int n = P.n, r = P.r, p = P.p;
+  const int n = P.n, r = P.r, p = P.p, K = P.K, np = P.np;
   const int tid = threadIdx.x;
-  double* ze = sm;              // [4][n]
-  double* le = ze + NP * n;     // [4][n]
-  double* kr = le + NP * n;     // [r]
+  double* ze = sm;              // [K+1][n]
+  double* le = ze + np * n;     // [K+1][n]
+  double* kr = le + np * n;     // [r]
   double* dkr = kr + r;         // [r]
   double* d2kr = dkr + r;       // [r]
-  double* mon = d2kr + r;       // [3][r]
-  double* da = mon + KC * r;    // [3][r] d mon / d z(slot 0)
-  double* db = da + KC * r;     // [3][r] d mon / d z(slot 1)
-  double* om = db + KC * r;     // [3][r] sum_s lambda_s nu_s,r
-  const size_t zoff = (size_t)i * NP * n;
+  double* mon = d2kr + r;       // [K][r]
+  double* da = mon + K * r;     // [K][r] d mon / d z(slot 0)
+  double* db = da + K * r;      // [K][r] d mon / d z(slot 1)
+  double* om = db + K * r;      // [K][r] sum_s lambda_s nu_s,r
+  const size_t zoff = (size_t)i * np * n;
 
-  for (int t = tid; t < NP * n; t += EVAL_BS) {
+  for (int t = tid; t < np * n; t += EVAL_BS) {
     double v = x[zoff + t];
     if (dx) v += alpha * dx[zoff + t];
     ze[t] = v;
@@ -103,7 +105,7 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < KC * r; idx += EVAL_BS) {
+  for (int idx = tid; idx < K * r; idx += EVAL_BS) {
     const int k = idx / r + 1, j = idx - (idx / r) * r;
     const int a = P.react[2 * j], b = P.react[2 * j + 1];
     const double za = ze[k * n + a];
@@ -122,24 +124,31 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
   }
   __syncthreads();
 
-  // constraints: continuity / initial (point 0) and collocation (points 1..3)
+  // constraints: continuity / initial (point 0) and collocation (points 1..K)
   double csum = 0.0, cmax = 0.0;
-  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
+  for (int idx = tid; idx < np * n; idx += EVAL_BS) {
     const int j = idx / n, s = idx - j * n;
     double c;
     if (j == 0) {
       double prev;
-      if (!chain_start(P, i)) {
+      if (!chain_start(P, i) && !P.gauss) {   // Radau: b_j = delta_jK
         prev = x[zoff - n + s];
         if (dx) prev += alpha * dx[zoff - n + s];
+      } else if (!chain_start(P, i)) {        // Gauss: sum_j b_j z[i-1][j]
+        const size_t po = zoff - (size_t)np * n + s;
+        prev = 0.0;
+        for (int jj = 0; jj < np; ++jj) {
+          double v = x[po + (size_t)jj * n];
+          if (dx) v += alpha * dx[po + (size_t)jj * n];
+          prev += P.bw[jj] * v;
+        }
       } else {   // initial condition of the element's experimental condition
         prev = P.x0[(size_t)(i / P.Nch) * n + s];
       }
       c = ze[s] - prev;
     } else {
       double acc = 0.0;
-#pragma unroll
-      for (int jj = 0; jj < NP; ++jj) acc += P.D[j][jj] * ze[jj * n + s];
+      for (int jj = 0; jj < np; ++jj) acc += P.D[j][jj] * ze[jj * n + s];
       double f = 0.0;
       for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
         const int rr = P.nu_r[e];
@@ -158,8 +167,7 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
   for (int o = o0 + tid; o < o1; o += EVAL_BS) {
     const int s = P.obs_s[o];
     double yh = 0.0;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) yh += P.obs_w[o * NP + j] * ze[j * n + s];
+    for (int j = 0; j < np; ++j) yh += P.obs_w[o * np + j] * ze[j * n + s];
     const double res = (yh - P.obs_y[o]) / P.obs_sig[o];
     phi += 0.5 * res * res;
   }
@@ -175,31 +183,31 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
   if (!DERIV) return;
 
   // gradient of obj_factor * Phi with respect to z[i][j][s]
-  for (int idx = tid; idx < NP * n; idx += EVAL_BS) {
+  for (int idx = tid; idx < np * n; idx += EVAL_BS) {
     const int j = idx / n, s = idx - j * n;
     double g = 0.0;
     for (int o = o0; o < o1; ++o) {
       if (P.obs_s[o] != s) continue;
       double yh = 0.0;
-#pragma unroll
-      for (int jj = 0; jj < NP; ++jj) yh += P.obs_w[o * NP + jj] * ze[jj * n + s];
+      for (int jj = 0; jj < np; ++jj) yh += P.obs_w[o * np + jj] * ze[jj * n + s];
       const double sg = P.obs_sig[o];
-      g += P.obs_w[o * NP + j] * (yh - P.obs_y[o]) / (sg * sg);
+      g += P.obs_w[o * np + j] * (yh - P.obs_y[o]) / (sg * sg);
     }
     E.grad[zoff + idx] = obj_factor * g;
   }
   if (i == 0)
-    for (int q = tid; q < p; q += EVAL_BS) E.grad[(size_t)P.N * NP * n + q] = 0.0;
+    for (int q = tid; q < p; q += EVAL_BS) E.grad[(size_t)P.N * np * n + q] = 0.0;
   // objective Hessian blocks Wobj[i][s][j][l]
-  for (int idx = tid; idx < n * NP * NP; idx += EVAL_BS) {
-    const int s = idx / (NP * NP), j = (idx / NP) % NP, l = idx % NP;
+  const int np2 = np * np;
+  for (int idx = tid; idx < n * np2; idx += EVAL_BS) {
+    const int s = idx / np2, j = (idx / np) % np, l = idx % np;
     double w = 0.0;
     for (int o = o0; o < o1; ++o) {
       if (P.obs_s[o] != s) continue;
       const double sg = P.obs_sig[o];
-      w += P.obs_w[o * NP + j] * P.obs_w[o * NP + l] / (sg * sg);
+      w += P.obs_w[o * np + j] * P.obs_w[o * np + l] / (sg * sg);
     }
-    E.Wobj[(size_t)i * n * NP * NP + idx] = obj_factor * w;
+    E.Wobj[(size_t)i * n * np2 + idx] = obj_factor * w;
   }
   const double mh = -P.h;
   // Derivative blocks, one thread per row.  Row s of JZ / JT at node k
@@ -208,10 +216,10 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
   // (into column pidx[r]).  Row t of Wzz / Wzt at node k accumulates, over the
   // reactions consuming t, -h om_r k_r d2mon_r/dz_t dz_u and
   // -h om_r dk_r dmon_r/dz_t.  Each row is owned by one thread (fixed order).
-  for (int idx = tid; idx < KC * n; idx += EVAL_BS) {
+  for (int idx = tid; idx < K * n; idx += EVAL_BS) {
     const int k = idx / n + 1, s = idx - (k - 1) * n;
-    double* jz = E.JZ + (((size_t)i * KC + (k - 1)) * n + s) * n;
-    double* jt = E.JT + (((size_t)i * KC + (k - 1)) * n + s) * p;
+    double* jz = E.JZ + (((size_t)i * K + (k - 1)) * n + s) * n;
+    double* jt = E.JT + (((size_t)i * K + (k - 1)) * n + s) * p;
     for (int t = 0; t < n; ++t) jz[t] = 0.0;
     for (int q = 0; q < p; ++q) jt[q] = 0.0;
     for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) {
@@ -225,10 +233,10 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
       if (q >= 0) jt[q] += c * dkr[rr] * mon[mi];
     }
   }
-  for (int idx = tid; idx < KC * n; idx += EVAL_BS) {
+  for (int idx = tid; idx < K * n; idx += EVAL_BS) {
     const int k = idx / n + 1, t = idx - (k - 1) * n;
-    double* wz = E.Wzz + (((size_t)i * KC + (k - 1)) * n + t) * n;
-    double* wt = E.Wzt + (((size_t)i * KC + (k - 1)) * n + t) * p;
+    double* wz = E.Wzz + (((size_t)i * K + (k - 1)) * n + t) * n;
+    double* wt = E.Wzt + (((size_t)i * K + (k - 1)) * n + t) * p;
     for (int u = 0; u < n; ++u) wz[u] = 0.0;
     for (int q = 0; q < p; ++q) wt[q] = 0.0;
     for (int e = P.rs_ptr[t]; e < P.rs_ptr[t + 1]; ++e) {
@@ -252,7 +260,7 @@ __device__ void eval_elem(const DevProb& P, const double* __restrict__ x,
   // theta-theta diagonal partial sums of this element
   for (int q = tid; q < p; q += EVAL_BS) {
     double v = 0.0;
-    for (int k = 1; k <= KC; ++k)
+    for (int k = 1; k <= K; ++k)
       for (int e = P.pr_ptr[q]; e < P.pr_ptr[q + 1]; ++e) {
         const int rr = P.pr_r[e];
         const int mi = (k - 1) * r + rr;
@@ -360,7 +368,7 @@ k_kkt_resid(DevProb P, DevEval E, const double* __restrict__ sigma, double dw, d
 }
 
 // BS: 64 when every instance of the batch has at most 64 state rows per
-// element (4n), else EVAL_BS; the results do not depend on it.
+// element ((K + 1) n), else EVAL_BS; the results do not depend on it.
 template <int BS>
 __global__ void __launch_bounds__(BS)
 k_kkt_resid_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
@@ -397,7 +405,7 @@ k_kkt_resid_theta_b(const DevInst* __restrict__ insts, const int* __restrict__ a
 
 // ---- host launchers -------------------------------------------------------------
 size_t eval_smem_bytes(const DevProb& P) {
-  return sizeof(double) * (size_t)(2 * NP * P.n + 3 * P.r + 4 * KC * P.r);
+  return sizeof(double) * (size_t)(2 * P.np * P.n + 3 * P.r + 4 * P.K * P.r);
 }
 
 cudaError_t launch_obs_weights(const DevProb& P, int M, int N, double T, const double* t,
@@ -508,7 +516,7 @@ cudaError_t launch_resid_b(const DevInst* insts, const int* act, int A, const in
                            cudaStream_t st) {
   if (A == 0) return cudaSuccess;
   count_launch();
-  if (NP * max_n <= 64)
+  if (max_n <= 64)
     k_kkt_resid_b<64><<<total_elems, 64, 0, st>>>(insts, act, A, pre_elem, prm, mode);
   else
     k_kkt_resid_b<EVAL_BS><<<total_elems, EVAL_BS, 0, st>>>(insts, act, A, pre_elem, prm, mode);

@@ -258,39 +258,45 @@ __device__ inline BigPlace<T> big_place(unsigned char* smraw, T* work, int msz, 
 }
 
 // Scatter assembly of element e's KKT block (packed lower triangle blk, zeroed)
-// from its FP64 derivative blocks Wzz, JZ (3 n^2), Wzt, JT (3 n p), Wobj
-// (16 n) and the barrier diagonal sig (4 n, or NULL: zero), which may be in
-// shared or global memory.  Three passes separated by barriers over the nt
+// from its FP64 derivative blocks Wzz, JZ (K n^2), Wzt, JT (K n p), Wobj
+// ((K+1)^2 n) and the barrier diagonal sig ((K+1) n, or NULL: zero), which may be in
+// shared or global memory.  Out of line (it is not on the elimination's
+// path).  Three passes separated by barriers over the nt
 // threads of the block: disjoint entries (point Hessian blocks, the identity
 // parts of the collocation rows D[k][j], continuity / initial rows, -delta_c,
 // border), sums onto those (objective blocks, -h df/dz), then the diagonal.
 template <typename T>
-__device__ inline void elem_scatter(const DevProb& P, const double* Wzz, const double* JZ,
-                                    const double* Wzt, const double* JT, const double* Wobj,
-                                    const double* sig, double dw, double dc, T* blk);
+__device__ __noinline__ void elem_scatter(const DevProb& P, int e, const double* Wzz,
+                                          const double* JZ, const double* Wzt, const double* JT,
+                                          const double* Wobj, const double* sig, double dw,
+                                          double dc, T* blk);
+template <typename T, class Tr>
+__device__ __noinline__ void gauss_chain_out(const DevProb& P, const DevFactor<T>& F, int e,
+                                             int i0, double dc, Tr tr);
 
 // ---- 1. element condensation --------------------------------------------------
-// One CUDA block condenses element e: assemble the bordered (8n + p) block,
-// eliminate the 3n interior pairs, write L, pivots, the 2n x 2n interface
-// block, its border, the p x p Schur contribution and the coupling -I.  For
-// blocks above the register-tile limit (elem_factor_rt below).
+// One CUDA block condenses element e: assemble the bordered (2 (K+1) n + p)
+// block, eliminate the K n interior pairs, write L, pivots, the 2n x 2n chain
+// block, its border, the p x p Schur contribution and the coupling (Radau:
+// -I; Gauss: gauss_chain_out).  For blocks above the register-tile limit
+// (elem_factor_rt below).
 template <typename T>
 __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                                 const double* __restrict__ sigma, double dw, double dc,
                                 const DevFactor<T>& F, int e, const BigPlace<T>& pl, int pb) {
-  const int n = P.n, p = P.p, m = P.m, ext = P.ext;
+  const int n = P.n, p = P.p, m = P.m, ext = P.ext, K = P.K, npt = P.np;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nint = 3 * n;          // interior pairs
-  const int i0 = 2 * nint;         // first interface row (6n)
+  const int nint = K * n;          // interior pairs
+  const int i0 = 2 * nint;         // first chain row (2Kn)
   const size_t nn = (size_t)n * n, np = (size_t)n * p;
   T* A = pl.A;
   const int ntri = ext * (ext + 1) / 2;
   for (int i = tid; i < ntri; i += nt) A[i] = T(0);
   __syncthreads();
-  elem_scatter<T>(P, E.Wzz + (size_t)e * 3 * nn, E.JZ + (size_t)e * 3 * nn,
-                  E.Wzt + (size_t)e * 3 * np, E.JT + (size_t)e * 3 * np,
-                  E.Wobj + (size_t)e * 16 * n, sigma ? sigma + (size_t)e * 4 * n : nullptr, dw,
-                  dc, A);
+  elem_scatter<T>(P, e, E.Wzz + (size_t)e * K * nn, E.JZ + (size_t)e * K * nn,
+                  E.Wzt + (size_t)e * K * np, E.JT + (size_t)e * K * np,
+                  E.Wobj + (size_t)e * npt * npt * n,
+                  sigma ? sigma + (size_t)e * npt * n : nullptr, dw, dc, A);
   int pos = 0, neg = 0, zero = 0;
   pair_eliminate_big<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
                         F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero, pb);
@@ -299,6 +305,16 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
   }
   const int n2 = 2 * n;
   auto tr = [&](int a, int b) { return a >= b ? A[tri_at(a, b)] : A[tri_at(b, a)]; };
+  double* Sc = F.Scon + (size_t)e * p * p;
+  for (int idx = tid; idx < p * p; idx += nt) {
+    const int q = idx / p, q2 = idx - q * p;
+    Sc[idx] = (double)tr(m + q, m + q2);
+  }
+  if (P.gauss) {
+    gauss_chain_out<T>(P, F, e, i0, dc, tr);
+    __syncthreads();
+    return;
+  }
   T* Aif = F.Aif + (size_t)e * n2 * n2;
   for (int idx = tid; idx < n2 * n2; idx += nt) {
     const int u = idx / n2, v = idx - u * n2;
@@ -308,11 +324,6 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
   for (int idx = tid; idx < n2 * p; idx += nt) {
     const int u = idx / p, q = idx - u * p;
     Bif[idx] = A[tri_at(m + q, i0 + u)];
-  }
-  double* Sc = F.Scon + (size_t)e * p * p;
-  for (int idx = tid; idx < p * p; idx += nt) {
-    const int q = idx / p, q2 = idx - q * p;
-    Sc[idx] = (double)tr(m + q, m + q2);
   }
   T* C = F.Cpl + (size_t)e * n * n;
   for (int idx = tid; idx < n * n; idx += nt) {
@@ -619,10 +630,11 @@ template <typename T>
 __host__ __device__ inline size_t elem_blk_bytes(const DevProb& P) {
   return (sizeof(T) * ((size_t)P.ext * (P.ext + 1) / 2) + 15) & ~size_t(15);
 }
-// The element's FP64 derivative blocks (Wzz, JZ: 3 n^2 each; Wzt, JT: 3 n p
-// each; Wobj: 16 n; sigma: 4 n), staged behind the triangle.
+// The element's FP64 derivative blocks (Wzz, JZ: K n^2 each; Wzt, JT: K n p
+// each; Wobj: (K+1)^2 n; sigma: (K+1) n), staged behind the triangle.
 __host__ __device__ inline size_t elem_raw_doubles(const DevProb& P) {
-  return 6 * (size_t)P.n * P.n + 6 * (size_t)P.n * P.p + 20 * (size_t)P.n;
+  const size_t K = P.K, np = P.np;
+  return 2 * K * P.n * P.n + 2 * K * P.n * P.p + (np * np + np) * P.n;
 }
 template <typename T>
 __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
@@ -634,12 +646,18 @@ __host__ __device__ inline size_t elem_stage_bytes(const DevProb& P) {
 __device__ inline int quot(int i, int d, float inv) {
   return (int)(((float)i + 0.5f) * inv);
 }
-// local index of the state of point j / the multiplier of constraint k
-// (groups (z1,c1), (z2,c2), (z0,c3), (z3,c0))
-__device__ inline int loc_state(int j, int s, int n) {
-  return 2 * ((j == 0 ? 2 : (j == 3 ? 3 : j - 1)) * n + s);
+// local index of the state of point j / the multiplier of the element's
+// constraint k (groups of grp_point / grp_con): Radau (z1,c1), (z2,c2),
+// (z0,c3), (z3,c0); Gauss (z1,c1) .. (z4,c4), (z0, c0 of the next element),
+// whose multiplier is k = 0 here
+__device__ inline int loc_state(const DevProb& P, int j, int s) {
+  const int K = P.K;
+  const int g = j == 0 ? (P.gauss ? K : K - 1) : ((!P.gauss && j == K) ? K : j - 1);
+  return 2 * (g * P.n + s);
 }
-__device__ inline int loc_dual(int k, int s, int n) { return 2 * ((k == 0 ? 3 : k - 1) * n + s) + 1; }
+__device__ inline int loc_dual(const DevProb& P, int k, int s) {
+  return 2 * ((k == 0 ? P.K : k - 1) * P.n + s) + 1;
+}
 
 // Element condensation (same elimination as elem_factor_big) with
 // pair_eliminate_rt over the nt threads of the block.
@@ -651,92 +669,156 @@ template <typename T>
 __device__ __noinline__ void elem_assemble_rt(const DevProb& P, const DevEval& E,
                                               const double* __restrict__ sigma, double dw,
                                               double dc, int e, T* blk) {
-  const int n = P.n, p = P.p, ext = P.ext;
+  const int n = P.n, p = P.p, ext = P.ext, K = P.K, npt = P.np;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nn = n * n, np = n * p, ntri = ext * (ext + 1) / 2;
+  const int nob = npt * npt * n, nsg = npt * n;
   // the derivative blocks arrive by asynchronous copies issued all at once
   // (one memory latency per element) while the triangle is cleared
   double* Wzz = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(blk) +
                                           elem_blk_bytes<T>(P));
-  double* JZ = Wzz + 3 * nn;
-  double* Wzt = JZ + 3 * nn;
-  double* JT = Wzt + 3 * np;
-  double* Wobj = JT + 3 * np;
-  double* sig = Wobj + 16 * n;
+  double* JZ = Wzz + K * nn;
+  double* Wzt = JZ + K * nn;
+  double* JT = Wzt + K * np;
+  double* Wobj = JT + K * np;
+  double* sig = Wobj + nob;
   {
     auto stage = [&](double* dst, const double* src, int cnt) {
       for (int i = tid; i < cnt; i += nt) cp_async_elem(dst + i, src + i);
     };
-    stage(Wzz, E.Wzz + (size_t)e * 3 * nn, 3 * nn);
-    stage(JZ, E.JZ + (size_t)e * 3 * nn, 3 * nn);
-    stage(Wzt, E.Wzt + (size_t)e * 3 * np, 3 * np);
-    stage(JT, E.JT + (size_t)e * 3 * np, 3 * np);
-    stage(Wobj, E.Wobj + (size_t)e * 16 * n, 16 * n);
-    if (sigma) stage(sig, sigma + (size_t)e * 4 * n, 4 * n);
+    stage(Wzz, E.Wzz + (size_t)e * K * nn, K * nn);
+    stage(JZ, E.JZ + (size_t)e * K * nn, K * nn);
+    stage(Wzt, E.Wzt + (size_t)e * K * np, K * np);
+    stage(JT, E.JT + (size_t)e * K * np, K * np);
+    stage(Wobj, E.Wobj + (size_t)e * nob, nob);
+    if (sigma) stage(sig, sigma + (size_t)e * nsg, nsg);
     else
-      for (int i = tid; i < 4 * n; i += nt) sig[i] = 0.0;
+      for (int i = tid; i < nsg; i += nt) sig[i] = 0.0;
     cp_async_commit();
   }
   for (int i = tid; i < ntri; i += nt) blk[i] = T(0);
   cp_async_wait_all();
   __syncthreads();
-  elem_scatter<T>(P, Wzz, JZ, Wzt, JT, Wobj, sig, dw, dc, blk);
+  elem_scatter<T>(P, e, Wzz, JZ, Wzt, JT, Wobj, sig, dw, dc, blk);
 }
 
 template <typename T>
-__device__ inline void elem_scatter(const DevProb& P, const double* Wzz, const double* JZ,
-                                    const double* Wzt, const double* JT, const double* Wobj,
-                                    const double* sig, double dw, double dc, T* blk) {
-  const int n = P.n, p = P.p, m = P.m;
+__device__ __noinline__ void elem_scatter(const DevProb& P, int e, const double* Wzz,
+                                          const double* JZ, const double* Wzt, const double* JT,
+                                          const double* Wobj, const double* sig, double dw,
+                                          double dc, T* blk) {
+  const int n = P.n, p = P.p, m = P.m, K = P.K, np = P.np;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nn = n * n, np = n * p;
+  const int nn = n * n, np_ = n * p;
   auto put = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] = v; };
   auto add = [&](int a, int b, T v) { blk[a >= b ? tri_at(a, b) : tri_at(b, a)] += v; };
   // 1. disjoint entries: point Hessian blocks, the identity parts of the
   //    collocation rows (D[k][j]), continuity / initial rows, -delta_c, border
   const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
-  for (int i = tid; i < 3 * nn; i += nt) {
+  const float inv_np = 1.f / (float)np;
+  for (int i = tid; i < K * nn; i += nt) {
     const int rs = quot(i, n, inv_n), sb = i - rs * n;   // rs = k n + sa
     const int k = quot(rs, n, inv_n), sa = rs - k * n;
-    if (sa >= sb) put(loc_state(k + 1, sa, n), loc_state(k + 1, sb, n), (T)Wzz[i]);
+    if (sa >= sb) put(loc_state(P, k + 1, sa), loc_state(P, k + 1, sb), (T)Wzz[i]);
   }
-  for (int i = tid; i < 12 * n; i += nt) {
-    const int kj = quot(i, n, inv_n), s2 = i - kj * n, k = (kj >> 2) + 1, j = kj & 3;
-    put(loc_dual(k, s2, n), loc_state(j, s2, n), (T)P.D[k][j]);
+  for (int i = tid; i < K * np * n; i += nt) {
+    const int kj = quot(i, n, inv_n), s2 = i - kj * n;
+    const int k1 = quot(kj, np, inv_np), j = kj - k1 * np;
+    put(loc_dual(P, k1 + 1, s2), loc_state(P, j, s2), (T)P.D[k1 + 1][j]);
   }
-  for (int s2 = tid; s2 < n; s2 += nt) put(loc_dual(0, s2, n), loc_state(0, s2, n), T(1));
-  for (int i = tid; i < 4 * n; i += nt) {
+  if (!P.gauss) {
+    // the element's own continuity / initial row c0 on z0
+    for (int s2 = tid; s2 < n; s2 += nt) put(loc_dual(P, 0, s2), loc_state(P, 0, s2), T(1));
+  } else if (chain_next(P, e)) {
+    // the next element's continuity row: -b_j on every point of this element
+    for (int i = tid; i < np * n; i += nt) {
+      const int j = quot(i, n, inv_n), s2 = i - j * n;
+      put(loc_dual(P, 0, s2), loc_state(P, j, s2), (T)(-P.bw[j]));
+    }
+  }
+  for (int i = tid; i < np * n; i += nt) {
     const int k = quot(i, n, inv_n), s2 = i - k * n;
-    const int a = loc_dual(k, s2, n);
+    const int a = loc_dual(P, k, s2);
     put(a, a, (T)(-dc));
   }
-  for (int i = tid; i < 3 * np; i += nt) {
+  for (int i = tid; i < K * np_; i += nt) {
     const int ks = quot(i, p, inv_p), q = i - ks * p;     // ks = k n + s
     const int k = quot(ks, n, inv_n), s2 = ks - k * n;
-    put(m + q, loc_state(k + 1, s2, n), (T)Wzt[i]);
-    put(m + q, loc_dual(k + 1, s2, n), (T)JT[i]);
+    put(m + q, loc_state(P, k + 1, s2), (T)Wzt[i]);
+    put(m + q, loc_dual(P, k + 1, s2), (T)JT[i]);
   }
   __syncthreads();
   // 2. sums onto those: objective blocks (same species across points) and the
   //    -h df/dz part of the collocation rows
-  for (int i = tid; i < 16 * n; i += nt) {
-    const int s2 = i >> 4, ja = (i >> 2) & 3, jb = i & 3;
-    const int a = loc_state(ja, s2, n), b = loc_state(jb, s2, n);
+  const int np2 = np * np;
+  const float inv_np2 = 1.f / (float)np2;
+  for (int i = tid; i < np2 * n; i += nt) {
+    const int s2 = quot(i, np2, inv_np2), jj = i - s2 * np2;
+    const int ja = quot(jj, np, inv_np), jb = jj - ja * np;
+    const int a = loc_state(P, ja, s2), b = loc_state(P, jb, s2);
     if (a >= b) add(a, b, (T)Wobj[i]);
   }
-  for (int i = tid; i < 3 * nn; i += nt) {
+  for (int i = tid; i < K * nn; i += nt) {
     const int rs = quot(i, n, inv_n), sp = i - rs * n;   // rs = k n + sd
     const int k = quot(rs, n, inv_n), sd = rs - k * n;
-    add(loc_dual(k + 1, sd, n), loc_state(k + 1, sp, n), (T)JZ[i]);
+    add(loc_dual(P, k + 1, sd), loc_state(P, k + 1, sp), (T)JZ[i]);
   }
   __syncthreads();
   // 3. barrier diagonal and delta_w on the states
-  for (int i = tid; i < 4 * n; i += nt) {
+  for (int i = tid; i < np * n; i += nt) {
     const int j = quot(i, n, inv_n), s2 = i - j * n;
-    const int a = loc_state(j, s2, n);
+    const int a = loc_state(P, j, s2);
     add(a, a, (T)((sig ? sig[i] : 0.0) + dw));
   }
   __syncthreads();
+}
+
+// Gauss points: the trailing chain group of element e, (z_e0, c_(e+1)0)
+// pairs at local rows i0 + 2s, i0 + 2s + 1, leaves in three parts: the z part
+// of chain block e (its c part and the constant identity between them are
+// written here only when e starts a chain, otherwise by element e - 1), the c
+// part of chain block e + 1 with the coupling Cpl[e + 1] = K[c_(e+1)0, z_e0],
+// and the borders of both.  tr(a, b): the trailing block's symmetric entry.
+// Out of line, so that it does not add to the register demand of the
+// elimination kernels it is called from.
+template <typename T, class Tr>
+__device__ __noinline__ void gauss_chain_out(const DevProb& P, const DevFactor<T>& F, int e,
+                                             int i0, double dc, Tr tr) {
+  const int n = P.n, p = P.p, m = P.m, n2 = 2 * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool start = chain_start(P, e), next = chain_next(P, e);
+  T* Ae = F.Aif + (size_t)e * n2 * n2;
+  for (int i = tid; i < n * n; i += nt) {
+    const int s2 = i / n, t = i - s2 * n;
+    Ae[(2 * s2) * n2 + 2 * t] = tr(i0 + 2 * s2, i0 + 2 * t);
+    Ae[(2 * s2) * n2 + 2 * t + 1] = s2 == t ? T(1) : T(0);
+    Ae[(2 * s2 + 1) * n2 + 2 * t] = s2 == t ? T(1) : T(0);
+    if (start) Ae[(2 * s2 + 1) * n2 + 2 * t + 1] = s2 == t ? (T)(-dc) : T(0);
+  }
+  T* Be = F.Bif + (size_t)e * n2 * p;
+  for (int i = tid; i < n * p; i += nt) {
+    const int s2 = i / p, q = i - s2 * p;
+    Be[(2 * s2) * p + q] = tr(m + q, i0 + 2 * s2);
+    if (start) Be[(2 * s2 + 1) * p + q] = T(0);
+  }
+  if (start) {
+    T* C = F.Cpl + (size_t)e * n * n;
+    for (int i = tid; i < n * n; i += nt) C[i] = T(0);
+  }
+  if (next) {
+    T* An = F.Aif + (size_t)(e + 1) * n2 * n2;
+    T* Cn = F.Cpl + (size_t)(e + 1) * n * n;
+    for (int i = tid; i < n * n; i += nt) {
+      const int s2 = i / n, t = i - s2 * n;
+      An[(2 * s2 + 1) * n2 + 2 * t + 1] = tr(i0 + 2 * s2 + 1, i0 + 2 * t + 1);
+      Cn[i] = tr(i0 + 2 * s2 + 1, i0 + 2 * t);
+    }
+    T* Bn = F.Bif + (size_t)(e + 1) * n2 * p;
+    for (int i = tid; i < n * p; i += nt) {
+      const int s2 = i / p, q = i - s2 * p;
+      Bn[(2 * s2 + 1) * p + q] = tr(m + q, i0 + 2 * s2 + 1);
+    }
+  }
 }
 
 template <typename T, int TPT>
@@ -745,7 +827,7 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
                                const DevFactor<T>& F, int e, Pair<T>* ub, T* blk) {
   const int n = P.n, p = P.p, m = P.m, ext = P.ext;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nint = 3 * n, i0 = 2 * nint, n2 = 2 * n;
+  const int nint = P.K * n, i0 = 2 * nint, n2 = 2 * n;
   const float inv_n = 1.f / (float)n, inv_p = p > 0 ? 1.f / (float)p : 0.f;
   elem_assemble_rt<T>(P, E, sigma, dw, dc, e, blk);
   auto entry = [&](int r, int c) -> T { return blk[tri_at(r, c)]; };
@@ -757,8 +839,19 @@ __device__ void elem_factor_rt(const DevProb& P, const DevEval& E,
   if (tid == 0) {
     F.inert[e * 3 + 0] = cnt[0]; F.inert[e * 3 + 1] = cnt[1]; F.inert[e * 3 + 2] = cnt[2];
   }
-  // trailing block: interface (2n x 2n, both triangles), its border (p x 2n),
+  // trailing block: chain block (2n x 2n, both triangles), its border (p x 2n),
   // parameter part (FP64)
+  if (P.gauss) {
+    __syncthreads();
+    auto tr = [&](int a, int b) { return a >= b ? blk[tri_at(a, b)] : blk[tri_at(b, a)]; };
+    gauss_chain_out<T>(P, F, e, i0, dc, tr);
+    double* Sc = F.Scon + (size_t)e * p * p;
+    for (int i = tid; i < p * p; i += nt) {
+      const int q = quot(i, p, inv_p), q2 = i - q * p;
+      Sc[i] = (double)(q >= q2 ? blk[tri_at(m + q, m + q2)] : blk[tri_at(m + q2, m + q)]);
+    }
+    return;
+  }
   const float inv_n2 = 1.f / (float)n2;
   T* Aif = F.Aif + (size_t)e * n2 * n2;
   for (int i = tid; i < n2 * n2; i += nt) {
@@ -1110,7 +1203,7 @@ __device__ void schur_block(const DevProb& P, const int* __restrict__ inert,
   __shared__ long long cnt[3];
   __shared__ long long red[3][SBS];
   const int p = P.p, N = P.N, tid = threadIdx.x;
-  const size_t nz = (size_t)N * NP * P.n;
+  const size_t nz = (size_t)N * P.np * P.n;
   double* l = sS + (size_t)p * p;
   for (int idx = tid; idx < p * p; idx += SBS) {
     const int q = idx / p, q2 = idx - q * p;
@@ -1303,13 +1396,64 @@ __device__ void warp_backward(T* x, const T* v, int msz, int npairs, const T* __
   }
 }
 
-// local index -> position in the API-layout KKT vector of element e
+// local index a < m -> position in the API-layout KKT vector of element e.
+// Radau: every local row is an unknown of the element.
 __device__ inline size_t elem_global(const DevProb& P, int e, int a) {
   const int n = P.n;
-  const size_t nx = (size_t)P.N * NP * n + P.p;
+  const size_t nx = (size_t)P.N * 4 * n + P.p;
   const int pr = a >> 1, g = pr / n, s = pr - g * n;
-  if (a & 1) return nx + ((size_t)e * NP + grp_con(g)) * n + s;
-  return ((size_t)e * NP + grp_point(g)) * n + s;
+  if (a & 1) return nx + ((size_t)e * 4 + grp_con(0, 3, g)) * n + s;
+  return ((size_t)e * 4 + grp_point(0, 3, g)) * n + s;
+}
+// Gauss: the chain group's multipliers are the next element's c0, absent
+// (-1) after a chain's last element, whose block has zero rows there apart
+// from -delta_c.
+__device__ inline long long elem_global_gauss(const DevProb& P, int e, int a) {
+  const int n = P.n, np = P.np;
+  const size_t nx = (size_t)P.N * np * n + P.p;
+  const int pr = a >> 1, g = pr / n, s = pr - g * n;
+  if (a & 1) {
+    if (g == P.K) return chain_next(P, e) ? (long long)(nx + (size_t)(e + 1) * np * n + s) : -1;
+    return (long long)(nx + ((size_t)e * np + g + 1) * n + s);
+  }
+  return (long long)(((size_t)e * np + (g < P.K ? g + 1 : 0)) * n + s);
+}
+// w[a] = v[global index of a] (0 where there is none) for a in [lo, hi), or
+// the reverse when store (Gauss elements, one warp; out of line).
+template <typename T>
+__device__ __noinline__ void gauss_elem_gather(const DevProb& P, int e, const double* v, T* w,
+                                               int lo, int hi) {
+  for (int a = lo + (threadIdx.x & 31); a < hi; a += 32) {
+    const long long gi = elem_global_gauss(P, e, a);
+    w[a] = gi >= 0 ? (T)v[gi] : T(0);
+  }
+}
+template <typename T>
+__device__ __noinline__ void gauss_elem_scatter(const DevProb& P, int e, const T* w, double* v,
+                                                int lo, int hi) {
+  for (int a = lo + (threadIdx.x & 31); a < hi; a += 32) {
+    const long long gi = elem_global_gauss(P, e, a);
+    if (gi >= 0) v[gi] = (double)w[a];
+  }
+}
+
+// Gauss points: chain right-hand sides after element e's forward
+// elimination (wt: the trailing rows (z_e0, c_(e+1)0) interleaved): the z part
+// of chain block e and the c part of chain block e + 1 (the rhs of c_(e+1)0
+// updated by this element's elimination); a chain's first element also sets
+// its own c part, the rhs of its initial condition.  One warp.
+template <typename T>
+__device__ __noinline__ void gauss_chain_rhs(const DevProb& P, const DevFactor<T>& F,
+                                             const double* __restrict__ b, int e, const T* wt) {
+  const int lane = threadIdx.x & 31, n = P.n;
+  const size_t nx = (size_t)P.N * P.np * n + P.p;
+  T* Rif = F.Rif + (size_t)e * 2 * n;
+  const bool start = chain_start(P, e), next = chain_next(P, e);
+  for (int s2 = lane; s2 < n; s2 += 32) {
+    Rif[2 * s2] = wt[2 * s2];
+    if (start) Rif[2 * s2 + 1] = (T)b[nx + (size_t)e * P.np * n + s2];
+    if (next) F.Rif[(size_t)(e + 1) * 2 * n + 2 * s2 + 1] = wt[2 * s2 + 1];
+  }
 }
 
 template <typename T>
@@ -1317,9 +1461,14 @@ __device__ void elem_fwd_one(const DevProb& P, const DevFactor<T>& F, const doub
                              int e, T* w) {
   const int lane = threadIdx.x & 31;
   const int n = P.n, ext = P.ext, m = P.m, p = P.p;
-  for (int a = lane; a < ext; a += 32) w[a] = a < m ? (T)b[elem_global(P, e, a)] : T(0);
+  if (!P.gauss) {
+    for (int a = lane; a < ext; a += 32) w[a] = a < m ? (T)b[elem_global(P, e, a)] : T(0);
+  } else {
+    gauss_elem_gather<T>(P, e, b, w, 0, m);
+    for (int a = m + lane; a < ext; a += 32) w[a] = T(0);
+  }
   __syncwarp();
-  const int nint = 3 * n;
+  const int nint = P.K * n;
   const T* Lc = F.Lel + (size_t)e * (2 * nint) * ext;
   warp_forward<T>(w, ext, nint, Lc, ext);
   const T* D = F.Del + (size_t)e * nint * 3;
@@ -1330,7 +1479,11 @@ __device__ void elem_fwd_one(const DevProb& P, const DevFactor<T>& F, const doub
     V[2 * q] = v0; V[2 * q + 1] = v1;
   }
   T* Rif = F.Rif + (size_t)e * 2 * n;
-  for (int u = lane; u < 2 * n; u += 32) Rif[u] = w[2 * nint + u];
+  if (!P.gauss) {
+    for (int u = lane; u < 2 * n; u += 32) Rif[u] = w[2 * nint + u];
+  } else {
+    gauss_chain_rhs<T>(P, F, b, e, w + 2 * nint);
+  }
   double* Rth = F.Rth + (size_t)e * p;
   for (int q = lane; q < p; q += 32) Rth[q] = (double)w[m + q];
   __syncwarp();
@@ -1375,7 +1528,7 @@ __device__ void theta_solve_block(const DevProb& P, const double* __restrict__ c
                                   const double* __restrict__ b, const DevSchur& S,
                                   double* __restrict__ sol, double* sv) {
   const int p = P.p, N = P.N, tid = threadIdx.x;
-  const size_t nz = (size_t)N * NP * P.n;
+  const size_t nz = (size_t)N * P.np * P.n;
   for (int q = tid; q < p; q += blockDim.x) sv[q] = b[nz + q] + sum_chunks(chunkR, n_chunks(2 * N), p, q);
   __syncthreads();
   for (int k = 0; k < p; ++k) {
@@ -1408,17 +1561,17 @@ template <typename T>
 __device__ void bcr_bwd_one(const DevProb& P, const DevFactor<T>& F, const DevSchur& S,
                             double* __restrict__ sol, int stride, int final_level, int bi, T* x) {
   const int lane = threadIdx.x & 31;
-  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n;
+  const int n = P.n, p = P.p, N = P.N, bext = P.bext, n2 = 2 * n, np = P.np, cpt = P.cpt;
   const int i = final_level ? 0 : stride * (2 * bi + 1);
   const int L = final_level ? -1 : i - stride;
   const int R = (!final_level && i + stride < N) ? i + stride : -1;
-  const size_t nx = (size_t)N * NP * n + p;
+  const size_t nx = (size_t)N * np * n + p;
   for (int a = lane; a < bext; a += 32) {
     T v = T(0);
     if (a >= n2 && a < 3 * n) {
-      if (L >= 0) v = (T)sol[((size_t)L * NP + KC) * n + (a - n2)];
+      if (L >= 0) v = (T)sol[((size_t)L * np + cpt) * n + (a - n2)];
     } else if (a >= 3 * n && a < 4 * n) {
-      if (R >= 0) v = (T)sol[nx + (size_t)R * NP * n + (a - 3 * n)];
+      if (R >= 0) v = (T)sol[nx + (size_t)R * np * n + (a - 3 * n)];
     } else if (a >= 4 * n) {
       v = (T)S.xth[a - 4 * n];
     }
@@ -1427,8 +1580,8 @@ __device__ void bcr_bwd_one(const DevProb& P, const DevFactor<T>& F, const DevSc
   __syncwarp();
   warp_backward<T>(x, F.Vb + (size_t)i * n2, bext, n, F.Lb + (size_t)i * n2 * bext, bext);
   for (int s = lane; s < n; s += 32) {
-    sol[((size_t)i * NP + KC) * n + s] = (double)x[2 * s];
-    sol[nx + (size_t)i * NP * n + s] = (double)x[2 * s + 1];
+    sol[((size_t)i * np + cpt) * n + s] = (double)x[2 * s];
+    sol[nx + (size_t)i * np * n + s] = (double)x[2 * s + 1];
   }
   __syncwarp();
 }
@@ -1438,17 +1591,26 @@ __device__ void elem_bwd_one(const DevProb& P, const DevFactor<T>& F, const DevS
                              double* __restrict__ sol, int e, T* x) {
   const int lane = threadIdx.x & 31;
   const int n = P.n, ext = P.ext, m = P.m;
-  const int nint = 3 * n;
-  for (int a = lane; a < ext; a += 32) {
-    T v = T(0);
-    if (a >= 2 * nint && a < m) v = (T)sol[elem_global(P, e, a)];
-    else if (a >= m) v = (T)S.xth[a - m];
-    x[a] = v;
+  const int nint = P.K * n;
+  if (!P.gauss) {
+    for (int a = lane; a < ext; a += 32) {
+      T v = T(0);
+      if (a >= 2 * nint && a < m) v = (T)sol[elem_global(P, e, a)];
+      else if (a >= m) v = (T)S.xth[a - m];
+      x[a] = v;
+    }
+  } else {
+    for (int a = lane; a < 2 * nint; a += 32) x[a] = T(0);
+    gauss_elem_gather<T>(P, e, sol, x, 2 * nint, m);
+    for (int a = m + lane; a < ext; a += 32) x[a] = (T)S.xth[a - m];
   }
   __syncwarp();
   warp_backward<T>(x, F.Vint + (size_t)e * 2 * nint, ext, nint,
                    F.Lel + (size_t)e * (2 * nint) * ext, ext);
-  for (int a = lane; a < 2 * nint; a += 32) sol[elem_global(P, e, a)] = (double)x[a];
+  if (!P.gauss)
+    for (int a = lane; a < 2 * nint; a += 32) sol[elem_global(P, e, a)] = (double)x[a];
+  else
+    gauss_elem_scatter<T>(P, e, x, sol, 0, 2 * nint);
   __syncwarp();
 }
 

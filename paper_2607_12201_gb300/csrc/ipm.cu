@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(IBS) k_sum_parts(const double* __restrict__ pa
 __global__ void k_init_point(DevProb P, const double* __restrict__ theta0, double* __restrict__ x,
                              double* __restrict__ zl, double* __restrict__ zu, double kappa1,
                              double kappa2) {
-  const size_t nz = (size_t)P.N * NP * P.n;
+  const size_t nz = (size_t)P.N * P.np * P.n;
   for (int q = threadIdx.x; q < P.p; q += blockDim.x) {
     const double lo = P.theta_lo[q], hi = P.theta_hi[q];
     const double pl = fmin(kappa1 * fmax(1.0, fabs(lo)), kappa2 * (hi - lo));
@@ -108,6 +108,17 @@ __global__ void k_init_point(DevProb P, const double* __restrict__ theta0, doubl
     zl[q] = 1.0;
     zu[q] = 1.0;
   }
+}
+
+// State at the element's end, the next element's z0 (Eq. 2c): Radau z_K
+// (tau_K = 1); Gauss the extrapolation sum_j b_j z_j, j = 0..K, with z_0 = z0
+// and z_j = Z[j - 1] (same order of terms as the continuity residual).
+__device__ inline double end_state(const DevProb& P, const double* z0, const double* Z, int s) {
+  const int n = P.n;
+  if (!P.gauss) return Z[(P.K - 1) * n + s];
+  double v = P.bw[0] * z0[s];
+  for (int j = 1; j <= P.K; ++j) v += P.bw[j] * Z[(j - 1) * n + s];
+  return v;
 }
 
 // Collocation forward sweep at theta = x[nz..]: for each element in turn,
@@ -120,7 +131,7 @@ __global__ void k_init_point(DevProb P, const double* __restrict__ theta0, doubl
 // error the FP64 residual of the next iteration corrects), so the sweep
 // converges to the same FP64 collocation solution.  One block of SWEEP_BS
 // threads; the FP32 augmented matrix [J | G] sits in shared memory, or in
-// gwork when 3n is too large.
+// gwork when Kn is too large.
 constexpr int SWEEP_MAXIT = 30;
 constexpr int SWEEP_BS = 256;
 __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
@@ -129,17 +140,17 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
   __shared__ float s_inv;
   __shared__ double s_red[SWEEP_BS];
   __shared__ int s_flag;
-  const int n = P.n, r = P.r, dim = KC * n, ldj = dim + 1;
+  const int n = P.n, r = P.r, K = P.K, dim = K * n, ldj = dim + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* kr = sm;                 // [r]
-  double* mon = kr + r;            // [3][r]
-  double* da = mon + KC * r;       // [3][r]
-  double* db = da + KC * r;        // [3][r]
-  double* z0 = db + KC * r;        // [n]
-  double* Z = z0 + n;              // [3n]
-  double* dZ = Z + dim;            // [3n]
+  double* mon = kr + r;            // [K][r]
+  double* da = mon + K * r;        // [K][r]
+  double* db = da + K * r;         // [K][r]
+  double* z0 = db + K * r;         // [n]
+  double* Z = z0 + n;              // [Kn]
+  double* dZ = Z + dim;            // [Kn]
   float* Jm = gwork ? gwork : reinterpret_cast<float*>(dZ + dim);  // [dim][dim+1]
-  const size_t nz = (size_t)P.N * NP * n;
+  const size_t nz = (size_t)P.N * P.np * n;
   int nfail = 0;
   for (int i = 0; i < P.N; ++i) {
     if (chain_start(P, i)) {   // a condition's first element: its rates and x0
@@ -157,7 +168,7 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
     __syncthreads();
     bool ok = false;
     for (int it = 0; it < SWEEP_MAXIT; ++it) {
-      for (int idx = tid; idx < KC * r; idx += SWEEP_BS) {
+      for (int idx = tid; idx < K * r; idx += SWEEP_BS) {
         const int k = idx / r, j = idx - k * r;
         const int a = P.react[2 * j], b = P.react[2 * j + 1];
         const double za = Z[k * n + a];
@@ -189,7 +200,7 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
       for (int row = tid; row < dim; row += SWEEP_BS) {
         const int k = row / n + 1, s = row - (k - 1) * n;
         double g = P.D[k][0] * z0[s];
-        for (int j = 1; j <= KC; ++j) g += P.D[k][j] * Z[(j - 1) * n + s];
+        for (int j = 1; j <= K; ++j) g += P.D[k][j] * Z[(j - 1) * n + s];
         double f = 0.0;
         for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e)
           f += P.nu_v[e] * kr[P.nu_r[e]] * mon[(k - 1) * r + P.nu_r[e]];
@@ -267,11 +278,11 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
       for (int t = tid; t < dim; t += SWEEP_BS) Z[t] = z0[t % n];
       __syncthreads();
     }
-    double* xi = x + (size_t)i * NP * n;
+    double* xi = x + (size_t)i * P.np * n;
     for (int s = tid; s < n; s += SWEEP_BS) xi[s] = z0[s];
     for (int t = tid; t < dim; t += SWEEP_BS) xi[n + t] = Z[t];
     __syncthreads();
-    for (int s = tid; s < n; s += SWEEP_BS) z0[s] = Z[(KC - 1) * n + s];
+    for (int s = tid; s < n; s += SWEEP_BS) z0[s] = end_state(P, z0, Z, s);
     __syncthreads();
   }
   if (tid == 0) *fails = nfail;
@@ -284,7 +295,7 @@ __global__ void __launch_bounds__(SWEEP_BS) k_forward_sweep(DevProb P, double* _
   sweep_cta(P, x, fails, gwork, sm);
 }
 
-// The same sweep for 3n <= 32 on one warp: lane l owns row l of the FP32
+// The same sweep for Kn <= 32 on one warp: lane l owns row l of the FP32
 // Newton matrix in registers, so the LU with partial pivoting and the
 // substitutions run on warp shuffles without block barriers.  The Newton
 // iteration is a chord iteration: the LU's multipliers (lrow, per step and
@@ -297,17 +308,17 @@ constexpr int WSWEEP = 32;
 constexpr double CHORD_RATE = 0.25;
 __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
                            double* sm) {
-  const int n = P.n, r = P.r, dim = KC * n;
+  const int n = P.n, r = P.r, K = P.K, dim = K * n;
   const int lane = threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   double* kr = sm;                 // [r]
-  double* mon = kr + r;            // [3][r]
-  float* daf = reinterpret_cast<float*>(mon + KC * r);   // [3][r]
-  float* dbf = daf + KC * r;                             // [3][r]
-  float* rows = dbf + KC * r;                            // [32][33] staging
+  double* mon = kr + r;            // [K][r]
+  float* daf = reinterpret_cast<float*>(mon + K * r);   // [K][r]
+  float* dbf = daf + K * r;                             // [K][r]
+  float* rows = dbf + K * r;                            // [32][33] staging
   double* z0 = reinterpret_cast<double*>(rows + WSWEEP * (WSWEEP + 1));  // [n]
-  double* Z = z0 + n;              // [3n]
-  const size_t nz = (size_t)P.N * NP * n;
+  double* Z = z0 + n;              // [Kn]
+  const size_t nz = (size_t)P.N * P.np * n;
   const int rk = lane < dim ? lane / n + 1 : 1;
   const int rs = lane < dim ? lane - (rk - 1) * n : 0;
   int nfail = 0;
@@ -333,7 +344,7 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
     double mdz_prev = 0.0;
     for (int it = 0; it < SWEEP_MAXIT; ++it) {
       const bool refactor = !have_lu;
-      for (int idx = lane; idx < KC * r; idx += 32) {
+      for (int idx = lane; idx < K * r; idx += 32) {
         const int k = idx / r, j = idx - k * r;
         const int a = P.react[2 * j], b = P.react[2 * j + 1];
         const double za = Z[k * n + a];
@@ -346,10 +357,10 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
       if (lane < dim) {
         if (refactor) {
           for (int c = 0; c < WSWEEP; ++c) myrow[c] = 0.f;
-          for (int j = 1; j <= KC; ++j) myrow[(j - 1) * n + rs] = (float)P.D[rk][j];
+          for (int j = 1; j <= K; ++j) myrow[(j - 1) * n + rs] = (float)P.D[rk][j];
         }
         g = P.D[rk][0] * z0[rs];
-        for (int j = 1; j <= KC; ++j) g += P.D[rk][j] * Z[(j - 1) * n + rs];
+        for (int j = 1; j <= K; ++j) g += P.D[rk][j] * Z[(j - 1) * n + rs];
         double f = 0.0;
         const float hf = (float)P.h;
         for (int e = P.nu_ptr[rs]; e < P.nu_ptr[rs + 1]; ++e) {
@@ -464,11 +475,11 @@ __device__ void sweep_warp(const DevProb& P, double* __restrict__ x, int* __rest
       __syncwarp();
     }
     dZ = lane < dim ? Z[lane] - z0[rs] : 0.0;
-    double* xi = x + (size_t)i * NP * n;
+    double* xi = x + (size_t)i * P.np * n;
     for (int s = lane; s < n; s += 32) xi[s] = z0[s];
     for (int t = lane; t < dim; t += 32) xi[n + t] = Z[t];
     __syncwarp();
-    for (int s = lane; s < n; s += 32) z0[s] = Z[(KC - 1) * n + s];
+    for (int s = lane; s < n; s += 32) z0[s] = end_state(P, z0, Z, s);
     __syncwarp();
   }
   if (lane == 0) *fails = nfail;
@@ -481,8 +492,8 @@ __global__ void __launch_bounds__(32) k_forward_sweep_warp(DevProb P, double* __
 }
 
 size_t sweep_warp_smem_bytes(const DevProb& P) {
-  size_t sm = sizeof(double) * ((size_t)P.r * (1 + KC) + P.n + KC * (size_t)P.n) +
-              sizeof(float) * ((size_t)2 * KC * P.r + WSWEEP * (WSWEEP + 1));
+  size_t sm = sizeof(double) * ((size_t)P.r * (1 + P.K) + P.n + P.K * (size_t)P.n) +
+              sizeof(float) * ((size_t)2 * P.K * P.r + WSWEEP * (WSWEEP + 1));
   return (sm + 15) & ~size_t(15);
 }
 
@@ -501,15 +512,15 @@ __global__ void __launch_bounds__(SWEEP_BS) k_sweep_cta_b(const DevInst* __restr
 }
 
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
-  const size_t dim = KC * (size_t)P.n;
-  size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * KC) + P.n + 2 * dim);
+  const size_t dim = P.K * (size_t)P.n;
+  size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * P.K) + P.n + 2 * dim);
   if (jm_in_smem) v += sizeof(float) * dim * (dim + 1);
   return v;
 }
 
 cudaError_t launch_forward_sweep(collo_problem* pr) {
   const DevProb& P = pr->P;
-  if (KC * P.n <= WSWEEP) {
+  if (P.K * P.n <= WSWEEP) {
     size_t sm = sweep_warp_smem_bytes(P);
     if (sm > SMEM_OPTIN_ABOVE)
       cudaFuncSetAttribute(k_forward_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -534,7 +545,7 @@ __global__ void k_init_point_b(const DevInst* __restrict__ insts, const int* __r
                                double kappa1, double kappa2) {
   const DevInst& I = insts[act[blockIdx.x]];
   const DevProb& P = I.P;
-  const size_t nz = (size_t)P.N * NP * P.n;
+  const size_t nz = (size_t)P.N * P.np * P.n;
   for (int q = threadIdx.x; q < P.p; q += blockDim.x) {
     const double lo = P.theta_lo[q], hi = P.theta_hi[q];
     const double pl = fmin(kappa1 * fmax(1.0, fabs(lo)), kappa2 * (hi - lo));
@@ -556,7 +567,7 @@ k_theta_prep_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
   const DevInst& I = insts[act[blockIdx.x]];
   const DevProb& P = I.P;
   const double mu = prm[blockIdx.x].mu;
-  const size_t nz = (size_t)P.N * NP * P.n;
+  const size_t nz = (size_t)P.N * P.np * P.n;
   double wmax = 0.0, wmin = 1e300, zs = 0.0, lg = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
     const double th = I.x[nz + q];
@@ -601,7 +612,7 @@ k_theta_step_b(const DevInst* __restrict__ insts, const int* __restrict__ act,
   const DevInst& I = insts[act[blockIdx.x]];
   const DevProb& P = I.P;
   const double mu = prm[blockIdx.x].mu, tau = prm[blockIdx.x].tau;
-  const size_t nz = (size_t)P.N * NP * P.n;
+  const size_t nz = (size_t)P.N * P.np * P.n;
   double amax = 1.0, az = 1.0, g = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
     const double th = I.x[nz + q], d = I.kb[nz + q];
@@ -630,7 +641,7 @@ k_trial_barrier_b(const DevInst* __restrict__ insts, const int* __restrict__ act
   const DevInst& I = insts[act[blockIdx.x]];
   const DevProb& P = I.P;
   const double alpha = prm[blockIdx.x].alpha;
-  const size_t nz = (size_t)P.N * NP * P.n;
+  const size_t nz = (size_t)P.N * P.np * P.n;
   double lg = 0.0, bad = 0.0;
   for (int q = threadIdx.x; q < P.p; q += IBS) {
     const double th = I.x[nz + q] + alpha * I.kb[nz + q];

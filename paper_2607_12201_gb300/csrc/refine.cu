@@ -29,11 +29,11 @@ namespace collo {
 
 constexpr int DEF_BS = 128;
 
-// Lagrange basis on the interpolation points tau[0..NP-1]: l_j(t) and l_j'(t).
+// Lagrange basis on the interpolation points tau[0..K]: l_j(t) and l_j'(t).
 __device__ inline void lagrange(const DevProb& P, double t, double* l, double* dl) {
-  for (int j = 0; j < NP; ++j) {
+  for (int j = 0; j < P.np; ++j) {
     double v = 1.0, d = 0.0;
-    for (int a = 0; a < NP; ++a) {
+    for (int a = 0; a < P.np; ++a) {
       if (a == j) continue;
       const double inv = 1.0 / (P.tau[j] - P.tau[a]);
       // product rule: d/dt prod (t - tau_a) inv
@@ -50,14 +50,15 @@ __global__ void __launch_bounds__(DEF_BS)
 k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
   extern __shared__ double sm[];
   const int n = P.n, r = P.r, i = blockIdx.x, tid = threadIdx.x;
-  double* ze = sm;                 // [NP][n] element states
-  double* zt = ze + NP * n;        // [KC][n] z(tau*_m)
-  double* dz = zt + KC * n;        // [KC][n] sum_j l_j'(tau*_m) z_j
-  double* kr = dz + KC * n;        // [r] rate constants
-  double* mon = kr + r;            // [KC][r] k_r prod of reactants at tau*_m
+  const int K = P.K, np = P.np;
+  double* ze = sm;                 // [K+1][n] element states
+  double* zt = ze + np * n;        // [K][n] z(tau*_m)
+  double* dz = zt + K * n;         // [K][n] sum_j l_j'(tau*_m) z_j
+  double* kr = dz + K * n;         // [r] rate constants
+  double* mon = kr + r;            // [K][r] k_r prod of reactants at tau*_m
   __shared__ double red[DEF_BS];
-  const size_t zoff = (size_t)i * NP * n, nz = (size_t)P.N * NP * n;
-  for (int t = tid; t < NP * n; t += DEF_BS) ze[t] = x[zoff + t];
+  const size_t zoff = (size_t)i * np * n, nz = (size_t)P.N * np * n;
+  for (int t = tid; t < np * n; t += DEF_BS) ze[t] = x[zoff + t];
   for (int j = tid; j < r; j += DEF_BS) {
     const int q = P.pidx[j];
     double k = q < 0 ? P.kfix[j] : (P.logscale ? exp10(x[nz + q]) : x[nz + q]);
@@ -65,12 +66,12 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
     kr[j] = k;
   }
   __syncthreads();
-  for (int idx = tid; idx < KC * n; idx += DEF_BS) {
+  for (int idx = tid; idx < K * n; idx += DEF_BS) {
     const int m = idx / n, s = idx - m * n;
-    double l[NP], dl[NP];
+    double l[NPMAX], dl[NPMAX];
     lagrange(P, 0.5 * (P.tau[m] + P.tau[m + 1]), l, dl);
     double v = 0.0, d = 0.0;
-    for (int j = 0; j < NP; ++j) {
+    for (int j = 0; j < np; ++j) {
       v += l[j] * ze[j * n + s];
       d += dl[j] * ze[j * n + s];
     }
@@ -78,7 +79,7 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
     dz[idx] = d;
   }
   __syncthreads();
-  for (int idx = tid; idx < KC * r; idx += DEF_BS) {
+  for (int idx = tid; idx < K * r; idx += DEF_BS) {
     const int m = idx / r, j = idx - m * r;
     const int a = P.react[2 * j], b = P.react[2 * j + 1];
     double mo = kr[j] * zt[m * n + a];
@@ -87,7 +88,7 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
   }
   __syncthreads();
   double mx = 0.0;
-  for (int idx = tid; idx < KC * n; idx += DEF_BS) {
+  for (int idx = tid; idx < K * n; idx += DEF_BS) {
     const int m = idx / n, s = idx - m * n;
     double f = 0.0;
     for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e) f += P.nu_v[e] * mon[m * r + P.nu_r[e]];
@@ -109,27 +110,27 @@ k_defect(DevProb P, const double* __restrict__ x, double* __restrict__ def) {
 // element, t = 0 to the first), at tau_c = t / h_c - i_c.
 __global__ void k_interp(DevProb C, const double* __restrict__ xc, DevProb F,
                          double* __restrict__ xf) {
-  const size_t nzf = (size_t)F.N * NP * F.n;
+  const size_t nzf = (size_t)F.N * F.np * F.n;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nzf + F.p) return;
   if (idx >= nzf) {   // theta
-    xf[idx] = xc[(size_t)C.N * NP * C.n + (idx - nzf)];
+    xf[idx] = xc[(size_t)C.N * C.np * C.n + (idx - nzf)];
     return;
   }
   const int n = F.n, s = (int)(idx % n);
   const size_t ij = idx / n;
-  const int j = (int)(ij % NP), ie = (int)(ij / NP);
+  const int j = (int)(ij % F.np), ie = (int)(ij / F.np);
   const int cond = ie / F.Nch, i = ie - cond * F.Nch;
   const double t = ((double)i + F.tau[j]) * F.h;
   const double u = t / C.h;
   int ic = (int)ceil(u) - 1;
   ic = ic < 0 ? 0 : (ic > C.Nch - 1 ? C.Nch - 1 : ic);
   const double tc = u - ic;
-  double l[NP];
+  double l[NPMAX];
   lagrange(C, tc, l, nullptr);
   const size_t ec = (size_t)cond * C.Nch + ic;
   double v = 0.0;
-  for (int a = 0; a < NP; ++a) v += l[a] * xc[(ec * NP + a) * n + s];
+  for (int a = 0; a < C.np; ++a) v += l[a] * xc[(ec * C.np + a) * n + s];
   xf[idx] = v;
 }
 
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(DEF_BS) k_max(const double* __restrict__ v, in
 }
 
 static size_t defect_smem(const DevProb& P) {
-  return sizeof(double) * ((size_t)NP * P.n + 2 * (size_t)KC * P.n + P.r + (size_t)KC * P.r);
+  return sizeof(double) * ((size_t)P.np * P.n + 2 * (size_t)P.K * P.n + P.r + (size_t)P.K * P.r);
 }
 
 // Defect of x (device, n_x) into def (device, N) and its maximum into *mx
@@ -193,7 +194,8 @@ collo_status collo_problem_create_refined(const collo_problem* coarse, int N,
   net.theta_hi = h.hi.data();
   collo_observables obs{(int)h.species.size(), h.species.data()};
   collo_data data{(int)h.t.size(), h.t.data(), h.observable.data(), h.y.data(), h.sigma.data()};
-  collo_mesh mesh{coarse->P.T, N, KC};
+  collo_mesh mesh{coarse->P.T, N, coarse->P.K,
+                  coarse->P.gauss ? COLLO_SCHEME_GAUSS : COLLO_SCHEME_RADAU};
   collo_problem_options o{};
   o.precision = coarse->precision;
   o.device = coarse->device;

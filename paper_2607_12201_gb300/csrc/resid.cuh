@@ -48,7 +48,7 @@ __device__ inline double block_max(double v, double* sh) {
 // only at their structural nonzeros (the pattern lists of DevProb, ascending,
 // so each sum keeps the order of the dense loop; the skipped terms are exact
 // zeros).  One block per element computes the
-// element's 8n rows and its contribution to the p parameter rows; norms per
+// element's 2 (K + 1) n rows and its contribution to the p parameter rows; norms per
 // element go to npart[i][0..2] (max |r_x|, max |r_c|, max |b| over the
 // element's rows).
 template <int BS = EVAL_BS>
@@ -58,27 +58,27 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
                            double bxs, const double* __restrict__ bc, double bcs,
                            double* __restrict__ rout, double* __restrict__ thpart,
                            double* __restrict__ npart, int i, double* red) {
-  const int n = P.n, p = P.p, N = P.N;
+  const int n = P.n, p = P.p, N = P.N, K = P.K, np = P.np;
   const int tid = threadIdx.x;
-  const size_t nz = (size_t)N * NP * n, nx = nz + p;
-  const size_t zoff = (size_t)i * NP * n;
+  const size_t nz = (size_t)N * np * n, nx = nz + p;
+  const size_t zoff = (size_t)i * np * n;
   const double* vz = vx;
   const double* vt = vx ? vx + nz : nullptr;
   const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
-  const double* JZ = E.JZ + (size_t)i * KC * nn;
-  const double* JT = E.JT + (size_t)i * KC * np_;
-  const double* Wzz = E.Wzz + (size_t)i * KC * nn;
-  const double* Wzt = E.Wzt + (size_t)i * KC * np_;
-  const double* Wob = E.Wobj + (size_t)i * n * NP * NP;
+  const double* JZ = E.JZ + (size_t)i * K * nn;
+  const double* JT = E.JT + (size_t)i * K * np_;
+  const double* Wzz = E.Wzz + (size_t)i * K * nn;
+  const double* Wzt = E.Wzt + (size_t)i * K * np_;
+  const double* Wob = E.Wobj + (size_t)i * n * np * np;
+  const bool next = chain_next(P, i);
   double mx = 0.0, mc = 0.0, mb = 0.0;
-  for (int idx = tid; idx < NP * n; idx += BS) {
+  for (int idx = tid; idx < np * n; idx += BS) {
     const int j = idx / n, s = idx - j * n;
     // primal row z[i][j][s]
     double y = 0.0;
     if (vz) {
       if (P.obs_sp[s])
-#pragma unroll
-        for (int l = 0; l < NP; ++l) y += Wob[(s * NP + j) * NP + l] * vz[zoff + l * n + s];
+        for (int l = 0; l < np; ++l) y += Wob[(s * np + j) * np + l] * vz[zoff + l * n + s];
       if (j >= 1) {
         const double* wr = Wzz + (size_t)(j - 1) * nn + (size_t)s * n;
         for (int e = P.wzr_ptr[s]; e < P.wzr_ptr[s + 1]; ++e) {
@@ -101,10 +101,13 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
           y += jz[(size_t)t * n + s] * vl[zoff + j * n + t];
         }
       }
-#pragma unroll
-      for (int k = 1; k < NP; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
+      for (int k = 1; k < np; ++k) y += P.D[k][j] * vl[zoff + k * n + s];
       if (j == 0) y += vl[zoff + s];
-      if (j == KC && i + 1 < N && !chain_start(P, i + 1)) y -= vl[zoff + NP * n + s];
+      // the next element's continuity row: -b_j (Radau: -1 at j = K)
+      if (next && P.bw[j] != 0.0) {
+        if (P.gauss) y -= P.bw[j] * vl[zoff + np * n + s];
+        else y -= vl[zoff + np * n + s];
+      }
     }
     if (bx) mb = fmax(mb, fabs(bx[zoff + idx]));
     if (bc) mb = fmax(mb, fabs(bc[zoff + idx]));
@@ -115,10 +118,18 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
     double yc = 0.0;
     if (vz) {
       if (j == 0) {
-        yc = vz[zoff + s] - (!chain_start(P, i) ? vz[zoff - n + s] : 0.0);
+        double prev = 0.0;
+        if (!chain_start(P, i)) {
+          if (!P.gauss) {
+            prev = vz[zoff - n + s];
+          } else {
+            const size_t po = zoff - (size_t)np * n + s;
+            for (int l = 0; l < np; ++l) prev += P.bw[l] * vz[po + (size_t)l * n];
+          }
+        }
+        yc = vz[zoff + s] - prev;
       } else {
-#pragma unroll
-        for (int l = 0; l < NP; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];
+        for (int l = 0; l < np; ++l) yc += P.D[j][l] * vz[zoff + l * n + s];
         const double* jz = JZ + (size_t)(j - 1) * nn + (size_t)s * n;
         for (int e = P.jzr_ptr[s]; e < P.jzr_ptr[s + 1]; ++e) {
           const int t = P.jzr_i[e];
@@ -139,7 +150,7 @@ __device__ inline void resid_elem(const DevProb& P, const DevEval& E, const doub
   // this element's part of the parameter rows
   for (int q = tid; q < p; q += BS) {
     double y = 0.0;
-    for (int k = 1; k < NP; ++k)
+    for (int k = 1; k < np; ++k)
       for (int e = P.thq_ptr[q]; e < P.thq_ptr[q + 1]; ++e) {
         const int s = P.thq_i[e];
         if (vz) y += Wzt[(size_t)(k - 1) * np_ + (size_t)s * p + q] * vz[zoff + k * n + s];
@@ -194,7 +205,7 @@ __device__ inline void resid_theta_one(const DevProb& P, const DevEval& E,
                                 double* sh) {
   const int tid = threadIdx.x, p = P.p, N = P.N;
   const int lane = tid & 31, warp = tid >> 5;
-  const size_t nz = (size_t)N * NP * P.n;
+  const size_t nz = (size_t)N * P.np * P.n;
   double mx = 0.0, mc = 0.0, mb = 0.0;
   for (int q = warp; q < p; q += RED_BS / 32) {
     double y = 0.0;

@@ -35,7 +35,7 @@ constexpr double ESCALATE_REL = 1e-6;
 // ---- plans ---------------------------------------------------------------------------
 struct Plan {
   std::vector<int> slots;
-  int A = 0, maxL = 0, tot_elem = 0, max_p = 0, max_n = 0;
+  int A = 0, maxL = 0, tot_elem = 0, max_p = 0, max_n = 0;   // max_n: most state rows of an element, (K + 1) n
   int lsplit = 0;   // first reduction level the solve runs one block per instance
   long long tot_upd = 0;
   int* d_int = nullptr; int* h_int = nullptr; size_t cap_int = 0;
@@ -204,7 +204,7 @@ struct Runner {
     pl.maxL = maxL;
     pl.max_p = maxp;
     pl.max_n = 0;
-    for (int s : slots) pl.max_n = std::max(pl.max_n, P(s).n);
+    for (int s : slots) pl.max_n = std::max(pl.max_n, P(s).np * P(s).n);
     const size_t n_int = (size_t)A + (A + 1) * (size_t)(4 + maxL + 1) + 2 * (size_t)A + 2 * (size_t)A;
     cudaError_t e = grow(&pl.d_int, &pl.h_int, &pl.cap_int, n_int);
     if (e == cudaSuccess) e = grow(&pl.d_ll, &pl.h_ll, &pl.cap_ll, (size_t)A + 1);
@@ -306,7 +306,7 @@ struct Runner {
     pl.off_sw_w = o;
     pl.n_sw_w = 0; pl.smem_sw_w = 0;
     for (int k = 0; k < A; ++k)
-      if (3 * P(slots[k]).n <= 32) {
+      if (P(slots[k]).K * P(slots[k]).n <= 32) {
         h[o + pl.n_sw_w++] = slots[k];
         pl.smem_sw_w = std::max(pl.smem_sw_w, sweep_warp_smem_bytes(P(slots[k])));
       }
@@ -314,7 +314,7 @@ struct Runner {
     pl.off_sw_c = o;
     pl.n_sw_c = 0; pl.smem_sw_c = 0;
     for (int k = 0; k < A; ++k)
-      if (3 * P(slots[k]).n > 32) {
+      if (P(slots[k]).K * P(slots[k]).n > 32) {
         h[o + pl.n_sw_c++] = slots[k];
         pl.smem_sw_c = std::max(pl.smem_sw_c,
                                 sweep_smem_bytes(P(slots[k]), probs[slots[k]]->sweep_work == nullptr));
@@ -1209,7 +1209,7 @@ collo_status collo_initial_states(collo_problem* prob, const double* theta, doub
   Runner* R = nullptr;
   collo_status s = self_attach(prob, &R);
   if (s != COLLO_OK) return s;
-  const size_t nz = (size_t)prob->P.N * NP * prob->P.n;
+  const size_t nz = (size_t)prob->P.N * prob->P.np * prob->P.n;
   if (prob->P.p)
     COLLO_CUDA(cudaMemcpyAsync(prob->x + nz, theta, prob->P.p * sizeof(double), cudaMemcpyDefault,
                                R->stream));

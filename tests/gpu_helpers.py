@@ -20,15 +20,20 @@ def random_point(oprob, seed, lam_scale=1.0):
 
 def assemble_J(oprob, out):
     """Sparse constraint Jacobian from the collo_eval layout + implied constants."""
-    n, N, p, K = oprob.n, oprob.N, oprob.p, 3
+    n, N, p, K = oprob.n, oprob.N, oprob.p, oprob.K
     D, h = oprob.tab.D, oprob.h
-    Z = np.arange(oprob.nz).reshape(N, 4, n)
-    # continuity rows of every element but each experimental condition's first
+    Z = np.arange(oprob.nz).reshape(N, K + 1, n)
+    # continuity rows of every element but each experimental condition's first:
+    # +1 on z[i][0], -b_j on z[i-1][j] (Radau: -1 on z[i-1][K] only)
     cont = np.array([i for i in range(1, N) if i % oprob.Nch != 0], dtype=np.int64)
-    rows, cols, vals = [Z[:, 0].ravel(), Z[cont, 0].ravel()], [Z[:, 0].ravel(), Z[cont - 1, 3].ravel()], \
-        [np.ones(N * n), -np.ones(len(cont) * n)]
-    for k in range(1, 4):
-        for j in range(4):
+    rows, cols, vals = [Z[:, 0].ravel()], [Z[:, 0].ravel()], [np.ones(N * n)]
+    for j in range(K + 1):
+        b = 1.0 if (oprob.radau and j == K) else (0.0 if oprob.radau else oprob.tab.b[j])
+        if b != 0.0:
+            rows.append(Z[cont, 0].ravel()); cols.append(Z[cont - 1, j].ravel())
+            vals.append(np.full(len(cont) * n, -b))
+    for k in range(1, K + 1):
+        for j in range(K + 1):
             if j != k:
                 rows.append(Z[:, k].ravel()); cols.append(Z[:, j].ravel())
                 vals.append(np.full(N * n, D[k, j]))
@@ -45,14 +50,14 @@ def assemble_J(oprob, out):
 
 
 def assemble_W(oprob, out):
-    n, N, p = oprob.n, oprob.N, oprob.p
-    Z = np.arange(oprob.nz).reshape(N, 4, n)
+    n, N, p, K = oprob.n, oprob.N, oprob.p, oprob.K
+    Z = np.arange(oprob.nz).reshape(N, K + 1, n)
     rows, cols, vals = [], [], []
     for s in range(n):
-        for j in range(4):
-            for l in range(4):
+        for j in range(K + 1):
+            for l in range(K + 1):
                 rows.append(Z[:, j, s]); cols.append(Z[:, l, s]); vals.append(out["hess_obj"][:, s, j, l])
-    for k in range(1, 4):
+    for k in range(1, K + 1):
         R = np.broadcast_to(Z[:, k, :, None], (N, n, n)).ravel()
         Cc = np.broadcast_to(Z[:, k, None, :], (N, n, n)).ravel()
         rows.append(R); cols.append(Cc); vals.append(out["hess_zz"][:, k - 1].ravel())

@@ -85,15 +85,26 @@ def test_calls_on_null_problem_fail_cleanly(lib):
     L.collo_problem_destroy(None)
 
 
-def test_binding_refuses_collocation_schemes_the_library_does_not_implement(lib):
+@pytest.mark.parametrize("K,scheme", [(4, 0), (3, 1), (2, 1), (3, 2), (3, -1)])
+def test_create_rejects_scheme_and_K_combinations_that_are_not_built(lib, K, scheme):
+    """Radau IIA with K = 3 and Gauss-Legendre with K = 4 are built; every
+    other (K, scheme) is INVALID_ARG before the device is touched."""
+    from paper_2607_12201_gb300 import workloads
+    inst = workloads.linear_cascade(N=4)
+    net, obs, data, mesh, keep = _structs(lib, inst, K=K)
+    mesh.scheme = scheme
+    h = C.c_void_p()
+    st = lib.lib.collo_problem_create(C.byref(net), C.byref(obs), C.byref(data), C.byref(mesh),
+                                      None, C.byref(h))
+    assert st == lib.ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_binding_refuses_unknown_scheme_names(lib):
     import dataclasses
     from paper_2607_12201_gb300 import workloads as W
-    base = W.linear_cascade(N=4)
-    for inst in (dataclasses.replace(base, K=4, scheme="gauss"),
-                 dataclasses.replace(base, scheme="gauss"),
-                 dataclasses.replace(base, K=4)):
-        with pytest.raises(ValueError, match="Radau IIA"):
-            lib.Problem(inst)
+    with pytest.raises(ValueError, match="collocation scheme"):
+        lib.Problem(dataclasses.replace(W.linear_cascade(N=4), scheme="lobatto"))
 
 
 def _unattached_problem(lib, n_x=10, n_c=8, p=2):
@@ -101,7 +112,7 @@ def _unattached_problem(lib, n_x=10, n_c=8, p=2):
     it before touching a device, so the binding's own checks run on the CPU."""
     pr = object.__new__(lib.Problem)
     pr.h = C.c_void_p()
-    pr.n, pr.r, pr.p, pr.N = 1, 1, p, 1
+    pr.n, pr.r, pr.p, pr.N, pr.K = 1, 1, p, 1, 3
     pr.n_x, pr.n_c = n_x, n_c
     pr.inst = None
     return pr
