@@ -313,7 +313,8 @@ collo_status collo_eval(collo_problem* prob, const double* x, const double* lamb
  * overwrites all of it), but every call shares it: calls whose kernels
  * overlap on the GPU race, so issue them on one stream or order them.  The
  * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) once.  The problem's derivative buffers are not
+ * (cudaGetSymbolAddress) once, so make that first call before any stream
+ * capture begins on that device.  The problem's derivative buffers are not
  * touched, so it does not replace collo_eval before collo_kkt_factor. */
 collo_status collo_eval_noalloc(collo_problem* prob, const double* x, const double* lambda,
                                 double obj_factor, const collo_eval_out* out, void* stream);

@@ -473,8 +473,10 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[256];   // device address of the array, per device ordinal
 
 // Device address of the scratch array on device `dev` (current device).
-// cudaGetSymbolAddress runs once per device; in host code the array's name is
-// only a host-side stand-in and must never be passed to a kernel.
+// cudaGetSymbolAddress runs once per device, at the first call there (which
+// therefore belongs before any stream capture on that device); in host code
+// the array's name is only a host-side stand-in and must never be passed to a
+// kernel.
 static cudaError_t noalloc_scratch(int dev, double** out) {
   if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
