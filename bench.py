@@ -22,8 +22,9 @@ reached a final status per second (all, and converged), their service-time
 percentiles, the plain FP64 single-instance path on a stratified subsample of
 the same instances, the parameter agreement of converged served solves with
 FP64 solves of the same starts, per-kernel timings and rooflines, an
-end-to-end number through host buffers, the previous config-2 multistart
-workload, a Poisson stream of the serving-stream shape, and the CPU oracle.
+end-to-end number through host buffers, the config-2 multistart workload (on
+Radau and on Gauss-Legendre K = 4 points), a Poisson stream of the
+serving-stream shape, and the CPU oracle.
 
 ``--impl reference`` times the CPU oracle instead (a bounded sample: each step
 is the oracle's initial point plus two Newton iterations of one instance of
@@ -36,6 +37,7 @@ region is bracketed by barriers and the slowest rank's time is used.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -507,6 +509,7 @@ def run_ours(args):
     out.update(kernel_rooflines(collo, insts[:S], local, per_step, clk))
     if not args.no_extra:
         out.update(config2_multistart(collo, workloads, local))
+        out.update(config2_multistart(collo, workloads, local, scheme="gauss"))
         out.update(poisson_stream(collo, workloads, local, budget))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(insts)
@@ -598,9 +601,12 @@ def kernel_rooflines(collo, insts, device, per_step, clk):
                             "that time x launches per Newton step of the served stream"}
 
 
-def config2_multistart(collo, workloads, device):
-    """The earlier config-2 workload: 256 starts of one 10-species network, served."""
+def config2_multistart(collo, workloads, device, scheme="radau"):
+    """The config-2 multistart workload: 256 starts of one 10-species network,
+    served; scheme "gauss" runs the same on Gauss-Legendre K = 4 points."""
     inst = workloads.config2()
+    if scheme == "gauss":
+        inst = dataclasses.replace(inst, K=4, scheme="gauss")
     starts = workloads.multistart_thetas(inst, 256, seed=2002)
     probs = [collo.Problem(inst, device=device) for _ in starts]
     srv = collo.Server(64, device=device, precision=collo.MIXED, tol=TOL)
@@ -619,11 +625,13 @@ def config2_multistart(collo, workloads, device):
         p.close()
     its = sum(r["iterations"] for r in res)
     conv = sum(1 for r in res if r["status"] in (collo.OK, collo.ACCEPTABLE))
-    return {"config2_multistart": {
+    key = "config2_multistart" if scheme == "radau" else "config2_multistart_gauss_k4"
+    return {key: {
         "newton_steps_per_s": its / dt, "solves_per_s": len(res) / dt,
         "converged_solves_per_s": conv / dt, "wall_s": dt,
         "what": "256 starts (theta_true + U[-0.1, 0.1]) of the 10-species / 20-reaction "
-                "network on N = 400 served through 64 slots, host clock, second pass"}}
+                "network on N = 400 served through 64 slots, host clock, second pass"
+                + ("; Gauss-Legendre K = 4 collocation" if scheme == "gauss" else "")}}
 
 
 def poisson_stream(collo, workloads, device, budget):
