@@ -517,7 +517,9 @@ collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int
  * in the global slab.  Change it only while no solve is running. */
 typedef struct collo_schedule {
   int big_threads;            /* threads per block of the condensation of element
-                                 blocks above 124 rows: 256 or 512 (default 512) */
+                                 blocks above 124 rows: 512 (one block per SM, the
+                                 default) or 256 (two blocks per SM where their
+                                 shared memory fits) */
   int slab_pairs;             /* pairs per panel of blocks whose packed triangle is
                                  held in the global slab: 8 or 16 (default 16) */
   int solve_top_blocks;       /* the batched solve runs the reduction levels with

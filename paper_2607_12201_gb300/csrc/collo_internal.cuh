@@ -254,7 +254,7 @@ void count_launch(int k = 1);
 // collo_autotune).  Results are bitwise reproducible for a fixed schedule;
 // slab_pairs changes the rounding of blocks held in the global slab.
 struct Schedule {
-  int big_threads = 512;   // threads per block of the large-element kernel (256 | 512)
+  int big_threads = 512;   // large-element kernel: 512 threads x 1 block per SM, or 256 x 2
   int slab_pairs = 16;     // pairs per panel of blocks in the global slab (8 | 16)
   int solve_top = 8;       // the solve's per-instance top levels: at most this many blocks
   int solve_elems = 8;     // elements per 8-warp block of the solve's grid

@@ -55,30 +55,169 @@ __device__ inline void tri_tile(int t, int& ti, int& tj) {
   tj = t - i * (i + 1) / 2;
 }
 
+// Panel buffer leading dimension: odd (the per-row and per-column accesses of
+// the panel eliminations spread over the banks) and PANEL_PAD rows past msz, so
+// that every warp tile of trailing_update (rows below msz + 4 TR, columns below
+// msz + 4 TR + 8 TC) reads inside the buffer.
+constexpr int PANEL_PAD = 96;
+__host__ __device__ inline int panel_ld(int msz) { return (msz + PANEL_PAD) | 1; }
+
+// Trailing update of pair_eliminate_packed for kernels with a small register
+// budget (the cyclic-reduction blocks inside the cooperative factorization
+// kernel when it runs three blocks per SM): 4 x 4 tiles of the packed
+// triangle, one per thread at a time; A[r][c] -= (sum_k Lp[k][r] W[k][c]), the
+// sum in ascending k, subtracted once (the same arithmetic per entry as
+// trailing_update, so the result does not depend on which of the two a
+// launch uses).
+template <typename T>
+__device__ void trailing_update_tiles4(T* A, int msz, int cend, int K, const T* __restrict__ Lp,
+                                       const T* __restrict__ W, int ldw) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int Tn = msz - cend;
+  if (Tn > 0) {
+    const int ntr = (Tn + 3) >> 2;
+    const int ntiles = ntr * (ntr + 1) / 2;
+    for (int t = tid; t < ntiles; t += nt) {
+      int ti, tj;
+      tri_tile(t, ti, tj);
+      const int r0 = cend + 4 * ti, cb = cend + 4 * tj;
+      // the tile's entries are loaded first, so that their latency (the
+      // triangle may be in global memory) overlaps the products below
+      T cur[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = r0 + u, c = cb + v;
+          cur[u][v] = (r < msz && c <= r) ? A[tri_at(r, c)] : T(0);
+        }
+      T acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+      for (int k = 0; k < K; ++k) {
+        T lr[4], uc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          lr[u] = (r0 + u < msz) ? Lp[k * ldw + r0 + u] : T(0);
+          uc[u] = (cb + u < msz) ? W[k * ldw + cb + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(lr[u], uc[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        if (r >= msz) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int c = cb + v;
+          if (c <= r) A[tri_at(r, c)] = cur[u][v] - acc[u][v];
+        }
+      }
+    }
+  }
+}
+
+// Trailing update of pair_eliminate_packed: A[r][c] -= sum_k Lp[k][r] W[k][c]
+// for cend <= c <= r < msz (packed lower triangle, shared or global memory),
+// the sum over k = 0..K-1 in ascending order, subtracted once.  Warp-blocked
+// register tiles: a warp owns 4 TR rows x 8 TC columns of the trailing
+// matrix, lane (ty, tx) = (lane / 8, lane % 8) the rows r0 + ty + 4u (u < TR)
+// and the columns c0 + tx + 8v (v < TC), so that for every k the warp reads
+// 4 TR entries of Lp[k] in runs of 4 and 8 TC entries of W[k] in runs of 8
+// (no bank conflicts), and each thread does TR TC multiply-adds per TR + TC
+// shared loads at fixed offsets from one address per k.  TR x TC is set by
+// the register budget of the calling kernel; out of line, so that the tile
+// gets the kernel's whole register budget.  Rows and columns past msz are
+// computed from the panel buffers' padding and never stored.
+template <typename T, int TR, int TC>
+__device__ __noinline__ void trailing_update(T* A, int msz, int cend, int K,
+                                             const T* __restrict__ Lp, const T* __restrict__ W,
+                                             int ldw) {
+  constexpr int WR = 4 * TR, WC = 8 * TC;
+  static_assert(WR + WC <= PANEL_PAD, "panel buffers padded for the warp tile");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ty = lane >> 3, tx = lane & 7;
+  const int Tn = msz - cend;
+  if (Tn <= 0) return;
+  const int nbr = (Tn + WR - 1) / WR;
+  int blk = 0;
+  for (int bi = 0; bi < nbr; ++bi) {
+    const int nbc = ((bi + 1) * WR + WC - 1) / WC;   // blocks meeting the lower triangle
+    for (int bj = 0; bj < nbc; ++bj, ++blk) {
+      if (blk % nw != warp) continue;
+      const int r0 = cend + bi * WR + ty, c0 = cend + bj * WC + tx;
+      // rows / columns past msz (fewer than WR + WC) read the padding of the
+      // panel buffers: indeterminate values in entries never stored
+      const T* lb = Lp + r0;
+      const T* wb = W + c0;
+      // the tile's entries are loaded first, so that their latency (the
+      // triangle may be in global memory) overlaps the products
+      T cur[TR][TC], acc[TR][TC];
+#pragma unroll
+      for (int u = 0; u < TR; ++u)
+#pragma unroll
+        for (int v = 0; v < TC; ++v) {
+          const int r = r0 + 4 * u, c = c0 + 8 * v;
+          cur[u][v] = (r < msz && c <= r) ? A[tri_at(r, c)] : T(0);
+          acc[u][v] = T(0);
+        }
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        const T* lk = lb + k * ldw;
+        const T* wk = wb + k * ldw;
+        T lr[TR], uc[TC];
+#pragma unroll
+        for (int u = 0; u < TR; ++u) lr[u] = lk[4 * u];
+#pragma unroll
+        for (int v = 0; v < TC; ++v) uc[v] = wk[8 * v];
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+          for (int v = 0; v < TC; ++v) acc[u][v] = fma(lr[u], uc[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < TR; ++u) {
+        const int r = r0 + 4 * u;
+        if (r >= msz) continue;
+#pragma unroll
+        for (int v = 0; v < TC; ++v) {
+          const int c = c0 + 8 * v;
+          if (c <= r) A[tri_at(r, c)] = cur[u][v] - acc[u][v];
+        }
+      }
+    }
+  }
+}
+
+
 // Eliminate the first npairs (state, multiplier) pairs of the symmetric msz x
 // msz matrix A, stored as a packed lower triangle (shared or global memory),
 // blocked right-looking: pairs are taken in panels of PB.  A panel's 2 PB
 // columns (rows >= the panel) are copied into W[j][r] (leading dimension
-// ldw = msz | 1).  One warp eliminates the panel's pairs on its own 2 PB rows
+// ldw = panel_ld(msz)).  One warp eliminates the panel's pairs on its own 2 PB rows
 // (the diagonal block), recording each pair's pivot inverse; then every
 // thread replays the same eliminations on the rows below, one row at a time
 // in registers (a row's multipliers depend only on the diagonal block), with
 // no barrier between pairs; then the trailing matrix receives one rank-2PB
-// update, in 4 x 4 register tiles, from the multipliers Lp[j][r] and the
-// unscaled columns W.  Every entry sees the arithmetic, in the order, of the
+// update, in register tiles of TR x TC (4 x 4 per thread at a time for TR = 0),
+// from the multipliers Lp[j][r] and the unscaled columns W.  Every entry sees the arithmetic, in the order, of the
 // pair-by-pair elimination: the pivot inverse ia = d / det, ib = -b / det,
 // id = a / det; multipliers l0 = x0 ia + x1 ib, l1 = x0 ib + x1 id; the
 // panel's remaining columns updated pair by pair; trailing entries by the sum
-// over the panel's 2 PB columns in ascending order, subtracted once.
+// over the panel's 2 PB columns in ascending order, subtracted once
+// (trailing_update for TR x TC > 0, trailing_update_tiles4 for TR = 0).
 // L columns go to Lout[c * lds + r] (rows r > pair), pivots (a, b, d) to
 // Dout[3 q]; pivot inertia is counted by thread 0.  The trailing block (rows
 // and columns >= 2 npairs) is left in A.
 // PB is 8 for blocks held in shared memory and 16 for blocks in the global
 // slab (half the trailing passes over global memory, twice the arithmetic per
 // entry read and written).
-__host__ __device__ inline int panel_ld(int msz) { return msz | 1; }
-
-template <typename T, int PB>
+template <typename T, int PB, int TR, int TC>
 __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__ Lout, int lds,
                                       T* __restrict__ Dout, T* Lp, T* W, int& pos, int& neg,
                                       int& zero) {
@@ -152,53 +291,10 @@ __device__ void pair_eliminate_packed(T* A, int msz, int npairs, T* __restrict__
     }
     __syncthreads();
     // trailing rank-K update of rows / columns >= cend (lower part)
-    const int Tn = msz - cend;
-    if (Tn > 0) {
-      const int ntr = (Tn + 3) >> 2;
-      const int ntiles = ntr * (ntr + 1) / 2;
-      for (int t = tid; t < ntiles; t += nt) {
-        int ti, tj;
-        tri_tile(t, ti, tj);
-        const int r0 = cend + 4 * ti, cb = cend + 4 * tj;
-        // the tile's entries are loaded first, so that their latency (the
-        // triangle may be in global memory) overlaps the products below
-        T cur[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int r = r0 + u, c = cb + v;
-            cur[u][v] = (r < msz && c <= r) ? A[tri_at(r, c)] : T(0);
-          }
-        T acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-        for (int k = 0; k < K; ++k) {
-          T lr[4], uc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            lr[u] = (r0 + u < msz) ? Lp[k * ldw + r0 + u] : T(0);
-            uc[u] = (cb + u < msz) ? W[k * ldw + cb + u] : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(lr[u], uc[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = r0 + u;
-          if (r >= msz) continue;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int c = cb + v;
-            if (c <= r) A[tri_at(r, c)] = cur[u][v] - acc[u][v];
-          }
-        }
-      }
-    }
+    if constexpr (TR == 0)
+      trailing_update_tiles4<T>(A, msz, cend, K, Lp, W, ldw);
+    else
+      trailing_update<T, TR, TC>(A, msz, cend, K, Lp, W, ldw);
     __syncthreads();
   }
 }
@@ -223,14 +319,14 @@ __host__ __device__ inline size_t big_panel_elems(int msz) {
 }
 // pair_eliminate_packed with PB = pb (8, or 16 for a block in the global slab,
 // whose panel buffers are sized for 16)
-template <typename T>
+template <typename T, int TR, int TC>
 __device__ inline void pair_eliminate_big(T* A, int msz, int npairs, T* __restrict__ Lout,
                                           int lds, T* __restrict__ Dout, T* Lp, T* W, int& pos,
                                           int& neg, int& zero, int pb) {
   if (pb == 16)
-    pair_eliminate_packed<T, 16>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
+    pair_eliminate_packed<T, 16, TR, TC>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
   else
-    pair_eliminate_packed<T, 8>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
+    pair_eliminate_packed<T, 8, TR, TC>(A, msz, npairs, Lout, lds, Dout, Lp, W, pos, neg, zero);
 }
 template <typename T>
 __host__ __device__ inline bool panel_in_global(int msz) {
@@ -279,8 +375,9 @@ __device__ __noinline__ void gauss_chain_out(const DevProb& P, const DevFactor<T
 // block, eliminate the K n interior pairs, write L, pivots, the 2n x 2n chain
 // block, its border, the p x p Schur contribution and the coupling (Radau:
 // -I; Gauss: gauss_chain_out).  For blocks above the register-tile limit
-// (elem_factor_rt below).
-template <typename T>
+// (elem_factor_rt below).  TR x TC: the trailing update's register tile
+// (trailing_update), set by the calling kernel's register budget.
+template <typename T, int TR, int TC>
 __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                                 const double* __restrict__ sigma, double dw, double dc,
                                 const DevFactor<T>& F, int e, const BigPlace<T>& pl, int pb) {
@@ -298,7 +395,7 @@ __device__ void elem_factor_big(const DevProb& P, const DevEval& E,
                   E.Wobj + (size_t)e * npt * npt * n,
                   sigma ? sigma + (size_t)e * npt * n : nullptr, dw, dc, A);
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_big<T>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
+  pair_eliminate_big<T, TR, TC>(A, ext, nint, F.Lel + (size_t)e * (2 * nint) * ext, ext,
                         F.Del + (size_t)e * nint * 3, pl.Lp, pl.W, pos, neg, zero, pb);
   if (tid == 0) {
     F.inert[e * 3 + 0] = pos; F.inert[e * 3 + 1] = neg; F.inert[e * 3 + 2] = zero;
@@ -340,7 +437,8 @@ k_elem_factor(DevProb P, DevEval E, const double* __restrict__ sigma, double dw,
   extern __shared__ unsigned char smraw[];
   const BigPlace<T> pl = big_place<T>(smraw, F.work, P.ext, use_smem != 0);
   for (int e = blockIdx.x; e < P.N; e += gridDim.x)
-    elem_factor_big<T>(P, E, sigma, dw, dc, F, e, pl, use_smem ? 8 : slab_pb);
+    elem_factor_big<T, 8, sizeof(T) == 4 ? 8 : 4>(P, E, sigma, dw, dc, F, e, pl,
+                                                  use_smem ? 8 : slab_pb);
 }
 
 // ---- 1'. pair elimination with the block held in registers -------------------------
@@ -911,7 +1009,7 @@ k_elem_factor_rt(DevProb P, DevEval E, const double* __restrict__ sigma, double 
 // Kept out of line: inside the cooperative kernel (80 registers per thread for
 // the latency-bound register-tiled reduction blocks) its register demand would
 // otherwise shape the whole kernel.
-template <typename T>
+template <typename T, int TR, int TC>
 __device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>& F, int stride,
                                             int final_level, int bi, const BigPlace<T> pl,
                                             int pb) {
@@ -943,7 +1041,7 @@ __device__ __noinline__ void bcr_factor_big(const DevProb& P, const DevFactor<T>
     }
   __syncthreads();
   int pos = 0, neg = 0, zero = 0;
-  pair_eliminate_big<T>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
+  pair_eliminate_big<T, TR, TC>(A, bext, n, F.Lb + (size_t)i * n2 * bext, bext,
                         F.Db + (size_t)i * n * 3, pl.Lp, pl.W, pos, neg, zero, pb);
   if (tid == 0) {
     int* in = F.inert + (size_t)(N + i) * 3;
@@ -1140,7 +1238,8 @@ k_bcr_factor(DevProb P, DevFactor<T> F, int stride, int final_level, int use_sme
   } else {
     const BigPlace<T> pl = big_place<T>(smraw, F.work, P.bext, use_smem != 0);
     for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x)
-      bcr_factor_big<T>(P, F, stride, final_level, bi, pl, use_smem ? 8 : slab_pb);
+      bcr_factor_big<T, 8, sizeof(T) == 4 ? 8 : 4>(P, F, stride, final_level, bi, pl,
+                                                    use_smem ? 8 : slab_pb);
   }
 }
 
@@ -1747,9 +1846,12 @@ k_elem_factor_rt_b(const DevInst* __restrict__ insts, const int* __restrict__ ac
 // above the register-tile limit (without flag 4): elements of the work list
 // taken in turn by the CUDA blocks of the grid (at most one global slab per
 // CUDA block), block storage in shared memory (flag 1) or in the slab.
-// BS threads per block (256 or 512: Schedule::big_threads).
+// BS threads per block (Schedule::big_threads): 512 with one block per SM, or
+// 256 compiled for two blocks per SM (128 registers per thread), so that where
+// the shared memory allows, two elements are condensed on an SM at once and
+// one block's panel phases overlap the other's trailing update.
 template <typename T, int BS>
-__global__ void __launch_bounds__(BS, 1)
+__global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
 k_elem_factor_big_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
                     const int* __restrict__ pre_elem, const InstParams* __restrict__ prm,
                     const int* __restrict__ flags, int slab_pb) {
@@ -1761,15 +1863,20 @@ k_elem_factor_big_b(const DevInst* __restrict__ insts, const int* __restrict__ a
     const DevFactor<T>& F = inst_factor<T>(I);
     const bool full = (flags[k] & 1) != 0;
     const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.ext, full);
-    elem_factor_big<T>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl,
-                       full ? 8 : slab_pb);
+    // trailing tiles: 8 x 4 (FP32) or 8 x 2 (FP64) within 128 registers per thread
+    constexpr int TC = sizeof(T) == 4 ? 4 : 2;
+    elem_factor_big<T, 8, TC>(I.P, I.E, I.sigma, prm[k].dw, prm[k].dc, F, t - pre_elem[k], pl,
+                              full ? 8 : slab_pb);
   }
 }
 
 // FP32: three blocks per SM (more reduction blocks in flight; the levels are
-// latency bound)
-template <typename T, int BT>
-__global__ void __launch_bounds__(FBS, sizeof(T) == 4 ? 3 : 1)
+// latency bound), unless WIDE: when the reduction blocks of the batch need so
+// much shared memory that one block per SM is all that fits, the kernel is
+// compiled for one block per SM and its large blocks get warp-blocked register
+// tiles (same arithmetic per entry).
+template <typename T, int BT, int WIDE>
+__global__ void __launch_bounds__(FBS, (sizeof(T) == 4 && !WIDE) ? 3 : 1)
 k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A,
            const int* __restrict__ pre_elem, const int* __restrict__ pre_lv, int maxL,
            const int* __restrict__ pre_cs, const InstParams* __restrict__ prm,
@@ -1836,8 +1943,11 @@ k_factor_b(const DevInst* __restrict__ insts, const int* __restrict__ act, int A
       const bool full = (flags[k] & 2) != 0;
       const BigPlace<T> pl = big_place<T>(smraw, F.work, I.P.bext, full);
       const int pb = full ? 8 : slab_pb;
-      if (fin) bcr_factor_big<T>(I.P, F, 1, 1, 0, pl, pb);
-      else bcr_factor_big<T>(I.P, F, 1 << lv, 0, t - pre[k], pl, pb);
+      // trailing tiles: warp-blocked 8 x 4 when the kernel runs one block per
+      // SM (WIDE), else the 4 x 4 tiles that fit 80 registers per thread
+      constexpr int TR = WIDE ? 8 : 0, TC = WIDE ? 4 : 0;
+      if (fin) bcr_factor_big<T, TR, TC>(I.P, F, 1, 1, 0, pl, pb);
+      else bcr_factor_big<T, TR, TC>(I.P, F, 1 << lv, 0, t - pre[k], pl, pb);
     }
     grid_barrier(gb, ep);
   }
@@ -2202,7 +2312,16 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
     if (e != cudaSuccess) return e;
   }
   if (!(parts & 2)) return cudaSuccess;
-  auto kern = bcr_tpt == 1 ? k_factor_b<T, 1> : bcr_tpt == 2 ? k_factor_b<T, 2> : k_factor_b<T, 0>;
+  // one block per SM is all that fits when smem exceeds a third of an SM's
+  // shared memory: then the kernel variant compiled for one block per SM
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const bool wide = sizeof(T) == 4 && bcr_full && 3 * (smem + 1024) > (size_t)smem_sm;
+  auto kern = wide ? (bcr_tpt == 1 ? k_factor_b<T, 1, 1>
+                      : bcr_tpt == 2 ? k_factor_b<T, 2, 1> : k_factor_b<T, 0, 1>)
+                   : (bcr_tpt == 1 ? k_factor_b<T, 1, 0>
+                      : bcr_tpt == 2 ? k_factor_b<T, 2, 0> : k_factor_b<T, 0, 0>);
   opt_in_smem(kern, smem);
   int grid = coop_grid(kern, FBS, smem, grid_cap);
   if (grid < 1) return cudaErrorInvalidConfiguration;

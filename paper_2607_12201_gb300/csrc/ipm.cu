@@ -127,17 +127,28 @@ __device__ inline double end_state(const DevProb& P, const double* z0, const dou
 // max|dZ| <= 1e-12 max(1, max|Z|) (at most 30 iterations); an element whose
 // iteration fails keeps the constant guess.  The residual, the update and
 // the stopping test are FP64; the Newton correction solves the Jacobian
-// system by FP32 LU with partial pivoting (an inexact Newton step whose
+// system by an FP32 LU with partial pivoting (an inexact Newton step whose
 // error the FP64 residual of the next iteration corrects), so the sweep
 // converges to the same FP64 collocation solution.  One block of SWEEP_BS
-// threads; the FP32 augmented matrix [J | G] sits in shared memory, or in
-// gwork when Kn is too large.
+// threads.  The LU carries the residual as an extra column (so the forward
+// substitution happens during the elimination) and runs with two barriers
+// per column: warp 0 picks the pivot among a compact list of the rows not yet
+// pivoted (rows are exchanged only in that list), then the block updates
+// those rows, one warp per row and the lanes along the columns.  The back
+// substitution runs on warp 0.  The FP32 matrix [J | G] sits in shared
+// memory, or in gwork when Kn is too large.
 constexpr int SWEEP_MAXIT = 30;
 constexpr int SWEEP_BS = 256;
+
+// Bytes of sweep_cta's dynamic shared memory before the matrix.
+__host__ __device__ inline size_t sweep_cta_vec_bytes(const DevProb& P) {
+  const size_t dim = P.K * (size_t)P.n;
+  return sizeof(double) * ((size_t)P.r * (1 + 3 * P.K) + P.n + 2 * dim) +
+         sizeof(float) * dim + sizeof(int) * 2 * dim;
+}
+
 __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
                           float* __restrict__ gwork, double* sm) {
-  __shared__ int s_piv;
-  __shared__ float s_inv;
   __shared__ double s_red[SWEEP_BS];
   __shared__ int s_flag;
   const int n = P.n, r = P.r, K = P.K, dim = K * n, ldj = dim + 1;
@@ -148,8 +159,11 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
   double* db = da + K * r;         // [K][r]
   double* z0 = db + K * r;         // [n]
   double* Z = z0 + n;              // [Kn]
-  double* dZ = Z + dim;            // [Kn]
-  float* Jm = gwork ? gwork : reinterpret_cast<float*>(dZ + dim);  // [dim][dim+1]
+  double* dZ = Z + dim;            // [Kn]  Newton correction
+  float* inv = reinterpret_cast<float*>(dZ + dim);    // [Kn]  1 / U[c][c]
+  int* perm = reinterpret_cast<int*>(inv + dim);      // [Kn]  row pivoted at step c
+  int* rem = perm + dim;           // [Kn]  rows not yet pivoted (first dim - c)
+  float* Jm = gwork ? gwork : reinterpret_cast<float*>(rem + dim);  // [dim][dim+1]
   const size_t nz = (size_t)P.N * P.np * n;
   int nfail = 0;
   for (int i = 0; i < P.N; ++i) {
@@ -176,7 +190,8 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
         else { const double zb = Z[k * n + b]; mon[idx] = za * zb; da[idx] = zb; db[idx] = za; }
       }
       __syncthreads();
-      // Jacobian entries D[k][j] delta_st - delta_kj h df_s/dz_t, and G (FP64)
+      // Jacobian entries D[k][j] delta_st - delta_kj h df_s/dz_t (FP32) and the
+      // residual G (FP64, rounded to FP32 in column dim)
       for (int idx = tid; idx < dim * dim; idx += SWEEP_BS) {
         const int row = idx / dim, col = idx - row * dim;
         const int k = row / n + 1, s = row - (k - 1) * n;
@@ -205,60 +220,65 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
         for (int e = P.nu_ptr[s]; e < P.nu_ptr[s + 1]; ++e)
           f += P.nu_v[e] * kr[P.nu_r[e]] * mon[(k - 1) * r + P.nu_r[e]];
         g -= P.h * f;
-        dZ[row] = g;
         Jm[(size_t)row * ldj + dim] = (float)g;
+        rem[row] = row;
       }
       if (tid == 0) s_flag = 0;
       __syncthreads();
-      // FP32 LU with partial pivoting of [J | G]
+      // FP32 LU with partial pivoting of [J | G]; L[r][c] = Jm[r][c] inv[c]
+      // (column c of a row is not updated after step c)
       for (int c = 0; c < dim; ++c) {
+        const int nrem = dim - c;
         if (warp == 0) {
           float best = -1.f;
-          int bidx = dim;
-          for (int rr = c + lane; rr < dim; rr += 32) {
+          int bpos = nrem, brow = dim;
+          for (int q = lane; q < nrem; q += 32) {
+            const int rr = rem[q];
             const float v = fabsf(Jm[(size_t)rr * ldj + c]);
-            if (v > best) { best = v; bidx = rr; }
+            if (v > best || (v == best && rr < brow)) { best = v; bpos = q; brow = rr; }
           }
           for (int o = 16; o > 0; o >>= 1) {
             const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+            const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+            const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+            if (ob > best || (ob == best && orow < brow)) { best = ob; bpos = op; brow = orow; }
           }
           if (lane == 0) {
-            s_piv = bidx;
-            if (!(best > 0.f) || !isfinite(best)) s_flag = 1;
+            if (!(best > 0.f) || !isfinite(best)) {
+              s_flag = 1;
+            } else {
+              perm[c] = brow;
+              inv[c] = 1.f / Jm[(size_t)brow * ldj + c];
+              rem[bpos] = rem[nrem - 1];   // the pivot row leaves the list
+            }
           }
         }
         __syncthreads();
         if (s_flag) break;
-        const int piv = s_piv;
-        if (piv != c)
-          for (int cc = c + tid; cc <= dim; cc += SWEEP_BS) {
-            const float t0 = Jm[(size_t)c * ldj + cc];
-            Jm[(size_t)c * ldj + cc] = Jm[(size_t)piv * ldj + cc];
-            Jm[(size_t)piv * ldj + cc] = t0;
-          }
-        __syncthreads();
-        if (tid == 0) s_inv = 1.f / Jm[(size_t)c * ldj + c];
-        __syncthreads();
-        const float inv = s_inv;
-        const int w = dim - c;   // columns c+1..dim
-        for (int idx = tid; idx < (dim - c - 1) * w; idx += SWEEP_BS) {
-          const int rr = c + 1 + idx / w, cc = c + 1 + idx % w;
-          Jm[(size_t)rr * ldj + cc] -= (Jm[(size_t)rr * ldj + c] * inv) * Jm[(size_t)c * ldj + cc];
+        const int piv = perm[c];
+        const float ic = inv[c];
+        const float* prow = Jm + (size_t)piv * ldj;
+        for (int q = warp; q < nrem - 1; q += SWEEP_BS / 32) {
+          float* row = Jm + (size_t)rem[q] * ldj;
+          const float m = row[c] * ic;
+          for (int cc = c + 1 + lane; cc <= dim; cc += 32) row[cc] -= m * prow[cc];
         }
         __syncthreads();
       }
       if (s_flag) break;
-      // back substitution U dZ = g (FP32), columns eliminated from the right
-      for (int c = dim - 1; c >= 0; --c) {
-        if (tid == 0) s_inv = Jm[(size_t)c * ldj + dim] / Jm[(size_t)c * ldj + c];
-        __syncthreads();
-        const float xc = s_inv;
-        for (int rr = tid; rr < c; rr += SWEEP_BS) Jm[(size_t)rr * ldj + dim] -= Jm[(size_t)rr * ldj + c] * xc;
-        if (tid == 0) dZ[c] = (double)xc;
-        __syncthreads();
+      // back substitution U dZ = y on warp 0 (U row c is row perm[c])
+      if (warp == 0) {
+        for (int c = dim - 1; c >= 0; --c) {
+          const float xc = Jm[(size_t)perm[c] * ldj + dim] * inv[c];
+          for (int q = lane; q < c; q += 32) {
+            float* row = Jm + (size_t)perm[q] * ldj;
+            row[dim] -= row[c] * xc;
+          }
+          if (lane == 0) dZ[c] = (double)xc;
+          __syncwarp();
+        }
       }
+      __syncthreads();
       double mdz = 0.0, mz = 0.0, bad = 0.0;
       for (int t = tid; t < dim; t += SWEEP_BS) {
         Z[t] -= dZ[t];
@@ -513,7 +533,7 @@ __global__ void __launch_bounds__(SWEEP_BS) k_sweep_cta_b(const DevInst* __restr
 
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem) {
   const size_t dim = P.K * (size_t)P.n;
-  size_t v = sizeof(double) * ((size_t)P.r * (1 + 3 * P.K) + P.n + 2 * dim);
+  size_t v = sweep_cta_vec_bytes(P);
   if (jm_in_smem) v += sizeof(float) * dim * (dim + 1);
   return v;
 }

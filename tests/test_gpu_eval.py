@@ -59,9 +59,23 @@ def test_eval_without_multipliers_and_nonfinite_detection(collo):
         assert e.value.status == collo.ERR_NUMERIC
 
 
-@pytest.mark.parametrize("name", ["cascade_N50", "tiny_N5", "config2_N400"])
+SWEEP_CASES = {
+    # 3n <= 32: the one-warp sweep
+    "cascade_N50": CASES["cascade_N50"], "tiny_N5": CASES["tiny_N5"],
+    "config2_N400": CASES["config2_N400"],
+    # the block sweep: its Jacobian (3n = 39, 90) in shared memory, then
+    # (3n = 210) in global memory
+    "n13_N20": lambda: W.random_network(13, 26, n_obs=4, M=20, T=5.0, N=20, seed=52,
+                                        theta0_spread=0.1),
+    "config3_N64": CASES["config3_N64"],
+    "n70_N3": lambda: W.random_network(70, 140, n_obs=4, M=12, T=3.0, N=3, seed=71,
+                                       theta0_spread=0.1),
+}
+
+
+@pytest.mark.parametrize("name", list(SWEEP_CASES))
 def test_forward_sweep_matches_oracle(collo, name):
-    inst = CASES[name]()
+    inst = SWEEP_CASES[name]()
     oprob = OProblem(inst)
     th = np.array(inst.theta0, dtype=float)
     z_ref, f_ref = forward_sweep(oprob, th)
