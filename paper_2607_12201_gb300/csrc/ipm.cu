@@ -138,7 +138,35 @@ __device__ inline double end_state(const DevProb& P, const double* z0, const dou
 // substitution runs on warp 0.  The FP32 matrix [J | G] sits in shared
 // memory, or in gwork when Kn is too large.
 constexpr int SWEEP_MAXIT = 30;
-constexpr int SWEEP_BS = 256;
+constexpr int SWEEP_BS = 1024;
+
+// Maxima of three values over a block of BS threads: shuffle trees within the
+// warps, then over the warps' maxima; two barriers.  sh: 3 (BS / 32 + 1) doubles.
+template <int BS>
+__device__ void bmax3(double& a, double& b, double& c, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = BS / 32;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
+  }
+  if (lane == 0) { sh[3 * warp] = a; sh[3 * warp + 1] = b; sh[3 * warp + 2] = c; }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < NW ? sh[3 * lane] : 0.0;
+    b = lane < NW ? sh[3 * lane + 1] : 0.0;
+    c = lane < NW ? sh[3 * lane + 2] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+      c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
+    }
+    if (lane == 0) { sh[3 * NW] = a; sh[3 * NW + 1] = b; sh[3 * NW + 2] = c; }
+  }
+  __syncthreads();
+  a = sh[3 * NW]; b = sh[3 * NW + 1]; c = sh[3 * NW + 2];
+}
 
 // Bytes of sweep_cta's dynamic shared memory before the matrix.
 __host__ __device__ inline size_t sweep_cta_vec_bytes(const DevProb& P) {
@@ -149,7 +177,7 @@ __host__ __device__ inline size_t sweep_cta_vec_bytes(const DevProb& P) {
 
 __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restrict__ fails,
                           float* __restrict__ gwork, double* sm) {
-  __shared__ double s_red[SWEEP_BS];
+  __shared__ double s_red[3 * (SWEEP_BS / 32 + 1)];
   __shared__ int s_flag;
   const int n = P.n, r = P.r, K = P.K, dim = K * n, ldj = dim + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -286,9 +314,7 @@ __device__ void sweep_cta(const DevProb& P, double* __restrict__ x, int* __restr
         mdz = fmax(mdz, fabs(dZ[t]));
         mz = fmax(mz, fabs(Z[t]));
       }
-      mdz = bmax<SWEEP_BS>(mdz, s_red);
-      mz = bmax<SWEEP_BS>(mz, s_red);
-      bad = bmax<SWEEP_BS>(bad, s_red);
+      bmax3<SWEEP_BS>(mdz, mz, bad, s_red);
       if (bad > 0) break;
       if (mdz <= 1e-12 * fmax(1.0, mz)) { ok = true; break; }
     }
