@@ -71,7 +71,9 @@ TOL = 1e-8
 # kernel over the first 64 instances of the batch at their initial points,
 # from one ncu capture of that launch (--only-phase); None until captured or
 # once the kernel changes.
-TRAFFIC_C4_64 = {}
+TRAFFIC_C4_64 = {"elem_big": 6077422592 + 15532304896,
+                 "reduction_schur": 5363395072 + 4618892288,
+                 "solve": 18268539648 + 184806400}
 
 
 def parse_args():
@@ -82,7 +84,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--slice", type=int, default=8, help="server steps per benchmark step")
-    ap.add_argument("--admit", type=int, default=16,
+    ap.add_argument("--admit", type=int, default=32,
                     help="admit waiting solves in groups of at least this many free slots")
     ap.add_argument("--budget-gib", type=float, default=180.0)
     ap.add_argument("--fp64-sample", type=int, default=8,
