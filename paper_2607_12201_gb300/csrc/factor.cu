@@ -2152,9 +2152,11 @@ cudaError_t launch_elem_factor(const DevProb& P, const DevEval& E, const double*
 }
 
 template <typename KernelT>
-static int coop_grid(KernelT kern, int threads, size_t smem, int want) {
-  // co-resident blocks per (device, kernel, threads, shared memory), cached:
-  // the query costs more host time than a launch
+static int coop_grid(KernelT kern, int threads, size_t smem, int want, int reserve = 0) {
+  // co-resident blocks per SM per (device, kernel, threads, shared memory),
+  // cached: the query costs more host time than a launch.  `reserve` SMs are
+  // left out (kernels of another stream hold them), so that the whole grid
+  // fits on the others.
   struct Key {
     int dev;
     const void* k;
@@ -2165,24 +2167,27 @@ static int coop_grid(KernelT kern, int threads, size_t smem, int want) {
     }
   };
   static std::mutex mu;
-  static std::map<Key, int> cache;
+  static std::map<Key, std::pair<int, int>> cache;   // (blocks per SM, SMs)
   int dev = 0;
   cudaGetDevice(&dev);
   const Key key{dev, (const void*)kern, threads, smem};
+  int per = -1, sms = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
-    if (it != cache.end()) return std::max(0, std::min(want, it->second));
+    if (it != cache.end()) { per = it->second.first; sms = it->second.second; }
   }
-  int sms = 0, per = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  if (per < 0) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {per, sms};
   }
-  std::lock_guard<std::mutex> lk(mu);
-  cache[key] = per * sms;
-  return std::max(0, std::min(want, per * sms));
+  const int usable = std::max(1, sms - std::max(0, reserve));
+  return std::max(0, std::min(want, per * usable));
 }
 
 template <typename T>
@@ -2285,7 +2290,7 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
                             int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
                             int big_grid, size_t big_smem, int bcr_tpt, int bcr_full, int parts,
-                            cudaStream_t st) {
+                            cudaStream_t st, int reserve) {
   if (A == 0) return cudaSuccess;
   if ((parts & 1) && rt_threads > 0 && tot_elem > 0) {
     if (rt_threads > RT_MAX_THREADS) return cudaErrorInvalidValue;
@@ -2323,7 +2328,7 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
                    : (bcr_tpt == 1 ? k_factor_b<T, 1, 0>
                       : bcr_tpt == 2 ? k_factor_b<T, 2, 0> : k_factor_b<T, 0, 0>);
   opt_in_smem(kern, smem);
-  int grid = coop_grid(kern, FBS, smem, grid_cap);
+  int grid = coop_grid(kern, FBS, smem, grid_cap, reserve);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   int slab_pb = sch.slab_pairs;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
@@ -2336,12 +2341,12 @@ template <typename T>
 cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                            const int* pre_lv, int maxL, int lsplit, const int* pre_cs, int ir,
                            int per_warp,
-                           GridBar* gb, int max_p, int grid_want, cudaStream_t st) {
+                           GridBar* gb, int max_p, int grid_want, cudaStream_t st, int reserve) {
   if (A == 0) return cudaSuccess;
   size_t smem = std::max(sizeof(T) * (size_t)per_warp * (FBS / 32),
                          sizeof(double) * (size_t)std::max(max_p, 1));
   opt_in_smem(k_solve_b<T>, smem);
-  int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want);
+  int grid = coop_grid(k_solve_b<T>, FBS, smem, grid_want, reserve);
   if (grid < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {(void*)&insts, (void*)&act, &A, (void*)&pre_elem, (void*)&pre_lv, &maxL,
                   &lsplit, (void*)&pre_cs, &ir, &per_warp, &gb};
@@ -2352,11 +2357,11 @@ cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const in
 template cudaError_t launch_factor_b<float>(const DevInst*, const int*, int, const int*,
                                             const int*, int, const int*, const InstParams*,
                                             const int*, GridBar*, size_t, int, int, size_t, int,
-                                            int, size_t, int, int, int, cudaStream_t);
+                                            int, size_t, int, int, int, cudaStream_t, int);
 template cudaError_t launch_factor_b<double>(const DevInst*, const int*, int, const int*,
                                              const int*, int, const int*, const InstParams*,
                                              const int*, GridBar*, size_t, int, int, size_t, int,
-                                             int, size_t, int, int, int, cudaStream_t);
+                                             int, size_t, int, int, int, cudaStream_t, int);
 int bcr_rt_tiles_of(const DevProb& P) { return bcr_rt_tiles(P.bext); }
 size_t elem_rt_stage_bytes(const DevProb& P, bool f32) {
   return f32 ? elem_stage_bytes<float>(P) : elem_stage_bytes<double>(P);
@@ -2370,10 +2375,10 @@ int elem_rt_threads(const DevProb& P, bool f32) {
 }
 template cudaError_t launch_solve_b<float>(const DevInst*, const int*, int, const int*, const int*,
                                            int, int, const int*, int, int, GridBar*, int, int,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template cudaError_t launch_solve_b<double>(const DevInst*, const int*, int, const int*,
                                             const int*, int, int, const int*, int, int, GridBar*,
-                                            int, int, cudaStream_t);
+                                            int, int, cudaStream_t, int);
 template size_t elem_factor_smem<float>(const DevProb&, bool);
 template size_t elem_factor_smem<double>(const DevProb&, bool);
 template size_t bcr_factor_smem<float>(const DevProb&, bool);

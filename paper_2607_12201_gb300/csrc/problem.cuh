@@ -58,7 +58,8 @@ cudaError_t launch_update_b(const DevInst* insts, const int* act, int A, const l
                             long long total, const InstParams* prm, int mode, cudaStream_t st);
 size_t sweep_smem_bytes(const DevProb& P, bool jm_in_smem);
 size_t sweep_warp_smem_bytes(const DevProb& P);
-// batched launchers (eval.cu, factor.cu)
+// batched launchers (eval.cu, factor.cu); `reserve`: SMs the cooperative
+// grids leave to kernels of another stream
 cudaError_t launch_eval_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                           int total_elems, const InstParams* prm, int xsel, int dxsel, int lsel,
                           bool deriv, size_t smem, cudaStream_t st);
@@ -71,7 +72,7 @@ cudaError_t launch_factor_b(const DevInst* insts, const int* act, int A, const i
                             const InstParams* prm, const int* flags, GridBar* gb, size_t smem,
                             int grid_cap, int rt_threads, size_t rt_smem, int tot_elem,
                             int big_grid, size_t big_smem, int bcr_tpt, int bcr_full, int parts,
-                            cudaStream_t st);
+                            cudaStream_t st, int reserve = 0);
 // Block size of the register-tiled element condensation for P (0: the
 // element does not fit it).
 int elem_rt_threads(const DevProb& P, bool f32);
@@ -86,7 +87,8 @@ template <typename T>
 cudaError_t launch_solve_b(const DevInst* insts, const int* act, int A, const int* pre_elem,
                            const int* pre_lv, int maxL, int lsplit, const int* pre_cs, int ir,
                            int per_warp,
-                           GridBar* gb, int max_p, int grid_want, cudaStream_t st);
+                           GridBar* gb, int max_p, int grid_want, cudaStream_t st,
+                           int reserve = 0);
 template <typename T>
 size_t elem_factor_smem(const DevProb& P, bool full);
 template <typename T>

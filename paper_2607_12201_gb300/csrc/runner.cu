@@ -104,7 +104,12 @@ struct Runner {
   double* d_outs = nullptr;
   double* h_outs = nullptr;
   GridBar* gbar = nullptr;
-  Plan plans[4];   // 0: all active, 1: subset, 2: sub-subset (precision split), 3: scratch
+  // 0: all active, 1: subset, 2: sub-subset (precision split), 3: scratch,
+  // 4: forward sweeps of the server's admissions on its side stream
+  Plan plans[5];
+  // SMs the cooperative factorization and solve grids leave free for the
+  // server's forward sweeps running on its side stream
+  int reserve_sms = 0;
 
   ~Runner() {
     if (d_insts) cudaFree(d_insts);
@@ -422,13 +427,15 @@ struct Runner {
                                  pl.pre_cs_s(), pl.d_prm, pl.flags(1), gbar, pl.smem_f[1],
                                  std::min(pl.cap_f[1], std::max(pl.tot_elem, pl.A)),
                                  pl.rt_threads[1], pl.rt_smem[1], pl.tot_elem, pl.big_grid[1],
-                                 pl.big_smem[1], pl.bcr_tpt, pl.bcr_full, parts, stream);
+                                 pl.big_smem[1], pl.bcr_tpt, pl.bcr_full, parts, stream,
+                                 reserve_sms);
     else
       e = launch_factor_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL,
                                   pl.pre_cs_s(), pl.d_prm, pl.flags(0), gbar, pl.smem_f[0],
                                   std::min(pl.cap_f[0], std::max(pl.tot_elem, pl.A)),
                                   pl.rt_threads[0], pl.rt_smem[0], pl.tot_elem, pl.big_grid[0],
-                                  pl.big_smem[0], pl.bcr_tpt, pl.bcr_full, parts, stream);
+                                  pl.big_smem[0], pl.bcr_tpt, pl.bcr_full, parts, stream,
+                                  reserve_sms);
     COLLO_CUDA(e);
     return COLLO_OK;
   }
@@ -440,10 +447,12 @@ struct Runner {
     const int want = std::max(pl.A, (pl.tot_elem + per - 1) / per);
     if (prec == COLLO_PRECISION_MIXED)
       e = launch_solve_b<float>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL, pl.lsplit,
-                                pl.pre_cs_r(), ir, pl.per_warp[1], gbar, pl.max_p, want, stream);
+                                pl.pre_cs_r(), ir, pl.per_warp[1], gbar, pl.max_p, want, stream,
+                                reserve_sms);
     else
       e = launch_solve_b<double>(d_insts, pl.act(), pl.A, pl.pre_elem(), pl.pre_lv(), pl.maxL, pl.lsplit,
-                                 pl.pre_cs_r(), ir, pl.per_warp[0], gbar, pl.max_p, want, stream);
+                                 pl.pre_cs_r(), ir, pl.per_warp[0], gbar, pl.max_p, want, stream,
+                                 reserve_sms);
     COLLO_CUDA(e);
     return COLLO_OK;
   }
@@ -630,21 +639,41 @@ struct IpmInst {
 };
 
 // Initial point, forward sweep and the constraint norm at x0 for new instances.
+// Initial parameters pushed into the bounds, bound duals 1, and the forward
+// sweep of the states, for the instances of plan `which` (already set), on
+// stream st.
+static collo_status ipm_begin_sweep(Runner& R, int which, const Opt& o, cudaStream_t st) {
+  const Plan& pl = R.plans[which];
+  COLLO_CUDA(launch_init_point_b(R.d_insts, pl.act(), pl.A, o.kappa1, o.kappa2, st));
+  COLLO_CUDA(launch_sweep_b(R.d_insts, pl.d_int + pl.off_sw_w, pl.n_sw_w, pl.smem_sw_w,
+                            pl.d_int + pl.off_sw_c, pl.n_sw_c, pl.smem_sw_c, st));
+  return COLLO_OK;
+}
+
+// The rest of an instance's start once its states are swept: lambda = 0, warm
+// starts, the first evaluation and the barrier parameter.
+static collo_status ipm_begin_rest(Runner& R, std::vector<IpmInst*>& ins);
+
 static collo_status ipm_begin(Runner& R, std::vector<IpmInst*>& ins) {
   if (ins.empty()) return COLLO_OK;
   std::vector<int> slots;
   for (auto* I : ins) slots.push_back(I->slot);
   collo_status s = R.set_plan(3, slots);
   if (s != COLLO_OK) return s;
-  const Plan& pl = R.plans[3];
-  const Opt& o = ins[0]->o;
-  COLLO_CUDA(launch_init_point_b(R.d_insts, pl.act(), pl.A, o.kappa1, o.kappa2, R.stream));
+  if ((s = ipm_begin_sweep(R, 3, ins[0]->o, R.stream)) != COLLO_OK) return s;
+  return ipm_begin_rest(R, ins);
+}
+
+static collo_status ipm_begin_rest(Runner& R, std::vector<IpmInst*>& ins) {
+  if (ins.empty()) return COLLO_OK;
+  std::vector<int> slots;
+  for (auto* I : ins) slots.push_back(I->slot);
+  collo_status s = R.set_plan(3, slots);
+  if (s != COLLO_OK) return s;
   s = R.set_params(3, [&](int, int, InstParams& ip) { ip.alpha = 0.0; });
   if (s != COLLO_OK) return s;
   s = R.update(3, 2 /* lambda = 0 */);
   if (s != COLLO_OK) return s;
-  COLLO_CUDA(launch_sweep_b(R.d_insts, pl.d_int + pl.off_sw_w, pl.n_sw_w, pl.smem_sw_w,
-                            pl.d_int + pl.off_sw_c, pl.n_sw_c, pl.smem_sw_c, R.stream));
   // warm starts: the given states and multipliers replace the sweep's (theta
   // was pushed into its bounds from the start's values by the initial point)
   for (auto* I : ins) {
@@ -1180,7 +1209,17 @@ struct collo_server {
   int admit_min = 1;                  // admit when this many slots are free (or none is busy)
   std::map<long long, Job*> jobs;
   std::mutex mu;
+  // Admitted jobs whose forward sweeps run on the side stream while the
+  // other jobs keep stepping; they join the Newton steps once side_ev has
+  // completed.  One such group at a time (it owns plan 4).
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_ev = nullptr;      // end of the group's sweeps
+  cudaEvent_t main_ev = nullptr;      // the group's set-up on the main stream
+  std::vector<Job*> sweeping;
   ~collo_server() {
+    if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); }
+    if (side_ev) cudaEventDestroy(side_ev);
+    if (main_ev) cudaEventDestroy(main_ev);
     for (auto& kv : jobs) delete kv.second;
   }
 };
@@ -1360,6 +1399,9 @@ collo_status collo_server_create(int max_slots, int64_t budget_bytes, const coll
   std::unique_ptr<collo_server> sv(new collo_server());
   collo_status s = sv->R.init(max_slots, device, nullptr);
   if (s != COLLO_OK) return s;
+  COLLO_CUDA(cudaStreamCreateWithFlags(&sv->side, cudaStreamNonBlocking));
+  COLLO_CUDA(cudaEventCreateWithFlags(&sv->side_ev, cudaEventDisableTiming));
+  COLLO_CUDA(cudaEventCreateWithFlags(&sv->main_ev, cudaEventDisableTiming));
   sv->o = make_opt(opts);
   sv->budget = budget_bytes;
   sv->slots.assign(max_slots, nullptr);
@@ -1401,17 +1443,33 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
   COLLO_CUDA(cudaSetDevice(sv->R.device));
   Runner& R = sv->R;
   collo_status s;
-  // admit waiting jobs into free slots within the device-memory budget, in
-  // groups of at least admit_min (initialising a group costs one forward
-  // sweep of the longest horizon, whatever the group's size).  A job's
-  // footprint is its problem's arrays plus every factorization store the
-  // solve allocates (counted before they exist); the stores are allocated at
-  // admission and freed when the job retires.  Jobs are admitted in
-  // submission order; one larger than the whole budget fails with OOM.
+  // Jobs whose forward sweeps (side stream) have finished join the Newton
+  // steps: their start is completed on the main stream after the sweeps.
   std::vector<IpmInst*> fresh;
+  if (!sv->sweeping.empty()) {
+    const cudaError_t q = cudaEventQuery(sv->side_ev);
+    if (q != cudaSuccess && q != cudaErrorNotReady) COLLO_CUDA(q);
+    if (q == cudaSuccess) {
+      COLLO_CUDA(cudaStreamWaitEvent(R.stream, sv->side_ev, 0));
+      for (auto* j : sv->sweeping) fresh.push_back(&j->I);
+      sv->sweeping.clear();
+      R.reserve_sms = 0;
+    }
+  }
+  // admit waiting jobs into free slots within the device-memory budget, in
+  // groups of at least admit_min (a group's forward sweeps run one block per
+  // job on the side stream, beside the other jobs' Newton steps, whose
+  // cooperative grids leave that many SMs free meanwhile; one group at a
+  // time).  A job's footprint is its problem's arrays plus every
+  // factorization store the solve allocates (counted before they exist); the
+  // stores are allocated at admission and freed when the job retires.  Jobs
+  // are admitted in submission order; one larger than the whole budget fails
+  // with OOM.
+  std::vector<collo_server::Job*> group;
   int n_free = 0, n_busy = 0;
   for (auto* j : sv->slots) (j ? n_busy : n_free)++;
-  const bool admit = n_busy == 0 || n_free >= std::min(sv->admit_min, (int)sv->slots.size());
+  const bool admit = sv->sweeping.empty() &&
+                     (n_busy == 0 || n_free >= std::min(sv->admit_min, (int)sv->slots.size()));
   while (admit && !sv->waiting.empty()) {
     auto* j = sv->waiting.front();
     int slot = -1;
@@ -1435,17 +1493,42 @@ collo_status collo_server_step(collo_server* sv, int* n_active, int* n_waiting) 
     sv->slots[slot] = j;
     sv->active_bytes += j->bytes;
     sv->peak_bytes = std::max(sv->peak_bytes, sv->active_bytes);
-    fresh.push_back(&j->I);
+    group.push_back(j);
+  }
+  if (!group.empty()) {
+    ProfClock prof(R.stream);
+    prof.mark(PF_ADMIT);
+    prof.round(PF_ADMIT);
+    std::vector<int> gs;
+    for (auto* j : group) gs.push_back(j->slot);
+    if ((s = R.set_plan(4, gs)) != COLLO_OK) return s;
+    if (n_busy == 0) {
+      // nothing else to run: sweep on the main stream and start at once
+      if ((s = ipm_begin_sweep(R, 4, sv->o, R.stream)) != COLLO_OK) return s;
+      for (auto* j : group) fresh.push_back(&j->I);
+    } else {
+      // the plan upload and the jobs' set-up precede the sweeps
+      COLLO_CUDA(cudaEventRecord(sv->main_ev, R.stream));
+      COLLO_CUDA(cudaStreamWaitEvent(sv->side, sv->main_ev, 0));
+      if ((s = ipm_begin_sweep(R, 4, sv->o, sv->side)) != COLLO_OK) return s;
+      COLLO_CUDA(cudaEventRecord(sv->side_ev, sv->side));
+      sv->sweeping = group;
+      R.reserve_sms = (int)group.size();   // one block per job's sweep
+    }
   }
   {
     ProfClock prof(R.stream);
-    if (!fresh.empty()) { prof.mark(PF_ADMIT); prof.round(PF_ADMIT); }
-    if ((s = ipm_begin(R, fresh)) != COLLO_OK) return s;
+    if (!fresh.empty()) { prof.mark(PF_ADMIT); }
+    if ((s = ipm_begin_rest(R, fresh)) != COLLO_OK) return s;
   }
   std::vector<IpmInst*> act;
   long long its0 = 0, its1 = 0;
-  for (auto* j : sv->slots)
-    if (j) { act.push_back(&j->I); its0 += j->I.it; }
+  for (auto* j : sv->slots) {
+    if (!j) continue;
+    bool sweeping = false;
+    for (auto* w : sv->sweeping) sweeping = sweeping || w == j;
+    if (!sweeping) { act.push_back(&j->I); its0 += j->I.it; }
+  }
   if ((s = ipm_iteration(R, act)) != COLLO_OK) return s;
   for (auto* I : act) its1 += I->it;
   sv->newton_steps += its1 - its0;
