@@ -386,6 +386,12 @@ collo_status collo_batch_time_phase(collo_problem* const* probs, int count, int 
  * slots while the device memory held by admitted problems stays within
  * budget_bytes (0: no limit), initialises them, advances every admitted
  * problem by one Newton step in batched launches, and retires finished ones.
+ * The forward sweeps (initial states) of an admitted group run on a second
+ * stream of the server beside the other problems' Newton steps, one block per
+ * problem (meanwhile the cooperative kernels of the steps leave that many SMs
+ * free); the group takes its first Newton step at the first collo_server_step
+ * after its sweeps have finished.  One group sweeps at a time; into an idle
+ * server a group is swept on the main stream at once.
  * A problem's footprint is collo_problem_solve_bytes: its factorization
  * stores are allocated when it is admitted and freed (stream-ordered) when it
  * retires, so a retired problem is left unfactored; a problem larger than the
@@ -410,11 +416,13 @@ collo_status collo_server_submit(collo_server* server, collo_problem* prob, cons
 collo_status collo_server_step(collo_server* server, int* n_active, int* n_waiting);
 collo_status collo_server_poll(collo_server* server, long long ticket, collo_result* result);
 /* Admission grouping: collo_server_step admits waiting problems only when at
- * least min_free_slots slots are free (or no slot is busy); default 1.  Each
- * admission round runs the new problems' forward sweeps before the step, so
- * grouping trades idle slots for fewer rounds.  INVALID_ARG if < 1. */
+ * least min_free_slots slots are free (or no slot is busy) and no earlier
+ * group is still sweeping; default 1.  Each group's forward sweeps take as
+ * long as its slowest problem's, so grouping trades idle slots for fewer
+ * rounds.  INVALID_ARG if < 1. */
 collo_status collo_server_set_admission(collo_server* server, int min_free_slots);
-/* The CUDA stream (cudaStream_t) all of the server's work is queued on. */
+/* The CUDA stream (cudaStream_t) the server's Newton steps are queued on
+ * (the forward sweeps of admitted groups run on a second stream of its own). */
 void* collo_server_stream(collo_server* server);
 /* Device bytes held by the admitted problems now and the most held at once
  * since the server was created (either pointer may be NULL). */
