@@ -19,6 +19,12 @@ Plain, slow, obviously-correct restatement of the paper's method:
 * ``ipm``    - a filter line-search primal-dual interior-point method in the
   form of Waechter & Biegler (2006), the algorithm family of the solver the
   paper uses (Introduction: "a filter line-search interior point solver").
+* ``lifted`` - the relaxed-equality ("lifted") form of the same method: slacks
+  for the relaxed constraints, steps from the condensed positive-definite
+  primal system W + Sigma + J^T D J by Cholesky (paper Section "Optimization
+  framework configurations": the LiftedKKT form), pinned by brute-force
+  solves of the whole primal-dual system, eigenvalue inertia and the limit of
+  a vanishing relaxation.
 * ``init``   - the initial state guess: an element-by-element collocation
   forward sweep at theta0 (paper: initial guesses from a forward solve at
   the nominal parameters, Section "Optimization framework configurations").
