@@ -107,6 +107,8 @@ def parse_args():
                          "rows, factored in the global slab)")
     ap.add_argument("--only-serve", type=int, default=0,
                     help="run this many server steps of the stream and exit (ncu launch list)")
+    ap.add_argument("--only-lifted", action="store_true",
+                    help="run the lifted vs augmented step comparison and exit")
     ap.add_argument("--phase-profile", action="store_true",
                     help="print the driver's per-phase wall time over --slice server steps")
     return ap.parse_args()
@@ -513,6 +515,7 @@ def run_ours(args):
         out.update(config2_multistart(collo, workloads, local))
         out.update(config2_multistart(collo, workloads, local, scheme="gauss"))
         out.update(poisson_stream(collo, workloads, local, budget))
+        out.update(lifted_comparison(collo, workloads, local))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(insts)
     if rank == 0:
@@ -636,6 +639,93 @@ def config2_multistart(collo, workloads, device, scheme="radau"):
                 + ("; Gauss-Legendre K = 4 collocation" if scheme == "gauss" else "")}}
 
 
+LIFTED_R = 1e-8   # relaxation of the lifted form's equalities
+
+
+def lifted_start(prob, inst, mu=0.1, r=LIFTED_R):
+    """Inputs of the lifted step at the interior-point start, from the GPU's own
+    forward sweep and evaluation: theta pushed 1e-2 into its bounds, slacks
+    s = c(x0) pushed into [-r, r], unit bound duals, lambda = 0.  Returns
+    (sigma_x, sigma_s, r_x, r_s, r_c, augmented rhs)."""
+    import numpy as np
+    lo, hi = np.asarray(inst.theta_lo, float), np.asarray(inst.theta_hi, float)
+    push = lambda v, a, b: np.minimum(np.maximum(v, a + np.minimum(1e-2 * np.maximum(1, abs(a)),
+                                                                    1e-2 * (b - a))),
+                                      b - np.minimum(1e-2 * np.maximum(1, abs(b)), 1e-2 * (b - a)))
+    th = push(np.asarray(inst.theta0, float), lo, hi)
+    x, _ = prob.initial_states(th)
+    ev = prob.eval(x, None)
+    c, grad = ev["c"], ev["grad"]
+    s = np.clip(c, -r + 2e-2 * r, r - 2e-2 * r)
+    nz = prob.n_x - prob.p
+    sl, su = th - lo, hi - th
+    sx = np.zeros(prob.n_x)
+    sx[nz:] = 1.0 / sl + 1.0 / su
+    ss = 1.0 / (s + r) + 1.0 / (r - s)
+    gphi = grad.copy()
+    gphi[nz:] += -mu / sl + mu / su
+    rx = -gphi
+    rs = -(-mu / (s + r) + mu / (r - s))
+    rc = -(c - s)
+    return sx, ss, rx, rs, rc, np.concatenate([rx, -c])
+
+
+def lifted_flops(n, p, N, K=3):
+    """Algorithmic FP64 flops of the lifted element kernel: G^T diag(d) G over
+    the element's K n + n constraint rows (lower triangle, 2 flops per row and
+    entry) plus the Cholesky of its K n interior columns (the trailing update,
+    2 flops per updated entry)."""
+    kn, me = K * n, K * n + 2 * n + p
+    rows = kn + n
+    chol = sum((me - c - 1) * (me - c) for c in range(kn))
+    return N * (rows * me * (me + 1) + chol)
+
+
+def lifted_comparison(collo, workloads, device):
+    """The lifted condensed-space step against the augmented step on the same
+    iterate: config 2 (N = 400) and config 3 (N = 2000)."""
+    peak64 = collo.alu_peak(collo.FP64)
+    out = {}
+    for key, inst in (("config2_N400", workloads.config2()),
+                      ("config3_N2000", workloads.config3())):
+        with collo.Problem(inst, device=device) as prob:
+            sx, ss, rx, rs, rc, rhs = lifted_start(prob, inst)
+            dw = 0.0
+            while not prob.lifted_factor(sx, ss, dw):
+                dw = 1e-4 if dw == 0.0 else 8.0 * dw
+            t0 = time.perf_counter()
+            dx, ds, dl, info = prob.lifted_solve(rx, rs, rc, refine_max=20, refine_tol=1e-12)
+            solve_wall = time.perf_counter() - t0
+            ms_elem = prob.time_phase(5, reps=5)
+            ms_fac = prob.time_phase(6, reps=5)
+            ms_sol = prob.time_phase(7, reps=5)
+            aug = {}
+            mu = 0.1
+            for name, prec in (("fp64", collo.FP64), ("mixed", collo.MIXED)):
+                prob.kkt_factor(sx, 0.0, 1e-8 * mu ** 0.25, precision=prec)
+                _, ainfo = prob.kkt_solve(rhs, refine_max=20, refine_tol=1e-12)
+                aug[name] = {"factor_ms": prob.time_phase(1, prec, reps=5),
+                             "solve_ms": prob.time_phase(2, prec, reps=5),
+                             "refinement_sweeps": ainfo["sweeps"]}
+        fl = lifted_flops(inst.n, inst.p, inst.N, inst.K)
+        ach = fl / (ms_elem * 1e-3) / 1e12
+        out[key] = {"lifted": {"factor_ms": ms_fac, "elem_kernel_ms": ms_elem,
+                               "solve_once_ms": ms_sol, "refinement_sweeps": info["sweeps"],
+                               "residual": info["residual"], "delta_w": dw,
+                               "solve_with_refinement_wall_ms": 1e3 * solve_wall},
+                    "augmented": aug,
+                    "elem_roofline": {"bound": "alu", "achieved": ach, "peak": peak64,
+                                      "unit": "TFLOP/s", "frac": ach / peak64,
+                                      "algorithmic_flops": fl,
+                                      "kernel": "k_lifted_elem (FP64)",
+                                      "peak_source": "collo_alu_peak FP64 FMA probe"}}
+    out["what"] = ("one Newton step at the interior-point start (slacks c(x0) in [-r, r], "
+                   f"r = {LIFTED_R:g}): lifted condensed Cholesky path (FP64) vs the augmented "
+                   "2x2-pivot path (FP64 and mixed), same problem and iterate; CUDA events "
+                   "per phase (collo_time_phase 1/2 and 5/6/7)")
+    return {"lifted_vs_augmented": out}
+
+
 def poisson_stream(collo, workloads, device, budget):
     """Requests of the serving-stream shape at their stated sizes (n log-uniform
     on [5, 100], N on [200, 5000]) arriving at 200 per second, served for a
@@ -693,8 +783,20 @@ def cpu_baseline(insts):
     t0 = time.perf_counter()
     r = oipm.solve(inst, opt=oipm.Options(max_iter=2))
     dt = time.perf_counter() - t0
+    from oracle import lifted as olifted
+    from oracle.nlp import Problem as OProblem
+    from paper_2607_12201_gb300 import workloads
+    c2 = workloads.config2()
+    op = OProblem(c2)
+    lopt = olifted.Options(relax=LIFTED_R)
+    st, _ = olifted.initial_point(op, c2.theta0, lopt)
+    t1 = time.perf_counter()
+    ev = op.evaluate(st.x, st.lam)
+    olifted.newton_direction(op, ev, st, lopt.mu_init, 0.0, lopt)
+    lifted_s = time.perf_counter() - t1
     return {"value": r.iterations / dt, "unit": "Newton steps/s", "cores": 1,
             "kind": "oracle",
+            "lifted_step_config2_N400_s": lifted_s,
             "sample": f"oracle IPM on one instance of the batch (n = {inst.n}, N = {inst.N}, "
                       f"the median by factorization work): initial point + "
                       f"{r.iterations} Newton iterations ({dt:.1f} s, numpy/scipy FP64, one BLAS "
@@ -811,7 +913,12 @@ def phase_profile(args):
 
 def main():
     args = parse_args()
-    if args.only_phase:
+    if args.only_lifted:
+        from paper_2607_12201_gb300 import build as B
+        B.build()
+        from paper_2607_12201_gb300 import collo, workloads
+        print(json.dumps(lifted_comparison(collo, workloads, 0)), flush=True)
+    elif args.only_phase:
         only_phase(args)
     elif args.only_serve:
         only_serve(args)

@@ -340,6 +340,45 @@ collo_status collo_kkt_factor(collo_problem* prob, const double* sigma, double d
 collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol,
                              int refine_max, double refine_tol, collo_solve_info* info);
 
+/* Lifted (relaxed-equality) condensed-space KKT form of the paper's solver
+ * configuration (Section "Optimization framework configurations": MadNLP's
+ * LiftedKKT; Introduction: a KKT form that factorizes without pivoting).
+ * With the equalities relaxed to -r <= c(x) <= r through slacks s, the
+ * Newton system in (dx, ds, dlam) is
+ *   [ W + diag(sigma_x) + delta_w I   0              J^T ] [dx  ]   [r_x]
+ *   [ 0                               diag(d)        -I  ] [ds  ] = [r_s]
+ *   [ J                               -I              0  ] [dlam]   [r_c]
+ * with d = sigma_s + delta_w; it condenses to the primal matrix
+ *   Kc = W + diag(sigma_x) + delta_w I + J^T diag(d) J,
+ * which is positive definite exactly when the system has the inertia
+ * (n_x + n_c, n_c, 0) an interior-point step needs.
+ *
+ * collo_lifted_factor factors Kc of the most recent collo_eval by Cholesky
+ * without pivoting, FP64 throughout: each element's interior points, then the
+ * chain of n x n blocks over the elements' first points by block cyclic
+ * reduction, then the p x p parameter block.  sigma_x [n_x] (host or device;
+ * NULL: zero), sigma_s [n_c] (host or device, the slacks' barrier diagonal,
+ * > 0).  *positive_definite (may be NULL) receives 1 when every pivot was
+ * positive, else 0 (then Kc is not positive definite, or not numerically so:
+ * raise delta_w).  The first call allocates the factorization's storage
+ * (about N (Kn + 2n + p)^2 doubles); it stays with the problem.  Returns
+ * NOT_EVALUATED before collo_eval, INVALID_ARG for a negative or non-finite
+ * delta_w, OOM when the storage cannot be allocated. */
+collo_status collo_lifted_factor(collo_problem* prob, const double* sigma_x,
+                                 const double* sigma_s, double delta_w, int* positive_definite);
+
+/* Solve the system above with the last positive-definite collo_lifted_factor
+ * of the current evaluation: dx = Kc^-1 (r_x + J^T (d r_c + r_s)),
+ * ds = J dx - r_c, dlam = d ds - r_s, refined in FP64 against the unreduced
+ * system until its residual max-norm is <= refine_tol max(1, max|b|) or
+ * refine_max sweeps.  r_x, dx: [n_x]; r_s, r_c, ds, dlam: [n_c]; host or
+ * device; outputs may not alias inputs.  info may be NULL.  Returns
+ * NOT_FACTORED without such a factorization (none, not positive definite, or
+ * made before the last evaluation), NUMERIC for a non-finite residual. */
+collo_status collo_lifted_solve(collo_problem* prob, const double* r_x, const double* r_s,
+                                const double* r_c, double* dx, double* ds, double* dlam,
+                                int refine_max, double refine_tol, collo_solve_info* info);
+
 /* Defaults: the paper's tolerances (relative KKT error 1e-6, acceptable 1e-4
  * for 15 iterations; Section "Optimization framework configurations"), 3000
  * iterations, a 3600 s wall cap, FP64 precision, refinement to 1e-10 in at
@@ -513,7 +552,12 @@ collo_status collo_initial_states(collo_problem* prob, const double* theta, doub
  *   phase 2: one solve without refinement (needs a factorization in
  *            `precision`), on the last right-hand side;
  *   phase 3: evaluation with derivatives at the solver's current iterate;
- *   phase 4: collocation forward sweep at the current theta.
+ *   phase 4: collocation forward sweep at the current theta;
+ *   phase 5: the lifted factorization's element kernel alone, phase 6 all of
+ *            its kernels, phase 7 one lifted solve without refinement on the
+ *            last right-hand side of collo_lifted_solve (each needs a
+ *            positive-definite collo_lifted_factor of the current evaluation
+ *            and leaves it intact; `precision` is ignored: FP64).
  * Returns NOT_EVALUATED / NOT_FACTORED when its input state is missing. */
 collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int reps,
                               double* ms_per_launch);

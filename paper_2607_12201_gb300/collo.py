@@ -137,6 +137,13 @@ def _load():
     lib.collo_kkt_solve.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                     C.POINTER(SolveInfo)]
     lib.collo_kkt_solve.restype = C.c_int
+    lib.collo_lifted_factor.argtypes = [P, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.POINTER(C.c_int)]
+    lib.collo_lifted_factor.restype = C.c_int
+    lib.collo_lifted_solve.argtypes = [P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                       C.POINTER(SolveInfo)]
+    lib.collo_lifted_solve.restype = C.c_int
     lib.collo_ipm_options_default.argtypes = [C.POINTER(IpmOptions)]
     lib.collo_ipm_options_default.restype = None
     lib.collo_ipm_solve.argtypes = [P, C.c_void_p, C.POINTER(IpmOptions), C.POINTER(Result)]
@@ -438,6 +445,31 @@ class Problem:
         _check(lib.collo_kkt_solve(self.h, _ptr(rhs), _ptr(sol), int(refine_max),
                                    float(refine_tol), C.byref(info)))
         return sol, dict(sweeps=info.refinement_sweeps, residual=info.residual)
+
+    def lifted_factor(self, sigma_x, sigma_s, delta_w=0.0) -> bool:
+        """Cholesky of the lifted condensed matrix of the last eval; True when
+        it is positive definite."""
+        sx = _host_vec(sigma_x, self.n_x, "sigma_x")
+        ss = _host_vec(sigma_s, self.n_c, "sigma_s")
+        if ss is None:
+            raise ValueError("sigma_s is required")
+        pd = C.c_int(0)
+        _check(lib.collo_lifted_factor(self.h, _ptr(sx), _ptr(ss), float(delta_w), C.byref(pd)))
+        return bool(pd.value)
+
+    def lifted_solve(self, r_x, r_s, r_c, refine_max: int = 10, refine_tol: float = 1e-12):
+        """(dx, ds, dlam) of the lifted system with the last lifted_factor."""
+        rx = _host_vec(r_x, self.n_x, "r_x")
+        rs = _host_vec(r_s, self.n_c, "r_s")
+        rc = _host_vec(r_c, self.n_c, "r_c")
+        if rx is None or rs is None or rc is None:
+            raise ValueError("r_x, r_s and r_c are required")
+        dx, ds, dl = np.zeros(self.n_x), np.zeros(self.n_c), np.zeros(self.n_c)
+        info = SolveInfo()
+        _check(lib.collo_lifted_solve(self.h, _ptr(rx), _ptr(rs), _ptr(rc), _ptr(dx), _ptr(ds),
+                                      _ptr(dl), int(refine_max), float(refine_tol),
+                                      C.byref(info)))
+        return dx, ds, dl, dict(sweeps=info.refinement_sweeps, residual=info.residual)
 
     # --- solver ------------------------------------------------------------------
     @staticmethod

@@ -677,6 +677,7 @@ collo_status collo_eval(collo_problem* prob, const double* x, const double* lamb
   COLLO_CUDA(cudaMemcpyAsync(prob->hscal, E.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   COLLO_CUDA(cudaStreamSynchronize(st));
   prob->evaluated = true;
+  ++prob->eval_count;
   prob->factored = -1;
   if (!std::isfinite(prob->hscal[0]) || !std::isfinite(prob->hscal[1])) {
     set_error("non-finite objective or constraint values");

@@ -159,6 +159,10 @@ struct FactorStore {
 
 struct collo_problem;
 namespace collo {
+// Storage of the relaxed-equality (lifted) condensed factorization (lifted.cu).
+struct LiftedStore;
+void lifted_free(LiftedStore* L);
+collo_status lifted_time_launch(collo_problem* pr, int which);
 // Host copies of a problem's inputs (for re-creating it on another mesh).
 struct HostInputs {
   std::vector<int> react, prod, pidx, species, observable, obs_cond;
@@ -259,6 +263,11 @@ struct collo_problem {
   double* start_x = nullptr;   // [n_x]
   double* start_lam = nullptr; // [n_c]
   double* refine_buf = nullptr;  // [N + 8] defects and their maximum
+  // evaluations with derivatives so far (a factorization records the one it used)
+  long long eval_count = 0;
+  // lifted condensed factorization (collo_lifted_factor), allocated on first use
+  collo::LiftedStore* lifted = nullptr;
+  double* lifted_gscr = nullptr;    // its element scratch when blocks exceed shared memory
   collo::DevInst inst{};            // this problem's device pointers (host copy)
   collo::Runner* self = nullptr;    // single-instance runner (batch of one)
   ~collo_problem();

@@ -71,6 +71,23 @@ collo_status collo_time_phase(collo_problem* prob, int phase, int precision, int
   if (!prob || !ms_per_launch || reps < 1) { set_error("bad argument"); return COLLO_ERR_INVALID_ARG; }
   if (!prob->evaluated) { set_error("collo_eval has not run"); return COLLO_ERR_NOT_EVALUATED; }
   COLLO_CUDA(cudaSetDevice(prob->device));
+  if (phase >= 5 && phase <= 7) {   // lifted path
+    collo_status s = lifted_time_launch(prob, phase - 5);   // warm-up, checks the state
+    if (s != COLLO_OK) return s;
+    cudaEvent_t e0, e1;
+    COLLO_CUDA(cudaEventCreate(&e0));
+    COLLO_CUDA(cudaEventCreate(&e1));
+    COLLO_CUDA(cudaEventRecord(e0, prob->stream));
+    for (int k = 0; k < reps && s == COLLO_OK; ++k) s = lifted_time_launch(prob, phase - 5);
+    COLLO_CUDA(cudaEventRecord(e1, prob->stream));
+    COLLO_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / reps;
+    return s;
+  }
   if (precision < 0) precision = prob->precision;
   collo_status s = ensure_factor_storage(prob, precision);
   if (s != COLLO_OK) return s;

@@ -730,6 +730,7 @@ static collo_status ipm_iteration(Runner& R, std::vector<IpmInst*>& ins) {
   std::vector<IpmInst*> cont;
   for (auto* I : run) {
     I->prob->evaluated = true;
+    ++I->prob->eval_count;
     const double* o = R.out(I->slot);
     I->phi = o[O_PHI];
     const double cinf = o[O_CINF];
@@ -1698,4 +1699,7 @@ void collo_server_destroy(collo_server* sv) {
 
 }  // extern "C"
 
-collo_problem::~collo_problem() { delete self; }
+collo_problem::~collo_problem() {
+  delete self;
+  collo::lifted_free(lifted);
+}
