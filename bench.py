@@ -109,6 +109,8 @@ def parse_args():
                     help="run this many server steps of the stream and exit (ncu launch list)")
     ap.add_argument("--only-lifted", action="store_true",
                     help="run the lifted vs augmented step comparison and exit")
+    ap.add_argument("--lifted-case", default="both", choices=["both", "config2", "config3"],
+                    help="--only-lifted: which configuration")
     ap.add_argument("--phase-profile", action="store_true",
                     help="print the driver's per-phase wall time over --slice server steps")
     return ap.parse_args()
@@ -670,24 +672,32 @@ def lifted_start(prob, inst, mu=0.1, r=LIFTED_R):
     return sx, ss, rx, rs, rc, np.concatenate([rx, -c])
 
 
-def lifted_flops(n, p, N, K=3):
-    """Algorithmic FP64 flops of the lifted element kernel: G^T diag(d) G over
-    the element's K n + n constraint rows (lower triangle, 2 flops per row and
-    entry) plus the Cholesky of its K n interior columns (the trailing update,
-    2 flops per updated entry)."""
+def lifted_flops(n, p, N, K=3, gauss=False):
+    """Algorithmic FP64 flops of the lifted element kernel: J^T diag(d) J as one
+    symmetric rank-1 update per constraint row over the row's nonzeros (a
+    collocation row: K other points, its node-block row of n, its p parameter
+    entries; a continuity row: 2 or K + 2 entries), 2 flops per updated
+    lower-triangle entry, plus the Cholesky of the K n interior columns (the
+    trailing update, 2 flops per updated entry)."""
     kn, me = K * n, K * n + 2 * n + p
-    rows = kn + n
+    nz_col = K + n + p
+    nz_cont = K + 2 if gauss else 2
+    rank1 = kn * nz_col * (nz_col + 1) + n * nz_cont * (nz_cont + 1)
     chol = sum((me - c - 1) * (me - c) for c in range(kn))
-    return N * (rows * me * (me + 1) + chol)
+    return N * (rank1 + chol)
 
 
-def lifted_comparison(collo, workloads, device):
+def lifted_comparison(collo, workloads, device, which="both"):
     """The lifted condensed-space step against the augmented step on the same
     iterate: config 2 (N = 400) and config 3 (N = 2000)."""
     peak64 = collo.alu_peak(collo.FP64)
     out = {}
-    for key, inst in (("config2_N400", workloads.config2()),
-                      ("config3_N2000", workloads.config3())):
+    cases = []
+    if which in ("both", "config2"):
+        cases.append(("config2_N400", workloads.config2()))
+    if which in ("both", "config3"):
+        cases.append(("config3_N2000", workloads.config3()))
+    for key, inst in cases:
         with collo.Problem(inst, device=device) as prob:
             sx, ss, rx, rs, rc, rhs = lifted_start(prob, inst)
             dw = 0.0
@@ -707,7 +717,7 @@ def lifted_comparison(collo, workloads, device):
                 aug[name] = {"factor_ms": prob.time_phase(1, prec, reps=5),
                              "solve_ms": prob.time_phase(2, prec, reps=5),
                              "refinement_sweeps": ainfo["sweeps"]}
-        fl = lifted_flops(inst.n, inst.p, inst.N, inst.K)
+        fl = lifted_flops(inst.n, inst.p, inst.N, inst.K, getattr(inst, "scheme", "") == "gauss")
         ach = fl / (ms_elem * 1e-3) / 1e12
         out[key] = {"lifted": {"factor_ms": ms_fac, "elem_kernel_ms": ms_elem,
                                "solve_once_ms": ms_sol, "refinement_sweeps": info["sweeps"],
@@ -917,7 +927,7 @@ def main():
         from paper_2607_12201_gb300 import build as B
         B.build()
         from paper_2607_12201_gb300 import collo, workloads
-        print(json.dumps(lifted_comparison(collo, workloads, 0)), flush=True)
+        print(json.dumps(lifted_comparison(collo, workloads, 0, args.lifted_case)), flush=True)
     elif args.only_phase:
         only_phase(args)
     elif args.only_serve:

@@ -361,7 +361,7 @@ collo_status collo_kkt_solve(collo_problem* prob, const double* rhs, double* sol
  * > 0).  *positive_definite (may be NULL) receives 1 when every pivot was
  * positive, else 0 (then Kc is not positive definite, or not numerically so:
  * raise delta_w).  The first call allocates the factorization's storage
- * (about N (Kn + 2n + p)^2 doubles); it stays with the problem.  Returns
+ * (about N (Kn + 2n + p)^2 / 2 doubles); it stays with the problem.  Returns
  * NOT_EVALUATED before collo_eval, INVALID_ARG for a negative or non-finite
  * delta_w, OOM when the storage cannot be allocated. */
 collo_status collo_lifted_factor(collo_problem* prob, const double* sigma_x,

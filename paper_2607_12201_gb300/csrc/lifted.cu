@@ -21,9 +21,11 @@
 // row of element i+1 couples them with z_(i+1)0.  Element i's block of Kc, in
 // the local order [interior z_i1..z_iK (Kn) | z_i0 (n) | z_(i+1)0 (n) | theta (p)],
 // holds W_i, the diagonal terms, and G_i^T diag(d) G_i over its collocation
-// rows and outgoing continuity row (the initial condition of a chain's first
-// element adds d on z_i0).  The tree of eliminations:
-//   1. each element's interior by Cholesky (one block per element), leaving
+// rows and outgoing continuity row G_i (the initial condition of a chain's
+// first element adds d on z_i0), assembled entry by entry from the rows'
+// structure and kept in packed lower storage.  The tree of eliminations:
+//   1. each element's interior by Cholesky (one block per element, in shared
+//      memory when the packed block fits, else in its global storage), leaving
 //      a Schur complement on (z_i0, z_(i+1)0, theta);
 //   2. the chain of n x n blocks over z_i0 (coupled to its successor) by block
 //      cyclic reduction with Cholesky pivots, each level one launch of
@@ -55,7 +57,7 @@ struct DevLifted {
   double dw = 0.0;
   double* sigx = nullptr;   // [n_x]
   double* d = nullptr;      // [n_c] Sigma_s + dw
-  double* blk = nullptr;    // [N][me][me] element blocks (row-major, lower triangle)
+  double* blk = nullptr;    // [N][me (me + 1) / 2] element blocks (packed lower)
   double* Dg = nullptr;     // [N][n][n] chain diagonal blocks, then their Cholesky factors
   double* Cp = nullptr;     // [N][n][n] coupling of chain block i to the next active one
   double* Xa = nullptr;     // [N][n][n] L_j^-1 (coupling to the left neighbour)
@@ -104,63 +106,106 @@ __device__ inline void local_decode(const DevProb& P, int kn, int a, int& pt, in
   else { pt = -1; s = a - kn - 2 * n; kind = 2; }
 }
 
-// Entry (a, b) of row g of G_i (its collocation rows, then its outgoing
-// continuity rows) at local column a.
-__device__ inline double g_entry(const DevProb& P, const DevEval& E, int i, int kn, int g, int a) {
-  const int n = P.n, p = P.p, K = P.K;
-  int pt, s, kind;
-  local_decode(P, kn, a, pt, s, kind);
-  if (g < kn) {
-    const int k = g / n + 1, rs = g - (k - 1) * n;
-    if (kind == 2) return E.JT[(((size_t)i * K + (k - 1)) * n + rs) * p + s];
-    if (kind == 1) return 0.0;
-    if (pt == k) {
-      double v = E.JZ[(((size_t)i * K + (k - 1)) * n + rs) * n + s];
-      if (s == rs) v += P.D[k][k];
-      return v;
-    }
-    return s == rs ? P.D[k][pt] : 0.0;
-  }
-  const int rs = g - kn;   // continuity row of element i + 1, species rs
-  if (!chain_next(P, i) || s != rs) return 0.0;
-  if (kind == 1) return 1.0;
-  if (kind == 2) return 0.0;
-  if (P.gauss) return -P.bw[pt];
-  return pt == K ? -1.0 : 0.0;
+// Packed lower-triangular storage of a symmetric block: row r holds columns
+// 0..r at tri(r).
+__host__ __device__ inline size_t tri(int r) { return (size_t)r * (r + 1) / 2; }
+
+// Coefficient of own point j in the outgoing continuity row (Eq. 2c).
+__device__ inline double cont_coef(const DevProb& P, int j) {
+  if (P.gauss) return -P.bw[j];
+  return j == P.K ? -1.0 : 0.0;
 }
 
-__device__ inline double g_weight(const DevProb& P, const double* __restrict__ d, int i, int kn,
-                                  int g) {
-  const int n = P.n;
-  if (g < kn) {
-    const int k = g / n + 1, rs = g - (k - 1) * n;
-    return d[zflat(P, i, k, rs)];
-  }
-  return chain_next(P, i) ? d[zflat(P, i + 1, 0, g - kn)] : 0.0;
-}
-
-// Entry (a, b), a >= b, of element i's block of Kc before elimination.
+// Entry (a, b), a >= b, of element i's block of Kc before elimination, from
+// the structure of its constraint rows: collocation row (k, t) has D[k][j] on
+// point j != k of species t, the node block M_k = D[k][k] I + JZ_k on point k
+// and JT_k on theta; the outgoing continuity row of species s has -b_j on the
+// element's points and 1 on the next element's z_0.  So J^T diag(d) J needs,
+// per entry, K terms and one length-n sum over the node block where both
+// columns sit on the same point.
 __device__ inline double elem_entry(const DevProb& P, const DevEval& E, const double* __restrict__ d,
                                     const double* __restrict__ sigx, double dw, int i, int kn,
-                                    const double* __restrict__ G, const double* __restrict__ gw,
-                                    int me, int a, int b) {
+                                    int a, int b) {
   const int n = P.n, np = P.np, K = P.K, p = P.p;
-  double v = 0.0;
-  for (int g = 0; g < kn + n; ++g) v += gw[g] * G[g * me + a] * G[g * me + b];
   int pa, sa, ka, pb, sb, kb;
   local_decode(P, kn, a, pa, sa, ka);
   local_decode(P, kn, b, pb, sb, kb);
+  const double* __restrict__ JZ = E.JZ + (size_t)i * K * n * n;   // [k-1][t][s]
+  const double* __restrict__ JT = E.JT + (size_t)i * K * n * p;   // [k-1][t][q]
+  const double* __restrict__ dk = d + zflat(P, i, 0, 0);         // [k][t]
+  auto M = [&](int k, int t, int c) {
+    return JZ[((size_t)(k - 1) * n + t) * n + c] + (t == c ? P.D[k][k] : 0.0);
+  };
+  double v = 0.0;
   if (ka == 0 && kb == 0) {
+    for (int k = 1; k <= K; ++k) {
+      if (pa != k && pb != k) {
+        if (sa == sb) v += P.D[k][pa] * P.D[k][pb] * dk[k * n + sa];
+      } else if (pa != k) {
+        v += P.D[k][pa] * dk[k * n + sa] * M(k, sa, sb);
+      } else if (pb != k) {
+        v += P.D[k][pb] * dk[k * n + sb] * M(k, sb, sa);
+      } else {
+        for (int t = 0; t < n; ++t) v += dk[k * n + t] * M(k, t, sa) * M(k, t, sb);
+      }
+    }
     if (sa == sb) v += E.Wobj[(((size_t)i * n + sa) * np + pa) * np + pb];
     if (pa == pb && pa >= 1) v += E.Wzz[(((size_t)i * K + (pa - 1)) * n + sa) * n + sb];
     if (a == b) {
       v += dw + sigx[zflat(P, i, pa, sa)];
       if (pa == 0 && chain_start(P, i)) v += d[zflat(P, i, 0, sa)];
     }
-  } else if (ka == 2 && kb == 0 && pb >= 1) {
-    v += E.Wzt[(((size_t)i * K + (pb - 1)) * n + sb) * p + sa];
+  } else if (ka == 2 && kb == 0) {
+    for (int k = 1; k <= K; ++k) {
+      if (pb != k) {
+        v += P.D[k][pb] * dk[k * n + sb] * JT[((size_t)(k - 1) * n + sb) * p + sa];
+      } else {
+        for (int t = 0; t < n; ++t)
+          v += dk[k * n + t] * JT[((size_t)(k - 1) * n + t) * p + sa] * M(k, t, sb);
+      }
+    }
+    if (pb >= 1) v += E.Wzt[(((size_t)i * K + (pb - 1)) * n + sb) * p + sa];
+  } else if (ka == 2 && kb == 2) {
+    for (int k = 1; k <= K; ++k)
+      for (int t = 0; t < n; ++t)
+        v += dk[k * n + t] * JT[((size_t)(k - 1) * n + t) * p + sa] *
+             JT[((size_t)(k - 1) * n + t) * p + sb];
+  }
+  if (ka != 2 && kb != 2 && sa == sb && chain_next(P, i)) {
+    const double ga = ka == 1 ? 1.0 : cont_coef(P, pa);
+    const double gb = kb == 1 ? 1.0 : cont_coef(P, pb);
+    v += d[zflat(P, i + 1, 0, sa)] * ga * gb;
   }
   return v;
+}
+
+// Right-looking Cholesky of the leading `cols` columns of an order-m block in
+// packed lower storage (shared or global memory); col: m doubles of shared
+// scratch.  Every thread of the block takes part.
+__device__ inline void chol_cols_packed(double* A, int m, int cols, double* col, int* flag) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+            nw = nt >> 5;
+  for (int c = 0; c < cols; ++c) {
+    if (tid == 0) {
+      const double pv = A[tri(c) + c];
+      if (!(pv > 0.0)) *flag = 1;
+      A[tri(c) + c] = sqrt(pv);
+    }
+    __syncthreads();
+    const double inv = 1.0 / A[tri(c) + c];
+    for (int r = c + 1 + tid; r < m; r += nt) {
+      const double v = A[tri(r) + c] * inv;
+      A[tri(r) + c] = v;
+      col[r] = v;
+    }
+    __syncthreads();
+    for (int r = c + 1 + warp; r < m; r += nw) {
+      const double lr = col[r];
+      double* row = A + tri(r);
+      for (int q = c + 1 + lane; q <= r; q += 32) row[q] -= lr * col[q];
+    }
+    __syncthreads();
+  }
 }
 
 // Right-looking Cholesky of the leading `cols` columns of the lower triangle
@@ -194,59 +239,50 @@ __device__ inline void chol_cols(double* A, int m, int cols, double* col, int* f
 
 // ---- factorization ----------------------------------------------------------------
 
-// Assemble element i's block of Kc and eliminate its interior.
-__global__ void __launch_bounds__(LBS) k_lifted_elem(DevProb P, DevEval E, DevLifted L,
-                                                      double* __restrict__ Gscr) {
+// Assemble element i's block of Kc (packed lower) and eliminate its interior.
+__global__ void __launch_bounds__(LBS) k_lifted_elem(DevProb P, DevEval E, DevLifted L) {
   extern __shared__ double sm[];
-  const int me = L.me, kn = L.kn, n = P.n, tid = threadIdx.x;
-  const int rows = kn + n;
+  const int me = L.me, kn = L.kn, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t msz = tri(me);
   for (int i = blockIdx.x; i < P.N; i += gridDim.x) {
-    double* A = L.elem_smem ? sm : L.blk + (size_t)i * me * me;
-    double* G = L.elem_smem ? sm + (size_t)me * me : Gscr + (size_t)blockIdx.x * rows * me;
-    double* gw = L.elem_smem ? G + (size_t)rows * me : sm;
-    double* col = gw + rows;
-    for (int idx = tid; idx < rows * me; idx += LBS) {
-      const int g = idx / me, a = idx - g * me;
-      G[idx] = g_entry(P, E, i, kn, g, a);
-    }
-    for (int g = tid; g < rows; g += LBS) gw[g] = g_weight(P, L.d, i, kn, g);
+    double* A = L.elem_smem ? sm : L.blk + (size_t)i * msz;
+    double* col = L.elem_smem ? sm + msz : sm;
+    for (int a = warp; a < me; a += LBS / 32)
+      for (int b = lane; b <= a; b += 32)
+        A[tri(a) + b] = elem_entry(P, E, L.d, L.sigx, L.dw, i, kn, a, b);
     __syncthreads();
-    for (int idx = tid; idx < me * me; idx += LBS) {
-      const int a = idx / me, b = idx - a * me;
-      if (b <= a) A[idx] = elem_entry(P, E, L.d, L.sigx, L.dw, i, kn, G, gw, me, a, b);
-    }
-    __syncthreads();
-    chol_cols(A, me, kn, col, L.flag);
+    chol_cols_packed(A, me, kn, col, L.flag);
     if (L.elem_smem) {
-      double* dst = L.blk + (size_t)i * me * me;
-      for (int idx = tid; idx < me * me; idx += LBS) dst[idx] = A[idx];
+      double* dst = L.blk + (size_t)i * msz;
+      for (size_t idx = tid; idx < msz; idx += LBS) dst[idx] = A[idx];
     }
     __syncthreads();
   }
 }
 
-__device__ inline double lower_at(const double* A, int m, int r, int c) {
-  return r >= c ? A[(size_t)r * m + c] : A[(size_t)c * m + r];
+__device__ inline double lower_at(const double* A, int r, int c) {
+  return r >= c ? A[tri(r) + c] : A[tri(c) + r];
 }
 
 // Chain blocks from the elements' frontal Schur complements.
 __global__ void __launch_bounds__(LBS) k_lifted_chain(DevProb P, DevLifted L) {
   const int i = blockIdx.x, n = P.n, p = P.p, me = L.me, kn = L.kn;
-  const double* Bi = L.blk + (size_t)i * me * me;
+  const size_t msz = tri(me);
+  const double* Bi = L.blk + (size_t)i * msz;
   const bool prev = i > 0 && chain_next(P, i - 1);
-  const double* Bp = prev ? L.blk + (size_t)(i - 1) * me * me : nullptr;
+  const double* Bp = prev ? L.blk + (size_t)(i - 1) * msz : nullptr;
   const bool next = chain_next(P, i);
   for (int idx = threadIdx.x; idx < n * n; idx += LBS) {
     const int s = idx / n, t = idx - s * n;
-    double v = lower_at(Bi, me, kn + s, kn + t);
-    if (prev) v += lower_at(Bp, me, kn + n + s, kn + n + t);
+    double v = lower_at(Bi, kn + s, kn + t);
+    if (prev) v += lower_at(Bp, kn + n + s, kn + n + t);
     L.Dg[(size_t)i * n * n + idx] = v;
-    L.Cp[(size_t)i * n * n + idx] = next ? Bi[(size_t)(kn + n + s) * me + kn + t] : 0.0;
+    L.Cp[(size_t)i * n * n + idx] = next ? Bi[tri(kn + n + s) + kn + t] : 0.0;
   }
   for (int idx = threadIdx.x; idx < n * p; idx += LBS) {
     const int s = idx / p, q = idx - s * p;
-    double v = Bi[(size_t)(kn + 2 * n + q) * me + kn + s];
-    if (prev) v += Bp[(size_t)(kn + 2 * n + q) * me + kn + n + s];
+    double v = Bi[tri(kn + 2 * n + q) + kn + s];
+    if (prev) v += Bp[tri(kn + 2 * n + q) + kn + n + s];
     L.Bd[(size_t)i * n * p + idx] = v;
   }
 }
@@ -346,7 +382,7 @@ __global__ void __launch_bounds__(LBS) k_lifted_theta_part(DevProb P, DevLifted 
   const int i0 = c * per, i1 = min(N, i0 + per);
   double v = 0.0;
   for (int i = i0; i < i1; ++i) {
-    v += L.blk[(size_t)i * me * me + (size_t)(kn + 2 * n + q1) * me + kn + 2 * n + q2];
+    v += L.blk[(size_t)i * tri(me) + tri(kn + 2 * n + q1) + kn + 2 * n + q2];
     const double* X = L.Xt + (size_t)i * n * p;
     double t = 0.0;
     for (int s = 0; s < n; ++s) t += X[s * p + q1] * X[s * p + q2];
@@ -400,15 +436,15 @@ __global__ void __launch_bounds__(LBS) k_lifted_fwd_elem(DevProb P, DevLifted L,
   const int me = L.me, kn = L.kn, n = P.n, tid = threadIdx.x;
   double* y = sm;
   for (int i = blockIdx.x; i < P.N; i += gridDim.x) {
-    const double* A = L.blk + (size_t)i * me * me;
+    const double* A = L.blk + (size_t)i * tri(me);
     for (int a = tid; a < me; a += LBS)
       y[a] = a < kn ? b[zflat(P, i, a / n + 1, a % n)] : 0.0;
     __syncthreads();
     for (int c = 0; c < kn; ++c) {
-      const double yc = y[c] / A[(size_t)c * me + c];
+      const double yc = y[c] / A[tri(c) + c];
       __syncthreads();
       if (tid == 0) y[c] = yc;
-      for (int r = c + 1 + tid; r < me; r += LBS) y[r] -= A[(size_t)r * me + c] * yc;
+      for (int r = c + 1 + tid; r < me; r += LBS) y[r] -= A[tri(r) + c] * yc;
       __syncthreads();
     }
     for (int a = tid; a < me; a += LBS) {
@@ -464,17 +500,15 @@ __global__ void __launch_bounds__(LBS) k_lifted_bcr_fwd_update(DevProb P, DevLif
   }
 }
 
-// Parameter right-hand side and solve: ct = b_theta + sum_i ue_i,theta -
-// sum_j Xt_j^T w_j, then S xt = ct by the Cholesky factor (one block).
-__global__ void __launch_bounds__(1024) k_lifted_theta_solve(DevProb P, DevLifted L,
-                                                              const double* __restrict__ b) {
-  extern __shared__ double sm[];
-  const int p = P.p, n = P.n, N = P.N, F = L.me - L.kn, tid = threadIdx.x;
-  const size_t nz = (size_t)N * P.np * n;
-  double* x = sm;
-  for (int q = tid; q < p; q += blockDim.x) {
-    double v = b[nz + q];
-    for (int i = 0; i < N; ++i) {
+// Partial sums of the parameter right-hand side over a chunk of elements /
+// chain blocks: sum_i (ue_i,theta - Xt_i^T w_i).
+__global__ void __launch_bounds__(LBS) k_lifted_theta_rhs_part(DevProb P, DevLifted L) {
+  const int p = P.p, n = P.n, N = P.N, F = L.me - L.kn;
+  const int c = blockIdx.x, per = (N + L.chunks - 1) / L.chunks;
+  const int i0 = c * per, i1 = min(N, i0 + per);
+  for (int q = threadIdx.x; q < p; q += LBS) {
+    double v = 0.0;
+    for (int i = i0; i < i1; ++i) {
       v += L.ue[(size_t)i * F + 2 * n + q];
       const double* X = L.Xt + (size_t)i * n * p;
       const double* w = L.cc + (size_t)i * n;
@@ -482,6 +516,21 @@ __global__ void __launch_bounds__(1024) k_lifted_theta_solve(DevProb P, DevLifte
       for (int s = 0; s < n; ++s) t += X[s * p + q] * w[s];
       v -= t;
     }
+    L.Spart[(size_t)c * p + q] = v;
+  }
+}
+
+// Parameter right-hand side ct = b_theta + the chunk sums in order, then
+// S xt = ct by the Cholesky factor (one block).
+__global__ void __launch_bounds__(1024) k_lifted_theta_solve(DevProb P, DevLifted L,
+                                                              const double* __restrict__ b) {
+  extern __shared__ double sm[];
+  const int p = P.p, n = P.n, N = P.N, tid = threadIdx.x;
+  const size_t nz = (size_t)N * P.np * n;
+  double* x = sm;
+  for (int q = tid; q < p; q += blockDim.x) {
+    double v = b[nz + q];
+    for (int c = 0; c < L.chunks; ++c) v += L.Spart[(size_t)c * p + q];
     x[q] = v;
   }
   __syncthreads();
@@ -541,7 +590,7 @@ __global__ void __launch_bounds__(LBS) k_lifted_back_elem(DevProb P, DevLifted L
   double* xf = sm;            // frontal solution (2n + p)
   double* t = sm + (me - kn); // interior (kn)
   for (int i = blockIdx.x; i < P.N; i += gridDim.x) {
-    const double* A = L.blk + (size_t)i * me * me;
+    const double* A = L.blk + (size_t)i * tri(me);
     const bool next = chain_next(P, i);
     for (int f = tid; f < me - kn; f += LBS) {
       double v;
@@ -553,15 +602,15 @@ __global__ void __launch_bounds__(LBS) k_lifted_back_elem(DevProb P, DevLifted L
     __syncthreads();
     for (int c = tid; c < kn; c += LBS) {
       double v = L.y[zflat(P, i, c / n + 1, c % n)];
-      for (int f = 0; f < me - kn; ++f) v -= A[(size_t)(kn + f) * me + c] * xf[f];
+      for (int f = 0; f < me - kn; ++f) v -= A[tri(kn + f) + c] * xf[f];
       t[c] = v;
     }
     __syncthreads();
     for (int c = kn - 1; c >= 0; --c) {
-      const double xc = t[c] / A[(size_t)c * me + c];
+      const double xc = t[c] / A[tri(c) + c];
       __syncthreads();
       if (tid == 0) t[c] = xc;
-      for (int r = tid; r < c; r += LBS) t[r] -= A[(size_t)c * me + r] * xc;
+      for (int r = tid; r < c; r += LBS) t[r] -= A[tri(c) + r] * xc;
       __syncthreads();
     }
     for (int c = tid; c < kn; c += LBS) dx[zflat(P, i, c / n + 1, c % n)] = t[c];
@@ -633,10 +682,8 @@ __global__ void __launch_bounds__(LBS) k_lifted_add(double* __restrict__ y,
 
 int grid_of(size_t n) { return (int)std::min<size_t>((n + LBS - 1) / LBS, 4 * 152); }
 
-size_t elem_smem_bytes(const DevProb& P, int me, int kn) {
-  const size_t rows = (size_t)kn + P.n;
-  return ((size_t)me * me + rows * me + rows + me) * sizeof(double);
-}
+// Shared memory of the element kernel: the packed block and a column.
+size_t elem_smem_bytes(int me) { return (tri(me) + me) * sizeof(double); }
 
 size_t bcr_smem_bytes(int n, int cw) { return ((size_t)n * n + (size_t)n * cw + n) * sizeof(double); }
 
@@ -659,17 +706,16 @@ static collo_status lifted_storage(collo_problem* pr) {
   DevLifted* L = &LS->V;
   L->kn = P.K * P.n;
   L->me = L->kn + 2 * P.n + P.p;
-  L->elem_smem = elem_smem_bytes(P, L->me, L->kn) <= FACTOR_SMEM_LIMIT;
-  L->grid_e = L->elem_smem ? P.N : std::min(P.N, 2 * 152);
+  L->elem_smem = elem_smem_bytes(L->me) <= FACTOR_SMEM_LIMIT;
+  L->grid_e = P.N;
   L->cw = LBS;
   while (L->cw > 32 && bcr_smem_bytes(P.n, L->cw) > FACTOR_SMEM_LIMIT) L->cw >>= 1;
   L->chunks = std::max(1, std::min(64, P.N));
   const size_t N = P.N, n = P.n, p = P.p, nx = pr->n_x, nc = pr->n_c, me = L->me;
-  const size_t rows = (size_t)L->kn + n;
   DevArena& m = LS->mem;
   L->sigx = m.alloc<double>(nx);
   L->d = m.alloc<double>(nc);
-  L->blk = m.alloc<double>(N * me * me);
+  L->blk = m.alloc<double>(N * tri((int)me));
   L->Dg = m.alloc<double>(N * n * n);
   L->Cp = m.alloc<double>(N * n * n);
   L->Xa = m.alloc<double>(N * n * n);
@@ -690,18 +736,16 @@ static collo_status lifted_storage(collo_problem* pr) {
   L->vneg = m.alloc<double>(nc);
   L->res = m.alloc<double>(nx + nc);
   L->nrm = m.alloc<double>(8);
-  double* gscr = L->elem_smem ? nullptr : m.alloc<double>((size_t)L->grid_e * rows * me);
   bool ok = L->sigx && L->d && L->blk && L->Dg && L->Cp && L->Xa && L->Xb && L->Bd && L->Xt &&
             L->S && L->Spart && L->flag && L->rx && L->rs && L->rc && L->dx && L->ds && L->dl &&
             L->ex && L->es && L->el && L->qx && L->qs && L->qc && L->y && L->ue && L->cc &&
-            L->ct && L->vneg && L->res && L->nrm && (L->elem_smem || gscr);
+            L->ct && L->vneg && L->res && L->nrm;
   if (!ok) {
     delete LS;
     set_error("out of device memory for the lifted factorization");
     return COLLO_ERR_OOM;
   }
   pr->lifted = LS;
-  pr->lifted_gscr = gscr;
   return COLLO_OK;
 }
 
@@ -728,7 +772,7 @@ cudaError_t lifted_solve_once(collo_problem* pr, const double* rx, const double*
     return e;
   const size_t sm_v = (size_t)L.me * sizeof(double);
   count_launch();
-  k_lifted_fwd_elem<<<L.grid_e, LBS, sm_v, st>>>(P, L, L.res);
+  k_lifted_fwd_elem<<<N, LBS, sm_v, st>>>(P, L, L.res);
   count_launch();
   k_lifted_chain_rhs<<<grid_of((size_t)N * n), LBS, 0, st>>>(P, L, L.res);
   int lv = 0;
@@ -740,6 +784,10 @@ cudaError_t lifted_solve_once(collo_problem* pr, const double* rx, const double*
   }
   count_launch(2);
   k_lifted_bcr_fwd<<<1, 32, 0, st>>>(P, L, 0, 1);
+  if (p > 0) {
+    count_launch();
+    k_lifted_theta_rhs_part<<<L.chunks, LBS, 0, st>>>(P, L);
+  }
   k_lifted_theta_solve<<<1, 1024, (size_t)std::max(p, 1) * sizeof(double), st>>>(P, L, L.res);
   const size_t sm_n = (size_t)n * sizeof(double);
   count_launch();
@@ -750,7 +798,7 @@ cudaError_t lifted_solve_once(collo_problem* pr, const double* rx, const double*
     k_lifted_bcr_back<<<cnt, 32, sm_n, st>>>(P, L, l, 0);
   }
   count_launch();
-  k_lifted_back_elem<<<L.grid_e, LBS, sm_v, st>>>(P, L, dx);
+  k_lifted_back_elem<<<N, LBS, sm_v, st>>>(P, L, dx);
   if ((e = launch_kkt_resid(P, pr->E, L.sigx, L.dw, 0.0, dx, nullptr, nullptr, 0.0, rc, 1.0,
                             L.res, pr->thpart, pr->npart, nullptr, pr->scal + 8, st)) != cudaSuccess)
     return e;
@@ -768,11 +816,10 @@ cudaError_t lifted_factor_kernels(collo_problem* pr, bool elem_only) {
   cudaStream_t st = pr->stream;
   const int n = P.n, p = P.p, N = P.N;
   cudaError_t e;
-  const size_t sm_e = L.elem_smem ? elem_smem_bytes(P, L.me, L.kn)
-                                  : ((size_t)L.kn + n + L.me) * sizeof(double);
+  const size_t sm_e = L.elem_smem ? elem_smem_bytes(L.me) : (size_t)L.me * sizeof(double);
   if ((e = set_smem((const void*)k_lifted_elem, sm_e)) != cudaSuccess) return e;
   count_launch();
-  k_lifted_elem<<<L.grid_e, LBS, sm_e, st>>>(P, pr->E, L, pr->lifted_gscr);
+  k_lifted_elem<<<L.grid_e, LBS, sm_e, st>>>(P, pr->E, L);
   if ((e = cudaGetLastError()) != cudaSuccess || elem_only) return e;
   count_launch();
   k_lifted_chain<<<N, LBS, 0, st>>>(P, L);

@@ -267,7 +267,6 @@ struct collo_problem {
   long long eval_count = 0;
   // lifted condensed factorization (collo_lifted_factor), allocated on first use
   collo::LiftedStore* lifted = nullptr;
-  double* lifted_gscr = nullptr;    // its element scratch when blocks exceed shared memory
   collo::DevInst inst{};            // this problem's device pointers (host copy)
   collo::Runner* self = nullptr;    // single-instance runner (batch of one)
   ~collo_problem();
