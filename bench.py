@@ -717,6 +717,19 @@ def lifted_comparison(collo, workloads, device, which="both"):
                 aug[name] = {"factor_ms": prob.time_phase(1, prec, reps=5),
                              "solve_ms": prob.time_phase(2, prec, reps=5),
                              "refinement_sweeps": ainfo["sweeps"]}
+        ipm = {}
+        if key == "config2_N400":
+            with collo.Problem(inst, device=device) as prob:
+                for name, fn in (("lifted", lambda: prob.lifted_ipm_solve(want_x=False)),
+                                 ("augmented_fp64",
+                                  lambda: prob.ipm_solve(want_x=False, precision=collo.FP64)),
+                                 ("augmented_mixed",
+                                  lambda: prob.ipm_solve(want_x=False, precision=collo.MIXED))):
+                    t0 = time.perf_counter()
+                    r = fn()
+                    dt = time.perf_counter() - t0
+                    ipm[name] = {"status": r["status"], "iterations": r["iterations"],
+                                 "wall_s": dt, "newton_steps_per_s": r["iterations"] / dt}
         fl = lifted_flops(inst.n, inst.p, inst.N, inst.K, getattr(inst, "scheme", "") == "gauss")
         ach = fl / (ms_elem * 1e-3) / 1e12
         out[key] = {"lifted": {"factor_ms": ms_fac, "elem_kernel_ms": ms_elem,
@@ -724,6 +737,7 @@ def lifted_comparison(collo, workloads, device, which="both"):
                                "residual": info["residual"], "delta_w": dw,
                                "solve_with_refinement_wall_ms": 1e3 * solve_wall},
                     "augmented": aug,
+                    **({"whole_solve_from_theta0": ipm} if ipm else {}),
                     "elem_roofline": {"bound": "alu", "achieved": ach, "peak": peak64,
                                       "unit": "TFLOP/s", "frac": ach / peak64,
                                       "algorithmic_flops": fl,

@@ -379,6 +379,25 @@ collo_status collo_lifted_solve(collo_problem* prob, const double* r_x, const do
                                 const double* r_c, double* dx, double* ds, double* dlam,
                                 int refine_max, double refine_tol, collo_solve_info* info);
 
+/* Solve the estimation problem in the lifted form: the filter line-search
+ * interior-point method of collo_ipm_solve (same constants, barrier update,
+ * inertia-correction schedule and line search, Waechter & Biegler 2006) on
+ * the relaxed problem -relax <= c(x) <= relax, with the slacks and their bound
+ * duals as bounded variables (constraint violation measured as
+ * ||c(x) - s||_1), each Newton step from collo_lifted_factor /
+ * collo_lifted_solve (FP64, refined to 1e-12 in at most 20 sweeps; a
+ * non-positive Cholesky pivot triggers the inertia correction).  States start
+ * from the collocation forward sweep at theta0 pushed into its bounds; slacks
+ * from c(x0) pushed into [-relax, relax]; multipliers 0, bound duals 1.
+ * relax > 0 (1e-8 in the library's reading of the paper's configuration).
+ * opts: tol, acceptable_tol, acceptable_iter, max_iter, max_wall_time and
+ * verbose are honoured (precision and refinement settings are not: the
+ * lifted form is FP64).  The iterate is left in the problem; result as for
+ * collo_ipm_solve (fp64_factorizations = factorizations).  Returns the
+ * solver status, or INVALID_ARG / OOM / DEVICE before the solve starts. */
+collo_status collo_lifted_ipm_solve(collo_problem* prob, const double* theta0, double relax,
+                                    const collo_ipm_options* opts, collo_result* result);
+
 /* Defaults: the paper's tolerances (relative KKT error 1e-6, acceptable 1e-4
  * for 15 iterations; Section "Optimization framework configurations"), 3000
  * iterations, a 3600 s wall cap, FP64 precision, refinement to 1e-10 in at

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcollo.so")
-SOURCES = ["api.cu", "eval.cu", "factor.cu", "ipm.cu", "lifted.cu", "profile.cu", "refine.cu",
-           "runner.cu"]
+SOURCES = ["api.cu", "eval.cu", "factor.cu", "ipm.cu", "lifted.cu", "lifted_ipm.cu", "profile.cu",
+           "refine.cu", "runner.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -144,6 +144,9 @@ def _load():
                                        C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                        C.POINTER(SolveInfo)]
     lib.collo_lifted_solve.restype = C.c_int
+    lib.collo_lifted_ipm_solve.argtypes = [P, C.c_void_p, C.c_double, C.POINTER(IpmOptions),
+                                           C.POINTER(Result)]
+    lib.collo_lifted_ipm_solve.restype = C.c_int
     lib.collo_ipm_options_default.argtypes = [C.POINTER(IpmOptions)]
     lib.collo_ipm_options_default.restype = None
     lib.collo_ipm_solve.argtypes = [P, C.c_void_p, C.POINTER(IpmOptions), C.POINTER(Result)]
@@ -493,6 +496,23 @@ class Problem:
         st = lib.collo_ipm_solve(self.h, th0.ctypes.data, C.byref(o), C.byref(res))
         # the call returns the solve's outcome, which it also stores in the result;
         # a call that failed before producing a result returns its error only
+        if st in _CALL_ERRORS or st != res.status:
+            raise ColloError(st, last_error())
+        return _result_dict(res, theta, x, lam)
+
+    def lifted_ipm_solve(self, theta0=None, relax: float = 1e-8, want_x: bool = True, **kw):
+        """collo_lifted_ipm_solve: the relaxed-equality form's interior-point solve."""
+        th0 = _host_vec(_f64(self.inst.theta0 if theta0 is None else theta0), self.p, "theta0")
+        o = self.ipm_options(**kw)
+        res = Result()
+        theta = np.zeros(self.p)
+        x = np.zeros(self.n_x) if want_x else None
+        lam = np.zeros(self.n_c) if want_x else None
+        res.theta = theta.ctypes.data
+        res.x = None if x is None else x.ctypes.data
+        res.lambda_ = None if lam is None else lam.ctypes.data
+        st = lib.collo_lifted_ipm_solve(self.h, th0.ctypes.data, float(relax), C.byref(o),
+                                        C.byref(res))
         if st in _CALL_ERRORS or st != res.status:
             raise ColloError(st, last_error())
         return _result_dict(res, theta, x, lam)

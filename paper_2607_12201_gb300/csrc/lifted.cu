@@ -40,53 +40,9 @@
 #include <cmath>
 #include <cstring>
 
-#include "problem.cuh"
+#include "lifted.cuh"
 
 namespace collo {
-
-constexpr int LBS = 256;   // threads of the lifted kernels
-
-// Device view of the lifted factorization (passed to kernels by value).
-struct DevLifted {
-  int me = 0;          // element block order Kn + 2n + p
-  int kn = 0;          // interior unknowns K n
-  int grid_e = 0;      // blocks of the element kernels
-  bool elem_smem = false;   // element blocks factored in shared memory
-  int cw = 0;          // right-hand-side columns per pass of the chain eliminations
-  int chunks = 0;      // partial sums of the parameter block
-  double dw = 0.0;
-  double* sigx = nullptr;   // [n_x]
-  double* d = nullptr;      // [n_c] Sigma_s + dw
-  double* blk = nullptr;    // [N][me (me + 1) / 2] element blocks (packed lower)
-  double* Dg = nullptr;     // [N][n][n] chain diagonal blocks, then their Cholesky factors
-  double* Cp = nullptr;     // [N][n][n] coupling of chain block i to the next active one
-  double* Xa = nullptr;     // [N][n][n] L_j^-1 (coupling to the left neighbour)
-  double* Xb = nullptr;     // [N][n][n] L_j^-1 (coupling to the right neighbour)
-  double* Bd = nullptr;     // [N][n][p] chain border
-  double* Xt = nullptr;     // [N][n][p] L_j^-1 border
-  double* S = nullptr;      // [p][p] parameter block, then its Cholesky factor
-  double* Spart = nullptr;  // [chunks][p][p]
-  int* flag = nullptr;      // [1] a pivot was not positive
-  // solve
-  double* rx = nullptr, *rs = nullptr, *rc = nullptr;   // right-hand side
-  double* dx = nullptr, *ds = nullptr, *dl = nullptr;   // solution
-  double* ex = nullptr, *es = nullptr, *el = nullptr;   // correction
-  double* qx = nullptr, *qs = nullptr, *qc = nullptr;   // residual of the unreduced system
-  double* y = nullptr;      // [n_x] condensed rhs, then interior forward values
-  double* ue = nullptr;     // [N][2n+p] element contributions to the frontal rhs
-  double* cc = nullptr;     // [N][n] chain rhs, then w, then the chain solution
-  double* ct = nullptr;     // [p] parameter rhs, then its solution
-  double* vneg = nullptr;   // [n_c]
-  double* res = nullptr;    // [n_x + n_c] output of the structured residual
-  double* nrm = nullptr;    // [8] residual norms
-};
-
-struct LiftedStore {
-  DevArena mem;
-  DevLifted V;
-  long long eval_count = -1;   // evaluation the factorization belongs to
-  bool pd = false;
-};
 
 void lifted_free(LiftedStore* L) { delete L; }
 
@@ -695,7 +651,7 @@ cudaError_t set_smem(const void* f, size_t bytes) {
 }  // namespace
 
 // Storage of the lifted factorization (allocated on the first call).
-static collo_status lifted_storage(collo_problem* pr) {
+collo_status lifted_storage(collo_problem* pr) {
   if (pr->lifted) return COLLO_OK;
   const DevProb& P = pr->P;
   if (bcr_smem_bytes(P.n, 32) > FACTOR_SMEM_LIMIT) {
@@ -867,37 +823,21 @@ collo_status lifted_time_launch(collo_problem* pr, int which) {
   return COLLO_OK;
 }
 
-}  // namespace collo
+int lifted_grid(size_t n) { return grid_of(n); }
 
-extern "C" {
-
-collo_status collo_lifted_factor(collo_problem* prob, const double* sigma_x, const double* sigma_s,
-                                 double delta_w, int* positive_definite) {
-  if (!prob || !sigma_s) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
-  if (!prob->evaluated) { set_error("collo_eval has not run"); return COLLO_ERR_NOT_EVALUATED; }
-  if (!std::isfinite(delta_w) || delta_w < 0) {
-    set_error("delta_w must be finite and >= 0"); return COLLO_ERR_INVALID_ARG;
-  }
-  COLLO_CUDA(cudaSetDevice(prob->device));
-  collo_status s = lifted_storage(prob);
-  if (s != COLLO_OK) return s;
+collo_status lifted_factor_dev(collo_problem* prob, const double* sigma_s, double dw, bool* pd) {
   LiftedStore& LS = *prob->lifted;
   DevLifted& L = LS.V;
-  const DevProb& P = prob->P;
   cudaStream_t st = prob->stream;
-  const size_t nx = prob->n_x, nc = prob->n_c;
-  const int n = P.n, p = P.p, N = P.N;
-  L.dw = delta_w;
+  const size_t nc = prob->n_c;
+  L.dw = dw;
   LS.pd = false;
   LS.eval_count = -1;
-  if (sigma_x)
-    COLLO_CUDA(cudaMemcpyAsync(L.sigx, sigma_x, nx * sizeof(double), cudaMemcpyDefault, st));
-  else
-    COLLO_CUDA(cudaMemsetAsync(L.sigx, 0, nx * sizeof(double), st));
-  COLLO_CUDA(cudaMemcpyAsync(L.d, sigma_s, nc * sizeof(double), cudaMemcpyDefault, st));
+  if (sigma_s != L.d)
+    COLLO_CUDA(cudaMemcpyAsync(L.d, sigma_s, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
   COLLO_CUDA(cudaMemsetAsync(L.flag, 0, sizeof(int), st));
   count_launch();
-  k_lifted_shift<<<grid_of(nc), LBS, 0, st>>>(L.d, delta_w, nc);
+  k_lifted_shift<<<grid_of(nc), LBS, 0, st>>>(L.d, dw, nc);
   COLLO_CUDA(lifted_factor_kernels(prob, false));
   int flag = 1;
   COLLO_CUDA(cudaMemcpyAsync(&prob->hscal[48], L.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -905,27 +845,15 @@ collo_status collo_lifted_factor(collo_problem* prob, const double* sigma_x, con
   std::memcpy(&flag, &prob->hscal[48], sizeof(int));
   LS.pd = flag == 0;
   LS.eval_count = prob->eval_count;
-  if (positive_definite) *positive_definite = LS.pd ? 1 : 0;
+  *pd = LS.pd;
   return COLLO_OK;
 }
 
-collo_status collo_lifted_solve(collo_problem* prob, const double* r_x, const double* r_s,
-                                const double* r_c, double* dx, double* ds, double* dlam,
-                                int refine_max, double refine_tol, collo_solve_info* info) {
-  if (!prob || !r_x || !r_s || !r_c || !dx || !ds || !dlam) {
-    set_error("NULL argument"); return COLLO_ERR_INVALID_ARG;
-  }
-  if (!prob->lifted || !prob->lifted->pd || prob->lifted->eval_count != prob->eval_count) {
-    set_error("no positive definite lifted factorization of the current evaluation");
-    return COLLO_ERR_NOT_FACTORED;
-  }
-  COLLO_CUDA(cudaSetDevice(prob->device));
+collo_status lifted_solve_dev(collo_problem* prob, int refine_max, double refine_tol, int* sweeps,
+                              double* relp) {
   DevLifted& L = prob->lifted->V;
   cudaStream_t st = prob->stream;
   const size_t nx = prob->n_x, nc = prob->n_c;
-  COLLO_CUDA(cudaMemcpyAsync(L.rx, r_x, nx * sizeof(double), cudaMemcpyDefault, st));
-  COLLO_CUDA(cudaMemcpyAsync(L.rs, r_s, nc * sizeof(double), cudaMemcpyDefault, st));
-  COLLO_CUDA(cudaMemcpyAsync(L.rc, r_c, nc * sizeof(double), cudaMemcpyDefault, st));
   COLLO_CUDA(lifted_solve_once(prob, L.rx, L.rs, L.rc, L.dx, L.ds, L.dl));
   int k = 0;
   double rel = 0.0;
@@ -948,8 +876,64 @@ collo_status collo_lifted_solve(collo_problem* prob, const double* r_x, const do
     k_lifted_add<<<grid_of(nc), LBS, 0, st>>>(L.dl, L.el, nc);
     ++k;
   }
-  if (info) { info->refinement_sweeps = k; info->residual = rel; }
+  if (sweeps) *sweeps = k;
+  if (relp) *relp = rel;
   if (!std::isfinite(rel)) { set_error("non-finite lifted solution"); return COLLO_ERR_NUMERIC; }
+  return COLLO_OK;
+}
+
+}  // namespace collo
+
+extern "C" {
+
+collo_status collo_lifted_factor(collo_problem* prob, const double* sigma_x, const double* sigma_s,
+                                 double delta_w, int* positive_definite) {
+  if (!prob || !sigma_s) { set_error("NULL argument"); return COLLO_ERR_INVALID_ARG; }
+  if (!prob->evaluated) { set_error("collo_eval has not run"); return COLLO_ERR_NOT_EVALUATED; }
+  if (!std::isfinite(delta_w) || delta_w < 0) {
+    set_error("delta_w must be finite and >= 0"); return COLLO_ERR_INVALID_ARG;
+  }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  collo_status s = lifted_storage(prob);
+  if (s != COLLO_OK) return s;
+  DevLifted& L = prob->lifted->V;
+  cudaStream_t st = prob->stream;
+  const size_t nx = prob->n_x, nc = prob->n_c;
+  prob->lifted->pd = false;
+  prob->lifted->eval_count = -1;
+  if (sigma_x)
+    COLLO_CUDA(cudaMemcpyAsync(L.sigx, sigma_x, nx * sizeof(double), cudaMemcpyDefault, st));
+  else
+    COLLO_CUDA(cudaMemsetAsync(L.sigx, 0, nx * sizeof(double), st));
+  COLLO_CUDA(cudaMemcpyAsync(L.d, sigma_s, nc * sizeof(double), cudaMemcpyDefault, st));
+  bool pd = false;
+  if ((s = lifted_factor_dev(prob, L.d, delta_w, &pd)) != COLLO_OK) return s;
+  if (positive_definite) *positive_definite = pd ? 1 : 0;
+  return COLLO_OK;
+}
+
+collo_status collo_lifted_solve(collo_problem* prob, const double* r_x, const double* r_s,
+                                const double* r_c, double* dx, double* ds, double* dlam,
+                                int refine_max, double refine_tol, collo_solve_info* info) {
+  if (!prob || !r_x || !r_s || !r_c || !dx || !ds || !dlam) {
+    set_error("NULL argument"); return COLLO_ERR_INVALID_ARG;
+  }
+  if (!prob->lifted || !prob->lifted->pd || prob->lifted->eval_count != prob->eval_count) {
+    set_error("no positive definite lifted factorization of the current evaluation");
+    return COLLO_ERR_NOT_FACTORED;
+  }
+  COLLO_CUDA(cudaSetDevice(prob->device));
+  DevLifted& L = prob->lifted->V;
+  cudaStream_t st = prob->stream;
+  const size_t nx = prob->n_x, nc = prob->n_c;
+  COLLO_CUDA(cudaMemcpyAsync(L.rx, r_x, nx * sizeof(double), cudaMemcpyDefault, st));
+  COLLO_CUDA(cudaMemcpyAsync(L.rs, r_s, nc * sizeof(double), cudaMemcpyDefault, st));
+  COLLO_CUDA(cudaMemcpyAsync(L.rc, r_c, nc * sizeof(double), cudaMemcpyDefault, st));
+  int k = 0;
+  double rel = 0.0;
+  collo_status s = lifted_solve_dev(prob, refine_max, refine_tol, &k, &rel);
+  if (info) { info->refinement_sweeps = k; info->residual = rel; }
+  if (s != COLLO_OK) return s;
   COLLO_CUDA(cudaMemcpyAsync(dx, L.dx, nx * sizeof(double), cudaMemcpyDefault, st));
   COLLO_CUDA(cudaMemcpyAsync(ds, L.ds, nc * sizeof(double), cudaMemcpyDefault, st));
   COLLO_CUDA(cudaMemcpyAsync(dlam, L.dl, nc * sizeof(double), cudaMemcpyDefault, st));

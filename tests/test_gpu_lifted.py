@@ -200,3 +200,55 @@ def test_lifted_solve_needs_a_current_positive_definite_factorization(collo):
         with pytest.raises(collo.ColloError) as e:
             prob.lifted_factor(sx, ss, -1.0)
         assert e.value.status == collo.ERR_INVALID_ARG
+
+
+def _lifted_compare(res, ref, inst, th_tol=1e-6):
+    assert res["status"] == ref.status
+    th_ref = ref.x[-inst.p:]
+    rel = np.max(np.abs(res["theta"] - th_ref) / np.maximum(np.abs(th_ref), 1e-12))
+    assert rel <= th_tol, (res["theta"], th_ref)
+    assert abs(res["phi"] - ref.phi) <= th_tol * max(1.0, abs(ref.phi))
+
+
+@pytest.mark.parametrize("name", ["cascade_N50", "gauss_cascade_N50"])
+def test_lifted_ipm_solve_matches_oracle(collo, name):
+    """The whole relaxed-equality interior-point solve (r = 1e-8) against the
+    oracle's on the well-identified cascade: status, iteration count, theta
+    and Phi."""
+    inst = CASES[name]()
+    ref = lifted.solve(inst)
+    with collo.Problem(inst) as prob:
+        res = prob.lifted_ipm_solve()
+    _lifted_compare(res, ref, inst)
+    assert res["iterations"] == ref.iterations
+
+
+def test_lifted_ipm_solve_on_a_network_reaches_the_oracle_objective(collo):
+    """A 4-species network whose sixth parameter is not identified (the
+    oracle's solve leaves it anywhere between -4.86 and -5.0, its bound,
+    depending on the tolerance): the lifted steps carry the forward error of
+    a matrix with Sigma_s near mu / r^2, so the two trajectories separate along
+    that direction.  Status and the objective must agree."""
+    inst = W.random_network(4, 8, n_obs=3, M=20, T=5.0, N=40, seed=41, theta0_spread=0.1)
+    ref = lifted.solve(inst)
+    with collo.Problem(inst) as prob:
+        res = prob.lifted_ipm_solve()
+    assert res["status"] == ref.status
+    assert abs(res["phi"] - ref.phi) <= 1e-5 * abs(ref.phi)
+
+
+def test_lifted_ipm_solve_status_on_config2_matches_oracle(collo):
+    """Config 2 from its theta0: the oracle's lifted solve ends in a line-search
+    failure; the GPU's ends with the same status and follows the oracle's
+    trajectory through the first iterations."""
+    inst = CASES["config2_N400"]()
+    hist = []
+    ref = lifted.solve(inst, on_iter=hist.append)
+    with collo.Problem(inst) as prob:
+        res = prob.lifted_ipm_solve()
+        k = max(1, len(hist) // 4)
+        early = prob.lifted_ipm_solve(max_iter=k)
+    assert res["status"] == ref.status
+    th_ref = hist[k - 1]["theta"]
+    rel = np.max(np.abs(early["theta"] - th_ref) / np.maximum(np.abs(th_ref), 1e-12))
+    assert rel <= 1e-6, rel
