@@ -6,8 +6,9 @@ The GPU factors Kc = W + Sigma_x + dw I + J^T (Sigma_s + dw) J by Cholesky in
 its own order (element interiors, block cyclic reduction over the chain of
 first points, parameter block) and refines against the unreduced system; the
 oracle factors the same matrix in natural block order.  Cases cover element
-blocks in shared memory and in global memory (config-3 networks), a single
-element, Gauss-Legendre K = 4 and chains cut at experimental conditions."""
+blocks in shared memory and in global memory (40 and 80 species), parameter
+blocks in shared and global memory, a single element, Gauss-Legendre K = 4 and
+chains cut at experimental conditions."""
 import dataclasses
 
 import numpy as np
@@ -38,6 +39,12 @@ CASES = {
     "gauss_n13_N20": lambda: gauss(W.random_network(13, 26, n_obs=4, M=20, T=5.0, N=20, seed=52,
                                                     theta0_spread=0.1)),
     "conditions_3x30": lambda: W.multi_condition(),
+    # element blocks of 280 and 560 unknowns (factored in global memory); the
+    # second has p = 160, so its parameter block is factored in global memory too
+    "n40_N6": lambda: W.random_network(40, 80, n_obs=8, M=40, T=5.0, N=6, seed=61,
+                                       theta0_spread=0.1),
+    "n80_N4": lambda: W.random_network(80, 160, n_obs=8, M=40, T=5.0, N=4, seed=62,
+                                       theta0_spread=0.1),
 }
 
 
@@ -101,7 +108,7 @@ def _forward_tol(ref, n_x):
     return max(1e-9, 10.0 * spread)
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", [c for c in CASES if c != "n80_N4"])
 @pytest.mark.parametrize("dw", [0.0, 1e-2])
 def test_lifted_step_matches_oracle(collo, name, dw):
     """Relaxation r = 1e-4 at a random iterate: backward error of the GPU step
@@ -116,6 +123,26 @@ def test_lifted_step_matches_oracle(collo, name, dw):
         ref = lifted.newton_direction(oprob, ev, st, 0.05, dw, opt)
     except lifted.NotPositiveDefinite:
         pytest.skip("not positive definite at this point")
+    dx, ds, dl, info = _gpu_step(collo, inst, st, ref, dw)
+    b = np.concatenate([ref["r_x"], ref["r_s"], ref["r_c"]])
+    assert _backward(ref["M"], np.concatenate([dx, ds, dl]), b) <= 1e-13, info
+    tol = _forward_tol(ref, oprob.n_x)
+    assert _rel(dx, ref["dx"]) <= tol
+    assert _rel(ds, ref["ds"]) <= tol
+    assert _rel(dl, ref["dlam"]) <= tol
+
+
+@pytest.mark.parametrize("dw", [0.1, 10.0])
+def test_lifted_step_with_parameter_block_in_global_memory(collo, dw):
+    """80 species, p = 160: element blocks of 560 unknowns and a 160 x 160
+    parameter block, both factored in global memory; small multipliers keep
+    the condensed matrix positive definite."""
+    inst = CASES["n80_N4"]()
+    oprob = OProblem(inst)
+    opt = lifted.Options(relax=1e-4)
+    st = _state(oprob, opt, 21, lam_scale=0.05)
+    ev = oprob.evaluate(st.x, st.lam)
+    ref = lifted.newton_direction(oprob, ev, st, 0.05, dw, opt)
     dx, ds, dl, info = _gpu_step(collo, inst, st, ref, dw)
     b = np.concatenate([ref["r_x"], ref["r_s"], ref["r_c"]])
     assert _backward(ref["M"], np.concatenate([dx, ds, dl]), b) <= 1e-13, info
