@@ -201,3 +201,46 @@ def test_relaxed_optimum_tends_to_the_reduced_space_optimum():
     assert gaps[1e-10] <= 1e-7
     # first order in r: ten times the relaxation, about ten times the gap
     assert 3.0 <= gaps[1e-7] / gaps[1e-8] <= 30.0
+
+
+def test_lifted_measures_are_those_of_the_slack_nlp_in_standard_form():
+    """The relaxed problem is a standard-form NLP in X = (z, theta, s) with
+    bounds on (theta, s) and constraints c(x) - s = 0.  Its scaled optimality
+    error and barrier function, computed by the pinned augmented-form
+    routines (``oracle.ipm``) on that NLP, equal the lifted routines' values."""
+    import types
+    inst = W.small_network(n=3, r=4, N=5, seed=7)
+    prob = Problem(inst)
+    opt = lifted.Options(relax=1e-3)
+    st = _state(prob, opt, 17, lam_scale=2.0)
+    ev = prob.evaluate(st.x, st.lam)
+    r, m, p = opt.r(), prob.n_c, prob.p
+    fake_inst = types.SimpleNamespace(theta_lo=np.concatenate([inst.theta_lo, np.full(m, -r)]),
+                                      theta_hi=np.concatenate([inst.theta_hi, np.full(m, r)]))
+    fake = types.SimpleNamespace(inst=fake_inst, nz=prob.nz, p=p + m, n_c=m,
+                                 n_x=prob.n_x + m)
+    X = np.concatenate([st.x, st.s])
+    ev_std = {"grad": np.concatenate([ev["grad"], np.zeros(m)]),
+              "J": sp.hstack([ev["J"], -sp.identity(m)]).tocsr(),
+              "c": ev["c"] - st.s}
+    zl = np.concatenate([st.zl, st.vl])
+    zu = np.concatenate([st.zu, st.vu])
+    for mu in (0.0, 0.07):
+        e_std = ipm.optimality_error(fake, ev_std, X, st.lam, zl, zu, mu, opt)
+        e_lift = lifted.optimality_error(prob, ev, st, mu, opt)
+        assert abs(e_std - e_lift) <= 1e-12 * max(1.0, e_std)
+        b_std = ipm.barrier_value(fake, ev["phi"], X, 0.07)
+        b_lift = lifted.barrier_value(prob, ev["phi"], st.x, st.s, 0.07, r)
+        assert abs(b_std - b_lift) <= 1e-12 * max(1.0, abs(b_std))
+
+
+def test_lifted_start_pushes_the_slacks_like_any_bounded_variable():
+    inst = W.small_network(n=3, r=4, N=5, seed=7)
+    prob = Problem(inst)
+    opt = lifted.Options(relax=1e-3)
+    st, _ = lifted.initial_point(prob, inst.theta0, opt)
+    r = opt.r()
+    c = prob.constraints(st.x)
+    assert np.array_equal(st.s, ipm.push_into_bounds(c, np.full(c.size, -r), np.full(c.size, r),
+                                                     opt))
+    assert np.all(st.vl == 1.0) and np.all(st.vu == 1.0) and not np.any(st.lam)
