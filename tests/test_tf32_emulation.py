@@ -10,7 +10,10 @@ factored in FP64 as on the GPU.  FP64 iterative refinement with the exact
 matrix then needs 1-2 sweeps from the FP32 factor to reach a relative residual
 of 1e-10, but 6 to 39 from the TF32 one, or diverges.  Every refinement sweep
 is a solve (an HBM-bound pass over the factor), and a step whose refinement
-fails is redone in FP64, so TF32 would cost more than it saves.
+fails is redone in FP64, so TF32 would cost more than it saves.  Splitting
+each operand into two TF32 parts and forming three TF32 products per update
+(hi·hi + hi·lo + lo·hi, FP32 accumulation) brings the sweeps back to the FP32
+count: FP32-accurate updates from tensor cores cost three MMAs per product.
 """
 import numpy as np
 import pytest
@@ -29,9 +32,21 @@ def to_tf32(a):
     return u.astype(np.uint32).view(np.float32)
 
 
+def split3_product(Lb, Xt):
+    """Lb @ Xt from three TF32 products (the split form a tensor core can run
+    at FP32 accuracy): hi_L hi_X + hi_L lo_X + lo_L hi_X, with hi = tf32(v) and
+    lo = tf32(v - hi), accumulated in FP32."""
+    Lh = to_tf32(Lb)
+    Ll = to_tf32(Lb - Lh)
+    Xh = to_tf32(Xt)
+    Xl = to_tf32(Xt - Xh)
+    return Lh @ Xh + Lh @ Xl + Ll @ Xh
+
+
 def static_factor(Kp, npairs, tf32):
     """L (unit lower) and block-diagonal D of the pair-by-pair elimination of the
-    permuted matrix in FP32; the trailing parameter block is left in D (FP64)."""
+    permuted matrix in FP32; the trailing parameter block is left in D (FP64).
+    tf32: False (FP32 products), True (TF32 products) or "split3"."""
     A = Kp.astype(np.float32)
     m = A.shape[0]
     L = np.eye(m)
@@ -43,7 +58,10 @@ def static_factor(Kp, npairs, tf32):
         X = A[c + 2:, c:c + 2]
         Lb = (X.astype(np.float64) @ np.linalg.inv(P)).astype(np.float32)
         L[c + 2:, c:c + 2] = Lb
-        upd = (to_tf32(Lb) @ to_tf32(X.T)) if tf32 else (Lb @ X.T)
+        if tf32 == "split3":
+            upd = split3_product(Lb, np.ascontiguousarray(X.T))
+        else:
+            upd = (to_tf32(Lb) @ to_tf32(X.T)) if tf32 else (Lb @ X.T)
         A[c + 2:, c + 2:] -= upd
         c += 2
     D[c:, c:] = A[c:, c:].astype(np.float64)
@@ -84,3 +102,6 @@ def test_tf32_schur_updates_break_fp64_refinement(make):
     ktf = refinement_sweeps(K, b, *static_factor(Kp, npairs, True), perm)
     assert k32 is not None and k32 <= 3
     assert ktf is None or ktf >= 3 * max(k32, 1)
+    # three TF32 products per update (split operands) recover the FP32 sweeps
+    k3 = refinement_sweeps(K, b, *static_factor(Kp, npairs, "split3"), perm)
+    assert k3 is not None and k3 <= k32 + 1
