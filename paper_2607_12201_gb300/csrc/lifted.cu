@@ -196,21 +196,25 @@ __device__ inline void chol_cols(double* A, int m, int cols, double* col, int* f
 // ---- factorization ----------------------------------------------------------------
 
 // Assemble element i's block of Kc (packed lower) and eliminate its interior.
-__global__ void __launch_bounds__(LBS) k_lifted_elem(DevProb P, DevEval E, DevLifted L) {
+// EBS threads: 512 for blocks above 128 unknowns (one block per SM; the
+// Cholesky's column steps are barrier-bound and more warps keep the FP64 pipe
+// busier), 256 below (two blocks per SM).
+template <int EBS>
+__global__ void __launch_bounds__(EBS) k_lifted_elem(DevProb P, DevEval E, DevLifted L) {
   extern __shared__ double sm[];
   const int me = L.me, kn = L.kn, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t msz = tri(me);
   for (int i = blockIdx.x; i < P.N; i += gridDim.x) {
     double* A = L.elem_smem ? sm : L.blk + (size_t)i * msz;
     double* col = L.elem_smem ? sm + msz : sm;
-    for (int a = warp; a < me; a += LBS / 32)
+    for (int a = warp; a < me; a += EBS / 32)
       for (int b = lane; b <= a; b += 32)
         A[tri(a) + b] = elem_entry(P, E, L.d, L.sigx, L.dw, i, kn, a, b);
     __syncthreads();
     chol_cols_packed(A, me, kn, col, L.flag);
     if (L.elem_smem) {
       double* dst = L.blk + (size_t)i * msz;
-      for (size_t idx = tid; idx < msz; idx += LBS) dst[idx] = A[idx];
+      for (size_t idx = tid; idx < msz; idx += EBS) dst[idx] = A[idx];
     }
     __syncthreads();
   }
@@ -773,9 +777,14 @@ cudaError_t lifted_factor_kernels(collo_problem* pr, bool elem_only) {
   const int n = P.n, p = P.p, N = P.N;
   cudaError_t e;
   const size_t sm_e = L.elem_smem ? elem_smem_bytes(L.me) : (size_t)L.me * sizeof(double);
-  if ((e = set_smem((const void*)k_lifted_elem, sm_e)) != cudaSuccess) return e;
   count_launch();
-  k_lifted_elem<<<L.grid_e, LBS, sm_e, st>>>(P, pr->E, L);
+  if (L.me > 128) {
+    if ((e = set_smem((const void*)k_lifted_elem<512>, sm_e)) != cudaSuccess) return e;
+    k_lifted_elem<512><<<L.grid_e, 512, sm_e, st>>>(P, pr->E, L);
+  } else {
+    if ((e = set_smem((const void*)k_lifted_elem<256>, sm_e)) != cudaSuccess) return e;
+    k_lifted_elem<256><<<L.grid_e, 256, sm_e, st>>>(P, pr->E, L);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess || elem_only) return e;
   count_launch();
   k_lifted_chain<<<N, LBS, 0, st>>>(P, L);
