@@ -13,7 +13,7 @@ constexpr int LBS = 256;   // threads of the lifted kernels
 struct DevLifted {
   int me = 0;          // element block order Kn + 2n + p
   int kn = 0;          // interior unknowns K n
-  int grid_e = 0;      // blocks of the element kernels
+  int grid_e = 0;      // blocks of the element kernels (one per element)
   bool elem_smem = false;   // element blocks factored in shared memory
   int cw = 0;          // right-hand-side columns per pass of the chain eliminations
   int chunks = 0;      // partial sums of the parameter block
@@ -28,7 +28,9 @@ struct DevLifted {
   double* Bd = nullptr;     // [N][n][p] chain border
   double* Xt = nullptr;     // [N][n][p] L_j^-1 border
   double* S = nullptr;      // [p][p] parameter block, then its Cholesky factor
-  double* Spart = nullptr;  // [chunks][p][p]
+  double* Spart = nullptr;  // [chunks][p][p] + p: partial sums of the parameter block, of
+                            // its right-hand side ([chunks][p]) and the scratch row of its
+                            // Cholesky in global memory
   int* flag = nullptr;      // [1] a pivot was not positive
   // solve
   double* rx = nullptr, *rs = nullptr, *rc = nullptr;   // right-hand side
