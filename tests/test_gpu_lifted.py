@@ -279,3 +279,19 @@ def test_lifted_ipm_solve_status_on_config2_matches_oracle(collo):
     th_ref = hist[k - 1]["theta"]
     rel = np.max(np.abs(early["theta"] - th_ref) / np.maximum(np.abs(th_ref), 1e-12))
     assert rel <= 1e-6, rel
+
+
+def test_lifted_ipm_solve_with_experimental_conditions(collo):
+    """Three experimental conditions (chains cut at each condition's first
+    element, theta shared): status, objective and theta within the
+    tolerance's ball (the oracle's own theta moves by 2e-5 between tolerances
+    1e-6 and 1e-8 here), iteration count within two."""
+    inst = CASES["conditions_3x30"]()
+    ref = lifted.solve(inst)
+    with collo.Problem(inst) as prob:
+        res = prob.lifted_ipm_solve()
+    assert res["status"] == ref.status
+    assert abs(res["phi"] - ref.phi) <= 1e-6 * abs(ref.phi)
+    th_ref = ref.x[-inst.p:]
+    assert np.max(np.abs(res["theta"] - th_ref) / np.abs(th_ref)) <= 1e-4
+    assert abs(res["iterations"] - ref.iterations) <= 2
