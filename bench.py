@@ -107,6 +107,8 @@ def parse_args():
                          "rows, factored in the global slab)")
     ap.add_argument("--only-serve", type=int, default=0,
                     help="run this many server steps of the stream and exit (ncu launch list)")
+    ap.add_argument("--only-next", action="store_true",
+                    help="run the conditions batch and the refinement loop and exit")
     ap.add_argument("--only-lifted", action="store_true",
                     help="run the lifted vs augmented step comparison and exit")
     ap.add_argument("--lifted-case", default="both", choices=["both", "config2", "config3"],
@@ -514,10 +516,13 @@ def run_ours(args):
     # instances at their initial points, and their rooflines
     out.update(kernel_rooflines(collo, insts[:S], local, per_step, clk))
     if not args.no_extra:
-        out.update(config2_multistart(collo, workloads, local))
-        out.update(config2_multistart(collo, workloads, local, scheme="gauss"))
-        out.update(poisson_stream(collo, workloads, local, budget))
-        out.update(lifted_comparison(collo, workloads, local))
+        out.update(guarded("config2_multistart", config2_multistart, collo, workloads, local))
+        out.update(guarded("config2_multistart_gauss_k4", config2_multistart, collo, workloads,
+                           local, "gauss"))
+        out.update(guarded("poisson_stream", poisson_stream, collo, workloads, local, budget))
+        out.update(guarded("lifted_vs_augmented", lifted_comparison, collo, workloads, local))
+        out.update(guarded("conditions_and_refinement", conditions_and_refinement, collo,
+                           workloads, local))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(insts)
     if rank == 0:
@@ -750,6 +755,56 @@ def lifted_comparison(collo, workloads, device, which="both"):
     return {"lifted_vs_augmented": out}
 
 
+def conditions_and_refinement(collo, workloads, device):
+    """Beside the headline: a batch of multistart solves of the three-condition
+    network (chains cut at each condition's first element, theta shared), and
+    the batched mesh-refinement loop over config-2 starts from N = 100."""
+    out = {}
+    inst = workloads.multi_condition()
+    starts = workloads.multistart_thetas(inst, 32, seed=2003)
+    probs = [collo.Problem(inst, device=device) for _ in starts]
+    t0 = time.perf_counter()
+    res = collo.batch_solve(probs, theta0s=starts, precision=collo.MIXED, tol=TOL)
+    dt = time.perf_counter() - t0
+    for p in probs:
+        p.close()
+    its = sum(r["iterations"] for r in res)
+    conv = sum(1 for r in res if r["status"] in (collo.OK, collo.ACCEPTABLE))
+    out["conditions_batch"] = {
+        "newton_steps_per_s": its / dt, "converged_solves_per_s": conv / dt, "solves": len(res),
+        "converged": conv, "wall_s": dt,
+        "what": "32 starts (theta_true + U[-0.1, 0.1]) of a 6-species network measured under "
+                "3 experimental conditions (N = 30 per condition), one batched solve (mixed)"}
+    c2 = workloads.config2(N=100)
+    starts = workloads.multistart_thetas(c2, 16, seed=2004)
+    probs = [collo.Problem(c2, device=device) for _ in starts]
+    t0 = time.perf_counter()
+    res, finals, levels = collo.refine_solve(probs, theta0s=starts, defect_tol=1e-6,
+                                             max_levels=2, precision=collo.MIXED, tol=TOL)
+    dt = time.perf_counter() - t0
+    fin_N = [f.N for f in finals]
+    for f, p in zip(finals, probs):
+        if f is not p:
+            f.close()
+    for p in probs:
+        p.close()
+    out["refinement_loop"] = {
+        "wall_s": dt, "solves": len(res), "levels": levels, "final_N": fin_N,
+        "converged": sum(1 for r in res if r["status"] in (collo.OK, collo.ACCEPTABLE)),
+        "what": "16 config-2 starts from N = 100: batched solve, then every converged solve "
+                "whose collocation defect exceeds 1e-6 re-solved on twice the elements, warm "
+                "started, up to two levels (collo_refine_solve, mixed)"}
+    return out
+
+
+def guarded(name, fn, *a):
+    """An extra measurement that cannot take the benchmark line down with it."""
+    try:
+        return fn(*a)
+    except Exception as e:   # reported in the line instead
+        return {name: {"error": f"{type(e).__name__}: {e}"}}
+
+
 def poisson_stream(collo, workloads, device, budget):
     """Requests of the serving-stream shape at their stated sizes (n log-uniform
     on [5, 100], N on [200, 5000]) arriving at 200 per second, served for a
@@ -937,7 +992,12 @@ def phase_profile(args):
 
 def main():
     args = parse_args()
-    if args.only_lifted:
+    if args.only_next:
+        from paper_2607_12201_gb300 import build as B
+        B.build()
+        from paper_2607_12201_gb300 import collo, workloads
+        print(json.dumps(conditions_and_refinement(collo, workloads, 0)), flush=True)
+    elif args.only_lifted:
         from paper_2607_12201_gb300 import build as B
         B.build()
         from paper_2607_12201_gb300 import collo, workloads
